@@ -1,0 +1,136 @@
+"""ORACLE — offline ROM construction (Algorithm 1 offline, lines 1-6).
+
+Writes data/rom_<name>.npz for the synthetic workloads: seeded training load
+paths -> full-order FE solves on the parent mesh (Sec. 2) -> POD of the
+fluctuation (V^p) and of the weighted stress (L^2) -> ECM points and weights
+(Sec. 3.2) -> basis gradients G_i = dphi_j/dX^p at the selected points.  The
+geometric map Gmu_k at the points comes from the seeded input generator.
+Every stored value is produced by this script from oracle code only.
+
+usage: python -m oracle.build_roms c1 [c2 c3 ...]
+"""
+import os
+import sys
+import time
+
+import numpy as np
+
+from . import fe, reduction
+from paper_2307_16894_gb300 import inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+DATA = os.path.join(ROOT, "data")
+
+MATRIX = dict(E=70e3, nu=0.3, law="power", s0=100.0, k=10.0, p=0.2)      # sigma_y = 100 (1 + 10 xi)^0.2
+INCLUSION = dict(E=700e3, nu=0.3, law="power", s0=np.inf, k=0.0, p=1.0)  # elastic, stiffness ratio 10
+
+VOID_R = 0.275           # parent void radius (2D family)
+INCL_R = 0.25            # parent inclusion radius (3D family)
+
+
+def phase_2d(c):
+    return -1 if np.hypot(c[0] - 0.5, c[1] - 0.5) < VOID_R else 0
+
+
+def phase_3d(c):
+    return 1 if np.linalg.norm(np.asarray(c) - 0.5) < INCL_R else 0
+
+
+CONFIGS = {
+    # 2D 16x16 Q4, void, n=8, m=40, L=20, three 20-step training paths (seeds 1001-1003), map seed 7
+    "c1": dict(d=2, N=16, n=8, m=40, L=20, map_seed=7, phases=[MATRIX],
+               train=[("u2d", 1001 + i, 20) for i in range(3)], mu_range=(0.2, 0.35)),
+    # 2D 64x64 Q4, same void, n=24 (32 modes kept for truncation), m=160, five 25-step paths
+    "c2": dict(d=2, N=64, n=32, n_use=24, m=160, L=20, map_seed=7, phases=[MATRIX],
+               train=[("stretch", 2001 + i, 25) for i in range(5)], mu_range=(0.2, 0.35)),
+    # 3D 24^3 hex8, spherical elastic inclusion (stiffness ratio 10), n=64 (96 kept), m=600
+    "c3": dict(d=3, N=24, n=96, n_use=64, m=600, L=20, map_seed=11, phases=[MATRIX, INCLUSION],
+               train=[("stretch", 3001 + i, 20) for i in range(6)], mu_range=(0.15, 0.35)),
+}
+
+
+def build(name, verbose=True, nthreads=None):
+    cfg = CONFIGS[name]
+    d, N = cfg["d"], cfg["N"]
+    t0 = time.time()
+    mesh = fe.Mesh(d, N, phase_2d if d == 2 else phase_3d)
+    npar = 1 if d == 2 else 3
+    modes = inputs.map_modes(d, npar, cfg["map_seed"])
+    Gq = inputs.map_gradients(modes, mesh.X.reshape(-1, d))              # [nq, d, d, npar]
+    if verbose:
+        print("[%s] mesh ne=%d ndof=%d nq=%d" % (name, mesh.ne, mesh.ndof, mesh.nq), flush=True)
+    snaps_w, snaps_W, train_info = [], [], []
+    for kind, seed, nst in cfg["train"]:
+        rng = np.random.default_rng(seed)
+        mu = rng.uniform(*cfg["mu_range"], size=npar)
+        coef = inputs.map_coefficients(d, mu)
+        Finv, J = fe.geometry(Gq, coef)
+        if kind == "u2d":
+            path = inputs.training_path_2d(seed, nst)
+        else:
+            path = inputs.stretch_path(d, seed, nst, rotate=False)
+        t1 = time.time()
+        out = fe.solve_path(mesh, cfg["phases"], Finv, J, path, nthreads=nthreads, verbose=verbose)
+        snaps_w += out["w"]
+        snaps_W += out["W"]
+        train_info.append(dict(seed=seed, mu=mu, steps=nst, Pbar_last=out["Pbar"][-1]))
+        if verbose:
+            print("[%s] training path seed %d done in %.1fs" % (name, seed, time.time() - t1), flush=True)
+    n, L, m = cfg["n"], cfg["L"], cfg["m"]
+    Phi, lam_w, MV = reduction.displacement_pod(mesh, snaps_w, n)
+    Bm, lam_W = reduction.stress_pod(mesh, snaps_W, L)
+    gradPhi = reduction.basis_gradients(mesh, Phi)                     # [nq, d, d, n]
+    wq = np.tile(mesh.gw, mesh.ne)
+    n_use = cfg.get("n_use", n)
+    Fint = reduction.ecm_integrands(gradPhi[..., :n_use], Bm)
+    t1 = time.time()
+    sel, wsel, err = reduction.ecm_greedy(Fint, wq, m)
+    if verbose:
+        print("[%s] ECM m=%d err=%.3e (%.1fs); sum w=%.6f vs %.6f" % (name, m, err, time.time() - t1,
+                                                                     wsel.sum(), wq.sum()), flush=True)
+    rom = pack(mesh, cfg, modes, Gq, gradPhi, sel, wsel, err, n_use)
+    rom.update(dict(lam_w=lam_w[:n], lam_W=lam_W[:L], n_snap=len(snaps_w)))
+    os.makedirs(DATA, exist_ok=True)
+    np.savez_compressed(os.path.join(DATA, "rom_%s.npz" % name), **rom)
+    # the full set of basis gradients at all Gauss points is kept out of the repo; the
+    # truncated (ragged) variants are refit from it by build_variant()
+    np.savez(os.path.join(ROOT, "oracle", "_build", "offline_%s.npz" % name),
+             gradPhi=gradPhi, Bm=Bm, wq=wq, el_phase=mesh.el_phase, X=mesh.X.reshape(-1, d), Gq=Gq)
+    if verbose:
+        print("[%s] done in %.1fs" % (name, time.time() - t0), flush=True)
+    return rom
+
+
+def pack(mesh, cfg, modes, Gq, gradPhi, sel, wsel, err, n_use):
+    d = mesh.d
+    G = gradPhi[sel][..., :n_use].reshape(len(sel), d * d, n_use)
+    phase = mesh.el_phase[sel // mesh.ngp]
+    phases = cfg["phases"]
+    Gmu = Gq[sel].reshape(len(sel), d * d, -1)
+    s0 = min(p["s0"] for p in phases)
+    tol_abs = 1e-12 * float(np.sum(wsel * np.linalg.norm(G.reshape(len(sel), -1), axis=1))) * s0
+    return dict(d=d, n=n_use, m=len(sel), G=G, w=wsel, phase=phase.astype(np.int32), qp_index=sel,
+                X=mesh.X.reshape(-1, d)[sel], Gmu=Gmu, omega=1.0, ecm_err=err, tol_abs=tol_abs,
+                ph_E=np.array([p["E"] for p in phases]), ph_nu=np.array([p["nu"] for p in phases]),
+                ph_law=np.array([1 if p["law"] == "power" else 0 for p in phases], np.int32),
+                ph_s0=np.array([p["s0"] for p in phases]), ph_k=np.array([p["k"] for p in phases]),
+                ph_p=np.array([p["p"] for p in phases]), map_seed=cfg["map_seed"], N=cfg["N"])
+
+
+def load(path):
+    """npz -> dict used by the oracle and by the CUDA binding"""
+    z = np.load(path)
+    rom = {k: z[k] for k in z.files}
+    for k in ("d", "n", "m", "N", "map_seed"):
+        rom[k] = int(rom[k])
+    rom["omega"] = float(rom["omega"])
+    rom["tol_abs"] = float(rom["tol_abs"])
+    rom["phases"] = [dict(E=float(E), nu=float(nu), law="power" if law == 1 else "linear", s0=float(s0), k=float(k),
+                          p=float(p)) for E, nu, law, s0, k, p in
+                     zip(rom["ph_E"], rom["ph_nu"], rom["ph_law"], rom["ph_s0"], rom["ph_k"], rom["ph_p"])]
+    return rom
+
+
+if __name__ == "__main__":
+    for nm in sys.argv[1:]:
+        build(nm)
