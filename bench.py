@@ -1,0 +1,292 @@
+"""Throughput of the hyper-reduced RVE load step on GB300.
+
+One bench "step" = one load step of the whole hot path for every instance of
+the batch: geometry, kinematics, FP64 return map, tangent, force and
+stiffness assembly, Newton with line search, effective stress and stiffness,
+history commit (all Newton iterations included).  Metric: macro-point ROM
+load-steps/s = instances x load steps / time.
+
+Default workload: 4096 macro points of the 2D plane-strain porous RVE family
+(64x64 Q4 parent mesh, POD n = 24, ECM m = 160), each with its own seeded
+geometry mu in [0.2, 0.35] and its own seeded 50-step load path (principal
+stretches 0.9-1.15, random axes and rotation); FP64 path.
+
+usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                       [--workload c2|c3] [--precision fp64|fp32] [--start plain|prev]
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz (unit count and clock of the recipe)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3"])
+    ap.add_argument("--precision", default=None, choices=["fp64", "fp32"])
+    ap.add_argument("--start", default="prev", choices=["plain", "prev"])
+    ap.add_argument("--batch", type=int, default=None, help="override the batch size (testing)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=clocks.sm,clocks.max.sm,power.draw,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def load_workload(args, first=0, B=None):
+    from paper_2307_16894_gb300 import workload
+    B = B or args.batch
+    rom, mu, coef, paths = workload.batch(args.workload, B=B, first=first)
+    return rom, mu, coef, paths
+
+
+def solver_opts(args, rom):
+    prec = args.precision or ("fp64" if args.workload == "c2" else "fp32")
+    tol_rel = 1e-10 if prec == "fp64" else 1e-9
+    max_iter = 25 if prec == "fp64" else 50
+    return prec, dict(tol_rel=tol_rel, tol_abs=rom["tol_abs"], max_iter=max_iter, max_ls=6, precision=prec,
+                      start=args.start, polar_split=True, want_abar=True)
+
+
+def flush_l2(buf):
+    buf.add_(1.0)
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2307_16894_gb300 import binding
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    from paper_2307_16894_gb300 import workload
+    B_total = args.batch or workload.WORKLOADS[args.workload]["B"]
+    # weak scaling: every rank solves its own B instances (seeds offset by rank)
+    rom, mu, coef, paths = load_workload(args, first=rank * B_total, B=B_total)
+    B = len(coef)
+    d = rom["d"]
+    nsteps = paths.shape[1]
+    W, K = args.warmup, args.steps
+    if W + K > nsteps:
+        raise SystemExit("warmup + steps must be <= %d load steps" % nsteps)
+    prec, kw = solver_opts(args, rom)
+    stream = torch.cuda.current_stream()
+    ctx = binding.Context(d, dev, stream.cuda_stream)
+    ctx.load_basis(rom["G"])
+    ctx.load_cubature(rom["w"], rom["phase"], rom["phases"], rom["omega"])
+    ctx.set_geometry(rom["Gmu"], coef)
+    st = ctx.state_create(B)
+    opts = binding.make_opts(**kw)
+    Fd = torch.from_numpy(np.ascontiguousarray(paths.transpose(1, 0, 2, 3))).to("cuda")    # [steps, B, d, d]
+    Pd = torch.empty((B, d, d), dtype=torch.float64, device="cuda")
+    Ad = torch.empty((B, d * d, d * d), dtype=torch.float64, device="cuda")
+    Id = torch.empty((B, binding.INFO_DTYPE.itemsize), dtype=torch.uint8, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > 129 MB L2
+    for k in range(W):
+        ctx.step_device(st, opts, Fd[k], Pd, Ad, Id)
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    clocks = Clocks(dev)
+    clocks.start()
+    ctx.profile(1)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    infos = []
+    torch.cuda.synchronize()
+    for k in range(K):
+        flush_l2(flush)
+        ev[k][0].record(stream)
+        ctx.step_device(st, opts, Fd[W + k], Pd, Ad, Id)
+        ev[k][1].record(stream)
+        infos.append(Id.clone())
+    torch.cuda.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile(0)
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    info = np.frombuffer(torch.cat(infos).cpu().numpy().tobytes(), dtype=binding.INFO_DTYPE)
+    n_ok = int((info["status"] == 0).sum())
+    value = B * world * K / (ms / 1e3)
+    # dominant kernel roofline (FP64-bound assembly or constitutive)
+    groups = {k: v for k, v in prof.items()}
+    dom = max(groups, key=lambda g: groups[g][0])
+    launches = sum(v[1] for v in groups.values())
+    res = dict(value=value, ms=ms, n_ok=n_ok, n_total=len(info), iters_mean=float(info["iters"].mean()),
+               evals_mean=float(info["evals"].mean()), prof=groups, dom=dom, launches=launches, clocks=clk,
+               prec=prec, B=B, W=W, K=K)
+    # end-to-end through the public host-buffer call (H2D of Fbar, D2H of Pbar, Abar, info each step)
+    if not args.no_e2e:
+        st2 = ctx.state_create(B)
+        ctx.sync()
+        for k in range(W):
+            ctx.step(st2, opts, paths[:, k])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(K):
+            ctx.step(st2, opts, paths[:, W + k])
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        res["e2e"] = dict(value=B * world * K / te, unit="macro-point load-steps/s",
+                          h2d_bytes_per_step=B * d * d * 8,
+                          d2h_bytes_per_step=B * (d * d + d ** 4) * 8 + B * binding.INFO_DTYPE.itemsize)
+        st2.close()
+    st.close()
+    ctx.close()
+    return res
+
+
+def cpu_baseline(args, n_inst=None, n_steps=None, budget_s=20.0):
+    """The FP64 oracle (as it stands) on the host cores, on a bounded sample of the workload:
+    the first n_inst instances over the first n_steps load steps."""
+    import oracle
+    from paper_2307_16894_gb300 import workload  # noqa: F401
+    rom, mu, coef, paths = load_workload(args, B=n_inst or (64 if args.workload == "c2" else 8))
+    B = len(coef)
+    d, n, m = rom["d"], rom["n"], rom["m"]
+    Gmu = rom["Gmu"].reshape(m, d, d, -1)
+    Fm = np.eye(d)[None, None] + np.einsum("iack,bk->biac", Gmu, coef)
+    Finv, J = np.linalg.inv(Fm), np.abs(np.linalg.det(Fm))
+    q = np.zeros((B, n))
+    Fp = np.tile(np.eye(3), (B, m, 1, 1)).copy()
+    xi = np.zeros((B, m))
+    prec, kw = solver_opts(args, rom)
+    nthreads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    done = 0
+    for k in range(paths.shape[1]):
+        oracle.rom_batch(rom, Finv, J, paths[:, k], q, Fp, xi, 1e-10, rom["tol_abs"], 25, max_ls=6,
+                         nthreads=nthreads)
+        done += 1
+        if (n_steps and done >= n_steps) or time.perf_counter() - t0 > budget_s:
+            break
+    t = time.perf_counter() - t0
+    return dict(value=B * done / t, unit="macro-point load-steps/s", cores=nthreads, kind="oracle",
+                sample="%d instances x first %d load steps of the %s workload (%.1f s)" % (B, done, args.workload, t))
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    metric = "macro-point ROM load-steps/s"
+    unit = "macro-point load-steps/s"
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        cb = cpu_baseline(args, budget_s=max(5.0, 60.0 / max(args.steps + args.warmup, 1)))
+        line = dict(metric=metric, value=cb["value"], unit=unit, n_gpus=args.gpus, steps=args.steps,
+                    warmup=args.warmup, impl="reference", higher_is_better=True, scaling="weak",
+                    vs_baseline=None, dtype="f64", data="synthetic",
+                    config=dict(workload=args.workload), cpu_baseline=cb,
+                    e2e=dict(value=cb["value"], unit=unit, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+        print(json.dumps(line))
+        return
+    r = run_ours(args, rank, world)
+    if rank != 0:
+        return
+    peaks = {}
+    if os.path.exists(PEAKS_FILE):
+        peaks = json.load(open(PEAKS_FILE))
+    ms_dom, ln_dom, fl_dom = r["prof"][r["dom"]]
+    if r["dom"] in ("assemble", "constitutive", "solve") and fl_dom > 0:
+        achieved = fl_dom / (ms_dom / 1e3) / 1e12
+        roof = dict(kernel=r["dom"], bound="alu", achieved=achieved, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
+                    frac=achieved / FP64_PEAK_TFLOPS, traffic=None, peak_source="FP64 FMA pipe: 152 SM x 2 DFMA/clk x 2.07 GHz",
+                    share=ms_dom / sum(v[0] for v in r["prof"].values()))
+    else:
+        roof = dict(kernel=r["dom"], bound="alu", achieved=None, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s", frac=None,
+                    traffic=None)
+    wl = {"c2": "2D porous RVE 64x64 Q4, n=24, m=160, B=4096, 50-step paths",
+          "c3": "3D inclusion RVE 24^3 hex8, n=64, m=600, B=16384, 50-step paths"}[args.workload]
+    line = dict(metric=metric, value=r["value"], unit=unit, n_gpus=world, steps=args.steps, warmup=args.warmup,
+                ms_per_step=r["ms"] / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f64" if r["prec"] == "fp64" else "f64+f32", data="synthetic",
+                config=dict(workload=wl, B_per_gpu=r["B"], precision=r["prec"], start=args.start,
+                            l2="flushed between timed steps (256 MB write)", converged=r["n_ok"],
+                            total=r["n_total"], newton_iters_mean=r["iters_mean"], evals_mean=r["evals_mean"]),
+                roofline=roof, clocks=r["clocks"], gpu_launches=int(r["launches"]),
+                kernels={k: dict(ms=v[0], launches=v[1], gflop=v[2] / 1e9) for k, v in r["prof"].items()})
+    if "e2e" in r:
+        line["e2e"] = r["e2e"]
+    if not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(args)
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,174 @@
+/*
+ * podecm.h -- C ABI of the GB300 hyper-reduced RVE solver.
+ *
+ * The library solves, for a batch of B independent macro points ("instances"),
+ * one load step of the hyper-reduced (POD + empirical cubature) micro problem
+ * of Guo, Rokos & Veroy, "A reduced order model for geometrically
+ * parameterized two-scale simulations of elasto-plastic microstructures under
+ * large deformations" (arXiv 2307.16894):
+ *
+ *   f_j(a)  = sum_i w_i J_i G_i^T vec(P_i F_mu,i^-T)            Eq. forcevector_ecm
+ *   K_jk(a) = sum_i w_i J_i (G_i F_mu^-1)_j : A_i : (G_i F_mu^-1)_k  Eq. stiffnessmatrix_ecm
+ *   K da = -f, a += da until ||f|| <= tol                       Eq. red_newton
+ *   Pbar = |Omega|^-1 sum_i w_i J_i P_i                          Eq. eff_stress_1
+ *   Abar from the d^2 reduced tangent problems                   Eqs. tangent_problem_red, eff_stiffness_1
+ *
+ * with F_i = Fbar + (G_i a) F_mu,i^-1 and the finite-strain J2 material of
+ * Appendix A (multiplicative split, exponential map, log strain, isotropic
+ * hardening).  Everything runs in the library's own CUDA kernels on one GPU.
+ *
+ * Conventions
+ *  - d = 2 (plane strain, F33 = 1) or 3.  Second-order tensors are row-major:
+ *    vec(T)[a*d + r] = T_ar.  Fourth-order tensors A[(a*d+b)*d*d + c*d+e] =
+ *    dP_ab / dF_ce.
+ *  - All host pointers are owned by the caller; the library copies what it
+ *    keeps.  Device pointers passed to *_device calls are owned by the caller
+ *    and must stay valid until the context's stream has passed the call.
+ *  - Every call returns a rom_status; no exception crosses the ABI.  The text
+ *    of the last error of a context is returned by rom_last_error.
+ *    Per-instance solver failures do not fail a call: the call returns ROM_OK
+ *    and the failure is reported in rom_step_info.status of that instance,
+ *    whose history is then left at the last converged step.
+ *  - A context is bound to one device and one CUDA stream and is not
+ *    thread-safe; use one context per host thread.
+ */
+#ifndef PODECM_H
+#define PODECM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rom_ctx rom_ctx;      /* library-owned: model data, device buffers, stream */
+typedef struct rom_state rom_state;  /* library-owned: per-instance reduced coordinates and history */
+
+typedef enum {
+    ROM_OK = 0,
+    ROM_E_ARG = 1,            /* invalid argument (sizes, pointers, det F_mu <= 0, ...) */
+    ROM_E_STATE = 2,          /* call out of order (e.g. step before basis/cubature/geometry) */
+    ROM_E_CUDA = 3,           /* a CUDA runtime call failed */
+    ROM_E_NOMEM = 4,          /* device or host allocation failed */
+    ROM_E_NOT_CONVERGED = 5,  /* per-instance status: Newton hit max_iter */
+    ROM_E_NONFINITE = 6       /* per-instance status: non-finite residual, singular K, det F <= 0 */
+} rom_status;
+
+enum { ROM_HARD_LINEAR = 0, ROM_HARD_POWER = 1 };
+enum { ROM_PREC_FP64 = 0, ROM_PREC_FP32 = 1, ROM_PREC_TF32 = 2, ROM_PREC_BF16 = 3 };
+enum { ROM_START_PLAIN = 0, ROM_START_PREV = 1, ROM_START_MLP = 2 };
+
+/* Material phase (Appendix A, Eqs. j2_1 - j2_10).
+ * hard_law = ROM_HARD_LINEAR: sigma_y(xi) = s0 + H_or_k * xi
+ * hard_law = ROM_HARD_POWER : sigma_y(xi) = s0 * (1 + H_or_k * xi)^p
+ * s0 = +inf makes the phase purely elastic. */
+typedef struct {
+    double E, nu;
+    int32_t hard_law;
+    double s0, H_or_k, p;
+} rom_phase;
+
+/* Solver options for one load step.
+ *  converged iff ||f||_2 <= max(tol_rel * ||f(a0)||_2, tol_abs), a0 = start iterate
+ *  (Sec. 2.1 stop rule ||f|| <= eps_newton, made relative);
+ *  max_iter: accepted Newton updates before ROM_E_NOT_CONVERGED;
+ *  max_ls: backtracking halvings of an update whose residual norm does not
+ *          decrease (0 = the plain Newton of Eq. red_newton);
+ *  precision: ROM_PREC_FP64 -- everything in FP64;
+ *             ROM_PREC_FP32/TF32/BF16 -- residual, kinematics, return map,
+ *             eigen log/exp and the n x n solve in FP64; the tangent and the
+ *             stiffness contraction K in FP32 CUDA cores / TF32 / BF16 tensor
+ *             cores with FP32 accumulation (an inexact-Newton Jacobian; the
+ *             converged answer still satisfies the FP64 residual test);
+ *  start: ROM_START_PLAIN a0 = a_n; ROM_START_PREV a0 = a_n + (a_n - a_{n-1});
+ *         ROM_START_MLP a0 = a_n + MLP prediction (see rom_mlp_load);
+ *  polar_split: 1 = solve on Ubar of Fbar = Rbar Ubar and rotate back (Sec. 4);
+ *  want_abar: 1 = compute the effective stiffness. */
+typedef struct {
+    double tol_rel, tol_abs;
+    int32_t max_iter;
+    int32_t max_ls;
+    int32_t precision;
+    int32_t start;
+    int32_t polar_split;
+    int32_t want_abar;
+} rom_opts;
+
+/* Per-instance result of a step. */
+typedef struct {
+    int32_t iters;    /* accepted Newton updates */
+    int32_t evals;    /* residual evaluations after the first (line-search trials included) */
+    int32_t status;   /* ROM_OK, ROM_E_NOT_CONVERGED or ROM_E_NONFINITE */
+    int32_t n_yield;  /* cubature points that yielded in the accepted state */
+    double res0, res; /* ||f|| at the start iterate and at exit */
+} rom_step_info;
+
+/* Create a context for dimension dim (2 or 3) on CUDA device `device`, issuing
+ * all work on `cuda_stream` (a cudaStream_t; NULL = a new stream owned by the
+ * context).  *ctx is set to NULL on failure. */
+rom_status rom_create(rom_ctx **ctx, int dim, int device, void *cuda_stream);
+rom_status rom_destroy(rom_ctx *ctx);
+
+/* POD basis gradients at the cubature points (Sec. 3.1, Eq. pod_disp):
+ * G[m][d*d][n], G[i][a*d+r][j] = d phi_j,a / d X^p_r at point i.  Host, copied.
+ * 1 <= n <= 128, 1 <= m. */
+rom_status rom_load_basis(rom_ctx *ctx, int n, int m, const double *G);
+
+/* Empirical cubature rule (Sec. 3.2, Eq. integral_ecm): positive weights w[m],
+ * phase index phase[m] into phases[n_phase] (n_phase <= 8) and the parent
+ * cell volume |Omega^p| (Eq. eff_stress_1).  Host, copied. */
+rom_status rom_load_cubature(rom_ctx *ctx, int m, const double *w, const int32_t *phase, int n_phase,
+                             const rom_phase *phases, double omega_vol);
+
+/* Geometry (Sec. 2.1, Eq. weakform-dep-mapped; the online line 1 of Algorithm 1):
+ * F_mu,i = I + sum_k mu[b][k] Gmu[i][a*d+r][k] at every point i of instance b.
+ * Gmu[m][d*d][n_par] and mu[B][n_par] on the host, copied.  Fails with ROM_E_ARG
+ * if any det F_mu <= 0.  1 <= n_par <= 4. */
+rom_status rom_set_geometry(rom_ctx *ctx, int64_t B, int n_par, const double *Gmu, const double *mu);
+
+/* Per-batch state for B instances: a = 0, C^p^-1 = I, xi = 0 (virgin material). */
+rom_status rom_state_create(rom_ctx *ctx, int64_t B, rom_state **st);
+rom_status rom_state_destroy(rom_state *st);
+
+/* Canonical history to/from host buffers: a[B][n], Cpinv[B][m][nc] with
+ * nc = 4 (d = 2: C11, C12, C22, C33) or 6 (d = 3: C11, C12, C13, C22, C23, C33)
+ * of the inverse plastic right Cauchy-Green tensor C^p^-1 = F^p^-1 F^p^-T,
+ * xi[B][m] the equivalent plastic strain.  Any pointer may be NULL (skipped).
+ * Blocking. */
+rom_status rom_state_export(rom_ctx *ctx, const rom_state *st, double *a, double *Cpinv, double *xi);
+rom_status rom_state_import(rom_ctx *ctx, rom_state *st, const double *a, const double *Cpinv, const double *xi);
+
+/* One load step for all B instances (Algorithm 1 online lines 2-5).
+ * Fbar[B][d*d] in; Pbar[B][d*d] out; Abar[B][d^4] out (may be NULL if
+ * opts->want_abar == 0); info[B] out (may be NULL).  Host buffers; the call
+ * copies in, runs, copies out and synchronises.  Converged instances commit
+ * their history; the others keep the history of their last converged step. */
+rom_status rom_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts, const double *Fbar,
+                    double *Pbar, double *Abar, rom_step_info *info);
+
+/* Same with device pointers; asynchronous on the context stream. */
+rom_status rom_step_device(rom_ctx *ctx, rom_state *st, const rom_opts *opts, const double *Fbar_d,
+                           double *Pbar_d, double *Abar_d, rom_step_info *info_d);
+
+/* Wait for the context stream. */
+rom_status rom_sync(rom_ctx *ctx);
+
+/* Text of the last error on this context ("" if none).  Owned by the context. */
+const char *rom_last_error(const rom_ctx *ctx);
+
+/* Kernel timing (tracing).  rom_profile(ctx, 1) resets the counters and records
+ * CUDA events around every kernel launch of later steps on the context stream;
+ * rom_profile(ctx, 0) stops.  rom_profile_read returns, for kernel group
+ * 0 start, 1 constitutive (kinematics, return map, tangent), 2 assembly
+ * (force and stiffness), 3 solve (convergence test, line search, LU),
+ * 4 finalize (Pbar, Abar, commit), 5 bookkeeping: the summed device time in ms,
+ * the number of kernel launches and the algorithmic FLOPs (kernel groups 1-3:
+ * kinematics 2 m d^2 n; assembly 2 m d^4 n + m d^2 n (n+1) + 2 m d^2 n; solve
+ * 2 n^3/3 + 2 n^2 -- per active instance and launch).  Any pointer may be NULL. */
+rom_status rom_profile(rom_ctx *ctx, int enable);
+rom_status rom_profile_read(rom_ctx *ctx, int kernel, double *ms, int64_t *launches, double *flops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

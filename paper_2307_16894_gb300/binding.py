@@ -1,0 +1,223 @@
+"""Thin ctypes binding of the C ABI in include/podecm.h (argument marshalling only).
+
+Every step of the hyper-reduced solve runs in libpodecm.so's CUDA kernels;
+there is no CPU fallback: loading fails loudly if the library is missing.
+Names follow the C calls (rom_create -> Context, rom_load_basis ->
+Context.load_basis, ...).  Device buffers are torch CUDA tensors (plumbing
+only); host buffers are numpy arrays.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpodecm.so")
+
+ROM_OK, ROM_E_ARG, ROM_E_STATE, ROM_E_CUDA, ROM_E_NOMEM, ROM_E_NOT_CONVERGED, ROM_E_NONFINITE = range(7)
+PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
+START = {"plain": 0, "prev": 1, "mlp": 2}
+
+INFO_DTYPE = np.dtype([("iters", "<i4"), ("evals", "<i4"), ("status", "<i4"), ("n_yield", "<i4"),
+                       ("res0", "<f8"), ("res", "<f8")])
+
+EXPORTED = ["rom_create", "rom_destroy", "rom_load_basis", "rom_load_cubature", "rom_set_geometry",
+            "rom_state_create", "rom_state_destroy", "rom_state_export", "rom_state_import", "rom_step",
+            "rom_step_device", "rom_sync", "rom_last_error", "rom_profile", "rom_profile_read"]
+
+KERNEL_GROUPS = ["start", "constitutive", "assemble", "solve", "finalize", "bookkeeping"]
+
+
+class RomPhase(ctypes.Structure):
+    _fields_ = [("E", ctypes.c_double), ("nu", ctypes.c_double), ("hard_law", ctypes.c_int32),
+                ("s0", ctypes.c_double), ("H_or_k", ctypes.c_double), ("p", ctypes.c_double)]
+
+
+class RomOpts(ctypes.Structure):
+    _fields_ = [("tol_rel", ctypes.c_double), ("tol_abs", ctypes.c_double), ("max_iter", ctypes.c_int32),
+                ("max_ls", ctypes.c_int32), ("precision", ctypes.c_int32), ("start", ctypes.c_int32),
+                ("polar_split", ctypes.c_int32), ("want_abar", ctypes.c_int32)]
+
+
+class RomError(RuntimeError):
+    pass
+
+
+_lib = None
+
+
+def lib(path=None):
+    """Load libpodecm.so (built by __graft_entry__.build()); raise if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RomError("CUDA library %s not built (run __graft_entry__.build())" % path)
+    L = ctypes.CDLL(path)
+    p, i, i64, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    L.rom_create.argtypes = [pp, i, i, p]
+    L.rom_destroy.argtypes = [p]
+    L.rom_load_basis.argtypes = [p, i, i, p]
+    L.rom_load_cubature.argtypes = [p, i, p, p, i, p, d]
+    L.rom_set_geometry.argtypes = [p, i64, i, p, p]
+    L.rom_state_create.argtypes = [p, i64, pp]
+    L.rom_state_destroy.argtypes = [p]
+    L.rom_state_export.argtypes = [p, p, p, p, p]
+    L.rom_state_import.argtypes = [p, p, p, p, p]
+    L.rom_step.argtypes = [p, p, p, p, p, p, p]
+    L.rom_step_device.argtypes = [p, p, p, p, p, p, p]
+    L.rom_sync.argtypes = [p]
+    L.rom_profile.argtypes = [p, i]
+    L.rom_profile_read.argtypes = [p, i, p, p, p]
+    L.rom_last_error.argtypes = [p]
+    L.rom_last_error.restype = ctypes.c_char_p
+    for f in EXPORTED:
+        if f != "rom_last_error":
+            getattr(L, f).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _p(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def make_opts(tol_rel=1e-10, tol_abs=0.0, max_iter=25, max_ls=6, precision="fp64", start="plain",
+              polar_split=True, want_abar=True):
+    return RomOpts(float(tol_rel), float(tol_abs), int(max_iter), int(max_ls), PREC[precision], START[start],
+                   int(bool(polar_split)), int(bool(want_abar)))
+
+
+class Context:
+    """rom_ctx: one model (basis, cubature, geometry) on one device and stream."""
+
+    def __init__(self, dim, device=0, stream=None):
+        self.L = lib()
+        self.dim = dim
+        h = ctypes.c_void_p()
+        st = ctypes.c_void_p(stream) if stream else None
+        self._check(self.L.rom_create(ctypes.byref(h), int(dim), int(device), st), "rom_create", ctx=None)
+        self.h = h
+        self.n = self.m = self.n_par = 0
+
+    def _check(self, status, what, ctx="self"):
+        if status != ROM_OK:
+            msg = ""
+            if ctx == "self" and getattr(self, "h", None):
+                msg = self.L.rom_last_error(self.h).decode()
+            raise RomError("%s failed with status %d: %s" % (what, status, msg))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.rom_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load_basis(self, G):
+        G = _f64(G)
+        m, d2, n = G.shape
+        self._check(self.L.rom_load_basis(self.h, n, m, _p(G)), "rom_load_basis")
+        self.n, self.m = n, m
+
+    def load_cubature(self, w, phase, phases, omega=1.0):
+        w = _f64(w)
+        phase = np.ascontiguousarray(phase, dtype=np.int32)
+        arr = (RomPhase * len(phases))()
+        for k, ph in enumerate(phases):
+            arr[k] = RomPhase(ph["E"], ph["nu"], 1 if ph.get("law", "power") == "power" else 0, ph["s0"], ph["k"],
+                              ph.get("p", 1.0))
+        self._check(self.L.rom_load_cubature(self.h, len(w), _p(w), _p(phase), len(phases),
+                                             ctypes.cast(arr, ctypes.c_void_p), float(omega)), "rom_load_cubature")
+
+    def set_geometry(self, Gmu, mu):
+        Gmu = _f64(Gmu)
+        mu = _f64(mu)
+        B, n_par = mu.shape
+        self._check(self.L.rom_set_geometry(self.h, B, n_par, _p(Gmu), _p(mu)), "rom_set_geometry")
+        self.n_par = n_par
+
+    def state_create(self, B):
+        h = ctypes.c_void_p()
+        self._check(self.L.rom_state_create(self.h, int(B), ctypes.byref(h)), "rom_state_create")
+        return State(self, h, B)
+
+    def step(self, state, opts, Fbar, want_abar=True):
+        """Host-buffer step: returns (Pbar [B,d,d], Abar [B,d2,d2] or None, info [B] structured)."""
+        d = self.dim
+        Fbar = _f64(Fbar)
+        B = Fbar.shape[0]
+        Pbar = np.empty((B, d, d))
+        Abar = np.empty((B, d * d, d * d)) if want_abar else None
+        info = np.zeros(B, INFO_DTYPE)
+        self._check(self.L.rom_step(self.h, state.h, ctypes.byref(opts), _p(Fbar), _p(Pbar), _p(Abar), _p(info)),
+                    "rom_step")
+        return Pbar, Abar, info
+
+    def step_device(self, state, opts, Fbar_d, Pbar_d, Abar_d, info_d):
+        """Device-buffer step (torch CUDA tensors), asynchronous on the context stream."""
+        self._check(self.L.rom_step_device(self.h, state.h, ctypes.byref(opts), _p(Fbar_d), _p(Pbar_d),
+                                           _p(Abar_d), _p(info_d)), "rom_step_device")
+
+    def sync(self):
+        self._check(self.L.rom_sync(self.h), "rom_sync")
+
+    def profile(self, enable):
+        self._check(self.L.rom_profile(self.h, int(enable)), "rom_profile")
+
+    def profile_read(self):
+        """{group: (ms, launches, flops)} of the kernels timed since profile(1)."""
+        out = {}
+        for k, name in enumerate(KERNEL_GROUPS):
+            ms, ln, fl = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
+            self._check(self.L.rom_profile_read(self.h, k, ctypes.byref(ms), ctypes.byref(ln), ctypes.byref(fl)),
+                        "rom_profile_read")
+            out[name] = (ms.value, ln.value, fl.value)
+        return out
+
+
+class State:
+    """rom_state: reduced coordinates and history of B instances."""
+
+    def __init__(self, ctx, h, B):
+        self.ctx, self.h, self.B = ctx, h, B
+
+    def export(self):
+        c = self.ctx
+        nc = 4 if c.dim == 2 else 6
+        a = np.empty((self.B, c.n))
+        cp = np.empty((self.B, c.m, nc))
+        xi = np.empty((self.B, c.m))
+        c._check(c.L.rom_state_export(c.h, self.h, _p(a), _p(cp), _p(xi)), "rom_state_export")
+        return a, cp, xi
+
+    def import_(self, a=None, Cpinv=None, xi=None):
+        c = self.ctx
+        c._check(c.L.rom_state_import(c.h, self.h, _p(None if a is None else _f64(a)),
+                                      _p(None if Cpinv is None else _f64(Cpinv)),
+                                      _p(None if xi is None else _f64(xi))), "rom_state_import")
+
+    def close(self):
+        if self.h:
+            self.ctx.L.rom_state_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,787 @@
+// CUDA kernels of one hyper-reduced load step (arXiv 2307.16894, Sec. 3.2-3.3,
+// Algorithm 1 online lines 2-5), batched over independent instances.
+//
+// One Newton "pass" over the active instances is three launches:
+//   k_constitutive : one thread per (instance, cubature point): geometry (F_mu),
+//                    kinematics F = Ubar + (G_i a) F_mu^-1, FP64 return map,
+//                    tangent, weighted pull-backs v_i = w_i J_i vec(P F_mu^-T) and
+//                    At_i = w_i J_i (I x F_mu^-1) A (I x F_mu^-1)^T   [Eqs. forcevector_ecm,
+//                    stiffnessmatrix_ecm integrands]
+//   k_assemble     : one CTA per instance: f = sum_i G_i^T v_i (FP64) and
+//                    K = sum_i G_i^T At_i G_i (FP64 or FP32 CUDA cores)
+//   k_solve        : one warp per instance: convergence test, line search,
+//                    LU of K (FP64, partial pivoting), da = -K^-1 f      [Eq. red_newton]
+// and k_finalize computes Pbar (Eq. eff_stress_1), Abar through the Schur
+// complement of the reduced tangent problems (Eqs. tangent_problem_red,
+// eff_stiffness_1) and commits the history of converged instances.
+#include <cstdio>
+#include "kernels.cuh"
+
+namespace podecm {
+
+__constant__ PhaseD c_phases[MAX_PHASES];
+
+void set_phases(const PhaseD *ph, int n, cudaStream_t s) {
+    cudaMemcpyToSymbolAsync(c_phases, ph, sizeof(PhaseD) * n, 0, cudaMemcpyHostToDevice, s);
+}
+
+// ------------------------------------------------------------------------ start
+template <int D>
+__global__ void k_start(Model M, Batch Bt, const double *__restrict__ Fbar, StepOpts o,
+                        const double *__restrict__ dq_pred) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= Bt.B) return;
+    constexpr int D2 = D * D;
+    double F[3][3] = {{0}}, R[3][3] = {{0}}, U[3][3] = {{0}};
+    for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) F[i][j] = Fbar[b * D2 + i * D + j];
+    if (!o.polar) {
+        for (int i = 0; i < D; ++i)
+            for (int j = 0; j < D; ++j) { U[i][j] = F[i][j]; R[i][j] = (i == j); }
+    } else if (D == 2) {
+        const double th = atan2(F[1][0] - F[0][1], F[0][0] + F[1][1]);
+        const double c = cos(th), s = sin(th);
+        R[0][0] = c; R[0][1] = -s; R[1][0] = s; R[1][1] = c;
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 2; ++j) U[i][j] = R[0][i] * F[0][j] + R[1][i] * F[1][j];
+        const double u = 0.5 * (U[0][1] + U[1][0]);
+        U[0][1] = U[1][0] = u;
+    } else {
+        // C = F^T F = N diag(l) N^T ;  U = N diag(sqrt l) N^T ; R = F U^-1
+        double C[3][3], N[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                double s = 0.0;
+                for (int k = 0; k < 3; ++k) s += F[k][i] * F[k][j];
+                C[i][j] = s;
+            }
+        jacobi3(C, N);
+        double sq[3], isq[3];
+        for (int a = 0; a < 3; ++a) { sq[a] = sqrt(C[a][a]); isq[a] = 1.0 / sq[a]; }
+        double Ui[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                double s = 0.0, si = 0.0;
+                for (int a = 0; a < 3; ++a) { s += N[i][a] * sq[a] * N[j][a]; si += N[i][a] * isq[a] * N[j][a]; }
+                U[i][j] = s;
+                Ui[i][j] = si;
+            }
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                double s = 0.0;
+                for (int k = 0; k < 3; ++k) s += F[i][k] * Ui[k][j];
+                R[i][j] = s;
+            }
+    }
+    for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) {
+            Bt.Ubar[b * D2 + i * D + j] = U[i][j];
+            Bt.Rbar[b * D2 + i * D + j] = R[i][j];
+        }
+    const int n = M.n;
+    for (int j = 0; j < n; ++j) {
+        double q = Bt.q_n[b * n + j];
+        if (o.start == 1) q += Bt.dq_prev[b * n + j];
+        else if (o.start == 2 && dq_pred) q += dq_pred[b * n + j];
+        Bt.q_trial[b * n + j] = q;
+        Bt.q_acc[b * n + j] = q;
+    }
+    Ctl c;
+    c.r0 = 0.0; c.tol = 0.0; c.rn_acc = 0.0; c.t = 1.0;
+    c.iters = 0; c.evals = 0; c.ls = 0; c.status = 0; c.active = 1; c.phase = 0; c.pad0 = c.pad1 = 0;
+    Bt.ctl[b] = c;
+    Bt.list[b] = (int32_t)b;
+}
+
+__global__ void k_set_counts(int32_t *counts, int64_t B) {
+    counts[0] = (int32_t)B;
+    counts[1] = 0;
+}
+
+__global__ void k_advance(int32_t *counts) {
+    counts[0] = counts[1];
+    counts[1] = 0;
+}
+
+// ------------------------------------------------------------------ constitutive
+template <int D, typename TT>
+__global__ void __launch_bounds__(128) k_constitutive(Model M, Batch Bt) {
+    constexpr int D2 = D * D;
+    const int m = M.m, n = M.n;
+    const int n_act = Bt.counts[0];
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t p = gid / m;
+    if (p >= n_act) return;
+    const int i = (int)(gid - p * m);
+    const int64_t b = Bt.list[p];
+
+    // a1: geometry F_mu = I + sum_k mu_k Gmu_k(X_i)
+    double Fm[D][D];
+    for (int a = 0; a < D; ++a)
+        for (int r = 0; r < D; ++r) {
+            double s = (a == r) ? 1.0 : 0.0;
+            for (int k = 0; k < M.n_par; ++k)
+                s += Bt.mu[b * M.n_par + k] * M.Gmu_T[((size_t)(a * D + r) * M.n_par + k) * m + i];
+            Fm[a][r] = s;
+        }
+    double Fmi[D][D], J;
+    if (D == 2) {
+        const double det = Fm[0][0] * Fm[1][1] - Fm[0][1] * Fm[1][0];
+        J = fabs(det);
+        const double id = 1.0 / det;
+        Fmi[0][0] = Fm[1][1] * id; Fmi[0][1] = -Fm[0][1] * id;
+        Fmi[1][0] = -Fm[1][0] * id; Fmi[1][1] = Fm[0][0] * id;
+    } else {
+        double c00 = Fm[1][1] * Fm[2][2] - Fm[1][2] * Fm[2][1];
+        double c01 = Fm[1][2] * Fm[2][0] - Fm[1][0] * Fm[2][2];
+        double c02 = Fm[1][0] * Fm[2][1] - Fm[1][1] * Fm[2][0];
+        const double det = Fm[0][0] * c00 + Fm[0][1] * c01 + Fm[0][2] * c02;
+        J = fabs(det);
+        const double id = 1.0 / det;
+        Fmi[0][0] = c00 * id; Fmi[1][0] = c01 * id; Fmi[2][0] = c02 * id;
+        Fmi[0][1] = (Fm[0][2] * Fm[2][1] - Fm[0][1] * Fm[2][2]) * id;
+        Fmi[1][1] = (Fm[0][0] * Fm[2][2] - Fm[0][2] * Fm[2][0]) * id;
+        Fmi[2][1] = (Fm[0][1] * Fm[2][0] - Fm[0][0] * Fm[2][1]) * id;
+        Fmi[0][2] = (Fm[0][1] * Fm[1][2] - Fm[0][2] * Fm[1][1]) * id;
+        Fmi[1][2] = (Fm[0][2] * Fm[1][0] - Fm[0][0] * Fm[1][2]) * id;
+        Fmi[2][2] = (Fm[0][0] * Fm[1][1] - Fm[0][1] * Fm[1][0]) * id;
+    }
+    const double wJ = M.w[i] * J;
+
+    // a2: kinematics H = G_i a, F = Ubar + H F_mu^-1
+    double H[D2];
+    for (int c = 0; c < D2; ++c) H[c] = 0.0;
+    const double *qb = Bt.q_trial + b * n;
+    for (int j = 0; j < n; ++j) {
+        const double qj = __ldg(qb + j);
+#pragma unroll
+        for (int c = 0; c < D2; ++c) H[c] += M.G_T[((size_t)c * n + j) * m + i] * qj;
+    }
+    double F[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 1.0}};
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int bb = 0; bb < D; ++bb) {
+            double s = Bt.Ubar[b * D2 + a * D + bb];
+#pragma unroll
+            for (int r = 0; r < D; ++r) s += H[a * D + r] * Fmi[r][bb];
+            F[a][bb] = s;
+        }
+
+    // a3: return map (FP64)
+    const int ncp = M.ncp;
+    const size_t hb = (size_t)b * ncp * m + i;
+    double cp[6];
+    if (D == 2) {
+        cp[0] = Bt.cp[hb]; cp[1] = Bt.cp[hb + m]; cp[2] = 0.0;
+        cp[3] = Bt.cp[hb + 2 * (size_t)m]; cp[4] = 0.0; cp[5] = Bt.cp[hb + 3 * (size_t)m];
+    } else {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) cp[k] = Bt.cp[hb + k * (size_t)m];
+    }
+    const double xi_n = Bt.xi[(size_t)b * m + i];
+    const PhaseD &ph = c_phases[M.phase[i]];
+    MatState S;
+    double tau[3][3], Finv[3][3], cpn[6], xin;
+    material_value<D>(F, cp, xi_n, ph, S, tau, Finv, cpn, &xin);
+    double P[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int bb = 0; bb < 3; ++bb) {
+            double s = 0.0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) s += tau[a][k] * Finv[bb][k];
+            P[a][bb] = s;
+        }
+    // a5: weighted pull-backs
+    const size_t vb = (size_t)b * D2 * m + i;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int r = 0; r < D; ++r) {
+            double s = 0.0;
+#pragma unroll
+            for (int bb = 0; bb < D; ++bb) s += P[a][bb] * Fmi[r][bb];
+            Bt.v[vb + (size_t)(a * D + r) * m] = wJ * s;
+            Bt.wP[vb + (size_t)(a * D + r) * m] = wJ * P[a][r];
+        }
+    if (D == 2) {
+        Bt.cp_tr[hb] = cpn[0]; Bt.cp_tr[hb + m] = cpn[1];
+        Bt.cp_tr[hb + 2 * (size_t)m] = cpn[3]; Bt.cp_tr[hb + 3 * (size_t)m] = cpn[5];
+    } else {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) Bt.cp_tr[hb + k * (size_t)m] = cpn[k];
+    }
+    Bt.xi_tr[(size_t)b * m + i] = xin;
+    Bt.pl[(size_t)b * m + i] = (uint8_t)S.plastic;
+
+    // a4 + a5: tangent columns At[(a,r),(c,s)] = wJ (dP(e_c x F_mu^-1[s,:]) F_mu^-T)_ar
+    TangentData<TT> td;
+    tangent_setup<D, TT>(S, ph, F, cp, Finv, P, td);
+    TT *At = reinterpret_cast<TT *>(Bt.At);
+    const size_t ab = (size_t)b * D2 * D2 * m + i;
+#pragma unroll 1
+    for (int c = 0; c < D; ++c)
+#pragma unroll 1
+        for (int s = 0; s < D; ++s) {
+            TT f[3] = {TT(0), TT(0), TT(0)};
+#pragma unroll
+            for (int l = 0; l < D; ++l) f[l] = TT(Fmi[s][l]);
+            TT dP[3][3];
+            tangent_direction<D, TT>(td, c, f, dP);
+            const int col = c * D + s;
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+#pragma unroll
+                for (int r = 0; r < D; ++r) {
+                    TT t = TT(0);
+#pragma unroll
+                    for (int bb = 0; bb < D; ++bb) t += dP[a][bb] * TT(Fmi[r][bb]);
+                    At[ab + (size_t)((a * D + r) * D2 + col) * m] = TT(wJ) * t;
+                }
+        }
+}
+
+// --------------------------------------------------------------------- assembly
+// smem layout: Gs64[CH][D2][np] | Ys[CH][D2][np] (TK) | As[CH][D4] (TK) | vs[CH][D2] | (FP32: Gs32)
+template <int D, typename TK, int TM>
+__global__ void __launch_bounds__(256) k_assemble(Model M, Batch Bt, int CH, int NG) {
+    constexpr int D2 = D * D, D4 = D2 * D2;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int n_act = Bt.counts[0];
+    const int p = blockIdx.x;
+    if (p >= n_act) return;
+    const int64_t b = Bt.list[p];
+    const int n = M.n, m = M.m;
+    const int NT = (n + TM - 1) / TM;
+    const int np = NT * TM;
+    double *Gs = reinterpret_cast<double *>(smem);
+    TK *Ys = reinterpret_cast<TK *>(Gs + (size_t)CH * D2 * np);
+    TK *As = Ys + (size_t)CH * D2 * np;
+    double *vs = reinterpret_cast<double *>(As + (size_t)CH * D4 + 2);   // keep 8-byte alignment
+    vs = reinterpret_cast<double *>((reinterpret_cast<uintptr_t>(vs) + 7) & ~uintptr_t(7));
+    TK *Gk = reinterpret_cast<TK *>(vs + (size_t)CH * D2);             // used when TK != double
+
+    const int tid = threadIdx.x;
+    const int nup = NT * (NT + 1) / 2;
+    const int grp = tid / nup;
+    const int tl = tid - grp * nup;
+    const bool has_tile = grp < NG;
+    int ti = 0, tj = 0;
+    if (has_tile) {   // tl -> (ti, tj), ti <= tj
+        int r = tl;
+        ti = 0;
+        while (r >= NT - ti) { r -= NT - ti; ++ti; }
+        tj = ti + r;
+    }
+    TK acc[TM][TM];
+#pragma unroll
+    for (int x = 0; x < TM; ++x)
+#pragma unroll
+        for (int y = 0; y < TM; ++y) acc[x][y] = TK(0);
+    double racc = 0.0;
+    const TK *At = reinterpret_cast<const TK *>(Bt.At);
+
+    for (int c0 = 0; c0 < m; c0 += CH) {
+        const int ch = min(CH, m - c0);
+        __syncthreads();
+        // load G chunk (rows = (point, component)), zero-padded to np columns
+        for (int e = tid; e < CH * D2 * np; e += blockDim.x) {
+            const int row = e / np, col = e - row * np;
+            const int ii = row / D2;
+            double g = 0.0;
+            if (ii < ch && col < n) g = M.G_pt[((size_t)(c0 + ii) * D2 + (row - ii * D2)) * n + col];
+            Gs[e] = g;
+            if (sizeof(TK) != sizeof(double)) Gk[e] = TK(g);
+        }
+        for (int e = tid; e < CH * D4; e += blockDim.x) {
+            const int ce = e / CH, ii = e - ce * CH;
+            As[ii * D4 + ce] = (ii < ch) ? At[((size_t)b * D4 + ce) * m + c0 + ii] : TK(0);
+        }
+        for (int e = tid; e < CH * D2; e += blockDim.x) {
+            const int c = e / CH, ii = e - c * CH;
+            vs[ii * D2 + c] = (ii < ch) ? Bt.v[((size_t)b * D2 + c) * m + c0 + ii] : 0.0;
+        }
+        __syncthreads();
+        // Y[ii][c][k] = sum_e As[ii][c][e] G[ii][e][k]
+        const TK *Gsrc = (sizeof(TK) == sizeof(double)) ? reinterpret_cast<const TK *>(Gs) : Gk;
+        for (int e = tid; e < CH * D2 * np; e += blockDim.x) {
+            const int k = e % np, rc = e / np;
+            const int ii = rc / D2, c = rc - ii * D2;
+            TK s = TK(0);
+#pragma unroll
+            for (int q = 0; q < D2; ++q) s += As[ii * D4 + c * D2 + q] * Gsrc[(ii * D2 + q) * np + k];
+            Ys[e] = s;
+        }
+        // force: r_j += sum_rows G[row][j] v[row]  (FP64, fixed order)
+        if (tid < n) {
+            for (int row = 0; row < ch * D2; ++row) racc += Gs[row * np + tid] * vs[row];
+        }
+        __syncthreads();
+        if (has_tile) {
+            for (int row = grp; row < ch * D2; row += NG) {
+                TK gj[TM], yk[TM];
+#pragma unroll
+                for (int x = 0; x < TM; ++x) gj[x] = Gsrc[row * np + ti * TM + x];
+#pragma unroll
+                for (int y = 0; y < TM; ++y) yk[y] = Ys[row * np + tj * TM + y];
+#pragma unroll
+                for (int x = 0; x < TM; ++x)
+#pragma unroll
+                    for (int y = 0; y < TM; ++y) acc[x][y] += gj[x] * yk[y];
+            }
+        }
+    }
+    __syncthreads();
+    // reduce groups in smem (reuse the G buffer): red[g][np][np]
+    TK *red = reinterpret_cast<TK *>(smem);
+    if (has_tile) {
+#pragma unroll
+        for (int x = 0; x < TM; ++x)
+#pragma unroll
+            for (int y = 0; y < TM; ++y) red[((size_t)grp * np + ti * TM + x) * np + tj * TM + y] = acc[x][y];
+    }
+    __syncthreads();
+    double *Kb = Bt.K + (size_t)b * n * n;
+    for (int e = tid; e < n * n; e += blockDim.x) {
+        const int j = e / n, k = e - j * n;
+        const int jj = min(j, k), kk = max(j, k);
+        // tile that holds (jj, kk) is upper (ti <= tj); within a diagonal tile both orders exist
+        int a = jj, c = kk;
+        if ((jj / TM) == (kk / TM)) { a = j; c = k; }
+        TK s = TK(0);
+        for (int g = 0; g < NG; ++g) s += red[((size_t)g * np + a) * np + c];
+        Kb[e] = double(s);
+    }
+    if (tid < n) Bt.r[b * n + tid] = racc;
+}
+
+// ------------------------------------------------------------------------ solve
+// LU with partial pivoting of the n x n matrix A (row-major, smem) by one warp;
+// piv[k] = pivot row.  Returns false if a pivot is zero or non-finite.
+__device__ bool warp_lu(double *A, int n, int *piv) {
+    const int lane = threadIdx.x & 31;
+    for (int k = 0; k < n; ++k) {
+        double best = -1.0;
+        int bi = k;
+        for (int i = k + lane; i < n; i += 32) {
+            const double v = fabs(A[i * n + k]);
+            if (v > best || (v == best && i < bi)) { best = v; bi = i; }
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            const double ob = __shfl_xor_sync(0xffffffffu, best, off);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (!(best > 0.0) || !isfinite(best)) return false;
+        if (lane == 0) piv[k] = bi;
+        if (bi != k)
+            for (int j = lane; j < n; j += 32) {
+                const double t = A[k * n + j];
+                A[k * n + j] = A[bi * n + j];
+                A[bi * n + j] = t;
+            }
+        __syncwarp();
+        const double akk = A[k * n + k];
+        for (int i = k + 1 + lane; i < n; i += 32) A[i * n + k] /= akk;
+        __syncwarp();
+        for (int i = k + 1; i < n; ++i) {
+            const double lik = A[i * n + k];
+            for (int j = k + 1 + lane; j < n; j += 32) A[i * n + j] -= lik * A[k * n + j];
+        }
+        __syncwarp();
+    }
+    return true;
+}
+
+// solve (LU) x = b in place, b in smem, by one warp
+__device__ void warp_lu_solve(const double *A, int n, const int *piv, double *x) {
+    const int lane = threadIdx.x & 31;
+    for (int k = 0; k < n; ++k) {
+        const int p = piv[k];
+        if (p != k && lane == 0) { const double t = x[k]; x[k] = x[p]; x[p] = t; }
+        __syncwarp();
+    }
+    for (int j = 0; j < n; ++j) {
+        const double xj = x[j];
+        for (int i = j + 1 + lane; i < n; i += 32) x[i] -= A[i * n + j] * xj;
+        __syncwarp();
+    }
+    for (int j = n - 1; j >= 0; --j) {
+        if (lane == 0) x[j] /= A[j * n + j];
+        __syncwarp();
+        const double xj = x[j];
+        for (int i = lane; i < j; i += 32) x[i] -= A[i * n + j] * xj;
+        __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(32) k_solve(Model M, Batch Bt, StepOpts o, int32_t *list_next) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int n_act = Bt.counts[0];
+    const int p = blockIdx.x;
+    if (p >= n_act) return;
+    const int64_t b = Bt.list[p];
+    const int n = M.n, lane = threadIdx.x;
+    double *A = reinterpret_cast<double *>(smem);
+    double *x = A + (size_t)n * n;
+    int *piv = reinterpret_cast<int *>(x + n);
+    const double *r = Bt.r + b * n;
+    double s = 0.0;
+    for (int j = lane; j < n; j += 32) s += r[j] * r[j];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    const double rn = sqrt(s);
+    Ctl c = Bt.ctl[b];
+    double *qt = Bt.q_trial + b * n, *qa = Bt.q_acc + b * n, *dq = Bt.dq + b * n;
+    bool accepted = false;
+    if (c.phase == 0) {
+        c.r0 = rn;
+        c.tol = fmax(o.tol_rel * rn, o.tol_abs);
+        c.rn_acc = rn;
+        c.phase = 1;
+        accepted = true;
+    } else {
+        c.evals += 1;
+        if (c.ls >= o.max_ls || (isfinite(rn) && rn < c.rn_acc)) {
+            for (int j = lane; j < n; j += 32) qa[j] = qt[j];
+            c.rn_acc = rn;
+            c.iters += 1;
+            c.ls = 0;
+            accepted = true;
+        } else {
+            c.ls += 1;
+            c.t *= 0.5;
+            for (int j = lane; j < n; j += 32) qt[j] = qa[j] + c.t * dq[j];
+        }
+    }
+    if (accepted) {
+        if (!isfinite(c.rn_acc)) { c.status = 6; c.active = 0; }
+        else if (c.rn_acc <= c.tol) { c.status = 0; c.active = 0; }
+        else if (c.iters >= o.max_iter) { c.status = 5; c.active = 0; }
+        else {
+            const double *Kb = Bt.K + (size_t)b * n * n;
+            for (int e = lane; e < n * n; e += 32) A[e] = Kb[e];
+            for (int j = lane; j < n; j += 32) x[j] = -r[j];
+            __syncwarp();
+            if (!warp_lu(A, n, piv)) { c.status = 6; c.active = 0; }
+            else {
+                warp_lu_solve(A, n, piv, x);
+                c.t = 1.0;
+                c.ls = 0;
+                for (int j = lane; j < n; j += 32) { dq[j] = x[j]; qt[j] = qa[j] + x[j]; }
+            }
+        }
+    }
+    __syncwarp();
+    if (lane == 0) {
+        Bt.ctl[b] = c;
+        if (c.active) {
+            const int pos = atomicAdd(&Bt.counts[1], 1);
+            list_next[pos] = (int32_t)b;
+        }
+    }
+}
+
+// --------------------------------------------------------------------- finalize
+template <int D, typename TT>
+__global__ void __launch_bounds__(256) k_finalize(Model M, Batch Bt, StepOpts o, double *__restrict__ Pbar,
+                                                  double *__restrict__ Abar, void *info_v, int CHF) {
+    constexpr int D2 = D * D, D4 = D2 * D2;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int64_t b = blockIdx.x;
+    const int n = M.n, m = M.m, tid = threadIdx.x;
+    const Ctl c = Bt.ctl[b];
+    __shared__ double red[256];
+    __shared__ double PU[D2], AU[D4], Rb[D2], Ub[D2];
+    __shared__ int ny_s;
+    // n_yield of the last evaluated state
+    int cnt = 0;
+    for (int i = tid; i < m; i += blockDim.x) cnt += Bt.pl[b * m + i];
+    red[tid] = cnt;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if (tid < off) red[tid] += red[tid + off];
+        __syncthreads();
+    }
+    if (tid == 0) ny_s = (int)red[0];
+    __syncthreads();
+    struct Info { int32_t iters, evals, status, n_yield; double res0, res; };
+    Info *info = reinterpret_cast<Info *>(info_v);
+    if (tid == 0 && info) {
+        Info f;
+        f.iters = c.iters; f.evals = c.evals; f.status = c.status; f.n_yield = ny_s;
+        f.res0 = c.r0; f.res = c.rn_acc;
+        info[b] = f;
+    }
+    if (c.status != 0) {
+        for (int e = tid; e < D2; e += blockDim.x) Pbar[b * D2 + e] = NAN;
+        if (Abar && o.want_abar)
+            for (int e = tid; e < D4; e += blockDim.x) Abar[b * D4 + e] = NAN;
+        return;
+    }
+    // a10: Pbar_U = |Omega|^-1 sum_i wJ P_i
+    for (int cc = 0; cc < D2; ++cc) {
+        double s = 0.0;
+        for (int i = tid; i < m; i += blockDim.x) s += Bt.wP[((size_t)b * D2 + cc) * m + i];
+        __syncthreads();
+        red[tid] = s;
+        __syncthreads();
+        for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+            if (tid < off) red[tid] += red[tid + off];
+            __syncthreads();
+        }
+        if (tid == 0) PU[cc] = red[0] / M.omega;
+    }
+    if (tid < D2) { Rb[tid] = Bt.Rbar[b * D2 + tid]; Ub[tid] = Bt.Ubar[b * D2 + tid]; }
+    __syncthreads();
+
+    if (Abar && o.want_abar) {
+        // a11: B = sum_i G_i^T Ahat_i,  A0 = sum_i wJ A_i, Ahat_i = At_i Xi_i (Xi: dH = E_kl F_mu)
+        double *Bm = reinterpret_cast<double *>(smem);              // [n][D2]
+        double *A0 = Bm + (size_t)n * D2;                          // [D4]
+        double *Fm = A0 + D4;                                      // [CHF][D2]
+        double *Ah = Fm + (size_t)CHF * D2;                        // [CHF][D4]
+        double *Gs = Ah + (size_t)CHF * D4;                        // [CHF][D2][n]
+        const TT *At = reinterpret_cast<const TT *>(Bt.At);
+        double bacc[4] = {0, 0, 0, 0};     // entries tid, tid+256, ... of Bm (n*D2 <= 1152)
+        double aacc = 0.0;                 // entry tid of A0 (D4 <= 81)
+        for (int c0 = 0; c0 < m; c0 += CHF) {
+            const int ch = min(CHF, m - c0);
+            __syncthreads();
+            for (int e = tid; e < ch * D2; e += blockDim.x) {
+                const int ii = e / D2, ar = e - ii * D2;
+                const int a = ar / D, r = ar - a * D;
+                double s = (a == r) ? 1.0 : 0.0;
+                for (int k = 0; k < M.n_par; ++k)
+                    s += Bt.mu[b * M.n_par + k] * M.Gmu_T[((size_t)ar * M.n_par + k) * m + c0 + ii];
+                Fm[ii * D2 + ar] = s;
+            }
+            for (int e = tid; e < ch * D2 * n; e += blockDim.x)
+                Gs[e] = M.G_pt[(size_t)c0 * D2 * n + e];
+            __syncthreads();
+            for (int e = tid; e < ch * D4; e += blockDim.x) {
+                const int ii = e / D4, rem = e - ii * D4;
+                const int ar = rem / D2, kl = rem - ar * D2;
+                const int k = kl / D, l = kl - k * D;
+                double s = 0.0;
+                for (int ss = 0; ss < D; ++ss)
+                    s += double(At[((size_t)b * D4 + ar * D2 + k * D + ss) * m + c0 + ii]) * Fm[ii * D2 + l * D + ss];
+                Ah[e] = s;
+            }
+            __syncthreads();
+            for (int q = 0; q < 4; ++q) {
+                const int e = tid + q * blockDim.x;
+                if (e < n * D2) {
+                    const int j = e / D2, kl = e - j * D2;
+                    double s = 0.0;
+                    for (int ii = 0; ii < ch; ++ii)
+                        for (int ar = 0; ar < D2; ++ar) s += Gs[(ii * D2 + ar) * n + j] * Ah[ii * D4 + ar * D2 + kl];
+                    bacc[q] += s;
+                }
+            }
+            if (tid < D4) {
+                const int ij = tid / D2, kl = tid - ij * D2;
+                const int ia = ij / D, jb = ij - ia * D;
+                double s = 0.0;
+                for (int ii = 0; ii < ch; ++ii)
+                    for (int r = 0; r < D; ++r) s += Fm[ii * D2 + jb * D + r] * Ah[ii * D4 + (ia * D + r) * D2 + kl];
+                aacc += s;
+            }
+        }
+        __syncthreads();
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + q * blockDim.x;
+            if (e < n * D2) Bm[e] = bacc[q];
+        }
+        if (tid < D4) A0[tid] = aacc;
+        __syncthreads();
+        // Schur complement with the factor of K at the solution (K* = K)
+        double *Aw = Gs;                              // reuse: n*n + n*D2 + n ints
+        double *Zs = Aw + (size_t)n * n;
+        int *piv = reinterpret_cast<int *>(Zs + (size_t)n * D2);
+        if (tid < 32) {
+            const double *Kb = Bt.K + (size_t)b * n * n;
+            for (int e = tid; e < n * n; e += 32) Aw[e] = Kb[e];
+            __syncwarp();
+            const bool ok = warp_lu(Aw, n, piv);
+            for (int kl = 0; kl < D2; ++kl) {
+                double *x = Zs + (size_t)kl * n;
+                for (int j = tid; j < n; j += 32) x[j] = Bm[j * D2 + kl];
+                __syncwarp();
+                if (ok) warp_lu_solve(Aw, n, piv, x);
+                else for (int j = tid; j < n; j += 32) x[j] = NAN;
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        if (tid < D4) {
+            const int ij = tid / D2, kl = tid - ij * D2;
+            double s = A0[tid];
+            for (int j = 0; j < n; ++j) s -= Bm[j * D2 + ij] * Zs[(size_t)kl * n + j];
+            AU[tid] = s / M.omega;
+        }
+        __syncthreads();
+        // rotate back: Abar = d(R Pbar_U(R^T Fbar))/dFbar
+        if (tid < D2) {
+            const int k = tid / D, l = tid - k * D;
+            double Mm[9] = {0}, W[9] = {0}, dU[9], dPU[9], t[9];
+            for (int i = 0; i < D; ++i) Mm[i * D + l] = Rb[k * D + i];
+            double trU = 0.0;
+            for (int i = 0; i < D; ++i) trU += Ub[i * D + i];
+            if (o.polar) {
+                if (D == 2) {
+                    const double om = (Mm[2] - Mm[1]) / trU;
+                    W[1] = -om; W[2] = om;
+                } else {
+                    const double a0 = Mm[7] - Mm[5], a1 = Mm[2] - Mm[6], a2 = Mm[3] - Mm[1];
+                    double S[9];
+                    for (int e = 0; e < 9; ++e) S[e] = -Ub[e];
+                    S[0] += trU; S[4] += trU; S[8] += trU;
+                    const double c00 = S[4] * S[8] - S[5] * S[7], c01 = S[5] * S[6] - S[3] * S[8], c02 = S[3] * S[7] - S[4] * S[6];
+                    const double det = S[0] * c00 + S[1] * c01 + S[2] * c02;
+                    const double Si[9] = {c00 / det, (S[2] * S[7] - S[1] * S[8]) / det, (S[1] * S[5] - S[2] * S[4]) / det,
+                                          c01 / det, (S[0] * S[8] - S[2] * S[6]) / det, (S[2] * S[3] - S[0] * S[5]) / det,
+                                          c02 / det, (S[1] * S[6] - S[0] * S[7]) / det, (S[0] * S[4] - S[1] * S[3]) / det};
+                    const double w0 = Si[0] * a0 + Si[1] * a1 + Si[2] * a2;
+                    const double w1 = Si[3] * a0 + Si[4] * a1 + Si[5] * a2;
+                    const double w2 = Si[6] * a0 + Si[7] * a1 + Si[8] * a2;
+                    W[1] = -w2; W[2] = w1; W[3] = w2; W[5] = -w0; W[6] = -w1; W[7] = w0;
+                }
+            }
+            for (int i = 0; i < D; ++i)
+                for (int j = 0; j < D; ++j) {
+                    double s = 0.0;
+                    for (int cc = 0; cc < D; ++cc) s += W[i * D + cc] * Ub[cc * D + j];
+                    dU[i * D + j] = Mm[i * D + j] - s;
+                }
+            for (int ij = 0; ij < D2; ++ij) {
+                double s = 0.0;
+                for (int cc = 0; cc < D2; ++cc) s += AU[ij * D2 + cc] * dU[cc];
+                dPU[ij] = s;
+            }
+            for (int i = 0; i < D; ++i)
+                for (int j = 0; j < D; ++j) {
+                    double s = dPU[i * D + j];
+                    for (int cc = 0; cc < D; ++cc) s += W[i * D + cc] * PU[cc * D + j];
+                    t[i * D + j] = s;
+                }
+            for (int i = 0; i < D; ++i)
+                for (int j = 0; j < D; ++j) {
+                    double s = 0.0;
+                    for (int cc = 0; cc < D; ++cc) s += Rb[i * D + cc] * t[cc * D + j];
+                    Abar[b * D4 + (i * D + j) * D2 + tid] = s;
+                }
+        }
+    }
+    if (tid < D2) {
+        const int i = tid / D, j = tid - i * D;
+        double s = 0.0;
+        for (int cc = 0; cc < D; ++cc) s += Rb[i * D + cc] * PU[cc * D + j];
+        Pbar[b * D2 + tid] = s;
+    }
+    // a12: commit
+    const int ncp = M.ncp;
+    for (int e = tid; e < ncp * m; e += blockDim.x) Bt.cp[(size_t)b * ncp * m + e] = Bt.cp_tr[(size_t)b * ncp * m + e];
+    for (int e = tid; e < m; e += blockDim.x) Bt.xi[(size_t)b * m + e] = Bt.xi_tr[(size_t)b * m + e];
+    for (int j = tid; j < n; j += blockDim.x) {
+        const double qa = Bt.q_acc[b * n + j];
+        Bt.dq_prev[b * n + j] = qa - Bt.q_n[b * n + j];
+        Bt.q_n[b * n + j] = qa;
+    }
+}
+
+// ----------------------------------------------------------------- host launchers
+template <int D>
+static int launch_kernels_t(int which, const Model &M, Batch Bt, const StepOpts &o, int32_t *list_next,
+                            cudaStream_t s) {
+    constexpr int D2 = D * D, D4 = D2 * D2;
+    if (which == 1) {
+        const int64_t nthr = Bt.B * (int64_t)M.m;
+        const int blk = 128;
+        const int grid = (int)((nthr + blk - 1) / blk);
+        if (o.precision == 0) k_constitutive<D, double><<<grid, blk, 0, s>>>(M, Bt);
+        else k_constitutive<D, float><<<grid, blk, 0, s>>>(M, Bt);
+        return 0;
+    }
+    if (which == 2) {
+        constexpr int TM = (D == 2) ? 2 : 4;
+        const int NT = (M.n + TM - 1) / TM, np = NT * TM;
+        const int nup = NT * (NT + 1) / 2;
+        int NG = nup >= 256 ? 1 : 256 / nup;
+        const int nthreads = ((NG * nup + 31) / 32) * 32;
+        if (nthreads > 256) return -1;   // n too large for one tile per thread
+        const int tksz = o.precision == 0 ? 8 : 4;
+        auto smem_for = [&](int CH) {
+            size_t bytes = (size_t)CH * D2 * np * 8 + (size_t)CH * D2 * np * tksz + (size_t)CH * D4 * tksz + 16 +
+                           (size_t)CH * D2 * 8 + (o.precision == 0 ? 0 : (size_t)CH * D2 * np * tksz);
+            const size_t red = (size_t)NG * np * np * tksz;
+            return bytes > red ? bytes : red;
+        };
+        int CH = 64;
+        while (CH > 1 && smem_for(CH) > 96 * 1024) CH /= 2;
+        const size_t sm = smem_for(CH);
+        if (o.precision == 0) {
+            cudaFuncSetAttribute(k_assemble<D, double, TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            k_assemble<D, double, TM><<<(int)Bt.B, nthreads, sm, s>>>(M, Bt, CH, NG);
+        } else {
+            cudaFuncSetAttribute(k_assemble<D, float, TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            k_assemble<D, float, TM><<<(int)Bt.B, nthreads, sm, s>>>(M, Bt, CH, NG);
+        }
+        return 0;
+    }
+    if (which == 3) {
+        const size_t sms = (size_t)M.n * M.n * 8 + (size_t)M.n * 8 + (size_t)M.n * 4 + 16;
+        cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sms);
+        k_solve<<<(int)Bt.B, 32, sms, s>>>(M, Bt, o, list_next);
+        return 0;
+    }
+    if (which == 5) {
+        k_advance<<<1, 1, 0, s>>>(Bt.counts);
+        return 0;
+    }
+    return -1;
+}
+
+// which: 1 constitutive, 2 assemble, 3 solve, 5 advance
+int launch_kernel(int which, const Model &M, Batch Bt, const StepOpts &o, int32_t *list_next, cudaStream_t s) {
+    return M.d == 2 ? launch_kernels_t<2>(which, M, Bt, o, list_next, s)
+                    : launch_kernels_t<3>(which, M, Bt, o, list_next, s);
+}
+
+int launch_start(const Model &M, Batch Bt, const double *Fbar, const StepOpts &o, const double *dq_pred,
+                 cudaStream_t s) {
+    const int blk = 128, grid = (int)((Bt.B + blk - 1) / blk);
+    if (M.d == 2) k_start<2><<<grid, blk, 0, s>>>(M, Bt, Fbar, o, dq_pred);
+    else k_start<3><<<grid, blk, 0, s>>>(M, Bt, Fbar, o, dq_pred);
+    k_set_counts<<<1, 1, 0, s>>>(Bt.counts, Bt.B);
+    return 0;
+}
+
+template <int D>
+static int launch_finalize_t(const Model &M, Batch Bt, const StepOpts &o, double *Pbar, double *Abar, void *info,
+                             cudaStream_t s) {
+    constexpr int D2 = D * D, D4 = D2 * D2;
+    if ((size_t)M.n * D2 > 1024) return -1;
+    const int CHF = 8;
+    size_t sm = ((size_t)M.n * D2 + D4 + (size_t)CHF * D2 + (size_t)CHF * D4 + (size_t)CHF * D2 * M.n) * 8;
+    const size_t sm2 = ((size_t)M.n * D2 + D4 + (size_t)CHF * D2 + (size_t)CHF * D4) * 8 +
+                       ((size_t)M.n * M.n + (size_t)M.n * D2) * 8 + (size_t)M.n * 4 + 16;
+    if (sm2 > sm) sm = sm2;
+    if (o.precision == 0) {
+        cudaFuncSetAttribute(k_finalize<D, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_finalize<D, double><<<(int)Bt.B, 256, sm, s>>>(M, Bt, o, Pbar, Abar, info, CHF);
+    } else {
+        cudaFuncSetAttribute(k_finalize<D, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_finalize<D, float><<<(int)Bt.B, 256, sm, s>>>(M, Bt, o, Pbar, Abar, info, CHF);
+    }
+    return 0;
+}
+
+int launch_finalize(const Model &M, Batch Bt, const StepOpts &o, double *Pbar, double *Abar, void *info,
+                    cudaStream_t s) {
+    return M.d == 2 ? launch_finalize_t<2>(M, Bt, o, Pbar, Abar, info, s)
+                    : launch_finalize_t<3>(M, Bt, o, Pbar, Abar, info, s);
+}
+
+}  // namespace podecm

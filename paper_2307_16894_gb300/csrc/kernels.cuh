@@ -1,0 +1,58 @@
+// Device data structures shared by the kernels of the hyper-reduced RVE step.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "material.cuh"
+
+namespace podecm {
+
+constexpr int MAX_PHASES = 8;
+constexpr int MAX_NPAR = 4;
+constexpr int MAX_N = 128;
+
+// per-instance Newton control block
+struct Ctl {
+    double r0, tol, rn_acc, t;
+    int32_t iters, evals, ls, status;
+    int32_t active, phase;   // phase 0: start evaluation pending, 1: trial evaluation pending
+    int32_t pad0, pad1;
+};
+
+// model (shared by all instances)
+struct Model {
+    int d, d2, n, m, n_par, nphase, ncp;
+    const double *G_pt;    // [m][d2][n]
+    const double *G_T;     // [d2][n][m]
+    const float *G32_pt;   // [m][d2][n]
+    const double *w;       // [m]
+    const int32_t *phase;  // [m]
+    const double *Gmu_T;   // [d2][n_par][m]
+    double omega;
+};
+
+// one batch (state + work arrays)
+struct Batch {
+    int64_t B;
+    const double *mu;        // [B][n_par]
+    double *q_n, *dq_prev;   // [B][n] committed coordinates, last converged increment
+    double *cp, *xi;         // [B][ncp][m], [B][m] committed history
+    double *q_trial, *q_acc, *dq;   // [B][n]
+    Ctl *ctl;                // [B]
+    int32_t *list;           // [B] active instances (compacted)
+    int32_t *counts;         // [0] = active count, [1] = next count
+    double *v;               // [B][d2][m]  wJ vec(P F_mu^-T)
+    double *wP;              // [B][d2][m]  wJ P
+    void *At;                // [B][d2*d2][m] pulled-back tangent (double or float)
+    double *cp_tr, *xi_tr;   // trial history
+    uint8_t *pl;             // [B][m] plastic flags of the last evaluation
+    double *r;               // [B][n]
+    double *K;               // [B][n][n]
+    double *Ubar, *Rbar;     // [B][d2]
+};
+
+struct StepOpts {
+    double tol_rel, tol_abs;
+    int max_iter, max_ls, precision, start, polar, want_abar;
+};
+
+}  // namespace podecm

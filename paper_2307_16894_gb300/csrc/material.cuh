@@ -1,0 +1,392 @@
+// Finite-strain J2 material point on the device (Appendix A of arXiv 2307.16894),
+// written in the spatial (left Cauchy-Green) form of the same model:
+//
+//   b_tr = F C^p_n^-1 F^T                       trial elastic left Cauchy-Green tensor
+//   b_tr = sum_a lambda_a n_a n_a^T             (FP64 Jacobi eigen-decomposition)
+//   eps_a = 1/2 ln lambda_a                      elastic log strain (Eq. j2_7, Hencky)
+//   tau_tr,a = lam tr(eps) + 2G eps_a            (Eq. j2_1 in principal Kirchhoff stresses)
+//   f = sqrt(3/2) |dev tau_tr| - sigma_y(xi_n)   (Eq. j2_2)
+//   radial return in log space, dgamma from g(dg) = q_tr - 3G dg - sigma_y(xi_n + dg) = 0
+//   tau_a = tau_tr,a - 2G dg sqrt(3/2) nhat_a    (Eqs. j2_3 - j2_5)
+//   P = tau F^-T
+//   b_new = sum_a exp(2 eps_a - 2 dg sqrt(3/2) nhat_a) n_a n_a^T,
+//   C^p_new^-1 = F^-1 b_new F^-T                 (equivalent to Eq. j2_10)
+//
+// The exponential update F^p_new = exp(dg r) F^p_n with r coaxial with the trial
+// elastic strain returns exactly to eps_tr - dg r in log space, so this form
+// and the paper's (F^p) form give the same P and the same C^p^-1 = F^p^-1 F^p^-T.
+//
+// Consistent tangent (not derived in the paper): for an isotropic function
+// tau(b) with principal values tau_a(lambda),
+//   d tau' _aa = sum_b (d tau_a / d eps_b) db'_bb / (2 lambda_b),
+//   d tau' _ab = (tau_a - tau_b)/(lambda_a - lambda_b) db'_ab   (a != b),
+// primes = components in the eigenbasis, with the algorithmic moduli of the
+// radial return d tau_a/d eps_b = lam + 2G beta (delta_ab) + 2G(1-beta)/3 ... (see
+// moduli()) and (tau_a - tau_b)/(lambda_a - lambda_b) = G beta L(lambda_a, lambda_b),
+// L(x, y) = (ln x - ln y)/(x - y) evaluated through log1p (finite at x = y).
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace podecm {
+
+struct PhaseD {
+    double E, nu, s0, k, p;
+    double lam, G, Kb;   // Lame lambda, shear modulus, bulk modulus
+    int law;             // 0 linear, 1 power
+    int elastic;         // s0 == +inf
+};
+
+__device__ __forceinline__ double yield_stress(const PhaseD &ph, double xi, double *slope) {
+    if (ph.elastic) { *slope = 0.0; return INFINITY; }
+    if (ph.law == 0) { *slope = ph.k; return ph.s0 + ph.k * xi; }
+    const double base = 1.0 + ph.k * xi;
+    const double v = ph.s0 * pow(base, ph.p);
+    *slope = v * ph.p * ph.k / base;
+    return v;
+}
+
+// symmetric 3x3 eigen-decomposition by cyclic Jacobi rotations (FP64).
+// a: symmetric matrix (overwritten: diagonal -> eigenvalues), V: eigenvectors in columns.
+__device__ __forceinline__ void jacobi3(double a[3][3], double V[3][3]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) V[i][j] = (i == j) ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 12; ++sweep) {
+        const double off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
+        const double dg = a[0][0] * a[0][0] + a[1][1] * a[1][1] + a[2][2] * a[2][2];
+        if (off <= 1e-34 * dg) break;
+#pragma unroll
+        for (int pq = 0; pq < 3; ++pq) {
+            const int p = (pq == 2) ? 1 : 0;
+            const int q = (pq == 0) ? 1 : 2;
+            const int r = 3 - p - q;
+            const double apq = a[p][q];
+            if (fabs(apq) <= 1e-300) continue;
+            const double theta = (a[q][q] - a[p][p]) / (2.0 * apq);
+            const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+            const double c = 1.0 / sqrt(t * t + 1.0);
+            const double s = t * c;
+            a[p][p] -= t * apq;
+            a[q][q] += t * apq;
+            a[p][q] = a[q][p] = 0.0;
+            const double arp = a[r][p], arq = a[r][q];
+            a[r][p] = a[p][r] = c * arp - s * arq;
+            a[r][q] = a[q][r] = s * arp + c * arq;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const double vkp = V[k][p], vkq = V[k][q];
+                V[k][p] = c * vkp - s * vkq;
+                V[k][q] = s * vkp + c * vkq;
+            }
+        }
+    }
+}
+
+// (ln x - ln y) / (x - y) for x, y > 0, finite and accurate when x ~ y
+template <typename T>
+__device__ __forceinline__ T log_divided_difference(T x, T y) {
+    const T u = y / x - T(1);
+    if (fabs(u) < T(1e-8)) return (T(1) - T(0.5) * u) / x;
+    return log1p(u) / (u * x);
+}
+
+// Result of the value part of the update at one point.
+struct MatState {
+    double N[3][3];      // eigenvectors of b_tr (columns)
+    double lam[3];       // eigenvalues of b_tr
+    double tau[3];       // principal Kirchhoff stresses
+    double nh[3];        // unit deviatoric direction of the trial log strain
+    double beta;         // 1 - 3 G dg / q_tr (1 if elastic)
+    double dg, q_tr, hs; // plastic multiplier, trial von Mises, hardening slope at xi_n + dg
+    int plastic;
+};
+
+// Value part.  F: 3x3 (plane strain: F[2][2] = 1, F[i][2] = F[2][i] = 0), cp: C^p^-1
+// (00, 01, 02, 11, 12, 22).  Outputs the state, the Kirchhoff stress tau (3x3), the
+// updated history cp_new, xi_new.  D = 2 uses the block structure.
+template <int D>
+__device__ __forceinline__ void material_value(const double F[3][3], const double cp[6], double xi_n,
+                                               const PhaseD &ph, MatState &S, double tau[3][3],
+                                               double Finv[3][3], double cp_new[6], double *xi_new) {
+    const double C[3][3] = {{cp[0], cp[1], cp[2]}, {cp[1], cp[3], cp[4]}, {cp[2], cp[4], cp[5]}};
+    // Z = C F^T, b = F Z
+    double Z[3][3], b[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) s += C[i][k] * F[j][k];
+            Z[i][j] = s;
+        }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j) {
+            double s = 0.0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) s += F[i][k] * Z[k][j];
+            b[i][j] = s;
+            b[j][i] = s;
+        }
+    if (D == 2) {
+        // one Jacobi rotation diagonalises the in-plane block; axis 3 is principal
+        double c = 1.0, s = 0.0;
+        const double apq = b[0][1];
+        if (fabs(apq) > 1e-300) {
+            const double theta = (b[1][1] - b[0][0]) / (2.0 * apq);
+            const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+            c = 1.0 / sqrt(t * t + 1.0);
+            s = t * c;
+            S.lam[0] = b[0][0] - t * apq;
+            S.lam[1] = b[1][1] + t * apq;
+        } else {
+            S.lam[0] = b[0][0];
+            S.lam[1] = b[1][1];
+        }
+        S.lam[2] = b[2][2];
+        S.N[0][0] = c;  S.N[0][1] = s;  S.N[0][2] = 0.0;
+        S.N[1][0] = -s; S.N[1][1] = c;  S.N[1][2] = 0.0;
+        S.N[2][0] = 0.0; S.N[2][1] = 0.0; S.N[2][2] = 1.0;
+    } else {
+        jacobi3(b, S.N);
+        S.lam[0] = b[0][0];
+        S.lam[1] = b[1][1];
+        S.lam[2] = b[2][2];
+    }
+    double eps[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) eps[a] = 0.5 * log(S.lam[a]);
+    const double tr = eps[0] + eps[1] + eps[2];
+    const double mean = tr * (1.0 / 3.0);
+    double e[3] = {eps[0] - mean, eps[1] - mean, eps[2] - mean};
+    const double enorm = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+    const double G = ph.G;
+    S.q_tr = sqrt(6.0) * G * enorm;
+    double h0;
+    const double sy_n = yield_stress(ph, xi_n, &h0);
+    S.plastic = (S.q_tr - sy_n) > 1e-12 * sy_n;
+    S.dg = 0.0;
+    S.beta = 1.0;
+    S.hs = h0;
+    if (S.plastic) {
+        double x = (S.q_tr - sy_n) / (3.0 * G + h0);
+        double hs = h0;
+        for (int it = 0; it < 60; ++it) {
+            const double sy = yield_stress(ph, xi_n + x, &hs);
+            const double step = (S.q_tr - 3.0 * G * x - sy) / (3.0 * G + hs);
+            x += step;
+            if (fabs(step) <= 1e-15 * fabs(x)) break;
+        }
+        yield_stress(ph, xi_n + x, &hs);
+        S.dg = x;
+        S.hs = hs;
+        S.beta = 1.0 - 3.0 * G * x / S.q_tr;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) S.nh[a] = e[a] / enorm;
+    } else {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) S.nh[a] = 0.0;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) S.tau[a] = ph.Kb * tr + 2.0 * G * S.beta * e[a];
+    // Kirchhoff stress tau = N diag(tau_a) N^T
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j) {
+            double s = 0.0;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) s += S.N[i][a] * S.tau[a] * S.N[j][a];
+            tau[i][j] = s;
+            tau[j][i] = s;
+        }
+    // F^-1 (adjugate)
+    {
+        double c00 = F[1][1] * F[2][2] - F[1][2] * F[2][1];
+        double c01 = F[1][2] * F[2][0] - F[1][0] * F[2][2];
+        double c02 = F[1][0] * F[2][1] - F[1][1] * F[2][0];
+        const double det = F[0][0] * c00 + F[0][1] * c01 + F[0][2] * c02;
+        const double id = 1.0 / det;
+        Finv[0][0] = c00 * id;
+        Finv[1][0] = c01 * id;
+        Finv[2][0] = c02 * id;
+        Finv[0][1] = (F[0][2] * F[2][1] - F[0][1] * F[2][2]) * id;
+        Finv[1][1] = (F[0][0] * F[2][2] - F[0][2] * F[2][0]) * id;
+        Finv[2][1] = (F[0][1] * F[2][0] - F[0][0] * F[2][1]) * id;
+        Finv[0][2] = (F[0][1] * F[1][2] - F[0][2] * F[1][1]) * id;
+        Finv[1][2] = (F[0][2] * F[1][0] - F[0][0] * F[1][2]) * id;
+        Finv[2][2] = (F[0][0] * F[1][1] - F[0][1] * F[1][0]) * id;
+        if (!(det > 0.0)) Finv[0][0] = NAN;   // det F <= 0: flagged as non-finite stress
+    }
+    if (S.plastic) {
+        // b_new = N diag(lambda_a exp(-2 dg sqrt(3/2) nhat_a)) N^T ; C^p_new^-1 = F^-1 b_new F^-T
+        double ln[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) ln[a] = S.lam[a] * exp(-2.0 * S.dg * 1.2247448713915890491 * S.nh[a]);
+        double bn[3][3], Wm[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = i; j < 3; ++j) {
+                double s = 0.0;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) s += S.N[i][a] * ln[a] * S.N[j][a];
+                bn[i][j] = s;
+                bn[j][i] = s;
+            }
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                double s = 0.0;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) s += Finv[i][k] * bn[k][j];
+                Wm[i][j] = s;
+            }
+        double c[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = i; j < 3; ++j) {
+                double s = 0.0;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) s += Wm[i][k] * Finv[j][k];
+                c[i][j] = s;
+            }
+        cp_new[0] = c[0][0]; cp_new[1] = c[0][1]; cp_new[2] = c[0][2];
+        cp_new[3] = c[1][1]; cp_new[4] = c[1][2]; cp_new[5] = c[2][2];
+        if (D == 2) { cp_new[2] = 0.0; cp_new[4] = 0.0; }
+        *xi_new = xi_n + S.dg;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) cp_new[k] = cp[k];
+        *xi_new = xi_n;
+    }
+}
+
+// Tangent data in the eigenbasis (precision T).
+template <typename T>
+struct TangentData {
+    T N[3][3];
+    T c[3][3];      // d tau_a / d eps_b
+    T th[3];        // theta_01, theta_02, theta_12
+    T inv2l[3];     // 1 / (2 lambda_a)
+    T Z[3][3];      // C^p^-1 F^T
+    T Finv[3][3];   // F^-1
+    T P[3][3];      // first Piola-Kirchhoff stress
+};
+
+template <int D, typename T>
+__device__ __forceinline__ void tangent_setup(const MatState &S, const PhaseD &ph, const double F[3][3],
+                                              const double cp[6], const double Finv[3][3],
+                                              const double P[3][3], TangentData<T> &td) {
+    const double G = ph.G;
+    // algorithmic moduli of the radial return in principal log strains
+    double cpl = 0.0;
+    if (S.plastic) cpl = 6.0 * G * G * (1.0 / (3.0 * G + S.hs) - S.dg / S.q_tr);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            td.c[a][b] = T(ph.Kb + 2.0 * G * S.beta * ((a == b ? 1.0 : 0.0) - 1.0 / 3.0) - cpl * S.nh[a] * S.nh[b]);
+    const double gb = G * S.beta;
+    td.th[0] = T(gb * log_divided_difference<double>(S.lam[0], S.lam[1]));
+    td.th[1] = T(gb * log_divided_difference<double>(S.lam[0], S.lam[2]));
+    td.th[2] = T(gb * log_divided_difference<double>(S.lam[1], S.lam[2]));
+#pragma unroll
+    for (int a = 0; a < 3; ++a) td.inv2l[a] = T(0.5 / S.lam[a]);
+    const double C[3][3] = {{cp[0], cp[1], cp[2]}, {cp[1], cp[3], cp[4]}, {cp[2], cp[4], cp[5]}};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) s += C[i][k] * F[j][k];
+            td.Z[i][j] = T(s);
+            td.N[i][j] = T(S.N[i][j]);
+            td.Finv[i][j] = T(Finv[i][j]);
+            td.P[i][j] = T(P[i][j]);
+        }
+}
+
+// dP for the direction dF = e_c (x) f  (dF_kl = delta_kc f_l).  Only the D x D block is formed.
+template <int D, typename T>
+__device__ __forceinline__ void tangent_direction(const TangentData<T> &td, int c, const T f[3], T dP[3][3]) {
+    // g = Z^T f, h = N^T g
+    T g[3], h[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        T s = T(0);
+#pragma unroll
+        for (int l = 0; l < D; ++l) s += td.Z[l][j] * f[l];
+        g[j] = s;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        T s = T(0);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) s += td.N[j][a] * g[j];
+        h[a] = s;
+    }
+    // db'_ab = N_ca h_b + h_a N_cb
+    T dbp[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = a; b < 3; ++b) {
+            dbp[a][b] = td.N[c][a] * h[b] + h[a] * td.N[c][b];
+            dbp[b][a] = dbp[a][b];
+        }
+    T dt[3][3];
+    T w[3] = {dbp[0][0] * td.inv2l[0], dbp[1][1] * td.inv2l[1], dbp[2][2] * td.inv2l[2]};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) dt[a][a] = td.c[a][0] * w[0] + td.c[a][1] * w[1] + td.c[a][2] * w[2];
+    dt[0][1] = dt[1][0] = td.th[0] * dbp[0][1];
+    dt[0][2] = dt[2][0] = td.th[1] * dbp[0][2];
+    dt[1][2] = dt[2][1] = td.th[2] * dbp[1][2];
+    // d tau = N dt N^T (D x D block), then dP = d tau F^-T - (P f) (x) F^-1[:, c]
+    T M[3][3];
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            T s = T(0);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) s += td.N[i][a] * dt[a][b];
+            M[i][b] = s;
+        }
+    T dtau[3][3];
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            T s = T(0);
+#pragma unroll
+            for (int b = 0; b < 3; ++b) s += M[i][b] * td.N[j][b];
+            dtau[i][j] = s;
+        }
+    T Pf[3];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        T s = T(0);
+#pragma unroll
+        for (int l = 0; l < D; ++l) s += td.P[i][l] * f[l];
+        Pf[i] = s;
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            T s = T(0);
+#pragma unroll
+            for (int k = 0; k < D; ++k) s += dtau[i][k] * td.Finv[j][k];
+            dP[i][j] = s - Pf[i] * td.Finv[j][c];
+        }
+}
+
+}  // namespace podecm

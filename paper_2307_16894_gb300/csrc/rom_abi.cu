@@ -1,0 +1,544 @@
+// C ABI of the GB300 hyper-reduced RVE solver (declarations and contracts in
+// include/podecm.h).  Host-side bookkeeping only: argument checks, device
+// buffers, and the launch sequence of one load step; all arithmetic of the
+// step runs in the kernels of kernels.cu.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/podecm.h"
+#include "kernels.cuh"
+
+namespace podecm {
+void set_phases(const PhaseD *ph, int n, cudaStream_t s);
+int launch_start(const Model &M, Batch Bt, const double *Fbar, const StepOpts &o, const double *dq_pred,
+                 cudaStream_t s);
+int launch_kernel(int which, const Model &M, Batch Bt, const StepOpts &o, int32_t *list_next, cudaStream_t s);
+int launch_finalize(const Model &M, Batch Bt, const StepOpts &o, double *Pbar, double *Abar, void *info,
+                    cudaStream_t s);
+}  // namespace podecm
+
+using namespace podecm;
+
+#define ROM_NKERNELS 6
+
+struct rom_ctx {
+    int dim = 0, device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    int n = 0, m = 0, n_par = 0, nphase = 0;
+    bool has_basis = false, has_cub = false, has_geom = false;
+    double omega = 1.0;
+    int64_t B = 0;
+    double *G_pt = nullptr, *G_T = nullptr, *w = nullptr, *Gmu_T = nullptr, *mu = nullptr;
+    float *G32 = nullptr;
+    int32_t *phase = nullptr;
+    // host-call staging
+    double *h_stage = nullptr;      // pinned
+    size_t h_stage_bytes = 0;
+    double *d_Fbar = nullptr, *d_Pbar = nullptr, *d_Abar = nullptr;
+    void *d_info = nullptr;
+    int64_t io_B = 0;
+    int32_t *h_count = nullptr;     // pinned
+    // per-kernel profiling (CUDA events around each launch on the context stream)
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    struct Rec { int kid; int ev0, ev1; double flops; };
+    std::vector<Rec> recs;
+    double prof_ms[ROM_NKERNELS] = {0};
+    int64_t prof_launches[ROM_NKERNELS] = {0};
+    double prof_flops[ROM_NKERNELS] = {0};
+};
+
+struct rom_state {
+    rom_ctx *ctx = nullptr;
+    int64_t B = 0;
+    int n = 0, m = 0, d = 0;
+    Batch bt{};
+    int32_t *list2 = nullptr;
+    std::vector<void *> allocs;
+};
+
+static rom_status fail(rom_ctx *c, rom_status s, const char *fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return s;
+}
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) return fail(ctx, ROM_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+static rom_status dalloc(rom_ctx *ctx, void **p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(ctx, e == cudaErrorMemoryAllocation ? ROM_E_NOMEM : ROM_E_CUDA, "cudaMalloc(%zu): %s", bytes,
+                    cudaGetErrorString(e));
+    }
+    return ROM_OK;
+}
+
+static void dfree(void *&p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+extern "C" {
+
+rom_status rom_create(rom_ctx **out, int dim, int device, void *cuda_stream) {
+    if (!out) return ROM_E_ARG;
+    *out = nullptr;
+    if (dim != 2 && dim != 3) return ROM_E_ARG;
+    rom_ctx *ctx = new (std::nothrow) rom_ctx();
+    if (!ctx) return ROM_E_NOMEM;
+    ctx->dim = dim;
+    ctx->device = device;
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) { delete ctx; return ROM_E_CUDA; }
+    if (cuda_stream) {
+        ctx->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) { delete ctx; return ROM_E_CUDA; }
+        ctx->own_stream = true;
+    }
+    if (cudaMallocHost((void **)&ctx->h_count, 64) != cudaSuccess) { delete ctx; return ROM_E_NOMEM; }
+    *out = ctx;
+    return ROM_OK;
+}
+
+static void free_io(rom_ctx *ctx) {
+    void *p;
+    p = ctx->d_Fbar; dfree(p); ctx->d_Fbar = nullptr;
+    p = ctx->d_Pbar; dfree(p); ctx->d_Pbar = nullptr;
+    p = ctx->d_Abar; dfree(p); ctx->d_Abar = nullptr;
+    dfree(ctx->d_info);
+    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+    ctx->h_stage = nullptr;
+    ctx->h_stage_bytes = 0;
+    ctx->io_B = 0;
+}
+
+rom_status rom_destroy(rom_ctx *ctx) {
+    if (!ctx) return ROM_E_ARG;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    void *p;
+    p = ctx->G_pt; dfree(p);
+    p = ctx->G_T; dfree(p);
+    p = ctx->G32; dfree(p);
+    p = ctx->w; dfree(p);
+    p = ctx->Gmu_T; dfree(p);
+    p = ctx->mu; dfree(p);
+    p = ctx->phase; dfree(p);
+    free_io(ctx);
+    if (ctx->h_count) cudaFreeHost(ctx->h_count);
+    for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return ROM_OK;
+}
+
+rom_status rom_load_basis(rom_ctx *ctx, int n, int m, const double *G) {
+    if (!ctx) return ROM_E_ARG;
+    if (n < 1 || n > MAX_N || m < 1 || !G) return fail(ctx, ROM_E_ARG, "rom_load_basis: bad n=%d m=%d or G", n, m);
+    if (ctx->has_cub && m != ctx->m) return fail(ctx, ROM_E_ARG, "rom_load_basis: m=%d differs from cubature m=%d", m, ctx->m);
+    for (size_t k = 0; k < (size_t)m * ctx->dim * ctx->dim * n; ++k)
+        if (!std::isfinite(G[k])) return fail(ctx, ROM_E_ARG, "rom_load_basis: non-finite G");
+    CK(cudaSetDevice(ctx->device));
+    const int d2 = ctx->dim * ctx->dim;
+    const size_t cnt = (size_t)m * d2 * n;
+    void *p;
+    p = ctx->G_pt; dfree(p); ctx->G_pt = nullptr;
+    p = ctx->G_T; dfree(p); ctx->G_T = nullptr;
+    p = ctx->G32; dfree(p); ctx->G32 = nullptr;
+    rom_status s;
+    if ((s = dalloc(ctx, (void **)&ctx->G_pt, cnt * 8)) != ROM_OK) return s;
+    if ((s = dalloc(ctx, (void **)&ctx->G_T, cnt * 8)) != ROM_OK) return s;
+    if ((s = dalloc(ctx, (void **)&ctx->G32, cnt * 4)) != ROM_OK) return s;
+    std::vector<double> gt(cnt);
+    std::vector<float> g32(cnt);
+    for (int i = 0; i < m; ++i)
+        for (int c = 0; c < d2; ++c)
+            for (int j = 0; j < n; ++j) {
+                const double g = G[((size_t)i * d2 + c) * n + j];
+                gt[((size_t)c * n + j) * m + i] = g;
+                g32[((size_t)i * d2 + c) * n + j] = (float)g;
+            }
+    CK(cudaMemcpy(ctx->G_pt, G, cnt * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->G_T, gt.data(), cnt * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->G32, g32.data(), cnt * 4, cudaMemcpyHostToDevice));
+    ctx->n = n;
+    ctx->m = m;
+    ctx->has_basis = true;
+    return ROM_OK;
+}
+
+rom_status rom_load_cubature(rom_ctx *ctx, int m, const double *w, const int32_t *phase, int n_phase,
+                             const rom_phase *phases, double omega_vol) {
+    if (!ctx) return ROM_E_ARG;
+    if (m < 1 || !w || !phase || !phases || n_phase < 1 || n_phase > MAX_PHASES || !(omega_vol > 0))
+        return fail(ctx, ROM_E_ARG, "rom_load_cubature: bad arguments");
+    if (ctx->has_basis && m != ctx->m) return fail(ctx, ROM_E_ARG, "rom_load_cubature: m=%d differs from basis m=%d", m, ctx->m);
+    for (int i = 0; i < m; ++i) {
+        if (!(w[i] > 0) || !std::isfinite(w[i])) return fail(ctx, ROM_E_ARG, "rom_load_cubature: weight %d not positive", i);
+        if (phase[i] < 0 || phase[i] >= n_phase) return fail(ctx, ROM_E_ARG, "rom_load_cubature: phase index %d out of range", i);
+    }
+    PhaseD ph[MAX_PHASES];
+    for (int k = 0; k < n_phase; ++k) {
+        const rom_phase &q = phases[k];
+        if (!(q.E > 0) || !(q.nu > -1 && q.nu < 0.5) || !(q.s0 > 0) || (q.hard_law != 0 && q.hard_law != 1))
+            return fail(ctx, ROM_E_ARG, "rom_load_cubature: bad phase %d", k);
+        ph[k].E = q.E; ph[k].nu = q.nu; ph[k].s0 = q.s0; ph[k].k = q.H_or_k; ph[k].p = q.p;
+        ph[k].law = q.hard_law;
+        ph[k].elastic = std::isinf(q.s0) ? 1 : 0;
+        ph[k].G = q.E / (2.0 * (1.0 + q.nu));
+        ph[k].lam = q.E * q.nu / ((1.0 + q.nu) * (1.0 - 2.0 * q.nu));
+        ph[k].Kb = ph[k].lam + 2.0 * ph[k].G / 3.0;
+    }
+    CK(cudaSetDevice(ctx->device));
+    void *p;
+    p = ctx->w; dfree(p); ctx->w = nullptr;
+    p = ctx->phase; dfree(p); ctx->phase = nullptr;
+    rom_status s;
+    if ((s = dalloc(ctx, (void **)&ctx->w, (size_t)m * 8)) != ROM_OK) return s;
+    if ((s = dalloc(ctx, (void **)&ctx->phase, (size_t)m * 4)) != ROM_OK) return s;
+    CK(cudaMemcpy(ctx->w, w, (size_t)m * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->phase, phase, (size_t)m * 4, cudaMemcpyHostToDevice));
+    set_phases(ph, n_phase, ctx->stream);
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->m = m;
+    ctx->nphase = n_phase;
+    ctx->omega = omega_vol;
+    ctx->has_cub = true;
+    return ROM_OK;
+}
+
+rom_status rom_set_geometry(rom_ctx *ctx, int64_t B, int n_par, const double *Gmu, const double *mu) {
+    if (!ctx) return ROM_E_ARG;
+    if (!ctx->has_basis && !ctx->has_cub) return fail(ctx, ROM_E_STATE, "rom_set_geometry before basis/cubature");
+    if (B < 1 || n_par < 1 || n_par > MAX_NPAR || !Gmu || !mu) return fail(ctx, ROM_E_ARG, "rom_set_geometry: bad arguments");
+    const int d = ctx->dim, d2 = d * d, m = ctx->m;
+    // det F_mu > 0 at every point of every instance (Eq. weakform-dep-mapped needs |det F_mu| > 0)
+    for (int64_t b = 0; b < B; ++b)
+        for (int i = 0; i < m; ++i) {
+            double F[9] = {0};
+            for (int a = 0; a < d; ++a)
+                for (int r = 0; r < d; ++r) {
+                    double s = (a == r) ? 1.0 : 0.0;
+                    for (int k = 0; k < n_par; ++k) s += mu[b * n_par + k] * Gmu[((size_t)i * d2 + a * d + r) * n_par + k];
+                    F[a * 3 + r] = s;
+                }
+            if (d == 2) F[8] = 1.0;
+            const double det = F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) +
+                               F[2] * (F[3] * F[7] - F[4] * F[6]);
+            if (!(det > 0) || !std::isfinite(det))
+                return fail(ctx, ROM_E_ARG, "rom_set_geometry: det F_mu = %g <= 0 at instance %lld point %d", det,
+                            (long long)b, i);
+        }
+    CK(cudaSetDevice(ctx->device));
+    std::vector<double> gt((size_t)d2 * n_par * m);
+    for (int i = 0; i < m; ++i)
+        for (int c = 0; c < d2; ++c)
+            for (int k = 0; k < n_par; ++k) gt[((size_t)c * n_par + k) * m + i] = Gmu[((size_t)i * d2 + c) * n_par + k];
+    void *p;
+    p = ctx->Gmu_T; dfree(p); ctx->Gmu_T = nullptr;
+    p = ctx->mu; dfree(p); ctx->mu = nullptr;
+    rom_status s;
+    if ((s = dalloc(ctx, (void **)&ctx->Gmu_T, gt.size() * 8)) != ROM_OK) return s;
+    if ((s = dalloc(ctx, (void **)&ctx->mu, (size_t)B * n_par * 8)) != ROM_OK) return s;
+    CK(cudaMemcpy(ctx->Gmu_T, gt.data(), gt.size() * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->mu, mu, (size_t)B * n_par * 8, cudaMemcpyHostToDevice));
+    ctx->B = B;
+    ctx->n_par = n_par;
+    ctx->has_geom = true;
+    return ROM_OK;
+}
+
+rom_status rom_state_create(rom_ctx *ctx, int64_t B, rom_state **out) {
+    if (!ctx || !out) return ROM_E_ARG;
+    *out = nullptr;
+    if (!ctx->has_basis || !ctx->has_cub) return fail(ctx, ROM_E_STATE, "rom_state_create before basis/cubature");
+    if (B < 1 || B > (int64_t)1 << 30) return fail(ctx, ROM_E_ARG, "rom_state_create: bad B");
+    CK(cudaSetDevice(ctx->device));
+    rom_state *st = new (std::nothrow) rom_state();
+    if (!st) return fail(ctx, ROM_E_NOMEM, "host allocation");
+    st->ctx = ctx;
+    st->B = B;
+    st->n = ctx->n;
+    st->m = ctx->m;
+    st->d = ctx->dim;
+    const int d2 = ctx->dim * ctx->dim, n = ctx->n, m = ctx->m;
+    const int ncp = ctx->dim == 2 ? 4 : 6;
+    Batch &bt = st->bt;
+    bt.B = B;
+    auto A = [&](void **p, size_t bytes) -> rom_status {
+        rom_status s = dalloc(ctx, p, bytes);
+        if (s == ROM_OK) st->allocs.push_back(*p);
+        return s;
+    };
+    rom_status s = ROM_OK;
+    const size_t Bz = (size_t)B;
+    if ((s = A((void **)&bt.q_n, Bz * n * 8)) || (s = A((void **)&bt.dq_prev, Bz * n * 8)) ||
+        (s = A((void **)&bt.cp, Bz * ncp * m * 8)) || (s = A((void **)&bt.xi, Bz * m * 8)) ||
+        (s = A((void **)&bt.q_trial, Bz * n * 8)) || (s = A((void **)&bt.q_acc, Bz * n * 8)) ||
+        (s = A((void **)&bt.dq, Bz * n * 8)) || (s = A((void **)&bt.ctl, Bz * sizeof(Ctl))) ||
+        (s = A((void **)&bt.list, Bz * 4)) || (s = A((void **)&st->list2, Bz * 4)) ||
+        (s = A((void **)&bt.counts, 64)) || (s = A((void **)&bt.v, Bz * d2 * m * 8)) ||
+        (s = A((void **)&bt.wP, Bz * d2 * m * 8)) || (s = A((void **)&bt.At, Bz * d2 * d2 * m * 8)) ||
+        (s = A((void **)&bt.cp_tr, Bz * ncp * m * 8)) || (s = A((void **)&bt.xi_tr, Bz * m * 8)) ||
+        (s = A((void **)&bt.pl, Bz * m)) || (s = A((void **)&bt.r, Bz * n * 8)) ||
+        (s = A((void **)&bt.K, Bz * n * n * 8)) || (s = A((void **)&bt.Ubar, Bz * d2 * 8)) ||
+        (s = A((void **)&bt.Rbar, Bz * d2 * 8))) {
+        rom_state_destroy(st);
+        return s;
+    }
+    // virgin state: a = 0, C^p^-1 = I, xi = 0
+    std::vector<double> cp(Bz * ncp * m, 0.0);
+    const int diag2[4] = {1, 0, 1, 1}, diag3[6] = {1, 0, 0, 1, 0, 1};
+    for (size_t b = 0; b < Bz; ++b)
+        for (int c = 0; c < ncp; ++c) {
+            const double v = ctx->dim == 2 ? diag2[c] : diag3[c];
+            for (int i = 0; i < m; ++i) cp[(b * ncp + c) * m + i] = v;
+        }
+    cudaError_t e;
+    if ((e = cudaMemset(bt.q_n, 0, Bz * n * 8)) != cudaSuccess || (e = cudaMemset(bt.dq_prev, 0, Bz * n * 8)) != cudaSuccess ||
+        (e = cudaMemset(bt.xi, 0, Bz * m * 8)) != cudaSuccess ||
+        (e = cudaMemcpy(bt.cp, cp.data(), cp.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess) {
+        rom_state_destroy(st);
+        return fail(ctx, ROM_E_CUDA, "rom_state_create: %s", cudaGetErrorString(e));
+    }
+    *out = st;
+    return ROM_OK;
+}
+
+rom_status rom_state_destroy(rom_state *st) {
+    if (!st) return ROM_E_ARG;
+    if (st->ctx) cudaSetDevice(st->ctx->device);
+    for (void *p : st->allocs) cudaFree(p);
+    delete st;
+    return ROM_OK;
+}
+
+rom_status rom_state_export(rom_ctx *ctx, const rom_state *st, double *a, double *Cpinv, double *xi) {
+    if (!ctx || !st || st->ctx != ctx) return ROM_E_ARG;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const int n = st->n, m = st->m, ncp = st->d == 2 ? 4 : 6;
+    const size_t B = (size_t)st->B;
+    if (a) CK(cudaMemcpy(a, st->bt.q_n, B * n * 8, cudaMemcpyDeviceToHost));
+    if (xi) CK(cudaMemcpy(xi, st->bt.xi, B * m * 8, cudaMemcpyDeviceToHost));
+    if (Cpinv) {
+        std::vector<double> t(B * ncp * m);
+        CK(cudaMemcpy(t.data(), st->bt.cp, t.size() * 8, cudaMemcpyDeviceToHost));
+        for (size_t b = 0; b < B; ++b)
+            for (int c = 0; c < ncp; ++c)
+                for (int i = 0; i < m; ++i) Cpinv[(b * m + i) * ncp + c] = t[(b * ncp + c) * m + i];
+    }
+    return ROM_OK;
+}
+
+rom_status rom_state_import(rom_ctx *ctx, rom_state *st, const double *a, const double *Cpinv, const double *xi) {
+    if (!ctx || !st || st->ctx != ctx) return ROM_E_ARG;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const int n = st->n, m = st->m, ncp = st->d == 2 ? 4 : 6;
+    const size_t B = (size_t)st->B;
+    if (a) {
+        CK(cudaMemcpy(st->bt.q_n, a, B * n * 8, cudaMemcpyHostToDevice));
+        CK(cudaMemset(st->bt.dq_prev, 0, B * n * 8));
+    }
+    if (xi) CK(cudaMemcpy(st->bt.xi, xi, B * m * 8, cudaMemcpyHostToDevice));
+    if (Cpinv) {
+        std::vector<double> t(B * ncp * m);
+        for (size_t b = 0; b < B; ++b)
+            for (int c = 0; c < ncp; ++c)
+                for (int i = 0; i < m; ++i) t[(b * ncp + c) * m + i] = Cpinv[(b * m + i) * ncp + c];
+        CK(cudaMemcpy(st->bt.cp, t.data(), t.size() * 8, cudaMemcpyHostToDevice));
+    }
+    return ROM_OK;
+}
+
+static rom_status check_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts) {
+    if (!ctx || !st || !opts || st->ctx != ctx) return ROM_E_ARG;
+    if (!ctx->has_basis || !ctx->has_cub || !ctx->has_geom) return fail(ctx, ROM_E_STATE, "rom_step before basis/cubature/geometry");
+    if (st->B != ctx->B) return fail(ctx, ROM_E_STATE, "rom_step: state has B=%lld but geometry B=%lld", (long long)st->B, (long long)ctx->B);
+    if (st->n != ctx->n || st->m != ctx->m) return fail(ctx, ROM_E_STATE, "rom_step: state built for another model");
+    if (!(opts->tol_rel >= 0) || !(opts->tol_abs >= 0) || opts->max_iter < 0 || opts->max_iter > 1000 ||
+        opts->max_ls < 0 || opts->max_ls > 60 || opts->precision < 0 || opts->precision > 3 || opts->start < 0 ||
+        opts->start > 2)
+        return fail(ctx, ROM_E_ARG, "rom_step: bad options");
+    if (opts->start == ROM_START_MLP) return fail(ctx, ROM_E_STATE, "rom_step: no MLP loaded");
+    if (opts->precision >= ROM_PREC_TF32) return fail(ctx, ROM_E_ARG, "rom_step: precision mode not available");
+    return ROM_OK;
+}
+
+static Model make_model(const rom_ctx *ctx) {
+    Model M;
+    M.d = ctx->dim; M.d2 = ctx->dim * ctx->dim; M.n = ctx->n; M.m = ctx->m; M.n_par = ctx->n_par;
+    M.nphase = ctx->nphase; M.ncp = ctx->dim == 2 ? 4 : 6;
+    M.G_pt = ctx->G_pt; M.G_T = ctx->G_T; M.G32_pt = ctx->G32; M.w = ctx->w; M.phase = ctx->phase;
+    M.Gmu_T = ctx->Gmu_T; M.omega = ctx->omega;
+    return M;
+}
+
+}  // extern "C"
+
+static int prof_event(rom_ctx *ctx, int idx) {
+    while ((int)ctx->ev_pool.size() <= idx) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return -1;
+        ctx->ev_pool.push_back(e);
+    }
+    cudaEventRecord(ctx->ev_pool[idx], ctx->stream);
+    return idx;
+}
+
+// launch one kernel group `kid` (0 start, 1 constitutive, 2 assemble, 3 solve, 4 finalize, 5 advance)
+// with optional event timing and an algorithmic FLOP count for the roofline
+template <typename F>
+static int timed(rom_ctx *ctx, int kid, double flops, F &&launch) {
+    int e0 = -1;
+    if (ctx->prof) e0 = prof_event(ctx, (int)ctx->recs.size() * 2);
+    const int r = launch();
+    if (ctx->prof && e0 >= 0) {
+        const int e1 = prof_event(ctx, e0 + 1);
+        ctx->recs.push_back({kid, e0, e1, flops});
+    }
+    return r;
+}
+
+static void prof_collect(rom_ctx *ctx) {
+    if (!ctx->prof || ctx->recs.empty()) return;
+    cudaStreamSynchronize(ctx->stream);
+    for (const auto &r : ctx->recs) {
+        float ms = 0.f;
+        if (r.ev1 >= 0 && cudaEventElapsedTime(&ms, ctx->ev_pool[r.ev0], ctx->ev_pool[r.ev1]) == cudaSuccess) {
+            ctx->prof_ms[r.kid] += ms;
+            ctx->prof_launches[r.kid] += (r.kid == 0 || r.kid == 5) ? 2 : 1;
+            ctx->prof_flops[r.kid] += r.flops;
+        }
+    }
+    ctx->recs.clear();
+}
+
+static rom_status run_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts, const double *Fbar_d, double *Pbar_d,
+                           double *Abar_d, void *info_d) {
+    StepOpts o;
+    o.tol_rel = opts->tol_rel; o.tol_abs = opts->tol_abs; o.max_iter = opts->max_iter; o.max_ls = opts->max_ls;
+    o.precision = opts->precision; o.start = opts->start; o.polar = opts->polar_split; o.want_abar = opts->want_abar;
+    const Model M = make_model(ctx);
+    Batch bt = st->bt;
+    bt.mu = ctx->mu;
+    int32_t *lists[2] = {st->bt.list, st->list2};
+    const double n = M.n, m = M.m, d2 = M.d2, d4 = d2 * d2;
+    // algorithmic FLOPs per active instance: kinematics + force 2 m d2 n each; Y = At G: 2 m d4 n;
+    // K upper triangle incl. diagonal: m d2 n (n + 1); LU + solve: 2 n^3 / 3 + 2 n^2
+    const double fl_asm = 2 * m * d4 * n + m * d2 * n * (n + 1) + 2 * m * d2 * n;
+    const double fl_kin = 2 * m * d2 * n;
+    const double fl_lu = 2 * n * n * n / 3 + 2 * n * n;
+    if (timed(ctx, 0, 0.0, [&] { return launch_start(M, bt, Fbar_d, o, nullptr, ctx->stream); }))
+        return fail(ctx, ROM_E_ARG, "launch_start");
+    const int max_pass = (opts->max_iter + 1) * (opts->max_ls + 1) + 2;
+    int64_t n_act = st->B;
+    for (int pass = 0; pass < max_pass; ++pass) {
+        bt.list = lists[pass & 1];
+        int32_t *nxt = lists[(pass + 1) & 1];
+        const double na = (double)n_act;
+        if (timed(ctx, 1, na * fl_kin, [&] { return launch_kernel(1, M, bt, o, nxt, ctx->stream); }) ||
+            timed(ctx, 2, na * fl_asm, [&] { return launch_kernel(2, M, bt, o, nxt, ctx->stream); }) ||
+            timed(ctx, 3, na * fl_lu, [&] { return launch_kernel(3, M, bt, o, nxt, ctx->stream); }) ||
+            timed(ctx, 5, 0.0, [&] { return launch_kernel(5, M, bt, o, nxt, ctx->stream); }))
+            return fail(ctx, ROM_E_ARG, "rom_step: basis size n=%d not supported by the assembly kernel", M.n);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(ctx->h_count, bt.counts, 4, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        n_act = ctx->h_count[0];
+        if (n_act == 0) break;
+    }
+    if (timed(ctx, 4, 0.0, [&] { return launch_finalize(M, bt, o, Pbar_d, Abar_d, info_d, ctx->stream); }))
+        return fail(ctx, ROM_E_ARG, "rom_step: n*d*d too large for the finalize kernel");
+    CK(cudaGetLastError());
+    prof_collect(ctx);
+    return ROM_OK;
+}
+
+extern "C" {
+
+rom_status rom_step_device(rom_ctx *ctx, rom_state *st, const rom_opts *opts, const double *Fbar_d, double *Pbar_d,
+                           double *Abar_d, rom_step_info *info_d) {
+    rom_status s = check_step(ctx, st, opts);
+    if (s != ROM_OK) return s;
+    if (!Fbar_d || !Pbar_d || (opts->want_abar && !Abar_d)) return fail(ctx, ROM_E_ARG, "rom_step_device: null buffer");
+    CK(cudaSetDevice(ctx->device));
+    return run_step(ctx, st, opts, Fbar_d, Pbar_d, Abar_d, info_d);
+}
+
+rom_status rom_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts, const double *Fbar, double *Pbar,
+                    double *Abar, rom_step_info *info) {
+    rom_status s = check_step(ctx, st, opts);
+    if (s != ROM_OK) return s;
+    if (!Fbar || !Pbar || (opts->want_abar && !Abar)) return fail(ctx, ROM_E_ARG, "rom_step: null buffer");
+    CK(cudaSetDevice(ctx->device));
+    const int64_t B = st->B;
+    const int d2 = ctx->dim * ctx->dim;
+    if (ctx->io_B != B) {
+        free_io(ctx);
+        if ((s = dalloc(ctx, (void **)&ctx->d_Fbar, (size_t)B * d2 * 8)) || (s = dalloc(ctx, (void **)&ctx->d_Pbar, (size_t)B * d2 * 8)) ||
+            (s = dalloc(ctx, (void **)&ctx->d_Abar, (size_t)B * d2 * d2 * 8)) ||
+            (s = dalloc(ctx, &ctx->d_info, (size_t)B * sizeof(rom_step_info))))
+            return s;
+        ctx->io_B = B;
+    }
+    CK(cudaMemcpyAsync(ctx->d_Fbar, Fbar, (size_t)B * d2 * 8, cudaMemcpyHostToDevice, ctx->stream));
+    s = run_step(ctx, st, opts, ctx->d_Fbar, ctx->d_Pbar, ctx->d_Abar, ctx->d_info);
+    if (s != ROM_OK) return s;
+    CK(cudaMemcpyAsync(Pbar, ctx->d_Pbar, (size_t)B * d2 * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    if (Abar && opts->want_abar)
+        CK(cudaMemcpyAsync(Abar, ctx->d_Abar, (size_t)B * d2 * d2 * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    if (info) CK(cudaMemcpyAsync(info, ctx->d_info, (size_t)B * sizeof(rom_step_info), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return ROM_OK;
+}
+
+rom_status rom_sync(rom_ctx *ctx) {
+    if (!ctx) return ROM_E_ARG;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return ROM_OK;
+}
+
+const char *rom_last_error(const rom_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+rom_status rom_profile(rom_ctx *ctx, int enable) {
+    if (!ctx) return ROM_E_ARG;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->recs.clear();
+    for (int k = 0; k < ROM_NKERNELS; ++k) { ctx->prof_ms[k] = 0; ctx->prof_launches[k] = 0; ctx->prof_flops[k] = 0; }
+    ctx->prof = enable != 0;
+    return ROM_OK;
+}
+
+rom_status rom_profile_read(rom_ctx *ctx, int kernel, double *ms, int64_t *launches, double *flops) {
+    if (!ctx || kernel < 0 || kernel >= ROM_NKERNELS) return ROM_E_ARG;
+    if (ms) *ms = ctx->prof_ms[kernel];
+    if (launches) *launches = ctx->prof_launches[kernel];
+    if (flops) *flops = ctx->prof_flops[kernel];
+    return ROM_OK;
+}
+
+}  // extern "C"
