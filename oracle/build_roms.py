@@ -45,7 +45,8 @@ CONFIGS = {
                train=[("stretch", 2001 + i, 25) for i in range(5)], mu_range=(0.2, 0.35)),
     # 3D 24^3 hex8, spherical elastic inclusion (stiffness ratio 10), n=64 (96 kept), m=600
     "c3": dict(d=3, N=24, n=96, n_use=64, m=600, L=20, map_seed=11, phases=[MATRIX, INCLUSION],
-               train=[("stretch", 3001 + i, 20) for i in range(6)], mu_range=(0.15, 0.35)),
+               train=[("stretch", 3001 + i, 20) for i in range(5)], mu_range=(0.15, 0.35),
+               fft_pcg=True, tol_rel=1e-8, parallel=True),
 }
 
 
@@ -60,22 +61,18 @@ def build(name, verbose=True, nthreads=None):
     if verbose:
         print("[%s] mesh ne=%d ndof=%d nq=%d" % (name, mesh.ne, mesh.ndof, mesh.nq), flush=True)
     snaps_w, snaps_W, train_info = [], [], []
-    for kind, seed, nst in cfg["train"]:
-        rng = np.random.default_rng(seed)
-        mu = rng.uniform(*cfg["mu_range"], size=npar)
-        coef = inputs.map_coefficients(d, mu)
-        Finv, J = fe.geometry(Gq, coef)
-        if kind == "u2d":
-            path = inputs.training_path_2d(seed, nst)
-        else:
-            path = inputs.stretch_path(d, seed, nst, rotate=False)
-        t1 = time.time()
-        out = fe.solve_path(mesh, cfg["phases"], Finv, J, path, nthreads=nthreads, verbose=verbose)
+    jobs = [(name, kind, seed, nst) for kind, seed, nst in cfg["train"]]
+    if cfg.get("parallel"):
+        import multiprocessing as mp
+        nproc = min(len(jobs), os.cpu_count() or 1)
+        with mp.get_context("spawn").Pool(nproc) as pool:
+            results = pool.starmap(_train_path, [j + (max(1, (os.cpu_count() or 1) // nproc), verbose) for j in jobs])
+    else:
+        results = [_train_path(*j, nthreads, verbose) for j in jobs]
+    for out, info in results:
         snaps_w += out["w"]
         snaps_W += out["W"]
-        train_info.append(dict(seed=seed, mu=mu, steps=nst, Pbar_last=out["Pbar"][-1]))
-        if verbose:
-            print("[%s] training path seed %d done in %.1fs" % (name, seed, time.time() - t1), flush=True)
+        train_info.append(info)
     n, L, m = cfg["n"], cfg["L"], cfg["m"]
     Phi, lam_w, MV = reduction.displacement_pod(mesh, snaps_w, n)
     Bm, lam_W = reduction.stress_pod(mesh, snaps_W, L)
@@ -99,6 +96,30 @@ def build(name, verbose=True, nthreads=None):
     if verbose:
         print("[%s] done in %.1fs" % (name, time.time() - t0), flush=True)
     return rom
+
+
+def _train_path(name, kind, seed, nst, nthreads, verbose):
+    """One seeded full-order training solve (Algorithm 1 offline lines 2-4)."""
+    cfg = CONFIGS[name]
+    d, N = cfg["d"], cfg["N"]
+    mesh = fe.Mesh(d, N, phase_2d if d == 2 else phase_3d)
+    npar = 1 if d == 2 else 3
+    modes = inputs.map_modes(d, npar, cfg["map_seed"])
+    Gq = inputs.map_gradients(modes, mesh.X.reshape(-1, d))
+    rng = np.random.default_rng(seed)
+    mu = rng.uniform(*cfg["mu_range"], size=npar)
+    Finv, J = fe.geometry(Gq, inputs.map_coefficients(d, mu))
+    if kind == "u2d":
+        path = inputs.training_path_2d(seed, nst)
+    else:
+        path = inputs.stretch_path(d, seed, nst, rotate=False)
+    precond = fe.FFTPreconditioner(mesh, cfg["phases"][0]["E"], cfg["phases"][0]["nu"]) if cfg.get("fft_pcg") else None
+    t1 = time.time()
+    out = fe.solve_path(mesh, cfg["phases"], Finv, J, path, nthreads=nthreads, verbose=verbose,
+                        tol_rel=cfg.get("tol_rel", 1e-10), precond=precond)
+    if verbose:
+        print("[%s] training path seed %d done in %.1fs" % (name, seed, time.time() - t1), flush=True)
+    return dict(w=out["w"], W=out["W"]), dict(seed=seed, mu=mu, steps=nst, Pbar_last=out["Pbar"][-1])
 
 
 def pack(mesh, cfg, modes, Gq, gradPhi, sel, wsel, err, n_use):

@@ -29,7 +29,7 @@ class Mesh:
 
     phase_fn(centroid[d]) -> -1 (void, removed), 0 (matrix) or 1 (inclusion)."""
 
-    def __init__(self, d, N, phase_fn):
+    def __init__(self, d, N, phase_fn, fix_node=True):
         self.d, self.N = d, N
         h = 1.0 / N
         self.h = h
@@ -70,7 +70,7 @@ class Mesh:
         self.nnode = N ** d
         used = np.zeros(self.nnode, bool)
         used[self.conn.ravel()] = True
-        fixed = int(self.conn[0, 0])
+        fixed = int(self.conn[0, 0]) if fix_node else -1
         dofmap = -np.ones((self.nnode, d), dtype=np.int64)
         k = 0
         for nid in range(self.nnode):
@@ -117,6 +117,51 @@ class Mesh:
         return self.assemble_mat(np.broadcast_to(blk, (self.ne, nen * d, nen * d)).copy())
 
 
+class FFTPreconditioner:
+    """Approximate inverse of the periodic stiffness matrix by the homogeneous isotropic
+    reference operator K0 on the same structured grid: K0 is block-circulant, so
+    K0^-1 r is one FFT, a 3x3 (2x2) solve per frequency and one inverse FFT (zero
+    frequency removed).  Used as the preconditioner of conjugate gradients for the
+    full-order training solves on large meshes (no void elements)."""
+
+    def __init__(self, mesh, E, nu):
+        d, N = mesh.d, mesh.N
+        full = Mesh(d, N, lambda c: 0, fix_node=False)
+        Finv = np.tile(np.eye(d), (full.nq, 1, 1))
+        J = np.ones(full.nq)
+        res = fe_elements(full, [dict(E=E, nu=nu, law="power", s0=np.inf, k=0.0, p=1.0)], Finv, J, np.eye(d),
+                          np.zeros(full.ndof), np.tile(np.eye(3).ravel(), (full.nq, 1)), np.zeros(full.nq))
+        K0 = full.assemble_mat(res["Ke"])
+        # dof index of (node, c) in the full mesh is 3 node + c (all nodes used)
+        shape = (N,) * d
+        sym = np.zeros(shape + (d, d), dtype=complex)
+        for c in range(d):
+            col = K0[:, c].toarray().ravel().reshape(N ** d, d)            # stencil around node 0
+            g = col.reshape(shape[::-1] + (d,))                              # [z][y][x] ordering of node ids
+            g = np.moveaxis(g, -1, 0)
+            sym[..., :, c] = np.moveaxis(np.fft.fftn(g, axes=tuple(range(1, d + 1))), 0, -1)
+        zero = (0,) * d
+        sym[zero] = np.eye(d)
+        inv = np.linalg.inv(sym)
+        inv[zero] = 0.0
+        self.inv, self.d, self.N, self.mesh = inv, d, N, mesh
+        nid = np.repeat(np.arange(mesh.nnode), d)
+        comp = np.tile(np.arange(d), mesh.nnode)
+        dof = mesh.dofmap.reshape(-1)
+        keep = dof >= 0
+        self.pos = (nid[keep] * d + comp[keep])[np.argsort(dof[keep])]
+
+    def apply(self, r):
+        d, N = self.d, self.N
+        full = np.zeros(N ** d * d)
+        full[self.pos] = r
+        g = np.moveaxis(full.reshape((N,) * d + (d,)), -1, 0)
+        gh = np.fft.fftn(g, axes=tuple(range(1, d + 1)))
+        uh = np.einsum("...ab,b...->a...", self.inv, gh)
+        u = np.real(np.fft.ifftn(uh, axes=tuple(range(1, d + 1))))
+        return np.moveaxis(u, 0, -1).reshape(-1)[self.pos]
+
+
 def geometry(Gmu_q, coef):
     """F_mu = I + sum_k coef_k Gmu_k at every point; returns (Finv, J) with J = |det F_mu|."""
     d = Gmu_q.shape[-2]
@@ -127,10 +172,19 @@ def geometry(Gmu_q, coef):
     return np.linalg.inv(Fm), np.abs(det)
 
 
-def _newton(mesh, phases, Finv, J, Fb, w, Fp, xi, tol_rel, tol_abs, max_iter, nthreads):
+def _linsolve(K, b, precond):
+    if precond is None:
+        return spla.spsolve(K.tocsc(), b)
+    M = spla.LinearOperator(K.shape, matvec=precond.apply)
+    x, info = spla.cg(K.tocsr(), b, rtol=1e-11, atol=0.0, maxiter=4000, M=M)
+    return x if info == 0 else np.full_like(b, np.nan)
+
+
+def _newton(mesh, phases, Finv, J, Fb, w, Fp, xi, tol_rel, tol_abs, max_iter, nthreads, precond=None):
     """Newton on f(w) = 0 at fixed history (Eq. full_newton), with a backtracking
     line search on ||f||_2 (halving, up to 10 times) for robustness of the
-    training solves.  Returns (w, res, iters) or None when it fails."""
+    training solves; trial points are evaluated without the tangent.  Returns
+    (w, res, iters) or None when it fails."""
     res = fe_elements(mesh, phases, Finv, J, Fb, w, Fp, xi, want_K=True, nthreads=nthreads)
     f = mesh.assemble_vec(res["fe"])
     rn = np.linalg.norm(f)
@@ -142,14 +196,16 @@ def _newton(mesh, phases, Finv, J, Fb, w, Fp, xi, tol_rel, tol_abs, max_iter, nt
             return w, res, it
         if it == max_iter:
             return None
+        if res["Ke"] is None:
+            res = fe_elements(mesh, phases, Finv, J, Fb, w, Fp, xi, want_K=True, nthreads=nthreads)
         K = mesh.assemble_mat(res["Ke"])
-        dw = spla.spsolve(K.tocsc(), -f)
+        dw = _linsolve(K, -f, precond)
         if not np.all(np.isfinite(dw)):
             return None
         step = 1.0
         for _ in range(11):
             wt = w + step * dw
-            rt = fe_elements(mesh, phases, Finv, J, Fb, wt, Fp, xi, want_K=True, nthreads=nthreads)
+            rt = fe_elements(mesh, phases, Finv, J, Fb, wt, Fp, xi, want_K=False, nthreads=nthreads)
             ft = mesh.assemble_vec(rt["fe"])
             rnt = np.linalg.norm(ft)
             if np.isfinite(rnt) and rnt < rn:
@@ -160,7 +216,7 @@ def _newton(mesh, phases, Finv, J, Fb, w, Fp, xi, tol_rel, tol_abs, max_iter, nt
 
 
 def solve_path(mesh, phases, Finv, J, Fbar_path, tol_rel=1e-10, tol_abs=1e-9, max_iter=40, nthreads=None,
-               want_snapshots=True, want_Abar=False, verbose=False, max_split=8):
+               want_snapshots=True, want_Abar=False, verbose=False, max_split=8, precond=None):
     """Full-order Newton along a macro load path (Sec. 2.1); each step starts from the
     previous solution.  A step whose Newton fails is split into two half increments
     (recursively, up to max_split levels; the paper notes that small load steps can be
@@ -182,7 +238,7 @@ def solve_path(mesh, phases, Finv, J, Fbar_path, tol_rel=1e-10, tol_abs=1e-9, ma
         nsub = 0
         while todo:
             Ft, lev = todo[-1]
-            sol = _newton(mesh, phases, Finv, J, Ft, w, Fp, xi, tol_rel, tol_abs, max_iter, nthreads)
+            sol = _newton(mesh, phases, Finv, J, Ft, w, Fp, xi, tol_rel, tol_abs, max_iter, nthreads, precond)
             if sol is None:
                 if lev >= max_split:
                     raise RuntimeError("FE Newton failed at step %d even after %d splits" % (k, lev))
@@ -190,6 +246,7 @@ def solve_path(mesh, phases, Finv, J, Fbar_path, tol_rel=1e-10, tol_abs=1e-9, ma
                 todo.append((Fmid, lev + 1))
                 continue
             w, res, it = sol
+            Fp_prev_step, xi_prev_step = Fp, xi
             Fp, xi = res["Fp_tr"], res["xi_tr"]
             Fprev = Ft
             todo.pop()
@@ -206,6 +263,9 @@ def solve_path(mesh, phases, Finv, J, Fbar_path, tol_rel=1e-10, tol_abs=1e-9, ma
             out["w"].append(w.copy())
             out["W"].append(np.einsum("qab,qcb->qac", P, Finv_q) * Jq[:, None, None])
         if want_Abar:
+            if res["Ke"] is None:
+                res = fe_elements(mesh, phases, Finv, J, Fprev, w, Fp_prev_step, xi_prev_step, want_K=True,
+                                  nthreads=nthreads)
             K = mesh.assemble_mat(res["Ke"])
             out["Abar"].append(effective_stiffness(mesh, K, res["Aq"], Finv, J))
     return out

@@ -448,7 +448,7 @@ static void *fe_worker(void *p) {
             }
             embed3(d, F, F3);
             double *P = a->Pq + qp * d2, *A = a->Aq + qp * d4;
-            a->plq[qp] = orc_material(d, F3, a->Fp + qp * 9, a->xi[qp], ph, P, A, a->P33q + qp,
+            a->plq[qp] = orc_material(d, F3, a->Fp + qp * 9, a->xi[qp], ph, P, Ke ? A : NULL, a->P33q + qp,
                                       a->Fp_tr + qp * 9, a->xi_tr + qp);
             const double wJ = a->gw[g] * a->J[qp];
             for (int node = 0; node < nen; ++node)
