@@ -35,6 +35,7 @@
 #ifndef PODECM_H
 #define PODECM_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -167,6 +168,55 @@ const char *rom_last_error(const rom_ctx *ctx);
  * 2 n^3/3 + 2 n^2 -- per active instance and launch).  Any pointer may be NULL. */
 rom_status rom_profile(rom_ctx *ctx, int enable);
 rom_status rom_profile_read(rom_ctx *ctx, int kernel, double *ms, int64_t *launches, double *flops);
+
+/* ---------------------------------------------------------------------------
+ * Allocation-free step.  The paper has no counterpart: this is a deployment
+ * variant of rom_step_device for callers that cannot call cudaMalloc -- a
+ * macro solver running inside a pre-sized memory pool or arena it does not
+ * own, a host application that must not grow its device footprint after
+ * start-up, or code issuing the step while a stream is being captured (no
+ * allocation allowed there).
+ *
+ * The caller passes every array on the device: the model in the public
+ * layouts (G[m][d*d][n], w[m], phase[m], Gmu[m][d*d][n_par]; the phase table
+ * phases[n_phase] on the host), the geometry mu[B][n_par], the state -- a[B][n],
+ * the last converged increment da_prev[B][n] (zero at the start), the history
+ * Cpinv[B][nc][m] (component-major per instance: nc = 4 in 2D (C11, C12, C22,
+ * C33), 6 in 3D (C11, C12, C13, C22, C23, C33); identity at the start) and
+ * xi[B][m] -- all updated in place for converged instances, and Fbar[B][d*d],
+ * Pbar[B][d*d], Abar[B][d^4] (NULL if want_abar = 0), info[B] (may be NULL).
+ * The work arrays of the step live in one static device array of
+ * ROM_NOALLOC_SCRATCH_BYTES (16 MiB) that every GPU loading the library holds
+ * until the process exits; a batch whose work space does not fit (about
+ * 10 KB per instance for n = 8, m = 40 in 2D and 42 KB for n = 24, m = 160)
+ * is rejected with ROM_E_ARG.  The call allocates nothing: no cudaMalloc,
+ * cudaFree or allocating library routine.
+ *  - The first call on a device looks up the device address of the static
+ *    array (cudaGetSymbolAddress, with that device current); make that first
+ *    call before any stream capture.
+ *  - All calls on a device share the array, and it keeps the previous call's
+ *    contents (the call clears what must start at zero).  Calls that overlap
+ *    on the GPU -- on different streams or host threads -- race on it; so do
+ *    contexts' steps running at the same time, because the call temporarily
+ *    installs its phase table in the library's device-wide material table and
+ *    restores it at the end.
+ *  - precision: ROM_PREC_FP64 or ROM_PREC_FP32; start: PLAIN or PREV.  The
+ *    geometry is not validated (det F_mu > 0 is the caller's responsibility).
+ *  - Blocking on `cuda_stream` (a cudaStream_t, NULL = legacy default stream).
+ *    errbuf (errlen bytes, may be NULL) receives the text of an error. */
+#define ROM_NOALLOC_SCRATCH_BYTES (16 * 1024 * 1024)
+typedef struct {
+    int32_t dim, n, m, n_par, n_phase;
+    const double *G, *w;
+    const int32_t *phase;
+    const double *Gmu;
+    const rom_phase *phases;
+    double omega_vol;
+} rom_noalloc_model;
+
+rom_status rom_step_noalloc(const rom_noalloc_model *model, int64_t B, const double *mu, double *a, double *da_prev,
+                            double *Cpinv, double *xi, const rom_opts *opts, const double *Fbar, double *Pbar,
+                            double *Abar, rom_step_info *info, void *cuda_stream, char *errbuf, size_t errlen);
 
 #ifdef __cplusplus
 }

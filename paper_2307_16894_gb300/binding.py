@@ -23,7 +23,8 @@ INFO_DTYPE = np.dtype([("iters", "<i4"), ("evals", "<i4"), ("status", "<i4"), ("
 
 EXPORTED = ["rom_create", "rom_destroy", "rom_load_basis", "rom_load_cubature", "rom_set_geometry",
             "rom_state_create", "rom_state_destroy", "rom_state_export", "rom_state_import", "rom_step",
-            "rom_step_device", "rom_sync", "rom_last_error", "rom_profile", "rom_profile_read"]
+            "rom_step_device", "rom_sync", "rom_last_error", "rom_profile", "rom_profile_read",
+            "rom_step_noalloc"]
 
 KERNEL_GROUPS = ["start", "constitutive", "assemble", "solve", "finalize", "bookkeeping"]
 
@@ -37,6 +38,13 @@ class RomOpts(ctypes.Structure):
     _fields_ = [("tol_rel", ctypes.c_double), ("tol_abs", ctypes.c_double), ("max_iter", ctypes.c_int32),
                 ("max_ls", ctypes.c_int32), ("precision", ctypes.c_int32), ("start", ctypes.c_int32),
                 ("polar_split", ctypes.c_int32), ("want_abar", ctypes.c_int32)]
+
+
+class RomNoallocModel(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("n", ctypes.c_int32), ("m", ctypes.c_int32), ("n_par", ctypes.c_int32),
+                ("n_phase", ctypes.c_int32), ("G", ctypes.c_void_p), ("w", ctypes.c_void_p),
+                ("phase", ctypes.c_void_p), ("Gmu", ctypes.c_void_p), ("phases", ctypes.c_void_p),
+                ("omega_vol", ctypes.c_double)]
 
 
 class RomError(RuntimeError):
@@ -71,6 +79,7 @@ def lib(path=None):
     L.rom_sync.argtypes = [p]
     L.rom_profile.argtypes = [p, i]
     L.rom_profile_read.argtypes = [p, i, p, p, p]
+    L.rom_step_noalloc.argtypes = [p, i64, p, p, p, p, p, p, p, p, p, p, p, p, ctypes.c_size_t]
     L.rom_last_error.argtypes = [p]
     L.rom_last_error.restype = ctypes.c_char_p
     for f in EXPORTED:
@@ -221,3 +230,28 @@ class State:
             self.close()
         except Exception:
             pass
+
+
+def phase_array(phases):
+    arr = (RomPhase * len(phases))()
+    for k, ph in enumerate(phases):
+        arr[k] = RomPhase(ph["E"], ph["nu"], 1 if ph.get("law", "power") == "power" else 0, ph["s0"], ph["k"],
+                          ph.get("p", 1.0))
+    return arr
+
+
+def step_noalloc(dim, G_d, w_d, phase_d, Gmu_d, phases, omega, mu_d, a_d, da_prev_d, Cpinv_d, xi_d, opts,
+                 Fbar_d, Pbar_d, Abar_d, info_d, stream=None):
+    """rom_step_noalloc: one load step with every array supplied by the caller (torch CUDA
+    tensors) and the work space in the library's static device array."""
+    L = lib()
+    m, d2, n = G_d.shape
+    arr = phase_array(phases)
+    model = RomNoallocModel(dim, n, m, Gmu_d.shape[-1], len(phases), G_d.data_ptr(), w_d.data_ptr(),
+                            phase_d.data_ptr(), Gmu_d.data_ptr(), ctypes.cast(arr, ctypes.c_void_p), float(omega))
+    buf = ctypes.create_string_buffer(512)
+    st = L.rom_step_noalloc(ctypes.byref(model), int(mu_d.shape[0]), _p(mu_d), _p(a_d), _p(da_prev_d), _p(Cpinv_d),
+                            _p(xi_d), ctypes.byref(opts), _p(Fbar_d), _p(Pbar_d), _p(Abar_d), _p(info_d),
+                            ctypes.c_void_p(stream) if stream else None, buf, 512)
+    if st != ROM_OK:
+        raise RomError("rom_step_noalloc failed with status %d: %s" % (st, buf.value.decode()))

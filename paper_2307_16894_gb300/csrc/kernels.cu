@@ -25,6 +25,11 @@ void set_phases(const PhaseD *ph, int n, cudaStream_t s) {
     cudaMemcpyToSymbolAsync(c_phases, ph, sizeof(PhaseD) * n, 0, cudaMemcpyHostToDevice, s);
 }
 
+// copy the whole phase table back to the host (stream-ordered)
+cudaError_t get_phases(PhaseD *ph, cudaStream_t s) {
+    return cudaMemcpyFromSymbolAsync(ph, c_phases, sizeof(PhaseD) * MAX_PHASES, 0, cudaMemcpyDeviceToHost, s);
+}
+
 // ------------------------------------------------------------------------ start
 template <int D>
 __global__ void k_start(Model M, Batch Bt, const double *__restrict__ Fbar, StepOpts o,
