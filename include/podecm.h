@@ -162,12 +162,54 @@ const char *rom_last_error(const rom_ctx *ctx);
  * rom_profile(ctx, 0) stops.  rom_profile_read returns, for kernel group
  * 0 start, 1 constitutive (kinematics, return map, tangent), 2 assembly
  * (force and stiffness), 3 solve (convergence test, line search, LU),
- * 4 finalize (Pbar, Abar, commit), 5 bookkeeping: the summed device time in ms,
+ * 4 finalize (Pbar, Abar, commit), 5 bookkeeping, 6 learned start (features, MLP
+ * inference): the summed device time in ms,
  * the number of kernel launches and the algorithmic FLOPs (kernel groups 1-3:
  * kinematics 2 m d^2 n; assembly 2 m d^4 n + m d^2 n (n+1) + 2 m d^2 n; solve
  * 2 n^3/3 + 2 n^2 -- per active instance and launch).  Any pointer may be NULL. */
 rom_status rom_profile(rom_ctx *ctx, int enable);
 rom_status rom_profile_read(rom_ctx *ctx, int kernel, double *ms, int64_t *launches, double *flops);
+
+/* ---------------------------------------------------------------------------
+ * Learned Newton start (not in the paper, whose Newton start is unspecified).
+ * A multilayer perceptron with `depth` hidden layers of `width` units (exact-erf
+ * GELU) maps the features of a step
+ *     x = [Ubar_k - Ubar_{k-1} (d*d), mu (n_par), a_n (n), mean_i xi_i, max_i xi_i]
+ * (n_in = d*d + n_par + n + 2; Ubar = stretch of the polar split of Fbar) to the
+ * predicted increment da of the reduced coordinates (n_out = n).  Inference uses
+ * BF16 weights with FP32 accumulation; training keeps an FP32 master copy updated by
+ * Adam (beta = 0.9, 0.999, eps = 1e-8) on the mean squared error of the standardised
+ * targets.  With opts->start = ROM_START_MLP, rom_step evaluates the residual at
+ * a_n + da_MLP and at the previous-step predictor a_n + (a_n - a_{n-1}) and starts
+ * Newton from the smaller one (one extra residual evaluation, counted in evals); the
+ * converged answer does not depend on the start.
+ *
+ * rom_mlp_init: allocate an MLP (random parameters are set by rom_mlp_params);
+ *   max_rows = largest batch of rows of any later train/grad/predict call.
+ * rom_mlp_params: get (get_host != NULL) and/or set (set_host) the packed FP32
+ *   parameters: for every linear map l (n_in -> width -> ... -> width -> n_out)
+ *   W_l[out][in] row-major then b_l[out]; rom_mlp_nparams gives their count.
+ *   Setting the parameters resets the Adam moments.
+ * rom_mlp_norm: x_mean[n_in], x_std[n_in], y_mean[n_out], y_std[n_out] (host);
+ *   the network sees (x - x_mean)/x_std and is trained on (y - y_mean)/y_std.
+ * rom_mlp_train_step: one Adam step (learning rate lr, step count t >= 1) on the
+ *   device batch X_d[N][n_in], Y_d[N][n_out] (raw units); the loss before the
+ *   update goes to loss_d[1] (device, may be NULL).  Asynchronous.
+ * rom_mlp_loss_grad: loss and gradient (packed like the parameters) without update;
+ *   bf16 = 0 uses the FP32 weights.  Device outputs.  Asynchronous.
+ * rom_mlp_predict: out_d[N][n_out] (double, raw units) for X_d[N][n_in].  Asynchronous.
+ * rom_features: the features X_d[B][n_in] (device) of the step Fbar_d[B][d*d] for
+ *   the current state of every instance.  Asynchronous. */
+rom_status rom_mlp_init(rom_ctx *ctx, int n_in, int width, int depth, int n_out, int64_t max_rows);
+rom_status rom_mlp_nparams(rom_ctx *ctx, int64_t *nparams);
+rom_status rom_mlp_params(rom_ctx *ctx, float *get_host, const float *set_host);
+rom_status rom_mlp_norm(rom_ctx *ctx, const float *norm_host);
+rom_status rom_mlp_train_step(rom_ctx *ctx, const float *X_d, const float *Y_d, int64_t N, float lr, int t,
+                              float *loss_d);
+rom_status rom_mlp_loss_grad(rom_ctx *ctx, const float *X_d, const float *Y_d, int64_t N, int bf16, float *grad_d,
+                             float *loss_d);
+rom_status rom_mlp_predict(rom_ctx *ctx, const float *X_d, int64_t N, int bf16, double *out_d);
+rom_status rom_features(rom_ctx *ctx, rom_state *st, const double *Fbar_d, float *X_d);
 
 /* ---------------------------------------------------------------------------
  * Allocation-free step.  The paper has no counterpart: this is a deployment

@@ -46,7 +46,7 @@ CONFIGS = {
     # 3D 24^3 hex8, spherical elastic inclusion (stiffness ratio 10), n=64 (96 kept), m=600
     "c3": dict(d=3, N=24, n=96, n_use=64, m=600, L=20, map_seed=11, phases=[MATRIX, INCLUSION],
                train=[("stretch", 3001 + i, 20) for i in range(5)], mu_range=(0.15, 0.35),
-               fft_pcg=True, tol_rel=1e-8, parallel=True),
+               fft_pcg=True, tol_rel=1e-7, parallel=True),
 }
 
 
@@ -100,6 +100,8 @@ def build(name, verbose=True, nthreads=None):
 
 def _train_path(name, kind, seed, nst, nthreads, verbose):
     """One seeded full-order training solve (Algorithm 1 offline lines 2-4)."""
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
     cfg = CONFIGS[name]
     d, N = cfg["d"], cfg["N"]
     mesh = fe.Mesh(d, N, phase_2d if d == 2 else phase_3d)

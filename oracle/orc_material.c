@@ -109,7 +109,16 @@ static dmat m_log_spd(dmat x) {
     dmat z2 = m_mul(z, z), term = z, s = z;
     for (int j = 1; j <= 16; ++j) {
         term = m_mul(term, z2);
-        s = m_add(s, m_scl(term, 1.0 / (2.0 * j + 1.0)));
+        dmat add_ = m_scl(term, 1.0 / (2.0 * j + 1.0));
+        s = m_add(s, add_);
+        /* stop once the added term (value and derivative) is below double rounding of the sum */
+        double tv = 0.0, td = 0.0, sv = 0.0, sd = 0.0;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                tv += fabs(add_.a[a][b].v); td += fabs(add_.a[a][b].d);
+                sv += fabs(s.a[a][b].v); sd += fabs(s.a[a][b].d);
+            }
+        if (tv <= 1e-18 * sv && td <= 1e-18 * (sd + sv)) break;
     }
     return m_scl(s, 2.0 * ldexp(1.0, k));
 }
@@ -125,6 +134,10 @@ static dmat m_exp(dmat x) {
     for (int j = 1; j <= 18; ++j) {
         term = m_scl(m_mul(term, xs), 1.0 / j);
         sum = m_add(sum, term);
+        double tv = 0.0, td = 0.0;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) { tv += fabs(term.a[a][b].v); td += fabs(term.a[a][b].d); }
+        if (tv <= 1e-19 && td <= 1e-19 * (1.0 + tv)) break;
     }
     for (int j = 0; j < s; ++j) sum = m_mul(sum, sum);
     return sum;

@@ -24,9 +24,10 @@ INFO_DTYPE = np.dtype([("iters", "<i4"), ("evals", "<i4"), ("status", "<i4"), ("
 EXPORTED = ["rom_create", "rom_destroy", "rom_load_basis", "rom_load_cubature", "rom_set_geometry",
             "rom_state_create", "rom_state_destroy", "rom_state_export", "rom_state_import", "rom_step",
             "rom_step_device", "rom_sync", "rom_last_error", "rom_profile", "rom_profile_read",
-            "rom_step_noalloc"]
+            "rom_step_noalloc", "rom_mlp_init", "rom_mlp_nparams", "rom_mlp_params", "rom_mlp_norm",
+            "rom_mlp_train_step", "rom_mlp_loss_grad", "rom_mlp_predict", "rom_features"]
 
-KERNEL_GROUPS = ["start", "constitutive", "assemble", "solve", "finalize", "bookkeeping"]
+KERNEL_GROUPS = ["start", "constitutive", "assemble", "solve", "finalize", "bookkeeping", "learned_start"]
 
 
 class RomPhase(ctypes.Structure):
@@ -80,6 +81,14 @@ def lib(path=None):
     L.rom_profile.argtypes = [p, i]
     L.rom_profile_read.argtypes = [p, i, p, p, p]
     L.rom_step_noalloc.argtypes = [p, i64, p, p, p, p, p, p, p, p, p, p, p, p, ctypes.c_size_t]
+    L.rom_mlp_init.argtypes = [p, i, i, i, i, i64]
+    L.rom_mlp_nparams.argtypes = [p, p]
+    L.rom_mlp_params.argtypes = [p, p, p]
+    L.rom_mlp_norm.argtypes = [p, p]
+    L.rom_mlp_train_step.argtypes = [p, p, p, i64, ctypes.c_float, i, p]
+    L.rom_mlp_loss_grad.argtypes = [p, p, p, i64, i, p, p]
+    L.rom_mlp_predict.argtypes = [p, p, i64, i, p]
+    L.rom_features.argtypes = [p, p, p, p]
     L.rom_last_error.argtypes = [p]
     L.rom_last_error.restype = ctypes.c_char_p
     for f in EXPORTED:
@@ -108,7 +117,11 @@ def make_opts(tol_rel=1e-10, tol_abs=0.0, max_iter=25, max_ls=6, precision="fp64
 
 
 class Context:
-    """rom_ctx: one model (basis, cubature, geometry) on one device and stream."""
+    """rom_ctx: one model (basis, cubature, geometry) on one device and stream.
+
+    stream: a cudaStream_t (int) or None (the context creates its own).  A context
+    that receives torch tensors must run on the stream those tensors are used on
+    (torch.cuda.current_stream().cuda_stream)."""
 
     def __init__(self, dim, device=0, stream=None):
         self.L = lib()
@@ -184,6 +197,40 @@ class Context:
 
     def sync(self):
         self._check(self.L.rom_sync(self.h), "rom_sync")
+
+    # ---- learned Newton start
+    def mlp_init(self, n_in, width, depth, n_out, max_rows):
+        self._check(self.L.rom_mlp_init(self.h, n_in, width, depth, n_out, int(max_rows)), "rom_mlp_init")
+        n = ctypes.c_int64()
+        self._check(self.L.rom_mlp_nparams(self.h, ctypes.byref(n)), "rom_mlp_nparams")
+        self.mlp_shape = (n_in, width, depth, n_out)
+        return n.value
+
+    def mlp_params(self, set_params=None):
+        n = ctypes.c_int64()
+        self._check(self.L.rom_mlp_nparams(self.h, ctypes.byref(n)), "rom_mlp_nparams")
+        out = np.empty(n.value, np.float32)
+        sp = None if set_params is None else np.ascontiguousarray(set_params, np.float32)
+        self._check(self.L.rom_mlp_params(self.h, _p(out), _p(sp)), "rom_mlp_params")
+        return out
+
+    def mlp_norm(self, x_mean, x_std, y_mean, y_std):
+        v = np.ascontiguousarray(np.concatenate([x_mean, x_std, y_mean, y_std]), np.float32)
+        self._check(self.L.rom_mlp_norm(self.h, _p(v)), "rom_mlp_norm")
+
+    def mlp_train_step(self, X_d, Y_d, lr, t, loss_d=None):
+        self._check(self.L.rom_mlp_train_step(self.h, _p(X_d), _p(Y_d), X_d.shape[0], float(lr), int(t), _p(loss_d)),
+                    "rom_mlp_train_step")
+
+    def mlp_loss_grad(self, X_d, Y_d, bf16, grad_d, loss_d):
+        self._check(self.L.rom_mlp_loss_grad(self.h, _p(X_d), _p(Y_d), X_d.shape[0], int(bf16), _p(grad_d),
+                                             _p(loss_d)), "rom_mlp_loss_grad")
+
+    def mlp_predict(self, X_d, bf16, out_d):
+        self._check(self.L.rom_mlp_predict(self.h, _p(X_d), X_d.shape[0], int(bf16), _p(out_d)), "rom_mlp_predict")
+
+    def features(self, state, Fbar_d, X_d):
+        self._check(self.L.rom_features(self.h, state.h, _p(Fbar_d), _p(X_d)), "rom_features")
 
     def profile(self, enable):
         self._check(self.L.rom_profile(self.h, int(enable)), "rom_profile")

@@ -93,7 +93,9 @@ __global__ void k_start(Model M, Batch Bt, const double *__restrict__ Fbar, Step
     }
     Ctl c;
     c.r0 = 0.0; c.tol = 0.0; c.rn_acc = 0.0; c.t = 1.0;
-    c.iters = 0; c.evals = 0; c.ls = 0; c.status = 0; c.active = 1; c.phase = 0; c.pad0 = c.pad1 = 0;
+    c.iters = 0; c.evals = 0; c.ls = 0; c.status = 0; c.active = 1; c.pad0 = c.pad1 = 0;
+    // learned start: evaluate the predicted point first, then the previous-step point (phase 2 -> 3)
+    c.phase = (o.start == 2) ? 2 : 0;
     Bt.ctl[b] = c;
     Bt.list[b] = (int32_t)b;
 }
@@ -440,12 +442,60 @@ __global__ void __launch_bounds__(32) k_solve(Model M, Batch Bt, StepOpts o, int
     Ctl c = Bt.ctl[b];
     double *qt = Bt.q_trial + b * n, *qa = Bt.q_acc + b * n, *dq = Bt.dq + b * n;
     bool accepted = false;
-    if (c.phase == 0) {
+    bool keep_dq = false;   // Newton direction already known (learned start chosen)
+    if (c.phase == 0 || c.phase == 4) {
+        if (c.phase == 4) c.evals += 1;
         c.r0 = rn;
         c.tol = fmax(o.tol_rel * rn, o.tol_abs);
         c.rn_acc = rn;
         c.phase = 1;
+        for (int j = lane; j < n; j += 32) qa[j] = qt[j];
         accepted = true;
+    } else if (c.phase == 2) {
+        // learned start evaluated: keep its residual norm and Newton direction, then
+        // evaluate the previous-step predictor a_n + (a_n - a_{n-1})
+        c.r0 = rn;
+        const double *Kb = Bt.K + (size_t)b * n * n;
+        for (int e = lane; e < n * n; e += 32) A[e] = Kb[e];
+        for (int j = lane; j < n; j += 32) x[j] = -r[j];
+        __syncwarp();
+        const bool ok = isfinite(rn) && warp_lu(A, n, piv);
+        if (ok) warp_lu_solve(A, n, piv, x);
+        if (!ok && lane == 0) c.r0 = NAN;
+        for (int j = lane; j < n; j += 32) {
+            dq[j] = ok ? x[j] : 0.0;
+            qa[j] = qt[j];
+            qt[j] = Bt.q_n[b * n + j] + Bt.dq_prev[b * n + j];
+        }
+        c.r0 = __shfl_sync(0xffffffffu, c.r0, 0);
+        c.phase = 3;
+    } else if (c.phase == 3) {
+        c.evals += 1;
+        const double rm = c.r0;
+        if (!(rm <= rn)) {
+            // previous-step predictor wins (or the learned start failed)
+            c.r0 = rn;
+            c.tol = fmax(o.tol_rel * rn, o.tol_abs);
+            c.rn_acc = rn;
+            c.phase = 1;
+            for (int j = lane; j < n; j += 32) qa[j] = qt[j];
+            accepted = true;
+        } else {
+            c.r0 = rm;
+            c.tol = fmax(o.tol_rel * rm, o.tol_abs);
+            c.rn_acc = rm;
+            if (rm <= c.tol || o.max_iter == 0) {
+                // the stored per-point data belong to the other candidate: re-evaluate here
+                for (int j = lane; j < n; j += 32) qt[j] = qa[j];
+                c.phase = 4;
+            } else {
+                c.t = 1.0;
+                c.ls = 0;
+                c.phase = 1;
+                for (int j = lane; j < n; j += 32) qt[j] = qa[j] + dq[j];
+                keep_dq = true;
+            }
+        }
     } else {
         c.evals += 1;
         if (c.ls >= o.max_ls || (isfinite(rn) && rn < c.rn_acc)) {
@@ -460,7 +510,7 @@ __global__ void __launch_bounds__(32) k_solve(Model M, Batch Bt, StepOpts o, int
             for (int j = lane; j < n; j += 32) qt[j] = qa[j] + c.t * dq[j];
         }
     }
-    if (accepted) {
+    if (accepted && !keep_dq) {
         if (!isfinite(c.rn_acc)) { c.status = 6; c.active = 0; }
         else if (c.rn_acc <= c.tol) { c.status = 0; c.active = 0; }
         else if (c.iters >= o.max_iter) { c.status = 5; c.active = 0; }
@@ -694,6 +744,21 @@ __global__ void __launch_bounds__(256) k_finalize(Model M, Batch Bt, StepOpts o,
         Bt.dq_prev[b * n + j] = qa - Bt.q_n[b * n + j];
         Bt.q_n[b * n + j] = qa;
     }
+    if (Bt.U_prev && tid < D2) Bt.U_prev[b * D2 + tid] = Ub[tid];
+}
+
+// learned start: q_trial = q_acc = q_n + prediction
+__global__ void k_add_pred(Batch Bt, int n, const double *__restrict__ pred) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= Bt.B * n) return;
+    const double q = Bt.q_n[e] + pred[e];
+    Bt.q_trial[e] = q;
+    Bt.q_acc[e] = q;
+}
+
+void launch_add_pred(Batch Bt, int n, const double *pred, cudaStream_t s) {
+    const int64_t tot = Bt.B * n;
+    k_add_pred<<<(int)((tot + 255) / 256), 256, 0, s>>>(Bt, n, pred);
 }
 
 // ----------------------------------------------------------------- host launchers

@@ -48,6 +48,20 @@ struct Batch {
     double *r;               // [B][n]
     double *K;               // [B][n][n]
     double *Ubar, *Rbar;     // [B][d2]
+    double *U_prev;          // [B][d2] stretch of the last converged step (learned start features), may be null
+};
+
+// learned Newton start (mlp.cu)
+struct MlpDev {
+    int n_in, width, depth, n_out, L;
+    int64_t nparams;
+    float *p32, *m, *v, *grad;
+    void *p16;                      // __nv_bfloat16 copy of p32
+    float *norm;                    // x_mean[n_in] x_std[n_in] y_mean[n_out] y_std[n_out]
+    float *Z, *H, *dH;              // work arrays
+    float *loss;
+    int64_t cap;
+    int wmax;
 };
 
 struct StepOpts {

@@ -40,8 +40,9 @@ struct PhaseD {
 __device__ __forceinline__ double yield_stress(const PhaseD &ph, double xi, double *slope) {
     if (ph.elastic) { *slope = 0.0; return INFINITY; }
     if (ph.law == 0) { *slope = ph.k; return ph.s0 + ph.k * xi; }
+    // (1 + k xi)^p as exp(p ln(1 + k xi)): two transcendental calls instead of pow()
     const double base = 1.0 + ph.k * xi;
-    const double v = ph.s0 * pow(base, ph.p);
+    const double v = ph.s0 * exp(ph.p * log(base));
     *slope = v * ph.p * ph.k / base;
     return v;
 }
@@ -295,8 +296,14 @@ __device__ __forceinline__ void tangent_setup(const MatState &S, const PhaseD &p
             td.c[a][b] = T(ph.Kb + 2.0 * G * S.beta * ((a == b ? 1.0 : 0.0) - 1.0 / 3.0) - cpl * S.nh[a] * S.nh[b]);
     const double gb = G * S.beta;
     td.th[0] = T(gb * log_divided_difference<double>(S.lam[0], S.lam[1]));
-    td.th[1] = T(gb * log_divided_difference<double>(S.lam[0], S.lam[2]));
-    td.th[2] = T(gb * log_divided_difference<double>(S.lam[1], S.lam[2]));
+    if (D == 3) {
+        td.th[1] = T(gb * log_divided_difference<double>(S.lam[0], S.lam[2]));
+        td.th[2] = T(gb * log_divided_difference<double>(S.lam[1], S.lam[2]));
+    } else {
+        // plane strain: db'_a2 = 0 for in-plane directions, so the out-of-plane pairs never enter
+        td.th[1] = T(0);
+        td.th[2] = T(0);
+    }
 #pragma unroll
     for (int a = 0; a < 3; ++a) td.inv2l[a] = T(0.5 / S.lam[a]);
     const double C[3][3] = {{cp[0], cp[1], cp[2]}, {cp[1], cp[3], cp[4]}, {cp[2], cp[4], cp[5]}};

@@ -20,11 +20,23 @@ int launch_start(const Model &M, Batch Bt, const double *Fbar, const StepOpts &o
 int launch_kernel(int which, const Model &M, Batch Bt, const StepOpts &o, int32_t *list_next, cudaStream_t s);
 int launch_finalize(const Model &M, Batch Bt, const StepOpts &o, double *Pbar, double *Abar, void *info,
                     cudaStream_t s);
+void launch_add_pred(Batch Bt, int n, const double *pred, cudaStream_t s);
+void launch_features(const Model &M, Batch Bt, const double *U_prev, float *X, int n_in, cudaStream_t s);
+int mlp_alloc(MlpDev &M, int n_in, int width, int depth, int n_out, int64_t cap);
+void mlp_free(MlpDev &M);
+void mlp_set_params(MlpDev &M, const float *host, cudaStream_t s);
+void mlp_get_params(const MlpDev &M, float *host, cudaStream_t s);
+void mlp_set_norm(MlpDev &M, const float *host, cudaStream_t s);
+void mlp_train_step(MlpDev &M, const float *X, const float *Y, int64_t N, float lr, int t, float *loss_out,
+                    cudaStream_t s);
+void mlp_loss_grad(MlpDev &M, const float *X, const float *Y, int64_t N, int bf16, float *grad_out, float *loss_out,
+                   cudaStream_t s);
+void mlp_predict(MlpDev &M, const float *X, int64_t N, int bf16, double *out, cudaStream_t s);
 }  // namespace podecm
 
 using namespace podecm;
 
-#define ROM_NKERNELS 6
+#define ROM_NKERNELS 7
 
 struct rom_ctx {
     int dim = 0, device = 0;
@@ -53,6 +65,12 @@ struct rom_ctx {
     double prof_ms[ROM_NKERNELS] = {0};
     int64_t prof_launches[ROM_NKERNELS] = {0};
     double prof_flops[ROM_NKERNELS] = {0};
+    // learned Newton start
+    bool has_mlp = false, mlp_norm = false;
+    MlpDev mlp{};
+    float *d_feat = nullptr;        // [B][n_in]
+    double *d_pred = nullptr;       // [B][n]
+    int64_t feat_B = 0;
 };
 
 struct rom_state {
@@ -147,6 +165,9 @@ rom_status rom_destroy(rom_ctx *ctx) {
     free_io(ctx);
     if (ctx->h_count) cudaFreeHost(ctx->h_count);
     for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+    if (ctx->has_mlp) mlp_free(ctx->mlp);
+    p = ctx->d_feat; dfree(p);
+    p = ctx->d_pred; dfree(p);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return ROM_OK;
@@ -302,7 +323,7 @@ rom_status rom_state_create(rom_ctx *ctx, int64_t B, rom_state **out) {
         (s = A((void **)&bt.cp_tr, Bz * ncp * m * 8)) || (s = A((void **)&bt.xi_tr, Bz * m * 8)) ||
         (s = A((void **)&bt.pl, Bz * m)) || (s = A((void **)&bt.r, Bz * n * 8)) ||
         (s = A((void **)&bt.K, Bz * n * n * 8)) || (s = A((void **)&bt.Ubar, Bz * d2 * 8)) ||
-        (s = A((void **)&bt.Rbar, Bz * d2 * 8))) {
+        (s = A((void **)&bt.Rbar, Bz * d2 * 8)) || (s = A((void **)&bt.U_prev, Bz * d2 * 8))) {
         rom_state_destroy(st);
         return s;
     }
@@ -314,8 +335,12 @@ rom_status rom_state_create(rom_ctx *ctx, int64_t B, rom_state **out) {
             const double v = ctx->dim == 2 ? diag2[c] : diag3[c];
             for (int i = 0; i < m; ++i) cp[(b * ncp + c) * m + i] = v;
         }
+    std::vector<double> eye(Bz * d2, 0.0);
+    for (size_t b = 0; b < Bz; ++b)
+        for (int a = 0; a < ctx->dim; ++a) eye[b * d2 + a * ctx->dim + a] = 1.0;
     cudaError_t e;
-    if ((e = cudaMemset(bt.q_n, 0, Bz * n * 8)) != cudaSuccess || (e = cudaMemset(bt.dq_prev, 0, Bz * n * 8)) != cudaSuccess ||
+    if ((e = cudaMemcpy(bt.U_prev, eye.data(), eye.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(bt.q_n, 0, Bz * n * 8)) != cudaSuccess || (e = cudaMemset(bt.dq_prev, 0, Bz * n * 8)) != cudaSuccess ||
         (e = cudaMemset(bt.xi, 0, Bz * m * 8)) != cudaSuccess ||
         (e = cudaMemcpy(bt.cp, cp.data(), cp.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess) {
         rom_state_destroy(st);
@@ -381,7 +406,10 @@ static rom_status check_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts) 
         opts->max_ls < 0 || opts->max_ls > 60 || opts->precision < 0 || opts->precision > 3 || opts->start < 0 ||
         opts->start > 2)
         return fail(ctx, ROM_E_ARG, "rom_step: bad options");
-    if (opts->start == ROM_START_MLP) return fail(ctx, ROM_E_STATE, "rom_step: no MLP loaded");
+    if (opts->start == ROM_START_MLP && (!ctx->has_mlp || !ctx->mlp_norm))
+        return fail(ctx, ROM_E_STATE, "rom_step: learned start requested but no MLP (rom_mlp_init, rom_mlp_params, rom_mlp_norm)");
+    if (opts->start == ROM_START_MLP && ctx->mlp.n_in != ctx->dim * ctx->dim + ctx->n_par + ctx->n + 2)
+        return fail(ctx, ROM_E_STATE, "rom_step: MLP input size %d does not match d^2 + n_par + n + 2", ctx->mlp.n_in);
     if (opts->precision >= ROM_PREC_TF32) return fail(ctx, ROM_E_ARG, "rom_step: precision mode not available");
     return ROM_OK;
 }
@@ -396,6 +424,18 @@ static Model make_model(const rom_ctx *ctx) {
 }
 
 }  // extern "C"
+
+static rom_status ensure_feat(rom_ctx *ctx, int64_t B) {
+    if (ctx->feat_B >= B) return ROM_OK;
+    void *p;
+    p = ctx->d_feat; dfree(p); ctx->d_feat = nullptr;
+    p = ctx->d_pred; dfree(p); ctx->d_pred = nullptr;
+    rom_status s;
+    if ((s = dalloc(ctx, (void **)&ctx->d_feat, (size_t)B * ctx->mlp.n_in * 4)) != ROM_OK) return s;
+    if ((s = dalloc(ctx, (void **)&ctx->d_pred, (size_t)B * ctx->mlp.n_out * 8)) != ROM_OK) return s;
+    ctx->feat_B = B;
+    return ROM_OK;
+}
 
 static int prof_event(rom_ctx *ctx, int idx) {
     while ((int)ctx->ev_pool.size() <= idx) {
@@ -428,7 +468,7 @@ static void prof_collect(rom_ctx *ctx) {
         float ms = 0.f;
         if (r.ev1 >= 0 && cudaEventElapsedTime(&ms, ctx->ev_pool[r.ev0], ctx->ev_pool[r.ev1]) == cudaSuccess) {
             ctx->prof_ms[r.kid] += ms;
-            ctx->prof_launches[r.kid] += (r.kid == 0 || r.kid == 5) ? 2 : 1;
+            ctx->prof_launches[r.kid] += (r.kid == 0 || r.kid == 5) ? 2 : (r.kid == 6 ? 3 + 2 * ctx->mlp.L : 1);
             ctx->prof_flops[r.kid] += r.flops;
         }
     }
@@ -452,6 +492,16 @@ static rom_status run_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts, co
     const double fl_lu = 2 * n * n * n / 3 + 2 * n * n;
     if (timed(ctx, 0, 0.0, [&] { return launch_start(M, bt, Fbar_d, o, nullptr, ctx->stream); }))
         return fail(ctx, ROM_E_ARG, "launch_start");
+    if (o.start == ROM_START_MLP) {
+        rom_status s2 = ensure_feat(ctx, st->B);
+        if (s2 != ROM_OK) return s2;
+        timed(ctx, 6, 0.0, [&] {
+            launch_features(M, bt, bt.U_prev, ctx->d_feat, ctx->mlp.n_in, ctx->stream);
+            mlp_predict(ctx->mlp, ctx->d_feat, st->B, 1, ctx->d_pred, ctx->stream);
+            launch_add_pred(bt, M.n, ctx->d_pred, ctx->stream);
+            return 0;
+        });
+    }
     const int max_pass = (opts->max_iter + 1) * (opts->max_ls + 1) + 2;
     int64_t n_act = st->B;
     for (int pass = 0; pass < max_pass; ++pass) {
@@ -522,6 +572,104 @@ rom_status rom_sync(rom_ctx *ctx) {
 }
 
 const char *rom_last_error(const rom_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+rom_status rom_mlp_init(rom_ctx *ctx, int n_in, int width, int depth, int n_out, int64_t max_rows) {
+    if (!ctx) return ROM_E_ARG;
+    if (n_in < 1 || n_in > 4096 || width < 1 || width > 4096 || depth < 1 || depth > 16 || n_out < 1 ||
+        n_out > 4096 || max_rows < 1)
+        return fail(ctx, ROM_E_ARG, "rom_mlp_init: bad shape");
+    CK(cudaSetDevice(ctx->device));
+    if (ctx->has_mlp) mlp_free(ctx->mlp);
+    ctx->has_mlp = false;
+    ctx->mlp_norm = false;
+    if (mlp_alloc(ctx->mlp, n_in, width, depth, n_out, max_rows)) {
+        mlp_free(ctx->mlp);
+        return fail(ctx, ROM_E_NOMEM, "rom_mlp_init: allocation failed");
+    }
+    ctx->has_mlp = true;
+    return ROM_OK;
+}
+
+rom_status rom_mlp_nparams(rom_ctx *ctx, int64_t *n) {
+    if (!ctx || !n) return ROM_E_ARG;
+    if (!ctx->has_mlp) return fail(ctx, ROM_E_STATE, "rom_mlp_nparams: no MLP");
+    *n = ctx->mlp.nparams;
+    return ROM_OK;
+}
+
+rom_status rom_mlp_params(rom_ctx *ctx, float *get_host, const float *set_host) {
+    if (!ctx) return ROM_E_ARG;
+    if (!ctx->has_mlp) return fail(ctx, ROM_E_STATE, "rom_mlp_params: no MLP");
+    CK(cudaSetDevice(ctx->device));
+    if (set_host) mlp_set_params(ctx->mlp, set_host, ctx->stream);
+    if (get_host) mlp_get_params(ctx->mlp, get_host, ctx->stream);
+    CK(cudaStreamSynchronize(ctx->stream));
+    return ROM_OK;
+}
+
+rom_status rom_mlp_norm(rom_ctx *ctx, const float *norm_host) {
+    if (!ctx || !norm_host) return ROM_E_ARG;
+    if (!ctx->has_mlp) return fail(ctx, ROM_E_STATE, "rom_mlp_norm: no MLP");
+    const int nn = 2 * ctx->mlp.n_in + 2 * ctx->mlp.n_out;
+    for (int k = 0; k < nn; ++k)
+        if (!std::isfinite(norm_host[k])) return fail(ctx, ROM_E_ARG, "rom_mlp_norm: non-finite entry");
+    for (int k = 0; k < ctx->mlp.n_in; ++k)
+        if (!(norm_host[ctx->mlp.n_in + k] > 0)) return fail(ctx, ROM_E_ARG, "rom_mlp_norm: x_std must be > 0");
+    for (int k = 0; k < ctx->mlp.n_out; ++k)
+        if (!(norm_host[2 * ctx->mlp.n_in + ctx->mlp.n_out + k] > 0)) return fail(ctx, ROM_E_ARG, "rom_mlp_norm: y_std must be > 0");
+    CK(cudaSetDevice(ctx->device));
+    mlp_set_norm(ctx->mlp, norm_host, ctx->stream);
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->mlp_norm = true;
+    return ROM_OK;
+}
+
+rom_status rom_mlp_train_step(rom_ctx *ctx, const float *X_d, const float *Y_d, int64_t N, float lr, int t,
+                              float *loss_d) {
+    if (!ctx || !X_d || !Y_d) return ROM_E_ARG;
+    if (!ctx->has_mlp || !ctx->mlp_norm) return fail(ctx, ROM_E_STATE, "rom_mlp_train_step: MLP or normalisation missing");
+    if (N < 1 || N > ctx->mlp.cap || t < 1 || !(lr > 0)) return fail(ctx, ROM_E_ARG, "rom_mlp_train_step: bad N, t or lr");
+    CK(cudaSetDevice(ctx->device));
+    mlp_train_step(ctx->mlp, X_d, Y_d, N, lr, t, loss_d, ctx->stream);
+    CK(cudaGetLastError());
+    return ROM_OK;
+}
+
+rom_status rom_mlp_loss_grad(rom_ctx *ctx, const float *X_d, const float *Y_d, int64_t N, int bf16, float *grad_d,
+                             float *loss_d) {
+    if (!ctx || !X_d || !Y_d || !grad_d || !loss_d) return ROM_E_ARG;
+    if (!ctx->has_mlp || !ctx->mlp_norm) return fail(ctx, ROM_E_STATE, "rom_mlp_loss_grad: MLP or normalisation missing");
+    if (N < 1 || N > ctx->mlp.cap) return fail(ctx, ROM_E_ARG, "rom_mlp_loss_grad: bad N");
+    CK(cudaSetDevice(ctx->device));
+    mlp_loss_grad(ctx->mlp, X_d, Y_d, N, bf16, grad_d, loss_d, ctx->stream);
+    CK(cudaGetLastError());
+    return ROM_OK;
+}
+
+rom_status rom_mlp_predict(rom_ctx *ctx, const float *X_d, int64_t N, int bf16, double *out_d) {
+    if (!ctx || !X_d || !out_d || N < 1) return ROM_E_ARG;
+    if (!ctx->has_mlp || !ctx->mlp_norm) return fail(ctx, ROM_E_STATE, "rom_mlp_predict: MLP or normalisation missing");
+    CK(cudaSetDevice(ctx->device));
+    mlp_predict(ctx->mlp, X_d, N, bf16, out_d, ctx->stream);
+    CK(cudaGetLastError());
+    return ROM_OK;
+}
+
+rom_status rom_features(rom_ctx *ctx, rom_state *st, const double *Fbar_d, float *X_d) {
+    if (!ctx || !st || !Fbar_d || !X_d || st->ctx != ctx) return ROM_E_ARG;
+    if (!ctx->has_basis || !ctx->has_cub || !ctx->has_geom || st->B != ctx->B)
+        return fail(ctx, ROM_E_STATE, "rom_features before basis/cubature/geometry");
+    CK(cudaSetDevice(ctx->device));
+    StepOpts o{};
+    o.polar = 1;
+    const Model M = make_model(ctx);
+    Batch bt = st->bt;
+    bt.mu = ctx->mu;
+    launch_start(M, bt, Fbar_d, o, nullptr, ctx->stream);
+    launch_features(M, bt, bt.U_prev, X_d, ctx->dim * ctx->dim + ctx->n_par + ctx->n + 2, ctx->stream);
+    CK(cudaGetLastError());
+    return ROM_OK;
+}
 
 rom_status rom_profile(rom_ctx *ctx, int enable) {
     if (!ctx) return ROM_E_ARG;

@@ -128,7 +128,7 @@ extern "C" rom_status rom_step_noalloc(const rom_noalloc_model *model, int64_t B
     M.d = d; M.d2 = d2; M.n = n; M.m = m; M.n_par = np; M.nphase = model->n_phase; M.ncp = ncp;
     M.G_pt = model->G; M.G_T = reinterpret_cast<double *>(S + o_GT); M.G32_pt = reinterpret_cast<float *>(S + o_G32);
     M.w = model->w; M.phase = model->phase; M.Gmu_T = reinterpret_cast<double *>(S + o_GmuT); M.omega = model->omega_vol;
-    Batch bt;
+    Batch bt{};
     bt.B = B; bt.mu = mu_d; bt.q_n = a_d; bt.dq_prev = da_prev_d; bt.cp = Cpinv_d; bt.xi = xi_d;
     bt.q_trial = reinterpret_cast<double *>(S + o_qt); bt.q_acc = reinterpret_cast<double *>(S + o_qa);
     bt.dq = reinterpret_cast<double *>(S + o_dq); bt.ctl = reinterpret_cast<Ctl *>(S + o_ctl);

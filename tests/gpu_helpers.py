@@ -21,11 +21,18 @@ def cpinv_from_fp(Fp, d):
     return np.stack([C[..., 0, 0], C[..., 0, 1], C[..., 0, 2], C[..., 1, 1], C[..., 1, 2], C[..., 2, 2]], -1)
 
 
+def torch_stream():
+    """cudaStream_t of torch's current stream: contexts that exchange torch tensors with
+    the library must run on it so that tensor lifetimes and kernels stay stream-ordered."""
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
 class GpuRun:
-    def __init__(self, rom, coef, device=0):
+    def __init__(self, rom, coef, device=0, stream=None):
         self.rom = rom
         d = rom["d"]
-        self.ctx = binding.Context(d, device)
+        self.ctx = binding.Context(d, device, stream)
         self.ctx.load_basis(rom["G"])
         self.ctx.load_cubature(rom["w"], rom["phase"], rom["phases"], rom["omega"])
         self.ctx.set_geometry(rom["Gmu"], coef)
