@@ -79,8 +79,10 @@ typedef struct {
  *             ROM_PREC_FP32/TF32/BF16 -- residual, kinematics, return map,
  *             eigen log/exp and the n x n solve in FP64; the tangent and the
  *             stiffness contraction K in FP32 CUDA cores / TF32 / BF16 tensor
- *             cores with FP32 accumulation (an inexact-Newton Jacobian; the
- *             converged answer still satisfies the FP64 residual test);
+ *             cores (tcgen05, FP32 accumulation in tensor memory; n <= 64) -- an
+ *             inexact-Newton Jacobian; the converged answer still satisfies the
+ *             FP64 residual test.  With TF32/BF16 the K used for Abar is one extra
+ *             FP32 assembly at the converged iterate;
  *  start: ROM_START_PLAIN a0 = a_n; ROM_START_PREV a0 = a_n + (a_n - a_{n-1});
  *         ROM_START_MLP a0 = a_n + MLP prediction (see rom_mlp_load);
  *  polar_split: 1 = solve on Ubar of Fbar = Rbar Ubar and rotate back (Sec. 4);
@@ -106,7 +108,8 @@ typedef struct {
 
 /* Create a context for dimension dim (2 or 3) on CUDA device `device`, issuing
  * all work on `cuda_stream` (a cudaStream_t; NULL = a new stream owned by the
- * context).  *ctx is set to NULL on failure. */
+ * context; pass cudaStreamLegacy for the legacy default stream).  *ctx is set
+ * to NULL on failure. */
 rom_status rom_create(rom_ctx **ctx, int dim, int device, void *cuda_stream);
 rom_status rom_destroy(rom_ctx *ctx);
 
@@ -168,6 +171,11 @@ const char *rom_last_error(const rom_ctx *ctx);
  * kinematics 2 m d^2 n; assembly 2 m d^4 n + m d^2 n (n+1) + 2 m d^2 n; solve
  * 2 n^3/3 + 2 n^2 -- per active instance and launch).  Any pointer may be NULL. */
 rom_status rom_profile(rom_ctx *ctx, int enable);
+
+/* Diagnostics: the reduced stiffness K[B][n][n] of the last evaluated iterate of every
+ * instance (as assembled by the selected precision mode; for ROM_PREC_TF32/BF16 and
+ * converged instances with want_abar, the FP32 re-assembly used for Abar).  Blocking. */
+rom_status rom_debug_stiffness(rom_ctx *ctx, const rom_state *st, double *K);
 rom_status rom_profile_read(rom_ctx *ctx, int kernel, double *ms, int64_t *launches, double *flops);
 
 /* ---------------------------------------------------------------------------

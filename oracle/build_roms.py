@@ -140,6 +140,33 @@ def pack(mesh, cfg, modes, Gq, gradPhi, sel, wsel, err, n_use):
                 ph_p=np.array([p["p"] for p in phases]), map_seed=cfg["map_seed"], N=cfg["N"])
 
 
+# ragged serving family: basis truncations of the 2D and 3D models with their own ECM rules
+VARIANTS = {
+    "r2_n16_m100": ("c2", 16, 100), "r2_n24_m150": ("c2", 24, 150), "r2_n32_m200": ("c2", 32, 200),
+    "r3_n48_m400": ("c3", 48, 400), "r3_n64_m650": ("c3", 64, 650), "r3_n96_m900": ("c3", 96, 900),
+}
+
+
+def build_variant(name, verbose=True):
+    """Truncate the base model's POD basis to n modes and run the ECM greedy for m points
+    (Sec. 3.2; Q grows with N*L, remark of Sec. 4.1)."""
+    base, n, m = VARIANTS[name]
+    cfg = CONFIGS[base]
+    z = np.load(os.path.join(ROOT, "oracle", "_build", "offline_%s.npz" % base))
+    gradPhi, Bm, wq = z["gradPhi"], z["Bm"], z["wq"]
+    d = cfg["d"]
+    mesh = fe.Mesh(d, cfg["N"], phase_2d if d == 2 else phase_3d)
+    t1 = time.time()
+    Fint = reduction.ecm_integrands(gradPhi[..., :n], Bm)
+    sel, wsel, err = reduction.ecm_greedy(Fint, wq, m)
+    if verbose:
+        print("[%s] ECM m=%d err=%.3e (%.1fs)" % (name, m, err, time.time() - t1), flush=True)
+    modes = inputs.map_modes(d, 1 if d == 2 else 3, cfg["map_seed"])
+    rom = pack(mesh, cfg, modes, z["Gq"], gradPhi, sel, wsel, err, n)
+    np.savez_compressed(os.path.join(DATA, "rom_%s.npz" % name), **rom)
+    return rom
+
+
 def load(path):
     """npz -> dict used by the oracle and by the CUDA binding"""
     z = np.load(path)
@@ -156,4 +183,7 @@ def load(path):
 
 if __name__ == "__main__":
     for nm in sys.argv[1:]:
-        build(nm)
+        if nm in VARIANTS:
+            build_variant(nm)
+        else:
+            build(nm)

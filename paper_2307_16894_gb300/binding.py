@@ -25,7 +25,7 @@ EXPORTED = ["rom_create", "rom_destroy", "rom_load_basis", "rom_load_cubature", 
             "rom_state_create", "rom_state_destroy", "rom_state_export", "rom_state_import", "rom_step",
             "rom_step_device", "rom_sync", "rom_last_error", "rom_profile", "rom_profile_read",
             "rom_step_noalloc", "rom_mlp_init", "rom_mlp_nparams", "rom_mlp_params", "rom_mlp_norm",
-            "rom_mlp_train_step", "rom_mlp_loss_grad", "rom_mlp_predict", "rom_features"]
+            "rom_mlp_train_step", "rom_mlp_loss_grad", "rom_mlp_predict", "rom_features", "rom_debug_stiffness"]
 
 KERNEL_GROUPS = ["start", "constitutive", "assemble", "solve", "finalize", "bookkeeping", "learned_start"]
 
@@ -89,6 +89,7 @@ def lib(path=None):
     L.rom_mlp_loss_grad.argtypes = [p, p, p, i64, i, p, p]
     L.rom_mlp_predict.argtypes = [p, p, i64, i, p]
     L.rom_features.argtypes = [p, p, p, p]
+    L.rom_debug_stiffness.argtypes = [p, p, p]
     L.rom_last_error.argtypes = [p]
     L.rom_last_error.restype = ctypes.c_char_p
     for f in EXPORTED:
@@ -119,15 +120,21 @@ def make_opts(tol_rel=1e-10, tol_abs=0.0, max_iter=25, max_ls=6, precision="fp64
 class Context:
     """rom_ctx: one model (basis, cubature, geometry) on one device and stream.
 
-    stream: a cudaStream_t (int) or None (the context creates its own).  A context
-    that receives torch tensors must run on the stream those tensors are used on
+    stream: a cudaStream_t (int) or None (the context creates its own); 0 (torch's
+    default stream) is passed as cudaStreamLegacy.  A context that receives torch
+    tensors must run on the stream those tensors are used on
     (torch.cuda.current_stream().cuda_stream)."""
 
     def __init__(self, dim, device=0, stream=None):
         self.L = lib()
         self.dim = dim
         h = ctypes.c_void_p()
-        st = ctypes.c_void_p(stream) if stream else None
+        if stream is None:
+            st = None                       # the library creates its own stream
+        elif int(stream) == 0:
+            st = ctypes.c_void_p(1)         # handle 0 = legacy default stream -> cudaStreamLegacy
+        else:
+            st = ctypes.c_void_p(int(stream))
         self._check(self.L.rom_create(ctypes.byref(h), int(dim), int(device), st), "rom_create", ctx=None)
         self.h = h
         self.n = self.m = self.n_par = 0
@@ -251,6 +258,13 @@ class State:
 
     def __init__(self, ctx, h, B):
         self.ctx, self.h, self.B = ctx, h, B
+
+    def stiffness(self):
+        """K [B, n, n] of the last evaluated iterate (diagnostics)."""
+        c = self.ctx
+        K = np.empty((self.B, c.n, c.n))
+        c._check(c.L.rom_debug_stiffness(c.h, self.h, _p(K)), "rom_debug_stiffness")
+        return K
 
     def export(self):
         c = self.ctx

@@ -747,6 +747,21 @@ __global__ void __launch_bounds__(256) k_finalize(Model M, Batch Bt, StepOpts o,
     if (Bt.U_prev && tid < D2) Bt.U_prev[b * D2 + tid] = Ub[tid];
 }
 
+// compacted list of the converged instances (status OK) into list / counts[0]
+__global__ void k_list_converged(Batch Bt) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= Bt.B) return;
+    if (Bt.ctl[b].status == 0) {
+        const int pos = atomicAdd(&Bt.counts[0], 1);
+        Bt.list[pos] = (int32_t)b;
+    }
+}
+
+void launch_list_converged(Batch Bt, cudaStream_t s) {
+    cudaMemsetAsync(Bt.counts, 0, 8, s);
+    k_list_converged<<<(int)((Bt.B + 255) / 256), 256, 0, s>>>(Bt);
+}
+
 // learned start: q_trial = q_acc = q_n + prediction
 __global__ void k_add_pred(Batch Bt, int n, const double *__restrict__ pred) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -762,6 +777,34 @@ void launch_add_pred(Batch Bt, int n, const double *pred, cudaStream_t s) {
 }
 
 // ----------------------------------------------------------------- host launchers
+template <int D, int TM>
+static int launch_assemble(const Model &M, Batch Bt, const StepOpts &o, cudaStream_t s) {
+    constexpr int D2 = D * D, D4 = D2 * D2;
+    const int NT = (M.n + TM - 1) / TM, np = NT * TM;
+    const int nup = NT * (NT + 1) / 2;
+    int NG = nup >= 256 ? 1 : 256 / nup;
+    const int nthreads = ((NG * nup + 31) / 32) * 32;
+    if (nthreads > 256 || nthreads < M.n) return -1;
+    const int tksz = o.precision == 0 ? 8 : 4;
+    auto smem_for = [&](int CH) {
+        size_t bytes = (size_t)CH * D2 * np * 8 + (size_t)CH * D2 * np * tksz + (size_t)CH * D4 * tksz + 16 +
+                       (size_t)CH * D2 * 8 + (o.precision == 0 ? 0 : (size_t)CH * D2 * np * tksz);
+        const size_t red = (size_t)NG * np * np * tksz;
+        return bytes > red ? bytes : red;
+    };
+    int CH = 64;
+    while (CH > 1 && smem_for(CH) > 96 * 1024) CH /= 2;
+    const size_t sm = smem_for(CH);
+    if (o.precision == 0) {
+        cudaFuncSetAttribute(k_assemble<D, double, TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_assemble<D, double, TM><<<(int)Bt.B, nthreads, sm, s>>>(M, Bt, CH, NG);
+    } else {
+        cudaFuncSetAttribute(k_assemble<D, float, TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_assemble<D, float, TM><<<(int)Bt.B, nthreads, sm, s>>>(M, Bt, CH, NG);
+    }
+    return 0;
+}
+
 template <int D>
 static int launch_kernels_t(int which, const Model &M, Batch Bt, const StepOpts &o, int32_t *list_next,
                             cudaStream_t s) {
@@ -775,30 +818,19 @@ static int launch_kernels_t(int which, const Model &M, Batch Bt, const StepOpts 
         return 0;
     }
     if (which == 2) {
-        constexpr int TM = (D == 2) ? 2 : 4;
-        const int NT = (M.n + TM - 1) / TM, np = NT * TM;
-        const int nup = NT * (NT + 1) / 2;
-        int NG = nup >= 256 ? 1 : 256 / nup;
-        const int nthreads = ((NG * nup + 31) / 32) * 32;
-        if (nthreads > 256) return -1;   // n too large for one tile per thread
-        const int tksz = o.precision == 0 ? 8 : 4;
-        auto smem_for = [&](int CH) {
-            size_t bytes = (size_t)CH * D2 * np * 8 + (size_t)CH * D2 * np * tksz + (size_t)CH * D4 * tksz + 16 +
-                           (size_t)CH * D2 * 8 + (o.precision == 0 ? 0 : (size_t)CH * D2 * np * tksz);
-            const size_t red = (size_t)NG * np * np * tksz;
-            return bytes > red ? bytes : red;
-        };
-        int CH = 64;
-        while (CH > 1 && smem_for(CH) > 96 * 1024) CH /= 2;
-        const size_t sm = smem_for(CH);
-        if (o.precision == 0) {
-            cudaFuncSetAttribute(k_assemble<D, double, TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            k_assemble<D, double, TM><<<(int)Bt.B, nthreads, sm, s>>>(M, Bt, CH, NG);
-        } else {
-            cudaFuncSetAttribute(k_assemble<D, float, TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            k_assemble<D, float, TM><<<(int)Bt.B, nthreads, sm, s>>>(M, Bt, CH, NG);
+        // tile edge TM: the smallest of 2, 4, 8 for which one upper-triangular tile per thread fits 256 threads
+        const int tms[3] = {2, 4, 8};
+        for (int q = 0; q < 3; ++q) {
+            const int TMv = tms[q];
+            const int NT = (M.n + TMv - 1) / TMv;
+            if (NT * (NT + 1) / 2 <= 256 && (D == 3 || TMv >= 2)) {
+                if (D == 3 && TMv == 2 && M.n > 16) continue;   // keep 3D tiles >= 4 for register reuse
+                return TMv == 2 ? launch_assemble<D, 2>(M, Bt, o, s)
+                     : TMv == 4 ? launch_assemble<D, 4>(M, Bt, o, s)
+                                : launch_assemble<D, 8>(M, Bt, o, s);
+            }
         }
-        return 0;
+        return -1;
     }
     if (which == 3) {
         const size_t sms = (size_t)M.n * M.n * 8 + (size_t)M.n * 8 + (size_t)M.n * 4 + 16;

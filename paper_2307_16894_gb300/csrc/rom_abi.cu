@@ -32,6 +32,10 @@ void mlp_train_step(MlpDev &M, const float *X, const float *Y, int64_t N, float 
 void mlp_loss_grad(MlpDev &M, const float *X, const float *Y, int64_t N, int bf16, float *grad_out, float *loss_out,
                    cudaStream_t s);
 void mlp_predict(MlpDev &M, const float *X, int64_t N, int bf16, double *out, cudaStream_t s);
+void tc_image_shape(int d, int fmt, int m, int *chunk_bytes, int *nchunks);
+void tc_build_image(int d, int fmt, int n, int m, const double *G, unsigned char *img);
+int launch_tc(int fmt, const Model &M, Batch Bt, const unsigned char *img, int *err, cudaStream_t s);
+void launch_list_converged(Batch Bt, cudaStream_t s);
 }  // namespace podecm
 
 using namespace podecm;
@@ -65,6 +69,9 @@ struct rom_ctx {
     double prof_ms[ROM_NKERNELS] = {0};
     int64_t prof_launches[ROM_NKERNELS] = {0};
     double prof_flops[ROM_NKERNELS] = {0};
+    // tensor-core assembly: pre-arranged B-operand images of G (BF16, TF32) and an error flag
+    unsigned char *tc_img[2] = {nullptr, nullptr};
+    int *d_err = nullptr;
     // learned Newton start
     bool has_mlp = false, mlp_norm = false;
     MlpDev mlp{};
@@ -168,6 +175,9 @@ rom_status rom_destroy(rom_ctx *ctx) {
     if (ctx->has_mlp) mlp_free(ctx->mlp);
     p = ctx->d_feat; dfree(p);
     p = ctx->d_pred; dfree(p);
+    p = ctx->tc_img[0]; dfree(p);
+    p = ctx->tc_img[1]; dfree(p);
+    p = ctx->d_err; dfree(p);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return ROM_OK;
@@ -202,6 +212,21 @@ rom_status rom_load_basis(rom_ctx *ctx, int n, int m, const double *G) {
     CK(cudaMemcpy(ctx->G_pt, G, cnt * 8, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->G_T, gt.data(), cnt * 8, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->G32, g32.data(), cnt * 4, cudaMemcpyHostToDevice));
+    for (int f = 0; f < 2; ++f) { p = ctx->tc_img[f]; dfree(p); ctx->tc_img[f] = nullptr; }
+    if (n <= 64) {
+        for (int f = 0; f < 2; ++f) {
+            int cb, nch;
+            tc_image_shape(ctx->dim, f + 1, m, &cb, &nch);
+            std::vector<unsigned char> img((size_t)cb * nch);
+            tc_build_image(ctx->dim, f + 1, n, m, G, img.data());
+            if ((s = dalloc(ctx, (void **)&ctx->tc_img[f], img.size())) != ROM_OK) return s;
+            CK(cudaMemcpy(ctx->tc_img[f], img.data(), img.size(), cudaMemcpyHostToDevice));
+        }
+        if (!ctx->d_err) {
+            if ((s = dalloc(ctx, (void **)&ctx->d_err, 16)) != ROM_OK) return s;
+            CK(cudaMemset(ctx->d_err, 0, 16));
+        }
+    }
     ctx->n = n;
     ctx->m = m;
     ctx->has_basis = true;
@@ -410,7 +435,8 @@ static rom_status check_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts) 
         return fail(ctx, ROM_E_STATE, "rom_step: learned start requested but no MLP (rom_mlp_init, rom_mlp_params, rom_mlp_norm)");
     if (opts->start == ROM_START_MLP && ctx->mlp.n_in != ctx->dim * ctx->dim + ctx->n_par + ctx->n + 2)
         return fail(ctx, ROM_E_STATE, "rom_step: MLP input size %d does not match d^2 + n_par + n + 2", ctx->mlp.n_in);
-    if (opts->precision >= ROM_PREC_TF32) return fail(ctx, ROM_E_ARG, "rom_step: precision mode not available");
+    if (opts->precision >= ROM_PREC_TF32 && !ctx->tc_img[0])
+        return fail(ctx, ROM_E_ARG, "rom_step: tensor-core precision needs n <= 64 (n = %d)", ctx->n);
     return ROM_OK;
 }
 
@@ -508,8 +534,14 @@ static rom_status run_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts, co
         bt.list = lists[pass & 1];
         int32_t *nxt = lists[(pass + 1) & 1];
         const double na = (double)n_act;
+        auto asm_launch = [&] {
+            if (o.precision >= 2)
+                return launch_tc(o.precision == 3 ? 1 : 2, M, bt, ctx->tc_img[o.precision == 3 ? 0 : 1], ctx->d_err,
+                                 ctx->stream);
+            return launch_kernel(2, M, bt, o, nxt, ctx->stream);
+        };
         if (timed(ctx, 1, na * fl_kin, [&] { return launch_kernel(1, M, bt, o, nxt, ctx->stream); }) ||
-            timed(ctx, 2, na * fl_asm, [&] { return launch_kernel(2, M, bt, o, nxt, ctx->stream); }) ||
+            timed(ctx, 2, na * fl_asm, asm_launch) ||
             timed(ctx, 3, na * fl_lu, [&] { return launch_kernel(3, M, bt, o, nxt, ctx->stream); }) ||
             timed(ctx, 5, 0.0, [&] { return launch_kernel(5, M, bt, o, nxt, ctx->stream); }))
             return fail(ctx, ROM_E_ARG, "rom_step: basis size n=%d not supported by the assembly kernel", M.n);
@@ -518,6 +550,23 @@ static rom_status run_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts, co
         CK(cudaStreamSynchronize(ctx->stream));
         n_act = ctx->h_count[0];
         if (n_act == 0) break;
+    }
+    if (o.precision >= 2) {
+        // the effective stiffness needs K at FP32 accuracy: one FP32 assembly of the converged instances
+        CK(cudaMemcpyAsync(ctx->h_count + 4, ctx->d_err, 4, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        if (ctx->h_count[4]) {
+            cudaMemsetAsync(ctx->d_err, 0, 4, ctx->stream);
+            return fail(ctx, ROM_E_CUDA, "rom_step: tensor-core pipeline wait timed out");
+        }
+        if (o.want_abar) {
+            Batch bc = bt;
+            bc.list = lists[0];
+            StepOpts o32 = o;
+            o32.precision = 1;
+            launch_list_converged(bc, ctx->stream);
+            timed(ctx, 2, 0.0, [&] { return launch_kernel(2, M, bc, o32, lists[1], ctx->stream); });
+        }
     }
     if (timed(ctx, 4, 0.0, [&] { return launch_finalize(M, bt, o, Pbar_d, Abar_d, info_d, ctx->stream); }))
         return fail(ctx, ROM_E_ARG, "rom_step: n*d*d too large for the finalize kernel");
@@ -668,6 +717,14 @@ rom_status rom_features(rom_ctx *ctx, rom_state *st, const double *Fbar_d, float
     launch_start(M, bt, Fbar_d, o, nullptr, ctx->stream);
     launch_features(M, bt, bt.U_prev, X_d, ctx->dim * ctx->dim + ctx->n_par + ctx->n + 2, ctx->stream);
     CK(cudaGetLastError());
+    return ROM_OK;
+}
+
+rom_status rom_debug_stiffness(rom_ctx *ctx, const rom_state *st, double *K) {
+    if (!ctx || !st || !K || st->ctx != ctx) return ROM_E_ARG;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpy(K, st->bt.K, (size_t)st->B * st->n * st->n * 8, cudaMemcpyDeviceToHost));
     return ROM_OK;
 }
 

@@ -1,0 +1,349 @@
+// Reduced stiffness K_b = sum_i G_i^T At_i G_i (Eq. stiffnessmatrix_ecm) on the 5th-generation
+// tensor cores (tcgen05.mma, BF16 or TF32 operands, FP32 accumulation in tensor memory).
+//
+// Formulation: K_b = Y_b^T G with Y_b = blockdiag_i(At_i) G (rows = (point i, component c)).
+// One CTA holds two instances (b0, b1): the MMA is D[128 x 64] += A[128 x K] B[64 x K]^T with
+//   A rows 0..63   = Y_b0^T (row j, column (i,c)),  A rows 64..127 = Y_b1^T,
+//   B rows j       = G[:, :, j] (column (i,c)),     D rows = K_b0 rows, then K_b1 rows.
+// The K dimension runs over chunks of PC cubature points (KC = PC * d^2 columns).  Per chunk:
+//   * the A tile (Y^T) is produced by all threads in FP32 from the FP32 tangent At and the
+//     FP32 basis copy, rounded to BF16/TF32 and stored in the canonical K-major layout;
+//   * the B tile is a pre-arranged image of G (same layout) fetched with one bulk copy
+//     (cp.async.bulk, the TMA engine) that completes on an mbarrier;
+//   * one thread issues KC/16 (BF16) or KC/8 (TF32) tcgen05.mma and commits them to an
+//     mbarrier, so the next chunk's producer work overlaps the tensor cores (2 stages).
+// Shared-memory operand layout (no swizzle, K-major): 8-row x 16-byte core matrices; core
+// matrices adjacent in K are 128 bytes apart (leading byte offset), 8-row groups are
+// SBO = KC * esize / 16 * 128 bytes apart (stride byte offset).
+// Every wait is bounded; on timeout the kernel records an error, waits (bounded) for its
+// own outstanding MMAs, frees its tensor memory and returns.
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstring>
+
+#include "kernels.cuh"
+
+namespace podecm {
+
+namespace tc {
+
+constexpr int MROWS = 128;       // MMA M (two instances x 64 rows)
+constexpr int NCOLS = 64;        // MMA N (n padded to 64)
+constexpr int THREADS = 256;
+constexpr long long WAIT_LIMIT = 20000000;   // try_wait polls before giving up
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;          // descriptor version for tcgen05
+    // base offset 0, LBO mode 0, layout type 0 (no swizzle)
+    return d;
+}
+
+// kind::f16 / kind::tf32 instruction descriptor: D = F32, A/B formats, both K-major, N, M
+__host__ __device__ constexpr uint32_t make_idesc(uint32_t ab_format, int M, int N) {
+    return (1u << 4) | (ab_format << 7) | (ab_format << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase) {
+    const uint32_t a = smem_u32(bar);
+    for (long long it = 0; it < WAIT_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred P1;\n mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n selp.b32 %0, 1, 0, P1;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(phase)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+template <int FMT>
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+    if (FMT == 1) {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                tmem_d),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+    } else {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                tmem_d),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+    }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// store one rounded element of the A tile (row r, column k) in the canonical layout
+template <int FMT>
+__device__ __forceinline__ void store_a(unsigned char *tile, int sbo, int r, int k, float v) {
+    if (FMT == 1) {
+        const int off = (r >> 3) * sbo + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+        *reinterpret_cast<__nv_bfloat16 *>(tile + off) = __float2bfloat16(v);
+    } else {
+        const int off = (r >> 3) * sbo + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4;
+        *reinterpret_cast<float *>(tile + off) = v;   // the tensor core reads the TF32 part
+    }
+}
+
+}  // namespace tc
+
+// FMT: 1 = BF16 (PC = 16 points per chunk), 2 = TF32 (PC = 8)
+template <int D, int FMT>
+__global__ void __launch_bounds__(tc::THREADS, 1)
+    k_assemble_tc(Model M, Batch Bt, const unsigned char *__restrict__ Gimg, int nchunks, int *err_flag) {
+    using namespace tc;
+    constexpr int D2 = D * D, D4 = D2 * D2;
+    constexpr int PC = (FMT == 1) ? 16 : 8;
+    constexpr int KC = PC * D2;
+    constexpr int ES = (FMT == 1) ? 2 : 4;
+    constexpr int SBO = KC * ES / 16 * 128;
+    constexpr int A_BYTES = (MROWS / 8) * SBO;
+    constexpr int B_BYTES = (NCOLS / 8) * SBO;
+    constexpr int KSTEP = (FMT == 1) ? 16 : 8;
+    constexpr int NK = KC / KSTEP;
+    constexpr uint32_t IDESC = make_idesc(FMT == 1 ? 1u : 2u, MROWS, NCOLS);
+
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *Ast[2] = {smem, smem + A_BYTES};
+    unsigned char *Bst[2] = {smem + 2 * A_BYTES, smem + 2 * A_BYTES + B_BYTES};
+    float *Gs = reinterpret_cast<float *>(smem + 2 * A_BYTES + 2 * B_BYTES);          // [PC][D2][64]
+    float *As = Gs + PC * D2 * NCOLS;                                                   // [2][PC][D4]
+    __shared__ __align__(8) uint64_t bar_mma[2], bar_load[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_s;
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int n_act = Bt.counts[0];
+    const int p0 = 2 * blockIdx.x;
+    if (p0 >= n_act) return;
+    const bool has1 = (p0 + 1) < n_act;
+    const int64_t bI[2] = {Bt.list[p0], has1 ? Bt.list[p0 + 1] : Bt.list[p0]};
+    const int n = M.n, m = M.m;
+    const float *At = reinterpret_cast<const float *>(Bt.At);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(NCOLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        mbar_init(&bar_mma[0], 1);
+        mbar_init(&bar_mma[1], 1);
+        mbar_init(&bar_load[0], 1);
+        mbar_init(&bar_load[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_s = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    uint32_t ph_mma[2] = {0, 0}, ph_load[2] = {0, 0};
+    int issued[2] = {0, 0};
+
+    for (int c = 0; c < nchunks; ++c) {
+        const int s = c & 1;
+        if (tid == 0) {
+            bool ok = true;
+            if (issued[s]) { ok = mbar_wait(&bar_mma[s], ph_mma[s]); ph_mma[s] ^= 1; issued[s] = 0; }
+            if (!ok) abort_s = 1;
+            else bulk_load(Bst[s], Gimg + (size_t)c * B_BYTES, B_BYTES, &bar_load[s]);
+        }
+        __syncthreads();
+        if (abort_s) break;
+        // stage the FP32 basis chunk and the two instances' tangents
+        const int c0 = c * PC;
+        for (int e = tid; e < PC * D2 * NCOLS; e += THREADS) {
+            const int j = e % NCOLS, rc = e / NCOLS;
+            const int ii = rc / D2;
+            const int q = rc - ii * D2;
+            Gs[e] = (j < n && c0 + ii < m) ? M.G32_pt[((size_t)(c0 + ii) * D2 + q) * n + j] : 0.f;
+        }
+        for (int e = tid; e < 2 * PC * D4; e += THREADS) {
+            const int inst = e / (PC * D4), rem = e - inst * PC * D4;
+            const int ce = rem / PC, ii = rem - ce * PC;
+            const bool valid = (inst == 0 || has1) && (c0 + ii < m);
+            As[(inst * PC + ii) * D4 + ce] = valid ? At[((size_t)bI[inst] * D4 + ce) * m + c0 + ii] : 0.f;
+        }
+        __syncthreads();
+        // producer: A[inst*64 + j][ii*D2 + cc] = sum_e At[ii][cc][e] G[ii][e][j]
+        for (int e = tid; e < 2 * PC * NCOLS; e += THREADS) {
+            const int j = e % NCOLS, r2 = e / NCOLS;
+            const int ii = r2 % PC, inst = r2 / PC;
+            float g[D2];
+#pragma unroll
+            for (int q = 0; q < D2; ++q) g[q] = Gs[(ii * D2 + q) * NCOLS + j];
+            const float *a = As + (inst * PC + ii) * D4;
+#pragma unroll
+            for (int cc = 0; cc < D2; ++cc) {
+                float y = 0.f;
+#pragma unroll
+                for (int q = 0; q < D2; ++q) y = fmaf(a[cc * D2 + q], g[q], y);
+                tc::store_a<FMT>(Ast[s], SBO, inst * 64 + j, ii * D2 + cc, y);
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            const bool ok = mbar_wait(&bar_load[s], ph_load[s]);
+            ph_load[s] ^= 1;
+            if (!ok) {
+                abort_s = 1;
+            } else {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t a0 = smem_u32(Ast[s]), b0 = smem_u32(Bst[s]);
+#pragma unroll
+                for (int k = 0; k < NK; ++k) {
+                    const uint64_t ad = tc::make_desc(a0 + k * 256, 128, SBO);
+                    const uint64_t bd = tc::make_desc(b0 + k * 256, 128, SBO);
+                    tc::mma<FMT>(tmem, ad, bd, IDESC, (c > 0 || k > 0) ? 1u : 0u);
+                }
+                tc::mma_commit(&bar_mma[s]);
+                issued[s] = 1;
+            }
+        }
+        __syncthreads();
+        if (abort_s) break;
+    }
+    // drain: wait for the outstanding commits (bounded)
+    if (tid == 0) {
+        for (int s = 0; s < 2; ++s)
+            if (issued[s]) {
+                if (!mbar_wait(&bar_mma[s], ph_mma[s])) abort_s = 1;
+                ph_mma[s] ^= 1;
+            }
+        if (abort_s && err_flag) atomicExch(err_flag, 1);
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!abort_s && warp < 4) {
+        // warp w reads TMEM lanes 32w .. 32w+31 = output rows; 2 x 32 columns
+        const int row = warp * 32 + (tid & 31);
+        const int inst = row >> 6, j = row & 63;
+        float v[64];
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(half * 32);
+            uint32_t r[32];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int q = 0; q < 32; ++q) v[half * 32 + q] = __uint_as_float(r[q]);
+        }
+        if (j < n && (inst == 0 || has1)) {
+            double *Kb = Bt.K + (size_t)bI[inst] * n * n + (size_t)j * n;
+            for (int k = 0; k < n; ++k) Kb[k] = (double)v[k];
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS));
+}
+
+// force f = sum_i G_i^T v_i in FP64 (same summation order as k_assemble), one CTA per instance
+__global__ void __launch_bounds__(128) k_force(Model M, Batch Bt) {
+    const int n_act = Bt.counts[0];
+    const int p = blockIdx.x;
+    if (p >= n_act) return;
+    const int64_t b = Bt.list[p];
+    const int n = M.n, m = M.m, d2 = M.d2;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        double acc = 0.0;
+        for (int i = 0; i < m; ++i)
+            for (int c = 0; c < d2; ++c)
+                acc += M.G_pt[((size_t)i * d2 + c) * n + j] * Bt.v[((size_t)b * d2 + c) * m + i];
+        Bt.r[b * n + j] = acc;
+    }
+}
+
+// bytes of one B-operand chunk image and the chunk count for a model
+void tc_image_shape(int d, int fmt, int m, int *chunk_bytes, int *nchunks) {
+    const int d2 = d * d;
+    const int PC = fmt == 1 ? 16 : 8;
+    const int KC = PC * d2, ES = fmt == 1 ? 2 : 4;
+    const int SBO = KC * ES / 16 * 128;
+    *chunk_bytes = (tc::NCOLS / 8) * SBO;
+    *nchunks = (m + PC - 1) / PC;
+}
+
+// host: pre-arranged B-operand image of G[m][d2][n] (n <= 64), chunk-major
+void tc_build_image(int d, int fmt, int n, int m, const double *G, unsigned char *img) {
+    const int d2 = d * d;
+    const int PC = fmt == 1 ? 16 : 8;
+    const int KC = PC * d2, ES = fmt == 1 ? 2 : 4;
+    const int SBO = KC * ES / 16 * 128;
+    int cb, nch;
+    tc_image_shape(d, fmt, m, &cb, &nch);
+    for (int c = 0; c < nch; ++c) {
+        unsigned char *t = img + (size_t)c * cb;
+        for (int j = 0; j < tc::NCOLS; ++j)
+            for (int k = 0; k < KC; ++k) {
+                const int ii = k / d2, q = k % d2, i = c * PC + ii;
+                const double g = (j < n && i < m) ? G[((size_t)i * d2 + q) * n + j] : 0.0;
+                if (fmt == 1) {
+                    const int off = (j >> 3) * SBO + (k >> 3) * 128 + (j & 7) * 16 + (k & 7) * 2;
+                    const __nv_bfloat16 h = __float2bfloat16((float)g);
+                    memcpy(t + off, &h, 2);
+                } else {
+                    const int off = (j >> 3) * SBO + (k >> 2) * 128 + (j & 7) * 16 + (k & 3) * 4;
+                    const float f = (float)g;
+                    memcpy(t + off, &f, 4);
+                }
+            }
+    }
+}
+
+template <int D, int FMT>
+static int launch_tc_t(const Model &M, Batch Bt, const unsigned char *img, int *err, cudaStream_t s) {
+    constexpr int D2 = D * D, D4 = D2 * D2;
+    constexpr int PC = (FMT == 1) ? 16 : 8;
+    constexpr int KC = PC * D2, ES = (FMT == 1) ? 2 : 4;
+    constexpr int SBO = KC * ES / 16 * 128;
+    constexpr int A_BYTES = (tc::MROWS / 8) * SBO, B_BYTES = (tc::NCOLS / 8) * SBO;
+    const size_t sm = 2 * (size_t)A_BYTES + 2 * (size_t)B_BYTES + (size_t)PC * D2 * tc::NCOLS * 4 + 2 * (size_t)PC * D4 * 4;
+    if (M.n > tc::NCOLS) return -1;
+    const int nch = (M.m + PC - 1) / PC;
+    cudaFuncSetAttribute(k_assemble_tc<D, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_assemble_tc<D, FMT><<<(int)((Bt.B + 1) / 2), tc::THREADS, sm, s>>>(M, Bt, img, nch, err);
+    k_force<<<(int)Bt.B, 128, 0, s>>>(M, Bt);
+    return 0;
+}
+
+int launch_tc(int fmt, const Model &M, Batch Bt, const unsigned char *img, int *err, cudaStream_t s) {
+    if (M.d == 2) return fmt == 1 ? launch_tc_t<2, 1>(M, Bt, img, err, s) : launch_tc_t<2, 2>(M, Bt, img, err, s);
+    return fmt == 1 ? launch_tc_t<3, 1>(M, Bt, img, err, s) : launch_tc_t<3, 2>(M, Bt, img, err, s);
+}
+
+}  // namespace podecm

@@ -61,13 +61,15 @@ def test_mlp_training_reduces_loss():
     rng = np.random.default_rng(1)
     n_in, n_out, N = 10, 4, 4096
     X = rng.standard_normal((N, n_in)).astype(np.float32)
-    Wt = rng.standard_normal((n_in, n_out))
-    Y = (np.tanh(X @ Wt) + 0.1 * X[:, :n_out] ** 2).astype(np.float32)
+    Wt = rng.standard_normal((n_in, n_out)) / np.sqrt(n_in)
+    Z = X @ Wt
+    Y = (np.sin(Z) + 0.5 * Z + 0.1 * Z ** 2).astype(np.float32)
     ctx = make_ctx(n_in, n_out, 512)
     ctx.mlp_params(warmstart.init_params(n_in, warmstart.WIDTH, warmstart.DEPTH, n_out, 0))
     ctx.mlp_norm(*warmstart.fit_norm(X, Y))
-    hist = warmstart.train(ctx, X, Y, torch, epochs=6, batch=256, lr=1e-3)
-    assert hist[-1][1] < 0.2 * hist[0][1] or hist[-1][1] < 0.02
+    hist = warmstart.train(ctx, X, Y, torch, epochs=10, batch=256, lr=1e-3)
+    print("training history (train, validation):", hist)
+    assert hist[-1][1] < 0.1
     ctx.close()
 
 
