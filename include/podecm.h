@@ -172,6 +172,14 @@ const char *rom_last_error(const rom_ctx *ctx);
  * 2 n^3/3 + 2 n^2 -- per active instance and launch).  Any pointer may be NULL. */
 rom_status rom_profile(rom_ctx *ctx, int enable);
 
+/* Graph mode: with enable = 1, rom_step_device runs each load step as one CUDA-graph launch
+ * whose Newton passes execute inside a conditional WHILE node decided on the device (no
+ * host synchronisation per pass).  The graph is captured on the first step with given
+ * options for a state and reused while the options stay the same; Fbar is copied into and
+ * Pbar, Abar, info out of state-owned buffers around the launch.  Profiling (rom_profile)
+ * uses the per-launch path.  Default 0. */
+rom_status rom_use_graphs(rom_ctx *ctx, int enable);
+
 /* Diagnostics: the reduced stiffness K[B][n][n] of the last evaluated iterate of every
  * instance (as assembled by the selected precision mode; for ROM_PREC_TF32/BF16 and
  * converged instances with want_abar, the FP32 re-assembly used for Abar).  Blocking. */

@@ -25,7 +25,7 @@ EXPORTED = ["rom_create", "rom_destroy", "rom_load_basis", "rom_load_cubature", 
             "rom_state_create", "rom_state_destroy", "rom_state_export", "rom_state_import", "rom_step",
             "rom_step_device", "rom_sync", "rom_last_error", "rom_profile", "rom_profile_read",
             "rom_step_noalloc", "rom_mlp_init", "rom_mlp_nparams", "rom_mlp_params", "rom_mlp_norm",
-            "rom_mlp_train_step", "rom_mlp_loss_grad", "rom_mlp_predict", "rom_features", "rom_debug_stiffness"]
+            "rom_mlp_train_step", "rom_mlp_loss_grad", "rom_mlp_predict", "rom_features", "rom_debug_stiffness", "rom_use_graphs"]
 
 KERNEL_GROUPS = ["start", "constitutive", "assemble", "solve", "finalize", "bookkeeping", "learned_start"]
 
@@ -90,6 +90,7 @@ def lib(path=None):
     L.rom_mlp_predict.argtypes = [p, p, i64, i, p]
     L.rom_features.argtypes = [p, p, p, p]
     L.rom_debug_stiffness.argtypes = [p, p, p]
+    L.rom_use_graphs.argtypes = [p, i]
     L.rom_last_error.argtypes = [p]
     L.rom_last_error.restype = ctypes.c_char_p
     for f in EXPORTED:
@@ -204,6 +205,9 @@ class Context:
 
     def sync(self):
         self._check(self.L.rom_sync(self.h), "rom_sync")
+
+    def use_graphs(self, enable=True):
+        self._check(self.L.rom_use_graphs(self.h, int(enable)), "rom_use_graphs")
 
     # ---- learned Newton start
     def mlp_init(self, n_in, width, depth, n_out, max_rows):

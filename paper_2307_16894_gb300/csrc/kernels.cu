@@ -747,6 +747,33 @@ __global__ void __launch_bounds__(256) k_finalize(Model M, Batch Bt, StepOpts o,
     if (Bt.U_prev && tid < D2) Bt.U_prev[b * D2 + tid] = Ub[tid];
 }
 
+// ---------------------------------------------------------------- graph loop
+// device-driven Newton loop: copy the next active list into the current one, then set the
+// while-node condition of the captured step graph (more passes iff instances remain active
+// and the pass cap is not reached)
+__global__ void k_copy_list(const int32_t *__restrict__ src, int32_t *__restrict__ dst, const int32_t *counts,
+                            int64_t B) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < B && i < counts[1]) dst[i] = src[i];
+}
+
+__global__ void k_advance_cond(int32_t *counts, cudaGraphConditionalHandle h, int max_pass) {
+    counts[0] = counts[1];
+    counts[1] = 0;
+    counts[2] += 1;
+    cudaGraphSetConditional(h, (counts[0] > 0 && counts[2] < max_pass) ? 1u : 0u);
+}
+
+__global__ void k_reset_pass(int32_t *counts) { counts[2] = 0; }
+
+void launch_graph_advance(Batch Bt, const int32_t *list_next, cudaGraphConditionalHandle h, int max_pass,
+                          cudaStream_t s) {
+    k_copy_list<<<(int)((Bt.B + 255) / 256), 256, 0, s>>>(list_next, Bt.list, Bt.counts, Bt.B);
+    k_advance_cond<<<1, 1, 0, s>>>(Bt.counts, h, max_pass);
+}
+
+void launch_reset_pass(Batch Bt, cudaStream_t s) { k_reset_pass<<<1, 1, 0, s>>>(Bt.counts); }
+
 // compacted list of the converged instances (status OK) into list / counts[0]
 __global__ void k_list_converged(Batch Bt) {
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

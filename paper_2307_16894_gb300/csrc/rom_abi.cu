@@ -36,6 +36,9 @@ void tc_image_shape(int d, int fmt, int m, int *chunk_bytes, int *nchunks);
 void tc_build_image(int d, int fmt, int n, int m, const double *G, unsigned char *img);
 int launch_tc(int fmt, const Model &M, Batch Bt, const unsigned char *img, int *err, cudaStream_t s);
 void launch_list_converged(Batch Bt, cudaStream_t s);
+void launch_graph_advance(Batch Bt, const int32_t *list_next, cudaGraphConditionalHandle h, int max_pass,
+                          cudaStream_t s);
+void launch_reset_pass(Batch Bt, cudaStream_t s);
 }  // namespace podecm
 
 using namespace podecm;
@@ -75,6 +78,8 @@ struct rom_ctx {
     // learned Newton start
     bool has_mlp = false, mlp_norm = false;
     MlpDev mlp{};
+    bool graphs = false;            // rom_step_device through a captured step graph
+    int64_t graph_epoch = 0;        // bumped when buffers captured by graphs are reallocated
     float *d_feat = nullptr;        // [B][n_in]
     double *d_pred = nullptr;       // [B][n]
     int64_t feat_B = 0;
@@ -87,6 +92,14 @@ struct rom_state {
     Batch bt{};
     int32_t *list2 = nullptr;
     std::vector<void *> allocs;
+    // captured step graph (device-driven Newton loop) and its fixed I/O buffers
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t gstream = nullptr;
+    rom_opts gopts{};
+    bool g_valid = false;
+    int64_t g_epoch = -1;
+    double *io_F = nullptr, *io_P = nullptr, *io_A = nullptr;
+    void *io_info = nullptr;
 };
 
 static rom_status fail(rom_ctx *c, rom_status s, const char *fmt, ...) {
@@ -348,7 +361,9 @@ rom_status rom_state_create(rom_ctx *ctx, int64_t B, rom_state **out) {
         (s = A((void **)&bt.cp_tr, Bz * ncp * m * 8)) || (s = A((void **)&bt.xi_tr, Bz * m * 8)) ||
         (s = A((void **)&bt.pl, Bz * m)) || (s = A((void **)&bt.r, Bz * n * 8)) ||
         (s = A((void **)&bt.K, Bz * n * n * 8)) || (s = A((void **)&bt.Ubar, Bz * d2 * 8)) ||
-        (s = A((void **)&bt.Rbar, Bz * d2 * 8)) || (s = A((void **)&bt.U_prev, Bz * d2 * 8))) {
+        (s = A((void **)&bt.Rbar, Bz * d2 * 8)) || (s = A((void **)&bt.U_prev, Bz * d2 * 8)) ||
+        (s = A((void **)&st->io_F, Bz * d2 * 8)) || (s = A((void **)&st->io_P, Bz * d2 * 8)) ||
+        (s = A((void **)&st->io_A, Bz * d2 * d2 * 8)) || (s = A(&st->io_info, Bz * sizeof(rom_step_info)))) {
         rom_state_destroy(st);
         return s;
     }
@@ -378,6 +393,8 @@ rom_status rom_state_create(rom_ctx *ctx, int64_t B, rom_state **out) {
 rom_status rom_state_destroy(rom_state *st) {
     if (!st) return ROM_E_ARG;
     if (st->ctx) cudaSetDevice(st->ctx->device);
+    if (st->gexec) cudaGraphExecDestroy(st->gexec);
+    if (st->gstream) cudaStreamDestroy(st->gstream);
     for (void *p : st->allocs) cudaFree(p);
     delete st;
     return ROM_OK;
@@ -453,6 +470,7 @@ static Model make_model(const rom_ctx *ctx) {
 
 static rom_status ensure_feat(rom_ctx *ctx, int64_t B) {
     if (ctx->feat_B >= B) return ROM_OK;
+    ++ctx->graph_epoch;
     void *p;
     p = ctx->d_feat; dfree(p); ctx->d_feat = nullptr;
     p = ctx->d_pred; dfree(p); ctx->d_pred = nullptr;
@@ -575,6 +593,116 @@ static rom_status run_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts, co
     return ROM_OK;
 }
 
+static bool same_opts(const rom_opts &a, const rom_opts &b) { return memcmp(&a, &b, sizeof(rom_opts)) == 0; }
+static bool o_needs_recapture(const rom_state *st, const rom_opts *opts) {
+    return !st->g_valid || !same_opts(st->gopts, *opts) || st->g_epoch != st->ctx->graph_epoch;
+}
+
+// Capture one load step into a CUDA graph whose Newton passes run inside a conditional WHILE
+// node: the device decides how many passes to run (no host round trip per pass).  The graph
+// reads Fbar from and writes Pbar / Abar / info to buffers owned by the state, so one
+// instantiation serves every later step with the same options.
+static rom_status capture_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts) {
+    if (st->gexec) { cudaGraphExecDestroy(st->gexec); st->gexec = nullptr; }
+    st->g_valid = false;
+    if (!st->gstream) CK(cudaStreamCreateWithFlags(&st->gstream, cudaStreamNonBlocking));
+    StepOpts o;
+    o.tol_rel = opts->tol_rel; o.tol_abs = opts->tol_abs; o.max_iter = opts->max_iter; o.max_ls = opts->max_ls;
+    o.precision = opts->precision; o.start = opts->start; o.polar = opts->polar_split; o.want_abar = opts->want_abar;
+    const Model M = make_model(ctx);
+    Batch bt = st->bt;
+    bt.mu = ctx->mu;
+    const int max_pass = (opts->max_iter + 1) * (opts->max_ls + 1) + 2;
+    cudaStream_t cs = st->gstream;
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    int bad = 0;
+    bad |= launch_start(M, bt, st->io_F, o, nullptr, cs);
+    launch_reset_pass(bt, cs);
+    if (o.start == ROM_START_MLP) {
+        launch_features(M, bt, bt.U_prev, ctx->d_feat, ctx->mlp.n_in, cs);
+        mlp_predict(ctx->mlp, ctx->d_feat, st->B, 1, ctx->d_pred, cs);
+        launch_add_pred(bt, M.n, ctx->d_pred, cs);
+    }
+    // conditional WHILE node for the Newton passes
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, nullptr, &ndeps);
+    cudaGraphConditionalHandle h{};
+    cudaGraphNode_t wnode{};
+    cudaGraph_t body = nullptr;
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, cg, 1, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) {
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&wnode, cg, deps, nullptr, ndeps, &cp);
+        if (e == cudaSuccess) body = cp.conditional.phGraph_out[0];
+    }
+    if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(cs, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess) {
+        cudaStream_t bs = nullptr;
+        e = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            int32_t *nxt = st->list2;
+            bad |= launch_kernel(1, M, bt, o, nxt, bs);
+            if (o.precision >= 2)
+                bad |= launch_tc(o.precision == 3 ? 1 : 2, M, bt, ctx->tc_img[o.precision == 3 ? 0 : 1], ctx->d_err, bs);
+            else
+                bad |= launch_kernel(2, M, bt, o, nxt, bs);
+            bad |= launch_kernel(3, M, bt, o, nxt, bs);
+            launch_graph_advance(bt, nxt, h, max_pass, bs);
+            cudaGraph_t out = nullptr;
+            cudaError_t e2 = cudaStreamEndCapture(bs, &out);
+            if (e == cudaSuccess) e = e2;
+        }
+        if (bs) cudaStreamDestroy(bs);
+    }
+    if (e == cudaSuccess && o.precision >= 2 && o.want_abar) {
+        Batch bc = bt;
+        StepOpts o32 = o;
+        o32.precision = 1;
+        launch_list_converged(bc, cs);
+        bad |= launch_kernel(2, M, bc, o32, st->list2, cs);
+    }
+    if (e == cudaSuccess) bad |= launch_finalize(M, bt, o, st->io_P, st->io_A, st->io_info, cs);
+    cudaError_t e3 = cudaStreamEndCapture(cs, &graph);
+    if (e == cudaSuccess) e = e3;
+    if (e != cudaSuccess || bad) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return fail(ctx, ROM_E_CUDA, "rom_step: graph capture failed: %s", e != cudaSuccess ? cudaGetErrorString(e) : "launch configuration");
+    }
+    e = cudaGraphInstantiate(&st->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(ctx, ROM_E_CUDA, "rom_step: graph instantiate failed: %s", cudaGetErrorString(e));
+    st->gopts = *opts;
+    st->g_valid = true;
+    st->g_epoch = ctx->graph_epoch;
+    return ROM_OK;
+}
+
+static rom_status run_step_graph(rom_ctx *ctx, rom_state *st, const rom_opts *opts, const double *Fbar_d,
+                                 double *Pbar_d, double *Abar_d, void *info_d) {
+    if (o_needs_recapture(st, opts)) {
+        rom_status s = capture_step(ctx, st, opts);
+        if (s != ROM_OK) return s;
+    }
+    const int d2 = ctx->dim * ctx->dim;
+    const size_t B = (size_t)st->B;
+    CK(cudaMemcpyAsync(st->io_F, Fbar_d, B * d2 * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaGraphLaunch(st->gexec, ctx->stream));
+    CK(cudaMemcpyAsync(Pbar_d, st->io_P, B * d2 * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (Abar_d && opts->want_abar) CK(cudaMemcpyAsync(Abar_d, st->io_A, B * d2 * d2 * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (info_d) CK(cudaMemcpyAsync(info_d, st->io_info, B * sizeof(rom_step_info), cudaMemcpyDeviceToDevice, ctx->stream));
+    return ROM_OK;
+}
+
 extern "C" {
 
 rom_status rom_step_device(rom_ctx *ctx, rom_state *st, const rom_opts *opts, const double *Fbar_d, double *Pbar_d,
@@ -583,6 +711,10 @@ rom_status rom_step_device(rom_ctx *ctx, rom_state *st, const rom_opts *opts, co
     if (s != ROM_OK) return s;
     if (!Fbar_d || !Pbar_d || (opts->want_abar && !Abar_d)) return fail(ctx, ROM_E_ARG, "rom_step_device: null buffer");
     CK(cudaSetDevice(ctx->device));
+    if (ctx->graphs && !ctx->prof) {
+        if (opts->start == ROM_START_MLP && (s = ensure_feat(ctx, st->B)) != ROM_OK) return s;
+        return run_step_graph(ctx, st, opts, Fbar_d, Pbar_d, Abar_d, info_d);
+    }
     return run_step(ctx, st, opts, Fbar_d, Pbar_d, Abar_d, info_d);
 }
 
@@ -725,6 +857,12 @@ rom_status rom_debug_stiffness(rom_ctx *ctx, const rom_state *st, double *K) {
     CK(cudaSetDevice(ctx->device));
     CK(cudaStreamSynchronize(ctx->stream));
     CK(cudaMemcpy(K, st->bt.K, (size_t)st->B * st->n * st->n * 8, cudaMemcpyDeviceToHost));
+    return ROM_OK;
+}
+
+rom_status rom_use_graphs(rom_ctx *ctx, int enable) {
+    if (!ctx) return ROM_E_ARG;
+    ctx->graphs = enable != 0;
     return ROM_OK;
 }
 
