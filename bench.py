@@ -9,10 +9,13 @@ load-steps/s = instances x load steps / time.
 Default workload: 4096 macro points of the 2D plane-strain porous RVE family
 (64x64 Q4 parent mesh, POD n = 24, ECM m = 160), each with its own seeded
 geometry mu in [0.2, 0.35] and its own seeded 50-step load path (principal
-stretches 0.9-1.15, random axes and rotation); FP64 path.
+stretches 0.9-1.15, random axes and rotation).  Default precision: FP64
+residual, kinematics, return map, eigen log/exp and n x n solve with an FP32
+tangent and stiffness (--precision fp64 for the all-FP64 path); previous-step
+Newton predictor.  Each step is one CUDA-graph launch.
 
 usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                       [--workload c2|c3] [--precision fp64|fp32] [--start plain|prev]
+                       [--workload c2|c3] [--precision fp64|fp32|tf32|bf16] [--start plain|prev|mlp]
 """
 import argparse
 import json
@@ -39,8 +42,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=["c2", "c3"])
-    ap.add_argument("--precision", default=None, choices=["fp64", "fp32"])
-    ap.add_argument("--start", default="prev", choices=["plain", "prev"])
+    ap.add_argument("--precision", default=None, choices=["fp64", "fp32", "tf32", "bf16"])
+    ap.add_argument("--start", default="prev", choices=["plain", "prev", "mlp"])
+    ap.add_argument("--mlp", default=None, help="trained learned-start network (npz) for --start mlp")
+    ap.add_argument("--no-graphs", action="store_true", help="time the host-driven pass loop instead of graphs")
     ap.add_argument("--batch", type=int, default=None, help="override the batch size (testing)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -110,7 +115,9 @@ def load_workload(args, first=0, B=None):
 
 
 def solver_opts(args, rom):
-    prec = args.precision or ("fp64" if args.workload == "c2" else "fp32")
+    # default: FP64 residual, kinematics, return map, eigen log/exp and solve; FP32 tangent and
+    # stiffness (the converged Pbar is within 1e-7 of the FP64 oracle -- tests/test_gpu_parity_c2.py)
+    prec = args.precision or "fp32"
     tol_rel = 1e-10 if prec == "fp64" else 1e-9
     max_iter = 25 if prec == "fp64" else 50
     return prec, dict(tol_rel=tol_rel, tol_abs=rom["tol_abs"], max_iter=max_iter, max_ls=6, precision=prec,
@@ -129,7 +136,7 @@ def run_ours(args, rank, world):
     from paper_2307_16894_gb300 import workload
     B_total = args.batch or workload.WORKLOADS[args.workload]["B"]
     # weak scaling: every rank solves its own B instances (seeds offset by rank)
-    rom, mu, coef, paths = load_workload(args, first=rank * B_total, B=B_total)
+    rom, mu, coef, paths = workload.shard(args.workload, B_total, rank)
     B = len(coef)
     d = rom["d"]
     nsteps = paths.shape[1]
@@ -142,53 +149,71 @@ def run_ours(args, rank, world):
     ctx.load_basis(rom["G"])
     ctx.load_cubature(rom["w"], rom["phase"], rom["phases"], rom["omega"])
     ctx.set_geometry(rom["Gmu"], coef)
-    st = ctx.state_create(B)
+    if args.start == "mlp":
+        from paper_2307_16894_gb300 import warmstart
+        warmstart.load_into(ctx, args.mlp, B)
     opts = binding.make_opts(**kw)
     Fd = torch.from_numpy(np.ascontiguousarray(paths.transpose(1, 0, 2, 3))).to("cuda")    # [steps, B, d, d]
     Pd = torch.empty((B, d, d), dtype=torch.float64, device="cuda")
     Ad = torch.empty((B, d * d, d * d), dtype=torch.float64, device="cuda")
     Id = torch.empty((B, binding.INFO_DTYPE.itemsize), dtype=torch.uint8, device="cuda")
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > 129 MB L2
-    for k in range(W):
-        ctx.step_device(st, opts, Fd[k], Pd, Ad, Id)
-    torch.cuda.synchronize()
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-    clocks = Clocks(dev)
-    clocks.start()
-    ctx.profile(1)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    infos = []
-    torch.cuda.synchronize()
-    for k in range(K):
-        flush_l2(flush)
-        ev[k][0].record(stream)
-        ctx.step_device(st, opts, Fd[W + k], Pd, Ad, Id)
-        ev[k][1].record(stream)
-        infos.append(Id.clone())
-    torch.cuda.synchronize()
-    prof = ctx.profile_read()
-    ctx.profile(0)
-    clk = clocks.stop()
-    ms = sum(a.elapsed_time(b) for a, b in ev)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    info = np.frombuffer(torch.cat(infos).cpu().numpy().tobytes(), dtype=binding.INFO_DTYPE)
+
+    def timed_region(graphs, profile):
+        st = ctx.state_create(B)
+        ctx.use_graphs(graphs)
+        for k in range(W):
+            ctx.step_device(st, opts, Fd[k], Pd, Ad, Id)
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        clocks = Clocks(dev)
+        clocks.start()
+        if profile:
+            ctx.profile(1)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        infos = []
+        torch.cuda.synchronize()
+        for k in range(K):
+            flush_l2(flush)
+            ev[k][0].record(stream)
+            ctx.step_device(st, opts, Fd[W + k], Pd, Ad, Id)
+            ev[k][1].record(stream)
+            infos.append(Id.clone())
+        torch.cuda.synchronize()
+        prof = ctx.profile_read() if profile else None
+        if profile:
+            ctx.profile(0)
+        clk = clocks.stop()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        info = np.frombuffer(torch.cat(infos).cpu().numpy().tobytes(), dtype=binding.INFO_DTYPE)
+        st.close()
+        return ms, info, prof, clk
+
+    graphs = not args.no_graphs
+    ms, info, prof_main, clk = timed_region(graphs, profile=not graphs)
+    if graphs:
+        # kernel times and FLOPs of the same K steps through the per-launch path (events per launch)
+        ms_prof, _, prof, clk_prof = timed_region(False, profile=True)
+    else:
+        ms_prof, prof, clk_prof = ms, prof_main, clk
     n_ok = int((info["status"] == 0).sum())
     value = B * world * K / (ms / 1e3)
-    # dominant kernel roofline (FP64-bound assembly or constitutive)
     groups = {k: v for k, v in prof.items()}
     dom = max(groups, key=lambda g: groups[g][0])
     launches = sum(v[1] for v in groups.values())
     res = dict(value=value, ms=ms, n_ok=n_ok, n_total=len(info), iters_mean=float(info["iters"].mean()),
                evals_mean=float(info["evals"].mean()), prof=groups, dom=dom, launches=launches, clocks=clk,
-               prec=prec, B=B, W=W, K=K)
+               prec=prec, B=B, W=W, K=K, graphs=graphs, ms_profiled=ms_prof, clocks_profiled=clk_prof)
     # end-to-end through the public host-buffer call (H2D of Fbar, D2H of Pbar, Abar, info each step)
     if not args.no_e2e:
+        ctx.use_graphs(False)
         st2 = ctx.state_create(B)
         ctx.sync()
         for k in range(W):
@@ -203,7 +228,6 @@ def run_ours(args, rank, world):
                           h2d_bytes_per_step=B * d * d * 8,
                           d2h_bytes_per_step=B * (d * d + d ** 4) * 8 + B * binding.INFO_DTYPE.itemsize)
         st2.close()
-    st.close()
     ctx.close()
     return res
 
@@ -263,23 +287,34 @@ def main():
     if os.path.exists(PEAKS_FILE):
         peaks = json.load(open(PEAKS_FILE))
     ms_dom, ln_dom, fl_dom = r["prof"][r["dom"]]
+    share = ms_dom / sum(v[0] for v in r["prof"].values())
     if r["dom"] in ("assemble", "constitutive", "solve") and fl_dom > 0:
         achieved = fl_dom / (ms_dom / 1e3) / 1e12
-        roof = dict(kernel=r["dom"], bound="alu", achieved=achieved, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
-                    frac=achieved / FP64_PEAK_TFLOPS, traffic=None, peak_source="FP64 FMA pipe: 152 SM x 2 DFMA/clk x 2.07 GHz",
-                    share=ms_dom / sum(v[0] for v in r["prof"].values()))
+        if r["dom"] == "assemble" and r["prec"] in ("tf32", "bf16"):
+            # tensor-core contraction: measured BF16 dense peak (TF32 at half of it, the nominal ratio)
+            pk = peaks.get("bf16_tflops", 1900.0) * (1.0 if r["prec"] == "bf16" else 0.5)
+            roof = dict(kernel=r["dom"], bound="tensor", achieved=achieved, peak=pk, unit="TFLOP/s",
+                        frac=achieved / pk, traffic=None, share=share,
+                        peak_source="MEASURED_PEAKS.json bf16_tflops" + (" x 0.5 (tf32)" if r["prec"] == "tf32" else ""))
+        else:
+            roof = dict(kernel=r["dom"], bound="alu", achieved=achieved, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
+                        frac=achieved / FP64_PEAK_TFLOPS, traffic=None, share=share,
+                        peak_source="FP64 pipe: 152 SM x 2 DFMA/clk x 2 FLOP x 2.07 GHz")
     else:
         roof = dict(kernel=r["dom"], bound="alu", achieved=None, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s", frac=None,
-                    traffic=None)
+                    traffic=None, share=share)
     wl = {"c2": "2D porous RVE 64x64 Q4, n=24, m=160, B=4096, 50-step paths",
           "c3": "3D inclusion RVE 24^3 hex8, n=64, m=600, B=16384, 50-step paths"}[args.workload]
     line = dict(metric=metric, value=r["value"], unit=unit, n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=r["ms"] / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
-                dtype="f64" if r["prec"] == "fp64" else "f64+f32", data="synthetic",
+                dtype={"fp64": "f64", "fp32": "f64+f32", "tf32": "f64+tf32", "bf16": "f64+bf16"}[r["prec"]],
+                data="synthetic",
                 config=dict(workload=wl, B_per_gpu=r["B"], precision=r["prec"], start=args.start,
+                            step_driver="CUDA graph, device-driven Newton loop" if r["graphs"] else "host-driven passes",
                             l2="flushed between timed steps (256 MB write)", converged=r["n_ok"],
                             total=r["n_total"], newton_iters_mean=r["iters_mean"], evals_mean=r["evals_mean"]),
                 roofline=roof, clocks=r["clocks"], gpu_launches=int(r["launches"]),
+                profiled_ms_per_step=r["ms_profiled"] / args.steps,
                 kernels={k: dict(ms=v[0], launches=v[1], gflop=v[2] / 1e9) for k, v in r["prof"].items()})
     if "e2e" in r:
         line["e2e"] = r["e2e"]

@@ -45,8 +45,8 @@ CONFIGS = {
                train=[("stretch", 2001 + i, 25) for i in range(5)], mu_range=(0.2, 0.35)),
     # 3D 24^3 hex8, spherical elastic inclusion (stiffness ratio 10), n=64 (96 kept), m=600
     "c3": dict(d=3, N=24, n=96, n_use=64, m=600, L=20, map_seed=11, phases=[MATRIX, INCLUSION],
-               train=[("stretch", 3001 + i, 20) for i in range(5)], mu_range=(0.15, 0.35),
-               fft_pcg=True, tol_rel=1e-7, parallel=True),
+               train=[("stretch", 3001 + i, 20) for i in range(8)], mu_range=(0.15, 0.35),
+               fft_pcg=True, tol_rel=1e-9, parallel=True),
 }
 
 
@@ -73,7 +73,13 @@ def build(name, verbose=True, nthreads=None):
         snaps_w += out["w"]
         snaps_W += out["W"]
         train_info.append(info)
+    # keep the snapshots (outside the repo) so that the reduction can be redone without the FE solves
+    np.savez(os.path.join(ROOT, "oracle", "_build", "snapshots_%s.npz" % name), w=np.stack(snaps_w),
+             W=np.stack(snaps_W).astype(np.float32))
     n, L, m = cfg["n"], cfg["L"], cfg["m"]
+    n = min(n, reduction.snapshot_rank(mesh, snaps_w))
+    if verbose:
+        print("[%s] POD modes kept: %d" % (name, n), flush=True)
     Phi, lam_w, MV = reduction.displacement_pod(mesh, snaps_w, n)
     Bm, lam_W = reduction.stress_pod(mesh, snaps_W, L)
     gradPhi = reduction.basis_gradients(mesh, Phi)                     # [nq, d, d, n]

@@ -24,6 +24,14 @@ def pod_method_of_snapshots(S, M, n):
     return Phi, lam
 
 
+def snapshot_rank(mesh, snaps_w, rel=1e-14):
+    """number of POD eigenvalues above rel * the largest (numerical rank in V^p)"""
+    MV = mesh.mass_and_laplace()
+    S = np.stack(snaps_w, axis=1)
+    lam = np.linalg.eigvalsh(S.T @ (MV @ S))
+    return int(np.sum(lam > lam.max() * rel))
+
+
 def displacement_pod(mesh, snaps_w, n):
     """POD basis phi_1..phi_n of the fluctuation field, (phi_i, phi_j)_{V^p} = delta_ij
     (Eqs. pod_disp and the orthonormality relation after it)."""

@@ -270,12 +270,13 @@ class State:
         c._check(c.L.rom_debug_stiffness(c.h, self.h, _p(K)), "rom_debug_stiffness")
         return K
 
-    def export(self):
+    def export(self, history=True):
+        """(a [B, n], C^p^-1 [B, m, nc], xi [B, m]); history=False skips the last two (None)."""
         c = self.ctx
         nc = 4 if c.dim == 2 else 6
         a = np.empty((self.B, c.n))
-        cp = np.empty((self.B, c.m, nc))
-        xi = np.empty((self.B, c.m))
+        cp = np.empty((self.B, c.m, nc)) if history else None
+        xi = np.empty((self.B, c.m)) if history else None
         c._check(c.L.rom_state_export(c.h, self.h, _p(a), _p(cp), _p(xi)), "rom_state_export")
         return a, cp, xi
 

@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(128) k_constitutive(Model M, Batch Bt) {
     const PhaseD &ph = c_phases[M.phase[i]];
     MatState S;
     double tau[3][3], Finv[3][3], cpn[6], xin;
-    material_value<D>(F, cp, xi_n, ph, S, tau, Finv, cpn, &xin);
+    material_value<D, sizeof(TT) == sizeof(double)>(F, cp, xi_n, ph, S, tau, Finv, cpn, &xin);
     double P[3][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -288,6 +288,8 @@ __global__ void __launch_bounds__(256) k_assemble(Model M, Batch Bt, int CH, int
 #pragma unroll
         for (int y = 0; y < TM; ++y) acc[x][y] = TK(0);
     double racc = 0.0;
+    const int FG = blockDim.x / n;          // thread groups sharing the force rows
+    const int fg = tid / n, fj = tid - (tid / n) * n;
     const TK *At = reinterpret_cast<const TK *>(Bt.At);
 
     for (int c0 = 0; c0 < m; c0 += CH) {
@@ -321,9 +323,9 @@ __global__ void __launch_bounds__(256) k_assemble(Model M, Batch Bt, int CH, int
             for (int q = 0; q < D2; ++q) s += As[ii * D4 + c * D2 + q] * Gsrc[(ii * D2 + q) * np + k];
             Ys[e] = s;
         }
-        // force: r_j += sum_rows G[row][j] v[row]  (FP64, fixed order)
-        if (tid < n) {
-            for (int row = 0; row < ch * D2; ++row) racc += Gs[row * np + tid] * vs[row];
+        // force: r_j += sum_rows G[row][j] v[row]  (FP64; rows split over FG thread groups, fixed order)
+        if (fg < FG) {
+            for (int row = fg; row < ch * D2; row += FG) racc += Gs[row * np + fj] * vs[row];
         }
         __syncthreads();
         if (has_tile) {
@@ -361,7 +363,16 @@ __global__ void __launch_bounds__(256) k_assemble(Model M, Batch Bt, int CH, int
         for (int g = 0; g < NG; ++g) s += red[((size_t)g * np + a) * np + c];
         Kb[e] = double(s);
     }
-    if (tid < n) Bt.r[b * n + tid] = racc;
+    // reduce the force groups in a fixed order (reuse the buffer after the K gather)
+    __syncthreads();
+    double *fr = reinterpret_cast<double *>(smem);
+    if (fg < FG) fr[fg * n + fj] = racc;
+    __syncthreads();
+    if (tid < n) {
+        double s = 0.0;
+        for (int g = 0; g < FG; ++g) s += fr[g * n + tid];
+        Bt.r[b * n + tid] = s;
+    }
 }
 
 // ------------------------------------------------------------------------ solve
@@ -547,19 +558,31 @@ __global__ void __launch_bounds__(256) k_finalize(Model M, Batch Bt, StepOpts o,
     const int64_t b = blockIdx.x;
     const int n = M.n, m = M.m, tid = threadIdx.x;
     const Ctl c = Bt.ctl[b];
-    __shared__ double red[256];
+    __shared__ double wred[8][D2 + 1];
     __shared__ double PU[D2], AU[D4], Rb[D2], Ub[D2];
     __shared__ int ny_s;
-    // n_yield of the last evaluated state
-    int cnt = 0;
-    for (int i = tid; i < m; i += blockDim.x) cnt += Bt.pl[b * m + i];
-    red[tid] = cnt;
-    __syncthreads();
-    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
-        if (tid < off) red[tid] += red[tid + off];
-        __syncthreads();
+    const int lane = tid & 31, wid = tid >> 5;
+    // n_yield of the last evaluated state and the partial sums of Pbar_U (one pass, fixed order)
+    double ps[D2 + 1];
+#pragma unroll
+    for (int cc = 0; cc <= D2; ++cc) ps[cc] = 0.0;
+    for (int i = tid; i < m; i += blockDim.x) {
+        ps[D2] += Bt.pl[b * m + i];
+#pragma unroll
+        for (int cc = 0; cc < D2; ++cc) ps[cc] += Bt.wP[((size_t)b * D2 + cc) * m + i];
     }
-    if (tid == 0) ny_s = (int)red[0];
+#pragma unroll
+    for (int cc = 0; cc <= D2; ++cc)
+        for (int off = 16; off > 0; off >>= 1) ps[cc] += __shfl_xor_sync(0xffffffffu, ps[cc], off);
+    if (lane == 0)
+        for (int cc = 0; cc <= D2; ++cc) wred[wid][cc] = ps[cc];
+    __syncthreads();
+    if (tid <= D2) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wred[w][tid];
+        if (tid == D2) ny_s = (int)t;
+        else PU[tid] = t / M.omega;
+    }
     __syncthreads();
     struct Info { int32_t iters, evals, status, n_yield; double res0, res; };
     Info *info = reinterpret_cast<Info *>(info_v);
@@ -575,19 +598,7 @@ __global__ void __launch_bounds__(256) k_finalize(Model M, Batch Bt, StepOpts o,
             for (int e = tid; e < D4; e += blockDim.x) Abar[b * D4 + e] = NAN;
         return;
     }
-    // a10: Pbar_U = |Omega|^-1 sum_i wJ P_i
-    for (int cc = 0; cc < D2; ++cc) {
-        double s = 0.0;
-        for (int i = tid; i < m; i += blockDim.x) s += Bt.wP[((size_t)b * D2 + cc) * m + i];
-        __syncthreads();
-        red[tid] = s;
-        __syncthreads();
-        for (int off = blockDim.x / 2; off > 0; off >>= 1) {
-            if (tid < off) red[tid] += red[tid + off];
-            __syncthreads();
-        }
-        if (tid == 0) PU[cc] = red[0] / M.omega;
-    }
+    // a10: Pbar_U = |Omega|^-1 sum_i wJ P_i (reduced above)
     if (tid < D2) { Rb[tid] = Bt.Rbar[b * D2 + tid]; Ub[tid] = Bt.Ubar[b * D2 + tid]; }
     __syncthreads();
 
@@ -892,7 +903,11 @@ static int launch_finalize_t(const Model &M, Batch Bt, const StepOpts &o, double
                              cudaStream_t s) {
     constexpr int D2 = D * D, D4 = D2 * D2;
     if ((size_t)M.n * D2 > 1024) return -1;
-    const int CHF = 8;
+    // cubature points per chunk: small chunks keep the shared memory per CTA low (several CTAs per
+    // SM hide the latency of this short, barrier-bound kernel)
+    int CHF = 16;
+    while (CHF > 4 && ((size_t)M.n * D2 + D4 + (size_t)CHF * D2 + (size_t)CHF * D4 + (size_t)CHF * D2 * M.n) * 8 > 48 * 1024)
+        CHF /= 2;
     size_t sm = ((size_t)M.n * D2 + D4 + (size_t)CHF * D2 + (size_t)CHF * D4 + (size_t)CHF * D2 * M.n) * 8;
     const size_t sm2 = ((size_t)M.n * D2 + D4 + (size_t)CHF * D2 + (size_t)CHF * D4) * 8 +
                        ((size_t)M.n * M.n + (size_t)M.n * D2) * 8 + (size_t)M.n * 4 + 16;

@@ -107,7 +107,7 @@ struct MatState {
 // Value part.  F: 3x3 (plane strain: F[2][2] = 1, F[i][2] = F[2][i] = 0), cp: C^p^-1
 // (00, 01, 02, 11, 12, 22).  Outputs the state, the Kirchhoff stress tau (3x3), the
 // updated history cp_new, xi_new.  D = 2 uses the block structure.
-template <int D>
+template <int D, bool FP64_SLOPE = true>
 __device__ __forceinline__ void material_value(const double F[3][3], const double cp[6], double xi_n,
                                                const PhaseD &ph, MatState &S, double tau[3][3],
                                                double Finv[3][3], double cp_new[6], double *xi_new) {
@@ -174,15 +174,42 @@ __device__ __forceinline__ void material_value(const double F[3][3], const doubl
     S.beta = 1.0;
     S.hs = h0;
     if (S.plastic) {
-        double x = (S.q_tr - sy_n) / (3.0 * G + h0);
+        const double x0 = (S.q_tr - sy_n) / (3.0 * G + h0);
+        // power law: Newton in FP32 first (cheap pipe) to ~1e-7, then FP64 Newton steps; from an
+        // FP32-accurate start one FP64 step reaches FP64 precision (quadratic convergence), so the
+        // FP64 loop stops once a step is below 1e-6 |dg| (otherwise at 1e-15 |dg|, as from x0)
+        bool conv32 = false;
+        float xf = (float)x0;
+        if (ph.law == 1) {
+            const float qf = (float)S.q_tr, g3 = (float)(3.0 * G), xin = (float)xi_n;
+            const float s0f = (float)ph.s0, kf = (float)ph.k, pf = (float)ph.p;
+            for (int it = 0; it < 30; ++it) {
+                const float base = 1.f + kf * (xin + xf);
+                const float sy = s0f * expf(pf * logf(base));
+                const float hsf = sy * pf * kf / base;
+                const float step = (qf - g3 * xf - sy) / (g3 + hsf);
+                xf += step;
+                if (fabsf(step) <= 1e-6f * fabsf(xf)) { conv32 = isfinite(xf) && xf > 0.f; break; }
+            }
+        }
+        double x = conv32 ? (double)xf : x0;
         double hs = h0;
         for (int it = 0; it < 60; ++it) {
             const double sy = yield_stress(ph, xi_n + x, &hs);
             const double step = (S.q_tr - 3.0 * G * x - sy) / (3.0 * G + hs);
             x += step;
             if (fabs(step) <= 1e-15 * fabs(x)) break;
+            if (conv32 && fabs(step) <= 1e-6 * fabs(x)) break;
         }
-        yield_stress(ph, xi_n + x, &hs);
+        if (FP64_SLOPE) {
+            yield_stress(ph, xi_n + x, &hs);
+        } else if (ph.law == 1) {
+            // slope for the (FP32) tangent only
+            const float base = 1.f + (float)ph.k * ((float)xi_n + (float)x);
+            hs = (double)((float)ph.s0 * expf((float)ph.p * logf(base)) * (float)ph.p * (float)ph.k / base);
+        } else {
+            hs = ph.k;
+        }
         S.dg = x;
         S.hs = hs;
         S.beta = 1.0 - 3.0 * G * x / S.q_tr;
@@ -285,36 +312,46 @@ template <int D, typename T>
 __device__ __forceinline__ void tangent_setup(const MatState &S, const PhaseD &ph, const double F[3][3],
                                               const double cp[6], const double Finv[3][3],
                                               const double P[3][3], TangentData<T> &td) {
-    const double G = ph.G;
+    // all in the tangent precision T (FP64 path: double; mixed path: float on the FP32 pipe)
+    const T G = T(ph.G), beta = T(S.beta);
     // algorithmic moduli of the radial return in principal log strains
-    double cpl = 0.0;
-    if (S.plastic) cpl = 6.0 * G * G * (1.0 / (3.0 * G + S.hs) - S.dg / S.q_tr);
+    T cpl = T(0);
+    if (S.plastic) cpl = T(6) * G * G * (T(1) / (T(3) * G + T(S.hs)) - T(S.dg) / T(S.q_tr));
+    const T nh[3] = {T(S.nh[0]), T(S.nh[1]), T(S.nh[2])};
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
         for (int b = 0; b < 3; ++b)
-            td.c[a][b] = T(ph.Kb + 2.0 * G * S.beta * ((a == b ? 1.0 : 0.0) - 1.0 / 3.0) - cpl * S.nh[a] * S.nh[b]);
-    const double gb = G * S.beta;
-    td.th[0] = T(gb * log_divided_difference<double>(S.lam[0], S.lam[1]));
+            td.c[a][b] = T(ph.Kb) + T(2) * G * beta * ((a == b ? T(1) : T(0)) - T(1) / T(3)) - cpl * nh[a] * nh[b];
+    const T gb = G * beta;
+    const T l0 = T(S.lam[0]), l1 = T(S.lam[1]), l2 = T(S.lam[2]);
+    td.th[0] = gb * log_divided_difference<T>(l0, l1);
     if (D == 3) {
-        td.th[1] = T(gb * log_divided_difference<double>(S.lam[0], S.lam[2]));
-        td.th[2] = T(gb * log_divided_difference<double>(S.lam[1], S.lam[2]));
+        td.th[1] = gb * log_divided_difference<T>(l0, l2);
+        td.th[2] = gb * log_divided_difference<T>(l1, l2);
     } else {
         // plane strain: db'_a2 = 0 for in-plane directions, so the out-of-plane pairs never enter
         td.th[1] = T(0);
         td.th[2] = T(0);
     }
+    td.inv2l[0] = T(0.5) / l0;
+    td.inv2l[1] = T(0.5) / l1;
+    td.inv2l[2] = T(0.5) / l2;
+    T C[3][3], Ft[3][3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) td.inv2l[a] = T(0.5 / S.lam[a]);
-    const double C[3][3] = {{cp[0], cp[1], cp[2]}, {cp[1], cp[3], cp[4]}, {cp[2], cp[4], cp[5]}};
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Ft[i][j] = T(F[i][j]);
+    C[0][0] = T(cp[0]); C[0][1] = C[1][0] = T(cp[1]); C[0][2] = C[2][0] = T(cp[2]);
+    C[1][1] = T(cp[3]); C[1][2] = C[2][1] = T(cp[4]); C[2][2] = T(cp[5]);
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-            double s = 0.0;
+            T s = T(0);
 #pragma unroll
-            for (int k = 0; k < 3; ++k) s += C[i][k] * F[j][k];
-            td.Z[i][j] = T(s);
+            for (int k = 0; k < 3; ++k) s += C[i][k] * Ft[j][k];
+            td.Z[i][j] = s;
             td.N[i][j] = T(S.N[i][j]);
             td.Finv[i][j] = T(Finv[i][j]);
             td.P[i][j] = T(P[i][j]);

@@ -272,19 +272,28 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS));
 }
 
-// force f = sum_i G_i^T v_i in FP64 (same summation order as k_assemble), one CTA per instance
-__global__ void __launch_bounds__(128) k_force(Model M, Batch Bt) {
+// force f = sum_i G_i^T v_i in FP64, one CTA per instance; the rows (point, component) are
+// split over thread groups in a fixed pattern and the group sums added in a fixed order
+__global__ void __launch_bounds__(256) k_force(Model M, Batch Bt) {
+    __shared__ double fr[256];
     const int n_act = Bt.counts[0];
     const int p = blockIdx.x;
     if (p >= n_act) return;
     const int64_t b = Bt.list[p];
-    const int n = M.n, m = M.m, d2 = M.d2;
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        double acc = 0.0;
-        for (int i = 0; i < m; ++i)
-            for (int c = 0; c < d2; ++c)
-                acc += M.G_pt[((size_t)i * d2 + c) * n + j] * Bt.v[((size_t)b * d2 + c) * m + i];
-        Bt.r[b * n + j] = acc;
+    const int n = M.n, m = M.m, d2 = M.d2, tid = threadIdx.x;
+    const int FG = blockDim.x / n, g = tid / n, j = tid - (tid / n) * n;
+    double acc = 0.0;
+    if (g < FG)
+        for (int row = g; row < m * d2; row += FG) {
+            const int i = row / d2, c = row - i * d2;
+            acc += M.G_pt[(size_t)row * n + j] * Bt.v[((size_t)b * d2 + c) * m + i];
+        }
+    if (g < FG) fr[g * n + j] = acc;
+    __syncthreads();
+    if (tid < n) {
+        double s = 0.0;
+        for (int q = 0; q < FG; ++q) s += fr[q * n + tid];
+        Bt.r[b * n + tid] = s;
     }
 }
 
@@ -337,7 +346,7 @@ static int launch_tc_t(const Model &M, Batch Bt, const unsigned char *img, int *
     const int nch = (M.m + PC - 1) / PC;
     cudaFuncSetAttribute(k_assemble_tc<D, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_assemble_tc<D, FMT><<<(int)((Bt.B + 1) / 2), tc::THREADS, sm, s>>>(M, Bt, img, nch, err);
-    k_force<<<(int)Bt.B, 128, 0, s>>>(M, Bt);
+    k_force<<<(int)Bt.B, 256, 0, s>>>(M, Bt);
     return 0;
 }
 

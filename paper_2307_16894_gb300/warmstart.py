@@ -49,10 +49,10 @@ def collect(ctx, state, paths, opts, torch, max_steps=None):
     Xs, Ys, its = [], [], []
     for k in range(S):
         ctx.features(state, Fd[k], Xd)
-        a0 = state.export()[0]
+        a0 = state.export(history=False)[0]
         ctx.step_device(state, opts, Fd[k], Pd, Ad, Id)
         ctx.sync()
-        a1 = state.export()[0]
+        a1 = state.export(history=False)[0]
         info = np.frombuffer(Id.cpu().numpy().tobytes(), dtype=binding.INFO_DTYPE)
         ok = info["status"] == 0
         Xs.append(Xd.cpu().numpy()[ok])

@@ -58,3 +58,9 @@ def batch(name, B=None, steps=None, first=0):
         mu = np.stack([inputs.batch_mu(d, 1, w["seed0"] + first + b, *w["mu"])[0] for b in range(B)])
         paths = np.stack([inputs.stretch_path(d, w["seed0"] + first + b, steps, *w["stretch"]) for b in range(B)])
     return rom, mu, inputs.map_coefficients(d, mu), paths
+
+
+def shard(name, B_per_rank, rank, steps=None):
+    """Weak-scaling shard: rank r solves instances r*B .. (r+1)*B - 1 of the workload's seeded
+    sequence (instances are independent, so no data exchange is needed)."""
+    return batch(name, B=B_per_rank, steps=steps, first=rank * B_per_rank)

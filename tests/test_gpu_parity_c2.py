@@ -62,3 +62,21 @@ def test_c2_full_batch_sampled():
     a, cp, xi = g.st.export()
     assert rel(a[sample], o.q) <= 1e-11
     g.close()
+
+
+def test_c2_full_batch_sampled_fp32():
+    """B = 4096, FP32 tangent and stiffness (FP64 residual, return map and solve): converged
+    Pbar within 1e-7 of the FP64 oracle on sampled instances."""
+    rom, mu, coef, paths = workload.batch("c2")
+    B = len(coef)
+    sample = np.array([5, 777, 2500, B - 2])
+    g = GpuRun(rom, coef)
+    o = OracleRun(rom, coef[sample])
+    for k in range(6):
+        P, A, info = g.step(paths[:, k], tol_rel=1e-9, tol_abs=rom["tol_abs"], max_iter=50, max_ls=6,
+                            precision="fp32", start="prev")
+        ref = o.step(paths[sample, k], tol_rel=1e-10, tol_abs=rom["tol_abs"], max_iter=25, max_ls=6, start="prev")
+        assert (info["status"] == 0).mean() >= 0.99
+        assert rel(P[sample], ref["Pbar"]) <= 1e-7
+        assert rel(A[sample], ref["Abar"]) <= 1e-4
+    g.close()
