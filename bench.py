@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5"])
     ap.add_argument("--precision", default=None, choices=["fp64", "fp32", "tf32", "bf16"])
     ap.add_argument("--start", default="prev", choices=["plain", "prev", "mlp"])
     ap.add_argument("--mlp", default=None, help="trained learned-start network (npz) for --start mlp")
@@ -232,6 +232,36 @@ def run_ours(args, rank, world):
     return res
 
 
+def run_serving(args, rank, world):
+    """Ragged batch of 2D and 3D models of different n and m served together (rom_serve)."""
+    import torch
+    from paper_2307_16894_gb300 import serving
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    B_total = args.batch or 65536
+    W, K = args.warmup, args.steps
+    groups = serving.make_groups(B_total, share_2d=0.75, steps=W + K, seed0=40_000 + rank * B_total)
+    srv = serving.Server(groups, precision=args.precision or "fp32", start=args.start)
+    for k in range(W):
+        srv.step(k)
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", 0)))
+    clocks.start()
+    walls, lats, its, ok = [], [], [], 0
+    for k in range(K):
+        wall, lat, info = srv.step(W + k)
+        walls.append(wall)
+        lats.append(lat)
+        its.append(info["iters"].mean())
+        ok += int((info["status"] == 0).sum())
+    clk = clocks.stop()
+    ms = float(np.sum(walls))
+    lat = np.concatenate(lats)
+    desc = ["%s:B=%d,n=%d,m=%d,wave=%d" % (g["name"], g["B"], g["rom"]["n"], g["rom"]["m"], g["wave"]) for g in groups]
+    srv.close()
+    return dict(value=B_total * world * K / (ms / 1e3), ms=ms, lat_p50=float(np.percentile(lat, 50)),
+                lat_p99=float(np.percentile(lat, 99)), iters=float(np.mean(its)), ok=ok, total=B_total * K,
+                groups=desc, clocks=clk)
+
+
 def cpu_baseline(args, n_inst=None, n_steps=None, budget_s=20.0):
     """The FP64 oracle (as it stands) on the host cores, on a bounded sample of the workload:
     the first n_inst instances over the first n_steps load steps."""
@@ -279,6 +309,18 @@ def main():
                     config=dict(workload=args.workload), cpu_baseline=cb,
                     e2e=dict(value=cb["value"], unit=unit, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
         print(json.dumps(line))
+        return
+    if args.workload == "c5":
+        r = run_serving(args, rank, world)
+        if rank == 0:
+            line = dict(metric=metric, value=r["value"], unit=unit, n_gpus=world, steps=args.steps,
+                        warmup=args.warmup, ms_per_step=r["ms"] / args.steps, higher_is_better=True,
+                        scaling="weak", vs_baseline=None, dtype="f64+f32", data="synthetic",
+                        config=dict(workload="ragged: 2D n 16/24/32 m 100/150/200 + 3D n 48/64/96 m 400/650/900",
+                                    groups=r["groups"], converged=r["ok"], total=r["total"],
+                                    newton_iters_mean=r["iters"], l2="working set >> L2"),
+                        latency_ms=dict(p50=r["lat_p50"], p99=r["lat_p99"]), roofline=None, clocks=r["clocks"])
+            print(json.dumps(line))
         return
     r = run_ours(args, rank, world)
     if rank != 0:

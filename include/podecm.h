@@ -172,6 +172,24 @@ const char *rom_last_error(const rom_ctx *ctx);
  * 2 n^3/3 + 2 n^2 -- per active instance and launch).  Any pointer may be NULL. */
 rom_status rom_profile(rom_ctx *ctx, int enable);
 
+/* Device bytes of a state of B instances (history and per-step work arrays) -- the
+ * admission budget of a serving layer. */
+rom_status rom_state_bytes(const rom_ctx *ctx, int64_t B, int64_t *bytes);
+
+/* Autotune the CUDA-core stiffness assembly (FP64/FP32 modes): times the tile edges
+ * 2/4/8 x points-per-chunk 8/16/32/64 on the state's current tangents (call after at
+ * least one step) and keeps the fastest for this context.  Outputs may be NULL. */
+rom_status rom_autotune(rom_ctx *ctx, rom_state *st, const rom_opts *opts, int *tile, int *chunk, float *ms);
+
+/* Ragged serving: one load step for G groups (each its own model/context, state, options
+ * and device I/O buffers) issued together; each group runs as one graph launch on its
+ * context's stream, so groups of different basis size n and cubature size m overlap on the
+ * GPU.  group_ms[g] (may be NULL) = time from the common start to the end of group g.
+ * Abar_d / info_d may be NULL.  Blocking. */
+rom_status rom_serve(int G, rom_ctx *const *ctxs, rom_state *const *sts, const rom_opts *opts,
+                     const double *const *Fbar_d, double *const *Pbar_d, double *const *Abar_d,
+                     rom_step_info *const *info_d, float *group_ms);
+
 /* Graph mode: with enable = 1, rom_step_device runs each load step as one CUDA-graph launch
  * whose Newton passes execute inside a conditional WHILE node decided on the device (no
  * host synchronisation per pass).  The graph is captured on the first step with given
@@ -190,15 +208,19 @@ rom_status rom_profile_read(rom_ctx *ctx, int kernel, double *ms, int64_t *launc
  * Learned Newton start (not in the paper, whose Newton start is unspecified).
  * A multilayer perceptron with `depth` hidden layers of `width` units (exact-erf
  * GELU) maps the features of a step
- *     x = [Ubar_k - Ubar_{k-1} (d*d), mu (n_par), a_n (n), mean_i xi_i, max_i xi_i]
- * (n_in = d*d + n_par + n + 2; Ubar = stretch of the polar split of Fbar) to the
- * predicted increment da of the reduced coordinates (n_out = n).  Inference uses
- * BF16 weights with FP32 accumulation; training keeps an FP32 master copy updated by
- * Adam (beta = 0.9, 0.999, eps = 1e-8) on the mean squared error of the standardised
- * targets.  With opts->start = ROM_START_MLP, rom_step evaluates the residual at
- * a_n + da_MLP and at the previous-step predictor a_n + (a_n - a_{n-1}) and starts
- * Newton from the smaller one (one extra residual evaluation, counted in evals); the
- * converged answer does not depend on the start.
+ *     x = [Ubar_k - Ubar_{k-1} (d*d), mu (n_par), a_n (n), a_n - a_{n-1} (n),
+ *          mean_i xi_i, max_i xi_i]
+ * (n_in = d*d + n_par + 2n + 2; Ubar = stretch of the polar split of Fbar) to the
+ * correction of the previous-step increment, da_k - da_{k-1} (n_out = n); the learned
+ * start is a_n + da_{k-1} + correction.  Inference uses BF16 weights with FP32
+ * accumulation; training keeps an FP32 master copy updated by Adam (beta = 0.9, 0.999,
+ * eps = 1e-8) on the mean squared error of the standardised targets.  With
+ * opts->start = ROM_START_MLP, rom_step evaluates the residual at the learned start and
+ * at the previous-step predictor a_n + (a_n - a_{n-1}) and starts Newton from the
+ * smaller one (one extra residual evaluation, counted in evals); the converged answer
+ * does not depend on the start.  In this mode the convergence tolerance is relative to
+ * the residual of the previous-step predictor (the fallback) whichever start is taken,
+ * so both starts are held to the same absolute residual.
  *
  * rom_mlp_init: allocate an MLP (random parameters are set by rom_mlp_params);
  *   max_rows = largest batch of rows of any later train/grad/predict call.

@@ -25,7 +25,8 @@ EXPORTED = ["rom_create", "rom_destroy", "rom_load_basis", "rom_load_cubature", 
             "rom_state_create", "rom_state_destroy", "rom_state_export", "rom_state_import", "rom_step",
             "rom_step_device", "rom_sync", "rom_last_error", "rom_profile", "rom_profile_read",
             "rom_step_noalloc", "rom_mlp_init", "rom_mlp_nparams", "rom_mlp_params", "rom_mlp_norm",
-            "rom_mlp_train_step", "rom_mlp_loss_grad", "rom_mlp_predict", "rom_features", "rom_debug_stiffness", "rom_use_graphs"]
+            "rom_mlp_train_step", "rom_mlp_loss_grad", "rom_mlp_predict", "rom_features", "rom_debug_stiffness", "rom_use_graphs",
+            "rom_state_bytes", "rom_autotune", "rom_serve"]
 
 KERNEL_GROUPS = ["start", "constitutive", "assemble", "solve", "finalize", "bookkeeping", "learned_start"]
 
@@ -91,6 +92,9 @@ def lib(path=None):
     L.rom_features.argtypes = [p, p, p, p]
     L.rom_debug_stiffness.argtypes = [p, p, p]
     L.rom_use_graphs.argtypes = [p, i]
+    L.rom_state_bytes.argtypes = [p, i64, p]
+    L.rom_autotune.argtypes = [p, p, p, p, p, p]
+    L.rom_serve.argtypes = [i, p, p, p, p, p, p, p, p]
     L.rom_last_error.argtypes = [p]
     L.rom_last_error.restype = ctypes.c_char_p
     for f in EXPORTED:
@@ -205,6 +209,17 @@ class Context:
 
     def sync(self):
         self._check(self.L.rom_sync(self.h), "rom_sync")
+
+    def state_bytes(self, B):
+        v = ctypes.c_int64()
+        self._check(self.L.rom_state_bytes(self.h, int(B), ctypes.byref(v)), "rom_state_bytes")
+        return v.value
+
+    def autotune(self, state, opts):
+        t, c, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+        self._check(self.L.rom_autotune(self.h, state.h, ctypes.byref(opts), ctypes.byref(t), ctypes.byref(c),
+                                        ctypes.byref(ms)), "rom_autotune")
+        return t.value, c.value, ms.value
 
     def use_graphs(self, enable=True):
         self._check(self.L.rom_use_graphs(self.h, int(enable)), "rom_use_graphs")
@@ -321,3 +336,18 @@ def step_noalloc(dim, G_d, w_d, phase_d, Gmu_d, phases, omega, mu_d, a_d, da_pre
                             ctypes.c_void_p(stream) if stream else None, buf, 512)
     if st != ROM_OK:
         raise RomError("rom_step_noalloc failed with status %d: %s" % (st, buf.value.decode()))
+
+
+def serve(ctxs, states, opts, F, P, A=None, I=None):
+    """rom_serve: one load step for G groups (torch device buffers); returns group_ms [G]."""
+    L = lib()
+    G = len(ctxs)
+    VP = ctypes.c_void_p * G
+    o = (RomOpts * G)(*opts)
+    ms = (ctypes.c_float * G)()
+    arr = lambda xs: VP(*[x.data_ptr() for x in xs]) if xs is not None else None
+    st = L.rom_serve(G, VP(*[c.h.value for c in ctxs]), VP(*[s.h.value for s in states]), o, arr(F), arr(P),
+                     arr(A), arr(I), ms)
+    if st != ROM_OK:
+        raise RomError("rom_serve failed with status %d: %s" % (st, L.rom_last_error(ctxs[0].h).decode()))
+    return np.array(ms[:])

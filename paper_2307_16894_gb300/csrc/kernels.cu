@@ -492,8 +492,10 @@ __global__ void __launch_bounds__(32) k_solve(Model M, Batch Bt, StepOpts o, int
             for (int j = lane; j < n; j += 32) qa[j] = qt[j];
             accepted = true;
         } else {
+            // the tolerance stays relative to the previous-step predictor's residual, so that the
+            // learned start is held to the same absolute residual as the fallback
             c.r0 = rm;
-            c.tol = fmax(o.tol_rel * rm, o.tol_abs);
+            c.tol = fmax(o.tol_rel * rn, o.tol_abs);
             c.rn_acc = rm;
             if (rm <= c.tol || o.max_iter == 0) {
                 // the stored per-point data belong to the other candidate: re-evaluate here
@@ -785,6 +787,16 @@ void launch_graph_advance(Batch Bt, const int32_t *list_next, cudaGraphCondition
 
 void launch_reset_pass(Batch Bt, cudaStream_t s) { k_reset_pass<<<1, 1, 0, s>>>(Bt.counts); }
 
+__global__ void k_iota_list(Batch Bt) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < Bt.B) Bt.list[b] = (int32_t)b;
+    if (b == 0) { Bt.counts[0] = (int32_t)Bt.B; Bt.counts[1] = 0; }
+}
+
+void launch_all_active(Batch Bt, cudaStream_t s) {
+    k_iota_list<<<(int)((Bt.B + 255) / 256), 256, 0, s>>>(Bt);
+}
+
 // compacted list of the converged instances (status OK) into list / counts[0]
 __global__ void k_list_converged(Batch Bt) {
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -800,11 +812,11 @@ void launch_list_converged(Batch Bt, cudaStream_t s) {
     k_list_converged<<<(int)((Bt.B + 255) / 256), 256, 0, s>>>(Bt);
 }
 
-// learned start: q_trial = q_acc = q_n + prediction
+// learned start: q_trial = q_acc = q_n + (q_n - q_{n-1}) + predicted correction
 __global__ void k_add_pred(Batch Bt, int n, const double *__restrict__ pred) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= Bt.B * n) return;
-    const double q = Bt.q_n[e] + pred[e];
+    const double q = Bt.q_n[e] + Bt.dq_prev[e] + pred[e];
     Bt.q_trial[e] = q;
     Bt.q_acc[e] = q;
 }
@@ -832,6 +844,10 @@ static int launch_assemble(const Model &M, Batch Bt, const StepOpts &o, cudaStre
     };
     int CH = 64;
     while (CH > 1 && smem_for(CH) > 96 * 1024) CH /= 2;
+    if (o.asm_ch > 0) {
+        if (smem_for(o.asm_ch) > 200 * 1024) return -1;
+        CH = o.asm_ch;
+    }
     const size_t sm = smem_for(CH);
     if (o.precision == 0) {
         cudaFuncSetAttribute(k_assemble<D, double, TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -856,6 +872,13 @@ static int launch_kernels_t(int which, const Model &M, Batch Bt, const StepOpts 
         return 0;
     }
     if (which == 2) {
+        if (o.asm_tm > 0) {
+            const int NT = (M.n + o.asm_tm - 1) / o.asm_tm;
+            if (NT * (NT + 1) / 2 > 256) return -1;
+            return o.asm_tm == 2 ? launch_assemble<D, 2>(M, Bt, o, s)
+                 : o.asm_tm == 4 ? launch_assemble<D, 4>(M, Bt, o, s)
+                 : o.asm_tm == 8 ? launch_assemble<D, 8>(M, Bt, o, s) : -1;
+        }
         // tile edge TM: the smallest of 2, 4, 8 for which one upper-triangular tile per thread fits 256 threads
         const int tms[3] = {2, 4, 8};
         for (int q = 0; q < 3; ++q) {

@@ -67,6 +67,7 @@ struct MlpDev {
 struct StepOpts {
     double tol_rel, tol_abs;
     int max_iter, max_ls, precision, start, polar, want_abar;
+    int asm_tm = 0, asm_ch = 0;   // assembly tile edge / points per chunk (0 = heuristic)
 };
 
 }  // namespace podecm

@@ -1,5 +1,6 @@
-// Learned Newton start: a small MLP that predicts the increment da of the reduced
-// coordinates of one load step from (dUbar, mu, a_n, mean xi, max xi).  Not part of
+// Learned Newton start: a small MLP that predicts the correction of the previous-step
+// increment of the reduced coordinates, da_k - da_{k-1}, from (dUbar, mu, a_n, da_{k-1},
+// mean xi, max xi).  Not part of
 // the paper (which is silent on the Newton predictor); the converged Newton answer
 // does not depend on it.  Hand-written kernels for inference (BF16 weights, FP32
 // accumulation, exact-erf GELU) and for training (forward, backward, MSE loss,
@@ -285,7 +286,7 @@ void mlp_predict(MlpDev &M, const float *X, int64_t N, int bf16, double *out, cu
 }
 
 // ---------------------------------------------------------------- features
-// x = [Ubar_k - Ubar_{k-1} (d2), mu (n_par), a_n (n), mean xi, max xi] per instance.
+// x = [Ubar_k - Ubar_{k-1} (d2), mu (n_par), a_n (n), a_n - a_{n-1} (n), mean xi, max xi] per instance.
 // Ubar_k is the stretch of the polar split of Fbar (computed by k_start); U_prev is
 // the stretch of the last converged step of the instance.
 __global__ void k_features(Model M, Batch Bt, const double *__restrict__ U_prev, float *__restrict__ X, int n_in) {
@@ -308,10 +309,13 @@ __global__ void k_features(Model M, Batch Bt, const double *__restrict__ U_prev,
     float *x = X + b * n_in;
     for (int c = tid; c < d2; c += blockDim.x) x[c] = (float)(Bt.Ubar[b * d2 + c] - U_prev[b * d2 + c]);
     for (int k = tid; k < M.n_par; k += blockDim.x) x[d2 + k] = (float)Bt.mu[b * M.n_par + k];
-    for (int j = tid; j < n; j += blockDim.x) x[d2 + M.n_par + j] = (float)Bt.q_n[b * n + j];
+    for (int j = tid; j < n; j += blockDim.x) {
+        x[d2 + M.n_par + j] = (float)Bt.q_n[b * n + j];
+        x[d2 + M.n_par + n + j] = (float)Bt.dq_prev[b * n + j];
+    }
     if (tid == 0) {
-        x[d2 + M.n_par + n] = (float)(s_sum[0] / m);
-        x[d2 + M.n_par + n + 1] = (float)s_max[0];
+        x[d2 + M.n_par + 2 * n] = (float)(s_sum[0] / m);
+        x[d2 + M.n_par + 2 * n + 1] = (float)s_max[0];
     }
 }
 

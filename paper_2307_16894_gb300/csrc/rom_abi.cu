@@ -39,6 +39,7 @@ void launch_list_converged(Batch Bt, cudaStream_t s);
 void launch_graph_advance(Batch Bt, const int32_t *list_next, cudaGraphConditionalHandle h, int max_pass,
                           cudaStream_t s);
 void launch_reset_pass(Batch Bt, cudaStream_t s);
+void launch_all_active(Batch Bt, cudaStream_t s);
 }  // namespace podecm
 
 using namespace podecm;
@@ -80,6 +81,7 @@ struct rom_ctx {
     MlpDev mlp{};
     bool graphs = false;            // rom_step_device through a captured step graph
     int64_t graph_epoch = 0;        // bumped when buffers captured by graphs are reallocated
+    int asm_tm = 0, asm_ch = 0;     // autotuned assembly tiles (0 = heuristic)
     float *d_feat = nullptr;        // [B][n_in]
     double *d_pred = nullptr;       // [B][n]
     int64_t feat_B = 0;
@@ -450,8 +452,8 @@ static rom_status check_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts) 
         return fail(ctx, ROM_E_ARG, "rom_step: bad options");
     if (opts->start == ROM_START_MLP && (!ctx->has_mlp || !ctx->mlp_norm))
         return fail(ctx, ROM_E_STATE, "rom_step: learned start requested but no MLP (rom_mlp_init, rom_mlp_params, rom_mlp_norm)");
-    if (opts->start == ROM_START_MLP && ctx->mlp.n_in != ctx->dim * ctx->dim + ctx->n_par + ctx->n + 2)
-        return fail(ctx, ROM_E_STATE, "rom_step: MLP input size %d does not match d^2 + n_par + n + 2", ctx->mlp.n_in);
+    if (opts->start == ROM_START_MLP && ctx->mlp.n_in != ctx->dim * ctx->dim + ctx->n_par + 2 * ctx->n + 2)
+        return fail(ctx, ROM_E_STATE, "rom_step: MLP input size %d does not match d^2 + n_par + 2n + 2", ctx->mlp.n_in);
     if (opts->precision >= ROM_PREC_TF32 && !ctx->tc_img[0])
         return fail(ctx, ROM_E_ARG, "rom_step: tensor-core precision needs n <= 64 (n = %d)", ctx->n);
     return ROM_OK;
@@ -524,6 +526,7 @@ static rom_status run_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts, co
     StepOpts o;
     o.tol_rel = opts->tol_rel; o.tol_abs = opts->tol_abs; o.max_iter = opts->max_iter; o.max_ls = opts->max_ls;
     o.precision = opts->precision; o.start = opts->start; o.polar = opts->polar_split; o.want_abar = opts->want_abar;
+    o.asm_tm = ctx->asm_tm; o.asm_ch = ctx->asm_ch;
     const Model M = make_model(ctx);
     Batch bt = st->bt;
     bt.mu = ctx->mu;
@@ -609,6 +612,7 @@ static rom_status capture_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts
     StepOpts o;
     o.tol_rel = opts->tol_rel; o.tol_abs = opts->tol_abs; o.max_iter = opts->max_iter; o.max_ls = opts->max_ls;
     o.precision = opts->precision; o.start = opts->start; o.polar = opts->polar_split; o.want_abar = opts->want_abar;
+    o.asm_tm = ctx->asm_tm; o.asm_ch = ctx->asm_ch;
     const Model M = make_model(ctx);
     Batch bt = st->bt;
     bt.mu = ctx->mu;
@@ -847,7 +851,7 @@ rom_status rom_features(rom_ctx *ctx, rom_state *st, const double *Fbar_d, float
     Batch bt = st->bt;
     bt.mu = ctx->mu;
     launch_start(M, bt, Fbar_d, o, nullptr, ctx->stream);
-    launch_features(M, bt, bt.U_prev, X_d, ctx->dim * ctx->dim + ctx->n_par + ctx->n + 2, ctx->stream);
+    launch_features(M, bt, bt.U_prev, X_d, ctx->dim * ctx->dim + ctx->n_par + 2 * ctx->n + 2, ctx->stream);
     CK(cudaGetLastError());
     return ROM_OK;
 }
@@ -858,6 +862,99 @@ rom_status rom_debug_stiffness(rom_ctx *ctx, const rom_state *st, double *K) {
     CK(cudaStreamSynchronize(ctx->stream));
     CK(cudaMemcpy(K, st->bt.K, (size_t)st->B * st->n * st->n * 8, cudaMemcpyDeviceToHost));
     return ROM_OK;
+}
+
+rom_status rom_state_bytes(const rom_ctx *ctx, int64_t B, int64_t *bytes) {
+    if (!ctx || !bytes || B < 1) return ROM_E_ARG;
+    const int64_t d2 = ctx->dim * ctx->dim, n = ctx->n, m = ctx->m, ncp = ctx->dim == 2 ? 4 : 6;
+    const int64_t per = n * 8 * 5 + (int64_t)sizeof(Ctl) + 8 + ncp * m * 8 * 2 + m * 8 * 2 + d2 * m * 8 * 2 +
+                        d2 * d2 * m * 8 + m + n * n * 8 + d2 * 8 * 4 + d2 * d2 * 8 + 32;
+    *bytes = per * B + 64;
+    return ROM_OK;
+}
+
+rom_status rom_autotune(rom_ctx *ctx, rom_state *st, const rom_opts *opts, int *tile, int *chunk, float *ms) {
+    rom_status s = check_step(ctx, st, opts);
+    if (s != ROM_OK) return s;
+    if (opts->precision >= ROM_PREC_TF32) {   // the tensor-core tiles are fixed
+        if (tile) *tile = 0;
+        if (chunk) *chunk = 0;
+        return ROM_OK;
+    }
+    CK(cudaSetDevice(ctx->device));
+    StepOpts o{};
+    o.precision = opts->precision;
+    const Model M = make_model(ctx);
+    Batch bt = st->bt;
+    bt.mu = ctx->mu;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bt_tm = 0, bt_ch = 0;
+    const int tms[3] = {2, 4, 8}, chs[4] = {8, 16, 32, 64};
+    for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 4; ++c) {
+            o.asm_tm = tms[a];
+            o.asm_ch = chs[c];
+            launch_all_active(bt, ctx->stream);
+            if (launch_kernel(2, M, bt, o, st->list2, ctx->stream)) { cudaGetLastError(); continue; }
+            float tot = 0.f;
+            for (int r = 0; r < 3; ++r) {
+                cudaEventRecord(e0, ctx->stream);
+                launch_kernel(2, M, bt, o, st->list2, ctx->stream);
+                cudaEventRecord(e1, ctx->stream);
+                cudaEventSynchronize(e1);
+                float t = 0.f;
+                cudaEventElapsedTime(&t, e0, e1);
+                tot += t;
+            }
+            if (cudaGetLastError() != cudaSuccess) continue;
+            if (tot / 3 < best) { best = tot / 3; bt_tm = tms[a]; bt_ch = chs[c]; }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!bt_tm) return fail(ctx, ROM_E_ARG, "rom_autotune: no valid assembly configuration");
+    ctx->asm_tm = bt_tm;
+    ctx->asm_ch = bt_ch;
+    ++ctx->graph_epoch;
+    if (tile) *tile = bt_tm;
+    if (chunk) *chunk = bt_ch;
+    if (ms) *ms = best;
+    return ROM_OK;
+}
+
+rom_status rom_serve(int G, rom_ctx *const *ctxs, rom_state *const *sts, const rom_opts *opts,
+                     const double *const *Fbar_d, double *const *Pbar_d, double *const *Abar_d,
+                     rom_step_info *const *info_d, float *group_ms) {
+    if (G < 1 || !ctxs || !sts || !opts || !Fbar_d || !Pbar_d) return ROM_E_ARG;
+    rom_ctx *ctx = ctxs[0];
+    for (int g = 0; g < G; ++g)
+        if (!ctxs[g] || !sts[g] || ctxs[g]->device != ctx->device) return ROM_E_ARG;
+    CK(cudaSetDevice(ctx->device));
+    std::vector<cudaEvent_t> ev(G + 1);
+    for (auto &e : ev) CK(cudaEventCreate(&e));
+    CK(cudaEventRecord(ev[G], ctx->stream));
+    rom_status s = ROM_OK;
+    for (int g = 0; g < G && s == ROM_OK; ++g) {
+        rom_ctx *c = ctxs[g];
+        if (c->stream != ctx->stream) CK(cudaStreamWaitEvent(c->stream, ev[G], 0));
+        const bool gr = c->graphs;
+        c->graphs = true;
+        s = rom_step_device(c, sts[g], &opts[g], Fbar_d[g], Pbar_d[g], Abar_d ? Abar_d[g] : nullptr,
+                            info_d ? info_d[g] : nullptr);
+        c->graphs = gr;
+        if (s == ROM_OK) CK(cudaEventRecord(ev[g], c->stream));
+        else ctx->err = c->err;
+    }
+    if (s == ROM_OK) {
+        for (int g = 0; g < G; ++g) {
+            CK(cudaEventSynchronize(ev[g]));
+            if (group_ms) CK(cudaEventElapsedTime(&group_ms[g], ev[G], ev[g]));
+        }
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    return s;
 }
 
 rom_status rom_use_graphs(rom_ctx *ctx, int enable) {

@@ -3,8 +3,8 @@ training with the library's MLP kernels, and persistence.
 
 Every arithmetic step (solve, features, forward/backward, Adam) runs in
 libpodecm.so; this module only moves batches between host and device.
-Features of a step: [Ubar_k - Ubar_{k-1}, mu, a_n, mean xi, max xi]; target:
-the converged increment a_{k} - a_{k-1}.
+Features of a step: [Ubar_k - Ubar_{k-1}, mu, a_n, a_n - a_{n-1}, mean xi, max xi];
+target: the correction of the previous-step increment, (a_k - a_n) - (a_n - a_{n-1}).
 
 The context passed to collect() and train() must have been created on torch's
 current stream (binding.Context(d, dev, torch.cuda.current_stream().cuda_stream))
@@ -18,7 +18,7 @@ WIDTH, DEPTH = 128, 4      # 4 hidden layers of width 128
 
 
 def n_features(d, n_par, n):
-    return d * d + n_par + n + 2
+    return d * d + n_par + 2 * n + 2
 
 
 def init_params(n_in, width, depth, n_out, seed):
@@ -55,8 +55,11 @@ def collect(ctx, state, paths, opts, torch, max_steps=None):
         a1 = state.export(history=False)[0]
         info = np.frombuffer(Id.cpu().numpy().tobytes(), dtype=binding.INFO_DTYPE)
         ok = info["status"] == 0
-        Xs.append(Xd.cpu().numpy()[ok])
-        Ys.append((a1 - a0)[ok].astype(np.float32))
+        X = Xd.cpu().numpy()
+        n = ctx.n
+        da_prev = X[:, d * d + ctx.n_par + n:d * d + ctx.n_par + 2 * n].astype(np.float64)
+        Xs.append(X[ok])
+        Ys.append(((a1 - a0) - da_prev)[ok].astype(np.float32))
         its.append(info["iters"][ok])
     return np.concatenate(Xs), np.concatenate(Ys), np.concatenate(its)
 
