@@ -149,7 +149,7 @@ def pack(mesh, cfg, modes, Gq, gradPhi, sel, wsel, err, n_use):
 # ragged serving family: basis truncations of the 2D and 3D models with their own ECM rules
 VARIANTS = {
     "r2_n16_m100": ("c2", 16, 100), "r2_n24_m150": ("c2", 24, 150), "r2_n32_m200": ("c2", 32, 200),
-    "r3_n48_m400": ("c3", 48, 400), "r3_n64_m650": ("c3", 64, 650), "r3_n96_m900": ("c3", 96, 900),
+    "r3_n48_m400": ("c3", 48, 400), "r3_n64_m650": ("c3", 64, 650), "r3_n95_m900": ("c3", 95, 900),
 }
 
 

@@ -85,6 +85,149 @@ __device__ __forceinline__ void jacobi3(double a[3][3], double V[3][3]) {
     }
 }
 
+// single-precision Jacobi sweeps (rotation angles only need ~1e-7 accuracy here)
+__device__ __forceinline__ void jacobi3_f32(float a[3][3], float V[3][3]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) V[i][j] = (i == j) ? 1.f : 0.f;
+    for (int sweep = 0; sweep < 8; ++sweep) {
+        const float off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
+        const float dg = a[0][0] * a[0][0] + a[1][1] * a[1][1] + a[2][2] * a[2][2];
+        if (off <= 1e-14f * dg) break;
+#pragma unroll
+        for (int pq = 0; pq < 3; ++pq) {
+            const int p = (pq == 2) ? 1 : 0;
+            const int q = (pq == 0) ? 1 : 2;
+            const int r = 3 - p - q;
+            const float apq = a[p][q];
+            if (fabsf(apq) <= 1e-30f) continue;
+            const float theta = (a[q][q] - a[p][p]) / (2.f * apq);
+            const float t = (theta >= 0.f ? 1.f : -1.f) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
+            const float c = rsqrtf(t * t + 1.f);
+            const float sn = t * c;
+            a[p][p] -= t * apq;
+            a[q][q] += t * apq;
+            a[p][q] = a[q][p] = 0.f;
+            const float arp = a[r][p], arq = a[r][q];
+            a[r][p] = a[p][r] = c * arp - sn * arq;
+            a[r][q] = a[q][r] = sn * arp + c * arq;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float vkp = V[k][p], vkq = V[k][q];
+                V[k][p] = c * vkp - sn * vkq;
+                V[k][q] = sn * vkp + c * vkq;
+            }
+        }
+    }
+}
+
+// FP64-accurate symmetric 3x3 eigen-decomposition: FP32 Jacobi gives approximate
+// eigenvectors, which are made exactly orthonormal in FP64 (Gram-Schmidt + cross product)
+// and used to rotate b in FP64; FP64 Jacobi sweeps then finish the nearly diagonal matrix.
+// Rotations with |2 a_pq| <= 1e-3 |a_qq - a_pp| use the series t = e/2 - e^3/8,
+// c = 1 - t^2/2 + 3 t^4/8 (e = 2 a_pq / (a_qq - a_pp); truncation below 1e-16).
+__device__ __forceinline__ void eig3_mixed(const double b[3][3], double lam[3], double N[3][3]) {
+    float af[3][3], Vf[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) af[i][j] = (float)b[i][j];
+    jacobi3_f32(af, Vf);
+    double q0[3], q1[3], q2[3];
+    {
+        double n0 = 0.0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { q0[k] = Vf[k][0]; n0 += q0[k] * q0[k]; }
+        const double i0 = 1.0 / sqrt(n0);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) q0[k] *= i0;
+        double dt = 0.0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) dt += q0[k] * (double)Vf[k][1];
+        double n1 = 0.0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { q1[k] = (double)Vf[k][1] - dt * q0[k]; n1 += q1[k] * q1[k]; }
+        const double i1 = 1.0 / sqrt(n1);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) q1[k] *= i1;
+        q2[0] = q0[1] * q1[2] - q0[2] * q1[1];
+        q2[1] = q0[2] * q1[0] - q0[0] * q1[2];
+        q2[2] = q0[0] * q1[1] - q0[1] * q1[0];
+    }
+    const double Q[3][3] = {{q0[0], q1[0], q2[0]}, {q0[1], q1[1], q2[1]}, {q0[2], q1[2], q2[2]}};
+    double a[3][3], T[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            double sm = 0.0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) sm += b[i][k] * Q[k][j];
+            T[i][j] = sm;
+        }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j) {
+            double sm = 0.0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) sm += Q[k][i] * T[k][j];
+            a[i][j] = sm;
+            a[j][i] = sm;
+        }
+    double V[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    for (int sweep = 0; sweep < 12; ++sweep) {
+        const double off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
+        const double dg = a[0][0] * a[0][0] + a[1][1] * a[1][1] + a[2][2] * a[2][2];
+        if (off <= 1e-34 * dg) break;
+#pragma unroll
+        for (int pq = 0; pq < 3; ++pq) {
+            const int p = (pq == 2) ? 1 : 0;
+            const int q = (pq == 0) ? 1 : 2;
+            const int r = 3 - p - q;
+            const double apq = a[p][q];
+            if (fabs(apq) <= 1e-300) continue;
+            const double gap = a[q][q] - a[p][p];
+            double t, c;
+            if (fabs(2.0 * apq) <= 1e-3 * fabs(gap)) {
+                const double e = 2.0 * apq / gap;
+                t = 0.5 * e - 0.125 * e * e * e;
+                const double t2 = t * t;
+                c = 1.0 - 0.5 * t2 + 0.375 * t2 * t2;
+            } else {
+                const double theta = gap / (2.0 * apq);
+                t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                c = 1.0 / sqrt(t * t + 1.0);
+            }
+            const double sn = t * c;
+            a[p][p] -= t * apq;
+            a[q][q] += t * apq;
+            a[p][q] = a[q][p] = 0.0;
+            const double arp = a[r][p], arq = a[r][q];
+            a[r][p] = a[p][r] = c * arp - sn * arq;
+            a[r][q] = a[q][r] = sn * arp + c * arq;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const double vkp = V[k][p], vkq = V[k][q];
+                V[k][p] = c * vkp - sn * vkq;
+                V[k][q] = sn * vkp + c * vkq;
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        lam[i] = a[i][i];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            double sm = 0.0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) sm += Q[i][k] * V[k][j];
+            N[i][j] = sm;
+        }
+    }
+}
+
 // (ln x - ln y) / (x - y) for x, y > 0, finite and accurate when x ~ y
 template <typename T>
 __device__ __forceinline__ T log_divided_difference(T x, T y) {
@@ -153,10 +296,7 @@ __device__ __forceinline__ void material_value(const double F[3][3], const doubl
         S.N[1][0] = -s; S.N[1][1] = c;  S.N[1][2] = 0.0;
         S.N[2][0] = 0.0; S.N[2][1] = 0.0; S.N[2][2] = 1.0;
     } else {
-        jacobi3(b, S.N);
-        S.lam[0] = b[0][0];
-        S.lam[1] = b[1][1];
-        S.lam[2] = b[2][2];
+        eig3_mixed(b, S.lam, S.N);
     }
     double eps[3];
 #pragma unroll

@@ -14,7 +14,7 @@ import numpy as np
 from . import binding, inputs, workload
 
 FAMILY_2D = ["r2_n16_m100", "r2_n24_m150", "r2_n32_m200"]
-FAMILY_3D = ["r3_n48_m400", "r3_n64_m650", "r3_n96_m900"]
+FAMILY_3D = ["r3_n48_m400", "r3_n64_m650", "r3_n95_m900"]
 
 
 def available(names):
