@@ -202,6 +202,12 @@ rom_status rom_use_graphs(rom_ctx *ctx, int enable);
  * instance (as assembled by the selected precision mode; for ROM_PREC_TF32/BF16 and
  * converged instances with want_abar, the FP32 re-assembly used for Abar).  Blocking. */
 rom_status rom_debug_stiffness(rom_ctx *ctx, const rom_state *st, double *K);
+/* Diagnostics: the pulled-back tangent At of the last evaluated iterate, copied to the host
+ * buffer `At` of `bytes` bytes (at most the array's size is copied).  Layout [B][d^4][mA],
+ * mA = m rounded up to a multiple of 4, entry (b, (a*d + r)*d*d + c*d + s, i) =
+ * w_i J_i sum_{t,u} Finv_i[r][t] dP_i[a][t]/dF[c][u] Finv_i[s][u]; element type double after a
+ * ROM_PREC_FP64 step, float otherwise.  Valid for the instances of the last pass.  Blocking. */
+rom_status rom_debug_tangent(rom_ctx *ctx, const rom_state *st, void *At, int64_t bytes);
 rom_status rom_profile_read(rom_ctx *ctx, int kernel, double *ms, int64_t *launches, double *flops);
 
 /* ---------------------------------------------------------------------------

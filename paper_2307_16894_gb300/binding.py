@@ -25,7 +25,8 @@ EXPORTED = ["rom_create", "rom_destroy", "rom_load_basis", "rom_load_cubature", 
             "rom_state_create", "rom_state_destroy", "rom_state_export", "rom_state_import", "rom_step",
             "rom_step_device", "rom_sync", "rom_last_error", "rom_profile", "rom_profile_read",
             "rom_step_noalloc", "rom_mlp_init", "rom_mlp_nparams", "rom_mlp_params", "rom_mlp_norm",
-            "rom_mlp_train_step", "rom_mlp_loss_grad", "rom_mlp_predict", "rom_features", "rom_debug_stiffness", "rom_use_graphs",
+            "rom_mlp_train_step", "rom_mlp_loss_grad", "rom_mlp_predict", "rom_features", "rom_debug_stiffness",
+            "rom_debug_tangent", "rom_use_graphs",
             "rom_state_bytes", "rom_autotune", "rom_serve"]
 
 KERNEL_GROUPS = ["start", "constitutive", "assemble", "solve", "finalize", "bookkeeping", "learned_start"]
@@ -91,6 +92,7 @@ def lib(path=None):
     L.rom_mlp_predict.argtypes = [p, p, i64, i, p]
     L.rom_features.argtypes = [p, p, p, p]
     L.rom_debug_stiffness.argtypes = [p, p, p]
+    L.rom_debug_tangent.argtypes = [p, p, p, i64]
     L.rom_use_graphs.argtypes = [p, i]
     L.rom_state_bytes.argtypes = [p, i64, p]
     L.rom_autotune.argtypes = [p, p, p, p, p, p]
@@ -284,6 +286,15 @@ class State:
         K = np.empty((self.B, c.n, c.n))
         c._check(c.L.rom_debug_stiffness(c.h, self.h, _p(K)), "rom_debug_stiffness")
         return K
+
+    def tangent(self, fp64):
+        """At [B, d^4, m] of the last pass (diagnostics); fp64: the step ran with precision fp64."""
+        c = self.ctx
+        d4 = c.dim ** 4
+        mA = (c.m + 3) & ~3
+        At = np.empty((self.B, d4, mA), dtype=np.float64 if fp64 else np.float32)
+        c._check(c.L.rom_debug_tangent(c.h, self.h, _p(At), At.nbytes), "rom_debug_tangent")
+        return At[:, :, :c.m]
 
     def export(self, history=True):
         """(a [B, n], C^p^-1 [B, m, nc], xi [B, m]); history=False skips the last two (None)."""

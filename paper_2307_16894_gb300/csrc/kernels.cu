@@ -93,7 +93,7 @@ __global__ void k_start(Model M, Batch Bt, const double *__restrict__ Fbar, Step
     }
     Ctl c;
     c.r0 = 0.0; c.tol = 0.0; c.rn_acc = 0.0; c.t = 1.0;
-    c.iters = 0; c.evals = 0; c.ls = 0; c.status = 0; c.active = 1; c.pad0 = c.pad1 = 0;
+    c.iters = 0; c.evals = 0; c.ls = 0; c.status = 0; c.active = 1; c.acc_k = c.pad1 = 0;
     // learned start: evaluate the predicted point first, then the previous-step point (phase 2 -> 3)
     c.phase = (o.start == 2) ? 2 : 0;
     Bt.ctl[b] = c;
@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(128) k_constitutive(Model M, Batch Bt) {
     TangentData<TT> td;
     tangent_setup<D, TT>(S, ph, F, cp, Finv, P, td);
     TT *At = reinterpret_cast<TT *>(Bt.At);
-    const size_t ab = (size_t)b * D2 * D2 * m + i;
+    const size_t ab = (size_t)b * D2 * D2 * M.mA + i;
 #pragma unroll 1
     for (int c = 0; c < D; ++c)
 #pragma unroll 1
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(128) k_constitutive(Model M, Batch Bt) {
                     TT t = TT(0);
 #pragma unroll
                     for (int bb = 0; bb < D; ++bb) t += dP[a][bb] * TT(Fmi[r][bb]);
-                    At[ab + (size_t)((a * D + r) * D2 + col) * m] = TT(wJ) * t;
+                    At[ab + (size_t)((a * D + r) * D2 + col) * M.mA] = TT(wJ) * t;
                 }
         }
 }
@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(256) k_assemble(Model M, Batch Bt, int CH, int
         }
         for (int e = tid; e < CH * D4; e += blockDim.x) {
             const int ce = e / CH, ii = e - ce * CH;
-            As[ii * D4 + ce] = (ii < ch) ? At[((size_t)b * D4 + ce) * m + c0 + ii] : TK(0);
+            As[ii * D4 + ce] = (ii < ch) ? At[((size_t)b * D4 + ce) * M.mA + c0 + ii] : TK(0);
         }
         for (int e = tid; e < CH * D2; e += blockDim.x) {
             const int c = e / CH, ii = e - c * CH;
@@ -435,6 +435,8 @@ __device__ void warp_lu_solve(const double *A, int n, const int *piv, double *x)
     }
 }
 
+constexpr int ESC_ITERS = 4;
+
 __global__ void __launch_bounds__(32) k_solve(Model M, Batch Bt, StepOpts o, int32_t *list_next) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int n_act = Bt.counts[0];
@@ -528,6 +530,9 @@ __global__ void __launch_bounds__(32) k_solve(Model M, Batch Bt, StepOpts o, int
         else if (c.rn_acc <= c.tol) { c.status = 0; c.active = 0; }
         else if (c.iters >= o.max_iter) { c.status = 5; c.active = 0; }
         else {
+            // low-precision stiffness (BF16/TF32): an instance still iterating after ESC_ITERS
+            // accepted steps gets the FP32-accurate assembly from its next evaluation on
+            if (o.precision >= 2 && c.iters >= ESC_ITERS) c.acc_k = 1;
             const double *Kb = Bt.K + (size_t)b * n * n;
             for (int e = lane; e < n * n; e += 32) A[e] = Kb[e];
             for (int j = lane; j < n; j += 32) x[j] = -r[j];
@@ -552,6 +557,251 @@ __global__ void __launch_bounds__(32) k_solve(Model M, Batch Bt, StepOpts o, int
 }
 
 // --------------------------------------------------------------------- finalize
+// a11 sums of one instance in FP64: B = sum_i G_i^T Ahat_i [n][D2] and A0 = sum_i Xi_i^T Ahat_i
+// [D4]; work = Ah [CHF][D4] | Gs [CHF][D2][n] (doubles).  Ends with Bm, A0 visible to the block.
+template <int D>
+__device__ void abar_sums_f64(const Model &M, const Batch &Bt, int64_t b, int CHF, double *Bm, double *A0,
+                              double *Fm, double *work) {
+    constexpr int D2 = D * D, D4 = D2 * D2;
+    const int n = M.n, m = M.m, tid = threadIdx.x;
+    double *Ah = work;
+    double *Gs = Ah + (size_t)CHF * D4;
+    const double *At = reinterpret_cast<const double *>(Bt.At);
+    double bacc[4] = {0, 0, 0, 0};     // entries tid, tid+256, ... of Bm (n*D2 <= 1152)
+    double aacc = 0.0;                 // entry tid of A0 (D4 <= 81)
+    for (int c0 = 0; c0 < m; c0 += CHF) {
+        const int ch = min(CHF, m - c0);
+        __syncthreads();
+        for (int e = tid; e < ch * D2; e += blockDim.x) {
+            const int ii = e / D2, ar = e - ii * D2;
+            const int a = ar / D, r = ar - a * D;
+            double s = (a == r) ? 1.0 : 0.0;
+            for (int k = 0; k < M.n_par; ++k)
+                s += Bt.mu[b * M.n_par + k] * M.Gmu_T[((size_t)ar * M.n_par + k) * m + c0 + ii];
+            Fm[ii * D2 + ar] = s;
+        }
+        for (int e = tid; e < ch * D2 * n; e += blockDim.x)
+            Gs[e] = M.G_pt[(size_t)c0 * D2 * n + e];
+        __syncthreads();
+        for (int e = tid; e < ch * D4; e += blockDim.x) {
+            const int ii = e / D4, rem = e - ii * D4;
+            const int ar = rem / D2, kl = rem - ar * D2;
+            const int k = kl / D, l = kl - k * D;
+            double s = 0.0;
+            for (int ss = 0; ss < D; ++ss)
+                s += At[((size_t)b * D4 + ar * D2 + k * D + ss) * M.mA + c0 + ii] * Fm[ii * D2 + l * D + ss];
+            Ah[e] = s;
+        }
+        __syncthreads();
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + q * blockDim.x;
+            if (e < n * D2) {
+                const int j = e / D2, kl = e - j * D2;
+                double s = 0.0;
+                for (int ii = 0; ii < ch; ++ii)
+                    for (int ar = 0; ar < D2; ++ar) s += Gs[(ii * D2 + ar) * n + j] * Ah[ii * D4 + ar * D2 + kl];
+                bacc[q] += s;
+            }
+        }
+        if (tid < D4) {
+            const int ij = tid / D2, kl = tid - ij * D2;
+            const int ia = ij / D, jb = ij - ia * D;
+            double s = 0.0;
+            for (int ii = 0; ii < ch; ++ii)
+                for (int r = 0; r < D; ++r) s += Fm[ii * D2 + jb * D + r] * Ah[ii * D4 + (ia * D + r) * D2 + kl];
+            aacc += s;
+        }
+    }
+    __syncthreads();
+    for (int q = 0; q < 4; ++q) {
+        const int e = tid + q * blockDim.x;
+        if (e < n * D2) Bm[e] = bacc[q];
+    }
+    if (tid < D4) A0[tid] = aacc;
+    __syncthreads();
+}
+
+// the same sums from the FP32 tangent of the mixed-precision path, in FP32 (B) and FP64 (A0):
+// thread (j = tid % 64 (+64), group = tid / 64) accumulates B[j][0..D2) over the points
+// i = group (mod blockDim / 64) of each chunk; the groups are added in a fixed order.
+// work = Ah [CHF][D4] | Gs [CHF][D2][n] (floats); the group sums reuse Gs.
+template <int D>
+__device__ void abar_sums_f32(const Model &M, const Batch &Bt, int64_t b, int CHF, double *Bm, double *A0,
+                              double *Fm, float *work) {
+    constexpr int D2 = D * D, D4 = D2 * D2;
+    const int n = M.n, m = M.m, tid = threadIdx.x;
+    float *Ah = work;
+    float *Gs = Ah + (size_t)CHF * D4;
+    const float *At = reinterpret_cast<const float *>(Bt.At);
+    const int jl = tid & 63, grp = tid >> 6, NGRP = blockDim.x >> 6;
+    const int AG = blockDim.x / D4, ag = tid / D4, ae = tid - ag * D4;   // A0: AG point groups
+    float bacc[2][D2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int kl = 0; kl < D2; ++kl) bacc[h][kl] = 0.f;
+    float aacc = 0.f;
+    for (int c0 = 0; c0 < m; c0 += CHF) {
+        const int ch = min(CHF, m - c0);
+        __syncthreads();
+        for (int e = tid; e < ch * D2; e += blockDim.x) {
+            const int ii = e / D2, ar = e - ii * D2;
+            const int a = ar / D, r = ar - a * D;
+            double s = (a == r) ? 1.0 : 0.0;
+            for (int k = 0; k < M.n_par; ++k)
+                s += Bt.mu[b * M.n_par + k] * M.Gmu_T[((size_t)ar * M.n_par + k) * m + c0 + ii];
+            Fm[ii * D2 + ar] = s;
+        }
+        for (int e = tid; e < ch * D2 * n; e += blockDim.x)
+            Gs[e] = M.G32_pt[(size_t)c0 * D2 * n + e];
+        __syncthreads();
+        for (int e = tid; e < ch * D4; e += blockDim.x) {
+            const int ii = e / D4, rem = e - ii * D4;
+            const int ar = rem / D2, kl = rem - ar * D2;
+            const int k = kl / D, l = kl - k * D;
+            float s = 0.f;
+            for (int ss = 0; ss < D; ++ss)
+                s = fmaf(At[((size_t)b * D4 + ar * D2 + k * D + ss) * M.mA + c0 + ii], (float)Fm[ii * D2 + l * D + ss], s);
+            Ah[e] = s;
+        }
+        __syncthreads();
+        for (int ii = grp; ii < ch; ii += NGRP) {
+#pragma unroll
+            for (int ar = 0; ar < D2; ++ar) {
+                float a[D2];
+#pragma unroll
+                for (int kl = 0; kl < D2; ++kl) a[kl] = Ah[ii * D4 + ar * D2 + kl];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int j = jl + 64 * h;
+                    if (j < n) {
+                        const float g = Gs[(ii * D2 + ar) * n + j];
+#pragma unroll
+                        for (int kl = 0; kl < D2; ++kl) bacc[h][kl] = fmaf(g, a[kl], bacc[h][kl]);
+                    }
+                }
+            }
+        }
+        if (ag < AG) {
+            const int ij = ae / D2, kl = ae - ij * D2;
+            const int ia = ij / D, jb = ij - ia * D;
+            for (int ii = ag; ii < ch; ii += AG)
+                for (int r = 0; r < D; ++r)
+                    aacc = fmaf((float)Fm[ii * D2 + jb * D + r], Ah[ii * D4 + (ia * D + r) * D2 + kl], aacc);
+        }
+    }
+    __syncthreads();
+    float *red = Gs;   // [NGRP][n][D2], then [AG][D4]
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int j = jl + 64 * h;
+        if (j < n)
+#pragma unroll
+            for (int kl = 0; kl < D2; ++kl) red[((size_t)grp * n + j) * D2 + kl] = bacc[h][kl];
+    }
+    __syncthreads();
+    for (int e = tid; e < n * D2; e += blockDim.x) {
+        double s = 0.0;
+        for (int g = 0; g < NGRP; ++g) s += (double)red[(size_t)g * n * D2 + e];
+        Bm[e] = s;
+    }
+    __syncthreads();
+    if (ag < AG) red[ag * D4 + ae] = aacc;
+    __syncthreads();
+    if (tid < D4) {
+        double s = 0.0;
+        for (int g = 0; g < AG; ++g) s += (double)red[g * D4 + tid];
+        A0[tid] = s;
+    }
+    __syncthreads();
+}
+
+// LU with partial pivoting of the n x n row-major matrix A (shared memory) by the whole block,
+// the same row operations applied to the nrhs right-hand sides X[r][0..n) (forward
+// substitution), then back substitution: X <- A^-1 X.  Pivot = largest |A[i][k]|, ties to the
+// lower row; every element sees the same operations in the same order as warp_lu followed by
+// warp_lu_solve.  Returns false (uniformly over the block) if a pivot is zero or non-finite.
+template <typename T>
+__device__ bool block_lu_solve(T *A, int n, T *X, int nrhs, int *s_piv) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int k = 0; k < n; ++k) {
+        if (tid < 32) {
+            double best = -1.0;
+            int bi = k;
+            for (int i = k + tid; i < n; i += 32) {
+                const double v = fabs((double)A[i * n + k]);
+                if (v > best || (v == best && i < bi)) { best = v; bi = i; }
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+                const double ob = __shfl_xor_sync(0xffffffffu, best, off);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            if (tid == 0) *s_piv = (!(best > 0.0) || !isfinite(best)) ? -1 : bi;
+        }
+        __syncthreads();
+        const int p = *s_piv;
+        if (p < 0) return false;
+        if (p != k) {
+            for (int j = tid; j < n; j += nt) { const T t = A[k * n + j]; A[k * n + j] = A[p * n + j]; A[p * n + j] = t; }
+            for (int r = tid; r < nrhs; r += nt) { const T t = X[r * n + k]; X[r * n + k] = X[r * n + p]; X[r * n + p] = t; }
+        }
+        __syncthreads();
+        const T akk = A[k * n + k];
+        for (int i = k + 1 + tid; i < n; i += nt) A[i * n + k] /= akk;
+        __syncthreads();
+        const int w = n - k - 1, wr = w + nrhs;
+        for (int e = tid; e < w * wr; e += nt) {
+            const int i = k + 1 + e / wr, c = e - (e / wr) * wr;
+            const T lik = A[i * n + k];
+            if (c < w) A[i * n + k + 1 + c] -= lik * A[k * n + k + 1 + c];
+            else X[(c - w) * n + i] -= lik * X[(c - w) * n + k];
+        }
+        __syncthreads();
+    }
+    for (int k = n - 1; k >= 0; --k) {
+        for (int r = tid; r < nrhs; r += nt) X[r * n + k] /= A[k * n + k];
+        __syncthreads();
+        for (int e = tid; e < k * nrhs; e += nt) {
+            const int r = e / k, i = e - r * k;
+            X[r * n + i] -= A[i * n + k] * X[r * n + k];
+        }
+        __syncthreads();
+    }
+    return true;
+}
+
+// Ahat part of the effective tangent: AU = (A0 - B^T K^-1 B) / |Omega| with the factor of K at
+// the solution (K* = K), factored and solved by the block in arithmetic T (FP64 on the FP64
+// path; FP32 on the mixed path, whose K, B and A0 carry FP32-level errors already)
+template <int D, typename T>
+__device__ void schur_abar(const Model &M, const Batch &Bt, int64_t b, const double *Bm, const double *A0,
+                           unsigned char *work, double *AU) {
+    constexpr int D2 = D * D, D4 = D2 * D2;
+    const int n = M.n, tid = threadIdx.x;
+    T *Aw = reinterpret_cast<T *>(work);     // [n][n]
+    T *Zs = Aw + (size_t)n * n;              // [D2][n]
+    int *piv = reinterpret_cast<int *>(Zs + (size_t)n * D2);
+    const double *Kb = Bt.K + (size_t)b * n * n;
+    for (int e = tid; e < n * n; e += blockDim.x) Aw[e] = (T)Kb[e];
+    for (int e = tid; e < n * D2; e += blockDim.x) {
+        const int kl = e / n, j = e - kl * n;
+        Zs[e] = (T)Bm[j * D2 + kl];
+    }
+    __syncthreads();
+    const bool ok = block_lu_solve<T>(Aw, n, Zs, D2, piv);
+    if (tid < D4) {
+        const int ij = tid / D2, kl = tid - ij * D2;
+        double s = A0[tid];
+        if (ok)
+            for (int j = 0; j < n; ++j) s -= Bm[j * D2 + ij] * (double)Zs[(size_t)kl * n + j];
+        else
+            s = NAN;
+        AU[tid] = s / M.omega;
+    }
+    __syncthreads();
+}
+
 template <int D, typename TT>
 __global__ void __launch_bounds__(256) k_finalize(Model M, Batch Bt, StepOpts o, double *__restrict__ Pbar,
                                                   double *__restrict__ Abar, void *info_v, int CHF) {
@@ -609,87 +859,12 @@ __global__ void __launch_bounds__(256) k_finalize(Model M, Batch Bt, StepOpts o,
         double *Bm = reinterpret_cast<double *>(smem);              // [n][D2]
         double *A0 = Bm + (size_t)n * D2;                          // [D4]
         double *Fm = A0 + D4;                                      // [CHF][D2]
-        double *Ah = Fm + (size_t)CHF * D2;                        // [CHF][D4]
-        double *Gs = Ah + (size_t)CHF * D4;                        // [CHF][D2][n]
-        const TT *At = reinterpret_cast<const TT *>(Bt.At);
-        double bacc[4] = {0, 0, 0, 0};     // entries tid, tid+256, ... of Bm (n*D2 <= 1152)
-        double aacc = 0.0;                 // entry tid of A0 (D4 <= 81)
-        for (int c0 = 0; c0 < m; c0 += CHF) {
-            const int ch = min(CHF, m - c0);
-            __syncthreads();
-            for (int e = tid; e < ch * D2; e += blockDim.x) {
-                const int ii = e / D2, ar = e - ii * D2;
-                const int a = ar / D, r = ar - a * D;
-                double s = (a == r) ? 1.0 : 0.0;
-                for (int k = 0; k < M.n_par; ++k)
-                    s += Bt.mu[b * M.n_par + k] * M.Gmu_T[((size_t)ar * M.n_par + k) * m + c0 + ii];
-                Fm[ii * D2 + ar] = s;
-            }
-            for (int e = tid; e < ch * D2 * n; e += blockDim.x)
-                Gs[e] = M.G_pt[(size_t)c0 * D2 * n + e];
-            __syncthreads();
-            for (int e = tid; e < ch * D4; e += blockDim.x) {
-                const int ii = e / D4, rem = e - ii * D4;
-                const int ar = rem / D2, kl = rem - ar * D2;
-                const int k = kl / D, l = kl - k * D;
-                double s = 0.0;
-                for (int ss = 0; ss < D; ++ss)
-                    s += double(At[((size_t)b * D4 + ar * D2 + k * D + ss) * m + c0 + ii]) * Fm[ii * D2 + l * D + ss];
-                Ah[e] = s;
-            }
-            __syncthreads();
-            for (int q = 0; q < 4; ++q) {
-                const int e = tid + q * blockDim.x;
-                if (e < n * D2) {
-                    const int j = e / D2, kl = e - j * D2;
-                    double s = 0.0;
-                    for (int ii = 0; ii < ch; ++ii)
-                        for (int ar = 0; ar < D2; ++ar) s += Gs[(ii * D2 + ar) * n + j] * Ah[ii * D4 + ar * D2 + kl];
-                    bacc[q] += s;
-                }
-            }
-            if (tid < D4) {
-                const int ij = tid / D2, kl = tid - ij * D2;
-                const int ia = ij / D, jb = ij - ia * D;
-                double s = 0.0;
-                for (int ii = 0; ii < ch; ++ii)
-                    for (int r = 0; r < D; ++r) s += Fm[ii * D2 + jb * D + r] * Ah[ii * D4 + (ia * D + r) * D2 + kl];
-                aacc += s;
-            }
-        }
-        __syncthreads();
-        for (int q = 0; q < 4; ++q) {
-            const int e = tid + q * blockDim.x;
-            if (e < n * D2) Bm[e] = bacc[q];
-        }
-        if (tid < D4) A0[tid] = aacc;
-        __syncthreads();
+        unsigned char *work = reinterpret_cast<unsigned char *>(Fm + (size_t)CHF * D2);
+        if (sizeof(TT) == 8) abar_sums_f64<D>(M, Bt, b, CHF, Bm, A0, Fm, reinterpret_cast<double *>(work));
+        else abar_sums_f32<D>(M, Bt, b, CHF, Bm, A0, Fm, reinterpret_cast<float *>(work));
         // Schur complement with the factor of K at the solution (K* = K)
-        double *Aw = Gs;                              // reuse: n*n + n*D2 + n ints
-        double *Zs = Aw + (size_t)n * n;
-        int *piv = reinterpret_cast<int *>(Zs + (size_t)n * D2);
-        if (tid < 32) {
-            const double *Kb = Bt.K + (size_t)b * n * n;
-            for (int e = tid; e < n * n; e += 32) Aw[e] = Kb[e];
-            __syncwarp();
-            const bool ok = warp_lu(Aw, n, piv);
-            for (int kl = 0; kl < D2; ++kl) {
-                double *x = Zs + (size_t)kl * n;
-                for (int j = tid; j < n; j += 32) x[j] = Bm[j * D2 + kl];
-                __syncwarp();
-                if (ok) warp_lu_solve(Aw, n, piv, x);
-                else for (int j = tid; j < n; j += 32) x[j] = NAN;
-                __syncwarp();
-            }
-        }
-        __syncthreads();
-        if (tid < D4) {
-            const int ij = tid / D2, kl = tid - ij * D2;
-            double s = A0[tid];
-            for (int j = 0; j < n; ++j) s -= Bm[j * D2 + ij] * Zs[(size_t)kl * n + j];
-            AU[tid] = s / M.omega;
-        }
-        __syncthreads();
+        if (sizeof(TT) == 8) schur_abar<D, double>(M, Bt, b, Bm, A0, work, AU);
+        else schur_abar<D, float>(M, Bt, b, Bm, A0, work, AU);
         // rotate back: Abar = d(R Pbar_U(R^T Fbar))/dFbar
         if (tid < D2) {
             const int k = tid / D, l = tid - k * D;

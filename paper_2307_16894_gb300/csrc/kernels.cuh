@@ -15,12 +15,13 @@ struct Ctl {
     double r0, tol, rn_acc, t;
     int32_t iters, evals, ls, status;
     int32_t active, phase;   // phase 0: start evaluation pending, 1: trial evaluation pending
-    int32_t pad0, pad1;
+    int32_t acc_k, pad1;   // acc_k: assemble this instance's stiffness FP32-accurately (BF16/TF32 modes)
 };
 
 // model (shared by all instances)
 struct Model {
     int d, d2, n, m, n_par, nphase, ncp;
+    int mA;                // row stride of the tangent array At (m rounded up to a multiple of 4)
     const double *G_pt;    // [m][d2][n]
     const double *G_T;     // [d2][n][m]
     const float *G32_pt;   // [m][d2][n]
@@ -42,7 +43,7 @@ struct Batch {
     int32_t *counts;         // [0] = active count, [1] = next count
     double *v;               // [B][d2][m]  wJ vec(P F_mu^-T)
     double *wP;              // [B][d2][m]  wJ P
-    void *At;                // [B][d2*d2][m] pulled-back tangent (double or float)
+    void *At;                // [B][d2*d2][mA] pulled-back tangent (double or float)
     double *cp_tr, *xi_tr;   // trial history
     uint8_t *pl;             // [B][m] plastic flags of the last evaluation
     double *r;               // [B][n]

@@ -2,6 +2,7 @@
 // include/podecm.h).  Host-side bookkeeping only: argument checks, device
 // buffers, and the launch sequence of one load step; all arithmetic of the
 // step runs in the kernels of kernels.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -35,6 +36,10 @@ void mlp_predict(MlpDev &M, const float *X, int64_t N, int bf16, double *out, cu
 void tc_image_shape(int d, int fmt, int m, int *chunk_bytes, int *nchunks);
 void tc_build_image(int d, int fmt, int n, int m, const double *G, unsigned char *img);
 int launch_tc(int fmt, const Model &M, Batch Bt, const unsigned char *img, int *err, cudaStream_t s);
+size_t tc3_image_bytes(int m);
+void tc3_build_images(int n, int m, const double *G, unsigned char *img);
+int launch_tc3(int mode, const Model &M, Batch Bt, const unsigned char *img, int *err, int sel, bool with_force,
+               cudaStream_t s);
 void launch_list_converged(Batch Bt, cudaStream_t s);
 void launch_graph_advance(Batch Bt, const int32_t *list_next, cudaGraphConditionalHandle h, int max_pass,
                           cudaStream_t s);
@@ -74,7 +79,8 @@ struct rom_ctx {
     int64_t prof_launches[ROM_NKERNELS] = {0};
     double prof_flops[ROM_NKERNELS] = {0};
     // tensor-core assembly: pre-arranged B-operand images of G (BF16, TF32) and an error flag
-    unsigned char *tc_img[2] = {nullptr, nullptr};
+    unsigned char *tc_img[2] = {nullptr, nullptr};   // 2D tensor-core B-operand images (BF16, TF32)
+    unsigned char *tc3_img = nullptr;                 // 3D tensor-core images (tc_assemble3.cu)
     int *d_err = nullptr;
     // learned Newton start
     bool has_mlp = false, mlp_norm = false;
@@ -192,6 +198,7 @@ rom_status rom_destroy(rom_ctx *ctx) {
     p = ctx->d_pred; dfree(p);
     p = ctx->tc_img[0]; dfree(p);
     p = ctx->tc_img[1]; dfree(p);
+    p = ctx->tc3_img; dfree(p);
     p = ctx->d_err; dfree(p);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -228,8 +235,15 @@ rom_status rom_load_basis(rom_ctx *ctx, int n, int m, const double *G) {
     CK(cudaMemcpy(ctx->G_T, gt.data(), cnt * 8, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->G32, g32.data(), cnt * 4, cudaMemcpyHostToDevice));
     for (int f = 0; f < 2; ++f) { p = ctx->tc_img[f]; dfree(p); ctx->tc_img[f] = nullptr; }
+    p = ctx->tc3_img; dfree(p); ctx->tc3_img = nullptr;
+    if (n <= 64 && ctx->dim == 3) {
+        std::vector<unsigned char> img(tc3_image_bytes(m));
+        tc3_build_images(n, m, G, img.data());
+        if ((s = dalloc(ctx, (void **)&ctx->tc3_img, img.size())) != ROM_OK) return s;
+        CK(cudaMemcpy(ctx->tc3_img, img.data(), img.size(), cudaMemcpyHostToDevice));
+    }
     if (n <= 64) {
-        for (int f = 0; f < 2; ++f) {
+        for (int f = 0; f < 2 && ctx->dim == 2; ++f) {
             int cb, nch;
             tc_image_shape(ctx->dim, f + 1, m, &cb, &nch);
             std::vector<unsigned char> img((size_t)cb * nch);
@@ -359,7 +373,7 @@ rom_status rom_state_create(rom_ctx *ctx, int64_t B, rom_state **out) {
         (s = A((void **)&bt.dq, Bz * n * 8)) || (s = A((void **)&bt.ctl, Bz * sizeof(Ctl))) ||
         (s = A((void **)&bt.list, Bz * 4)) || (s = A((void **)&st->list2, Bz * 4)) ||
         (s = A((void **)&bt.counts, 64)) || (s = A((void **)&bt.v, Bz * d2 * m * 8)) ||
-        (s = A((void **)&bt.wP, Bz * d2 * m * 8)) || (s = A((void **)&bt.At, Bz * d2 * d2 * m * 8)) ||
+        (s = A((void **)&bt.wP, Bz * d2 * m * 8)) || (s = A((void **)&bt.At, Bz * d2 * d2 * (size_t)((m + 3) & ~3) * 8)) ||
         (s = A((void **)&bt.cp_tr, Bz * ncp * m * 8)) || (s = A((void **)&bt.xi_tr, Bz * m * 8)) ||
         (s = A((void **)&bt.pl, Bz * m)) || (s = A((void **)&bt.r, Bz * n * 8)) ||
         (s = A((void **)&bt.K, Bz * n * n * 8)) || (s = A((void **)&bt.Ubar, Bz * d2 * 8)) ||
@@ -454,7 +468,7 @@ static rom_status check_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts) 
         return fail(ctx, ROM_E_STATE, "rom_step: learned start requested but no MLP (rom_mlp_init, rom_mlp_params, rom_mlp_norm)");
     if (opts->start == ROM_START_MLP && ctx->mlp.n_in != ctx->dim * ctx->dim + ctx->n_par + 2 * ctx->n + 2)
         return fail(ctx, ROM_E_STATE, "rom_step: MLP input size %d does not match d^2 + n_par + 2n + 2", ctx->mlp.n_in);
-    if (opts->precision >= ROM_PREC_TF32 && !ctx->tc_img[0])
+    if (opts->precision >= ROM_PREC_TF32 && !ctx->tc_img[0] && !ctx->tc3_img)
         return fail(ctx, ROM_E_ARG, "rom_step: tensor-core precision needs n <= 64 (n = %d)", ctx->n);
     return ROM_OK;
 }
@@ -463,6 +477,7 @@ static Model make_model(const rom_ctx *ctx) {
     Model M;
     M.d = ctx->dim; M.d2 = ctx->dim * ctx->dim; M.n = ctx->n; M.m = ctx->m; M.n_par = ctx->n_par;
     M.nphase = ctx->nphase; M.ncp = ctx->dim == 2 ? 4 : 6;
+    M.mA = (ctx->m + 3) & ~3;
     M.G_pt = ctx->G_pt; M.G_T = ctx->G_T; M.G32_pt = ctx->G32; M.w = ctx->w; M.phase = ctx->phase;
     M.Gmu_T = ctx->Gmu_T; M.omega = ctx->omega;
     return M;
@@ -521,6 +536,32 @@ static void prof_collect(rom_ctx *ctx) {
     ctx->recs.clear();
 }
 
+// K (and, with_force, the residual r) of the active list: 3D models with n <= 64 use the
+// tensor-core kernel (BF16, TF32, or the FP32-accurate TF32 split for precision fp32; in BF16
+// and TF32 the instances that the solve flagged for an accurate stiffness get the split
+// assembly); 2D models use the 2D tensor-core kernel for BF16/TF32 and the SIMT kernel
+// otherwise (the SIMT and 2D tensor-core launches always produce r as well)
+static int launch_assembly(rom_ctx *ctx, const Model &M, Batch bt, const StepOpts &o, int32_t *nxt, bool with_force,
+                           cudaStream_t s) {
+    if (M.d == 3 && ctx->tc3_img && o.precision >= 1) {
+        if (o.precision == 1) return launch_tc3(3, M, bt, ctx->tc3_img, ctx->d_err, 0, with_force, s);
+        const int r = launch_tc3(o.precision == 3 ? 1 : 2, M, bt, ctx->tc3_img, ctx->d_err, 1, with_force, s);
+        return r ? r : launch_tc3(3, M, bt, ctx->tc3_img, ctx->d_err, 2, false, s);
+    }
+    if (o.precision >= 2)
+        return launch_tc(o.precision == 3 ? 1 : 2, M, bt, ctx->tc_img[o.precision == 3 ? 0 : 1], ctx->d_err, s);
+    return launch_kernel(2, M, bt, o, nxt, s);
+}
+
+// the effective stiffness needs K at FP32 accuracy: after a BF16/TF32 solve, one FP32-accurate
+// assembly of the converged instances (list rebuilt by launch_list_converged)
+static int launch_abar_assembly(rom_ctx *ctx, const Model &M, Batch bc, const StepOpts &o, int32_t *nxt,
+                                cudaStream_t s) {
+    StepOpts o32 = o;
+    o32.precision = 1;
+    return launch_assembly(ctx, M, bc, o32, nxt, false, s);
+}
+
 static rom_status run_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts, const double *Fbar_d, double *Pbar_d,
                            double *Abar_d, void *info_d) {
     StepOpts o;
@@ -555,12 +596,7 @@ static rom_status run_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts, co
         bt.list = lists[pass & 1];
         int32_t *nxt = lists[(pass + 1) & 1];
         const double na = (double)n_act;
-        auto asm_launch = [&] {
-            if (o.precision >= 2)
-                return launch_tc(o.precision == 3 ? 1 : 2, M, bt, ctx->tc_img[o.precision == 3 ? 0 : 1], ctx->d_err,
-                                 ctx->stream);
-            return launch_kernel(2, M, bt, o, nxt, ctx->stream);
-        };
+        auto asm_launch = [&] { return launch_assembly(ctx, M, bt, o, nxt, true, ctx->stream); };
         if (timed(ctx, 1, na * fl_kin, [&] { return launch_kernel(1, M, bt, o, nxt, ctx->stream); }) ||
             timed(ctx, 2, na * fl_asm, asm_launch) ||
             timed(ctx, 3, na * fl_lu, [&] { return launch_kernel(3, M, bt, o, nxt, ctx->stream); }) ||
@@ -572,21 +608,19 @@ static rom_status run_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts, co
         n_act = ctx->h_count[0];
         if (n_act == 0) break;
     }
-    if (o.precision >= 2) {
-        // the effective stiffness needs K at FP32 accuracy: one FP32 assembly of the converged instances
+    const bool tc_used = o.precision >= 2 || (M.d == 3 && ctx->tc3_img && o.precision == 1);
+    if (tc_used) {
+        if (o.precision >= 2 && o.want_abar) {
+            Batch bc = bt;
+            bc.list = lists[0];
+            launch_list_converged(bc, ctx->stream);
+            timed(ctx, 2, 0.0, [&] { return launch_abar_assembly(ctx, M, bc, o, lists[1], ctx->stream); });
+        }
         CK(cudaMemcpyAsync(ctx->h_count + 4, ctx->d_err, 4, cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
         if (ctx->h_count[4]) {
             cudaMemsetAsync(ctx->d_err, 0, 4, ctx->stream);
             return fail(ctx, ROM_E_CUDA, "rom_step: tensor-core pipeline wait timed out");
-        }
-        if (o.want_abar) {
-            Batch bc = bt;
-            bc.list = lists[0];
-            StepOpts o32 = o;
-            o32.precision = 1;
-            launch_list_converged(bc, ctx->stream);
-            timed(ctx, 2, 0.0, [&] { return launch_kernel(2, M, bc, o32, lists[1], ctx->stream); });
         }
     }
     if (timed(ctx, 4, 0.0, [&] { return launch_finalize(M, bt, o, Pbar_d, Abar_d, info_d, ctx->stream); }))
@@ -655,10 +689,7 @@ static rom_status capture_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts
         if (e == cudaSuccess) {
             int32_t *nxt = st->list2;
             bad |= launch_kernel(1, M, bt, o, nxt, bs);
-            if (o.precision >= 2)
-                bad |= launch_tc(o.precision == 3 ? 1 : 2, M, bt, ctx->tc_img[o.precision == 3 ? 0 : 1], ctx->d_err, bs);
-            else
-                bad |= launch_kernel(2, M, bt, o, nxt, bs);
+            bad |= launch_assembly(ctx, M, bt, o, nxt, true, bs);
             bad |= launch_kernel(3, M, bt, o, nxt, bs);
             launch_graph_advance(bt, nxt, h, max_pass, bs);
             cudaGraph_t out = nullptr;
@@ -669,10 +700,8 @@ static rom_status capture_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts
     }
     if (e == cudaSuccess && o.precision >= 2 && o.want_abar) {
         Batch bc = bt;
-        StepOpts o32 = o;
-        o32.precision = 1;
         launch_list_converged(bc, cs);
-        bad |= launch_kernel(2, M, bc, o32, st->list2, cs);
+        bad |= launch_abar_assembly(ctx, M, bc, o, st->list2, cs);
     }
     if (e == cudaSuccess) bad |= launch_finalize(M, bt, o, st->io_P, st->io_A, st->io_info, cs);
     cudaError_t e3 = cudaStreamEndCapture(cs, &graph);
@@ -864,6 +893,15 @@ rom_status rom_debug_stiffness(rom_ctx *ctx, const rom_state *st, double *K) {
     return ROM_OK;
 }
 
+rom_status rom_debug_tangent(rom_ctx *ctx, const rom_state *st, void *At, int64_t bytes) {
+    if (!ctx || !st || !At || bytes < 0 || st->ctx != ctx) return ROM_E_ARG;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const size_t have = (size_t)st->B * ctx->dim * ctx->dim * ctx->dim * ctx->dim * (size_t)((st->m + 3) & ~3) * 8;
+    CK(cudaMemcpy(At, st->bt.At, std::min((size_t)bytes, have), cudaMemcpyDeviceToHost));
+    return ROM_OK;
+}
+
 rom_status rom_state_bytes(const rom_ctx *ctx, int64_t B, int64_t *bytes) {
     if (!ctx || !bytes || B < 1) return ROM_E_ARG;
     const int64_t d2 = ctx->dim * ctx->dim, n = ctx->n, m = ctx->m, ncp = ctx->dim == 2 ? 4 : 6;
@@ -876,7 +914,7 @@ rom_status rom_state_bytes(const rom_ctx *ctx, int64_t B, int64_t *bytes) {
 rom_status rom_autotune(rom_ctx *ctx, rom_state *st, const rom_opts *opts, int *tile, int *chunk, float *ms) {
     rom_status s = check_step(ctx, st, opts);
     if (s != ROM_OK) return s;
-    if (opts->precision >= ROM_PREC_TF32) {   // the tensor-core tiles are fixed
+    if (opts->precision >= ROM_PREC_TF32 || (ctx->dim == 3 && ctx->tc3_img)) {   // the tensor-core tiles are fixed
         if (tile) *tile = 0;
         if (chunk) *chunk = 0;
         return ROM_OK;

@@ -93,7 +93,7 @@ extern "C" rom_status rom_step_noalloc(const rom_noalloc_model *model, int64_t B
     const size_t o_qt = take(Bz * n * 8), o_qa = take(Bz * n * 8), o_dq = take(Bz * n * 8);
     const size_t o_ctl = take(Bz * sizeof(Ctl)), o_l1 = take(Bz * 4), o_l2 = take(Bz * 4);
     const size_t o_v = take(Bz * d2 * m * 8), o_wP = take(Bz * d2 * m * 8);
-    const size_t o_At = take(Bz * d4 * m * (opts->precision == 0 ? 8 : 4));
+    const size_t o_At = take(Bz * d4 * (size_t)((m + 3) & ~3) * (opts->precision == 0 ? 8 : 4));
     const size_t o_cptr = take(Bz * ncp * m * 8), o_xitr = take(Bz * m * 8), o_pl = take(Bz * m);
     const size_t o_r = take(Bz * n * 8), o_K = take(Bz * n * n * 8), o_U = take(Bz * d2 * 8), o_R = take(Bz * d2 * 8);
     if (off > (size_t)ROM_NOALLOC_SCRATCH_BYTES) {
@@ -126,6 +126,7 @@ extern "C" rom_status rom_step_noalloc(const rom_noalloc_model *model, int64_t B
 
     Model M;
     M.d = d; M.d2 = d2; M.n = n; M.m = m; M.n_par = np; M.nphase = model->n_phase; M.ncp = ncp;
+    M.mA = (m + 3) & ~3;
     M.G_pt = model->G; M.G_T = reinterpret_cast<double *>(S + o_GT); M.G32_pt = reinterpret_cast<float *>(S + o_G32);
     M.w = model->w; M.phase = model->phase; M.Gmu_T = reinterpret_cast<double *>(S + o_GmuT); M.omega = model->omega_vol;
     Batch bt{};

@@ -187,10 +187,10 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             const int inst = e / (PC * D4), rem = e - inst * PC * D4;
             const int ce = rem / PC, ii = rem - ce * PC;
             const bool valid = (inst == 0 || has1) && (c0 + ii < m);
-            As[(inst * PC + ii) * D4 + ce] = valid ? At[((size_t)bI[inst] * D4 + ce) * m + c0 + ii] : 0.f;
+            As[(inst * PC + ii) * D4 + ce] = valid ? At[((size_t)bI[inst] * D4 + ce) * M.mA + c0 + ii] : 0.f;
         }
         __syncthreads();
-        // producer: A[inst*64 + j][ii*D2 + cc] = sum_e At[ii][cc][e] G[ii][e][j]
+        // producer: A[inst*64 + j][ii*D2 + cc] = sum_e At[ii][e][cc] G[ii][e][j]
         for (int e = tid; e < 2 * PC * NCOLS; e += THREADS) {
             const int j = e % NCOLS, r2 = e / NCOLS;
             const int ii = r2 % PC, inst = r2 / PC;
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             for (int cc = 0; cc < D2; ++cc) {
                 float y = 0.f;
 #pragma unroll
-                for (int q = 0; q < D2; ++q) y = fmaf(a[cc * D2 + q], g[q], y);
+                for (int q = 0; q < D2; ++q) y = fmaf(a[q * D2 + cc], g[q], y);   // Y = At^T G (K, not K^T)
                 tc::store_a<FMT>(Ast[s], SBO, inst * 64 + j, ii * D2 + cc, y);
             }
         }

@@ -1,0 +1,559 @@
+// Reduced stiffness of the 3D model, K_b = sum_i G_i^T At_i G_i (Eq. stiffnessmatrix_ecm), on the
+// 5th-generation tensor cores, with several instances per CTA sharing every basis tile.
+//
+// Formulation (per instance b): Y_b = blockdiag_i(At_i^T) G (rows = (point i, component c)), then
+// K_b = Y_b^T G, i.e. K[j][l] = sum_i sum_{a,c} G_i[a][j] At_i[a][c] G_i[c][l].  One CTA holds NI = 2 NP instances; instance pair p owns one tensor-memory
+// accumulator D_p[128 x 64] (rows 0..63 = K rows of instance 2p, rows 64..127 = instance 2p+1),
+// and every MMA of a chunk uses the same B operand (the shared basis tile):
+//   D_p += A_p[128 x KC] B[64 x KC]^T,  A_p rows = (instance, j), B rows = l, K = (point, component).
+// The K dimension runs over chunks of PC = 4 cubature points; inside a chunk point pt owns KP
+// consecutive K slots (its 9 components followed by zero padding: 16 slots in BF16, 12 in TF32),
+// so that one producer thread writes the 9 values of a row with 16-byte stores.
+//
+// Roles (warp specialisation):
+//   * producer warps (NPROD threads): thread (instance, point, j-block) keeps the 81 tangent
+//     entries of its cubature point in registers, reads the FP32 basis block G_i[:, j..j+3] from
+//     shared memory and writes Y^T = (At_i^T G_i)^T for its rows (so that D = K, not K^T, when
+//     the FP32 tangent is not exactly symmetric), rounded to BF16 or TF32 (MODE 3
+//     writes a TF32 hi/lo pair, see below) into the canonical K-major layout;
+//     the tangent of the next chunk is prefetched with cp.async while the current one is used;
+//   * one control thread: bulk copies (TMA engine, cp.async.bulk) of the FP32 basis chunk and of
+//     the pre-arranged B-operand image into a 2-stage ring, then, once the producers have
+//     arrived on the stage's mbarrier, NP x (KC / KSTEP) tcgen05.mma and one tcgen05.commit.
+// MODE 1 = BF16 operands, MODE 2 = TF32, MODE 3 = TF32 split: A = A_hi + A_lo, B = B_hi + B_lo
+// with A_hi = tf32(A), A_lo = tf32(A - A_hi); the MMA computes A_hi B_hi + A_lo B_hi + A_hi B_lo,
+// an FP32-accurate product (the dropped A_lo B_lo term is below FP32 rounding).
+// Shared-memory operand layout (no swizzle, K-major): 8-row x 16-byte core matrices, core
+// matrices adjacent in K 128 bytes apart (LBO); 8-row groups SBO bytes apart.  The A tiles use
+// SBO = (K core blocks) * 128 + 16: the extra 16 bytes spread the producers' 16-byte stores of
+// neighbouring row groups over distinct banks.
+// Every wait is bounded (wall clock); on timeout the CTA records an error, stops issuing work,
+// waits (bounded) for its own outstanding copies and MMAs, frees its tensor memory and returns.
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstring>
+
+#include "kernels.cuh"
+
+namespace podecm {
+
+namespace tc3 {
+
+constexpr int D2 = 9, D4 = 81;
+constexpr int PC = 4;                         // cubature points per chunk
+constexpr int NCOLS = 64;                     // MMA N (n padded to 64)
+constexpr int GS_BYTES = PC * D2 * NCOLS * 4; // FP32 basis chunk [PC][9][64]
+constexpr unsigned long long WAIT_NS = 1000000000ull;   // 1 s per wait
+
+template <int MODE>
+struct Cfg {
+    static constexpr bool SPLIT = MODE == 3;
+    static constexpr int ES = MODE == 1 ? 2 : 4;            // operand element bytes
+    static constexpr int KP = MODE == 1 ? 16 : 12;          // K slots per point
+    static constexpr int CW = 16 / ES;                      // elements per core-matrix row
+    static constexpr int KSTEP = MODE == 1 ? 16 : 8;        // K per tcgen05.mma
+    static constexpr int NP = MODE == 1 ? 4 : (MODE == 2 ? 2 : 1);   // instance pairs per CTA
+    static constexpr int NI = 2 * NP;
+    static constexpr int JT = MODE == 1 ? 8 : 4;            // basis columns per producer thread
+    static constexpr int TPI = NCOLS / JT;                  // threads per (instance, point)
+    static constexpr int NPROD = NI * PC * TPI;
+    static constexpr int THREADS = NPROD + 32;
+    static constexpr int KC = PC * KP;
+    static constexpr int NKB = KC / CW;                     // core blocks along K
+    static constexpr int SBO_A = NKB * 128 + 16;
+    static constexpr int A_BYTES = 16 * SBO_A;
+    static constexpr int SBO_B = NKB * 128;
+    static constexpr int B_BYTES = 8 * SBO_B;
+    static constexpr int NK = KC / KSTEP;
+    static constexpr int NAT = NP * (SPLIT ? 2 : 1);
+    static constexpr int NBT = SPLIT ? 2 : 1;
+    static constexpr int STAGE = NAT * A_BYTES + NBT * B_BYTES + GS_BYTES;
+    static constexpr int AS_BYTES = NI * D4 * PC * 4;
+    static constexpr int SMEM = 2 * STAGE + 2 * AS_BYTES;
+    // accumulators: the tensor core adds into FP32 with truncation, so the error of a long
+    // chain of MMAs grows with its length; chunk c of pair p goes to accumulator c % NH, and in
+    // the split mode the small A_lo B_hi + A_hi B_lo terms go to one more accumulator (NL = 1)
+    static constexpr int NL = SPLIT ? 1 : 0;
+    static constexpr int NH = 512 / (NP * NCOLS) - NL;
+    static constexpr int NACC = NH + NL;
+    static constexpr int TMEM_COLS = 512;
+    static constexpr uint32_t IDESC = (1u << 4) | ((MODE == 1 ? 1u : 2u) << 7) | ((MODE == 1 ? 1u : 2u) << 10) |
+                                      ((uint32_t)(NCOLS >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long now_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;          // descriptor version for tcgen05; no swizzle, base offset 0
+    return d;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred P1;\n mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n selp.b32 %0, 1, 0, P1;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// bounded wait; gives up early when another thread of the CTA has raised the abort flag
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+    if (mbar_test(bar, parity)) return true;
+    const unsigned long long t0 = now_ns();
+    for (;;) {
+        if (mbar_test(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (now_ns() - t0 > WAIT_NS) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+// named barrier over the producer warps with an OR reduction (uniform abort decision)
+__device__ __forceinline__ int bar_or(int nthreads, int pred) {
+    int r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.b32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.b32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"(pred), "r"(nthreads)
+        : "memory");
+    return r;
+}
+
+__device__ __forceinline__ uint32_t tf32_bits(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+template <int MODE>
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+    constexpr uint32_t IDESC = Cfg<MODE>::IDESC;
+    if (MODE == 1) {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                tmem_d),
+            "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(acc));
+    } else {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                tmem_d),
+            "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(acc));
+    }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// image offsets (bytes) inside the per-model image buffer
+struct ImgLayout {
+    size_t g32, bf16, tf_hi, tf_lo, total;
+    int nch;
+};
+
+__host__ __device__ inline ImgLayout img_layout(int m) {
+    ImgLayout L;
+    L.nch = (m + PC - 1) / PC;
+    L.g32 = 0;
+    L.bf16 = L.g32 + (size_t)L.nch * GS_BYTES;
+    L.tf_hi = L.bf16 + (size_t)L.nch * Cfg<1>::B_BYTES;
+    L.tf_lo = L.tf_hi + (size_t)L.nch * Cfg<2>::B_BYTES;
+    L.total = L.tf_lo + (size_t)L.nch * Cfg<2>::B_BYTES;
+    return L;
+}
+
+}  // namespace tc3
+
+template <int MODE>
+__global__ void __launch_bounds__(tc3::Cfg<MODE>::THREADS, 1)
+    k_assemble_tc3(Model M, Batch Bt, const unsigned char *__restrict__ img, int *err_flag, int sel) {
+    using namespace tc3;
+    using C = Cfg<MODE>;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar_full[2], bar_afull[2], bar_mma[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int64_t bI[C::NI];
+    __shared__ volatile int abort_s;
+    __shared__ int n_sel;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n_act = Bt.counts[0];
+    const int p0 = C::NI * blockIdx.x;
+    if (p0 >= n_act) return;
+    const int n = M.n, m = M.m, mA = M.mA;
+    const ImgLayout L = img_layout(m);
+    const int nch = L.nch;
+    const float *At = reinterpret_cast<const float *>(Bt.At);
+    const unsigned char *img_g32 = img + L.g32;
+    const unsigned char *img_b0 = img + (MODE == 1 ? L.bf16 : L.tf_hi);
+    const unsigned char *img_b1 = img + L.tf_lo;
+    auto stage_ptr = [&](int s) { return smem + (size_t)s * C::STAGE; };
+    auto a_tile = [&](int s, int t) { return stage_ptr(s) + (size_t)t * C::A_BYTES; };
+    auto b_tile = [&](int s, int t) { return stage_ptr(s) + (size_t)C::NAT * C::A_BYTES + (size_t)t * C::B_BYTES; };
+    auto g_tile = [&](int s) {
+        return reinterpret_cast<float *>(stage_ptr(s) + (size_t)C::NAT * C::A_BYTES + (size_t)C::NBT * C::B_BYTES);
+    };
+    float *As[2] = {reinterpret_cast<float *>(smem + 2 * (size_t)C::STAGE),
+                    reinterpret_cast<float *>(smem + 2 * (size_t)C::STAGE + C::AS_BYTES)};
+
+    // sel: 0 every listed instance, 1 those without the accurate-stiffness flag, 2 those with it
+    if (tid == 0) n_sel = 0;
+    __syncthreads();
+    if (tid < C::NI) {
+        int64_t b = -1;
+        if (p0 + tid < n_act) {
+            b = Bt.list[p0 + tid];
+            if (sel != 0 && ((Bt.ctl[b].acc_k != 0) != (sel == 2))) b = -1;
+        }
+        bI[tid] = b;
+        if (b >= 0) atomicAdd(&n_sel, 1);
+    }
+    __syncthreads();
+    if (n_sel == 0) return;
+    if (warp == C::NPROD / 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(C::TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&bar_full[s], 1);
+            mbar_init(&bar_afull[s], C::NPROD);
+            mbar_init(&bar_mma[s], 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_s = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+
+    if (tid < C::NPROD) {
+        // ------------------------------------------------------------------ producers
+        const int jb = tid % C::TPI, pi = tid / C::TPI;
+        const int inst = pi / PC, pt = pi % PC;
+        const int pair = inst >> 1, half = inst & 1;
+        const bool inst_ok = bI[inst] >= 0;
+        auto prefetch = [&](int c, int buf) {
+            const int c0 = c * PC;
+            for (int e = tid; e < C::NI * D4; e += C::NPROD) {
+                const int ie = e / D4, ce = e - ie * D4;
+                const int64_t be = bI[ie];
+                if (be >= 0) cp_async16(As[buf] + (size_t)e * PC, At + ((size_t)be * D4 + ce) * mA + c0);
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        prefetch(0, 0);
+        int local_abort = 0;
+        for (int c = 0; c < nch; ++c) {
+            const int s = c & 1;
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            if (bar_or(C::NPROD, local_abort | abort_s)) break;   // also: chunk c's tangents visible
+            if (c + 1 < nch) prefetch(c + 1, (c + 1) & 1);
+            const uint32_t par = (uint32_t)(c >> 1) & 1u;
+            if (!mbar_wait(&bar_full[s], par, &abort_s)) { local_abort = 1; continue; }
+            if (c >= 2 && !mbar_wait(&bar_mma[s], par ^ 1u, &abort_s)) { local_abort = 1; continue; }
+            float a[D4];
+            const bool pt_ok = inst_ok && (c * PC + pt < m);
+            const float *asrc = As[c & 1] + (size_t)inst * D4 * PC + pt;
+#pragma unroll
+            for (int e = 0; e < D4; ++e) a[e] = pt_ok ? asrc[e * PC] : 0.f;
+            const float *Gs = g_tile(s);
+            unsigned char *Ahi = a_tile(s, C::SPLIT ? 2 * pair : pair);
+            unsigned char *Alo = a_tile(s, C::SPLIT ? 2 * pair + 1 : pair);
+#pragma unroll
+            for (int q4 = 0; q4 < C::JT / 4; ++q4) {
+                const int j0 = q4 * 4 * C::TPI + jb * 4;
+                float4 g[D2];
+#pragma unroll
+                for (int q = 0; q < D2; ++q) g[q] = *reinterpret_cast<const float4 *>(Gs + (pt * D2 + q) * NCOLS + j0);
+                float y[D2][4];
+#pragma unroll
+                for (int cc = 0; cc < D2; ++cc) {
+                    float y0 = 0.f, y1 = 0.f, y2 = 0.f, y3 = 0.f;
+#pragma unroll
+                    for (int q = 0; q < D2; ++q) {
+                        const float av = a[q * D2 + cc];   // Y = At^T G: K[j][l] = sum G[q][j] At[q][cc] G[cc][l]
+                        y0 = fmaf(av, g[q].x, y0);
+                        y1 = fmaf(av, g[q].y, y1);
+                        y2 = fmaf(av, g[q].z, y2);
+                        y3 = fmaf(av, g[q].w, y3);
+                    }
+                    y[cc][0] = y0; y[cc][1] = y1; y[cc][2] = y2; y[cc][3] = y3;
+                }
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    const int r = half * 64 + j0 + jj;
+                    const size_t rb = (size_t)(r >> 3) * C::SBO_A + (size_t)(r & 7) * 16;
+                    if (MODE == 1) {
+                        uint4 v0, v1;
+                        v0.x = pack_bf16(y[0][jj], y[1][jj]); v0.y = pack_bf16(y[2][jj], y[3][jj]);
+                        v0.z = pack_bf16(y[4][jj], y[5][jj]); v0.w = pack_bf16(y[6][jj], y[7][jj]);
+                        v1.x = pack_bf16(y[8][jj], 0.f); v1.y = 0u; v1.z = 0u; v1.w = 0u;
+                        *reinterpret_cast<uint4 *>(Ahi + rb + (size_t)(2 * pt) * 128) = v0;
+                        *reinterpret_cast<uint4 *>(Ahi + rb + (size_t)(2 * pt + 1) * 128) = v1;
+                    } else {
+                        uint32_t h[D2];
+#pragma unroll
+                        for (int cc = 0; cc < D2; ++cc) h[cc] = tf32_bits(y[cc][jj]);
+                        *reinterpret_cast<uint4 *>(Ahi + rb + (size_t)(3 * pt) * 128) = make_uint4(h[0], h[1], h[2], h[3]);
+                        *reinterpret_cast<uint4 *>(Ahi + rb + (size_t)(3 * pt + 1) * 128) = make_uint4(h[4], h[5], h[6], h[7]);
+                        *reinterpret_cast<uint4 *>(Ahi + rb + (size_t)(3 * pt + 2) * 128) = make_uint4(h[8], 0u, 0u, 0u);
+                        if (C::SPLIT) {
+                            uint32_t l[D2];
+#pragma unroll
+                            for (int cc = 0; cc < D2; ++cc) l[cc] = tf32_bits(y[cc][jj] - __uint_as_float(h[cc]));
+                            *reinterpret_cast<uint4 *>(Alo + rb + (size_t)(3 * pt) * 128) = make_uint4(l[0], l[1], l[2], l[3]);
+                            *reinterpret_cast<uint4 *>(Alo + rb + (size_t)(3 * pt + 1) * 128) = make_uint4(l[4], l[5], l[6], l[7]);
+                            *reinterpret_cast<uint4 *>(Alo + rb + (size_t)(3 * pt + 2) * 128) = make_uint4(l[8], 0u, 0u, 0u);
+                        }
+                    }
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(&bar_afull[s]);
+        }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+    } else if (lane == 0) {
+        // ------------------------------------------------------------- control thread
+        int copy_pending[2] = {0, 0};
+        uint32_t copy_par[2] = {0, 0};
+        int mma_pending = 0;
+        uint32_t mma_par = 0;
+        int mma_stage = 0;
+        auto issue_copies = [&](int c) {
+            const int s = c & 1;
+            const uint32_t bytes = GS_BYTES + C::NBT * C::B_BYTES;
+            mbar_expect_tx(&bar_full[s], bytes);
+            bulk_g2s(g_tile(s), img_g32 + (size_t)c * GS_BYTES, GS_BYTES, &bar_full[s]);
+            bulk_g2s(b_tile(s, 0), img_b0 + (size_t)c * C::B_BYTES, C::B_BYTES, &bar_full[s]);
+            if (C::SPLIT) bulk_g2s(b_tile(s, 1), img_b1 + (size_t)c * C::B_BYTES, C::B_BYTES, &bar_full[s]);
+            copy_pending[s] = 1;
+            copy_par[s] = (uint32_t)(c >> 1) & 1u;
+        };
+        issue_copies(0);
+        if (nch > 1) issue_copies(1);
+        for (int c = 0; c < nch; ++c) {
+            const int s = c & 1;
+            const uint32_t par = (uint32_t)(c >> 1) & 1u;
+            if (!mbar_wait(&bar_full[s], par, &abort_s)) break;
+            copy_pending[s] = 0;
+            if (!mbar_wait(&bar_afull[s], par, &abort_s)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int ah_idx = c % C::NH;
+#pragma unroll 1
+            for (int p = 0; p < C::NP; ++p) {
+                // accumulator a of pair p: TMEM columns (a * NP + p) * 64
+                const uint32_t dh = tmem + (uint32_t)((ah_idx * C::NP + p) * NCOLS);
+                const uint32_t dl = tmem + (uint32_t)((C::NH * C::NP + p) * NCOLS);
+                const uint32_t ah = smem_u32(a_tile(s, C::SPLIT ? 2 * p : p));
+                const uint32_t bh = smem_u32(b_tile(s, 0));
+#pragma unroll
+                for (int k = 0; k < C::NK; ++k) {
+                    const uint64_t adh = make_desc(ah + k * 256, 128, C::SBO_A);
+                    const uint64_t bdh = make_desc(bh + k * 256, 128, C::SBO_B);
+                    mma<MODE>(dh, adh, bdh, (c >= C::NH || k > 0) ? 1u : 0u);
+                    if (C::SPLIT) {
+                        const uint32_t al = smem_u32(a_tile(s, 2 * p + 1));
+                        const uint32_t bl = smem_u32(b_tile(s, 1));
+                        mma<MODE>(dl, make_desc(al + k * 256, 128, C::SBO_A), bdh, (c > 0 || k > 0) ? 1u : 0u);
+                        mma<MODE>(dl, adh, make_desc(bl + k * 256, 128, C::SBO_B), 1u);
+                    }
+                }
+            }
+            mma_commit(&bar_mma[s]);
+            mma_pending = 1;
+            mma_par = par;
+            mma_stage = s;
+            if (c + 2 < nch) {
+                if (!mbar_wait(&bar_mma[s], par, &abort_s)) break;
+                issue_copies(c + 2);
+            }
+        }
+        // drain: the last commit covers every MMA issued before it; outstanding copies must land
+        if (mma_pending && !mbar_wait(&bar_mma[mma_stage], mma_par, &abort_s)) {
+            // a second bounded wait that ignores the abort flag: the MMAs read shared memory
+            const unsigned long long t0 = now_ns();
+            while (!mbar_test(&bar_mma[mma_stage], mma_par) && now_ns() - t0 < WAIT_NS) {}
+        }
+        for (int s = 0; s < 2; ++s)
+            if (copy_pending[s]) {
+                const unsigned long long t0 = now_ns();
+                while (!mbar_test(&bar_full[s], copy_par[s]) && now_ns() - t0 < WAIT_NS) {}
+            }
+        if (abort_s && err_flag) atomicExch(err_flag, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!abort_s && tid < C::NPROD) {
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 of the pairs p = w / 4 (mod NPROD / 128)
+        const int quad = warp & 3;
+        const int row = quad * 32 + lane;
+        const int ih = row >> 6, j = row & 63;
+        const int n_used = (nch < C::NH ? nch : C::NH) + C::NL;   // accumulators written
+        for (int p = warp >> 2; p < C::NP; p += C::NPROD / 128) {
+            double v[64];
+#pragma unroll
+            for (int q = 0; q < 64; ++q) v[q] = 0.0;
+#pragma unroll 1
+            for (int ai = 0; ai < C::NACC; ++ai) {
+                if (ai < C::NH && ai >= n_used - C::NL) continue;   // hi accumulator never written
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)((ai * C::NP + p) * NCOLS + hh * 32);
+                uint32_t r[32];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                      "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                      "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                      "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int q = 0; q < 32; ++q) v[hh * 32 + q] += (double)__uint_as_float(r[q]);
+            }
+            }
+            const int64_t b = bI[2 * p + ih];
+            if (j < n && b >= 0) {
+                double *Kb = Bt.K + (size_t)b * n * n + (size_t)j * n;
+#pragma unroll
+                for (int k = 0; k < NCOLS; ++k)
+                    if (k < n) Kb[k] = v[k];
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == C::NPROD / 32) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS));
+    }
+}
+
+__global__ void k_force(Model M, Batch Bt);
+
+// ------------------------------------------------------------------------ host side
+
+size_t tc3_image_bytes(int m) { return tc3::img_layout(m).total; }
+
+static float tf32_round_host(float x) {
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x1000u) & ~0x1FFFu;   // nearest, ties away (cvt.rna)
+    float r;
+    memcpy(&r, &u, 4);
+    return r;
+}
+
+// B-operand images of G[m][9][n] (n <= 64) and the zero-padded FP32 basis chunks, one buffer
+void tc3_build_images(int n, int m, const double *G, unsigned char *img) {
+    using namespace tc3;
+    const ImgLayout L = img_layout(m);
+    memset(img, 0, L.total);
+    float *g32 = reinterpret_cast<float *>(img + L.g32);
+    for (int i = 0; i < m; ++i)
+        for (int q = 0; q < D2; ++q)
+            for (int j = 0; j < n; ++j) g32[((size_t)i * D2 + q) * NCOLS + j] = (float)G[((size_t)i * D2 + q) * n + j];
+    for (int c = 0; c < L.nch; ++c)
+        for (int l = 0; l < n; ++l)
+            for (int pt = 0; pt < PC; ++pt) {
+                const int i = c * PC + pt;
+                if (i >= m) continue;
+                for (int q = 0; q < D2; ++q) {
+                    const double g = G[((size_t)i * D2 + q) * n + l];
+                    {   // BF16, KP = 16
+                        using C1 = Cfg<1>;
+                        const int k = pt * C1::KP + q;
+                        const size_t off = (size_t)c * C1::B_BYTES + (size_t)(l >> 3) * C1::SBO_B + (size_t)(k >> 3) * 128 +
+                                           (size_t)(l & 7) * 16 + (size_t)(k & 7) * 2;
+                        const __nv_bfloat16 h = __float2bfloat16((float)g);
+                        memcpy(img + L.bf16 + off, &h, 2);
+                    }
+                    {   // TF32 hi / lo, KP = 12
+                        using C2 = Cfg<2>;
+                        const int k = pt * C2::KP + q;
+                        const size_t off = (size_t)c * C2::B_BYTES + (size_t)(l >> 3) * C2::SBO_B + (size_t)(k >> 2) * 128 +
+                                           (size_t)(l & 7) * 16 + (size_t)(k & 3) * 4;
+                        const float f = (float)g;
+                        const float hi = tf32_round_host(f);
+                        const float lo = tf32_round_host(f - hi);
+                        memcpy(img + L.tf_hi + off, &hi, 4);
+                        memcpy(img + L.tf_lo + off, &lo, 4);
+                    }
+                }
+            }
+}
+
+template <int MODE>
+static int launch_tc3_t(const Model &M, Batch Bt, const unsigned char *img, int *err, int sel, cudaStream_t s) {
+    using C = tc3::Cfg<MODE>;
+    if (M.d != 3 || M.n > tc3::NCOLS || (M.mA & 3)) return -1;
+    cudaFuncSetAttribute(k_assemble_tc3<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    const int grid = (int)((Bt.B + C::NI - 1) / C::NI);
+    k_assemble_tc3<MODE><<<grid, C::THREADS, C::SMEM, s>>>(M, Bt, img, err, sel);
+    return 0;
+}
+
+// mode 1 BF16, 2 TF32, 3 TF32 split (FP32-accurate); sel 0 = all listed instances, 1 = those
+// without, 2 = those with the accurate-stiffness flag (Ctl::acc_k); with_force also launches the
+// FP64 force for every listed instance
+int launch_tc3(int mode, const Model &M, Batch Bt, const unsigned char *img, int *err, int sel, bool with_force,
+               cudaStream_t s) {
+    int r = mode == 1 ? launch_tc3_t<1>(M, Bt, img, err, sel, s)
+          : mode == 2 ? launch_tc3_t<2>(M, Bt, img, err, sel, s)
+          : mode == 3 ? launch_tc3_t<3>(M, Bt, img, err, sel, s) : -1;
+    if (r == 0 && with_force) k_force<<<(int)Bt.B, 256, 0, s>>>(M, Bt);
+    return r;
+}
+
+}  // namespace podecm

@@ -1,6 +1,8 @@
 """Tensor-core (tcgen05) stiffness assembly: K in TF32/BF16 vs the FP32 CUDA-core
 assembly on the same tangent, and converged answers of the mixed-precision path vs
 the FP64 oracle (the inexact Jacobian changes iteration counts, not the answer)."""
+import os
+
 import numpy as np
 import pytest
 
@@ -53,3 +55,42 @@ def test_tc_converged_answer(prec):
     its = np.array(its)
     print(prec, "mean Newton iterations (mixed, FP64 oracle):", its.mean(0))
     g.close()
+
+
+def first_pass_K_At(rom, coef, F, precision):
+    g = GpuRun(rom, coef)
+    g.step(F, tol_rel=1e-9, tol_abs=rom["tol_abs"], max_iter=0, precision=precision)
+    K = g.st.stiffness()
+    At = g.st.tangent(precision == "fp64")
+    g.close()
+    return K, At
+
+
+def stiffness_from_tangent(G, At):
+    """K_b = sum_i G_i^T At_i G_i in FP64 from the tangent the kernels used (At [B, d^4, m])."""
+    m, d2, n = G.shape
+    A = At.astype(np.float64).reshape(len(At), d2, d2, m)
+    Y = np.einsum("baci,icl->bial", A, G, optimize=True)
+    return np.einsum("iaj,bial->bjl", G, Y, optimize=True)
+
+
+@pytest.mark.skipif(not os.path.exists(os.path.join(workload.DATA, "rom_c3.npz")), reason="3D model file not generated")
+@pytest.mark.parametrize("B", [3, 37])
+def test_tc3_stiffness(B):
+    """3D model (n = 64, m = 600): K of the first Newton pass from the 3D tensor-core kernel (BF16,
+    TF32, and the TF32 hi/lo split used for FP32 precision) vs K = sum_i G_i^T At_i G_i evaluated
+    in FP64 from the same FP32 tangent; B = 37 leaves partly filled CTAs (8, 4 and 2 instances
+    per CTA).  The FP64 path's K is printed for reference (it also differs by the FP32 tangent)."""
+    rom, mu, coef, paths = workload.batch("c3", B=B)
+    F = paths[:, 3]
+    K64, _ = first_pass_K_At(rom, coef, F, "fp64")
+    errs = {}
+    for prec, tol in (("fp32", 2e-5), ("tf32", 1e-3), ("bf16", 5e-3)):
+        K, At = first_pass_K_At(rom, coef, F, prec)
+        Kref = stiffness_from_tangent(rom["G"], At)
+        err = np.linalg.norm(K - Kref, axis=(1, 2)) / np.linalg.norm(Kref, axis=(1, 2))
+        e64 = np.linalg.norm(K - K64, axis=(1, 2)) / np.linalg.norm(K64, axis=(1, 2))
+        print("c3 B=%d %s max rel Frobenius error of K: %.3e (vs FP64-path K: %.3e)" % (B, prec, err.max(), e64.max()))
+        errs[prec] = (np.isfinite(K).all(), err.max(), tol)
+    for prec, (fin, e, tol) in errs.items():
+        assert fin and e <= tol, (prec, e)
