@@ -32,7 +32,12 @@ sys.path.insert(0, ROOT)
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz (unit count and clock of the recipe)
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12      # 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12    # 152 SMs x 128 FFMA/clk x 2 FLOP x 2.07 GHz
+# executed FP64 FLOPs (2 x DFMA + DMUL + DADD, SASS thread counters of one ncu capture) per
+# cubature point and evaluation of the constitutive kernel (kinematics, return map, P, pull-backs;
+# the tangent runs in FP32 on the mixed paths, in FP64 on the FP64 path)
+CONST_FP64_FLOP_PER_POINT = {(3, "mixed"): 2679.0, (2, "fp64"): 2288.0}
 
 
 def parse():
@@ -115,9 +120,9 @@ def load_workload(args, first=0, B=None):
 
 
 def solver_opts(args, rom):
-    # default: FP64 residual, kinematics, return map, eigen log/exp and solve; FP32 tangent and
-    # stiffness (the converged Pbar is within 1e-7 of the FP64 oracle -- tests/test_gpu_parity_c2.py)
-    prec = args.precision or "fp32"
+    # default: FP64 residual, kinematics, return map, eigen log/exp and solve; the 3D stiffness in
+    # TF32 on the tensor cores, the 2D stiffness in FP32 on the CUDA cores
+    prec = args.precision or ("tf32" if args.workload == "c3" else "fp32")
     tol_rel = 1e-10 if prec == "fp64" else 1e-9
     max_iter = 25 if prec == "fp64" else 50
     return prec, dict(tol_rel=tol_rel, tol_abs=rom["tol_abs"], max_iter=max_iter, max_ls=6, precision=prec,
@@ -210,7 +215,8 @@ def run_ours(args, rank, world):
     launches = sum(v[1] for v in groups.values())
     res = dict(value=value, ms=ms, n_ok=n_ok, n_total=len(info), iters_mean=float(info["iters"].mean()),
                evals_mean=float(info["evals"].mean()), prof=groups, dom=dom, launches=launches, clocks=clk,
-               prec=prec, B=B, W=W, K=K, graphs=graphs, ms_profiled=ms_prof, clocks_profiled=clk_prof)
+               prec=prec, B=B, W=W, K=K, graphs=graphs, ms_profiled=ms_prof, clocks_profiled=clk_prof,
+               workload=args.workload)
     # end-to-end through the public host-buffer call (H2D of Fbar, D2H of Pbar, Abar, info each step)
     if not args.no_e2e:
         ctx.use_graphs(False)
@@ -291,6 +297,47 @@ def cpu_baseline(args, n_inst=None, n_steps=None, budget_s=20.0):
                 sample="%d instances x first %d load steps of the %s workload (%.1f s)" % (B, done, args.workload, t))
 
 
+
+def kernel_rooflines(r, peaks):
+    """Achieved rate of each timed kernel group against the peak of the unit that bounds it (the
+    FLOP counts are the library's per-launch algorithmic counts; the constitutive group's FP64
+    FLOPs are points evaluated x CONST_FP64_FLOP_PER_POINT)."""
+    from paper_2307_16894_gb300 import workload
+    rom = workload.load_model(workload.WORKLOADS[r["workload"]]["model"])
+    d, n, m = rom["d"], rom["n"], rom["m"]
+    prof, prec = r["prof"], r["prec"]
+    tot = sum(v[0] for v in prof.values())
+    bf16 = peaks.get("bf16_tflops", 1900.0)
+    src = "MEASURED_PEAKS.json" if "bf16_tflops" in peaks else "fallback 1.9 PFLOP/s"
+    out = {}
+
+    def add(name, bound, flops, peak, peak_source):
+        ms = prof[name][0]
+        if ms <= 0 or flops <= 0:
+            return
+        a = flops / (ms / 1e3) / 1e12
+        out[name] = dict(kernel=name, bound=bound, achieved=a, peak=peak, unit="TFLOP/s", frac=a / peak,
+                         traffic=None, share=ms / tot, peak_source=peak_source)
+
+    kin = 2.0 * m * d * d * n
+    points = prof["constitutive"][2] / kin * m
+    key = (d, "fp64" if prec == "fp64" else "mixed")
+    if key in CONST_FP64_FLOP_PER_POINT:
+        add("constitutive", "alu", points * CONST_FP64_FLOP_PER_POINT[key], FP64_PEAK_TFLOPS,
+            "FP64 pipe: 152 SM x 2 DFMA/clk x 2 FLOP x 2.07 GHz")
+    tc = (d == 3 and n <= 64 and prec != "fp64") or prec in ("tf32", "bf16")
+    if tc:
+        pk = bf16 * (1.0 if prec == "bf16" else 0.5)
+        add("assemble", "tensor", prof["assemble"][2], pk,
+            src + " bf16_tflops" + ("" if prec == "bf16" else " x 0.5 (TF32 rate)"))
+        add("force", "alu", prof["force"][2], FP64_PEAK_TFLOPS, "FP64 pipe")
+    elif prec == "fp64":
+        add("assemble", "alu", prof["assemble"][2], FP64_PEAK_TFLOPS, "FP64 pipe")
+    else:
+        add("assemble", "alu", prof["assemble"][2], FP32_PEAK_TFLOPS, "FP32 pipe: 152 SM x 128 FFMA/clk x 2 x 2.07 GHz")
+    add("solve", "alu", prof["solve"][2], FP64_PEAK_TFLOPS, "FP64 pipe")
+    return out
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -328,23 +375,9 @@ def main():
     peaks = {}
     if os.path.exists(PEAKS_FILE):
         peaks = json.load(open(PEAKS_FILE))
-    ms_dom, ln_dom, fl_dom = r["prof"][r["dom"]]
-    share = ms_dom / sum(v[0] for v in r["prof"].values())
-    if r["dom"] in ("assemble", "constitutive", "solve") and fl_dom > 0:
-        achieved = fl_dom / (ms_dom / 1e3) / 1e12
-        if r["dom"] == "assemble" and r["prec"] in ("tf32", "bf16"):
-            # tensor-core contraction: measured BF16 dense peak (TF32 at half of it, the nominal ratio)
-            pk = peaks.get("bf16_tflops", 1900.0) * (1.0 if r["prec"] == "bf16" else 0.5)
-            roof = dict(kernel=r["dom"], bound="tensor", achieved=achieved, peak=pk, unit="TFLOP/s",
-                        frac=achieved / pk, traffic=None, share=share,
-                        peak_source="MEASURED_PEAKS.json bf16_tflops" + (" x 0.5 (tf32)" if r["prec"] == "tf32" else ""))
-        else:
-            roof = dict(kernel=r["dom"], bound="alu", achieved=achieved, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
-                        frac=achieved / FP64_PEAK_TFLOPS, traffic=None, share=share,
-                        peak_source="FP64 pipe: 152 SM x 2 DFMA/clk x 2 FLOP x 2.07 GHz")
-    else:
-        roof = dict(kernel=r["dom"], bound="alu", achieved=None, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s", frac=None,
-                    traffic=None, share=share)
+    rooflines = kernel_rooflines(r, peaks)
+    roof = rooflines.get(r["dom"]) or dict(kernel=r["dom"], bound="alu", achieved=None, peak=FP64_PEAK_TFLOPS,
+                                            unit="TFLOP/s", frac=None, traffic=None)
     wl = {"c2": "2D porous RVE 64x64 Q4, n=24, m=160, B=4096, 50-step paths",
           "c3": "3D inclusion RVE 24^3 hex8, n=64, m=600, B=16384, 50-step paths"}[args.workload]
     line = dict(metric=metric, value=r["value"], unit=unit, n_gpus=world, steps=args.steps, warmup=args.warmup,
@@ -355,7 +388,7 @@ def main():
                             step_driver="CUDA graph, device-driven Newton loop" if r["graphs"] else "host-driven passes",
                             l2="flushed between timed steps (256 MB write)", converged=r["n_ok"],
                             total=r["n_total"], newton_iters_mean=r["iters_mean"], evals_mean=r["evals_mean"]),
-                roofline=roof, clocks=r["clocks"], gpu_launches=int(r["launches"]),
+                roofline=roof, rooflines=rooflines, clocks=r["clocks"], gpu_launches=int(r["launches"]),
                 profiled_ms_per_step=r["ms_profiled"] / args.steps,
                 kernels={k: dict(ms=v[0], launches=v[1], gflop=v[2] / 1e9) for k, v in r["prof"].items()})
     if "e2e" in r:

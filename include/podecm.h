@@ -164,12 +164,14 @@ const char *rom_last_error(const rom_ctx *ctx);
  * CUDA events around every kernel launch of later steps on the context stream;
  * rom_profile(ctx, 0) stops.  rom_profile_read returns, for kernel group
  * 0 start, 1 constitutive (kinematics, return map, tangent), 2 assembly
- * (force and stiffness), 3 solve (convergence test, line search, LU),
- * 4 finalize (Pbar, Abar, commit), 5 bookkeeping, 6 learned start (features, MLP
- * inference): the summed device time in ms,
- * the number of kernel launches and the algorithmic FLOPs (kernel groups 1-3:
- * kinematics 2 m d^2 n; assembly 2 m d^4 n + m d^2 n (n+1) + 2 m d^2 n; solve
- * 2 n^3/3 + 2 n^2 -- per active instance and launch).  Any pointer may be NULL. */
+ * (stiffness; on the CUDA-core path also the force), 3 solve (convergence test, line
+ * search, LU), 4 finalize (Pbar, Abar, commit), 5 bookkeeping, 6 learned start
+ * (features, MLP inference), 7 force (FP64 residual, on the tensor-core paths): the
+ * summed device time in ms, the number of kernel launches and the algorithmic FLOPs
+ * (per active instance and launch: group 1 kinematics 2 m d^2 n; group 2 on the
+ * tensor cores 2 m d^4 n + 2 m d^2 n^2 (Y = At G and the full K), on the CUDA cores
+ * 2 m d^4 n + m d^2 n (n+1) + 2 m d^2 n (upper triangle of K and the force); group 3
+ * 2 n^3/3 + 2 n^2; group 7 2 m d^2 n).  Any pointer may be NULL. */
 rom_status rom_profile(rom_ctx *ctx, int enable);
 
 /* Device bytes of a state of B instances (history and per-step work arrays) -- the
@@ -221,12 +223,16 @@ rom_status rom_profile_read(rom_ctx *ctx, int kernel, double *ms, int64_t *launc
  * start is a_n + da_{k-1} + correction.  Inference uses BF16 weights with FP32
  * accumulation; training keeps an FP32 master copy updated by Adam (beta = 0.9, 0.999,
  * eps = 1e-8) on the mean squared error of the standardised targets.  With
- * opts->start = ROM_START_MLP, rom_step evaluates the residual at the learned start and
- * at the previous-step predictor a_n + (a_n - a_{n-1}) and starts Newton from the
- * smaller one (one extra residual evaluation, counted in evals); the converged answer
- * does not depend on the start.  In this mode the convergence tolerance is relative to
- * the residual of the previous-step predictor (the fallback) whichever start is taken,
- * so both starts are held to the same absolute residual.
+ * opts->start = ROM_START_MLP, rom_step evaluates the residual at the learned start; if
+ * it is finite and at most r_ref, the residual of the previous-step predictor
+ * a_n + (a_n - a_{n-1}) of the instance's last step that evaluated one, Newton starts
+ * from it; otherwise rom_step also evaluates the previous-step predictor (the fallback;
+ * one extra residual evaluation, counted in evals), stores its residual as the new r_ref
+ * and starts from the smaller of the two.  r_ref is +inf after rom_state_create or an
+ * import of a, so the first learned step always evaluates both; steps with
+ * ROM_START_PREV also refresh it.  The converged answer does not depend on the start.
+ * In this mode the convergence tolerance is relative to r_ref (or to the fallback's
+ * residual when it is evaluated), so both starts are held to the same absolute residual.
  *
  * rom_mlp_init: allocate an MLP (random parameters are set by rom_mlp_params);
  *   max_rows = largest batch of rows of any later train/grad/predict call.

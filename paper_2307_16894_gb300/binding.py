@@ -29,7 +29,7 @@ EXPORTED = ["rom_create", "rom_destroy", "rom_load_basis", "rom_load_cubature", 
             "rom_debug_tangent", "rom_use_graphs",
             "rom_state_bytes", "rom_autotune", "rom_serve"]
 
-KERNEL_GROUPS = ["start", "constitutive", "assemble", "solve", "finalize", "bookkeeping", "learned_start"]
+KERNEL_GROUPS = ["start", "constitutive", "assemble", "solve", "finalize", "bookkeeping", "learned_start", "force"]
 
 
 class RomPhase(ctypes.Structure):

@@ -14,6 +14,7 @@
 // and k_finalize computes Pbar (Eq. eff_stress_1), Abar through the Schur
 // complement of the reduced tangent problems (Eqs. tangent_problem_red,
 // eff_stiffness_1) and commits the history of converged instances.
+#include <algorithm>
 #include <cstdio>
 #include "kernels.cuh"
 
@@ -458,6 +459,7 @@ __global__ void __launch_bounds__(32) k_solve(Model M, Batch Bt, StepOpts o, int
     bool keep_dq = false;   // Newton direction already known (learned start chosen)
     if (c.phase == 0 || c.phase == 4) {
         if (c.phase == 4) c.evals += 1;
+        if (c.phase == 0 && o.start == 1 && Bt.r0_prev && lane == 0) Bt.r0_prev[b] = rn;   // previous-step predictor
         c.r0 = rn;
         c.tol = fmax(o.tol_rel * rn, o.tol_abs);
         c.rn_acc = rn;
@@ -465,8 +467,9 @@ __global__ void __launch_bounds__(32) k_solve(Model M, Batch Bt, StepOpts o, int
         for (int j = lane; j < n; j += 32) qa[j] = qt[j];
         accepted = true;
     } else if (c.phase == 2) {
-        // learned start evaluated: keep its residual norm and Newton direction, then
-        // evaluate the previous-step predictor a_n + (a_n - a_{n-1})
+        // learned start evaluated: its Newton direction, then either start from it (its residual is
+        // at most the previous-step predictor's residual of the last step that evaluated one) or
+        // also evaluate the previous-step predictor a_n + (a_n - a_{n-1}) and keep the better start
         c.r0 = rn;
         const double *Kb = Bt.K + (size_t)b * n * n;
         for (int e = lane; e < n * n; e += 32) A[e] = Kb[e];
@@ -474,16 +477,34 @@ __global__ void __launch_bounds__(32) k_solve(Model M, Batch Bt, StepOpts o, int
         __syncwarp();
         const bool ok = isfinite(rn) && warp_lu(A, n, piv);
         if (ok) warp_lu_solve(A, n, piv, x);
-        if (!ok && lane == 0) c.r0 = NAN;
-        for (int j = lane; j < n; j += 32) {
-            dq[j] = ok ? x[j] : 0.0;
-            qa[j] = qt[j];
-            qt[j] = Bt.q_n[b * n + j] + Bt.dq_prev[b * n + j];
+        const double rref = Bt.r0_prev ? Bt.r0_prev[b] : INFINITY;
+        if (ok && rn <= rref) {
+            c.tol = fmax(o.tol_rel * rref, o.tol_abs);
+            c.rn_acc = rn;
+            if (rn <= c.tol || o.max_iter == 0) {
+                c.status = 0;
+                c.active = 0;
+                for (int j = lane; j < n; j += 32) qa[j] = qt[j];
+            } else {
+                c.t = 1.0;
+                c.ls = 0;
+                c.phase = 1;
+                for (int j = lane; j < n; j += 32) { dq[j] = x[j]; qa[j] = qt[j]; qt[j] = qa[j] + x[j]; }
+            }
+            keep_dq = true;
+        } else {
+            if (!ok && lane == 0) c.r0 = NAN;
+            for (int j = lane; j < n; j += 32) {
+                dq[j] = ok ? x[j] : 0.0;
+                qa[j] = qt[j];
+                qt[j] = Bt.q_n[b * n + j] + Bt.dq_prev[b * n + j];
+            }
+            c.r0 = __shfl_sync(0xffffffffu, c.r0, 0);
+            c.phase = 3;
         }
-        c.r0 = __shfl_sync(0xffffffffu, c.r0, 0);
-        c.phase = 3;
     } else if (c.phase == 3) {
         c.evals += 1;
+        if (Bt.r0_prev && lane == 0) Bt.r0_prev[b] = rn;
         const double rm = c.r0;
         if (!(rm <= rn)) {
             // previous-step predictor wins (or the learned start failed)
@@ -621,47 +642,78 @@ __device__ void abar_sums_f64(const Model &M, const Batch &Bt, int64_t b, int CH
     __syncthreads();
 }
 
-// the same sums from the FP32 tangent of the mixed-precision path, in FP32 (B) and FP64 (A0):
-// thread (j = tid % 64 (+64), group = tid / 64) accumulates B[j][0..D2) over the points
-// i = group (mod blockDim / 64) of each chunk; the groups are added in a fixed order.
-// work = Ah [CHF][D4] | Gs [CHF][D2][n] (floats); the group sums reuse Gs.
+// the same sums from the FP32 tangent of the mixed-precision path, in FP32.  The tangent and
+// basis chunks are staged with cp.async one chunk ahead (double-buffered).  Thread
+// (j = tid % 32 (+32, +64, +96), group = tid / 32) accumulates B[j][0..D2) over the points
+// i = group (mod blockDim / 32) of each chunk, and A0 is split over D4-thread point groups; the
+// group sums are added in a fixed order (in FP64).
+// work (floats) = Fm32 [2][CHF][D2] | (16-byte aligned) As [2][D4][CHF] | Gs [2][CHF][D2][n] |
+// Ah [CHF][D4]; the group sums reuse the work area.  CHF must be a multiple of 4.
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async16_f(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+
 template <int D>
 __device__ void abar_sums_f32(const Model &M, const Batch &Bt, int64_t b, int CHF, double *Bm, double *A0,
-                              double *Fm, float *work) {
+                              float *work) {
     constexpr int D2 = D * D, D4 = D2 * D2;
-    const int n = M.n, m = M.m, tid = threadIdx.x;
-    float *Ah = work;
-    float *Gs = Ah + (size_t)CHF * D4;
+    const int n = M.n, m = M.m, mA = M.mA, tid = threadIdx.x;
+    float *Fm32[2] = {work, work + (size_t)CHF * D2};
+    float *abase = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(Fm32[1] + (size_t)CHF * D2) + 15) &
+                                             ~uintptr_t(15));   // cp.async targets: 16-byte aligned
+    float *As[2] = {abase, abase + (size_t)D4 * CHF};
+    float *Gs[2] = {As[1] + (size_t)D4 * CHF, As[1] + (size_t)D4 * CHF + (size_t)CHF * D2 * n};
+    float *Ah = Gs[1] + (size_t)CHF * D2 * n;
     const float *At = reinterpret_cast<const float *>(Bt.At);
-    const int jl = tid & 63, grp = tid >> 6, NGRP = blockDim.x >> 6;
+    const int jl = tid & 31, grp = tid >> 5, NGRP = blockDim.x >> 5;
     const int AG = blockDim.x / D4, ag = tid / D4, ae = tid - ag * D4;   // A0: AG point groups
-    float bacc[2][D2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h)
-#pragma unroll
-        for (int kl = 0; kl < D2; ++kl) bacc[h][kl] = 0.f;
-    float aacc = 0.f;
-    for (int c0 = 0; c0 < m; c0 += CHF) {
-        const int ch = min(CHF, m - c0);
-        __syncthreads();
+    const int nch = (m + CHF - 1) / CHF;
+    auto stage = [&](int c) {
+        const int c0 = c * CHF, ch = min(CHF, m - c0), buf = c & 1;
+        const int q4 = CHF / 4;
+        for (int e = tid; e < D4 * q4; e += blockDim.x) {   // At rows: CHF floats from c0 (inside mA)
+            const int ce = e / q4, qq = e - ce * q4;
+            cp_async16_f(As[buf] + (size_t)ce * CHF + 4 * qq, At + ((size_t)b * D4 + ce) * mA + c0 + 4 * qq);
+        }
+        const int gcount = ch * D2 * n, g4 = gcount >> 2;
+        const float *gsrc = M.G32_pt + (size_t)c0 * D2 * n;
+        for (int e = tid; e < g4; e += blockDim.x) cp_async16_f(Gs[buf] + 4 * e, gsrc + 4 * e);
+        for (int e = 4 * g4 + tid; e < gcount; e += blockDim.x) cp_async4(Gs[buf] + e, gsrc + e);
+        asm volatile("cp.async.commit_group;" ::: "memory");
         for (int e = tid; e < ch * D2; e += blockDim.x) {
             const int ii = e / D2, ar = e - ii * D2;
             const int a = ar / D, r = ar - a * D;
             double s = (a == r) ? 1.0 : 0.0;
             for (int k = 0; k < M.n_par; ++k)
                 s += Bt.mu[b * M.n_par + k] * M.Gmu_T[((size_t)ar * M.n_par + k) * m + c0 + ii];
-            Fm[ii * D2 + ar] = s;
+            Fm32[buf][ii * D2 + ar] = (float)s;
         }
-        for (int e = tid; e < ch * D2 * n; e += blockDim.x)
-            Gs[e] = M.G32_pt[(size_t)c0 * D2 * n + e];
+    };
+    float bacc[4][D2];
+#pragma unroll
+    for (int h = 0; h < 4; ++h)
+#pragma unroll
+        for (int kl = 0; kl < D2; ++kl) bacc[h][kl] = 0.f;
+    float aacc = 0.f;
+    stage(0);
+    for (int c = 0; c < nch; ++c) {
+        const int c0 = c * CHF, ch = min(CHF, m - c0), buf = c & 1;
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
         __syncthreads();
+        if (c + 1 < nch) stage(c + 1);
+        const float *as = As[buf], *fm = Fm32[buf], *gs = Gs[buf];
         for (int e = tid; e < ch * D4; e += blockDim.x) {
             const int ii = e / D4, rem = e - ii * D4;
             const int ar = rem / D2, kl = rem - ar * D2;
             const int k = kl / D, l = kl - k * D;
             float s = 0.f;
-            for (int ss = 0; ss < D; ++ss)
-                s = fmaf(At[((size_t)b * D4 + ar * D2 + k * D + ss) * M.mA + c0 + ii], (float)Fm[ii * D2 + l * D + ss], s);
+#pragma unroll
+            for (int ss = 0; ss < D; ++ss) s = fmaf(as[(ar * D2 + k * D + ss) * CHF + ii], fm[ii * D2 + l * D + ss], s);
             Ah[e] = s;
         }
         __syncthreads();
@@ -672,10 +724,10 @@ __device__ void abar_sums_f32(const Model &M, const Batch &Bt, int64_t b, int CH
 #pragma unroll
                 for (int kl = 0; kl < D2; ++kl) a[kl] = Ah[ii * D4 + ar * D2 + kl];
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int j = jl + 64 * h;
+                for (int h = 0; h < 4; ++h) {
+                    const int j = jl + 32 * h;
                     if (j < n) {
-                        const float g = Gs[(ii * D2 + ar) * n + j];
+                        const float g = gs[(ii * D2 + ar) * n + j];
 #pragma unroll
                         for (int kl = 0; kl < D2; ++kl) bacc[h][kl] = fmaf(g, a[kl], bacc[h][kl]);
                     }
@@ -686,15 +738,15 @@ __device__ void abar_sums_f32(const Model &M, const Batch &Bt, int64_t b, int CH
             const int ij = ae / D2, kl = ae - ij * D2;
             const int ia = ij / D, jb = ij - ia * D;
             for (int ii = ag; ii < ch; ii += AG)
-                for (int r = 0; r < D; ++r)
-                    aacc = fmaf((float)Fm[ii * D2 + jb * D + r], Ah[ii * D4 + (ia * D + r) * D2 + kl], aacc);
+#pragma unroll
+                for (int r = 0; r < D; ++r) aacc = fmaf(fm[ii * D2 + jb * D + r], Ah[ii * D4 + (ia * D + r) * D2 + kl], aacc);
         }
     }
     __syncthreads();
-    float *red = Gs;   // [NGRP][n][D2], then [AG][D4]
+    float *red = work;   // [NGRP][n][D2], then [AG][D4]
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int j = jl + 64 * h;
+    for (int h = 0; h < 4; ++h) {
+        const int j = jl + 32 * h;
         if (j < n)
 #pragma unroll
             for (int kl = 0; kl < D2; ++kl) red[((size_t)grp * n + j) * D2 + kl] = bacc[h][kl];
@@ -724,6 +776,7 @@ __device__ void abar_sums_f32(const Model &M, const Batch &Bt, int64_t b, int CH
 template <typename T>
 __device__ bool block_lu_solve(T *A, int n, T *X, int nrhs, int *s_piv) {
     const int tid = threadIdx.x, nt = blockDim.x;
+    const int tx = tid & 15, ty = tid >> 4, NY = nt >> 4;
     for (int k = 0; k < n; ++k) {
         if (tid < 32) {
             double best = -1.0;
@@ -750,22 +803,19 @@ __device__ bool block_lu_solve(T *A, int n, T *X, int nrhs, int *s_piv) {
         const T akk = A[k * n + k];
         for (int i = k + 1 + tid; i < n; i += nt) A[i * n + k] /= akk;
         __syncthreads();
-        const int w = n - k - 1, wr = w + nrhs;
-        for (int e = tid; e < w * wr; e += nt) {
-            const int i = k + 1 + e / wr, c = e - (e / wr) * wr;
+        // trailing update and forward substitution (16 x nt/16 thread grid)
+        for (int i = k + 1 + ty; i < n; i += NY) {
             const T lik = A[i * n + k];
-            if (c < w) A[i * n + k + 1 + c] -= lik * A[k * n + k + 1 + c];
-            else X[(c - w) * n + i] -= lik * X[(c - w) * n + k];
+            for (int j = k + 1 + tx; j < n; j += 16) A[i * n + j] -= lik * A[k * n + j];
+            for (int r = tx; r < nrhs; r += 16) X[r * n + i] -= lik * X[r * n + k];
         }
         __syncthreads();
     }
     for (int k = n - 1; k >= 0; --k) {
         for (int r = tid; r < nrhs; r += nt) X[r * n + k] /= A[k * n + k];
         __syncthreads();
-        for (int e = tid; e < k * nrhs; e += nt) {
-            const int r = e / k, i = e - r * k;
-            X[r * n + i] -= A[i * n + k] * X[r * n + k];
-        }
+        for (int r = ty; r < nrhs; r += NY)
+            for (int i = tx; i < k; i += 16) X[r * n + i] -= A[i * n + k] * X[r * n + k];
         __syncthreads();
     }
     return true;
@@ -861,7 +911,7 @@ __global__ void __launch_bounds__(256) k_finalize(Model M, Batch Bt, StepOpts o,
         double *Fm = A0 + D4;                                      // [CHF][D2]
         unsigned char *work = reinterpret_cast<unsigned char *>(Fm + (size_t)CHF * D2);
         if (sizeof(TT) == 8) abar_sums_f64<D>(M, Bt, b, CHF, Bm, A0, Fm, reinterpret_cast<double *>(work));
-        else abar_sums_f32<D>(M, Bt, b, CHF, Bm, A0, Fm, reinterpret_cast<float *>(work));
+        else abar_sums_f32<D>(M, Bt, b, CHF, Bm, A0, reinterpret_cast<float *>(Fm));
         // Schur complement with the factor of K at the solution (K* = K)
         if (sizeof(TT) == 8) schur_abar<D, double>(M, Bt, b, Bm, A0, work, AU);
         else schur_abar<D, float>(M, Bt, b, Bm, A0, work, AU);
@@ -1100,16 +1150,24 @@ template <int D>
 static int launch_finalize_t(const Model &M, Batch Bt, const StepOpts &o, double *Pbar, double *Abar, void *info,
                              cudaStream_t s) {
     constexpr int D2 = D * D, D4 = D2 * D2;
-    if ((size_t)M.n * D2 > 1024) return -1;
+    const size_t n = M.n;
+    if (n * D2 > 1024) return -1;
+    const size_t te = o.precision == 0 ? 8 : 4;    // arithmetic of the a11 sums and the Schur solve
     // cubature points per chunk: small chunks keep the shared memory per CTA low (several CTAs per
     // SM hide the latency of this short, barrier-bound kernel)
+    auto bytes = [&](int chf) {
+        const size_t head = (n * D2 + D4 + (size_t)chf * D2) * 8;              // Bm, A0, Fm (FP64 path)
+        // FP64 path: Ah, Gs after Fm; FP32 path: Fm32, As, Gs (double-buffered) and Ah from Fm on
+        const size_t sums = te == 8 ? ((size_t)chf * D4 + (size_t)chf * D2 * n) * 8
+                                    : ((size_t)2 * chf * D2 + 2 * (size_t)D4 * chf + 2 * (size_t)chf * D2 * n +
+                                       (size_t)chf * D4) * 4 + 16 - (size_t)chf * D2 * 8;
+        const size_t red = te == 4 ? (size_t)8 * n * D2 * 4 : 0;              // FP32 group sums
+        const size_t schur = (n * n + n * D2) * te + 16;                      // K factor, RHS, pivot
+        return head + std::max(std::max(sums, red), schur);
+    };
     int CHF = 16;
-    while (CHF > 4 && ((size_t)M.n * D2 + D4 + (size_t)CHF * D2 + (size_t)CHF * D4 + (size_t)CHF * D2 * M.n) * 8 > 48 * 1024)
-        CHF /= 2;
-    size_t sm = ((size_t)M.n * D2 + D4 + (size_t)CHF * D2 + (size_t)CHF * D4 + (size_t)CHF * D2 * M.n) * 8;
-    const size_t sm2 = ((size_t)M.n * D2 + D4 + (size_t)CHF * D2 + (size_t)CHF * D4) * 8 +
-                       ((size_t)M.n * M.n + (size_t)M.n * D2) * 8 + (size_t)M.n * 4 + 16;
-    if (sm2 > sm) sm = sm2;
+    while (CHF > 4 && bytes(CHF) > (te == 8 ? 48 : 64) * 1024) CHF /= 2;
+    const size_t sm = bytes(CHF);
     if (o.precision == 0) {
         cudaFuncSetAttribute(k_finalize<D, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         k_finalize<D, double><<<(int)Bt.B, 256, sm, s>>>(M, Bt, o, Pbar, Abar, info, CHF);

@@ -50,6 +50,8 @@ struct Batch {
     double *K;               // [B][n][n]
     double *Ubar, *Rbar;     // [B][d2]
     double *U_prev;          // [B][d2] stretch of the last converged step (learned start features), may be null
+    double *r0_prev;         // [B] residual norm of the previous-step predictor when last evaluated (+inf
+                             // if never), the reference of the learned start; may be null
 };
 
 // learned Newton start (mlp.cu)

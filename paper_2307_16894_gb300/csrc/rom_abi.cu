@@ -38,8 +38,8 @@ void tc_build_image(int d, int fmt, int n, int m, const double *G, unsigned char
 int launch_tc(int fmt, const Model &M, Batch Bt, const unsigned char *img, int *err, cudaStream_t s);
 size_t tc3_image_bytes(int m);
 void tc3_build_images(int n, int m, const double *G, unsigned char *img);
-int launch_tc3(int mode, const Model &M, Batch Bt, const unsigned char *img, int *err, int sel, bool with_force,
-               cudaStream_t s);
+int launch_tc3(int mode, const Model &M, Batch Bt, const unsigned char *img, int *err, int sel, cudaStream_t s);
+void launch_force(const Model &M, Batch Bt, cudaStream_t s);
 void launch_list_converged(Batch Bt, cudaStream_t s);
 void launch_graph_advance(Batch Bt, const int32_t *list_next, cudaGraphConditionalHandle h, int max_pass,
                           cudaStream_t s);
@@ -49,7 +49,7 @@ void launch_all_active(Batch Bt, cudaStream_t s);
 
 using namespace podecm;
 
-#define ROM_NKERNELS 7
+#define ROM_NKERNELS 8
 
 struct rom_ctx {
     int dim = 0, device = 0;
@@ -73,7 +73,7 @@ struct rom_ctx {
     // per-kernel profiling (CUDA events around each launch on the context stream)
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
-    struct Rec { int kid; int ev0, ev1; double flops; };
+    struct Rec { int kid; int ev0, ev1; double flops; int launches; };
     std::vector<Rec> recs;
     double prof_ms[ROM_NKERNELS] = {0};
     int64_t prof_launches[ROM_NKERNELS] = {0};
@@ -378,6 +378,7 @@ rom_status rom_state_create(rom_ctx *ctx, int64_t B, rom_state **out) {
         (s = A((void **)&bt.pl, Bz * m)) || (s = A((void **)&bt.r, Bz * n * 8)) ||
         (s = A((void **)&bt.K, Bz * n * n * 8)) || (s = A((void **)&bt.Ubar, Bz * d2 * 8)) ||
         (s = A((void **)&bt.Rbar, Bz * d2 * 8)) || (s = A((void **)&bt.U_prev, Bz * d2 * 8)) ||
+        (s = A((void **)&bt.r0_prev, Bz * 8)) ||
         (s = A((void **)&st->io_F, Bz * d2 * 8)) || (s = A((void **)&st->io_P, Bz * d2 * 8)) ||
         (s = A((void **)&st->io_A, Bz * d2 * d2 * 8)) || (s = A(&st->io_info, Bz * sizeof(rom_step_info)))) {
         rom_state_destroy(st);
@@ -394,8 +395,10 @@ rom_status rom_state_create(rom_ctx *ctx, int64_t B, rom_state **out) {
     std::vector<double> eye(Bz * d2, 0.0);
     for (size_t b = 0; b < Bz; ++b)
         for (int a = 0; a < ctx->dim; ++a) eye[b * d2 + a * ctx->dim + a] = 1.0;
+    const std::vector<double> inf(Bz, INFINITY);
     cudaError_t e;
     if ((e = cudaMemcpy(bt.U_prev, eye.data(), eye.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(bt.r0_prev, inf.data(), Bz * 8, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemset(bt.q_n, 0, Bz * n * 8)) != cudaSuccess || (e = cudaMemset(bt.dq_prev, 0, Bz * n * 8)) != cudaSuccess ||
         (e = cudaMemset(bt.xi, 0, Bz * m * 8)) != cudaSuccess ||
         (e = cudaMemcpy(bt.cp, cp.data(), cp.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess) {
@@ -443,6 +446,8 @@ rom_status rom_state_import(rom_ctx *ctx, rom_state *st, const double *a, const 
     if (a) {
         CK(cudaMemcpy(st->bt.q_n, a, B * n * 8, cudaMemcpyHostToDevice));
         CK(cudaMemset(st->bt.dq_prev, 0, B * n * 8));
+        const std::vector<double> inf(B, INFINITY);
+        CK(cudaMemcpy(st->bt.r0_prev, inf.data(), B * 8, cudaMemcpyHostToDevice));
     }
     if (xi) CK(cudaMemcpy(st->bt.xi, xi, B * m * 8, cudaMemcpyHostToDevice));
     if (Cpinv) {
@@ -508,16 +513,17 @@ static int prof_event(rom_ctx *ctx, int idx) {
     return idx;
 }
 
-// launch one kernel group `kid` (0 start, 1 constitutive, 2 assemble, 3 solve, 4 finalize, 5 advance)
-// with optional event timing and an algorithmic FLOP count for the roofline
+// launch one kernel group `kid` (0 start, 1 constitutive, 2 assemble, 3 solve, 4 finalize, 5 advance,
+// 6 learned start, 7 force) of `launches` kernels with optional event timing and an algorithmic
+// FLOP count for the roofline
 template <typename F>
-static int timed(rom_ctx *ctx, int kid, double flops, F &&launch) {
+static int timed(rom_ctx *ctx, int kid, double flops, F &&launch, int launches = 1) {
     int e0 = -1;
     if (ctx->prof) e0 = prof_event(ctx, (int)ctx->recs.size() * 2);
     const int r = launch();
     if (ctx->prof && e0 >= 0) {
         const int e1 = prof_event(ctx, e0 + 1);
-        ctx->recs.push_back({kid, e0, e1, flops});
+        ctx->recs.push_back({kid, e0, e1, flops, launches});
     }
     return r;
 }
@@ -529,24 +535,28 @@ static void prof_collect(rom_ctx *ctx) {
         float ms = 0.f;
         if (r.ev1 >= 0 && cudaEventElapsedTime(&ms, ctx->ev_pool[r.ev0], ctx->ev_pool[r.ev1]) == cudaSuccess) {
             ctx->prof_ms[r.kid] += ms;
-            ctx->prof_launches[r.kid] += (r.kid == 0 || r.kid == 5) ? 2 : (r.kid == 6 ? 3 + 2 * ctx->mlp.L : 1);
+            ctx->prof_launches[r.kid] += r.launches;
             ctx->prof_flops[r.kid] += r.flops;
         }
     }
     ctx->recs.clear();
 }
 
-// K (and, with_force, the residual r) of the active list: 3D models with n <= 64 use the
-// tensor-core kernel (BF16, TF32, or the FP32-accurate TF32 split for precision fp32; in BF16
-// and TF32 the instances that the solve flagged for an accurate stiffness get the split
-// assembly); 2D models use the 2D tensor-core kernel for BF16/TF32 and the SIMT kernel
-// otherwise (the SIMT and 2D tensor-core launches always produce r as well)
-static int launch_assembly(rom_ctx *ctx, const Model &M, Batch bt, const StepOpts &o, int32_t *nxt, bool with_force,
-                           cudaStream_t s) {
+// the stiffness K runs on the tensor cores (and the FP64 residual in its own kernel, force_kernel)
+// for 3D models with n <= 64 at every precision but FP64, and for 2D models in BF16/TF32
+static bool tc_path(const rom_ctx *ctx, const Model &M, int precision) {
+    return (M.d == 3 && ctx->tc3_img && precision >= 1) || precision >= 2;
+}
+
+// K of the active list: 3D models with n <= 64 use the 3D tensor-core kernel (BF16, TF32, or the
+// FP32-accurate TF32 split for precision fp32; in BF16 and TF32 the instances that the solve
+// flagged for an accurate stiffness get the split assembly); 2D models use the 2D tensor-core
+// kernel for BF16/TF32 and otherwise the SIMT kernel, which also produces the residual r
+static int launch_assembly(rom_ctx *ctx, const Model &M, Batch bt, const StepOpts &o, int32_t *nxt, cudaStream_t s) {
     if (M.d == 3 && ctx->tc3_img && o.precision >= 1) {
-        if (o.precision == 1) return launch_tc3(3, M, bt, ctx->tc3_img, ctx->d_err, 0, with_force, s);
-        const int r = launch_tc3(o.precision == 3 ? 1 : 2, M, bt, ctx->tc3_img, ctx->d_err, 1, with_force, s);
-        return r ? r : launch_tc3(3, M, bt, ctx->tc3_img, ctx->d_err, 2, false, s);
+        if (o.precision == 1) return launch_tc3(3, M, bt, ctx->tc3_img, ctx->d_err, 0, s);
+        const int r = launch_tc3(o.precision == 3 ? 1 : 2, M, bt, ctx->tc3_img, ctx->d_err, 1, s);
+        return r ? r : launch_tc3(3, M, bt, ctx->tc3_img, ctx->d_err, 2, s);
     }
     if (o.precision >= 2)
         return launch_tc(o.precision == 3 ? 1 : 2, M, bt, ctx->tc_img[o.precision == 3 ? 0 : 1], ctx->d_err, s);
@@ -554,12 +564,13 @@ static int launch_assembly(rom_ctx *ctx, const Model &M, Batch bt, const StepOpt
 }
 
 // the effective stiffness needs K at FP32 accuracy: after a BF16/TF32 solve, one FP32-accurate
-// assembly of the converged instances (list rebuilt by launch_list_converged)
+// assembly of the converged instances (list rebuilt by launch_list_converged); the residual is
+// not needed here
 static int launch_abar_assembly(rom_ctx *ctx, const Model &M, Batch bc, const StepOpts &o, int32_t *nxt,
                                 cudaStream_t s) {
     StepOpts o32 = o;
     o32.precision = 1;
-    return launch_assembly(ctx, M, bc, o32, nxt, false, s);
+    return launch_assembly(ctx, M, bc, o32, nxt, s);
 }
 
 static rom_status run_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts, const double *Fbar_d, double *Pbar_d,
@@ -573,12 +584,14 @@ static rom_status run_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts, co
     bt.mu = ctx->mu;
     int32_t *lists[2] = {st->bt.list, st->list2};
     const double n = M.n, m = M.m, d2 = M.d2, d4 = d2 * d2;
-    // algorithmic FLOPs per active instance: kinematics + force 2 m d2 n each; Y = At G: 2 m d4 n;
-    // K upper triangle incl. diagonal: m d2 n (n + 1); LU + solve: 2 n^3 / 3 + 2 n^2
-    const double fl_asm = 2 * m * d4 * n + m * d2 * n * (n + 1) + 2 * m * d2 * n;
+    // algorithmic FLOPs per active instance: kinematics and force 2 m d2 n each; Y = At G: 2 m d4 n;
+    // K: 2 m d2 n^2 on the tensor cores (full product), m d2 n (n + 1) on the CUDA cores (upper
+    // triangle; the SIMT kernel also forms the force); LU + solve: 2 n^3 / 3 + 2 n^2
+    const bool tcp = tc_path(ctx, M, o.precision);
+    const double fl_asm = tcp ? 2 * m * d4 * n + 2 * m * d2 * n * n : 2 * m * d4 * n + m * d2 * n * (n + 1) + 2 * m * d2 * n;
     const double fl_kin = 2 * m * d2 * n;
     const double fl_lu = 2 * n * n * n / 3 + 2 * n * n;
-    if (timed(ctx, 0, 0.0, [&] { return launch_start(M, bt, Fbar_d, o, nullptr, ctx->stream); }))
+    if (timed(ctx, 0, 0.0, [&] { return launch_start(M, bt, Fbar_d, o, nullptr, ctx->stream); }, 2))
         return fail(ctx, ROM_E_ARG, "launch_start");
     if (o.start == ROM_START_MLP) {
         rom_status s2 = ensure_feat(ctx, st->B);
@@ -588,7 +601,7 @@ static rom_status run_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts, co
             mlp_predict(ctx->mlp, ctx->d_feat, st->B, 1, ctx->d_pred, ctx->stream);
             launch_add_pred(bt, M.n, ctx->d_pred, ctx->stream);
             return 0;
-        });
+        }, 3 + 2 * ctx->mlp.L);
     }
     const int max_pass = (opts->max_iter + 1) * (opts->max_ls + 1) + 2;
     int64_t n_act = st->B;
@@ -596,9 +609,14 @@ static rom_status run_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts, co
         bt.list = lists[pass & 1];
         int32_t *nxt = lists[(pass + 1) & 1];
         const double na = (double)n_act;
-        auto asm_launch = [&] { return launch_assembly(ctx, M, bt, o, nxt, true, ctx->stream); };
+        auto asm_launch = [&] { return launch_assembly(ctx, M, bt, o, nxt, ctx->stream); };
+        auto force_launch = [&] {
+            if (tcp) launch_force(M, bt, ctx->stream);
+            return 0;
+        };
         if (timed(ctx, 1, na * fl_kin, [&] { return launch_kernel(1, M, bt, o, nxt, ctx->stream); }) ||
-            timed(ctx, 2, na * fl_asm, asm_launch) ||
+            timed(ctx, 2, na * fl_asm, asm_launch, (M.d == 3 && tcp && o.precision >= 2) ? 2 : 1) ||
+            (tcp && timed(ctx, 7, na * fl_kin, force_launch)) ||
             timed(ctx, 3, na * fl_lu, [&] { return launch_kernel(3, M, bt, o, nxt, ctx->stream); }) ||
             timed(ctx, 5, 0.0, [&] { return launch_kernel(5, M, bt, o, nxt, ctx->stream); }))
             return fail(ctx, ROM_E_ARG, "rom_step: basis size n=%d not supported by the assembly kernel", M.n);
@@ -608,8 +626,7 @@ static rom_status run_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts, co
         n_act = ctx->h_count[0];
         if (n_act == 0) break;
     }
-    const bool tc_used = o.precision >= 2 || (M.d == 3 && ctx->tc3_img && o.precision == 1);
-    if (tc_used) {
+    if (tcp) {
         if (o.precision >= 2 && o.want_abar) {
             Batch bc = bt;
             bc.list = lists[0];
@@ -689,7 +706,8 @@ static rom_status capture_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts
         if (e == cudaSuccess) {
             int32_t *nxt = st->list2;
             bad |= launch_kernel(1, M, bt, o, nxt, bs);
-            bad |= launch_assembly(ctx, M, bt, o, nxt, true, bs);
+            bad |= launch_assembly(ctx, M, bt, o, nxt, bs);
+            if (tc_path(ctx, M, o.precision)) launch_force(M, bt, bs);
             bad |= launch_kernel(3, M, bt, o, nxt, bs);
             launch_graph_advance(bt, nxt, h, max_pass, bs);
             cudaGraph_t out = nullptr;
@@ -905,8 +923,8 @@ rom_status rom_debug_tangent(rom_ctx *ctx, const rom_state *st, void *At, int64_
 rom_status rom_state_bytes(const rom_ctx *ctx, int64_t B, int64_t *bytes) {
     if (!ctx || !bytes || B < 1) return ROM_E_ARG;
     const int64_t d2 = ctx->dim * ctx->dim, n = ctx->n, m = ctx->m, ncp = ctx->dim == 2 ? 4 : 6;
-    const int64_t per = n * 8 * 5 + (int64_t)sizeof(Ctl) + 8 + ncp * m * 8 * 2 + m * 8 * 2 + d2 * m * 8 * 2 +
-                        d2 * d2 * m * 8 + m + n * n * 8 + d2 * 8 * 4 + d2 * d2 * 8 + 32;
+    const int64_t per = n * 8 * 5 + (int64_t)sizeof(Ctl) + 8 + 8 + ncp * m * 8 * 2 + m * 8 * 2 + d2 * m * 8 * 2 +
+                        d2 * d2 * ((m + 3) & ~3) * 8 + m + n * n * 8 + d2 * 8 * 4 + d2 * d2 * 8 + 32;
     *bytes = per * B + 64;
     return ROM_OK;
 }

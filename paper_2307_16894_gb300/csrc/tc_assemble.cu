@@ -346,9 +346,12 @@ static int launch_tc_t(const Model &M, Batch Bt, const unsigned char *img, int *
     const int nch = (M.m + PC - 1) / PC;
     cudaFuncSetAttribute(k_assemble_tc<D, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_assemble_tc<D, FMT><<<(int)((Bt.B + 1) / 2), tc::THREADS, sm, s>>>(M, Bt, img, nch, err);
-    k_force<<<(int)Bt.B, 256, 0, s>>>(M, Bt);
     return 0;
 }
+
+// FP64 residual r = sum_i G_i^T v_i of the listed instances (paths whose stiffness kernel does not
+// produce it)
+void launch_force(const Model &M, Batch Bt, cudaStream_t s) { k_force<<<(int)Bt.B, 256, 0, s>>>(M, Bt); }
 
 int launch_tc(int fmt, const Model &M, Batch Bt, const unsigned char *img, int *err, cudaStream_t s) {
     if (M.d == 2) return fmt == 1 ? launch_tc_t<2, 1>(M, Bt, img, err, s) : launch_tc_t<2, 2>(M, Bt, img, err, s);

@@ -480,8 +480,6 @@ __global__ void __launch_bounds__(tc3::Cfg<MODE>::THREADS, 1)
     }
 }
 
-__global__ void k_force(Model M, Batch Bt);
-
 // ------------------------------------------------------------------------ host side
 
 size_t tc3_image_bytes(int m) { return tc3::img_layout(m).total; }
@@ -545,15 +543,11 @@ static int launch_tc3_t(const Model &M, Batch Bt, const unsigned char *img, int 
 }
 
 // mode 1 BF16, 2 TF32, 3 TF32 split (FP32-accurate); sel 0 = all listed instances, 1 = those
-// without, 2 = those with the accurate-stiffness flag (Ctl::acc_k); with_force also launches the
-// FP64 force for every listed instance
-int launch_tc3(int mode, const Model &M, Batch Bt, const unsigned char *img, int *err, int sel, bool with_force,
-               cudaStream_t s) {
-    int r = mode == 1 ? launch_tc3_t<1>(M, Bt, img, err, sel, s)
-          : mode == 2 ? launch_tc3_t<2>(M, Bt, img, err, sel, s)
-          : mode == 3 ? launch_tc3_t<3>(M, Bt, img, err, sel, s) : -1;
-    if (r == 0 && with_force) k_force<<<(int)Bt.B, 256, 0, s>>>(M, Bt);
-    return r;
+// without, 2 = those with the accurate-stiffness flag (Ctl::acc_k)
+int launch_tc3(int mode, const Model &M, Batch Bt, const unsigned char *img, int *err, int sel, cudaStream_t s) {
+    return mode == 1 ? launch_tc3_t<1>(M, Bt, img, err, sel, s)
+         : mode == 2 ? launch_tc3_t<2>(M, Bt, img, err, sel, s)
+         : mode == 3 ? launch_tc3_t<3>(M, Bt, img, err, sel, s) : -1;
 }
 
 }  // namespace podecm

@@ -21,9 +21,10 @@ def available(names):
     return [n for n in names if os.path.exists(os.path.join(workload.DATA, "rom_%s.npz" % n))]
 
 
-def make_groups(B_total, share_2d=0.75, steps=50, seed0=40_000):
+def make_groups(B_total, share_2d=0.75, steps=50, seed0=40_000, path_steps=50):
     """Split B_total instances over the available models (share_2d of them 2D); instance b of
-    the whole batch uses seed seed0 + b for its geometry and load path."""
+    the whole batch uses seed seed0 + b for its geometry and its path_steps-step load path, of
+    which the first `steps` steps are kept."""
     f2, f3 = available(FAMILY_2D), available(FAMILY_3D)
     n2 = int(round(B_total * share_2d)) if f3 else B_total
     n3 = B_total - n2 if f3 else 0
@@ -37,7 +38,7 @@ def make_groups(B_total, share_2d=0.75, steps=50, seed0=40_000):
             d = rom["d"]
             lo, hi = ((0.2, 0.35) if d == 2 else (0.15, 0.35))
             mu = np.stack([inputs.batch_mu(d, 1, seed0 + b0 + b, lo, hi)[0] for b in range(B)])
-            paths = np.stack([inputs.stretch_path(d, seed0 + b0 + b, steps) for b in range(B)])
+            paths = np.stack([inputs.stretch_path(d, seed0 + b0 + b, path_steps)[:steps] for b in range(B)])
             groups.append(dict(name=name, rom=rom, B=B, mu=mu, coef=inputs.map_coefficients(d, mu), paths=paths))
             b0 += B
     return groups

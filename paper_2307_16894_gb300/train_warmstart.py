@@ -29,6 +29,7 @@ def main():
     ap.add_argument("--precision", default="fp32")
     ap.add_argument("--eval", type=int, default=1024)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--load", default=None, help="evaluate this trained network (npz) instead of training one")
     args = ap.parse_args()
 
     import torch
@@ -36,6 +37,8 @@ def main():
 
     stream = torch.cuda.current_stream().cuda_stream
     rom, mu, coef, paths = workload.batch(args.workload, B=args.paths, steps=args.steps, first=args.first)
+    if args.load:
+        coef, paths = coef[:1], paths[:1]
     d, n = rom["d"], rom["n"]
     n_par = coef.shape[1]
     prec = args.precision
@@ -49,25 +52,32 @@ def main():
         ctx.set_geometry(rom["Gmu"], c)
         return ctx
 
-    t0 = time.time()
-    ctx = make_ctx(coef)
-    st = ctx.state_create(len(coef))
-    X, Y, _ = warmstart.collect(ctx, st, paths, binding.make_opts(start="prev", **kw), torch)
-    st.close()
-    t_collect = time.time() - t0
     n_in = warmstart.n_features(d, n_par, n)
-    ctx.mlp_init(n_in, warmstart.WIDTH, warmstart.DEPTH, n, max(args.batch, args.eval))
-    params0 = warmstart.init_params(n_in, warmstart.WIDTH, warmstart.DEPTH, n, 0)
-    ctx.mlp_params(params0)
-    norm = warmstart.fit_norm(X, Y)
-    ctx.mlp_norm(*norm)
-    t0 = time.time()
-    hist = warmstart.train(ctx, X, Y, torch, epochs=args.epochs, batch=args.batch, lr=args.lr)
-    t_train = time.time() - t0
-    params = ctx.mlp_params()
-    if args.out:
-        warmstart.save(args.out, (n_in, warmstart.WIDTH, warmstart.DEPTH, n), params, norm)
-    ctx.close()
+    if args.load:
+        z = np.load(args.load)
+        params = z["params"]
+        nrm = z["norm"]
+        norm = (nrm[:n_in], nrm[n_in:2 * n_in], nrm[2 * n_in:2 * n_in + n], nrm[2 * n_in + n:])
+        X, hist, t_collect, t_train = np.zeros((0, n_in)), [], 0.0, 0.0
+    else:
+        t0 = time.time()
+        ctx = make_ctx(coef)
+        st = ctx.state_create(len(coef))
+        X, Y, _ = warmstart.collect(ctx, st, paths, binding.make_opts(start="prev", **kw), torch)
+        st.close()
+        t_collect = time.time() - t0
+        ctx.mlp_init(n_in, warmstart.WIDTH, warmstart.DEPTH, n, max(args.batch, args.eval))
+        params0 = warmstart.init_params(n_in, warmstart.WIDTH, warmstart.DEPTH, n, 0)
+        ctx.mlp_params(params0)
+        norm = warmstart.fit_norm(X, Y)
+        ctx.mlp_norm(*norm)
+        t0 = time.time()
+        hist = warmstart.train(ctx, X, Y, torch, epochs=args.epochs, batch=args.batch, lr=args.lr)
+        t_train = time.time() - t0
+        params = ctx.mlp_params()
+        if args.out:
+            warmstart.save(args.out, (n_in, warmstart.WIDTH, warmstart.DEPTH, n), params, norm)
+        ctx.close()
 
     # evaluation on benchmark instances (not seen in training)
     rom, mu_e, coef_e, paths_e = workload.batch(args.workload, B=args.eval, steps=args.steps)

@@ -21,7 +21,8 @@ def built():
 
 @pytest.mark.skipif(not HAVE, reason="3D model file not generated")
 def test_c3_fp64_small_batch():
-    rom, mu, coef, paths = workload.batch("c3", B=3, steps=6)
+    rom, mu, coef, paths = workload.batch("c3", B=3)
+    paths = paths[:, :6]      # first 6 steps of the 50-step load paths
     g = GpuRun(rom, coef)
     o = OracleRun(rom, coef)
     kw = dict(tol_rel=1e-10, tol_abs=rom["tol_abs"], max_iter=25, max_ls=6, start="prev")
@@ -43,7 +44,8 @@ def test_c3_fp64_small_batch():
 @pytest.mark.skipif(not HAVE, reason="3D model file not generated")
 @pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16"])
 def test_c3_mixed_precision(prec):
-    rom, mu, coef, paths = workload.batch("c3", B=3, steps=5)
+    rom, mu, coef, paths = workload.batch("c3", B=3)
+    paths = paths[:, :5]
     g = GpuRun(rom, coef)
     o = OracleRun(rom, coef)
     for k in range(paths.shape[1]):
@@ -60,8 +62,10 @@ def test_c3_mixed_precision(prec):
 
 @pytest.mark.skipif(not HAVE, reason="3D model file not generated")
 def test_c3_full_batch_sampled_tf32():
-    """B = 16384 in the bench configuration (TF32 tensor cores), first 3 steps; 3 sampled instances vs the oracle."""
-    rom, mu, coef, paths = workload.batch("c3", steps=3)
+    """B = 16384 in the bench configuration (TF32 tensor cores), first 3 steps of the 50-step
+    paths; every instance converges and 3 sampled instances match the oracle."""
+    rom, mu, coef, paths = workload.batch("c3")
+    paths = paths[:, :3]
     B = len(coef)
     sample = np.array([0, 8191, B - 1])
     g = GpuRun(rom, coef)
@@ -70,6 +74,6 @@ def test_c3_full_batch_sampled_tf32():
         P, A, info = g.step(paths[:, k], tol_rel=1e-9, tol_abs=rom["tol_abs"], max_iter=50, precision="tf32",
                             start="prev")
         ref = o.step(paths[sample, k], tol_rel=1e-10, tol_abs=rom["tol_abs"], start="prev")
-        assert (info["status"] == 0).mean() >= 0.99
+        assert (info["status"] == 0).all()
         assert rel(P[sample], ref["Pbar"]) <= 1e-7
     g.close()
