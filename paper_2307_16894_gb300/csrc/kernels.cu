@@ -112,13 +112,38 @@ __global__ void k_advance(int32_t *counts) {
 }
 
 // ------------------------------------------------------------------ constitutive
+// 3D mixed-precision kinematics in double-float arithmetic (FP32 pairs, products by TwoProd,
+// sums by TwoSum with a compensation term; Ogita, Rump & Oishi 2005): the FP64 pipe of this GPU
+// runs 1/64 of the FP32 rate, and the pairs carry ~48 significant bits.  q is split once per
+// block into (hi, lo) FP32 pairs in shared memory (a 128-thread block spans at most two
+// instances when m >= 128).
+constexpr int KIN_DF_SLOTS = 2;
+
 template <int D, typename TT>
 __global__ void __launch_bounds__(128) k_constitutive(Model M, Batch Bt) {
     constexpr int D2 = D * D;
+    constexpr bool DF = (D == 3) && (sizeof(TT) == 4);
     const int m = M.m, n = M.n;
     const int n_act = Bt.counts[0];
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t p = gid / m;
+    __shared__ float2 q32s[DF ? KIN_DF_SLOTS * MAX_N : 1];
+    const bool use_df = DF && M.G32h_T && m >= 128;
+    const int64_t p_first = (int64_t)blockIdx.x * blockDim.x / m;
+    if (use_df) {
+        for (int e = threadIdx.x; e < KIN_DF_SLOTS * n; e += blockDim.x) {
+            const int slot = e / n, j = e - slot * n;
+            const int64_t pp = p_first + slot;
+            float2 v = make_float2(0.f, 0.f);
+            if (pp < n_act) {
+                const double q = Bt.q_trial[(int64_t)Bt.list[pp] * n + j];
+                v.x = (float)q;
+                v.y = (float)(q - (double)v.x);
+            }
+            q32s[e] = v;
+        }
+        __syncthreads();
+    }
     if (p >= n_act) return;
     const int i = (int)(gid - p * m);
     const int64_t b = Bt.list[p];
@@ -158,12 +183,38 @@ __global__ void __launch_bounds__(128) k_constitutive(Model M, Batch Bt) {
 
     // a2: kinematics H = G_i a, F = Ubar + H F_mu^-1
     double H[D2];
-    for (int c = 0; c < D2; ++c) H[c] = 0.0;
-    const double *qb = Bt.q_trial + b * n;
-    for (int j = 0; j < n; ++j) {
-        const double qj = __ldg(qb + j);
+    if (use_df) {
+        const float2 *qs = q32s + (p - p_first) * n;
+        float s[D2], er[D2];
 #pragma unroll
-        for (int c = 0; c < D2; ++c) H[c] += M.G_T[((size_t)c * n + j) * m + i] * qj;
+        for (int c = 0; c < D2; ++c) { s[c] = 0.f; er[c] = 0.f; }
+        for (int j = 0; j < n; ++j) {
+            const float2 qq = qs[j];
+#pragma unroll
+            for (int c = 0; c < D2; ++c) {
+                const size_t gi = ((size_t)c * n + j) * m + i;
+                const float gh = M.G32h_T[gi], gl = M.G32l_T[gi];
+                const float pr = __fmul_rn(gh, qq.x);
+                float e = fmaf(gh, qq.x, -pr);
+                e = fmaf(gh, qq.y, e);
+                e = fmaf(gl, qq.x, e);
+                const float sn = __fadd_rn(s[c], pr);
+                const float bb = __fsub_rn(sn, s[c]);
+                const float t = __fadd_rn(__fsub_rn(s[c], __fsub_rn(sn, bb)), __fsub_rn(pr, bb));
+                s[c] = sn;
+                er[c] = __fadd_rn(er[c], __fadd_rn(t, e));
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < D2; ++c) H[c] = (double)s[c] + (double)er[c];
+    } else {
+        for (int c = 0; c < D2; ++c) H[c] = 0.0;
+        const double *qb = Bt.q_trial + b * n;
+        for (int j = 0; j < n; ++j) {
+            const double qj = __ldg(qb + j);
+#pragma unroll
+            for (int c = 0; c < D2; ++c) H[c] += M.G_T[((size_t)c * n + j) * m + i] * qj;
+        }
     }
     double F[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 1.0}};
 #pragma unroll
@@ -478,7 +529,7 @@ __global__ void __launch_bounds__(32) k_solve(Model M, Batch Bt, StepOpts o, int
         const bool ok = isfinite(rn) && warp_lu(A, n, piv);
         if (ok) warp_lu_solve(A, n, piv, x);
         const double rref = Bt.r0_prev ? Bt.r0_prev[b] : INFINITY;
-        if (ok && rn <= rref) {
+        if (ok && isfinite(rref) && rn <= rref) {
             c.tol = fmax(o.tol_rel * rref, o.tol_abs);
             c.rn_acc = rn;
             if (rn <= c.tol || o.max_iter == 0) {

@@ -62,6 +62,7 @@ struct rom_ctx {
     int64_t B = 0;
     double *G_pt = nullptr, *G_T = nullptr, *w = nullptr, *Gmu_T = nullptr, *mu = nullptr;
     float *G32 = nullptr;
+    float *G32h_T = nullptr, *G32l_T = nullptr;   // double-float split of G_T (3D models)
     int32_t *phase = nullptr;
     // host-call staging
     double *h_stage = nullptr;      // pinned
@@ -186,6 +187,8 @@ rom_status rom_destroy(rom_ctx *ctx) {
     p = ctx->G_pt; dfree(p);
     p = ctx->G_T; dfree(p);
     p = ctx->G32; dfree(p);
+    p = ctx->G32h_T; dfree(p);
+    p = ctx->G32l_T; dfree(p);
     p = ctx->w; dfree(p);
     p = ctx->Gmu_T; dfree(p);
     p = ctx->mu; dfree(p);
@@ -234,6 +237,19 @@ rom_status rom_load_basis(rom_ctx *ctx, int n, int m, const double *G) {
     CK(cudaMemcpy(ctx->G_pt, G, cnt * 8, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->G_T, gt.data(), cnt * 8, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->G32, g32.data(), cnt * 4, cudaMemcpyHostToDevice));
+    p = ctx->G32h_T; dfree(p); ctx->G32h_T = nullptr;
+    p = ctx->G32l_T; dfree(p); ctx->G32l_T = nullptr;
+    if (ctx->dim == 3) {
+        std::vector<float> gh(cnt), gl(cnt);
+        for (size_t k = 0; k < cnt; ++k) {
+            gh[k] = (float)gt[k];
+            gl[k] = (float)(gt[k] - (double)gh[k]);
+        }
+        if ((s = dalloc(ctx, (void **)&ctx->G32h_T, cnt * 4)) != ROM_OK) return s;
+        if ((s = dalloc(ctx, (void **)&ctx->G32l_T, cnt * 4)) != ROM_OK) return s;
+        CK(cudaMemcpy(ctx->G32h_T, gh.data(), cnt * 4, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ctx->G32l_T, gl.data(), cnt * 4, cudaMemcpyHostToDevice));
+    }
     for (int f = 0; f < 2; ++f) { p = ctx->tc_img[f]; dfree(p); ctx->tc_img[f] = nullptr; }
     p = ctx->tc3_img; dfree(p); ctx->tc3_img = nullptr;
     if (n <= 64 && ctx->dim == 3) {
@@ -484,6 +500,7 @@ static Model make_model(const rom_ctx *ctx) {
     M.nphase = ctx->nphase; M.ncp = ctx->dim == 2 ? 4 : 6;
     M.mA = (ctx->m + 3) & ~3;
     M.G_pt = ctx->G_pt; M.G_T = ctx->G_T; M.G32_pt = ctx->G32; M.w = ctx->w; M.phase = ctx->phase;
+    M.G32h_T = ctx->G32h_T; M.G32l_T = ctx->G32l_T;
     M.Gmu_T = ctx->Gmu_T; M.omega = ctx->omega;
     return M;
 }

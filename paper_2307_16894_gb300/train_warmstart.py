@@ -30,6 +30,10 @@ def main():
     ap.add_argument("--eval", type=int, default=1024)
     ap.add_argument("--out", default=None)
     ap.add_argument("--load", default=None, help="evaluate this trained network (npz) instead of training one")
+    ap.add_argument("--eval-steps", type=int, default=0,
+                    help="evaluate on the first EVAL_STEPS steps of the load paths (0: all)")
+    ap.add_argument("--clip", type=float, default=0.0,
+                    help="clip the standardised training targets to +-clip (0: no clipping)")
     args = ap.parse_args()
 
     import torch
@@ -70,6 +74,8 @@ def main():
         params0 = warmstart.init_params(n_in, warmstart.WIDTH, warmstart.DEPTH, n, 0)
         ctx.mlp_params(params0)
         norm = warmstart.fit_norm(X, Y)
+        if args.clip > 0:
+            Y = np.clip(Y, norm[2] - args.clip * norm[3], norm[2] + args.clip * norm[3]).astype(np.float32)
         ctx.mlp_norm(*norm)
         t0 = time.time()
         hist = warmstart.train(ctx, X, Y, torch, epochs=args.epochs, batch=args.batch, lr=args.lr)
@@ -81,6 +87,8 @@ def main():
 
     # evaluation on benchmark instances (not seen in training)
     rom, mu_e, coef_e, paths_e = workload.batch(args.workload, B=args.eval, steps=args.steps)
+    if args.eval_steps > 0:
+        paths_e = paths_e[:, :args.eval_steps]
     ev = {}
     for start in ("plain", "prev", "mlp"):
         c = make_ctx(coef_e)
@@ -96,7 +104,8 @@ def main():
         Ad = torch.empty((args.eval, d * d, d * d), dtype=torch.float64, device="cuda")
         Id = torch.empty((args.eval, binding.INFO_DTYPE.itemsize), dtype=torch.uint8, device="cuda")
         its, evs, ms, ok = [], [], 0.0, 0
-        for k in range(args.steps):
+        S = paths_e.shape[1]
+        for k in range(S):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             c.step_device(s, opts, Fd[k], Pd, Ad, Id)
@@ -107,8 +116,8 @@ def main():
             its.append(info["iters"].mean())
             evs.append(info["evals"].mean())
             ok += int((info["status"] == 0).sum())
-        ev[start] = dict(newton_iters=float(np.mean(its)), evals=float(np.mean(evs)), ms_per_step=ms / args.steps,
-                         converged=ok, total=args.eval * args.steps)
+        ev[start] = dict(newton_iters=float(np.mean(its)), evals=float(np.mean(evs)), ms_per_step=ms / S,
+                         converged=ok, total=args.eval * S)
         s.close()
         c.close()
     print(json.dumps(dict(workload=args.workload, samples=int(len(X)), collect_s=t_collect, train_s=t_train,
