@@ -428,106 +428,112 @@ __global__ void __launch_bounds__(256) k_assemble(Model M, Batch Bt, int CH, int
 }
 
 // ------------------------------------------------------------------------ solve
-// LU with partial pivoting of the n x n matrix A (row-major, smem) by one warp;
-// piv[k] = pivot row.  Returns false if a pivot is zero or non-finite.
-__device__ bool warp_lu(double *A, int n, int *piv) {
-    const int lane = threadIdx.x & 31;
+// LU with partial pivoting of the n x n row-major matrix A (shared memory) by the whole block,
+// the same row operations applied to the nrhs right-hand sides X[r][0..n) (forward
+// substitution), then back substitution: X <- A^-1 X.  Pivot = largest |A[i][k]|, ties to the
+// lower row; full rows are swapped (L included).  Returns false (uniformly over the block) if a
+// pivot is zero or non-finite.
+template <typename T>
+__device__ bool block_lu_solve(T *A, int n, T *X, int nrhs, int *s_piv) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int tx = tid & 15, ty = tid >> 4, NY = nt >> 4;
     for (int k = 0; k < n; ++k) {
-        double best = -1.0;
-        int bi = k;
-        for (int i = k + lane; i < n; i += 32) {
-            const double v = fabs(A[i * n + k]);
-            if (v > best || (v == best && i < bi)) { best = v; bi = i; }
-        }
-        for (int off = 16; off > 0; off >>= 1) {
-            const double ob = __shfl_xor_sync(0xffffffffu, best, off);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-        }
-        if (!(best > 0.0) || !isfinite(best)) return false;
-        if (lane == 0) piv[k] = bi;
-        if (bi != k)
-            for (int j = lane; j < n; j += 32) {
-                const double t = A[k * n + j];
-                A[k * n + j] = A[bi * n + j];
-                A[bi * n + j] = t;
+        if (tid < 32) {
+            double best = -1.0;
+            int bi = k;
+            for (int i = k + tid; i < n; i += 32) {
+                const double v = fabs((double)A[i * n + k]);
+                if (v > best || (v == best && i < bi)) { best = v; bi = i; }
             }
-        __syncwarp();
-        const double akk = A[k * n + k];
-        for (int i = k + 1 + lane; i < n; i += 32) A[i * n + k] /= akk;
-        __syncwarp();
-        for (int i = k + 1; i < n; ++i) {
-            const double lik = A[i * n + k];
-            for (int j = k + 1 + lane; j < n; j += 32) A[i * n + j] -= lik * A[k * n + j];
+            for (int off = 16; off > 0; off >>= 1) {
+                const double ob = __shfl_xor_sync(0xffffffffu, best, off);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            if (tid == 0) *s_piv = (!(best > 0.0) || !isfinite(best)) ? -1 : bi;
         }
-        __syncwarp();
+        __syncthreads();
+        const int p = *s_piv;
+        if (p < 0) return false;
+        if (p != k) {
+            for (int j = tid; j < n; j += nt) { const T t = A[k * n + j]; A[k * n + j] = A[p * n + j]; A[p * n + j] = t; }
+            for (int r = tid; r < nrhs; r += nt) { const T t = X[r * n + k]; X[r * n + k] = X[r * n + p]; X[r * n + p] = t; }
+        }
+        __syncthreads();
+        const T akk = A[k * n + k];
+        for (int i = k + 1 + tid; i < n; i += nt) A[i * n + k] /= akk;
+        __syncthreads();
+        // trailing update and forward substitution (16 x nt/16 thread grid)
+        for (int i = k + 1 + ty; i < n; i += NY) {
+            const T lik = A[i * n + k];
+            for (int j = k + 1 + tx; j < n; j += 16) A[i * n + j] -= lik * A[k * n + j];
+            for (int r = tx; r < nrhs; r += 16) X[r * n + i] -= lik * X[r * n + k];
+        }
+        __syncthreads();
+    }
+    for (int k = n - 1; k >= 0; --k) {
+        for (int r = tid; r < nrhs; r += nt) X[r * n + k] /= A[k * n + k];
+        __syncthreads();
+        for (int r = ty; r < nrhs; r += NY)
+            for (int i = tx; i < k; i += 16) X[r * n + i] -= A[i * n + k] * X[r * n + k];
+        __syncthreads();
     }
     return true;
 }
 
-// solve (LU) x = b in place, b in smem, by one warp
-__device__ void warp_lu_solve(const double *A, int n, const int *piv, double *x) {
-    const int lane = threadIdx.x & 31;
-    for (int k = 0; k < n; ++k) {
-        const int p = piv[k];
-        if (p != k && lane == 0) { const double t = x[k]; x[k] = x[p]; x[p] = t; }
-        __syncwarp();
-    }
-    for (int j = 0; j < n; ++j) {
-        const double xj = x[j];
-        for (int i = j + 1 + lane; i < n; i += 32) x[i] -= A[i * n + j] * xj;
-        __syncwarp();
-    }
-    for (int j = n - 1; j >= 0; --j) {
-        if (lane == 0) x[j] /= A[j * n + j];
-        __syncwarp();
-        const double xj = x[j];
-        for (int i = lane; i < j; i += 32) x[i] -= A[i * n + j] * xj;
-        __syncwarp();
-    }
-}
-
 constexpr int ESC_ITERS = 4;
 
-__global__ void __launch_bounds__(32) k_solve(Model M, Batch Bt, StepOpts o, int32_t *list_next) {
+// one CTA of SOLVE_THREADS per active instance: convergence test, line search, start selection
+// and the FP64 LU solve of K da = -r (block_lu_solve); every thread runs the same per-instance
+// state machine on the same values, so all branches are uniform over the block
+constexpr int SOLVE_THREADS = 128;
+
+__global__ void __launch_bounds__(SOLVE_THREADS) k_solve(Model M, Batch Bt, StepOpts o, int32_t *list_next) {
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double bc_rn;
+    __shared__ int s_piv;
     const int n_act = Bt.counts[0];
     const int p = blockIdx.x;
     if (p >= n_act) return;
     const int64_t b = Bt.list[p];
-    const int n = M.n, lane = threadIdx.x;
+    const int n = M.n, tid = threadIdx.x, nt = blockDim.x;
     double *A = reinterpret_cast<double *>(smem);
     double *x = A + (size_t)n * n;
-    int *piv = reinterpret_cast<int *>(x + n);
     const double *r = Bt.r + b * n;
-    double s = 0.0;
-    for (int j = lane; j < n; j += 32) s += r[j] * r[j];
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    const double rn = sqrt(s);
+    if (tid < 32) {   // residual norm: lane-strided partial sums, then a butterfly over the warp
+        double s = 0.0;
+        for (int j = tid; j < n; j += 32) s += r[j] * r[j];
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (tid == 0) bc_rn = sqrt(s);
+    }
+    __syncthreads();
+    const double rn = bc_rn;
     Ctl c = Bt.ctl[b];
     double *qt = Bt.q_trial + b * n, *qa = Bt.q_acc + b * n, *dq = Bt.dq + b * n;
     bool accepted = false;
     bool keep_dq = false;   // Newton direction already known (learned start chosen)
+    auto load_system = [&]() {
+        const double *Kb = Bt.K + (size_t)b * n * n;
+        for (int e = tid; e < n * n; e += nt) A[e] = Kb[e];
+        for (int j = tid; j < n; j += nt) x[j] = -r[j];
+        __syncthreads();
+    };
     if (c.phase == 0 || c.phase == 4) {
         if (c.phase == 4) c.evals += 1;
-        if (c.phase == 0 && o.start == 1 && Bt.r0_prev && lane == 0) Bt.r0_prev[b] = rn;   // previous-step predictor
+        if (c.phase == 0 && o.start == 1 && Bt.r0_prev && tid == 0) Bt.r0_prev[b] = rn;   // previous-step predictor
         c.r0 = rn;
         c.tol = fmax(o.tol_rel * rn, o.tol_abs);
         c.rn_acc = rn;
         c.phase = 1;
-        for (int j = lane; j < n; j += 32) qa[j] = qt[j];
+        for (int j = tid; j < n; j += nt) qa[j] = qt[j];
         accepted = true;
     } else if (c.phase == 2) {
         // learned start evaluated: its Newton direction, then either start from it (its residual is
         // at most the previous-step predictor's residual of the last step that evaluated one) or
         // also evaluate the previous-step predictor a_n + (a_n - a_{n-1}) and keep the better start
         c.r0 = rn;
-        const double *Kb = Bt.K + (size_t)b * n * n;
-        for (int e = lane; e < n * n; e += 32) A[e] = Kb[e];
-        for (int j = lane; j < n; j += 32) x[j] = -r[j];
-        __syncwarp();
-        const bool ok = isfinite(rn) && warp_lu(A, n, piv);
-        if (ok) warp_lu_solve(A, n, piv, x);
+        load_system();
+        const bool ok = isfinite(rn) && block_lu_solve<double>(A, n, x, 1, &s_piv);
         const double rref = Bt.r0_prev ? Bt.r0_prev[b] : INFINITY;
         if (ok && isfinite(rref) && rn <= rref) {
             c.tol = fmax(o.tol_rel * rref, o.tol_abs);
@@ -535,27 +541,26 @@ __global__ void __launch_bounds__(32) k_solve(Model M, Batch Bt, StepOpts o, int
             if (rn <= c.tol || o.max_iter == 0) {
                 c.status = 0;
                 c.active = 0;
-                for (int j = lane; j < n; j += 32) qa[j] = qt[j];
+                for (int j = tid; j < n; j += nt) qa[j] = qt[j];
             } else {
                 c.t = 1.0;
                 c.ls = 0;
                 c.phase = 1;
-                for (int j = lane; j < n; j += 32) { dq[j] = x[j]; qa[j] = qt[j]; qt[j] = qa[j] + x[j]; }
+                for (int j = tid; j < n; j += nt) { dq[j] = x[j]; qa[j] = qt[j]; qt[j] = qa[j] + x[j]; }
             }
             keep_dq = true;
         } else {
-            if (!ok && lane == 0) c.r0 = NAN;
-            for (int j = lane; j < n; j += 32) {
+            if (!ok) c.r0 = NAN;
+            for (int j = tid; j < n; j += nt) {
                 dq[j] = ok ? x[j] : 0.0;
                 qa[j] = qt[j];
                 qt[j] = Bt.q_n[b * n + j] + Bt.dq_prev[b * n + j];
             }
-            c.r0 = __shfl_sync(0xffffffffu, c.r0, 0);
             c.phase = 3;
         }
     } else if (c.phase == 3) {
         c.evals += 1;
-        if (Bt.r0_prev && lane == 0) Bt.r0_prev[b] = rn;
+        if (Bt.r0_prev && tid == 0) Bt.r0_prev[b] = rn;
         const double rm = c.r0;
         if (!(rm <= rn)) {
             // previous-step predictor wins (or the learned start failed)
@@ -563,7 +568,7 @@ __global__ void __launch_bounds__(32) k_solve(Model M, Batch Bt, StepOpts o, int
             c.tol = fmax(o.tol_rel * rn, o.tol_abs);
             c.rn_acc = rn;
             c.phase = 1;
-            for (int j = lane; j < n; j += 32) qa[j] = qt[j];
+            for (int j = tid; j < n; j += nt) qa[j] = qt[j];
             accepted = true;
         } else {
             // the tolerance stays relative to the previous-step predictor's residual, so that the
@@ -573,20 +578,20 @@ __global__ void __launch_bounds__(32) k_solve(Model M, Batch Bt, StepOpts o, int
             c.rn_acc = rm;
             if (rm <= c.tol || o.max_iter == 0) {
                 // the stored per-point data belong to the other candidate: re-evaluate here
-                for (int j = lane; j < n; j += 32) qt[j] = qa[j];
+                for (int j = tid; j < n; j += nt) qt[j] = qa[j];
                 c.phase = 4;
             } else {
                 c.t = 1.0;
                 c.ls = 0;
                 c.phase = 1;
-                for (int j = lane; j < n; j += 32) qt[j] = qa[j] + dq[j];
+                for (int j = tid; j < n; j += nt) qt[j] = qa[j] + dq[j];
                 keep_dq = true;
             }
         }
     } else {
         c.evals += 1;
         if (c.ls >= o.max_ls || (isfinite(rn) && rn < c.rn_acc)) {
-            for (int j = lane; j < n; j += 32) qa[j] = qt[j];
+            for (int j = tid; j < n; j += nt) qa[j] = qt[j];
             c.rn_acc = rn;
             c.iters += 1;
             c.ls = 0;
@@ -594,7 +599,7 @@ __global__ void __launch_bounds__(32) k_solve(Model M, Batch Bt, StepOpts o, int
         } else {
             c.ls += 1;
             c.t *= 0.5;
-            for (int j = lane; j < n; j += 32) qt[j] = qa[j] + c.t * dq[j];
+            for (int j = tid; j < n; j += nt) qt[j] = qa[j] + c.t * dq[j];
         }
     }
     if (accepted && !keep_dq) {
@@ -605,21 +610,18 @@ __global__ void __launch_bounds__(32) k_solve(Model M, Batch Bt, StepOpts o, int
             // low-precision stiffness (BF16/TF32): an instance still iterating after ESC_ITERS
             // accepted steps gets the FP32-accurate assembly from its next evaluation on
             if (o.precision >= 2 && c.iters >= ESC_ITERS) c.acc_k = 1;
-            const double *Kb = Bt.K + (size_t)b * n * n;
-            for (int e = lane; e < n * n; e += 32) A[e] = Kb[e];
-            for (int j = lane; j < n; j += 32) x[j] = -r[j];
-            __syncwarp();
-            if (!warp_lu(A, n, piv)) { c.status = 6; c.active = 0; }
+            __syncthreads();   // qa written above is read below by other threads
+            load_system();
+            if (!block_lu_solve<double>(A, n, x, 1, &s_piv)) { c.status = 6; c.active = 0; }
             else {
-                warp_lu_solve(A, n, piv, x);
                 c.t = 1.0;
                 c.ls = 0;
-                for (int j = lane; j < n; j += 32) { dq[j] = x[j]; qt[j] = qa[j] + x[j]; }
+                for (int j = tid; j < n; j += nt) { dq[j] = x[j]; qt[j] = qa[j] + x[j]; }
             }
         }
     }
-    __syncwarp();
-    if (lane == 0) {
+    __syncthreads();
+    if (tid == 0) {
         Bt.ctl[b] = c;
         if (c.active) {
             const int pos = atomicAdd(&Bt.counts[1], 1);
@@ -817,59 +819,6 @@ __device__ void abar_sums_f32(const Model &M, const Batch &Bt, int64_t b, int CH
         A0[tid] = s;
     }
     __syncthreads();
-}
-
-// LU with partial pivoting of the n x n row-major matrix A (shared memory) by the whole block,
-// the same row operations applied to the nrhs right-hand sides X[r][0..n) (forward
-// substitution), then back substitution: X <- A^-1 X.  Pivot = largest |A[i][k]|, ties to the
-// lower row; every element sees the same operations in the same order as warp_lu followed by
-// warp_lu_solve.  Returns false (uniformly over the block) if a pivot is zero or non-finite.
-template <typename T>
-__device__ bool block_lu_solve(T *A, int n, T *X, int nrhs, int *s_piv) {
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int tx = tid & 15, ty = tid >> 4, NY = nt >> 4;
-    for (int k = 0; k < n; ++k) {
-        if (tid < 32) {
-            double best = -1.0;
-            int bi = k;
-            for (int i = k + tid; i < n; i += 32) {
-                const double v = fabs((double)A[i * n + k]);
-                if (v > best || (v == best && i < bi)) { best = v; bi = i; }
-            }
-            for (int off = 16; off > 0; off >>= 1) {
-                const double ob = __shfl_xor_sync(0xffffffffu, best, off);
-                const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-            }
-            if (tid == 0) *s_piv = (!(best > 0.0) || !isfinite(best)) ? -1 : bi;
-        }
-        __syncthreads();
-        const int p = *s_piv;
-        if (p < 0) return false;
-        if (p != k) {
-            for (int j = tid; j < n; j += nt) { const T t = A[k * n + j]; A[k * n + j] = A[p * n + j]; A[p * n + j] = t; }
-            for (int r = tid; r < nrhs; r += nt) { const T t = X[r * n + k]; X[r * n + k] = X[r * n + p]; X[r * n + p] = t; }
-        }
-        __syncthreads();
-        const T akk = A[k * n + k];
-        for (int i = k + 1 + tid; i < n; i += nt) A[i * n + k] /= akk;
-        __syncthreads();
-        // trailing update and forward substitution (16 x nt/16 thread grid)
-        for (int i = k + 1 + ty; i < n; i += NY) {
-            const T lik = A[i * n + k];
-            for (int j = k + 1 + tx; j < n; j += 16) A[i * n + j] -= lik * A[k * n + j];
-            for (int r = tx; r < nrhs; r += 16) X[r * n + i] -= lik * X[r * n + k];
-        }
-        __syncthreads();
-    }
-    for (int k = n - 1; k >= 0; --k) {
-        for (int r = tid; r < nrhs; r += nt) X[r * n + k] /= A[k * n + k];
-        __syncthreads();
-        for (int r = ty; r < nrhs; r += NY)
-            for (int i = tx; i < k; i += 16) X[r * n + i] -= A[i * n + k] * X[r * n + k];
-        __syncthreads();
-    }
-    return true;
 }
 
 // Ahat part of the effective tangent: AU = (A0 - B^T K^-1 B) / |Omega| with the factor of K at
@@ -1172,7 +1121,7 @@ static int launch_kernels_t(int which, const Model &M, Batch Bt, const StepOpts 
     if (which == 3) {
         const size_t sms = (size_t)M.n * M.n * 8 + (size_t)M.n * 8 + (size_t)M.n * 4 + 16;
         cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sms);
-        k_solve<<<(int)Bt.B, 32, sms, s>>>(M, Bt, o, list_next);
+        k_solve<<<(int)Bt.B, SOLVE_THREADS, sms, s>>>(M, Bt, o, list_next);
         return 0;
     }
     if (which == 5) {
