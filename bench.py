@@ -48,13 +48,22 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5"])
     ap.add_argument("--precision", default=None, choices=["fp64", "fp32", "tf32", "bf16"])
-    ap.add_argument("--start", default="prev", choices=["plain", "prev", "mlp"])
-    ap.add_argument("--mlp", default=None, help="trained learned-start network (npz) for --start mlp")
+    ap.add_argument("--start", default=None, choices=["plain", "prev", "mlp"],
+                    help="Newton start (default: the learned start with data/mlp_<workload>.npz on the 2D workload, "
+                         "where it beats the previous-step predictor, else the previous-step predictor)")
+    ap.add_argument("--mlp", default=None, help="trained learned-start network (npz) for --start mlp "
+                                                "(default data/mlp_<workload>.npz)")
     ap.add_argument("--no-graphs", action="store_true", help="time the host-driven pass loop instead of graphs")
     ap.add_argument("--batch", type=int, default=None, help="override the batch size (testing)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    return ap.parse_args()
+    args = ap.parse_args()
+    default_mlp = os.path.join(ROOT, "data", "mlp_%s.npz" % args.workload)
+    if args.start is None:
+        args.start = "mlp" if (args.workload == "c2" and os.path.exists(default_mlp)) else "prev"
+    if args.start == "mlp" and args.mlp is None:
+        args.mlp = default_mlp
+    return args
 
 
 def dist_env():

@@ -112,7 +112,7 @@ __global__ void k_advance(int32_t *counts) {
 }
 
 // ------------------------------------------------------------------ constitutive
-// 3D mixed-precision kinematics in double-float arithmetic (FP32 pairs, products by TwoProd,
+// Mixed-precision kinematics in double-float arithmetic (FP32 pairs, products by TwoProd,
 // sums by TwoSum with a compensation term; Ogita, Rump & Oishi 2005): the FP64 pipe of this GPU
 // runs 1/64 of the FP32 rate, and the pairs carry ~48 significant bits.  q is split once per
 // block into (hi, lo) FP32 pairs in shared memory (a 128-thread block spans at most two
@@ -122,7 +122,7 @@ constexpr int KIN_DF_SLOTS = 2;
 template <int D, typename TT>
 __global__ void __launch_bounds__(128) k_constitutive(Model M, Batch Bt) {
     constexpr int D2 = D * D;
-    constexpr bool DF = (D == 3) && (sizeof(TT) == 4);
+    constexpr bool DF = sizeof(TT) == 4;
     const int m = M.m, n = M.n;
     const int n_act = Bt.counts[0];
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -434,7 +434,7 @@ __global__ void __launch_bounds__(256) k_assemble(Model M, Batch Bt, int CH, int
 // lower row; full rows are swapped (L included).  Returns false (uniformly over the block) if a
 // pivot is zero or non-finite.
 template <typename T>
-__device__ bool block_lu_solve(T *A, int n, T *X, int nrhs, int *s_piv) {
+__device__ bool block_lu_solve(T *A, int n, int lda, T *X, int ldx, int nrhs, int *s_piv) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int tx = tid & 15, ty = tid >> 4, NY = nt >> 4;
     for (int k = 0; k < n; ++k) {
@@ -442,7 +442,7 @@ __device__ bool block_lu_solve(T *A, int n, T *X, int nrhs, int *s_piv) {
             double best = -1.0;
             int bi = k;
             for (int i = k + tid; i < n; i += 32) {
-                const double v = fabs((double)A[i * n + k]);
+                const double v = fabs((double)A[i * lda + k]);
                 if (v > best || (v == best && i < bi)) { best = v; bi = i; }
             }
             for (int off = 16; off > 0; off >>= 1) {
@@ -456,41 +456,175 @@ __device__ bool block_lu_solve(T *A, int n, T *X, int nrhs, int *s_piv) {
         const int p = *s_piv;
         if (p < 0) return false;
         if (p != k) {
-            for (int j = tid; j < n; j += nt) { const T t = A[k * n + j]; A[k * n + j] = A[p * n + j]; A[p * n + j] = t; }
-            for (int r = tid; r < nrhs; r += nt) { const T t = X[r * n + k]; X[r * n + k] = X[r * n + p]; X[r * n + p] = t; }
+            for (int j = tid; j < n; j += nt) { const T t = A[k * lda + j]; A[k * lda + j] = A[p * lda + j]; A[p * lda + j] = t; }
+            for (int r = tid; r < nrhs; r += nt) { const T t = X[r * ldx + k]; X[r * ldx + k] = X[r * ldx + p]; X[r * ldx + p] = t; }
         }
         __syncthreads();
-        const T akk = A[k * n + k];
-        for (int i = k + 1 + tid; i < n; i += nt) A[i * n + k] /= akk;
+        const T akk = A[k * lda + k];
+        for (int i = k + 1 + tid; i < n; i += nt) A[i * lda + k] /= akk;
         __syncthreads();
         // trailing update and forward substitution (16 x nt/16 thread grid)
         for (int i = k + 1 + ty; i < n; i += NY) {
-            const T lik = A[i * n + k];
-            for (int j = k + 1 + tx; j < n; j += 16) A[i * n + j] -= lik * A[k * n + j];
-            for (int r = tx; r < nrhs; r += 16) X[r * n + i] -= lik * X[r * n + k];
+            const T lik = A[i * lda + k];
+            for (int j = k + 1 + tx; j < n; j += 16) A[i * lda + j] -= lik * A[k * lda + j];
+            for (int r = tx; r < nrhs; r += 16) X[r * ldx + i] -= lik * X[r * ldx + k];
         }
         __syncthreads();
     }
     for (int k = n - 1; k >= 0; --k) {
-        for (int r = tid; r < nrhs; r += nt) X[r * n + k] /= A[k * n + k];
+        for (int r = tid; r < nrhs; r += nt) X[r * ldx + k] /= A[k * lda + k];
         __syncthreads();
         for (int r = ty; r < nrhs; r += NY)
-            for (int i = tx; i < k; i += 16) X[r * n + i] -= A[i * n + k] * X[r * n + k];
+            for (int i = tx; i < k; i += 16) X[r * ldx + i] -= A[i * lda + k] * X[r * ldx + k];
         __syncthreads();
     }
     return true;
 }
 
+// LU with partial pivoting by the whole block without right-hand sides: A <- L\U, piv[k] =
+// pivot row of step k (full rows swapped).  Returns false (uniformly) on a zero or non-finite
+// pivot.
+template <typename T>
+__device__ bool block_lu_factor(T *A, int n, int lda, int *piv, int *s_piv) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int tx = tid & 15, ty = tid >> 4, NY = nt >> 4;
+    for (int k = 0; k < n; ++k) {
+        if (tid < 32) {
+            float best = -1.f;
+            int bi = k;
+            for (int i = k + tid; i < n; i += 32) {
+                const float v = fabsf((float)A[i * lda + k]);
+                if (v > best || (v == best && i < bi)) { best = v; bi = i; }
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+                const float ob = __shfl_xor_sync(0xffffffffu, best, off);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            if (tid == 0) {
+                *s_piv = (!(best > 0.f) || !isfinite(best)) ? -1 : bi;
+                piv[k] = bi;
+            }
+        }
+        __syncthreads();
+        const int p = *s_piv;
+        if (p < 0) return false;
+        if (p != k)
+            for (int j = tid; j < n; j += nt) { const T t = A[k * lda + j]; A[k * lda + j] = A[p * lda + j]; A[p * lda + j] = t; }
+        __syncthreads();
+        const T akk = A[k * lda + k];
+        for (int i = k + 1 + tid; i < n; i += nt) A[i * lda + k] /= akk;
+        __syncthreads();
+        for (int i = k + 1 + ty; i < n; i += NY) {
+            const T lik = A[i * lda + k];
+            for (int j = k + 1 + tx; j < n; j += 16) A[i * lda + j] -= lik * A[k * lda + j];
+        }
+        __syncthreads();
+    }
+    return true;
+}
+
+// y <- A^-1 y with the factors of block_lu_factor, by warp 0 (the others wait at the final barrier)
+template <typename T>
+__device__ void block_lu_apply(const T *A, int n, int lda, const int *piv, T *y) {
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < 32) {
+        if (lane == 0)
+            for (int k = 0; k < n; ++k)
+                if (piv[k] != k) { const T t = y[k]; y[k] = y[piv[k]]; y[piv[k]] = t; }
+        __syncwarp();
+        for (int k = 0; k < n; ++k) {
+            const T yk = y[k];
+            for (int i = k + 1 + lane; i < n; i += 32) y[i] -= A[i * lda + k] * yk;
+            __syncwarp();
+        }
+        for (int k = n - 1; k >= 0; --k) {
+            if (lane == 0) y[k] /= A[k * lda + k];
+            __syncwarp();
+            const T yk = y[k];
+            for (int i = lane; i < k; i += 32) y[i] -= A[i * lda + k] * yk;
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+}
+
+// max over the block of v (>= 0); red = shared scratch of blockDim / 32 doubles
+__device__ double block_max(double v, double *red) {
+    for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double m = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+    __syncthreads();
+    return m;
+}
+
+// Newton direction x = -K^-1 r into shared x[0..n).  FP64 path: LU of K in FP64 by the block.
+// Mixed paths: LU of K rounded to FP32, then iterative refinement with FP64 residuals
+// -r - K x (at most 3 corrections, until a correction is below 1e-15 max|x|); a correction that
+// does not shrink below half of the previous one sends the solve to the FP64 LU.  The result
+// solves the same K to FP64 accuracy either way.  A: n*n doubles of shared scratch.
+__device__ bool newton_direction(const Batch &Bt, int64_t b, int n, int precision, double *A, double *x, int *s_piv,
+                                 double *red) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const double *Kb = Bt.K + (size_t)b * n * n;
+    const double *r = Bt.r + b * n;
+    const int lda = n + 1;   // padded rows: column accesses of the factors hit distinct banks
+    if (precision >= 1 && n >= 48) {
+        float *A32 = reinterpret_cast<float *>(A);
+        float *y = A32 + (size_t)n * lda;                                 // n floats
+        int *piv = reinterpret_cast<int *>(y + n);                        // n ints  (n lda + 2n floats <= 2 n lda)
+        for (int e = tid; e < n * n; e += nt) A32[(e / n) * lda + e % n] = (float)Kb[e];
+        for (int j = tid; j < n; j += nt) y[j] = (float)(-r[j]);
+        __syncthreads();
+        bool ok = block_lu_factor<float>(A32, n, lda, piv, s_piv);
+        if (ok) {
+            block_lu_apply<float>(A32, n, lda, piv, y);
+            for (int j = tid; j < n; j += nt) x[j] = (double)y[j];
+            __syncthreads();
+            double prev = INFINITY;
+            const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+            for (int it = 0; it < 3; ++it) {
+                // FP64 residual of the current solution, one warp per row
+                for (int i = wid; i < n; i += nw) {
+                    double s = 0.0;
+                    for (int j = lane; j < n; j += 32) s += Kb[(size_t)i * n + j] * x[j];
+                    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+                    if (lane == 0) y[i] = (float)(-r[i] - s);
+                }
+                __syncthreads();
+                block_lu_apply<float>(A32, n, lda, piv, y);
+                double dl = 0.0, xl = 0.0;
+                for (int j = tid; j < n; j += nt) { dl = fmax(dl, fabs((double)y[j])); xl = fmax(xl, fabs(x[j])); }
+                const double dn = block_max(dl, red), xn = block_max(xl, red);
+                if (!(dn <= 0.5 * prev)) { ok = false; break; }
+                for (int j = tid; j < n; j += nt) x[j] += (double)y[j];
+                __syncthreads();
+                prev = dn;
+                if (dn <= 1e-15 * xn) break;
+            }
+        }
+        if (ok) return true;
+        __syncthreads();
+    }
+    for (int e = tid; e < n * n; e += nt) A[(e / n) * lda + e % n] = Kb[e];
+    for (int j = tid; j < n; j += nt) x[j] = -r[j];
+    __syncthreads();
+    return block_lu_solve<double>(A, n, lda, x, n, 1, s_piv);
+}
+
 constexpr int ESC_ITERS = 4;
 
 // one CTA of SOLVE_THREADS per active instance: convergence test, line search, start selection
-// and the FP64 LU solve of K da = -r (block_lu_solve); every thread runs the same per-instance
-// state machine on the same values, so all branches are uniform over the block
+// and the solve of K da = -r (newton_direction); every thread runs the same per-instance state
+// machine on the same values, so all branches are uniform over the block
 constexpr int SOLVE_THREADS = 128;
 
 __global__ void __launch_bounds__(SOLVE_THREADS) k_solve(Model M, Batch Bt, StepOpts o, int32_t *list_next) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double bc_rn;
+    __shared__ double red[SOLVE_THREADS / 32];
     __shared__ int s_piv;
     const int n_act = Bt.counts[0];
     const int p = blockIdx.x;
@@ -498,7 +632,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve(Model M, Batch Bt, Step
     const int64_t b = Bt.list[p];
     const int n = M.n, tid = threadIdx.x, nt = blockDim.x;
     double *A = reinterpret_cast<double *>(smem);
-    double *x = A + (size_t)n * n;
+    double *x = A + (size_t)n * (n + 1);
     const double *r = Bt.r + b * n;
     if (tid < 32) {   // residual norm: lane-strided partial sums, then a butterfly over the warp
         double s = 0.0;
@@ -512,12 +646,6 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve(Model M, Batch Bt, Step
     double *qt = Bt.q_trial + b * n, *qa = Bt.q_acc + b * n, *dq = Bt.dq + b * n;
     bool accepted = false;
     bool keep_dq = false;   // Newton direction already known (learned start chosen)
-    auto load_system = [&]() {
-        const double *Kb = Bt.K + (size_t)b * n * n;
-        for (int e = tid; e < n * n; e += nt) A[e] = Kb[e];
-        for (int j = tid; j < n; j += nt) x[j] = -r[j];
-        __syncthreads();
-    };
     if (c.phase == 0 || c.phase == 4) {
         if (c.phase == 4) c.evals += 1;
         if (c.phase == 0 && o.start == 1 && Bt.r0_prev && tid == 0) Bt.r0_prev[b] = rn;   // previous-step predictor
@@ -532,8 +660,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve(Model M, Batch Bt, Step
         // at most the previous-step predictor's residual of the last step that evaluated one) or
         // also evaluate the previous-step predictor a_n + (a_n - a_{n-1}) and keep the better start
         c.r0 = rn;
-        load_system();
-        const bool ok = isfinite(rn) && block_lu_solve<double>(A, n, x, 1, &s_piv);
+        const bool ok = isfinite(rn) && newton_direction(Bt, b, n, o.precision, A, x, &s_piv, red);
         const double rref = Bt.r0_prev ? Bt.r0_prev[b] : INFINITY;
         if (ok && isfinite(rref) && rn <= rref) {
             c.tol = fmax(o.tol_rel * rref, o.tol_abs);
@@ -611,8 +738,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve(Model M, Batch Bt, Step
             // accepted steps gets the FP32-accurate assembly from its next evaluation on
             if (o.precision >= 2 && c.iters >= ESC_ITERS) c.acc_k = 1;
             __syncthreads();   // qa written above is read below by other threads
-            load_system();
-            if (!block_lu_solve<double>(A, n, x, 1, &s_piv)) { c.status = 6; c.active = 0; }
+            if (!newton_direction(Bt, b, n, o.precision, A, x, &s_piv, red)) { c.status = 6; c.active = 0; }
             else {
                 c.t = 1.0;
                 c.ls = 0;
@@ -760,14 +886,15 @@ __device__ void abar_sums_f32(const Model &M, const Batch &Bt, int64_t b, int CH
         __syncthreads();
         if (c + 1 < nch) stage(c + 1);
         const float *as = As[buf], *fm = Fm32[buf], *gs = Gs[buf];
-        for (int e = tid; e < ch * D4; e += blockDim.x) {
-            const int ii = e / D4, rem = e - ii * D4;
+        for (int e = tid; e < CHF * D4; e += blockDim.x) {   // consecutive threads: consecutive points
+            const int ii = e % CHF, rem = e / CHF;
+            if (ii >= ch) continue;
             const int ar = rem / D2, kl = rem - ar * D2;
             const int k = kl / D, l = kl - k * D;
             float s = 0.f;
 #pragma unroll
             for (int ss = 0; ss < D; ++ss) s = fmaf(as[(ar * D2 + k * D + ss) * CHF + ii], fm[ii * D2 + l * D + ss], s);
-            Ah[e] = s;
+            Ah[ii * D4 + rem] = s;
         }
         __syncthreads();
         for (int ii = grp; ii < ch; ii += NGRP) {
@@ -829,22 +956,23 @@ __device__ void schur_abar(const Model &M, const Batch &Bt, int64_t b, const dou
                            unsigned char *work, double *AU) {
     constexpr int D2 = D * D, D4 = D2 * D2;
     const int n = M.n, tid = threadIdx.x;
-    T *Aw = reinterpret_cast<T *>(work);     // [n][n]
-    T *Zs = Aw + (size_t)n * n;              // [D2][n]
-    int *piv = reinterpret_cast<int *>(Zs + (size_t)n * D2);
+    const int ld = n + 1;                    // padded rows and right-hand sides: distinct banks
+    T *Aw = reinterpret_cast<T *>(work);     // [n][n + 1]
+    T *Zs = Aw + (size_t)n * ld;             // [D2][n + 1]
+    int *piv = reinterpret_cast<int *>(Zs + (size_t)ld * D2);
     const double *Kb = Bt.K + (size_t)b * n * n;
-    for (int e = tid; e < n * n; e += blockDim.x) Aw[e] = (T)Kb[e];
+    for (int e = tid; e < n * n; e += blockDim.x) Aw[(e / n) * ld + e % n] = (T)Kb[e];
     for (int e = tid; e < n * D2; e += blockDim.x) {
         const int kl = e / n, j = e - kl * n;
-        Zs[e] = (T)Bm[j * D2 + kl];
+        Zs[kl * ld + j] = (T)Bm[j * D2 + kl];
     }
     __syncthreads();
-    const bool ok = block_lu_solve<T>(Aw, n, Zs, D2, piv);
+    const bool ok = block_lu_solve<T>(Aw, n, ld, Zs, ld, D2, piv);
     if (tid < D4) {
         const int ij = tid / D2, kl = tid - ij * D2;
         double s = A0[tid];
         if (ok)
-            for (int j = 0; j < n; ++j) s -= Bm[j * D2 + ij] * (double)Zs[(size_t)kl * n + j];
+            for (int j = 0; j < n; ++j) s -= Bm[j * D2 + ij] * (double)Zs[(size_t)kl * ld + j];
         else
             s = NAN;
         AU[tid] = s / M.omega;
@@ -1119,7 +1247,7 @@ static int launch_kernels_t(int which, const Model &M, Batch Bt, const StepOpts 
         return -1;
     }
     if (which == 3) {
-        const size_t sms = (size_t)M.n * M.n * 8 + (size_t)M.n * 8 + (size_t)M.n * 4 + 16;
+        const size_t sms = (size_t)M.n * (M.n + 1) * 8 + (size_t)M.n * 8 + (size_t)M.n * 4 + 16;
         cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sms);
         k_solve<<<(int)Bt.B, SOLVE_THREADS, sms, s>>>(M, Bt, o, list_next);
         return 0;
@@ -1162,7 +1290,7 @@ static int launch_finalize_t(const Model &M, Batch Bt, const StepOpts &o, double
                                     : ((size_t)2 * chf * D2 + 2 * (size_t)D4 * chf + 2 * (size_t)chf * D2 * n +
                                        (size_t)chf * D4) * 4 + 16 - (size_t)chf * D2 * 8;
         const size_t red = te == 4 ? (size_t)8 * n * D2 * 4 : 0;              // FP32 group sums
-        const size_t schur = (n * n + n * D2) * te + 16;                      // K factor, RHS, pivot
+        const size_t schur = ((n + 1) * n + (n + 1) * D2) * te + 16;          // K factor, RHS, pivot
         return head + std::max(std::max(sums, red), schur);
     };
     int CHF = 16;

@@ -25,7 +25,7 @@ struct Model {
     const double *G_pt;    // [m][d2][n]
     const double *G_T;     // [d2][n][m]
     const float *G32_pt;   // [m][d2][n]
-    const float *G32h_T;   // [d2][n][m] FP32 high part of G_T (3D mixed-precision kinematics), may be null
+    const float *G32h_T;   // [d2][n][m] FP32 high part of G_T (mixed-precision kinematics), may be null
     const float *G32l_T;   // [d2][n][m] FP32 low part, G_T - G32h_T rounded to FP32
     const double *w;       // [m]
     const int32_t *phase;  // [m]

@@ -62,7 +62,7 @@ struct rom_ctx {
     int64_t B = 0;
     double *G_pt = nullptr, *G_T = nullptr, *w = nullptr, *Gmu_T = nullptr, *mu = nullptr;
     float *G32 = nullptr;
-    float *G32h_T = nullptr, *G32l_T = nullptr;   // double-float split of G_T (3D models)
+    float *G32h_T = nullptr, *G32l_T = nullptr;   // double-float split of G_T (mixed-precision kinematics)
     int32_t *phase = nullptr;
     // host-call staging
     double *h_stage = nullptr;      // pinned
@@ -239,7 +239,7 @@ rom_status rom_load_basis(rom_ctx *ctx, int n, int m, const double *G) {
     CK(cudaMemcpy(ctx->G32, g32.data(), cnt * 4, cudaMemcpyHostToDevice));
     p = ctx->G32h_T; dfree(p); ctx->G32h_T = nullptr;
     p = ctx->G32l_T; dfree(p); ctx->G32l_T = nullptr;
-    if (ctx->dim == 3) {
+    {
         std::vector<float> gh(cnt), gl(cnt);
         for (size_t k = 0; k < cnt; ++k) {
             gh[k] = (float)gt[k];
