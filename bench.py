@@ -288,7 +288,7 @@ def cpu_baseline(args, n_inst=None, n_steps=None, budget_s=20.0):
     the first n_inst instances over the first n_steps load steps."""
     import oracle
     from paper_2307_16894_gb300 import workload  # noqa: F401
-    rom, mu, coef, paths = load_workload(args, B=n_inst or (64 if args.workload == "c2" else 8))
+    rom, mu, coef, paths = load_workload(args, B=n_inst or (512 if args.workload == "c2" else 16))
     B = len(coef)
     d, n, m = rom["d"], rom["n"], rom["m"]
     Gmu = rom["Gmu"].reshape(m, d, d, -1)

@@ -150,7 +150,11 @@ rom_status rom_state_import(rom_ctx *ctx, rom_state *st, const double *a, const 
 rom_status rom_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts, const double *Fbar,
                     double *Pbar, double *Abar, rom_step_info *info);
 
-/* Same with device pointers; asynchronous on the context stream. */
+/* Same with device pointers; asynchronous on the context stream.
+ * Tensor-core stiffness (3D models, and 2D in ROM_PREC_TF32/BF16): every pipeline wait inside
+ * the kernel is bounded; if one gives up, rom_step (and rom_step_device without graphs)
+ * returns ROM_E_CUDA after the Newton passes, and in graph mode the step's Abar entries are
+ * NaN (Pbar, info and the history come from exact FP64 residuals and stay valid). */
 rom_status rom_step_device(rom_ctx *ctx, rom_state *st, const rom_opts *opts, const double *Fbar_d,
                            double *Pbar_d, double *Abar_d, rom_step_info *info_d);
 

@@ -1032,7 +1032,11 @@ __global__ void __launch_bounds__(256) k_finalize(Model M, Batch Bt, StepOpts o,
     if (tid < D2) { Rb[tid] = Bt.Rbar[b * D2 + tid]; Ub[tid] = Bt.Ubar[b * D2 + tid]; }
     __syncthreads();
 
-    if (Abar && o.want_abar) {
+    if (Abar && o.want_abar && Bt.err && *Bt.err) {
+        // a tensor-core assembly of this step gave up on a wait: K at the solution is not
+        // trustworthy, so Abar is not produced (Pbar and the history come from exact residuals)
+        for (int e = tid; e < D4; e += blockDim.x) Abar[b * D4 + e] = NAN;
+    } else if (Abar && o.want_abar) {
         // a11: B = sum_i G_i^T Ahat_i,  A0 = sum_i wJ A_i, Ahat_i = At_i Xi_i (Xi: dH = E_kl F_mu)
         double *Bm = reinterpret_cast<double *>(smem);              // [n][D2]
         double *A0 = Bm + (size_t)n * D2;                          // [D4]

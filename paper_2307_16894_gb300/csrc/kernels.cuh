@@ -54,6 +54,7 @@ struct Batch {
     double *U_prev;          // [B][d2] stretch of the last converged step (learned start features), may be null
     double *r0_prev;         // [B] residual norm of the previous-step predictor when last evaluated (+inf
                              // if never), the reference of the learned start; may be null
+    const int *err;          // tensor-core pipeline error flag (a bounded wait gave up), may be null
 };
 
 // learned Newton start (mlp.cu)

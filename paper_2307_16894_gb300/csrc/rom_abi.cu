@@ -572,7 +572,7 @@ static bool tc_path(const rom_ctx *ctx, const Model &M, int precision) {
 static int launch_assembly(rom_ctx *ctx, const Model &M, Batch bt, const StepOpts &o, int32_t *nxt, cudaStream_t s) {
     if (M.d == 3 && ctx->tc3_img && o.precision >= 1) {
         if (o.precision == 1) return launch_tc3(3, M, bt, ctx->tc3_img, ctx->d_err, 0, s);
-        const int r = launch_tc3(o.precision == 3 ? 1 : 2, M, bt, ctx->tc3_img, ctx->d_err, 1, s);
+        const int r = launch_tc3(o.precision == 3 ? 1 : 4, M, bt, ctx->tc3_img, ctx->d_err, 1, s);
         return r ? r : launch_tc3(3, M, bt, ctx->tc3_img, ctx->d_err, 2, s);
     }
     if (o.precision >= 2)
@@ -599,6 +599,7 @@ static rom_status run_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts, co
     const Model M = make_model(ctx);
     Batch bt = st->bt;
     bt.mu = ctx->mu;
+    bt.err = ctx->d_err;
     int32_t *lists[2] = {st->bt.list, st->list2};
     const double n = M.n, m = M.m, d2 = M.d2, d4 = d2 * d2;
     // algorithmic FLOPs per active instance: kinematics and force 2 m d2 n each; Y = At G: 2 m d4 n;
@@ -608,6 +609,7 @@ static rom_status run_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts, co
     const double fl_asm = tcp ? 2 * m * d4 * n + 2 * m * d2 * n * n : 2 * m * d4 * n + m * d2 * n * (n + 1) + 2 * m * d2 * n;
     const double fl_kin = 2 * m * d2 * n;
     const double fl_lu = 2 * n * n * n / 3 + 2 * n * n;
+    if (ctx->d_err) CK(cudaMemsetAsync(ctx->d_err, 0, 4, ctx->stream));   // tensor-core error flag of this step
     if (timed(ctx, 0, 0.0, [&] { return launch_start(M, bt, Fbar_d, o, nullptr, ctx->stream); }, 2))
         return fail(ctx, ROM_E_ARG, "launch_start");
     if (o.start == ROM_START_MLP) {
@@ -684,11 +686,13 @@ static rom_status capture_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts
     const Model M = make_model(ctx);
     Batch bt = st->bt;
     bt.mu = ctx->mu;
+    bt.err = ctx->d_err;
     const int max_pass = (opts->max_iter + 1) * (opts->max_ls + 1) + 2;
     cudaStream_t cs = st->gstream;
     cudaGraph_t graph = nullptr;
     CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     int bad = 0;
+    if (ctx->d_err) cudaMemsetAsync(ctx->d_err, 0, 4, cs);   // tensor-core error flag of this step
     bad |= launch_start(M, bt, st->io_F, o, nullptr, cs);
     launch_reset_pass(bt, cs);
     if (o.start == ROM_START_MLP) {

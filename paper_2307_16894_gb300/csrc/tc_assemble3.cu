@@ -191,8 +191,14 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
 }
 
 // image offsets (bytes) inside the per-model image buffer
+// A operand of the Y-MMA (k_assemble_tc4): for the cubature point pair (2p, 2p+1) of a chunk the
+// block-diagonal [G_2p^T 0; 0 G_2p+1^T] as 128 rows (s, j) x 24 K slots (s', q; 9 used per
+// point), TF32, canonical K-major layout (SBO 768 B)
+constexpr int AY_SBO = 6 * 128;
+constexpr int AY_BYTES = 16 * AY_SBO;
+
 struct ImgLayout {
-    size_t g32, bf16, tf_hi, tf_lo, total;
+    size_t g32, bf16, tf_hi, tf_lo, ay, total;
     int nch;
 };
 
@@ -203,7 +209,8 @@ __host__ __device__ inline ImgLayout img_layout(int m) {
     L.bf16 = L.g32 + (size_t)L.nch * GS_BYTES;
     L.tf_hi = L.bf16 + (size_t)L.nch * Cfg<1>::B_BYTES;
     L.tf_lo = L.tf_hi + (size_t)L.nch * Cfg<2>::B_BYTES;
-    L.total = L.tf_lo + (size_t)L.nch * Cfg<2>::B_BYTES;
+    L.ay = L.tf_lo + (size_t)L.nch * Cfg<2>::B_BYTES;
+    L.total = L.ay + (size_t)L.nch * 2 * AY_BYTES;
     return L;
 }
 
@@ -316,16 +323,16 @@ __global__ void __launch_bounds__(tc3::Cfg<MODE>::THREADS, 1)
                 float y[D2][4];
 #pragma unroll
                 for (int cc = 0; cc < D2; ++cc) {
-                    float y0 = 0.f, y1 = 0.f, y2 = 0.f, y3 = 0.f;
+                    // Y = At^T G: K[j][l] = sum G[q][j] At[q][cc] G[cc][l]; packed FP32 pairs (FFMA2)
+                    float2 y01 = make_float2(0.f, 0.f), y23 = make_float2(0.f, 0.f);
 #pragma unroll
                     for (int q = 0; q < D2; ++q) {
-                        const float av = a[q * D2 + cc];   // Y = At^T G: K[j][l] = sum G[q][j] At[q][cc] G[cc][l]
-                        y0 = fmaf(av, g[q].x, y0);
-                        y1 = fmaf(av, g[q].y, y1);
-                        y2 = fmaf(av, g[q].z, y2);
-                        y3 = fmaf(av, g[q].w, y3);
+                        const float av = a[q * D2 + cc];
+                        const float2 aa = make_float2(av, av);
+                        y01 = __ffma2_rn(aa, make_float2(g[q].x, g[q].y), y01);
+                        y23 = __ffma2_rn(aa, make_float2(g[q].z, g[q].w), y23);
                     }
-                    y[cc][0] = y0; y[cc][1] = y1; y[cc][2] = y2; y[cc][3] = y3;
+                    y[cc][0] = y01.x; y[cc][1] = y01.y; y[cc][2] = y23.x; y[cc][3] = y23.y;
                 }
 #pragma unroll
                 for (int jj = 0; jj < 4; ++jj) {
@@ -480,6 +487,333 @@ __global__ void __launch_bounds__(tc3::Cfg<MODE>::THREADS, 1)
     }
 }
 
+// ---------------------------------------------------------------- Y on the tensor cores
+// k_assemble_tc4 (TF32): the same K_b = Y_b^T G, but Y = At^T G is formed by the tensor cores as
+// well.  For a pair of cubature points (2p, 2p+1) of a chunk, one Y-MMA computes
+//   D_Y[(s, j)][(inst, c)] = sum_q G_{2p+s}[q][j] At_{inst, 2p+s}[q][c]      (M 128, N 80, K 24)
+// with the block-diagonal A = [G_2p^T 0; 0 G_2p+1^T] (a pre-arranged image) and B = the tangents
+// of the 8 instances of the CTA (rows (inst, c), written by the producer warps); converter warps
+// read D_Y from tensor memory (lane (s, j) holds 72 values), round them to TF32 and store them as
+// rows (inst, j) of the K-GEMM A tiles, and the control thread then issues the K-MMAs of the
+// chunk (4 instance pairs, M 128, N 64, K 48) into one tensor-memory accumulator per pair.
+// Roles: warps 0-3 converters (tensor-memory lane quadrants), warps 4-7 producers (tangent
+// staging with cp.async, B operand of the Y-MMA), warp 8 control (bulk copies of the images,
+// MMA issue, commits).  A_K is single-buffered: the converters write chunk c + 1 after the K-MMAs
+// of chunk c completed; the Y-MMAs of chunk c + 1 overlap with the conversion of chunk c.
+namespace tc4 {
+using tc3::D2;
+using tc3::D4;
+using tc3::PC;
+using tc3::NCOLS;
+constexpr int NI = 8, NP = 4;                    // instances, instance pairs per CTA
+constexpr int NY = 80;                           // Y-MMA N: 8 instances x 9 components + 8 zero rows
+constexpr int BY_SBO = 6 * 128;                  // B_Y: 80 rows x 24 TF32 slots
+constexpr int BY_BYTES = 10 * BY_SBO;
+constexpr int KP = 12, KC = PC * KP;             // K-MMA K per chunk: 4 points x 12 slots
+constexpr int SBO_A = (KC / 4) * 128 + 16;       // A_K rows (inst, j); +16 B spreads row groups over banks
+constexpr int A_BYTES = 16 * SBO_A;
+constexpr int B_BYTES = tc3::Cfg<2>::B_BYTES;    // the TF32 (hi) B-operand image of G
+constexpr int SBO_B = tc3::Cfg<2>::SBO_B;
+constexpr int AS_BYTES = NI * D4 * PC * 4;
+constexpr int OFF_AK = 0;
+constexpr int OFF_AY = OFF_AK + NP * A_BYTES;
+constexpr int OFF_BK = OFF_AY + 2 * 2 * tc3::AY_BYTES;
+constexpr int OFF_BY = OFF_BK + 2 * B_BYTES;
+constexpr int OFF_AS = OFF_BY + 2 * BY_BYTES;
+constexpr int SMEM = OFF_AS + 2 * AS_BYTES;
+constexpr int THREADS = 288;
+constexpr int TMEM_Y = 256;                      // D_K[ip] at columns 64 ip, D_Y[pp] at 256 + 128 pp
+constexpr uint32_t IDESC_Y = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NY >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+constexpr uint32_t IDESC_K = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NCOLS >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+}
+
+// named barrier `id` over `nthreads` threads with an OR reduction
+__device__ __forceinline__ int bar_or_id(int id, int nthreads, int pred) {
+    int r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.b32 p, %1, 0;\n bar.red.or.pred q, %2, %3, p;\n selp.b32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"(pred), "r"(id), "r"(nthreads)
+        : "memory");
+    return r;
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t *r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t *r) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+}  // namespace tc4
+
+__global__ void __launch_bounds__(tc4::THREADS, 1)
+    k_assemble_tc4(Model M, Batch Bt, const unsigned char *__restrict__ img, int *err_flag, int sel) {
+    using namespace tc3;
+    using namespace tc4;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar_fay[2], bar_fbk[2], bar_by[2], bar_y[2], bar_yfree[2], bar_ak, bar_k;
+    __shared__ uint32_t tmem_base;
+    __shared__ int64_t bI[NI];
+    __shared__ volatile int abort_s;
+    __shared__ int n_sel;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n_act = Bt.counts[0];
+    const int p0 = NI * blockIdx.x;
+    if (p0 >= n_act) return;
+    const int n = M.n, m = M.m, mA = M.mA;
+    const ImgLayout L = img_layout(m);
+    const int nch = L.nch;
+    const float *At = reinterpret_cast<const float *>(Bt.At);
+    float *As[2] = {reinterpret_cast<float *>(smem + OFF_AS), reinterpret_cast<float *>(smem + OFF_AS + AS_BYTES)};
+
+    if (tid == 0) n_sel = 0;
+    __syncthreads();
+    if (tid < NI) {
+        int64_t b = -1;
+        if (p0 + tid < n_act) {
+            b = Bt.list[p0 + tid];
+            if (sel != 0 && ((Bt.ctl[b].acc_k != 0) != (sel == 2))) b = -1;
+        }
+        bI[tid] = b;
+        if (b >= 0) atomicAdd(&n_sel, 1);
+    }
+    __syncthreads();
+    if (n_sel == 0) return;
+    if (warp == 8) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&bar_fay[s], 1);
+            mbar_init(&bar_fbk[s], 1);
+            mbar_init(&bar_by[s], 128);
+            mbar_init(&bar_y[s], 1);
+            mbar_init(&bar_yfree[s], 128);
+        }
+        mbar_init(&bar_ak, 128);
+        mbar_init(&bar_k, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_s = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+
+    if (warp < 4) {
+        // ------------------------------------------------------------------ converters
+        const int row = tid, sp = row >> 6, j = row & 63;
+        int local_abort = 0;
+        for (int c = 0; c < nch; ++c) {
+            if (bar_or_id(2, 128, local_abort | abort_s)) break;
+            const uint32_t par = (uint32_t)c & 1u;
+            if (c >= 1 && !mbar_wait(&bar_k, par ^ 1u, &abort_s)) { local_abort = 1; continue; }
+            for (int pp = 0; pp < 2; ++pp) {
+                if (!mbar_wait(&bar_y[pp], par, &abort_s)) { local_abort = 1; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                uint32_t v[72];
+                const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(TMEM_Y + 128 * pp);
+                tmem_ld32(ta, v);
+                tmem_ld32(ta + 32, v + 32);
+                tmem_ld8(ta + 64, v + 64);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                mbar_arrive(&bar_yfree[pp]);
+                const int kb = 3 * (2 * pp + sp);
+#pragma unroll
+                for (int inst = 0; inst < NI; ++inst) {
+                    unsigned char *Ak = smem + OFF_AK + (size_t)(inst >> 1) * A_BYTES;
+                    const int r = (inst & 1) * 64 + j;
+                    const size_t rb = (size_t)(r >> 3) * SBO_A + (size_t)(r & 7) * 16;
+                    uint32_t h[D2];
+#pragma unroll
+                    for (int cc = 0; cc < D2; ++cc) h[cc] = tf32_bits(__uint_as_float(v[inst * D2 + cc]));
+                    *reinterpret_cast<uint4 *>(Ak + rb + (size_t)kb * 128) = make_uint4(h[0], h[1], h[2], h[3]);
+                    *reinterpret_cast<uint4 *>(Ak + rb + (size_t)(kb + 1) * 128) = make_uint4(h[4], h[5], h[6], h[7]);
+                    *reinterpret_cast<uint4 *>(Ak + rb + (size_t)(kb + 2) * 128) = make_uint4(h[8], 0u, 0u, 0u);
+                }
+            }
+            if (local_abort) continue;
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(&bar_ak);
+        }
+    } else if (warp < 8) {
+        // ------------------------------------------------------------------ producers
+        const int ptid = tid - 128;
+        auto prefetch = [&](int c, int buf) {
+            const int c0 = c * PC;
+            for (int e = ptid; e < NI * D4; e += 128) {
+                const int ie = e / D4, ce = e - ie * D4;
+                const int64_t be = bI[ie];
+                if (be >= 0) cp_async16(As[buf] + (size_t)e * PC, At + ((size_t)be * D4 + ce) * mA + c0);
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        prefetch(0, 0);
+        int local_abort = 0;
+        for (int c = 0; c < nch; ++c) {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            if (bar_or_id(1, 128, local_abort | abort_s)) break;   // also: chunk c's tangents visible
+            if (c + 1 < nch) prefetch(c + 1, (c + 1) & 1);
+            const float *as = As[c & 1];
+            for (int pp = 0; pp < 2; ++pp) {
+                if (c >= 1 && !mbar_wait(&bar_y[pp], (uint32_t)(c - 1) & 1u, &abort_s)) { local_abort = 1; break; }
+                unsigned char *By = smem + OFF_BY + (size_t)pp * BY_BYTES;
+                for (int e = ptid; e < 2 * NY; e += 128) {
+                    const int nrow = e % NY, sq = e / NY;
+                    const int inst = nrow / D2, cc = nrow - inst * D2;
+                    const int pt = 2 * pp + sq;
+                    const bool valid = nrow < NI * D2 && bI[inst] >= 0 && c * PC + pt < m;
+                    uint32_t h[12];
+#pragma unroll
+                    for (int q = 0; q < 12; ++q)
+                        h[q] = (valid && q < D2) ? tf32_bits(as[((size_t)inst * D4 + q * D2 + cc) * PC + pt]) : 0u;
+                    const size_t rb = (size_t)(nrow >> 3) * BY_SBO + (size_t)(nrow & 7) * 16 + (size_t)(3 * sq) * 128;
+                    *reinterpret_cast<uint4 *>(By + rb) = make_uint4(h[0], h[1], h[2], h[3]);
+                    *reinterpret_cast<uint4 *>(By + rb + 128) = make_uint4(h[4], h[5], h[6], h[7]);
+                    *reinterpret_cast<uint4 *>(By + rb + 256) = make_uint4(h[8], h[9], h[10], h[11]);
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(&bar_by[pp]);
+            }
+        }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+    } else if (lane == 0) {
+        // ------------------------------------------------------------- control thread
+        int ay_pend[2] = {0, 0}, bk_pend[2] = {0, 0};
+        uint32_t ay_par[2] = {0, 0}, bk_par[2] = {0, 0};
+        int k_pending = 0;
+        uint32_t k_par = 0;
+        auto copy_ay = [&](int c) {
+            const int s = c & 1;
+            mbar_expect_tx(&bar_fay[s], 2 * AY_BYTES);
+            bulk_g2s(smem + OFF_AY + (size_t)s * 2 * AY_BYTES, img + L.ay + (size_t)c * 2 * AY_BYTES, 2 * AY_BYTES,
+                     &bar_fay[s]);
+            ay_pend[s] = 1;
+            ay_par[s] = (uint32_t)(c >> 1) & 1u;
+        };
+        auto copy_bk = [&](int c) {
+            const int s = c & 1;
+            mbar_expect_tx(&bar_fbk[s], B_BYTES);
+            bulk_g2s(smem + OFF_BK + (size_t)s * B_BYTES, img + L.tf_hi + (size_t)c * B_BYTES, B_BYTES, &bar_fbk[s]);
+            bk_pend[s] = 1;
+            bk_par[s] = (uint32_t)(c >> 1) & 1u;
+        };
+        copy_ay(0);
+        copy_bk(0);
+        if (nch > 1) { copy_ay(1); copy_bk(1); }
+        for (int c = 0; c < nch; ++c) {
+            const int s = c & 1;
+            const uint32_t par = (uint32_t)c & 1u, spar = (uint32_t)(c >> 1) & 1u;
+            if (!mbar_wait(&bar_fay[s], spar, &abort_s)) break;
+            ay_pend[s] = 0;
+            bool ok = true;
+            for (int pp = 0; pp < 2 && ok; ++pp) {
+                if (!mbar_wait(&bar_by[pp], par, &abort_s)) { ok = false; break; }
+                if (c >= 1 && !mbar_wait(&bar_yfree[pp], par ^ 1u, &abort_s)) { ok = false; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t a0 = smem_u32(smem + OFF_AY + (size_t)s * 2 * AY_BYTES + (size_t)pp * AY_BYTES);
+                const uint32_t b0 = smem_u32(smem + OFF_BY + (size_t)pp * BY_BYTES);
+                const uint32_t d = tmem + (uint32_t)(TMEM_Y + 128 * pp);
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    mma_tf32(d, make_desc(a0 + k * 256, 128, AY_SBO), make_desc(b0 + k * 256, 128, BY_SBO), IDESC_Y,
+                             k > 0 ? 1u : 0u);
+                mma_commit(&bar_y[pp]);
+            }
+            if (!ok) break;
+            if (c + 2 < nch) {   // A_Y stage s is free once this chunk's Y-MMAs are done
+                if (!mbar_wait(&bar_y[1], par, &abort_s)) break;
+                copy_ay(c + 2);
+            }
+            if (c >= 1) {        // B_K stage (c + 1) & 1 is free once the K-MMAs of chunk c - 1 are done
+                if (!mbar_wait(&bar_k, par ^ 1u, &abort_s)) break;
+                k_pending = 0;
+                if (c + 1 < nch && c + 1 >= 2) copy_bk(c + 1);
+            }
+            if (!mbar_wait(&bar_fbk[s], spar, &abort_s)) break;
+            bk_pend[s] = 0;
+            if (!mbar_wait(&bar_ak, par, &abort_s)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t bk0 = smem_u32(smem + OFF_BK + (size_t)s * B_BYTES);
+#pragma unroll 1
+            for (int ip = 0; ip < NP; ++ip) {
+                const uint32_t ak0 = smem_u32(smem + OFF_AK + (size_t)ip * A_BYTES);
+                const uint32_t d = tmem + (uint32_t)(ip * NCOLS);
+#pragma unroll
+                for (int k = 0; k < KC / 8; ++k)
+                    mma_tf32(d, make_desc(ak0 + k * 256, 128, SBO_A), make_desc(bk0 + k * 256, 128, SBO_B), IDESC_K,
+                             (c > 0 || k > 0) ? 1u : 0u);
+            }
+            mma_commit(&bar_k);
+            k_pending = 1;
+            k_par = par;
+        }
+        // drain: the last commit covers every MMA issued before it; outstanding copies must land
+        if (k_pending && !mbar_wait(&bar_k, k_par, &abort_s)) {
+            const unsigned long long t0 = now_ns();
+            while (!mbar_test(&bar_k, k_par) && now_ns() - t0 < WAIT_NS) {}
+        }
+        for (int s = 0; s < 2; ++s) {
+            if (ay_pend[s]) {
+                const unsigned long long t0 = now_ns();
+                while (!mbar_test(&bar_fay[s], ay_par[s]) && now_ns() - t0 < WAIT_NS) {}
+            }
+            if (bk_pend[s]) {
+                const unsigned long long t0 = now_ns();
+                while (!mbar_test(&bar_fbk[s], bk_par[s]) && now_ns() - t0 < WAIT_NS) {}
+            }
+        }
+        if (abort_s && err_flag) atomicExch(err_flag, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!abort_s && warp < 4) {
+        // epilogue: warp w reads tensor-memory lanes 32 w .. 32 w + 31 of the four pair accumulators
+        const int row = warp * 32 + lane, ih = row >> 6, j = row & 63;
+        for (int ip = 0; ip < NP; ++ip) {
+            uint32_t v[64];
+            const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ip * NCOLS);
+            tmem_ld32(ta, v);
+            tmem_ld32(ta + 32, v + 32);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const int64_t b = bI[2 * ip + ih];
+            if (j < n && b >= 0) {
+                double *Kb = Bt.K + (size_t)b * n * n + (size_t)j * n;
+#pragma unroll
+                for (int k = 0; k < NCOLS; ++k)
+                    if (k < n) Kb[k] = (double)__uint_as_float(v[k]);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 8) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+    }
+}
+
 // ------------------------------------------------------------------------ host side
 
 size_t tc3_image_bytes(int m) { return tc3::img_layout(m).total; }
@@ -528,6 +862,14 @@ void tc3_build_images(int n, int m, const double *G, unsigned char *img) {
                         memcpy(img + L.tf_hi + off, &hi, 4);
                         memcpy(img + L.tf_lo + off, &lo, 4);
                     }
+                    {   // Y-MMA A operand: point pt of the chunk = point s of pair pt / 2
+                        const int pp = pt >> 1, sp = pt & 1;
+                        const int r = sp * 64 + l, k = sp * 12 + q;
+                        const size_t off = (size_t)(c * 2 + pp) * AY_BYTES + (size_t)(r >> 3) * AY_SBO + (size_t)(k >> 2) * 128 +
+                                           (size_t)(r & 7) * 16 + (size_t)(k & 3) * 4;
+                        const float t = tf32_round_host((float)g);
+                        memcpy(img + L.ay + off, &t, 4);
+                    }
                 }
             }
 }
@@ -542,12 +884,22 @@ static int launch_tc3_t(const Model &M, Batch Bt, const unsigned char *img, int 
     return 0;
 }
 
-// mode 1 BF16, 2 TF32, 3 TF32 split (FP32-accurate); sel 0 = all listed instances, 1 = those
-// without, 2 = those with the accurate-stiffness flag (Ctl::acc_k)
+static int launch_tc4(const Model &M, Batch Bt, const unsigned char *img, int *err, int sel, cudaStream_t s) {
+    if (M.d != 3 || M.n > tc3::NCOLS || (M.mA & 3)) return -1;
+    cudaFuncSetAttribute(k_assemble_tc4, cudaFuncAttributeMaxDynamicSharedMemorySize, tc4::SMEM);
+    const int grid = (int)((Bt.B + tc4::NI - 1) / tc4::NI);
+    k_assemble_tc4<<<grid, tc4::THREADS, tc4::SMEM, s>>>(M, Bt, img, err, sel);
+    return 0;
+}
+
+// mode 1 BF16, 2 TF32 (Y on the CUDA cores), 3 TF32 split (FP32-accurate), 4 TF32 with Y on the
+// tensor cores; sel 0 = all listed instances, 1 = those without, 2 = those with the
+// accurate-stiffness flag (Ctl::acc_k)
 int launch_tc3(int mode, const Model &M, Batch Bt, const unsigned char *img, int *err, int sel, cudaStream_t s) {
     return mode == 1 ? launch_tc3_t<1>(M, Bt, img, err, sel, s)
          : mode == 2 ? launch_tc3_t<2>(M, Bt, img, err, sel, s)
-         : mode == 3 ? launch_tc3_t<3>(M, Bt, img, err, sel, s) : -1;
+         : mode == 3 ? launch_tc3_t<3>(M, Bt, img, err, sel, s)
+         : mode == 4 ? launch_tc4(M, Bt, img, err, sel, s) : -1;
 }
 
 }  // namespace podecm
