@@ -497,9 +497,11 @@ __global__ void __launch_bounds__(tc3::Cfg<MODE>::THREADS, 1)
 // rows (inst, j) of the K-GEMM A tiles, and the control thread then issues the K-MMAs of the
 // chunk (4 instance pairs, M 128, N 64, K 48) into one tensor-memory accumulator per pair.
 // Roles: warps 0-3 converters (tensor-memory lane quadrants), warps 4-7 producers (tangent
-// staging with cp.async, B operand of the Y-MMA), warp 8 control (bulk copies of the images,
-// MMA issue, commits).  A_K is single-buffered: the converters write chunk c + 1 after the K-MMAs
-// of chunk c completed; the Y-MMAs of chunk c + 1 overlap with the conversion of chunk c.
+// staging with cp.async, both Y-MMA operands: the block-diagonal A is assembled in shared memory
+// from the K-GEMM B tile of the chunk, so only that tile comes from L2), warp 8 control (bulk
+// copies of the B tiles into a 3-stage ring, MMA issue, commits).  A_K is single-buffered: the
+// converters write chunk c + 1 after the K-MMAs of chunk c completed; the Y-MMAs of chunk c + 1
+// overlap with the conversion of chunk c.
 namespace tc4 {
 using tc3::D2;
 using tc3::D4;
@@ -515,10 +517,11 @@ constexpr int A_BYTES = 16 * SBO_A;
 constexpr int B_BYTES = tc3::Cfg<2>::B_BYTES;    // the TF32 (hi) B-operand image of G
 constexpr int SBO_B = tc3::Cfg<2>::SBO_B;
 constexpr int AS_BYTES = NI * D4 * PC * 4;
+constexpr int NBK = 3;                           // B tile ring stages
 constexpr int OFF_AK = 0;
 constexpr int OFF_AY = OFF_AK + NP * A_BYTES;
 constexpr int OFF_BK = OFF_AY + 2 * 2 * tc3::AY_BYTES;
-constexpr int OFF_BY = OFF_BK + 2 * B_BYTES;
+constexpr int OFF_BY = OFF_BK + NBK * B_BYTES;
 constexpr int OFF_AS = OFF_BY + 2 * BY_BYTES;
 constexpr int SMEM = OFF_AS + 2 * AS_BYTES;
 constexpr int THREADS = 288;
@@ -567,7 +570,7 @@ __global__ void __launch_bounds__(tc4::THREADS, 1)
     using namespace tc3;
     using namespace tc4;
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bar_fay[2], bar_fbk[2], bar_by[2], bar_y[2], bar_yfree[2], bar_ak, bar_k;
+    __shared__ __align__(8) uint64_t bar_fbk[NBK], bar_by[2], bar_y[2], bar_yfree[2], bar_ak, bar_k;
     __shared__ uint32_t tmem_base;
     __shared__ int64_t bI[NI];
     __shared__ volatile int abort_s;
@@ -602,9 +605,8 @@ __global__ void __launch_bounds__(tc4::THREADS, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
+        for (int s = 0; s < NBK; ++s) mbar_init(&bar_fbk[s], 1);
         for (int s = 0; s < 2; ++s) {
-            mbar_init(&bar_fay[s], 1);
-            mbar_init(&bar_fbk[s], 1);
             mbar_init(&bar_by[s], 128);
             mbar_init(&bar_y[s], 1);
             mbar_init(&bar_yfree[s], 128);
@@ -668,6 +670,9 @@ __global__ void __launch_bounds__(tc4::THREADS, 1)
             }
             asm volatile("cp.async.commit_group;" ::: "memory");
         };
+        // the off-diagonal blocks of the Y-MMA A operand stay zero
+        for (int e = ptid; e < 2 * 2 * AY_BYTES / 16; e += 128)
+            reinterpret_cast<uint4 *>(smem + OFF_AY)[e] = make_uint4(0u, 0u, 0u, 0u);
         prefetch(0, 0);
         int local_abort = 0;
         for (int c = 0; c < nch; ++c) {
@@ -675,8 +680,22 @@ __global__ void __launch_bounds__(tc4::THREADS, 1)
             if (bar_or_id(1, 128, local_abort | abort_s)) break;   // also: chunk c's tangents visible
             if (c + 1 < nch) prefetch(c + 1, (c + 1) & 1);
             const float *as = As[c & 1];
+            const int kst = c % NBK;
+            if (!mbar_wait(&bar_fbk[kst], (uint32_t)(c / NBK) & 1u, &abort_s)) { local_abort = 1; continue; }
             for (int pp = 0; pp < 2; ++pp) {
+                // Y-MMA (c - 1, pp) done: B_Y[pp] free, and (with pp = 1) every MMA reading A_Y stage c & 1
                 if (c >= 1 && !mbar_wait(&bar_y[pp], (uint32_t)(c - 1) & 1u, &abort_s)) { local_abort = 1; break; }
+                if (pp == 0 && c >= 2 && !mbar_wait(&bar_y[1], (uint32_t)(c - 1) & 1u, &abort_s)) { local_abort = 1; break; }
+                // A_Y[c & 1][pp]: core matrices of the B tile, rows (s, j) <- B rows j, K blocks of point 2 pp + s
+                unsigned char *Ay = smem + OFF_AY + (size_t)((c & 1) * 2 + pp) * AY_BYTES;
+                const unsigned char *Bk = smem + OFF_BK + (size_t)kst * B_BYTES;
+                for (int e = ptid; e < 2 * 64 * 3; e += 128) {
+                    const int t = e % 3, r2 = e / 3, j = r2 % 64, sq = r2 / 64;
+                    const uint4 v = *reinterpret_cast<const uint4 *>(Bk + (size_t)(j >> 3) * SBO_B +
+                                                                      (size_t)(3 * (2 * pp + sq) + t) * 128 + (size_t)(j & 7) * 16);
+                    const int r = sq * 64 + j;
+                    *reinterpret_cast<uint4 *>(Ay + (size_t)(r >> 3) * AY_SBO + (size_t)(3 * sq + t) * 128 + (size_t)(r & 7) * 16) = v;
+                }
                 unsigned char *By = smem + OFF_BY + (size_t)pp * BY_BYTES;
                 for (int e = ptid; e < 2 * NY; e += 128) {
                     const int nrow = e % NY, sq = e / NY;
@@ -699,39 +718,29 @@ __global__ void __launch_bounds__(tc4::THREADS, 1)
         asm volatile("cp.async.wait_group 0;" ::: "memory");
     } else if (lane == 0) {
         // ------------------------------------------------------------- control thread
-        int ay_pend[2] = {0, 0}, bk_pend[2] = {0, 0};
-        uint32_t ay_par[2] = {0, 0}, bk_par[2] = {0, 0};
+        int bk_pend[NBK] = {0, 0, 0};
+        uint32_t bk_par[NBK] = {0, 0, 0};
         int k_pending = 0;
         uint32_t k_par = 0;
-        auto copy_ay = [&](int c) {
-            const int s = c & 1;
-            mbar_expect_tx(&bar_fay[s], 2 * AY_BYTES);
-            bulk_g2s(smem + OFF_AY + (size_t)s * 2 * AY_BYTES, img + L.ay + (size_t)c * 2 * AY_BYTES, 2 * AY_BYTES,
-                     &bar_fay[s]);
-            ay_pend[s] = 1;
-            ay_par[s] = (uint32_t)(c >> 1) & 1u;
-        };
         auto copy_bk = [&](int c) {
-            const int s = c & 1;
-            mbar_expect_tx(&bar_fbk[s], B_BYTES);
-            bulk_g2s(smem + OFF_BK + (size_t)s * B_BYTES, img + L.tf_hi + (size_t)c * B_BYTES, B_BYTES, &bar_fbk[s]);
-            bk_pend[s] = 1;
-            bk_par[s] = (uint32_t)(c >> 1) & 1u;
+            const int st = c % NBK;
+            mbar_expect_tx(&bar_fbk[st], B_BYTES);
+            bulk_g2s(smem + OFF_BK + (size_t)st * B_BYTES, img + L.tf_hi + (size_t)c * B_BYTES, B_BYTES, &bar_fbk[st]);
+            bk_pend[st] = 1;
+            bk_par[st] = (uint32_t)(c / NBK) & 1u;
         };
-        copy_ay(0);
-        copy_bk(0);
-        if (nch > 1) { copy_ay(1); copy_bk(1); }
+        for (int c = 0; c < NBK && c < nch; ++c) copy_bk(c);
         for (int c = 0; c < nch; ++c) {
-            const int s = c & 1;
-            const uint32_t par = (uint32_t)c & 1u, spar = (uint32_t)(c >> 1) & 1u;
-            if (!mbar_wait(&bar_fay[s], spar, &abort_s)) break;
-            ay_pend[s] = 0;
+            const int s = c & 1, kst = c % NBK;
+            const uint32_t par = (uint32_t)c & 1u;
+            if (!mbar_wait(&bar_fbk[kst], (uint32_t)(c / NBK) & 1u, &abort_s)) break;
+            bk_pend[kst] = 0;
             bool ok = true;
             for (int pp = 0; pp < 2 && ok; ++pp) {
                 if (!mbar_wait(&bar_by[pp], par, &abort_s)) { ok = false; break; }
                 if (c >= 1 && !mbar_wait(&bar_yfree[pp], par ^ 1u, &abort_s)) { ok = false; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t a0 = smem_u32(smem + OFF_AY + (size_t)s * 2 * AY_BYTES + (size_t)pp * AY_BYTES);
+                const uint32_t a0 = smem_u32(smem + OFF_AY + (size_t)(s * 2 + pp) * AY_BYTES);
                 const uint32_t b0 = smem_u32(smem + OFF_BY + (size_t)pp * BY_BYTES);
                 const uint32_t d = tmem + (uint32_t)(TMEM_Y + 128 * pp);
 #pragma unroll
@@ -741,20 +750,14 @@ __global__ void __launch_bounds__(tc4::THREADS, 1)
                 mma_commit(&bar_y[pp]);
             }
             if (!ok) break;
-            if (c + 2 < nch) {   // A_Y stage s is free once this chunk's Y-MMAs are done
-                if (!mbar_wait(&bar_y[1], par, &abort_s)) break;
-                copy_ay(c + 2);
-            }
-            if (c >= 1) {        // B_K stage (c + 1) & 1 is free once the K-MMAs of chunk c - 1 are done
+            if (c >= 1) {        // B stage (c + 2) % 3 = (c - 1) % 3 is free once the K-MMAs of chunk c - 1 are done
                 if (!mbar_wait(&bar_k, par ^ 1u, &abort_s)) break;
                 k_pending = 0;
-                if (c + 1 < nch && c + 1 >= 2) copy_bk(c + 1);
+                if (c + 2 < nch) copy_bk(c + 2);
             }
-            if (!mbar_wait(&bar_fbk[s], spar, &abort_s)) break;
-            bk_pend[s] = 0;
             if (!mbar_wait(&bar_ak, par, &abort_s)) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t bk0 = smem_u32(smem + OFF_BK + (size_t)s * B_BYTES);
+            const uint32_t bk0 = smem_u32(smem + OFF_BK + (size_t)kst * B_BYTES);
 #pragma unroll 1
             for (int ip = 0; ip < NP; ++ip) {
                 const uint32_t ak0 = smem_u32(smem + OFF_AK + (size_t)ip * A_BYTES);
@@ -773,16 +776,11 @@ __global__ void __launch_bounds__(tc4::THREADS, 1)
             const unsigned long long t0 = now_ns();
             while (!mbar_test(&bar_k, k_par) && now_ns() - t0 < WAIT_NS) {}
         }
-        for (int s = 0; s < 2; ++s) {
-            if (ay_pend[s]) {
+        for (int st = 0; st < NBK; ++st)
+            if (bk_pend[st]) {
                 const unsigned long long t0 = now_ns();
-                while (!mbar_test(&bar_fay[s], ay_par[s]) && now_ns() - t0 < WAIT_NS) {}
+                while (!mbar_test(&bar_fbk[st], bk_par[st]) && now_ns() - t0 < WAIT_NS) {}
             }
-            if (bk_pend[s]) {
-                const unsigned long long t0 = now_ns();
-                while (!mbar_test(&bar_fbk[s], bk_par[s]) && now_ns() - t0 < WAIT_NS) {}
-            }
-        }
         if (abort_s && err_flag) atomicExch(err_flag, 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
