@@ -114,11 +114,14 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
     return done != 0;
 }
 
-// bounded wait; gives up early when another thread of the CTA has raised the abort flag
+// bounded wait; gives up early when another thread of the CTA has raised the abort flag.  Between
+// polls the thread sleeps briefly, so that waiting warps leave the issue slots of their SM
+// sub-partition to the warps that work.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
     if (mbar_test(bar, parity)) return true;
     const unsigned long long t0 = now_ns();
     for (;;) {
+        __nanosleep(40);
         if (mbar_test(bar, parity)) return true;
         if (*abort_flag) return false;
         if (now_ns() - t0 > WAIT_NS) {
@@ -158,10 +161,11 @@ __device__ __forceinline__ int bar_or(int nthreads, int pred) {
     return r;
 }
 
+// TF32 rounding (nearest, ties away from zero) by integer operations on the bit pattern: add half
+// of the 13 dropped mantissa bits to the magnitude and clear them (finite inputs; two integer
+// instructions instead of a conversion-unit instruction)
 __device__ __forceinline__ uint32_t tf32_bits(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
+    return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
