@@ -345,7 +345,9 @@ def kernel_rooflines(r, peaks):
         pk = bf16 * (1.0 if prec == "bf16" else 0.5)
         add("assemble", "tensor", prof["assemble"][2], pk,
             src + " bf16_tflops" + ("" if prec == "bf16" else " x 0.5 (TF32 rate)"))
-        add("force", "alu", prof["force"][2], FP64_PEAK_TFLOPS, "FP64 pipe")
+        # double-float residual: 12 FP32 pipe operations per multiply-add
+        add("force", "alu", prof["force"][2], FP32_PEAK_TFLOPS / 12,
+            "FP32 pipe / 12: double-float multiply-add of 12 FP32 operations")
     elif prec == "fp64":
         add("assemble", "alu", prof["assemble"][2], FP64_PEAK_TFLOPS, "FP64 pipe")
     else:

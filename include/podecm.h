@@ -214,6 +214,12 @@ rom_status rom_debug_stiffness(rom_ctx *ctx, const rom_state *st, double *K);
  * w_i J_i sum_{t,u} Finv_i[r][t] dP_i[a][t]/dF[c][u] Finv_i[s][u]; element type double after a
  * ROM_PREC_FP64 step, float otherwise.  Valid for the instances of the last pass.  Blocking. */
 rom_status rom_debug_tangent(rom_ctx *ctx, const rom_state *st, void *At, int64_t bytes);
+/* Diagnostics: the reduced residual r[B][n] = sum_i w_i J_i G_i^T vec(P_i F_mu,i^-T) of the last
+ * evaluated iterate (Eq. of the ECM force vector, Sec. 3.2) and, when `v` is not NULL, the weighted
+ * pulled-back stresses v[B][d*d][m] it was formed from (entry (b, a*d + r, i)).  The residual is
+ * formed in FP64 after a ROM_PREC_FP64 step and in double-float arithmetic (FP32 pairs) on the
+ * mixed-precision tensor-core paths.  Valid for the instances of the last pass.  Blocking. */
+rom_status rom_debug_residual(rom_ctx *ctx, const rom_state *st, double *r, double *v);
 rom_status rom_profile_read(rom_ctx *ctx, int kernel, double *ms, int64_t *launches, double *flops);
 
 /* ---------------------------------------------------------------------------

@@ -26,7 +26,7 @@ EXPORTED = ["rom_create", "rom_destroy", "rom_load_basis", "rom_load_cubature", 
             "rom_step_device", "rom_sync", "rom_last_error", "rom_profile", "rom_profile_read",
             "rom_step_noalloc", "rom_mlp_init", "rom_mlp_nparams", "rom_mlp_params", "rom_mlp_norm",
             "rom_mlp_train_step", "rom_mlp_loss_grad", "rom_mlp_predict", "rom_features", "rom_debug_stiffness",
-            "rom_debug_tangent", "rom_use_graphs",
+            "rom_debug_tangent", "rom_debug_residual", "rom_use_graphs",
             "rom_state_bytes", "rom_autotune", "rom_serve"]
 
 KERNEL_GROUPS = ["start", "constitutive", "assemble", "solve", "finalize", "bookkeeping", "learned_start", "force"]
@@ -295,6 +295,14 @@ class State:
         At = np.empty((self.B, d4, mA), dtype=np.float64 if fp64 else np.float32)
         c._check(c.L.rom_debug_tangent(c.h, self.h, _p(At), At.nbytes), "rom_debug_tangent")
         return At[:, :, :c.m]
+
+    def residual(self):
+        """(r [B, n], v [B, d*d, m]) of the last pass (diagnostics)."""
+        c = self.ctx
+        r = np.empty((self.B, c.n))
+        v = np.empty((self.B, c.dim * c.dim, c.m))
+        c._check(c.L.rom_debug_residual(c.h, self.h, _p(r), _p(v)), "rom_debug_residual")
+        return r, v
 
     def export(self, history=True):
         """(a [B, n], C^p^-1 [B, m, nc], xi [B, m]); history=False skips the last two (None)."""

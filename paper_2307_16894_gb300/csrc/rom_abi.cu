@@ -63,6 +63,7 @@ struct rom_ctx {
     double *G_pt = nullptr, *G_T = nullptr, *w = nullptr, *Gmu_T = nullptr, *mu = nullptr;
     float *G32 = nullptr;
     float *G32h_T = nullptr, *G32l_T = nullptr;   // double-float split of G_T (mixed-precision kinematics)
+    float2 *Gdf = nullptr;                        // double-float split of G in v order (mixed-precision residual)
     int32_t *phase = nullptr;
     // host-call staging
     double *h_stage = nullptr;      // pinned
@@ -189,6 +190,7 @@ rom_status rom_destroy(rom_ctx *ctx) {
     p = ctx->G32; dfree(p);
     p = ctx->G32h_T; dfree(p);
     p = ctx->G32l_T; dfree(p);
+    p = ctx->Gdf; dfree(p);
     p = ctx->w; dfree(p);
     p = ctx->Gmu_T; dfree(p);
     p = ctx->mu; dfree(p);
@@ -249,6 +251,19 @@ rom_status rom_load_basis(rom_ctx *ctx, int n, int m, const double *G) {
         if ((s = dalloc(ctx, (void **)&ctx->G32l_T, cnt * 4)) != ROM_OK) return s;
         CK(cudaMemcpy(ctx->G32h_T, gh.data(), cnt * 4, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(ctx->G32l_T, gl.data(), cnt * 4, cudaMemcpyHostToDevice));
+    }
+    p = ctx->Gdf; dfree(p); ctx->Gdf = nullptr;
+    {
+        std::vector<float2> gdf(cnt);
+        for (int c = 0; c < d2; ++c)
+            for (int i = 0; i < m; ++i)
+                for (int j = 0; j < n; ++j) {
+                    const double g = G[((size_t)i * d2 + c) * n + j];
+                    const float h = (float)g;
+                    gdf[((size_t)c * m + i) * n + j] = make_float2(h, (float)(g - (double)h));
+                }
+        if ((s = dalloc(ctx, (void **)&ctx->Gdf, cnt * 8)) != ROM_OK) return s;
+        CK(cudaMemcpy(ctx->Gdf, gdf.data(), cnt * 8, cudaMemcpyHostToDevice));
     }
     for (int f = 0; f < 2; ++f) { p = ctx->tc_img[f]; dfree(p); ctx->tc_img[f] = nullptr; }
     p = ctx->tc3_img; dfree(p); ctx->tc3_img = nullptr;
@@ -500,7 +515,7 @@ static Model make_model(const rom_ctx *ctx) {
     M.nphase = ctx->nphase; M.ncp = ctx->dim == 2 ? 4 : 6;
     M.mA = (ctx->m + 3) & ~3;
     M.G_pt = ctx->G_pt; M.G_T = ctx->G_T; M.G32_pt = ctx->G32; M.w = ctx->w; M.phase = ctx->phase;
-    M.G32h_T = ctx->G32h_T; M.G32l_T = ctx->G32l_T;
+    M.G32h_T = ctx->G32h_T; M.G32l_T = ctx->G32l_T; M.Gdf = ctx->Gdf;
     M.Gmu_T = ctx->Gmu_T; M.omega = ctx->omega;
     return M;
 }
@@ -938,6 +953,15 @@ rom_status rom_debug_tangent(rom_ctx *ctx, const rom_state *st, void *At, int64_
     CK(cudaStreamSynchronize(ctx->stream));
     const size_t have = (size_t)st->B * ctx->dim * ctx->dim * ctx->dim * ctx->dim * (size_t)((st->m + 3) & ~3) * 8;
     CK(cudaMemcpy(At, st->bt.At, std::min((size_t)bytes, have), cudaMemcpyDeviceToHost));
+    return ROM_OK;
+}
+
+rom_status rom_debug_residual(rom_ctx *ctx, const rom_state *st, double *r, double *v) {
+    if (!ctx || !st || !r || st->ctx != ctx) return ROM_E_ARG;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpy(r, st->bt.r, (size_t)st->B * st->n * 8, cudaMemcpyDeviceToHost));
+    if (v) CK(cudaMemcpy(v, st->bt.v, (size_t)st->B * ctx->dim * ctx->dim * st->m * 8, cudaMemcpyDeviceToHost));
     return ROM_OK;
 }
 

@@ -297,6 +297,95 @@ __global__ void __launch_bounds__(256) k_force(Model M, Batch Bt) {
     }
 }
 
+// Mixed-precision residual r_b = sum_k Gdf[k] v_b[k] (k = (component, point) in the order of v) in
+// double-float arithmetic: G is held as an FP32 (hi, lo) pair, each v element is split once when it
+// is staged, products are formed by TwoProd with the two cross terms and summed by TwoSum with a
+// separate FP32 compensation (Ogita, Rump & Oishi 2005), ~1e-13 relative to sum |terms|.  The FP64
+// pipe of this GPU runs at 1/64 of the FP32 rate, so the 12 FP32 operations of one double-float
+// multiply-add cost ~5x less than one DFMA.  The instances share G: a CTA of 256 threads takes
+// FDF_NI instances and 64 columns j (blockIdx.y), thread (j, ig) accumulates FDF_IPT instances, and
+// the v rows of all FDF_NI instances pass through a double-buffered shared-memory chunk.  Each
+// thread sums its rows in a fixed order, so the result does not depend on the launch.
+constexpr int FDF_RC = 64;                 // rows per staged chunk
+constexpr int FDF_IPT = 4;                 // instances per thread
+constexpr int FDF_NI = 4 * FDF_IPT;        // instances per CTA (4 groups of 64 columns)
+constexpr int FDF_LD = FDF_NI * FDF_RC / 256;   // staged elements per thread and chunk
+
+__device__ __forceinline__ void df_mac(float &s, float &er, float2 g, float2 v) {
+    const float pr = __fmul_rn(g.x, v.x);
+    float e = fmaf(g.x, v.x, -pr);
+    e = fmaf(g.x, v.y, e);
+    e = fmaf(g.y, v.x, e);
+    const float sn = __fadd_rn(s, pr);
+    const float bb = __fsub_rn(sn, s);
+    const float t = __fadd_rn(__fsub_rn(s, __fsub_rn(sn, bb)), __fsub_rn(pr, bb));
+    s = sn;
+    er = __fadd_rn(er, __fadd_rn(t, e));
+}
+
+__global__ void __launch_bounds__(256) k_force_df(Model M, Batch Bt) {
+    __shared__ float2 vs[2][FDF_NI][FDF_RC];
+    const int n_act = Bt.counts[0];
+    const int p0 = blockIdx.x * FDF_NI;
+    if (p0 >= n_act) return;
+    const int n = M.n, K = M.m * M.d2;
+    const int tid = threadIdx.x, ig = tid >> 6;
+    const int j = blockIdx.y * 64 + (tid & 63);
+    const int nch = (K + FDF_RC - 1) / FDF_RC;
+    // staging map: element e = tid + 256 t of a chunk is row e % FDF_RC of instance slot e / FDF_RC
+    const double *vrow[FDF_LD];
+#pragma unroll
+    for (int t = 0; t < FDF_LD; ++t) {
+        const int e = tid + 256 * t, slot = e / FDF_RC;
+        vrow[t] = (p0 + slot < n_act) ? Bt.v + (size_t)Bt.list[p0 + slot] * K + (e % FDF_RC) : nullptr;
+    }
+    double pre[FDF_LD];
+    auto load = [&](int c) {
+#pragma unroll
+        for (int t = 0; t < FDF_LD; ++t) {
+            const int k = c * FDF_RC + (tid + 256 * t) % FDF_RC;
+            pre[t] = (vrow[t] && k < K) ? vrow[t][(size_t)c * FDF_RC] : 0.0;
+        }
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int t = 0; t < FDF_LD; ++t) {
+            const int e = tid + 256 * t;
+            const float h = (float)pre[t];
+            vs[buf][e / FDF_RC][e % FDF_RC] = make_float2(h, (float)(pre[t] - (double)h));
+        }
+    };
+    float s[FDF_IPT], er[FDF_IPT];
+#pragma unroll
+    for (int u = 0; u < FDF_IPT; ++u) { s[u] = 0.f; er[u] = 0.f; }
+    load(0);
+    store(0);
+    __syncthreads();
+    const bool colok = j < n;
+    for (int c = 0; c < nch; ++c) {
+        if (c + 1 < nch) load(c + 1);
+        const int k0 = c * FDF_RC, rows = min(FDF_RC, K - k0);
+        const float2 *g = M.Gdf + (size_t)k0 * n + j;
+        const float2 (*vb)[FDF_RC] = vs[c & 1] + ig * FDF_IPT;
+        if (colok) {
+#pragma unroll 4
+            for (int r = 0; r < rows; ++r) {
+                const float2 gg = __ldg(g + (size_t)r * n);
+#pragma unroll
+                for (int u = 0; u < FDF_IPT; ++u) df_mac(s[u], er[u], gg, vb[u][r]);
+            }
+        }
+        if (c + 1 < nch) store((c + 1) & 1);
+        __syncthreads();
+    }
+    if (colok)
+#pragma unroll
+        for (int u = 0; u < FDF_IPT; ++u) {
+            const int p = p0 + ig * FDF_IPT + u;
+            if (p < n_act) Bt.r[(size_t)Bt.list[p] * n + j] = (double)s[u] + (double)er[u];
+        }
+}
+
 // bytes of one B-operand chunk image and the chunk count for a model
 void tc_image_shape(int d, int fmt, int m, int *chunk_bytes, int *nchunks) {
     const int d2 = d * d;
@@ -349,9 +438,16 @@ static int launch_tc_t(const Model &M, Batch Bt, const unsigned char *img, int *
     return 0;
 }
 
-// FP64 residual r = sum_i G_i^T v_i of the listed instances (paths whose stiffness kernel does not
-// produce it)
-void launch_force(const Model &M, Batch Bt, cudaStream_t s) { k_force<<<(int)Bt.B, 256, 0, s>>>(M, Bt); }
+// residual r = sum_i G_i^T v_i of the listed instances (paths whose stiffness kernel does not
+// produce it): double-float when the model carries the split image of G, else FP64
+void launch_force(const Model &M, Batch Bt, cudaStream_t s) {
+    if (M.Gdf) {
+        const dim3 grid((unsigned)((Bt.B + FDF_NI - 1) / FDF_NI), (unsigned)((M.n + 63) / 64));
+        k_force_df<<<grid, 256, 0, s>>>(M, Bt);
+    } else {
+        k_force<<<(int)Bt.B, 256, 0, s>>>(M, Bt);
+    }
+}
 
 int launch_tc(int fmt, const Model &M, Batch Bt, const unsigned char *img, int *err, cudaStream_t s) {
     if (M.d == 2) return fmt == 1 ? launch_tc_t<2, 1>(M, Bt, img, err, s) : launch_tc_t<2, 2>(M, Bt, img, err, s);
