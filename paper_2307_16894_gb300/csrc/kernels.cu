@@ -823,17 +823,16 @@ __device__ void abar_sums_f64(const Model &M, const Batch &Bt, int64_t b, int CH
     __syncthreads();
 }
 
-// the same sums from the FP32 tangent of the mixed-precision path, in FP32.  The tangent and
-// basis chunks are staged with cp.async one chunk ahead (double-buffered).  Thread
-// (j = tid % 32 (+32, +64, +96), group = tid / 32) accumulates B[j][0..D2) over the points
-// i = group (mod blockDim / 32) of each chunk, and A0 is split over D4-thread point groups; the
-// group sums are added in a fixed order (in FP64).
-// work (floats) = Fm32 [2][CHF][D2] | (16-byte aligned) As [2][D4][CHF] | Gs [2][CHF][D2][n] |
-// Ah [CHF][D4]; the group sums reuse the work area.  CHF must be a multiple of 4.
-__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
-                 : "memory");
-}
+// the same sums from the FP32 tangent of the mixed-precision path, in FP32.  The tangent chunks
+// (CHF points) are staged with cp.async one chunk ahead (double-buffered) and Ahat_i = At_i Xi_i
+// is formed for the chunk in shared memory.  Thread (tj = tid % JG, pg = tid / JG) accumulates
+// B[4 tj .. 4 tj + 3][0..D2) (36 FP32 accumulators in 3D) over the points pg, pg + NPG, ... of
+// each chunk, reading G (FP32, shared by all instances and resident in L2) straight from global
+// memory, so that each loaded value feeds D2 (G) or 4 (Ahat) multiply-adds; A0 is split over
+// D4-thread point groups.  The group sums are added in a fixed order (in FP64).
+// work (floats, 16-byte aligned) = As [2][D4][CHF] | Fm32 [2][CHF][D2] | Ah [CHF][D4]; the group
+// sums reuse the work area.  CHF must be a multiple of 4.
+constexpr int ABAR_JT = 4;   // columns j per thread in the FP32 B sums
 __device__ __forceinline__ void cp_async16_f(void *dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
                  : "memory");
@@ -842,29 +841,28 @@ __device__ __forceinline__ void cp_async16_f(void *dst, const void *src) {
 template <int D>
 __device__ void abar_sums_f32(const Model &M, const Batch &Bt, int64_t b, int CHF, double *Bm, double *A0,
                               float *work) {
-    constexpr int D2 = D * D, D4 = D2 * D2;
+    constexpr int D2 = D * D, D4 = D2 * D2, JT = ABAR_JT;
     const int n = M.n, m = M.m, mA = M.mA, tid = threadIdx.x;
-    float *Fm32[2] = {work, work + (size_t)CHF * D2};
-    float *abase = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(Fm32[1] + (size_t)CHF * D2) + 15) &
-                                             ~uintptr_t(15));   // cp.async targets: 16-byte aligned
-    float *As[2] = {abase, abase + (size_t)D4 * CHF};
-    float *Gs[2] = {As[1] + (size_t)D4 * CHF, As[1] + (size_t)D4 * CHF + (size_t)CHF * D2 * n};
-    float *Ah = Gs[1] + (size_t)CHF * D2 * n;
+    float *As[2], *Fm32[2];
+    As[0] = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(work) + 15) & ~uintptr_t(15));
+    As[1] = As[0] + (size_t)D4 * CHF;
+    Fm32[0] = As[1] + (size_t)D4 * CHF;
+    Fm32[1] = Fm32[0] + (size_t)CHF * D2;
+    float *Ah = Fm32[1] + (size_t)CHF * D2;
     const float *At = reinterpret_cast<const float *>(Bt.At);
-    const int jl = tid & 31, grp = tid >> 5, NGRP = blockDim.x >> 5;
+    const int JG = (n + JT - 1) / JT, NPG = blockDim.x / JG;
+    const int tj = tid % JG, pg = tid / JG;
+    const bool bact = pg < NPG, vec4 = (n & 3) == 0;
     const int AG = blockDim.x / D4, ag = tid / D4, ae = tid - ag * D4;   // A0: AG point groups
     const int nch = (m + CHF - 1) / CHF;
     auto stage = [&](int c) {
         const int c0 = c * CHF, ch = min(CHF, m - c0), buf = c & 1;
         const int q4 = CHF / 4;
-        for (int e = tid; e < D4 * q4; e += blockDim.x) {   // At rows: CHF floats from c0 (inside mA)
+        for (int e = tid; e < D4 * q4; e += blockDim.x) {   // At rows: CHF floats from c0, inside the row
             const int ce = e / q4, qq = e - ce * q4;
-            cp_async16_f(As[buf] + (size_t)ce * CHF + 4 * qq, At + ((size_t)b * D4 + ce) * mA + c0 + 4 * qq);
+            if (c0 + 4 * qq < mA)
+                cp_async16_f(As[buf] + (size_t)ce * CHF + 4 * qq, At + ((size_t)b * D4 + ce) * mA + c0 + 4 * qq);
         }
-        const int gcount = ch * D2 * n, g4 = gcount >> 2;
-        const float *gsrc = M.G32_pt + (size_t)c0 * D2 * n;
-        for (int e = tid; e < g4; e += blockDim.x) cp_async16_f(Gs[buf] + 4 * e, gsrc + 4 * e);
-        for (int e = 4 * g4 + tid; e < gcount; e += blockDim.x) cp_async4(Gs[buf] + e, gsrc + e);
         asm volatile("cp.async.commit_group;" ::: "memory");
         for (int e = tid; e < ch * D2; e += blockDim.x) {
             const int ii = e / D2, ar = e - ii * D2;
@@ -875,11 +873,11 @@ __device__ void abar_sums_f32(const Model &M, const Batch &Bt, int64_t b, int CH
             Fm32[buf][ii * D2 + ar] = (float)s;
         }
     };
-    float bacc[4][D2];
+    float acc[JT][D2];
 #pragma unroll
-    for (int h = 0; h < 4; ++h)
+    for (int t = 0; t < JT; ++t)
 #pragma unroll
-        for (int kl = 0; kl < D2; ++kl) bacc[h][kl] = 0.f;
+        for (int kl = 0; kl < D2; ++kl) acc[t][kl] = 0.f;
     float aacc = 0.f;
     stage(0);
     for (int c = 0; c < nch; ++c) {
@@ -887,35 +885,41 @@ __device__ void abar_sums_f32(const Model &M, const Batch &Bt, int64_t b, int CH
         asm volatile("cp.async.wait_group 0;" ::: "memory");
         __syncthreads();
         if (c + 1 < nch) stage(c + 1);
-        const float *as = As[buf], *fm = Fm32[buf], *gs = Gs[buf];
+        const float *as = As[buf], *fm = Fm32[buf];
         for (int e = tid; e < CHF * D4; e += blockDim.x) {   // consecutive threads: consecutive points
             const int ii = e % CHF, rem = e / CHF;
             if (ii >= ch) continue;
             const int ar = rem / D2, kl = rem - ar * D2;
             const int k = kl / D, l = kl - k * D;
-            float s = 0.f;
+            float sacc = 0.f;
 #pragma unroll
-            for (int ss = 0; ss < D; ++ss) s = fmaf(as[(ar * D2 + k * D + ss) * CHF + ii], fm[ii * D2 + l * D + ss], s);
-            Ah[ii * D4 + rem] = s;
+            for (int ss = 0; ss < D; ++ss)
+                sacc = fmaf(as[(ar * D2 + k * D + ss) * CHF + ii], fm[ii * D2 + l * D + ss], sacc);
+            Ah[ii * D4 + rem] = sacc;
         }
         __syncthreads();
-        for (int ii = grp; ii < ch; ii += NGRP) {
+        if (bact)
+            for (int ii = pg; ii < ch; ii += NPG) {
+                const float *ah = Ah + ii * D4;
+                const float *g = M.G32_pt + (size_t)(c0 + ii) * D2 * n + JT * tj;
 #pragma unroll
-            for (int ar = 0; ar < D2; ++ar) {
-                float a[D2];
+                for (int ar = 0; ar < D2; ++ar) {
+                    float gv[JT];
+                    if (vec4) {
+                        const float4 t4 = __ldg(reinterpret_cast<const float4 *>(g + (size_t)ar * n));
+                        gv[0] = t4.x; gv[1] = t4.y; gv[2] = t4.z; gv[3] = t4.w;
+                    } else {
 #pragma unroll
-                for (int kl = 0; kl < D2; ++kl) a[kl] = Ah[ii * D4 + ar * D2 + kl];
+                        for (int t = 0; t < JT; ++t) gv[t] = (JT * tj + t < n) ? __ldg(g + (size_t)ar * n + t) : 0.f;
+                    }
 #pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const int j = jl + 32 * h;
-                    if (j < n) {
-                        const float g = gs[(ii * D2 + ar) * n + j];
+                    for (int kl = 0; kl < D2; ++kl) {
+                        const float av = ah[ar * D2 + kl];
 #pragma unroll
-                        for (int kl = 0; kl < D2; ++kl) bacc[h][kl] = fmaf(g, a[kl], bacc[h][kl]);
+                        for (int t = 0; t < JT; ++t) acc[t][kl] = fmaf(gv[t], av, acc[t][kl]);
                     }
                 }
             }
-        }
         if (ag < AG) {
             const int ij = ae / D2, kl = ae - ij * D2;
             const int ia = ij / D, jb = ij - ia * D;
@@ -925,27 +929,28 @@ __device__ void abar_sums_f32(const Model &M, const Batch &Bt, int64_t b, int CH
         }
     }
     __syncthreads();
-    float *red = work;   // [NGRP][n][D2], then [AG][D4]
+    float *red = As[0];   // [NPG][n][D2], then [AG][D4]
+    if (bact)
 #pragma unroll
-    for (int h = 0; h < 4; ++h) {
-        const int j = jl + 32 * h;
-        if (j < n)
+        for (int t = 0; t < JT; ++t) {
+            const int j = JT * tj + t;
+            if (j < n)
 #pragma unroll
-            for (int kl = 0; kl < D2; ++kl) red[((size_t)grp * n + j) * D2 + kl] = bacc[h][kl];
-    }
+                for (int kl = 0; kl < D2; ++kl) red[((size_t)pg * n + j) * D2 + kl] = acc[t][kl];
+        }
     __syncthreads();
     for (int e = tid; e < n * D2; e += blockDim.x) {
-        double s = 0.0;
-        for (int g = 0; g < NGRP; ++g) s += (double)red[(size_t)g * n * D2 + e];
-        Bm[e] = s;
+        double sacc = 0.0;
+        for (int g = 0; g < NPG; ++g) sacc += (double)red[(size_t)g * n * D2 + e];
+        Bm[e] = sacc;
     }
     __syncthreads();
     if (ag < AG) red[ag * D4 + ae] = aacc;
     __syncthreads();
     if (tid < D4) {
-        double s = 0.0;
-        for (int g = 0; g < AG; ++g) s += (double)red[g * D4 + tid];
-        A0[tid] = s;
+        double sacc = 0.0;
+        for (int g = 0; g < AG; ++g) sacc += (double)red[g * D4 + tid];
+        A0[tid] = sacc;
     }
     __syncthreads();
 }
@@ -983,7 +988,7 @@ __device__ void schur_abar(const Model &M, const Batch &Bt, int64_t b, const dou
 }
 
 template <int D, typename TT>
-__global__ void __launch_bounds__(256) k_finalize(Model M, Batch Bt, StepOpts o, double *__restrict__ Pbar,
+__global__ void __launch_bounds__(256, D == 3 ? 3 : 4) k_finalize(Model M, Batch Bt, StepOpts o, double *__restrict__ Pbar,
                                                   double *__restrict__ Abar, void *info_v, int CHF) {
     constexpr int D2 = D * D, D4 = D2 * D2;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1043,7 +1048,8 @@ __global__ void __launch_bounds__(256) k_finalize(Model M, Batch Bt, StepOpts o,
         double *Bm = reinterpret_cast<double *>(smem);              // [n][D2]
         double *A0 = Bm + (size_t)n * D2;                          // [D4]
         double *Fm = A0 + D4;                                      // [CHF][D2]
-        unsigned char *work = reinterpret_cast<unsigned char *>(Fm + (size_t)CHF * D2);
+        // FP32 path: the sums' staging area starts at Fm (its FP64 chunk is not used)
+        unsigned char *work = reinterpret_cast<unsigned char *>(sizeof(TT) == 8 ? Fm + (size_t)CHF * D2 : Fm);
         if (sizeof(TT) == 8) abar_sums_f64<D>(M, Bt, b, CHF, Bm, A0, Fm, reinterpret_cast<double *>(work));
         else abar_sums_f32<D>(M, Bt, b, CHF, Bm, A0, reinterpret_cast<float *>(Fm));
         // Schur complement with the factor of K at the solution (K* = K)
@@ -1290,16 +1296,22 @@ static int launch_finalize_t(const Model &M, Batch Bt, const StepOpts &o, double
     // cubature points per chunk: small chunks keep the shared memory per CTA low (several CTAs per
     // SM hide the latency of this short, barrier-bound kernel)
     auto bytes = [&](int chf) {
-        const size_t head = (n * D2 + D4 + (size_t)chf * D2) * 8;              // Bm, A0, Fm (FP64 path)
-        // FP64 path: Ah, Gs after Fm; FP32 path: Fm32, As, Gs (double-buffered) and Ah from Fm on
-        const size_t sums = te == 8 ? ((size_t)chf * D4 + (size_t)chf * D2 * n) * 8
-                                    : ((size_t)2 * chf * D2 + 2 * (size_t)D4 * chf + 2 * (size_t)chf * D2 * n +
-                                       (size_t)chf * D4) * 4 + 16 - (size_t)chf * D2 * 8;
-        const size_t red = te == 4 ? (size_t)8 * n * D2 * 4 : 0;              // FP32 group sums
-        const size_t schur = ((n + 1) * n + (n + 1) * D2) * te + 16;          // K factor, RHS, pivot
-        return head + std::max(std::max(sums, red), schur);
+        // FP64 path: Bm, A0, Fm [chf][D2], then Ah, Gs; FP32 path: Bm, A0, then (16-byte aligned)
+        // As [2][D4][chf], Fm32 [2][chf][D2], Ah [chf][D4], or the group sums [NPG][n][D2]
+        if (te == 8) {
+            const size_t head = (n * D2 + D4 + (size_t)chf * D2) * 8;
+            const size_t sums = ((size_t)chf * D4 + (size_t)chf * D2 * n) * 8;
+            const size_t schur = ((n + 1) * n + (n + 1) * D2) * 8 + 16;
+            return head + std::max(sums, schur);
+        }
+        const size_t head = (n * D2 + D4) * 8;
+        const size_t npg = 256 / ((n + ABAR_JT - 1) / ABAR_JT);
+        const size_t sums = ((size_t)2 * D4 * chf + (size_t)2 * chf * D2 + (size_t)chf * D4) * 4;
+        const size_t red = std::max(npg * n * D2, (size_t)256) * 4;
+        const size_t schur = ((n + 1) * n + (n + 1) * D2) * 4 + 16;
+        return head + 16 + std::max(std::max(sums, red), schur);
     };
-    int CHF = 16;
+    int CHF = te == 8 ? 16 : 32;
     while (CHF > 4 && bytes(CHF) > (te == 8 ? 48 : 64) * 1024) CHF /= 2;
     const size_t sm = bytes(CHF);
     if (o.precision == 0) {
