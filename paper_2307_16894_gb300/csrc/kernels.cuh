@@ -27,8 +27,8 @@ struct Model {
     const float *G32_pt;   // [m][d2][n]
     const float *G32h_T;   // [d2][n][m] FP32 high part of G_T (mixed-precision kinematics), may be null
     const float *G32l_T;   // [d2][n][m] FP32 low part, G_T - G32h_T rounded to FP32
-    const float2 *Gdf;     // [d2][m][n] (hi, lo) FP32 split of G in the order of v (double-float
-                           // residual of the mixed-precision paths), may be null
+    const float2 *Gdf;     // [d2][m][n rounded up to even] (hi, lo) FP32 split of G in the order of v,
+                           // zero padded (double-float residual of the mixed-precision paths), may be null
     const double *w;       // [m]
     const int32_t *phase;  // [m]
     const double *Gmu_T;   // [d2][n_par][m]

@@ -254,16 +254,17 @@ rom_status rom_load_basis(rom_ctx *ctx, int n, int m, const double *G) {
     }
     p = ctx->Gdf; dfree(p); ctx->Gdf = nullptr;
     {
-        std::vector<float2> gdf(cnt);
+        const int np = (n + 1) & ~1;   // rows of 16-byte multiples
+        std::vector<float2> gdf((size_t)d2 * m * np, make_float2(0.f, 0.f));
         for (int c = 0; c < d2; ++c)
             for (int i = 0; i < m; ++i)
                 for (int j = 0; j < n; ++j) {
                     const double g = G[((size_t)i * d2 + c) * n + j];
                     const float h = (float)g;
-                    gdf[((size_t)c * m + i) * n + j] = make_float2(h, (float)(g - (double)h));
+                    gdf[((size_t)c * m + i) * np + j] = make_float2(h, (float)(g - (double)h));
                 }
-        if ((s = dalloc(ctx, (void **)&ctx->Gdf, cnt * 8)) != ROM_OK) return s;
-        CK(cudaMemcpy(ctx->Gdf, gdf.data(), cnt * 8, cudaMemcpyHostToDevice));
+        if ((s = dalloc(ctx, (void **)&ctx->Gdf, gdf.size() * 8)) != ROM_OK) return s;
+        CK(cudaMemcpy(ctx->Gdf, gdf.data(), gdf.size() * 8, cudaMemcpyHostToDevice));
     }
     for (int f = 0; f < 2; ++f) { p = ctx->tc_img[f]; dfree(p); ctx->tc_img[f] = nullptr; }
     p = ctx->tc3_img; dfree(p); ctx->tc3_img = nullptr;

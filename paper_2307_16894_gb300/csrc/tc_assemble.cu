@@ -303,13 +303,16 @@ __global__ void __launch_bounds__(256) k_force(Model M, Batch Bt) {
 // separate FP32 compensation (Ogita, Rump & Oishi 2005), ~1e-13 relative to sum |terms|.  The FP64
 // pipe of this GPU runs at 1/64 of the FP32 rate, so the 12 FP32 operations of one double-float
 // multiply-add cost ~5x less than one DFMA.  The instances share G: a CTA of 256 threads takes
-// FDF_NI instances and 64 columns j (blockIdx.y), thread (j, ig) accumulates FDF_IPT instances, and
-// the v rows of all FDF_NI instances pass through a double-buffered shared-memory chunk.  Each
-// thread sums its rows in a fixed order, so the result does not depend on the launch.
-constexpr int FDF_RC = 64;                 // rows per staged chunk
+// FDF_NI instances and 64 columns j (blockIdx.y), thread (j, ig) accumulates FDF_IPT instances.
+// Chunks of FDF_RC rows of G (cp.async) and of the v rows of the FDF_NI instances (through
+// registers, split on the way) are double-buffered in shared memory, so that the loads of the next
+// chunk overlap the arithmetic of this one.  Each thread sums its rows in a fixed order, so the
+// result does not depend on the launch.
+constexpr int FDF_RC = 32;                 // rows per staged chunk
 constexpr int FDF_IPT = 4;                 // instances per thread
 constexpr int FDF_NI = 4 * FDF_IPT;        // instances per CTA (4 groups of 64 columns)
-constexpr int FDF_LD = FDF_NI * FDF_RC / 256;   // staged elements per thread and chunk
+constexpr int FDF_LD = FDF_NI * FDF_RC / 256;   // staged v elements per thread and chunk
+constexpr int FDF_GLD = FDF_RC * 32 / 256;      // 16-byte G copies per thread and chunk
 
 __device__ __forceinline__ void df_mac(float &s, float &er, float2 g, float2 v) {
     const float pr = __fmul_rn(g.x, v.x);
@@ -323,16 +326,23 @@ __device__ __forceinline__ void df_mac(float &s, float &er, float2 g, float2 v) 
     er = __fadd_rn(er, __fadd_rn(t, e));
 }
 
+__device__ __forceinline__ void fdf_cp16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+
 __global__ void __launch_bounds__(256) k_force_df(Model M, Batch Bt) {
+    __shared__ __align__(16) float2 gs[2][FDF_RC][64];
     __shared__ float2 vs[2][FDF_NI][FDF_RC];
     const int n_act = Bt.counts[0];
     const int p0 = blockIdx.x * FDF_NI;
     if (p0 >= n_act) return;
-    const int n = M.n, K = M.m * M.d2;
-    const int tid = threadIdx.x, ig = tid >> 6;
-    const int j = blockIdx.y * 64 + (tid & 63);
+    const int n = M.n, np = (n + 1) & ~1, K = M.m * M.d2;
+    const int tid = threadIdx.x, ig = tid >> 6, jl = tid & 63;
+    const int j0 = blockIdx.y * 64, j = j0 + jl;
+    const int nc2 = min(64, np - j0) / 2;   // 16-byte column pairs of this column block
     const int nch = (K + FDF_RC - 1) / FDF_RC;
-    // staging map: element e = tid + 256 t of a chunk is row e % FDF_RC of instance slot e / FDF_RC
+    // v staging map: element e = tid + 256 t of a chunk is row e % FDF_RC of instance slot e / FDF_RC
     const double *vrow[FDF_LD];
 #pragma unroll
     for (int t = 0; t < FDF_LD; ++t) {
@@ -355,27 +365,43 @@ __global__ void __launch_bounds__(256) k_force_df(Model M, Batch Bt) {
             vs[buf][e / FDF_RC][e % FDF_RC] = make_float2(h, (float)(pre[t] - (double)h));
         }
     };
+    // G rows k0 .. k0 + FDF_RC of this column block (rows of the image are np pairs, 16-byte aligned)
+    auto stage_g = [&](int c) {
+        const int k0 = c * FDF_RC;
+#pragma unroll
+        for (int t = 0; t < FDF_GLD; ++t) {
+            const int e = tid + 256 * t, row = e >> 5, q = e & 31;
+            if (q < nc2 && k0 + row < K) fdf_cp16(&gs[c & 1][row][2 * q], M.Gdf + (size_t)(k0 + row) * np + j0 + 2 * q);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
     float s[FDF_IPT], er[FDF_IPT];
 #pragma unroll
     for (int u = 0; u < FDF_IPT; ++u) { s[u] = 0.f; er[u] = 0.f; }
+    stage_g(0);
     load(0);
     store(0);
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
     const bool colok = j < n;
     for (int c = 0; c < nch; ++c) {
-        if (c + 1 < nch) load(c + 1);
-        const int k0 = c * FDF_RC, rows = min(FDF_RC, K - k0);
-        const float2 *g = M.Gdf + (size_t)k0 * n + j;
+        if (c + 1 < nch) {
+            stage_g(c + 1);
+            load(c + 1);
+        }
+        const int rows = min(FDF_RC, K - c * FDF_RC);
         const float2 (*vb)[FDF_RC] = vs[c & 1] + ig * FDF_IPT;
+        const float2 (*gb)[64] = gs[c & 1];
         if (colok) {
 #pragma unroll 4
             for (int r = 0; r < rows; ++r) {
-                const float2 gg = __ldg(g + (size_t)r * n);
+                const float2 gg = gb[r][jl];
 #pragma unroll
                 for (int u = 0; u < FDF_IPT; ++u) df_mac(s[u], er[u], gg, vb[u][r]);
             }
         }
         if (c + 1 < nch) store((c + 1) & 1);
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
         __syncthreads();
     }
     if (colok)
