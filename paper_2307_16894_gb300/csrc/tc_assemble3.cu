@@ -503,9 +503,11 @@ __global__ void __launch_bounds__(tc3::Cfg<MODE>::THREADS, 1)
 // Roles: warps 0-3 converters (tensor-memory lane quadrants), warps 4-7 producers (tangent
 // staging with cp.async, both Y-MMA operands: the block-diagonal A is assembled in shared memory
 // from the K-GEMM B tile of the chunk, so only that tile comes from L2), warp 8 control (bulk
-// copies of the B tiles into a 3-stage ring, MMA issue, commits).  A_K is single-buffered: the
-// converters write chunk c + 1 after the K-MMAs of chunk c completed; the Y-MMAs of chunk c + 1
-// overlap with the conversion of chunk c.
+// copies of the B tiles into a 3-stage ring, MMA issue, commits).  A_K is split into two halves
+// (the K slots of point pair 0 and 1): the converters write half h of chunk c + 1 once the K-MMAs
+// of chunk c that read it are done, and the control thread issues the K-MMAs of half 0, the
+// Y-MMA of the next chunk's first point pair, the K-MMAs of half 1 and the second Y-MMA, so
+// that conversion, Y and K overlap.
 namespace tc4 {
 using tc3::D2;
 using tc3::D4;
@@ -574,7 +576,9 @@ __global__ void __launch_bounds__(tc4::THREADS, 1)
     using namespace tc3;
     using namespace tc4;
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bar_fbk[NBK], bar_by[2], bar_y[2], bar_yfree[2], bar_ak, bar_k;
+    // bar_akh[h] / bar_kh[h]: A_K half h (the K slots of point pair h) written by the converters /
+    // the K-MMAs reading it done
+    __shared__ __align__(8) uint64_t bar_fbk[NBK], bar_by[2], bar_y[2], bar_yfree[2], bar_akh[2], bar_kh[2];
     __shared__ uint32_t tmem_base;
     __shared__ int64_t bI[NI];
     __shared__ volatile int abort_s;
@@ -614,9 +618,9 @@ __global__ void __launch_bounds__(tc4::THREADS, 1)
             mbar_init(&bar_by[s], 128);
             mbar_init(&bar_y[s], 1);
             mbar_init(&bar_yfree[s], 128);
+            mbar_init(&bar_akh[s], 128);
+            mbar_init(&bar_kh[s], 1);
         }
-        mbar_init(&bar_ak, 128);
-        mbar_init(&bar_k, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         abort_s = 0;
     }
@@ -632,8 +636,9 @@ __global__ void __launch_bounds__(tc4::THREADS, 1)
         for (int c = 0; c < nch; ++c) {
             if (bar_or_id(2, 128, local_abort | abort_s)) break;
             const uint32_t par = (uint32_t)c & 1u;
-            if (c >= 1 && !mbar_wait(&bar_k, par ^ 1u, &abort_s)) { local_abort = 1; continue; }
             for (int pp = 0; pp < 2; ++pp) {
+                // A_K half pp is free once the K-MMAs of chunk c - 1 that read it are done
+                if (c >= 1 && !mbar_wait(&bar_kh[pp], par ^ 1u, &abort_s)) { local_abort = 1; break; }
                 if (!mbar_wait(&bar_y[pp], par, &abort_s)) { local_abort = 1; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 uint32_t v[72];
@@ -657,10 +662,9 @@ __global__ void __launch_bounds__(tc4::THREADS, 1)
                     *reinterpret_cast<uint4 *>(Ak + rb + (size_t)(kb + 1) * 128) = make_uint4(h[4], h[5], h[6], h[7]);
                     *reinterpret_cast<uint4 *>(Ak + rb + (size_t)(kb + 2) * 128) = make_uint4(h[8], 0u, 0u, 0u);
                 }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(&bar_akh[pp]);
             }
-            if (local_abort) continue;
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_arrive(&bar_ak);
         }
     } else if (warp < 8) {
         // ------------------------------------------------------------------ producers
@@ -722,10 +726,13 @@ __global__ void __launch_bounds__(tc4::THREADS, 1)
         asm volatile("cp.async.wait_group 0;" ::: "memory");
     } else if (lane == 0) {
         // ------------------------------------------------------------- control thread
+        // issue order per chunk c: K-MMAs of half 0 (chunk c), Y-MMA of point pair 0 (chunk c + 1),
+        // K-MMAs of half 1, Y-MMA of point pair 1, so that the Y of the next chunk and the
+        // conversion of its first half overlap the K-GEMM of this chunk
         int bk_pend[NBK] = {0, 0, 0};
         uint32_t bk_par[NBK] = {0, 0, 0};
-        int k_pending = 0;
-        uint32_t k_par = 0;
+        uint64_t *last_bar = nullptr;   // the last commit covers every MMA issued before it
+        uint32_t last_par = 0;
         auto copy_bk = [&](int c) {
             const int st = c % NBK;
             mbar_expect_tx(&bar_fbk[st], B_BYTES);
@@ -733,52 +740,59 @@ __global__ void __launch_bounds__(tc4::THREADS, 1)
             bk_pend[st] = 1;
             bk_par[st] = (uint32_t)(c / NBK) & 1u;
         };
-        for (int c = 0; c < NBK && c < nch; ++c) copy_bk(c);
-        for (int c = 0; c < nch; ++c) {
-            const int s = c & 1, kst = c % NBK;
+        auto issue_y = [&](int c, int pp) -> bool {
             const uint32_t par = (uint32_t)c & 1u;
-            if (!mbar_wait(&bar_fbk[kst], (uint32_t)(c / NBK) & 1u, &abort_s)) break;
-            bk_pend[kst] = 0;
-            bool ok = true;
-            for (int pp = 0; pp < 2 && ok; ++pp) {
-                if (!mbar_wait(&bar_by[pp], par, &abort_s)) { ok = false; break; }
-                if (c >= 1 && !mbar_wait(&bar_yfree[pp], par ^ 1u, &abort_s)) { ok = false; break; }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t a0 = smem_u32(smem + OFF_AY + (size_t)(s * 2 + pp) * AY_BYTES);
-                const uint32_t b0 = smem_u32(smem + OFF_BY + (size_t)pp * BY_BYTES);
-                const uint32_t d = tmem + (uint32_t)(TMEM_Y + 128 * pp);
-#pragma unroll
-                for (int k = 0; k < 3; ++k)
-                    mma_tf32(d, make_desc(a0 + k * 256, 128, AY_SBO), make_desc(b0 + k * 256, 128, BY_SBO), IDESC_Y,
-                             k > 0 ? 1u : 0u);
-                mma_commit(&bar_y[pp]);
-            }
-            if (!ok) break;
-            if (c >= 1) {        // B stage (c + 2) % 3 = (c - 1) % 3 is free once the K-MMAs of chunk c - 1 are done
-                if (!mbar_wait(&bar_k, par ^ 1u, &abort_s)) break;
-                k_pending = 0;
-                if (c + 2 < nch) copy_bk(c + 2);
-            }
-            if (!mbar_wait(&bar_ak, par, &abort_s)) break;
+            if (!mbar_wait(&bar_by[pp], par, &abort_s)) return false;
+            if (c >= 1 && !mbar_wait(&bar_yfree[pp], par ^ 1u, &abort_s)) return false;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t bk0 = smem_u32(smem + OFF_BK + (size_t)kst * B_BYTES);
+            const uint32_t a0 = smem_u32(smem + OFF_AY + (size_t)((c & 1) * 2 + pp) * AY_BYTES);
+            const uint32_t b0 = smem_u32(smem + OFF_BY + (size_t)pp * BY_BYTES);
+            const uint32_t d = tmem + (uint32_t)(TMEM_Y + 128 * pp);
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                mma_tf32(d, make_desc(a0 + k * 256, 128, AY_SBO), make_desc(b0 + k * 256, 128, BY_SBO), IDESC_Y,
+                         k > 0 ? 1u : 0u);
+            mma_commit(&bar_y[pp]);
+            last_bar = &bar_y[pp];
+            last_par = par;
+            return true;
+        };
+        auto issue_k = [&](int c, int h) -> bool {
+            const uint32_t par = (uint32_t)c & 1u;
+            if (!mbar_wait(&bar_akh[h], par, &abort_s)) return false;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t bk0 = smem_u32(smem + OFF_BK + (size_t)(c % NBK) * B_BYTES);
 #pragma unroll 1
             for (int ip = 0; ip < NP; ++ip) {
                 const uint32_t ak0 = smem_u32(smem + OFF_AK + (size_t)ip * A_BYTES);
                 const uint32_t d = tmem + (uint32_t)(ip * NCOLS);
 #pragma unroll
-                for (int k = 0; k < KC / 8; ++k)
+                for (int k = 3 * h; k < 3 * h + 3; ++k)
                     mma_tf32(d, make_desc(ak0 + k * 256, 128, SBO_A), make_desc(bk0 + k * 256, 128, SBO_B), IDESC_K,
                              (c > 0 || k > 0) ? 1u : 0u);
             }
-            mma_commit(&bar_k);
-            k_pending = 1;
-            k_par = par;
+            mma_commit(&bar_kh[h]);
+            last_bar = &bar_kh[h];
+            last_par = par;
+            return true;
+        };
+        for (int c = 0; c < NBK && c < nch; ++c) copy_bk(c);
+        bool ok = issue_y(0, 0) && issue_y(0, 1);
+        for (int c = 0; ok && c < nch; ++c) {
+            const int kst = c % NBK;
+            if (!mbar_wait(&bar_fbk[kst], (uint32_t)(c / NBK) & 1u, &abort_s)) break;
+            bk_pend[kst] = 0;
+            if (c >= 1) {        // B stage (c + 2) % 3 = (c - 1) % 3 is free once the K-MMAs of chunk c - 1 are done
+                if (!mbar_wait(&bar_kh[1], (uint32_t)(c - 1) & 1u, &abort_s)) break;
+                if (c + 2 < nch) copy_bk(c + 2);
+            }
+            ok = issue_k(c, 0) && (c + 1 >= nch || issue_y(c + 1, 0)) && issue_k(c, 1) &&
+                 (c + 1 >= nch || issue_y(c + 1, 1));
         }
-        // drain: the last commit covers every MMA issued before it; outstanding copies must land
-        if (k_pending && !mbar_wait(&bar_k, k_par, &abort_s)) {
+        // drain: outstanding MMAs and copies must complete before the tensor memory is freed
+        if (last_bar && !mbar_wait(last_bar, last_par, &abort_s)) {
             const unsigned long long t0 = now_ns();
-            while (!mbar_test(&bar_k, k_par) && now_ns() - t0 < WAIT_NS) {}
+            while (!mbar_test(last_bar, last_par) && now_ns() - t0 < WAIT_NS) {}
         }
         for (int st = 0; st < NBK; ++st)
             if (bk_pend[st]) {
