@@ -55,6 +55,8 @@ def parse():
                                                 "(default data/mlp_<workload>.npz)")
     ap.add_argument("--no-graphs", action="store_true", help="time the host-driven pass loop instead of graphs")
     ap.add_argument("--batch", type=int, default=None, help="override the batch size (testing)")
+    ap.add_argument("--fp64-residual", action="store_true",
+                    help="form the residual of the tensor-core paths in FP64 instead of double-float FP32 pairs")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
@@ -129,13 +131,14 @@ def load_workload(args, first=0, B=None):
 
 
 def solver_opts(args, rom):
-    # default: FP64 residual, kinematics, return map, eigen log/exp and solve; the 3D stiffness in
+    # default: FP64 return map, eigen log/exp, stresses and convergence test; the residual of the
+    # tensor-core paths in double-float FP32 pairs (--fp64-residual: FP64); the 3D stiffness in
     # TF32 on the tensor cores, the 2D stiffness in FP32 on the CUDA cores
     prec = args.precision or ("tf32" if args.workload == "c3" else "fp32")
     tol_rel = 1e-10 if prec == "fp64" else 1e-9
     max_iter = 25 if prec == "fp64" else 50
     return prec, dict(tol_rel=tol_rel, tol_abs=rom["tol_abs"], max_iter=max_iter, max_ls=6, precision=prec,
-                      start=args.start, polar_split=True, want_abar=True)
+                      start=args.start, polar_split=True, want_abar=True, fp64_residual=args.fp64_residual)
 
 
 def flush_l2(buf):
@@ -230,7 +233,7 @@ def run_ours(args, rank, world):
     launches = sum(v[1] for v in groups.values())
     res = dict(value=value, ms=ms, n_ok=n_ok, n_total=len(info), iters_mean=float(info["iters"].mean()),
                evals_mean=float(info["evals"].mean()), prof=groups, dom=dom, launches=launches, clocks=clk,
-               prec=prec, B=B, W=W, K=K, graphs=graphs, ms_profiled=ms_prof, clocks_profiled=clk_prof,
+               prec=prec, fp64_residual=bool(args.fp64_residual), B=B, W=W, K=K, graphs=graphs, ms_profiled=ms_prof, clocks_profiled=clk_prof,
                workload=args.workload, tile=tile)
     # end-to-end through the public host-buffer call (H2D of Fbar, D2H of Pbar, Abar, info each step)
     if not args.no_e2e:
@@ -345,9 +348,11 @@ def kernel_rooflines(r, peaks):
         pk = bf16 * (1.0 if prec == "bf16" else 0.5)
         add("assemble", "tensor", prof["assemble"][2], pk,
             src + " bf16_tflops" + ("" if prec == "bf16" else " x 0.5 (TF32 rate)"))
-        # double-float residual: 12 FP32 pipe operations per multiply-add
-        add("force", "alu", prof["force"][2], FP32_PEAK_TFLOPS / 12,
-            "FP32 pipe / 12: double-float multiply-add of 12 FP32 operations")
+        if r.get("fp64_residual"):
+            add("force", "alu", prof["force"][2], FP64_PEAK_TFLOPS, "FP64 pipe")
+        else:   # double-float residual: 12 FP32 pipe operations per multiply-add
+            add("force", "alu", prof["force"][2], FP32_PEAK_TFLOPS / 12,
+                "FP32 pipe / 12: double-float multiply-add of 12 FP32 operations")
     elif prec == "fp64":
         add("assemble", "alu", prof["assemble"][2], FP64_PEAK_TFLOPS, "FP64 pipe")
     else:
@@ -402,6 +407,8 @@ def main():
                 dtype={"fp64": "f64", "fp32": "f64+f32", "tf32": "f64+tf32", "bf16": "f64+bf16"}[r["prec"]],
                 data="synthetic",
                 config=dict(workload=wl, B_per_gpu=r["B"], precision=r["prec"], start=args.start,
+                            residual=("fp64" if r["prec"] == "fp64" or args.fp64_residual or
+                                      (args.workload == "c2" and r["prec"] == "fp32") else "double-float FP32 pairs"),
                             step_driver="CUDA graph, device-driven Newton loop" if r["graphs"] else "host-driven passes",
                             l2="flushed between timed steps (256 MB write)", converged=r["n_ok"],
                             assembly_tile=dict(edge=r["tile"][0], chunk=r["tile"][1]),

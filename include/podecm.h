@@ -76,17 +76,25 @@ typedef struct {
  *  max_ls: backtracking halvings of an update whose residual norm does not
  *          decrease (0 = the plain Newton of Eq. red_newton);
  *  precision: ROM_PREC_FP64 -- everything in FP64;
- *             ROM_PREC_FP32/TF32/BF16 -- residual, kinematics, return map,
- *             eigen log/exp and the n x n solve in FP64; the tangent and the
- *             stiffness contraction K in FP32 CUDA cores / TF32 / BF16 tensor
- *             cores (tcgen05, FP32 accumulation in tensor memory; n <= 64) -- an
- *             inexact-Newton Jacobian; the converged answer still satisfies the
- *             FP64 residual test.  With TF32/BF16 the K used for Abar is one extra
- *             FP32 assembly at the converged iterate;
+ *             ROM_PREC_FP32/TF32/BF16 -- return map, yield check, eigen log/exp,
+ *             stresses and the convergence test in FP64; the kinematics of 3D models
+ *             and the residual of the tensor-core paths in double-float arithmetic
+ *             (FP32 pairs, ~48 significant bits; residual error ~1e-12 of
+ *             sum |terms|, see fp64_residual); the n x n solve by an FP32 LU with
+ *             FP64 residual refinement (n >= 48, FP64 LU fallback) or an FP64 LU;
+ *             the tangent and the stiffness contraction K in FP32 CUDA cores / TF32 /
+ *             BF16 tensor cores (tcgen05, FP32 accumulation in tensor memory;
+ *             n <= 64) -- an inexact-Newton Jacobian; the converged answer still
+ *             satisfies the residual test.  With TF32/BF16 the K used for Abar is one
+ *             extra FP32-accurate assembly at the converged iterate;
  *  start: ROM_START_PLAIN a0 = a_n; ROM_START_PREV a0 = a_n + (a_n - a_{n-1});
  *         ROM_START_MLP a0 = a_n + MLP prediction (see rom_mlp_load);
  *  polar_split: 1 = solve on Ubar of Fbar = Rbar Ubar and rotate back (Sec. 4);
- *  want_abar: 1 = compute the effective stiffness. */
+ *  want_abar: 1 = compute the effective stiffness;
+ *  fp64_residual: 1 = form the residual of the mixed-precision tensor-core paths in
+ *         FP64 (one DFMA per multiply-add) instead of double-float FP32 pairs; the
+ *         FP64 and CUDA-core paths always form it in FP64.  Default 0.
+ * Zero-initialise the struct before setting fields, so that fields added later read 0. */
 typedef struct {
     double tol_rel, tol_abs;
     int32_t max_iter;
@@ -95,6 +103,7 @@ typedef struct {
     int32_t start;
     int32_t polar_split;
     int32_t want_abar;
+    int32_t fp64_residual;
 } rom_opts;
 
 /* Per-instance result of a step. */

@@ -40,7 +40,7 @@ class RomPhase(ctypes.Structure):
 class RomOpts(ctypes.Structure):
     _fields_ = [("tol_rel", ctypes.c_double), ("tol_abs", ctypes.c_double), ("max_iter", ctypes.c_int32),
                 ("max_ls", ctypes.c_int32), ("precision", ctypes.c_int32), ("start", ctypes.c_int32),
-                ("polar_split", ctypes.c_int32), ("want_abar", ctypes.c_int32)]
+                ("polar_split", ctypes.c_int32), ("want_abar", ctypes.c_int32), ("fp64_residual", ctypes.c_int32)]
 
 
 class RomNoallocModel(ctypes.Structure):
@@ -119,9 +119,9 @@ def _f64(a):
 
 
 def make_opts(tol_rel=1e-10, tol_abs=0.0, max_iter=25, max_ls=6, precision="fp64", start="plain",
-              polar_split=True, want_abar=True):
+              polar_split=True, want_abar=True, fp64_residual=False):
     return RomOpts(float(tol_rel), float(tol_abs), int(max_iter), int(max_ls), PREC[precision], START[start],
-                   int(bool(polar_split)), int(bool(want_abar)))
+                   int(bool(polar_split)), int(bool(want_abar)), int(bool(fp64_residual)))
 
 
 class Context:

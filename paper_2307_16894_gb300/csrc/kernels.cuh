@@ -75,6 +75,7 @@ struct MlpDev {
 struct StepOpts {
     double tol_rel, tol_abs;
     int max_iter, max_ls, precision, start, polar, want_abar;
+    int fp64_residual = 0;          // tensor-core paths: FP64 residual instead of double-float
     int asm_tm = 0, asm_ch = 0;   // assembly tile edge / points per chunk (0 = heuristic)
 };
 

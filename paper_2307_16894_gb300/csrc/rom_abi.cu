@@ -39,7 +39,7 @@ int launch_tc(int fmt, const Model &M, Batch Bt, const unsigned char *img, int *
 size_t tc3_image_bytes(int m);
 void tc3_build_images(int n, int m, const double *G, unsigned char *img);
 int launch_tc3(int mode, const Model &M, Batch Bt, const unsigned char *img, int *err, int sel, cudaStream_t s);
-void launch_force(const Model &M, Batch Bt, cudaStream_t s);
+void launch_force(const Model &M, Batch Bt, bool fp64, cudaStream_t s);
 void launch_list_converged(Batch Bt, cudaStream_t s);
 void launch_graph_advance(Batch Bt, const int32_t *list_next, cudaGraphConditionalHandle h, int max_pass,
                           cudaStream_t s);
@@ -611,6 +611,7 @@ static rom_status run_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts, co
     StepOpts o;
     o.tol_rel = opts->tol_rel; o.tol_abs = opts->tol_abs; o.max_iter = opts->max_iter; o.max_ls = opts->max_ls;
     o.precision = opts->precision; o.start = opts->start; o.polar = opts->polar_split; o.want_abar = opts->want_abar;
+    o.fp64_residual = opts->fp64_residual;
     o.asm_tm = ctx->asm_tm; o.asm_ch = ctx->asm_ch;
     const Model M = make_model(ctx);
     Batch bt = st->bt;
@@ -646,7 +647,7 @@ static rom_status run_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts, co
         const double na = (double)n_act;
         auto asm_launch = [&] { return launch_assembly(ctx, M, bt, o, nxt, ctx->stream); };
         auto force_launch = [&] {
-            if (tcp) launch_force(M, bt, ctx->stream);
+            if (tcp) launch_force(M, bt, o.fp64_residual != 0, ctx->stream);
             return 0;
         };
         if (timed(ctx, 1, na * fl_kin, [&] { return launch_kernel(1, M, bt, o, nxt, ctx->stream); }) ||
@@ -682,7 +683,11 @@ static rom_status run_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts, co
     return ROM_OK;
 }
 
-static bool same_opts(const rom_opts &a, const rom_opts &b) { return memcmp(&a, &b, sizeof(rom_opts)) == 0; }
+static bool same_opts(const rom_opts &a, const rom_opts &b) {   // field by field: the struct has tail padding
+    return a.tol_rel == b.tol_rel && a.tol_abs == b.tol_abs && a.max_iter == b.max_iter && a.max_ls == b.max_ls &&
+           a.precision == b.precision && a.start == b.start && a.polar_split == b.polar_split &&
+           a.want_abar == b.want_abar && a.fp64_residual == b.fp64_residual;
+}
 static bool o_needs_recapture(const rom_state *st, const rom_opts *opts) {
     return !st->g_valid || !same_opts(st->gopts, *opts) || st->g_epoch != st->ctx->graph_epoch;
 }
@@ -698,6 +703,7 @@ static rom_status capture_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts
     StepOpts o;
     o.tol_rel = opts->tol_rel; o.tol_abs = opts->tol_abs; o.max_iter = opts->max_iter; o.max_ls = opts->max_ls;
     o.precision = opts->precision; o.start = opts->start; o.polar = opts->polar_split; o.want_abar = opts->want_abar;
+    o.fp64_residual = opts->fp64_residual;
     o.asm_tm = ctx->asm_tm; o.asm_ch = ctx->asm_ch;
     const Model M = make_model(ctx);
     Batch bt = st->bt;
@@ -744,7 +750,7 @@ static rom_status capture_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts
             int32_t *nxt = st->list2;
             bad |= launch_kernel(1, M, bt, o, nxt, bs);
             bad |= launch_assembly(ctx, M, bt, o, nxt, bs);
-            if (tc_path(ctx, M, o.precision)) launch_force(M, bt, bs);
+            if (tc_path(ctx, M, o.precision)) launch_force(M, bt, o.fp64_residual != 0, bs);
             bad |= launch_kernel(3, M, bt, o, nxt, bs);
             launch_graph_advance(bt, nxt, h, max_pass, bs);
             cudaGraph_t out = nullptr;

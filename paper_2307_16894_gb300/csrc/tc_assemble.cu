@@ -465,9 +465,10 @@ static int launch_tc_t(const Model &M, Batch Bt, const unsigned char *img, int *
 }
 
 // residual r = sum_i G_i^T v_i of the listed instances (paths whose stiffness kernel does not
-// produce it): double-float when the model carries the split image of G, else FP64
-void launch_force(const Model &M, Batch Bt, cudaStream_t s) {
-    if (M.Gdf) {
+// produce it): double-float when the model carries the split image of G and fp64 is not asked
+// for, else FP64
+void launch_force(const Model &M, Batch Bt, bool fp64, cudaStream_t s) {
+    if (M.Gdf && !fp64) {
         const dim3 grid((unsigned)((Bt.B + FDF_NI - 1) / FDF_NI), (unsigned)((M.n + 63) / 64));
         k_force_df<<<grid, 256, 0, s>>>(M, Bt);
     } else {

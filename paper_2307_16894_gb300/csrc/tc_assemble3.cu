@@ -697,27 +697,36 @@ __global__ void __launch_bounds__(tc4::THREADS, 1)
                 // A_Y[c & 1][pp]: core matrices of the B tile, rows (s, j) <- B rows j, K blocks of point 2 pp + s
                 unsigned char *Ay = smem + OFF_AY + (size_t)((c & 1) * 2 + pp) * AY_BYTES;
                 const unsigned char *Bk = smem + OFF_BK + (size_t)kst * B_BYTES;
-                for (int e = ptid; e < 2 * 64 * 3; e += 128) {
-                    const int t = e % 3, r2 = e / 3, j = r2 % 64, sq = r2 / 64;
+                for (int e = ptid; e < 2 * 64 * 3; e += 128) {   // consecutive threads: consecutive rows j
+                    const int j = e & 63, t = (e >> 6) % 3, sq = (e >> 6) / 3;
                     const uint4 v = *reinterpret_cast<const uint4 *>(Bk + (size_t)(j >> 3) * SBO_B +
                                                                       (size_t)(3 * (2 * pp + sq) + t) * 128 + (size_t)(j & 7) * 16);
                     const int r = sq * 64 + j;
                     *reinterpret_cast<uint4 *>(Ay + (size_t)(r >> 3) * AY_SBO + (size_t)(3 * sq + t) * 128 + (size_t)(r & 7) * 16) = v;
                 }
+                // B_Y[pp]: row (inst, cc), K slots (s, q) <- At_{inst, 2 pp + s}[q][cc]; one thread per row
+                // reads both points of the pair with 8-byte loads (points are the innermost index of the
+                // staged tangent)
                 unsigned char *By = smem + OFF_BY + (size_t)pp * BY_BYTES;
-                for (int e = ptid; e < 2 * NY; e += 128) {
-                    const int nrow = e % NY, sq = e / NY;
+                for (int nrow = ptid; nrow < NY; nrow += 128) {
                     const int inst = nrow / D2, cc = nrow - inst * D2;
-                    const int pt = 2 * pp + sq;
-                    const bool valid = nrow < NI * D2 && bI[inst] >= 0 && c * PC + pt < m;
-                    uint32_t h[12];
+                    const bool vrow = nrow < NI * D2 && bI[inst] >= 0;
+                    const bool v0 = vrow && c * PC + 2 * pp < m, v1 = vrow && c * PC + 2 * pp + 1 < m;
+                    uint32_t h0[D2], h1[D2];
 #pragma unroll
-                    for (int q = 0; q < 12; ++q)
-                        h[q] = (valid && q < D2) ? tf32_bits(as[((size_t)inst * D4 + q * D2 + cc) * PC + pt]) : 0u;
-                    const size_t rb = (size_t)(nrow >> 3) * BY_SBO + (size_t)(nrow & 7) * 16 + (size_t)(3 * sq) * 128;
-                    *reinterpret_cast<uint4 *>(By + rb) = make_uint4(h[0], h[1], h[2], h[3]);
-                    *reinterpret_cast<uint4 *>(By + rb + 128) = make_uint4(h[4], h[5], h[6], h[7]);
-                    *reinterpret_cast<uint4 *>(By + rb + 256) = make_uint4(h[8], h[9], h[10], h[11]);
+                    for (int q = 0; q < D2; ++q) {
+                        float2 t = make_float2(0.f, 0.f);
+                        if (vrow) t = *reinterpret_cast<const float2 *>(as + ((size_t)inst * D4 + q * D2 + cc) * PC + 2 * pp);
+                        h0[q] = v0 ? tf32_bits(t.x) : 0u;
+                        h1[q] = v1 ? tf32_bits(t.y) : 0u;
+                    }
+                    const size_t rb = (size_t)(nrow >> 3) * BY_SBO + (size_t)(nrow & 7) * 16;
+                    *reinterpret_cast<uint4 *>(By + rb) = make_uint4(h0[0], h0[1], h0[2], h0[3]);
+                    *reinterpret_cast<uint4 *>(By + rb + 128) = make_uint4(h0[4], h0[5], h0[6], h0[7]);
+                    *reinterpret_cast<uint4 *>(By + rb + 256) = make_uint4(h0[8], 0u, 0u, 0u);
+                    *reinterpret_cast<uint4 *>(By + rb + 384) = make_uint4(h1[0], h1[1], h1[2], h1[3]);
+                    *reinterpret_cast<uint4 *>(By + rb + 512) = make_uint4(h1[4], h1[5], h1[6], h1[7]);
+                    *reinterpret_cast<uint4 *>(By + rb + 640) = make_uint4(h1[8], 0u, 0u, 0u);
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_arrive(&bar_by[pp]);

@@ -46,5 +46,6 @@ def test_argument_errors_without_gpu(L):
 
 def test_struct_layouts():
     assert ctypes.sizeof(binding.RomPhase) == 48
-    assert ctypes.sizeof(binding.RomOpts) == 40
+    assert ctypes.sizeof(binding.RomOpts) == 48   # 2 doubles, 7 int32, 4 bytes tail padding
+    assert binding.RomOpts.fp64_residual.offset == 40
     assert binding.INFO_DTYPE.itemsize == 32

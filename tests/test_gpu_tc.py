@@ -96,10 +96,11 @@ def test_tc3_stiffness(B):
         assert fin and e <= tol, (prec, e)
 
 
-def residual_check(name, B, prec):
+def residual_check(name, B, prec, fp64_residual=False):
     rom, mu, coef, paths = workload.batch(name, B=B)
     g = GpuRun(rom, coef)
-    g.step(paths[:, 3], tol_rel=1e-9, tol_abs=rom["tol_abs"], max_iter=0, precision=prec)
+    g.step(paths[:, 3], tol_rel=1e-9, tol_abs=rom["tol_abs"], max_iter=0, precision=prec,
+           fp64_residual=fp64_residual)
     r, v = g.st.residual()
     g.close()
     G = rom["G"]
@@ -115,7 +116,29 @@ def test_residual_double_float(name, B):
     pairs, below 1e-11 with the worst-case growth of the FP32 compensation over 5400 terms)."""
     if name == "c3" and not os.path.exists(os.path.join(workload.DATA, "rom_c3.npz")):
         pytest.skip("3D model file not generated")
-    for prec, tol in (("tf32", 1e-11), ("fp64", 1e-13)):
-        err = residual_check(name, B, prec)
-        print("%s B=%d %s residual max error / sum|terms|: %.3e" % (name, B, prec, err.max()))
-        assert np.isfinite(err).all() and err.max() <= tol, (prec, err.max())
+    for prec, f64, tol in (("tf32", False, 1e-11), ("tf32", True, 1e-13), ("fp64", False, 1e-13)):
+        err = residual_check(name, B, prec, f64)
+        print("%s B=%d %s%s residual max error / sum|terms|: %.3e" % (name, B, prec, " fp64_residual" if f64 else "",
+                                                                      err.max()))
+        assert np.isfinite(err).all() and err.max() <= tol, (prec, f64, err.max())
+
+
+def test_fp64_residual_option_converged_answer():
+    """The FP64 residual option on the 3D TF32 path converges to the same answers as the default
+    double-float residual (both within the mixed-path tolerance of the FP64 oracle)."""
+    if not os.path.exists(os.path.join(workload.DATA, "rom_c3.npz")):
+        pytest.skip("3D model file not generated")
+    rom, mu, coef, paths = workload.batch("c3", B=9)
+    paths = paths[:, :6]   # the first steps of the 50-step paths
+    runs = [GpuRun(rom, coef), GpuRun(rom, coef)]
+    o = OracleRun(rom, coef)
+    for k in range(paths.shape[1]):
+        out = [g.step(paths[:, k], tol_rel=1e-9, tol_abs=rom["tol_abs"], max_iter=50, precision="tf32",
+                      start="prev", fp64_residual=f64) for g, f64 in zip(runs, (False, True))]
+        ref = o.step(paths[:, k], tol_rel=1e-10, tol_abs=rom["tol_abs"], start="prev")
+        for P, A, info in out:
+            assert (info["status"] == 0).all()
+            assert rel(P, ref["Pbar"]) <= 1e-7
+        assert rel(out[0][0], out[1][0]) <= 1e-8
+    for g in runs:
+        g.close()
