@@ -349,14 +349,15 @@ __global__ void __launch_bounds__(256) k_assemble(Model M, Batch Bt, int CH, int
     for (int c0 = 0; c0 < m; c0 += CH) {
         const int ch = min(CH, m - c0);
         __syncthreads();
-        // load G chunk (rows = (point, component)), zero-padded to np columns
+        // load G chunk (rows = (point, component)), zero-padded to np columns; the FP32 copy comes
+        // from the FP32 image of G (the same rounding), not from conversions on the FP64 pipe
         for (int e = tid; e < CH * D2 * np; e += blockDim.x) {
             const int row = e / np, col = e - row * np;
             const int ii = row / D2;
-            double g = 0.0;
-            if (ii < ch && col < n) g = M.G_pt[((size_t)(c0 + ii) * D2 + (row - ii * D2)) * n + col];
-            Gs[e] = g;
-            if (sizeof(TK) != sizeof(double)) Gk[e] = TK(g);
+            const bool in = ii < ch && col < n;
+            const size_t gi = ((size_t)(c0 + ii) * D2 + (row - ii * D2)) * n + col;
+            Gs[e] = in ? M.G_pt[gi] : 0.0;
+            if (sizeof(TK) != sizeof(double)) Gk[e] = in ? TK(M.G32_pt[gi]) : TK(0);
         }
         for (int e = tid; e < CH * D4; e += blockDim.x) {
             const int ce = e / CH, ii = e - ce * CH;
@@ -618,7 +619,7 @@ __device__ bool newton_direction(const Batch &Bt, int64_t b, int n, int precisio
 
 constexpr int ESC_ITERS = 4;
 
-// one CTA of SOLVE_THREADS per active instance: convergence test, line search, start selection
+// one CTA of SOLVE_THREADS (32 for n <= 32) per active instance: convergence test, line search, start selection
 // and the solve of K da = -r (newton_direction); every thread runs the same per-instance state
 // machine on the same values, so all branches are uniform over the block
 constexpr int SOLVE_THREADS = 128;
@@ -1261,7 +1262,9 @@ static int launch_kernels_t(int which, const Model &M, Batch Bt, const StepOpts 
     if (which == 3) {
         const size_t sms = (size_t)M.n * (M.n + 1) * 8 + (size_t)M.n * 8 + (size_t)M.n * 4 + 16;
         cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sms);
-        k_solve<<<(int)Bt.B, SOLVE_THREADS, sms, s>>>(M, Bt, o, list_next);
+        // n <= 32: one warp per instance (its block barriers cost next to nothing and twice as many
+        // instances are resident per SM); the arithmetic and its order do not depend on the width
+        k_solve<<<(int)Bt.B, M.n <= 32 ? 32 : SOLVE_THREADS, sms, s>>>(M, Bt, o, list_next);
         return 0;
     }
     if (which == 5) {
