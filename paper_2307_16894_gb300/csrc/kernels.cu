@@ -564,7 +564,7 @@ __device__ double block_max(double v, double *red) {
 }
 
 // Newton direction x = -K^-1 r into shared x[0..n).  FP64 path: LU of K in FP64 by the block.
-// Mixed paths: LU of K rounded to FP32, then iterative refinement with FP64 residuals
+// Mixed paths (n >= 16): LU of K rounded to FP32, then iterative refinement with FP64 residuals
 // -r - K x (at most 3 corrections, until a correction is below 1e-15 max|x|); a correction that
 // does not shrink below half of the previous one sends the solve to the FP64 LU.  The result
 // solves the same K to FP64 accuracy either way.  A: n*n doubles of shared scratch.
@@ -574,7 +574,7 @@ __device__ bool newton_direction(const Batch &Bt, int64_t b, int n, int precisio
     const double *Kb = Bt.K + (size_t)b * n * n;
     const double *r = Bt.r + b * n;
     const int lda = n + 1;   // padded rows: column accesses of the factors hit distinct banks
-    if (precision >= 1 && n >= 48) {
+    if (precision >= 1 && n >= 16) {   // mixed paths (below n = 16 the FP64 LU is as fast)
         float *A32 = reinterpret_cast<float *>(A);
         float *y = A32 + (size_t)n * lda;                                 // n floats
         int *piv = reinterpret_cast<int *>(y + n);                        // n ints  (n lda + 2n floats <= 2 n lda)
@@ -587,14 +587,15 @@ __device__ bool newton_direction(const Batch &Bt, int64_t b, int n, int precisio
             for (int j = tid; j < n; j += nt) x[j] = (double)y[j];
             __syncthreads();
             double prev = INFINITY;
-            const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
             for (int it = 0; it < 3; ++it) {
-                // FP64 residual of the current solution, one warp per row
-                for (int i = wid; i < n; i += nw) {
+                // FP64 residual of the current solution, one thread per row (serial sum over the
+                // row): every FP64 warp instruction has all its lanes busy, which matters on a part
+                // whose FP64 pipe takes 16 cycles per warp instruction whatever the active lanes
+                for (int i = tid; i < n; i += nt) {
+                    const double *Ki = Kb + (size_t)i * n;
                     double s = 0.0;
-                    for (int j = lane; j < n; j += 32) s += Kb[(size_t)i * n + j] * x[j];
-                    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-                    if (lane == 0) y[i] = (float)(-r[i] - s);
+                    for (int j = 0; j < n; ++j) s += Ki[j] * x[j];
+                    y[i] = (float)(-r[i] - s);
                 }
                 __syncthreads();
                 block_lu_apply<float>(A32, n, lda, piv, y);
