@@ -38,6 +38,13 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12    # 152 SMs x 128 FFMA/clk x 2
 # cubature point and evaluation of the constitutive kernel (kinematics, return map, P, pull-backs;
 # the tangent runs in FP32 on the mixed paths, in FP64 on the FP64 path)
 CONST_FP64_FLOP_PER_POINT = {(3, "mixed"): 1590.0, (3, "fp64"): 5917.0, (2, "mixed"): 881.0, (2, "fp64"): 2288.0}
+# DRAM bytes (read + write) per evaluated cubature point of the constitutive kernel, from one ncu
+# capture of its first (all instances active) launch: --metrics dram__bytes_read.sum,
+# dram__bytes_write.sum -k regex:k_constitutive -s 0 -c 1 on `bench.py --workload c3 --batch 2048
+# --steps 2 --warmup 3 --no-cpu --no-e2e --no-graphs` (1.083 GB / 2048 x 600 points) and on
+# `bench.py --steps 2 --warmup 3 --no-cpu --no-e2e --no-graphs` (83.1 MB / 4096 x 160 points; the
+# 2D outputs stay in L2 during the kernel, so DRAM sees less than the algorithmic bytes)
+CONST_DRAM_BYTES_PER_POINT = {(3, "mixed"): 881.3, (2, "mixed"): 126.8}
 
 
 def parse():
@@ -329,20 +336,22 @@ def kernel_rooflines(r, peaks):
     src = "MEASURED_PEAKS.json" if "bf16_tflops" in peaks else "fallback 1.9 PFLOP/s"
     out = {}
 
-    def add(name, bound, flops, peak, peak_source):
+    def add(name, bound, flops, peak, peak_source, traffic=None):
         ms = prof[name][0]
         if ms <= 0 or flops <= 0:
             return
         a = flops / (ms / 1e3) / 1e12
         out[name] = dict(kernel=name, bound=bound, achieved=a, peak=peak, unit="TFLOP/s", frac=a / peak,
-                         traffic=None, share=ms / tot, peak_source=peak_source)
+                         traffic=traffic, share=ms / tot, peak_source=peak_source)
 
     kin = 2.0 * m * d * d * n
     points = prof["constitutive"][2] / kin * m
     key = (d, "fp64" if prec == "fp64" else "mixed")
     if key in CONST_FP64_FLOP_PER_POINT:
+        nl = max(prof["constitutive"][1], 1)
+        traffic = (points / nl * CONST_DRAM_BYTES_PER_POINT[key]) if key in CONST_DRAM_BYTES_PER_POINT else None
         add("constitutive", "alu", points * CONST_FP64_FLOP_PER_POINT[key], FP64_PEAK_TFLOPS,
-            "FP64 pipe: 152 SM x 2 DFMA/clk x 2 FLOP x 2.07 GHz")
+            "FP64 pipe: 152 SM x 2 DFMA/clk x 2 FLOP x 2.07 GHz", traffic)
     tc = (d == 3 and n <= 64 and prec != "fp64") or prec in ("tf32", "bf16")
     if tc:
         pk = bf16 * (1.0 if prec == "bf16" else 0.5)
