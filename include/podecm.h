@@ -163,7 +163,8 @@ rom_status rom_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts, const dou
  * Tensor-core stiffness (3D models, and 2D in ROM_PREC_TF32/BF16): every pipeline wait inside
  * the kernel is bounded; if one gives up, rom_step (and rom_step_device without graphs)
  * returns ROM_E_CUDA after the Newton passes, and in graph mode the step's Abar entries are
- * NaN (Pbar, info and the history come from exact FP64 residuals and stay valid). */
+ * NaN (Pbar, info and the history come from the residual test, which no tensor-core result
+ * enters, and stay valid). */
 rom_status rom_step_device(rom_ctx *ctx, rom_state *st, const rom_opts *opts, const double *Fbar_d,
                            double *Pbar_d, double *Abar_d, rom_step_info *info_d);
 
@@ -179,7 +180,8 @@ const char *rom_last_error(const rom_ctx *ctx);
  * 0 start, 1 constitutive (kinematics, return map, tangent), 2 assembly
  * (stiffness; on the CUDA-core path also the force), 3 solve (convergence test, line
  * search, LU), 4 finalize (Pbar, Abar, commit), 5 bookkeeping, 6 learned start
- * (features, MLP inference), 7 force (FP64 residual, on the tensor-core paths): the
+ * (features, MLP inference), 7 force (the residual on the tensor-core paths: double-float,
+ * or FP64 with fp64_residual): the
  * summed device time in ms, the number of kernel launches and the algorithmic FLOPs
  * (per active instance and launch: group 1 kinematics 2 m d^2 n; group 2 on the
  * tensor cores 2 m d^4 n + 2 m d^2 n^2 (Y = At G and the full K), on the CUDA cores

@@ -575,7 +575,7 @@ static void prof_collect(rom_ctx *ctx) {
     ctx->recs.clear();
 }
 
-// the stiffness K runs on the tensor cores (and the FP64 residual in its own kernel, force_kernel)
+// the stiffness K runs on the tensor cores (and the residual in its own kernel, launch_force)
 // for 3D models with n <= 64 at every precision but FP64, and for 2D models in BF16/TF32
 static bool tc_path(const rom_ctx *ctx, const Model &M, int precision) {
     return (M.d == 3 && ctx->tc3_img && precision >= 1) || precision >= 2;

@@ -130,7 +130,7 @@ extern "C" rom_status rom_step_noalloc(const rom_noalloc_model *model, int64_t B
     M.G_pt = model->G; M.G_T = reinterpret_cast<double *>(S + o_GT); M.G32_pt = reinterpret_cast<float *>(S + o_G32);
     M.w = model->w; M.phase = model->phase; M.Gmu_T = reinterpret_cast<double *>(S + o_GmuT); M.omega = model->omega_vol;
     M.G32h_T = nullptr; M.G32l_T = nullptr;   // FP64 kinematics
-    M.Gdf = nullptr;                           // FP64 residual
+    M.Gdf = nullptr;                           // residual in FP64 (k_force)
     Batch bt{};
     bt.B = B; bt.mu = mu_d; bt.q_n = a_d; bt.dq_prev = da_prev_d; bt.cp = Cpinv_d; bt.xi = xi_d;
     bt.q_trial = reinterpret_cast<double *>(S + o_qt); bt.q_acc = reinterpret_cast<double *>(S + o_qa);
