@@ -60,7 +60,7 @@ def lib():
         _lib.orc_material_batch.argtypes = [i, i, p, p, p, p, p, p, p, p, p, p, p]
         _lib.orc_rom_step.restype = i
         _lib.orc_rom_batch.argtypes = [i, i, i, i, i, i, p, p, p, p, p, p, d, p, p, p, p, d, d, i, i,
-                                       p, p, p, p, p, p, p, p, p]
+                                       p, p, p, p, p, p, p, p, p, i, p, p, p]
         _lib.orc_fe_elements.argtypes = [i, i, i, i, p, p, p, p, p, p, p, p, p, p, p, p,
                                          p, p, p, p, p, p, p, p, i, i]
         _lib.orc_polar.argtypes = [i, p, p, p]
@@ -127,13 +127,27 @@ def polar(F):
     return R, U
 
 
+def geometry_derivatives(rom, Finv, J):
+    """dF_mu^-1/dmu_k = -F_mu^-1 Gmu_k F_mu^-1 and d|det F_mu|/dmu_k = |det F_mu| tr(F_mu^-1 Gmu_k)
+    at every point, for the affine map F_mu = I + sum_k mu_k Gmu_k (the derivative of the inverse
+    and of the determinant that Eq. eff_sensitivities_full needs).  Finv [B, m, d, d], J [B, m]
+    -> dFinv [B, m, n_par, d, d], dJ [B, m, n_par]."""
+    d, m = rom["d"], rom["m"]
+    Gmu = rom["Gmu"].reshape(m, d, d, -1)                         # [m, d, d, n_par]
+    FG = np.einsum("bmac,mcdk->bmkad", Finv, Gmu)                 # F_mu^-1 Gmu_k
+    dFinv = -np.einsum("bmkac,bmcd->bmkad", FG, Finv)
+    dJ = J[:, :, None] * np.einsum("bmkaa->bmk", FG)
+    return np.ascontiguousarray(dFinv), np.ascontiguousarray(dJ)
+
+
 def rom_batch(rom, Finv, J, Fbar, q, Fp, xi, tol_rel, tol_abs, max_iter, max_ls=6, polar_split=True,
-              nthreads=None, want_A=True):
+              nthreads=None, want_A=True, dFinv=None, dJ=None):
     """One load step of the online reduced solve for B instances (in place on q, Fp, xi).
 
     rom: dict with d, n, m, G [m, d*d, n], w [m], phase [m], phases (list), omega.
     Finv [B, m, d, d], J [B, m], Fbar [B, d, d], q [B, n] (start iterate on entry,
-    solution on exit), Fp [B, m, 3, 3], xi [B, m].  Returns a dict of outputs."""
+    solution on exit), Fp [B, m, 3, 3], xi [B, m].  With dFinv, dJ (geometry_derivatives)
+    the outputs include the shape sensitivities dPdmu [B, d, d, n_par].  Returns a dict."""
     d, n, m = rom["d"], rom["n"], rom["m"]
     B = Fbar.shape[0]
     for name, arr in (("q", q), ("Fp", Fp), ("xi", xi)):
@@ -149,13 +163,20 @@ def rom_batch(rom, Finv, J, Fbar, q, Fp, xi, tol_rel, tol_abs, max_iter, max_ls=
         "P33bar": np.zeros(B), "iters": np.zeros(B, np.int32), "evals": np.zeros(B, np.int32),
         "n_yield": np.zeros(B, np.int32),
         "status": np.zeros(B, np.int32), "res0": np.zeros(B), "res": np.zeros(B)}
+    npar = 0
+    if dFinv is not None:
+        npar = dFinv.shape[2]
+        dFinv, dJ = _f64(dFinv), _f64(dJ)
+        out["dPdmu"] = np.zeros((B, d, d, npar))
     parr = phases_array(rom["phases"])
     nthreads = nthreads or min(os.cpu_count() or 1, max(B, 1))
     lib().orc_rom_batch(B, nthreads, 1 if polar_split else 0, d, n, m, _ptr(G), _ptr(w), _ptr(ph),
                         ctypes.cast(parr, ctypes.c_void_p), _ptr(Finv), _ptr(J), float(rom.get("omega", 1.0)),
                         _ptr(Fbar), _ptr(q), _ptr(Fp), _ptr(xi), float(tol_rel), float(tol_abs), int(max_iter),
                         int(max_ls), _ptr(out["Pbar"]), _ptr(out["Abar"]), _ptr(out["P33bar"]), _ptr(out["iters"]),
-                        _ptr(out["evals"]), _ptr(out["n_yield"]), _ptr(out["status"]), _ptr(out["res0"]), _ptr(out["res"]))
+                        _ptr(out["evals"]), _ptr(out["n_yield"]), _ptr(out["status"]), _ptr(out["res0"]), _ptr(out["res"]),
+                        npar, _ptr(dFinv) if npar else None, _ptr(dJ) if npar else None,
+                        _ptr(out["dPdmu"]) if npar else None)
     return out
 
 

@@ -13,6 +13,12 @@
  *                                                                           Eqs. eff_stiffness_1, eff_stress_f11
  *    F = Fbar + (sum_n a_n dphi_n/dX^p) F_mu^-1 (Eq. forcevector_ecm).
  *    A linear solve is a plain LU with partial pivoting.
+ *    Shape sensitivities (Eq. eff_sensitivities_full), optional: with
+ *      dF_k = (sum_n dq_k,n dphi_n/dX^p) F_mu^-1 + H dF_mu^-1/dmu_k,  H = sum_n a_n dphi_n/dX^p,
+ *      K dq_k = -df/dmu_k at fixed a (the reduced counterpart of the fluctuation
+ *      sensitivity, same factor K* = K), the derivative of f_j taken term by term,
+ *      dPbar_ij/dmu_k = |Omega^p|^-1 sum_q w_q [ A_ijmn dF_k,mn |det F_mu| + P_ij d|det F_mu|/dmu_k ],
+ *    given dF_mu^-1/dmu_k and d|det F_mu|/dmu_k at every point (inputs).
  * 2. The macro rotation split Fbar = Rbar Ubar (Sec. 4): the reduced problem
  *    is solved on Ubar and Pbar = Rbar Pbar(Ubar); Abar follows by the
  *    chain rule through the polar decomposition.
@@ -130,7 +136,8 @@ int orc_rom_step(int d, int n, int m, const double *G, const double *w, const in
                  const double *Fbar, double *q, double *Fp, double *xi,
                  double tol_rel, double tol_abs, int max_iter, int max_ls,
                  double *Pbar, double *Abar, double *P33bar,
-                 int *iters_out, int *evals_out, int *n_yield_out, double *res0_out, double *res_out)
+                 int *iters_out, int *evals_out, int *n_yield_out, double *res0_out, double *res_out,
+                 int npar, const double *dFinv, const double *dJ, double *dPdmu)
 {
     const int d2 = d * d, d4 = d2 * d2;
     rom_ws s = { d, n, m, G, w, Finv, J, Fbar, Fp, xi, phase, phases };
@@ -186,6 +193,76 @@ int orc_rom_step(int d, int n, int m, const double *G, const double *w, const in
     for (int i = 0; i < m; ++i) ny += s.pl[i];
     if (n_yield_out) *n_yield_out = ny;
 
+    if (status == 0 && dPdmu && npar > 0) {
+        /* shape sensitivities, Eq. eff_sensitivities_full (dFinv [m][npar][d2], dJ [m][npar]) */
+        double *Kf = malloc(sizeof(double) * n * n), *rhs = malloc(sizeof(double) * n);
+        memcpy(Kf, K, sizeof(double) * n * n);
+        int *pv = malloc(sizeof(int) * n);
+        const int fac = lu_factor(n, Kf, pv);
+        for (int k = 0; k < npar; ++k) {
+            /* rhs = -df/dmu_k at fixed a: the three terms of the derivative of
+             * w (dphi_j/dX^p F_mu^-1) : P(F) |det F_mu| with F = Fbar + H F_mu^-1 */
+            for (int j = 0; j < n; ++j) rhs[j] = 0.0;
+            for (int i = 0; i < m; ++i) {
+                const double *Fi = dFinv + ((size_t)i * npar + k) * d2;
+                const double *P = s.Pq + (size_t)i * d2, *A = s.Aq + (size_t)i * d4;
+                double H[9] = {0}, dF[9], AdF[9];
+                for (int c = 0; c < d2; ++c)
+                    for (int j = 0; j < n; ++j) H[c] += G[((size_t)i * d2 + c) * n + j] * q[j];
+                for (int a = 0; a < d; ++a)
+                    for (int b = 0; b < d; ++b) {
+                        double t = 0.0;
+                        for (int rr = 0; rr < d; ++rr) t += H[a * d + rr] * Fi[rr * d + b];
+                        dF[a * d + b] = t;
+                    }
+                for (int ab = 0; ab < d2; ++ab) {
+                    double t = 0.0;
+                    for (int c = 0; c < d2; ++c) t += A[ab * d2 + c] * dF[c];
+                    AdF[ab] = t;
+                }
+                const double dJk = dJ[(size_t)i * npar + k];
+                for (int j = 0; j < n; ++j) {
+                    const double *g = s.gF + ((size_t)i * n + j) * d2;
+                    double t1 = 0.0, t2 = 0.0, t3 = 0.0;
+                    for (int a = 0; a < d; ++a)
+                        for (int b = 0; b < d; ++b) {
+                            double gd = 0.0;   /* (dphi_j/dX^p dF_mu^-1/dmu_k)_ab */
+                            for (int rr = 0; rr < d; ++rr) gd += G[((size_t)i * d2 + a * d + rr) * n + j] * Fi[rr * d + b];
+                            t1 += gd * P[a * d + b];
+                        }
+                    for (int c = 0; c < d2; ++c) { t2 += g[c] * AdF[c]; t3 += g[c] * P[c]; }
+                    rhs[j] -= w[i] * (J[i] * (t1 + t2) + dJk * t3);
+                }
+            }
+            if (fac == 0) lu_solve(n, Kf, pv, rhs);
+            for (int ij = 0; ij < d2; ++ij) {
+                double sum = 0.0;
+                for (int i = 0; i < m; ++i) {
+                    const double *Fi = dFinv + ((size_t)i * npar + k) * d2;
+                    const double *A = s.Aq + (size_t)i * d4;
+                    double H[9] = {0}, Hq[9] = {0}, dF[9];
+                    for (int c = 0; c < d2; ++c)
+                        for (int j = 0; j < n; ++j) {
+                            const double gg = G[((size_t)i * d2 + c) * n + j];
+                            H[c] += gg * q[j];
+                            Hq[c] += gg * rhs[j];
+                        }
+                    for (int a = 0; a < d; ++a)
+                        for (int b = 0; b < d; ++b) {
+                            double t = 0.0;
+                            for (int rr = 0; rr < d; ++rr)
+                                t += Hq[a * d + rr] * Finv[(size_t)i * d2 + rr * d + b] + H[a * d + rr] * Fi[rr * d + b];
+                            dF[a * d + b] = t;
+                        }
+                    double t = 0.0;
+                    for (int c = 0; c < d2; ++c) t += A[ij * d2 + c] * dF[c];
+                    sum += w[i] * (J[i] * t + s.Pq[(size_t)i * d2 + ij] * dJ[(size_t)i * npar + k]);
+                }
+                dPdmu[ij * npar + k] = fac == 0 ? sum / omega : NAN;
+            }
+        }
+        free(Kf); free(rhs); free(pv);
+    }
     if (status == 0) {
         /* effective stress, Eq. eff_stress_1 */
         for (int c = 0; c < d2; ++c) {
@@ -301,18 +378,27 @@ int orc_rom_step_polar(int d, int n, int m, const double *G, const double *w, co
                        const double *Fbar, double *q, double *Fp, double *xi,
                        double tol_rel, double tol_abs, int max_iter, int max_ls,
                        double *Pbar, double *Abar, double *P33bar,
-                       int *iters, int *evals, int *n_yield, double *res0, double *res)
+                       int *iters, int *evals, int *n_yield, double *res0, double *res,
+                       int npar, const double *dFinv, const double *dJ, double *dPdmu)
 {
     const int d2 = d * d;
-    double R[9], U[9], PU[9], AU[81];
+    double R[9], U[9], PU[9], AU[81], dPU[27];
     orc_polar(d, Fbar, R, U);
     int st = orc_rom_step(d, n, m, G, w, phase, phases, Finv, J, omega, U, q, Fp, xi,
-                          tol_rel, tol_abs, max_iter, max_ls, PU, AU, P33bar, iters, evals, n_yield, res0, res);
+                          tol_rel, tol_abs, max_iter, max_ls, PU, AU, P33bar, iters, evals, n_yield, res0, res,
+                          npar, dFinv, dJ, dPdmu ? dPU : NULL);
     if (st != 0) return st;
     for (int i = 0; i < d; ++i) for (int j = 0; j < d; ++j) {
         double s = 0; for (int k = 0; k < d; ++k) s += R[i * d + k] * PU[k * d + j];
         Pbar[i * d + j] = s;
     }
+    /* the rotation does not depend on the geometry: dPbar/dmu = Rbar dPbar_U/dmu */
+    if (dPdmu)
+        for (int kp = 0; kp < npar; ++kp)
+            for (int i = 0; i < d; ++i) for (int j = 0; j < d; ++j) {
+                double s = 0; for (int k = 0; k < d; ++k) s += R[i * d + k] * dPU[(k * d + j) * npar + kp];
+                dPdmu[(i * d + j) * npar + kp] = s;
+            }
     if (!Abar) return st;
     double trU = 0; for (int i = 0; i < d; ++i) trU += U[i * d + i];
     for (int k = 0; k < d; ++k)
@@ -360,6 +446,7 @@ typedef struct {
     const double *Fbar; double *q, *Fp, *xi;
     double tol_rel, tol_abs; int max_iter, max_ls;
     double *Pbar, *Abar, *P33bar; int *iters, *evals, *n_yield, *status; double *res0, *res;
+    int npar; const double *dFinv, *dJ; double *dPdmu;
     int B, nthreads, tid;
 } rom_batch_args;
 
@@ -371,14 +458,18 @@ static void *rom_batch_worker(void *p) {
         const double *J = a->J + (size_t)b * a->m;
         int (*fn)(int, int, int, const double *, const double *, const int *, const orc_phase *,
                   const double *, const double *, double, const double *, double *, double *, double *,
-                  double, double, int, int, double *, double *, double *, int *, int *, int *, double *, double *)
+                  double, double, int, int, double *, double *, double *, int *, int *, int *, double *, double *,
+                  int, const double *, const double *, double *)
             = a->polar ? orc_rom_step_polar : orc_rom_step;
+        const int np = a->dPdmu ? a->npar : 0;
         a->status[b] = fn(a->d, a->n, a->m, a->G, a->w, a->phase, a->phases, Finv, J, a->omega,
                           a->Fbar + (size_t)b * d2, a->q + (size_t)b * a->n, a->Fp + (size_t)b * a->m * 9,
                           a->xi + (size_t)b * a->m, a->tol_rel, a->tol_abs, a->max_iter, a->max_ls,
                           a->Pbar + (size_t)b * d2, a->Abar ? a->Abar + (size_t)b * d2 * d2 : NULL,
                           a->P33bar ? a->P33bar + b : NULL,
-                          a->iters + b, a->evals + b, a->n_yield + b, a->res0 + b, a->res + b);
+                          a->iters + b, a->evals + b, a->n_yield + b, a->res0 + b, a->res + b,
+                          np, np ? a->dFinv + (size_t)b * a->m * np * d2 : NULL, np ? a->dJ + (size_t)b * a->m * np : NULL,
+                          np ? a->dPdmu + (size_t)b * d2 * np : NULL);
     }
     return NULL;
 }
@@ -389,7 +480,7 @@ void orc_rom_batch(int B, int nthreads, int polar, int d, int n, int m, const do
                    const double *Fbar, double *q, double *Fp, double *xi,
                    double tol_rel, double tol_abs, int max_iter, int max_ls,
                    double *Pbar, double *Abar, double *P33bar, int *iters, int *evals, int *n_yield, int *status,
-                   double *res0, double *res)
+                   double *res0, double *res, int npar, const double *dFinv, const double *dJ, double *dPdmu)
 {
     if (nthreads < 1) nthreads = 1;
     pthread_t *th = malloc(sizeof(pthread_t) * nthreads);
@@ -397,7 +488,7 @@ void orc_rom_batch(int B, int nthreads, int polar, int d, int n, int m, const do
     for (int t = 0; t < nthreads; ++t) {
         rom_batch_args a = { d, n, m, polar, G, w, phase, phases, Finv, J, omega, Fbar, q, Fp, xi,
                              tol_rel, tol_abs, max_iter, max_ls, Pbar, Abar, P33bar, iters, evals, n_yield, status, res0, res,
-                             B, nthreads, t };
+                             npar, dFinv, dJ, dPdmu, B, nthreads, t };
         args[t] = a;
         pthread_create(&th[t], NULL, rom_batch_worker, &args[t]);
     }
