@@ -168,6 +168,21 @@ rom_status rom_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts, const dou
 rom_status rom_step_device(rom_ctx *ctx, rom_state *st, const rom_opts *opts, const double *Fbar_d,
                            double *Pbar_d, double *Abar_d, rom_step_info *info_d);
 
+/* Shape sensitivities of the effective stress with respect to the geometry parameters
+ * (Sec. 2.3, Eq. eff_sensitivities_full) at the converged state of the last rom_step /
+ * rom_step_device of `st`: dPbar_ij/dmu_k with mu the coefficients of the affine map
+ * F_mu = I + sum_k mu_k Gmu_k given to rom_set_geometry.  The fluctuation sensitivity is the
+ * reduced one, K dq_k = -df/dmu_k at fixed a, solved with the factor of K at the solution
+ * (K* = K); with the polar split dPbar/dmu = Rbar dPbar(Ubar)/dmu.  Output layout
+ * [B][d*d][n_par], entry (b, i*d + j, k); NaN for the instances whose last step did not
+ * converge.  Arithmetic: FP64 after a ROM_PREC_FP64 step, FP32 after a mixed-precision step
+ * (whose tangent is FP32; the K used is the one of the step: the FP32-accurate re-assembly when
+ * the step computed Abar).  At most 3 geometry parameters (ROM_E_ARG otherwise); ROM_E_STATE
+ * before the first step.  rom_sensitivity_device: device buffer, asynchronous on the context
+ * stream; rom_sensitivity: host buffer, blocking. */
+rom_status rom_sensitivity_device(rom_ctx *ctx, rom_state *st, double *dPdmu_d);
+rom_status rom_sensitivity(rom_ctx *ctx, rom_state *st, double *dPdmu);
+
 /* Wait for the context stream. */
 rom_status rom_sync(rom_ctx *ctx);
 
@@ -181,7 +196,7 @@ const char *rom_last_error(const rom_ctx *ctx);
  * (stiffness; on the CUDA-core path also the force), 3 solve (convergence test, line
  * search, LU), 4 finalize (Pbar, Abar, commit), 5 bookkeeping, 6 learned start
  * (features, MLP inference), 7 force (the residual on the tensor-core paths: double-float,
- * or FP64 with fp64_residual): the
+ * or FP64 with fp64_residual), 8 sensitivity (rom_sensitivity): the
  * summed device time in ms, the number of kernel launches and the algorithmic FLOPs
  * (per active instance and launch: group 1 kinematics 2 m d^2 n; group 2 on the
  * tensor cores 2 m d^4 n + 2 m d^2 n^2 (Y = At G and the full K), on the CUDA cores

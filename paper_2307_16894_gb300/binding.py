@@ -26,10 +26,11 @@ EXPORTED = ["rom_create", "rom_destroy", "rom_load_basis", "rom_load_cubature", 
             "rom_step_device", "rom_sync", "rom_last_error", "rom_profile", "rom_profile_read",
             "rom_step_noalloc", "rom_mlp_init", "rom_mlp_nparams", "rom_mlp_params", "rom_mlp_norm",
             "rom_mlp_train_step", "rom_mlp_loss_grad", "rom_mlp_predict", "rom_features", "rom_debug_stiffness",
-            "rom_debug_tangent", "rom_debug_residual", "rom_use_graphs",
+            "rom_debug_tangent", "rom_debug_residual", "rom_use_graphs", "rom_sensitivity", "rom_sensitivity_device",
             "rom_state_bytes", "rom_autotune", "rom_serve"]
 
-KERNEL_GROUPS = ["start", "constitutive", "assemble", "solve", "finalize", "bookkeeping", "learned_start", "force"]
+KERNEL_GROUPS = ["start", "constitutive", "assemble", "solve", "finalize", "bookkeeping", "learned_start", "force",
+                 "sensitivity"]
 
 
 class RomPhase(ctypes.Structure):
@@ -208,6 +209,17 @@ class Context:
         """Device-buffer step (torch CUDA tensors), asynchronous on the context stream."""
         self._check(self.L.rom_step_device(self.h, state.h, ctypes.byref(opts), _p(Fbar_d), _p(Pbar_d),
                                            _p(Abar_d), _p(info_d)), "rom_step_device")
+
+    def sensitivity(self, state):
+        """dPbar/dmu [B, d, d, n_par] of the last step (Eq. eff_sensitivities_full); NaN where the
+        step did not converge."""
+        out = np.empty((state.B, self.dim, self.dim, self.n_par))
+        self._check(self.L.rom_sensitivity(self.h, state.h, _p(out)), "rom_sensitivity")
+        return out
+
+    def sensitivity_device(self, state, out_d):
+        """Same into a device buffer of B * d * d * n_par doubles, asynchronous on the stream."""
+        self._check(self.L.rom_sensitivity_device(self.h, state.h, _p(out_d)), "rom_sensitivity_device")
 
     def sync(self):
         self._check(self.L.rom_sync(self.h), "rom_sync")

@@ -1290,6 +1290,245 @@ int launch_start(const Model &M, Batch Bt, const double *Fbar, const StepOpts &o
     return 0;
 }
 
+// ------------------------------------------------------------------ shape sensitivities
+// dPbar/dmu_k (Eq. eff_sensitivities_full) at the converged state of the last step, one CTA per
+// instance, in arithmetic T (FP64 after an FP64 step, FP32 after a mixed-precision step, whose
+// tangent is FP32).  With M_k = -H F_mu^-1 Gmu_k (so that dF/dmu_k at fixed a = M_k F_mu^-1),
+// tr_k = tr(F_mu^-1 Gmu_k) (= d ln|det F_mu| / dmu_k) and the stored pull-backs v, wP and At:
+//   dv_k = tr_k v + At vec(M_k) - V Gmu_k^T F_mu^-T            (derivative of v at fixed a)
+//   z_k = sum_i G_i^T dv_k,i ;  K dq_k = -z_k                  (reduced fluctuation sensitivity)
+//   dPbar_U/dmu_k = |Omega|^-1 sum_i [ tr_k wP + Xi^T At vec(G_i dq_k + M_k) ],  Xi^T y = (I x F_mu) y
+//   dPbar/dmu_k = Rbar dPbar_U/dmu_k.
+// Points go in chunks of SENS_CH: one thread per point forms dv (shared memory) and its share of
+// the tr_k wP and Xi^T At vec(M_k) sums; then thread (j, k) adds G^T dv over the chunk.  The
+// partial sums are added in a fixed order.
+constexpr int SENS_CH = 128;
+constexpr int SENS_THREADS = 256;
+constexpr int SENS_MAXP = 3;   // geometry parameters
+
+template <int D, typename T>
+__global__ void __launch_bounds__(SENS_THREADS) k_sensitivity(Model M, Batch Bt, double *__restrict__ out) {
+    constexpr int D2 = D * D, D4 = D2 * D2;
+    constexpr int NA = 2 * D2 * SENS_MAXP;   // per-thread partial sums: S and T+U
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int64_t b = blockIdx.x;
+    const int n = M.n, m = M.m, np = M.n_par, tid = threadIdx.x;
+    const int ld = n + 1;
+    const Ctl c = Bt.ctl[b];
+    if (c.status != 0 || np > SENS_MAXP) {
+        for (int e = tid; e < D2 * np; e += blockDim.x) out[b * D2 * np + e] = NAN;
+        return;
+    }
+    // layout: qs [n] | zs [SENS_MAXP][ld] | region (dv chunk | partial sums | LU of K)
+    T *qs = reinterpret_cast<T *>(smem);
+    T *zs = qs + n;
+    T *reg = zs + SENS_MAXP * ld;
+    T *dv = reg;                                  // [SENS_CH][SENS_MAXP][D2]
+    T *red = reg;                                 // [SENS_CH][NA] (after the chunks)
+    T *Ks = reg;                                  // [n][ld] (after the reduction)
+    __shared__ int s_piv;
+    __shared__ double mu_s[SENS_MAXP];
+    const T *At = reinterpret_cast<const T *>(Bt.At);
+    const T *Gp = (sizeof(T) == 8) ? reinterpret_cast<const T *>(M.G_pt) : reinterpret_cast<const T *>(M.G32_pt);
+    for (int j = tid; j < n; j += blockDim.x) qs[j] = (T)Bt.q_n[b * n + j];
+    for (int e = tid; e < SENS_MAXP * ld; e += blockDim.x) zs[e] = T(0);
+    if (tid < np) mu_s[tid] = Bt.mu[b * np + tid];
+    __syncthreads();
+
+    // per-point geometry (F_mu, its inverse, Gmu_k) of point i
+    auto geometry = [&](int i, T Fm[3][3], T Fmi[3][3], T Gk[SENS_MAXP][3][3]) {
+        double F[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+        for (int a = 0; a < D; ++a)
+            for (int r = 0; r < D; ++r) {
+                double s0 = (a == r) ? 1.0 : 0.0;
+                for (int k = 0; k < np; ++k) {
+                    const double g = M.Gmu_T[((size_t)(a * D + r) * np + k) * m + i];
+                    s0 += mu_s[k] * g;
+                    Gk[k][a][r] = (T)g;
+                }
+                F[a][r] = s0;
+            }
+        double I[3][3];
+        if (D == 2) {
+            const double id = 1.0 / (F[0][0] * F[1][1] - F[0][1] * F[1][0]);
+            I[0][0] = F[1][1] * id; I[0][1] = -F[0][1] * id; I[1][0] = -F[1][0] * id; I[1][1] = F[0][0] * id;
+        } else {
+            const double c00 = F[1][1] * F[2][2] - F[1][2] * F[2][1], c01 = F[1][2] * F[2][0] - F[1][0] * F[2][2],
+                         c02 = F[1][0] * F[2][1] - F[1][1] * F[2][0];
+            const double id = 1.0 / (F[0][0] * c00 + F[0][1] * c01 + F[0][2] * c02);
+            I[0][0] = c00 * id; I[1][0] = c01 * id; I[2][0] = c02 * id;
+            I[0][1] = (F[0][2] * F[2][1] - F[0][1] * F[2][2]) * id;
+            I[1][1] = (F[0][0] * F[2][2] - F[0][2] * F[2][0]) * id;
+            I[2][1] = (F[0][1] * F[2][0] - F[0][0] * F[2][1]) * id;
+            I[0][2] = (F[0][1] * F[1][2] - F[0][2] * F[1][1]) * id;
+            I[1][2] = (F[0][2] * F[1][0] - F[0][0] * F[1][2]) * id;
+            I[2][2] = (F[0][0] * F[1][1] - F[0][1] * F[1][0]) * id;
+        }
+        for (int a = 0; a < D; ++a)
+            for (int r = 0; r < D; ++r) { Fm[a][r] = (T)F[a][r]; Fmi[a][r] = (T)I[a][r]; }
+    };
+    // y[(a,r)] = sum_{(c,s)} At_i[(a,r),(c,s)] X[(c,s)], then acc[(a,t)] += sum_r Fm[t][r] y[(a,r)]
+    auto at_apply = [&](int i, const T X[D2], T Fm[3][3], T *acc) {
+        for (int ar = 0; ar < D2; ++ar) {
+            T y = T(0);
+#pragma unroll
+            for (int cs = 0; cs < D2; ++cs) y += At[((size_t)b * D4 + ar * D2 + cs) * M.mA + i] * X[cs];
+            const int a = ar / D, r = ar - a * D;
+#pragma unroll
+            for (int t = 0; t < D; ++t) acc[a * D + t] += Fm[t][r] * y;
+        }
+    };
+
+    T acc[NA];
+#pragma unroll
+    for (int e = 0; e < NA; ++e) acc[e] = T(0);
+    const int nch = (m + SENS_CH - 1) / SENS_CH;
+    for (int ch = 0; ch < nch; ++ch) {
+        const int i0 = ch * SENS_CH, cnt = min(SENS_CH, m - i0);
+        if (tid < cnt) {
+            const int i = i0 + tid;
+            T Fm[3][3], Fmi[3][3], Gk[SENS_MAXP][3][3];
+            geometry(i, Fm, Fmi, Gk);
+            T H[D2];
+#pragma unroll
+            for (int cc = 0; cc < D2; ++cc) {
+                T h = T(0);
+                for (int j = 0; j < n; ++j) h += Gp[((size_t)i * D2 + cc) * n + j] * qs[j];
+                H[cc] = h;
+            }
+            T V[D2], WP[D2];
+#pragma unroll
+            for (int cc = 0; cc < D2; ++cc) {
+                V[cc] = (T)Bt.v[((size_t)b * D2 + cc) * m + i];
+                WP[cc] = (T)Bt.wP[((size_t)b * D2 + cc) * m + i];
+            }
+            for (int k = 0; k < np; ++k) {
+                T FG[3][3], Mk[D2], y[D2];
+                T tr = T(0);
+                for (int a = 0; a < D; ++a)
+                    for (int r = 0; r < D; ++r) {
+                        T s0 = T(0);
+                        for (int t = 0; t < D; ++t) s0 += Fmi[a][t] * Gk[k][t][r];
+                        FG[a][r] = s0;
+                    }
+                for (int a = 0; a < D; ++a) tr += FG[a][a];
+                for (int a = 0; a < D; ++a)
+                    for (int r = 0; r < D; ++r) {
+                        T s0 = T(0);
+                        for (int t = 0; t < D; ++t) s0 -= H[a * D + t] * FG[t][r];
+                        Mk[a * D + r] = s0;
+                    }
+                // y = At vec(M_k) (pulled back), its Xi^T image into T+U, and dv_k
+                for (int ar = 0; ar < D2; ++ar) {
+                    T yy = T(0);
+#pragma unroll
+                    for (int cs = 0; cs < D2; ++cs) yy += At[((size_t)b * D4 + ar * D2 + cs) * M.mA + i] * Mk[cs];
+                    y[ar] = yy;
+                }
+                for (int ar = 0; ar < D2; ++ar) {
+                    const int a = ar / D, r = ar - a * D;
+                    for (int t = 0; t < D; ++t) acc[D2 * SENS_MAXP + k * D2 + a * D + t] += Fm[t][r] * y[ar];
+                    // (V Gmu_k^T F_mu^-T)_ar = sum_s V_as sum_t Gmu_k[t][s] Fmi[r][t]
+                    T w3 = T(0);
+                    for (int s1 = 0; s1 < D; ++s1) {
+                        T gf = T(0);
+                        for (int t = 0; t < D; ++t) gf += Gk[k][t][s1] * Fmi[r][t];
+                        w3 += V[a * D + s1] * gf;
+                    }
+                    dv[((size_t)tid * SENS_MAXP + k) * D2 + ar] = tr * V[ar] + y[ar] - w3;
+                    acc[k * D2 + ar] += tr * WP[ar];
+                }
+            }
+        }
+        __syncthreads();
+        // z_k[j] += sum over the chunk's points and components of G[i][c][j] dv_k[i][c]
+        for (int e = tid; e < n * np; e += blockDim.x) {
+            const int k = e / n, j = e - k * n;
+            T z = T(0);
+            for (int ii = 0; ii < cnt; ++ii)
+#pragma unroll
+                for (int cc = 0; cc < D2; ++cc)
+                    z += Gp[((size_t)(i0 + ii) * D2 + cc) * n + j] * dv[((size_t)ii * SENS_MAXP + k) * D2 + cc];
+            zs[k * ld + j] += z;
+        }
+        __syncthreads();
+    }
+    // K dq_k = -z_k with the factor of K at the solution (K* = K)
+    for (int e = tid; e < np * ld; e += blockDim.x) zs[e] = -zs[e];
+    for (int e = tid; e < n * n; e += blockDim.x) Ks[(e / n) * ld + e % n] = (T)Bt.K[(size_t)b * n * n + e];
+    __syncthreads();
+    const bool ok = block_lu_solve<T>(Ks, n, ld, zs, ld, np, &s_piv);
+    __syncthreads();
+    // U_k: sum_i Xi^T At vec(G_i dq_k) (into the same accumulators as T)
+    for (int i = tid; i < m && ok; i += blockDim.x) {
+        T Fm[3][3], Fmi[3][3], Gk[SENS_MAXP][3][3];
+        geometry(i, Fm, Fmi, Gk);
+        for (int k = 0; k < np; ++k) {
+            T X[D2];
+#pragma unroll
+            for (int cc = 0; cc < D2; ++cc) {
+                T h = T(0);
+                for (int j = 0; j < n; ++j) h += Gp[((size_t)i * D2 + cc) * n + j] * zs[k * ld + j];
+                X[cc] = h;
+            }
+            at_apply(i, X, Fm, acc + D2 * SENS_MAXP + k * D2);
+        }
+    }
+    // fixed-order reduction of the per-thread sums: butterfly within each warp, then the warps in
+    // order (the LU region is free again)
+    __syncthreads();
+    const int lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    for (int e = 0; e < NA; ++e) {
+        T v = acc[e];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0) red[(size_t)wid * NA + e] = v;
+    }
+    __syncthreads();
+    __shared__ double dPU[D2 * SENS_MAXP];
+    if (tid < D2 * np) {
+        const int k = tid / D2, at = tid - k * D2;
+        double sacc = 0.0;
+        for (int w2 = 0; w2 < nw; ++w2)
+            sacc += (double)red[(size_t)w2 * NA + k * D2 + at] + (double)red[(size_t)w2 * NA + D2 * SENS_MAXP + k * D2 + at];
+        dPU[tid] = sacc / M.omega;
+    }
+    __syncthreads();
+    // rotate back: dPbar/dmu_k = Rbar dPbar_U/dmu_k
+    if (tid < D2 * np) {
+        const int k = tid / D2, ij = tid - k * D2, ii = ij / D, jj = ij - ii * D;
+        double s0 = 0.0;
+        for (int cc = 0; cc < D; ++cc) s0 += Bt.Rbar[b * D2 + ii * D + cc] * dPU[k * D2 + cc * D + jj];
+        out[(b * D2 + ij) * np + k] = ok ? s0 : NAN;
+    }
+}
+
+// shared memory of k_sensitivity: q, the right-hand sides, then max(dv chunk, partial sums, K)
+static size_t sensitivity_smem(int D, int n, size_t te) {
+    const size_t d2 = (size_t)D * D, na = 2 * d2 * SENS_MAXP;
+    const size_t region = std::max(std::max((size_t)SENS_CH * SENS_MAXP * d2, (size_t)(SENS_THREADS / 32) * na),
+                                   (size_t)n * (n + 1));
+    return ((size_t)n + (size_t)SENS_MAXP * (n + 1) + region) * te + 16;
+}
+
+int launch_sensitivity(const Model &M, Batch Bt, int precision, double *out, cudaStream_t s) {
+    if (M.n_par > SENS_MAXP) return -1;
+    const size_t te = precision == 0 ? 8 : 4;
+    const size_t sm = sensitivity_smem(M.d, M.n, te);
+    if (sm > 200 * 1024) return -1;
+#define PODECM_SENS(DD, TT)                                                                                  \
+    do {                                                                                                   \
+        cudaFuncSetAttribute(k_sensitivity<DD, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+        k_sensitivity<DD, TT><<<(int)Bt.B, SENS_THREADS, sm, s>>>(M, Bt, out);                             \
+    } while (0)
+    if (M.d == 2) {
+        if (precision == 0) PODECM_SENS(2, double); else PODECM_SENS(2, float);
+    } else {
+        if (precision == 0) PODECM_SENS(3, double); else PODECM_SENS(3, float);
+    }
+#undef PODECM_SENS
+    return 0;
+}
+
 template <int D>
 static int launch_finalize_t(const Model &M, Batch Bt, const StepOpts &o, double *Pbar, double *Abar, void *info,
                              cudaStream_t s) {

@@ -40,6 +40,7 @@ size_t tc3_image_bytes(int m);
 void tc3_build_images(int n, int m, const double *G, unsigned char *img);
 int launch_tc3(int mode, const Model &M, Batch Bt, const unsigned char *img, int *err, int sel, cudaStream_t s);
 void launch_force(const Model &M, Batch Bt, bool fp64, cudaStream_t s);
+int launch_sensitivity(const Model &M, Batch Bt, int precision, double *out, cudaStream_t s);
 void launch_list_converged(Batch Bt, cudaStream_t s);
 void launch_graph_advance(Batch Bt, const int32_t *list_next, cudaGraphConditionalHandle h, int max_pass,
                           cudaStream_t s);
@@ -49,7 +50,7 @@ void launch_all_active(Batch Bt, cudaStream_t s);
 
 using namespace podecm;
 
-#define ROM_NKERNELS 8
+#define ROM_NKERNELS 9
 
 struct rom_ctx {
     int dim = 0, device = 0;
@@ -110,6 +111,7 @@ struct rom_state {
     int64_t g_epoch = -1;
     double *io_F = nullptr, *io_P = nullptr, *io_A = nullptr;
     void *io_info = nullptr;
+    int last_prec = -1;   // precision of the last step (type of the stored tangent), -1 before the first
 };
 
 static rom_status fail(rom_ctx *c, rom_status s, const char *fmt, ...) {
@@ -608,6 +610,7 @@ static int launch_abar_assembly(rom_ctx *ctx, const Model &M, Batch bc, const St
 
 static rom_status run_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts, const double *Fbar_d, double *Pbar_d,
                            double *Abar_d, void *info_d) {
+    st->last_prec = opts->precision;
     StepOpts o;
     o.tol_rel = opts->tol_rel; o.tol_abs = opts->tol_abs; o.max_iter = opts->max_iter; o.max_ls = opts->max_ls;
     o.precision = opts->precision; o.start = opts->start; o.polar = opts->polar_split; o.want_abar = opts->want_abar;
@@ -783,6 +786,7 @@ static rom_status capture_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts
 
 static rom_status run_step_graph(rom_ctx *ctx, rom_state *st, const rom_opts *opts, const double *Fbar_d,
                                  double *Pbar_d, double *Abar_d, void *info_d) {
+    st->last_prec = opts->precision;
     if (o_needs_recapture(st, opts)) {
         rom_status s = capture_step(ctx, st, opts);
         if (s != ROM_OK) return s;
@@ -961,6 +965,37 @@ rom_status rom_debug_tangent(rom_ctx *ctx, const rom_state *st, void *At, int64_
     const size_t have = (size_t)st->B * ctx->dim * ctx->dim * ctx->dim * ctx->dim * (size_t)((st->m + 3) & ~3) * 8;
     CK(cudaMemcpy(At, st->bt.At, std::min((size_t)bytes, have), cudaMemcpyDeviceToHost));
     return ROM_OK;
+}
+
+rom_status rom_sensitivity_device(rom_ctx *ctx, rom_state *st, double *dPdmu_d) {
+    if (!ctx || !st || !dPdmu_d || st->ctx != ctx) return ROM_E_ARG;
+    if (st->last_prec < 0 || !ctx->has_geom) return fail(ctx, ROM_E_STATE, "rom_sensitivity before a step");
+    if (ctx->n_par > 3) return fail(ctx, ROM_E_ARG, "rom_sensitivity: at most 3 geometry parameters");
+    CK(cudaSetDevice(ctx->device));
+    const Model M = make_model(ctx);
+    Batch bt = st->bt;
+    bt.mu = ctx->mu;
+    if (timed(ctx, 8, 0.0, [&] { return launch_sensitivity(M, bt, st->last_prec, dPdmu_d, ctx->stream); }))
+        return fail(ctx, ROM_E_ARG, "rom_sensitivity: basis size n=%d too large", M.n);
+    CK(cudaGetLastError());
+    return ROM_OK;
+}
+
+rom_status rom_sensitivity(rom_ctx *ctx, rom_state *st, double *dPdmu) {
+    if (!ctx || !st || !dPdmu || st->ctx != ctx) return ROM_E_ARG;
+    CK(cudaSetDevice(ctx->device));
+    const size_t bytes = (size_t)st->B * ctx->dim * ctx->dim * ctx->n_par * 8;
+    double *d = nullptr;
+    rom_status s = dalloc(ctx, (void **)&d, bytes);
+    if (s != ROM_OK) return s;
+    s = rom_sensitivity_device(ctx, st, d);
+    if (s == ROM_OK) {
+        CK(cudaMemcpyAsync(dPdmu, d, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    void *p = d;
+    dfree(p);
+    return s;
 }
 
 rom_status rom_debug_residual(rom_ctx *ctx, const rom_state *st, double *r, double *v) {

@@ -58,11 +58,15 @@ class OracleRun:
         self.Fp = np.tile(np.eye(3), (B, m, 1, 1)).copy()
         self.xi = np.zeros((B, m))
 
-    def step(self, Fbar, tol_rel=1e-10, tol_abs=0.0, max_iter=25, max_ls=6, start="plain", polar_split=True, **kw):
+    def step(self, Fbar, tol_rel=1e-10, tol_abs=0.0, max_iter=25, max_ls=6, start="plain", polar_split=True,
+             sensitivity=False, **kw):
         q0 = self.q.copy()
         qs = self.q + (self.dq_prev if start == "prev" else 0.0)
+        sk = {}
+        if sensitivity:
+            sk["dFinv"], sk["dJ"] = oracle.geometry_derivatives(self.rom, self.Finv, self.J)
         out = oracle.rom_batch(self.rom, self.Finv, self.J, Fbar, qs, self.Fp, self.xi, tol_rel, tol_abs, max_iter,
-                               max_ls=max_ls, polar_split=polar_split)
+                               max_ls=max_ls, polar_split=polar_split, **sk)
         ok = out["status"] == 0
         self.dq_prev[ok] = qs[ok] - q0[ok]
         self.q[ok] = qs[ok]
