@@ -62,6 +62,8 @@ def parse():
                                                 "(default data/mlp_<workload>.npz)")
     ap.add_argument("--no-graphs", action="store_true", help="time the host-driven pass loop instead of graphs")
     ap.add_argument("--batch", type=int, default=None, help="override the batch size (testing)")
+    ap.add_argument("--sensitivity", action="store_true",
+                    help="also compute the shape sensitivities dPbar/dmu after every step (rom_sensitivity_device)")
     ap.add_argument("--fp64-residual", action="store_true",
                     help="form the residual of the tensor-core paths in FP64 instead of double-float FP32 pairs")
     ap.add_argument("--no-e2e", action="store_true")
@@ -189,6 +191,9 @@ def run_ours(args, rank, world):
     tile = ctx.autotune(st0, opts)
     st0.close()
 
+    # shape sensitivities dPbar/dmu after every step (optional, inside the timed region)
+    Sd = torch.empty(B * rom["d"] ** 2 * coef.shape[1], dtype=torch.float64, device="cuda") if args.sensitivity else None
+
     def timed_region(graphs, profile):
         st = ctx.state_create(B)
         ctx.use_graphs(graphs)
@@ -209,6 +214,8 @@ def run_ours(args, rank, world):
             flush_l2(flush)
             ev[k][0].record(stream)
             ctx.step_device(st, opts, Fd[W + k], Pd, Ad, Id)
+            if Sd is not None:
+                ctx.sensitivity_device(st, Sd)
             ev[k][1].record(stream)
             infos.append(Id.clone())
         torch.cuda.synchronize()
@@ -416,6 +423,7 @@ def main():
                 dtype={"fp64": "f64", "fp32": "f64+f32", "tf32": "f64+tf32", "bf16": "f64+bf16"}[r["prec"]],
                 data="synthetic",
                 config=dict(workload=wl, B_per_gpu=r["B"], precision=r["prec"], start=args.start,
+                            sensitivity=bool(args.sensitivity),
                             residual=("fp64" if r["prec"] == "fp64" or args.fp64_residual or
                                       (args.workload == "c2" and r["prec"] == "fp32") else "double-float FP32 pairs"),
                             step_driver="CUDA graph, device-driven Newton loop" if r["graphs"] else "host-driven passes",

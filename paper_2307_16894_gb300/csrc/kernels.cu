@@ -1302,14 +1302,14 @@ int launch_start(const Model &M, Batch Bt, const double *Fbar, const StepOpts &o
 // Points go in chunks of SENS_CH: one thread per point forms dv (shared memory) and its share of
 // the tr_k wP and Xi^T At vec(M_k) sums; then thread (j, k) adds G^T dv over the chunk.  The
 // partial sums are added in a fixed order.
-constexpr int SENS_CH = 128;
+constexpr int SENS_CH = 256;
 constexpr int SENS_THREADS = 256;
 constexpr int SENS_MAXP = 3;   // geometry parameters
 
 template <int D, typename T>
 __global__ void __launch_bounds__(SENS_THREADS) k_sensitivity(Model M, Batch Bt, double *__restrict__ out) {
     constexpr int D2 = D * D, D4 = D2 * D2;
-    constexpr int NA = 2 * D2 * SENS_MAXP;   // per-thread partial sums: S and T+U
+    constexpr int NA = D2 * SENS_MAXP;   // per-thread partial sums of dPbar_U/dmu_k
     extern __shared__ __align__(16) unsigned char smem[];
     const int64_t b = blockIdx.x;
     const int n = M.n, m = M.m, np = M.n_par, tid = threadIdx.x;
@@ -1330,6 +1330,8 @@ __global__ void __launch_bounds__(SENS_THREADS) k_sensitivity(Model M, Batch Bt,
     __shared__ double mu_s[SENS_MAXP];
     const T *At = reinterpret_cast<const T *>(Bt.At);
     const T *Gp = (sizeof(T) == 8) ? reinterpret_cast<const T *>(M.G_pt) : reinterpret_cast<const T *>(M.G32_pt);
+    // [d2][n][m] copy of G: per-point sums over j read consecutive points in consecutive threads
+    const T *Gt = (sizeof(T) == 8) ? reinterpret_cast<const T *>(M.G_T) : reinterpret_cast<const T *>(M.G32h_T);
     for (int j = tid; j < n; j += blockDim.x) qs[j] = (T)Bt.q_n[b * n + j];
     for (int e = tid; e < SENS_MAXP * ld; e += blockDim.x) zs[e] = T(0);
     if (tid < np) mu_s[tid] = Bt.mu[b * np + tid];
@@ -1367,15 +1369,24 @@ __global__ void __launch_bounds__(SENS_THREADS) k_sensitivity(Model M, Batch Bt,
         for (int a = 0; a < D; ++a)
             for (int r = 0; r < D; ++r) { Fm[a][r] = (T)F[a][r]; Fmi[a][r] = (T)I[a][r]; }
     };
-    // y[(a,r)] = sum_{(c,s)} At_i[(a,r),(c,s)] X[(c,s)], then acc[(a,t)] += sum_r Fm[t][r] y[(a,r)]
-    auto at_apply = [&](int i, const T X[D2], T Fm[3][3], T *acc) {
+    // y_k[(a,r)] = sum_{(c,s)} At_i[(a,r),(c,s)] X_k[(c,s)], then acc_k[(a,t)] += sum_r Fm[t][r] y_k[(a,r)]
+    // (acc_k at acc + k D2; each At entry read once for all k)
+    auto at_apply = [&](int i, const T X[SENS_MAXP][D2], T Fm[3][3], T *acc) {
         for (int ar = 0; ar < D2; ++ar) {
-            T y = T(0);
+            T y[SENS_MAXP];
 #pragma unroll
-            for (int cs = 0; cs < D2; ++cs) y += At[((size_t)b * D4 + ar * D2 + cs) * M.mA + i] * X[cs];
+            for (int k = 0; k < SENS_MAXP; ++k) y[k] = T(0);
+#pragma unroll
+            for (int cs = 0; cs < D2; ++cs) {
+                const T av = At[((size_t)b * D4 + ar * D2 + cs) * M.mA + i];
+#pragma unroll
+                for (int k = 0; k < SENS_MAXP; ++k) y[k] += av * X[k][cs];
+            }
             const int a = ar / D, r = ar - a * D;
 #pragma unroll
-            for (int t = 0; t < D; ++t) acc[a * D + t] += Fm[t][r] * y;
+            for (int k = 0; k < SENS_MAXP; ++k)
+#pragma unroll
+                for (int t = 0; t < D; ++t) acc[k * D2 + a * D + t] += Fm[t][r] * y[k];
         }
     };
 
@@ -1391,10 +1402,11 @@ __global__ void __launch_bounds__(SENS_THREADS) k_sensitivity(Model M, Batch Bt,
             geometry(i, Fm, Fmi, Gk);
             T H[D2];
 #pragma unroll
-            for (int cc = 0; cc < D2; ++cc) {
-                T h = T(0);
-                for (int j = 0; j < n; ++j) h += Gp[((size_t)i * D2 + cc) * n + j] * qs[j];
-                H[cc] = h;
+            for (int cc = 0; cc < D2; ++cc) H[cc] = T(0);
+            for (int j = 0; j < n; ++j) {
+                const T qj = qs[j];
+#pragma unroll
+                for (int cc = 0; cc < D2; ++cc) H[cc] += Gt[((size_t)cc * n + j) * m + i] * qj;
             }
             T V[D2], WP[D2];
 #pragma unroll
@@ -1402,41 +1414,49 @@ __global__ void __launch_bounds__(SENS_THREADS) k_sensitivity(Model M, Batch Bt,
                 V[cc] = (T)Bt.v[((size_t)b * D2 + cc) * m + i];
                 WP[cc] = (T)Bt.wP[((size_t)b * D2 + cc) * m + i];
             }
-            for (int k = 0; k < np; ++k) {
-                T FG[3][3], Mk[D2], y[D2];
-                T tr = T(0);
+            // M_k = -H F_mu^-1 Gmu_k and tr_k = tr(F_mu^-1 Gmu_k) for every k, then one pass over
+            // the rows of At_i gives y_k = At vec(M_k) for all k (each At entry read once)
+            T Mk[SENS_MAXP][D2], trk[SENS_MAXP];
+            for (int k = 0; k < SENS_MAXP; ++k) {
+                T FG[3][3];
+                trk[k] = T(0);
                 for (int a = 0; a < D; ++a)
                     for (int r = 0; r < D; ++r) {
                         T s0 = T(0);
-                        for (int t = 0; t < D; ++t) s0 += Fmi[a][t] * Gk[k][t][r];
+                        if (k < np)
+                            for (int t = 0; t < D; ++t) s0 += Fmi[a][t] * Gk[k][t][r];
                         FG[a][r] = s0;
                     }
-                for (int a = 0; a < D; ++a) tr += FG[a][a];
+                for (int a = 0; a < D; ++a) trk[k] += FG[a][a];
                 for (int a = 0; a < D; ++a)
                     for (int r = 0; r < D; ++r) {
                         T s0 = T(0);
                         for (int t = 0; t < D; ++t) s0 -= H[a * D + t] * FG[t][r];
-                        Mk[a * D + r] = s0;
+                        Mk[k][a * D + r] = s0;
                     }
-                // y = At vec(M_k) (pulled back), its Xi^T image into T+U, and dv_k
-                for (int ar = 0; ar < D2; ++ar) {
-                    T yy = T(0);
+            }
+            for (int ar = 0; ar < D2; ++ar) {
+                T yk[SENS_MAXP];
 #pragma unroll
-                    for (int cs = 0; cs < D2; ++cs) yy += At[((size_t)b * D4 + ar * D2 + cs) * M.mA + i] * Mk[cs];
-                    y[ar] = yy;
+                for (int k = 0; k < SENS_MAXP; ++k) yk[k] = T(0);
+#pragma unroll
+                for (int cs = 0; cs < D2; ++cs) {
+                    const T av = At[((size_t)b * D4 + ar * D2 + cs) * M.mA + i];
+#pragma unroll
+                    for (int k = 0; k < SENS_MAXP; ++k) yk[k] += av * Mk[k][cs];
                 }
-                for (int ar = 0; ar < D2; ++ar) {
-                    const int a = ar / D, r = ar - a * D;
-                    for (int t = 0; t < D; ++t) acc[D2 * SENS_MAXP + k * D2 + a * D + t] += Fm[t][r] * y[ar];
-                    // (V Gmu_k^T F_mu^-T)_ar = sum_s V_as sum_t Gmu_k[t][s] Fmi[r][t]
+                const int a = ar / D, r = ar - a * D;
+                for (int k = 0; k < np; ++k) {
+                    // Xi^T image of y into the sums, and dv_k = tr_k v + y - V Gmu_k^T F_mu^-T
+                    for (int t = 0; t < D; ++t) acc[k * D2 + a * D + t] += Fm[t][r] * yk[k];
                     T w3 = T(0);
                     for (int s1 = 0; s1 < D; ++s1) {
                         T gf = T(0);
                         for (int t = 0; t < D; ++t) gf += Gk[k][t][s1] * Fmi[r][t];
                         w3 += V[a * D + s1] * gf;
                     }
-                    dv[((size_t)tid * SENS_MAXP + k) * D2 + ar] = tr * V[ar] + y[ar] - w3;
-                    acc[k * D2 + ar] += tr * WP[ar];
+                    dv[((size_t)tid * SENS_MAXP + k) * D2 + ar] = trk[k] * V[ar] + yk[k] - w3;
+                    acc[k * D2 + ar] += trk[k] * WP[ar];
                 }
             }
         }
@@ -1463,16 +1483,23 @@ __global__ void __launch_bounds__(SENS_THREADS) k_sensitivity(Model M, Batch Bt,
     for (int i = tid; i < m && ok; i += blockDim.x) {
         T Fm[3][3], Fmi[3][3], Gk[SENS_MAXP][3][3];
         geometry(i, Fm, Fmi, Gk);
-        for (int k = 0; k < np; ++k) {
-            T X[D2];
+        T X[SENS_MAXP][D2];
+#pragma unroll
+        for (int k = 0; k < SENS_MAXP; ++k)
+#pragma unroll
+            for (int cc = 0; cc < D2; ++cc) X[k][cc] = T(0);
+        for (int j = 0; j < n; ++j) {
+            T dj[SENS_MAXP];
+#pragma unroll
+            for (int k = 0; k < SENS_MAXP; ++k) dj[k] = k < np ? zs[k * ld + j] : T(0);
 #pragma unroll
             for (int cc = 0; cc < D2; ++cc) {
-                T h = T(0);
-                for (int j = 0; j < n; ++j) h += Gp[((size_t)i * D2 + cc) * n + j] * zs[k * ld + j];
-                X[cc] = h;
+                const T g = Gt[((size_t)cc * n + j) * m + i];
+#pragma unroll
+                for (int k = 0; k < SENS_MAXP; ++k) X[k][cc] += g * dj[k];
             }
-            at_apply(i, X, Fm, acc + D2 * SENS_MAXP + k * D2);
         }
+        at_apply(i, X, Fm, acc);
     }
     // fixed-order reduction of the per-thread sums: butterfly within each warp, then the warps in
     // order (the LU region is free again)
@@ -1488,8 +1515,7 @@ __global__ void __launch_bounds__(SENS_THREADS) k_sensitivity(Model M, Batch Bt,
     if (tid < D2 * np) {
         const int k = tid / D2, at = tid - k * D2;
         double sacc = 0.0;
-        for (int w2 = 0; w2 < nw; ++w2)
-            sacc += (double)red[(size_t)w2 * NA + k * D2 + at] + (double)red[(size_t)w2 * NA + D2 * SENS_MAXP + k * D2 + at];
+        for (int w2 = 0; w2 < nw; ++w2) sacc += (double)red[(size_t)w2 * NA + k * D2 + at];
         dPU[tid] = sacc / M.omega;
     }
     __syncthreads();
@@ -1504,7 +1530,7 @@ __global__ void __launch_bounds__(SENS_THREADS) k_sensitivity(Model M, Batch Bt,
 
 // shared memory of k_sensitivity: q, the right-hand sides, then max(dv chunk, partial sums, K)
 static size_t sensitivity_smem(int D, int n, size_t te) {
-    const size_t d2 = (size_t)D * D, na = 2 * d2 * SENS_MAXP;
+    const size_t d2 = (size_t)D * D, na = d2 * SENS_MAXP;
     const size_t region = std::max(std::max((size_t)SENS_CH * SENS_MAXP * d2, (size_t)(SENS_THREADS / 32) * na),
                                    (size_t)n * (n + 1));
     return ((size_t)n + (size_t)SENS_MAXP * (n + 1) + region) * te + 16;
