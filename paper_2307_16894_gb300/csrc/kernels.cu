@@ -282,13 +282,21 @@ __global__ void __launch_bounds__(128, (D == 3 && sizeof(TT) == 4) ? 4 : 1) k_co
     tangent_setup<D, TT>(S, ph, F, cp, Finv, P, td);
     TT *At = reinterpret_cast<TT *>(Bt.At);
     const size_t ab = (size_t)b * D2 * D2 * M.mA + i;
+    // F_mu^-1 and wJ in the tangent precision, converted once (inside the direction loop the
+    // conversions would be redone per direction: on the mixed path they run on the FP64 pipe)
+    TT Fmt[3][3];
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+        for (int l = 0; l < D; ++l) Fmt[r][l] = TT(Fmi[r][l]);
+    const TT wJt = TT(wJ);
 #pragma unroll 1
     for (int c = 0; c < D; ++c)
 #pragma unroll 1
         for (int s = 0; s < D; ++s) {
             TT f[3] = {TT(0), TT(0), TT(0)};
 #pragma unroll
-            for (int l = 0; l < D; ++l) f[l] = TT(Fmi[s][l]);
+            for (int l = 0; l < D; ++l) f[l] = Fmt[s][l];
             TT dP[3][3];
             tangent_direction<D, TT>(td, c, f, dP);
             const int col = c * D + s;
@@ -298,8 +306,8 @@ __global__ void __launch_bounds__(128, (D == 3 && sizeof(TT) == 4) ? 4 : 1) k_co
                 for (int r = 0; r < D; ++r) {
                     TT t = TT(0);
 #pragma unroll
-                    for (int bb = 0; bb < D; ++bb) t += dP[a][bb] * TT(Fmi[r][bb]);
-                    At[ab + (size_t)((a * D + r) * D2 + col) * M.mA] = TT(wJ) * t;
+                    for (int bb = 0; bb < D; ++bb) t += dP[a][bb] * Fmt[r][bb];
+                    At[ab + (size_t)((a * D + r) * D2 + col) * M.mA] = wJt * t;
                 }
         }
 }
