@@ -448,23 +448,40 @@ struct TangentData {
     T P[3][3];      // first Piola-Kirchhoff stress
 };
 
+// FP64 -> tangent precision.  For FP32 the conversion truncates the mantissa by integer
+// operations on the bit pattern (|x| < 2^-126 flushes to zero, beyond the FP32 range gives
+// infinity): the tangent only forms the inexact-Newton Jacobian, and the integer pipe is idle
+// while the FP64 pipe, which executes the conversion instruction, bounds the kernel.
+template <typename T>
+__device__ __forceinline__ T to_tangent(double x) { return T(x); }
+template <>
+__device__ __forceinline__ float to_tangent<float>(double x) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const uint32_t hi = (uint32_t)(u >> 32), lo = (uint32_t)u;
+    const int e = (int)((hi >> 20) & 0x7FFu);
+    const uint32_t sign = hi & 0x80000000u;
+    if (e < 1023 - 126) return __uint_as_float(sign);
+    if (e > 1023 + 127) return __uint_as_float(sign | 0x7F800000u);
+    return __uint_as_float(sign | ((uint32_t)(e - 896) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
+}
+
 template <int D, typename T>
 __device__ __forceinline__ void tangent_setup(const MatState &S, const PhaseD &ph, const double F[3][3],
                                               const double cp[6], const double Finv[3][3],
                                               const double P[3][3], TangentData<T> &td) {
     // all in the tangent precision T (FP64 path: double; mixed path: float on the FP32 pipe)
-    const T G = T(ph.G), beta = T(S.beta);
+    const T G = to_tangent<T>(ph.G), beta = to_tangent<T>(S.beta);
     // algorithmic moduli of the radial return in principal log strains
     T cpl = T(0);
-    if (S.plastic) cpl = T(6) * G * G * (T(1) / (T(3) * G + T(S.hs)) - T(S.dg) / T(S.q_tr));
-    const T nh[3] = {T(S.nh[0]), T(S.nh[1]), T(S.nh[2])};
+    if (S.plastic) cpl = T(6) * G * G * (T(1) / (T(3) * G + to_tangent<T>(S.hs)) - to_tangent<T>(S.dg) / to_tangent<T>(S.q_tr));
+    const T nh[3] = {to_tangent<T>(S.nh[0]), to_tangent<T>(S.nh[1]), to_tangent<T>(S.nh[2])};
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
         for (int b = 0; b < 3; ++b)
-            td.c[a][b] = T(ph.Kb) + T(2) * G * beta * ((a == b ? T(1) : T(0)) - T(1) / T(3)) - cpl * nh[a] * nh[b];
+            td.c[a][b] = to_tangent<T>(ph.Kb) + T(2) * G * beta * ((a == b ? T(1) : T(0)) - T(1) / T(3)) - cpl * nh[a] * nh[b];
     const T gb = G * beta;
-    const T l0 = T(S.lam[0]), l1 = T(S.lam[1]), l2 = T(S.lam[2]);
+    const T l0 = to_tangent<T>(S.lam[0]), l1 = to_tangent<T>(S.lam[1]), l2 = to_tangent<T>(S.lam[2]);
     td.th[0] = gb * log_divided_difference<T>(l0, l1);
     if (D == 3) {
         td.th[1] = gb * log_divided_difference<T>(l0, l2);
@@ -481,9 +498,9 @@ __device__ __forceinline__ void tangent_setup(const MatState &S, const PhaseD &p
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) Ft[i][j] = T(F[i][j]);
-    C[0][0] = T(cp[0]); C[0][1] = C[1][0] = T(cp[1]); C[0][2] = C[2][0] = T(cp[2]);
-    C[1][1] = T(cp[3]); C[1][2] = C[2][1] = T(cp[4]); C[2][2] = T(cp[5]);
+        for (int j = 0; j < 3; ++j) Ft[i][j] = to_tangent<T>(F[i][j]);
+    C[0][0] = to_tangent<T>(cp[0]); C[0][1] = C[1][0] = to_tangent<T>(cp[1]); C[0][2] = C[2][0] = to_tangent<T>(cp[2]);
+    C[1][1] = to_tangent<T>(cp[3]); C[1][2] = C[2][1] = to_tangent<T>(cp[4]); C[2][2] = to_tangent<T>(cp[5]);
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -492,9 +509,9 @@ __device__ __forceinline__ void tangent_setup(const MatState &S, const PhaseD &p
 #pragma unroll
             for (int k = 0; k < 3; ++k) s += C[i][k] * Ft[j][k];
             td.Z[i][j] = s;
-            td.N[i][j] = T(S.N[i][j]);
-            td.Finv[i][j] = T(Finv[i][j]);
-            td.P[i][j] = T(P[i][j]);
+            td.N[i][j] = to_tangent<T>(S.N[i][j]);
+            td.Finv[i][j] = to_tangent<T>(Finv[i][j]);
+            td.P[i][j] = to_tangent<T>(P[i][j]);
         }
 }
 
