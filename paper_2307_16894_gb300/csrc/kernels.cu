@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(128, (D == 3 && sizeof(TT) == 4) ? 4 : 1) k_co
             }
         }
 #pragma unroll
-        for (int c = 0; c < D2; ++c) H[c] = (double)s[c] + (double)er[c];
+        for (int c = 0; c < D2; ++c) H[c] = f2d_exact(s[c]) + f2d_exact(er[c]);
     } else {
         for (int c = 0; c < D2; ++c) H[c] = 0.0;
         const double *qb = Bt.q_trial + b * n;

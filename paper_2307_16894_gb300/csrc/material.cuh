@@ -122,6 +122,35 @@ __device__ __forceinline__ void jacobi3_f32(float a[3][3], float V[3][3]) {
     }
 }
 
+// FP64 -> tangent precision.  For FP32 the conversion truncates the mantissa by integer
+// operations on the bit pattern (|x| < 2^-126 flushes to zero, beyond the FP32 range gives
+// infinity): the tangent only forms the inexact-Newton Jacobian, and the integer pipe is idle
+// while the FP64 pipe, which executes the conversion instruction, bounds the kernel.
+template <typename T>
+__device__ __forceinline__ T to_tangent(double x) { return T(x); }
+template <>
+__device__ __forceinline__ float to_tangent<float>(double x) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const uint32_t hi = (uint32_t)(u >> 32), lo = (uint32_t)u;
+    const int e = (int)((hi >> 20) & 0x7FFu);
+    const uint32_t sign = hi & 0x80000000u;
+    if (e < 1023 - 126) return __uint_as_float(sign);
+    if (e > 1023 + 127) return __uint_as_float(sign | 0x7F800000u);
+    return __uint_as_float(sign | ((uint32_t)(e - 896) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
+}
+
+// FP32 -> FP64 by integer operations on the bit pattern: exact for normal numbers, infinities
+// and NaNs (the exponent is rebiased, the mantissa widened); FP32 subnormals flush to zero.  The
+// same value as the conversion instruction, without occupying the FP64 pipe.
+__device__ __forceinline__ double f2d_exact(float x) {
+    const uint32_t u = __float_as_uint(x);
+    const uint32_t e = (u >> 23) & 0xFFu;
+    const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+    if (e == 0) return __longlong_as_double((long long)sign);
+    const unsigned long long ee = (e == 0xFFu) ? 0x7FFull : (unsigned long long)(e + 896u);
+    return __longlong_as_double((long long)(sign | (ee << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+}
+
 // FP64-accurate symmetric 3x3 eigen-decomposition: FP32 Jacobi gives approximate
 // eigenvectors, which are made exactly orthonormal in FP64 (Gram-Schmidt + cross product)
 // and used to rotate b in FP64; FP64 Jacobi sweeps then finish the nearly diagonal matrix.
@@ -132,22 +161,22 @@ __device__ __forceinline__ void eig3_mixed(const double b[3][3], double lam[3], 
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) af[i][j] = (float)b[i][j];
+        for (int j = 0; j < 3; ++j) af[i][j] = to_tangent<float>(b[i][j]);   // approximate start only
     jacobi3_f32(af, Vf);
     double q0[3], q1[3], q2[3];
     {
         double n0 = 0.0;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) { q0[k] = Vf[k][0]; n0 += q0[k] * q0[k]; }
+        for (int k = 0; k < 3; ++k) { q0[k] = f2d_exact(Vf[k][0]); n0 += q0[k] * q0[k]; }
         const double i0 = 1.0 / sqrt(n0);
 #pragma unroll
         for (int k = 0; k < 3; ++k) q0[k] *= i0;
         double dt = 0.0;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) dt += q0[k] * (double)Vf[k][1];
+        for (int k = 0; k < 3; ++k) dt += q0[k] * f2d_exact(Vf[k][1]);
         double n1 = 0.0;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) { q1[k] = (double)Vf[k][1] - dt * q0[k]; n1 += q1[k] * q1[k]; }
+        for (int k = 0; k < 3; ++k) { q1[k] = f2d_exact(Vf[k][1]) - dt * q0[k]; n1 += q1[k] * q1[k]; }
         const double i1 = 1.0 / sqrt(n1);
 #pragma unroll
         for (int k = 0; k < 3; ++k) q1[k] *= i1;
@@ -447,23 +476,6 @@ struct TangentData {
     T Finv[3][3];   // F^-1
     T P[3][3];      // first Piola-Kirchhoff stress
 };
-
-// FP64 -> tangent precision.  For FP32 the conversion truncates the mantissa by integer
-// operations on the bit pattern (|x| < 2^-126 flushes to zero, beyond the FP32 range gives
-// infinity): the tangent only forms the inexact-Newton Jacobian, and the integer pipe is idle
-// while the FP64 pipe, which executes the conversion instruction, bounds the kernel.
-template <typename T>
-__device__ __forceinline__ T to_tangent(double x) { return T(x); }
-template <>
-__device__ __forceinline__ float to_tangent<float>(double x) {
-    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-    const uint32_t hi = (uint32_t)(u >> 32), lo = (uint32_t)u;
-    const int e = (int)((hi >> 20) & 0x7FFu);
-    const uint32_t sign = hi & 0x80000000u;
-    if (e < 1023 - 126) return __uint_as_float(sign);
-    if (e > 1023 + 127) return __uint_as_float(sign | 0x7F800000u);
-    return __uint_as_float(sign | ((uint32_t)(e - 896) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
-}
 
 template <int D, typename T>
 __device__ __forceinline__ void tangent_setup(const MatState &S, const PhaseD &ph, const double F[3][3],
