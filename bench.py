@@ -364,15 +364,16 @@ def kernel_rooflines(r, peaks):
         pk = bf16 * (1.0 if prec == "bf16" else 0.5)
         add("assemble", "tensor", prof["assemble"][2], pk,
             src + " bf16_tflops" + ("" if prec == "bf16" else " x 0.5 (TF32 rate)"))
+    elif prec == "fp64":
+        add("assemble", "alu", prof["assemble"][2], FP64_PEAK_TFLOPS, "FP64 pipe")
+    else:
+        add("assemble", "alu", prof["assemble"][2], FP32_PEAK_TFLOPS, "FP32 pipe: 152 SM x 128 FFMA/clk x 2 x 2.07 GHz")
+    if prof.get("force", (0, 0, 0))[2] > 0:
         if r.get("fp64_residual"):
             add("force", "alu", prof["force"][2], FP64_PEAK_TFLOPS, "FP64 pipe")
         else:   # double-float residual: 12 FP32 pipe operations per multiply-add
             add("force", "alu", prof["force"][2], FP32_PEAK_TFLOPS / 12,
                 "FP32 pipe / 12: double-float multiply-add of 12 FP32 operations")
-    elif prec == "fp64":
-        add("assemble", "alu", prof["assemble"][2], FP64_PEAK_TFLOPS, "FP64 pipe")
-    else:
-        add("assemble", "alu", prof["assemble"][2], FP32_PEAK_TFLOPS, "FP32 pipe: 152 SM x 128 FFMA/clk x 2 x 2.07 GHz")
     add("solve", "alu", prof["solve"][2], FP64_PEAK_TFLOPS, "FP64 pipe")
     return out
 
@@ -424,8 +425,7 @@ def main():
                 data="synthetic",
                 config=dict(workload=wl, B_per_gpu=r["B"], precision=r["prec"], start=args.start,
                             sensitivity=bool(args.sensitivity),
-                            residual=("fp64" if r["prec"] == "fp64" or args.fp64_residual or
-                                      (args.workload == "c2" and r["prec"] == "fp32") else "double-float FP32 pairs"),
+                            residual=("fp64" if r["prec"] == "fp64" or args.fp64_residual else "double-float FP32 pairs"),
                             step_driver="CUDA graph, device-driven Newton loop" if r["graphs"] else "host-driven passes",
                             l2="flushed between timed steps (256 MB write)", converged=r["n_ok"],
                             assembly_tile=dict(edge=r["tile"][0], chunk=r["tile"][1]),

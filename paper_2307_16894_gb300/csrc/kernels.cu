@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(128, (D == 3 && sizeof(TT) == 4) ? 4 : 1) k_co
 // --------------------------------------------------------------------- assembly
 // smem layout: Gs64[CH][D2][np] | Ys[CH][D2][np] (TK) | As[CH][D4] (TK) | vs[CH][D2] | (FP32: Gs32)
 template <int D, typename TK, int TM>
-__global__ void __launch_bounds__(256) k_assemble(Model M, Batch Bt, int CH, int NG) {
+__global__ void __launch_bounds__(256) k_assemble(Model M, Batch Bt, int CH, int NG, int do_force) {
     constexpr int D2 = D * D, D4 = D2 * D2;
     extern __shared__ __align__(16) unsigned char smem[];
     const int n_act = Bt.counts[0];
@@ -364,17 +364,18 @@ __global__ void __launch_bounds__(256) k_assemble(Model M, Batch Bt, int CH, int
             const int ii = row / D2;
             const bool in = ii < ch && col < n;
             const size_t gi = ((size_t)(c0 + ii) * D2 + (row - ii * D2)) * n + col;
-            Gs[e] = in ? M.G_pt[gi] : 0.0;
+            if (sizeof(TK) == sizeof(double) || do_force) Gs[e] = in ? M.G_pt[gi] : 0.0;
             if (sizeof(TK) != sizeof(double)) Gk[e] = in ? TK(M.G32_pt[gi]) : TK(0);
         }
         for (int e = tid; e < CH * D4; e += blockDim.x) {
             const int ce = e / CH, ii = e - ce * CH;
             As[ii * D4 + ce] = (ii < ch) ? At[((size_t)b * D4 + ce) * M.mA + c0 + ii] : TK(0);
         }
-        for (int e = tid; e < CH * D2; e += blockDim.x) {
-            const int c = e / CH, ii = e - c * CH;
-            vs[ii * D2 + c] = (ii < ch) ? Bt.v[((size_t)b * D2 + c) * m + c0 + ii] : 0.0;
-        }
+        if (do_force)
+            for (int e = tid; e < CH * D2; e += blockDim.x) {
+                const int c = e / CH, ii = e - c * CH;
+                vs[ii * D2 + c] = (ii < ch) ? Bt.v[((size_t)b * D2 + c) * m + c0 + ii] : 0.0;
+            }
         __syncthreads();
         // Y[ii][c][k] = sum_e As[ii][c][e] G[ii][e][k]
         const TK *Gsrc = (sizeof(TK) == sizeof(double)) ? reinterpret_cast<const TK *>(Gs) : Gk;
@@ -387,7 +388,7 @@ __global__ void __launch_bounds__(256) k_assemble(Model M, Batch Bt, int CH, int
             Ys[e] = s;
         }
         // force: r_j += sum_rows G[row][j] v[row]  (FP64; rows split over FG thread groups, fixed order)
-        if (fg < FG) {
+        if (do_force && fg < FG) {
             for (int row = fg; row < ch * D2; row += FG) racc += Gs[row * np + fj] * vs[row];
         }
         __syncthreads();
@@ -427,6 +428,7 @@ __global__ void __launch_bounds__(256) k_assemble(Model M, Batch Bt, int CH, int
         Kb[e] = double(s);
     }
     // reduce the force groups in a fixed order (reuse the buffer after the K gather)
+    if (!do_force) return;   // the residual comes from the double-float force kernel
     __syncthreads();
     double *fr = reinterpret_cast<double *>(smem);
     if (fg < FG) fr[fg * n + fj] = racc;
@@ -1202,6 +1204,10 @@ void launch_add_pred(Batch Bt, int n, const double *pred, cudaStream_t s) {
 }
 
 // ----------------------------------------------------------------- host launchers
+// the residual of a mixed-precision step comes from the double-float force kernel (launch_force)
+// unless the model has no split image of G or the step asks for the FP64 residual
+bool separate_force(const Model &M, const StepOpts &o) { return o.precision >= 1 && M.Gdf && !o.fp64_residual; }
+
 template <int D, int TM>
 static int launch_assemble(const Model &M, Batch Bt, const StepOpts &o, cudaStream_t s) {
     constexpr int D2 = D * D, D4 = D2 * D2;
@@ -1226,10 +1232,10 @@ static int launch_assemble(const Model &M, Batch Bt, const StepOpts &o, cudaStre
     const size_t sm = smem_for(CH);
     if (o.precision == 0) {
         cudaFuncSetAttribute(k_assemble<D, double, TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_assemble<D, double, TM><<<(int)Bt.B, nthreads, sm, s>>>(M, Bt, CH, NG);
+        k_assemble<D, double, TM><<<(int)Bt.B, nthreads, sm, s>>>(M, Bt, CH, NG, 1);
     } else {
         cudaFuncSetAttribute(k_assemble<D, float, TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_assemble<D, float, TM><<<(int)Bt.B, nthreads, sm, s>>>(M, Bt, CH, NG);
+        k_assemble<D, float, TM><<<(int)Bt.B, nthreads, sm, s>>>(M, Bt, CH, NG, separate_force(M, o) ? 0 : 1);
     }
     return 0;
 }

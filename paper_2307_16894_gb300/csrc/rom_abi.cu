@@ -41,6 +41,7 @@ void tc3_build_images(int n, int m, const double *G, unsigned char *img);
 int launch_tc3(int mode, const Model &M, Batch Bt, const unsigned char *img, int *err, int sel, cudaStream_t s);
 void launch_force(const Model &M, Batch Bt, bool fp64, cudaStream_t s);
 int launch_sensitivity(const Model &M, Batch Bt, int precision, double *out, cudaStream_t s);
+bool separate_force(const Model &M, const StepOpts &o);
 void launch_list_converged(Batch Bt, cudaStream_t s);
 void launch_graph_advance(Batch Bt, const int32_t *list_next, cudaGraphConditionalHandle h, int max_pass,
                           cudaStream_t s);
@@ -626,7 +627,11 @@ static rom_status run_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts, co
     // K: 2 m d2 n^2 on the tensor cores (full product), m d2 n (n + 1) on the CUDA cores (upper
     // triangle; the SIMT kernel also forms the force); LU + solve: 2 n^3 / 3 + 2 n^2
     const bool tcp = tc_path(ctx, M, o.precision);
-    const double fl_asm = tcp ? 2 * m * d4 * n + 2 * m * d2 * n * n : 2 * m * d4 * n + m * d2 * n * (n + 1) + 2 * m * d2 * n;
+    // the residual in its own kernel: always on the tensor-core paths, and on the mixed CUDA-core
+    // path when it is formed in double-float arithmetic
+    const bool sepf = tcp || separate_force(M, o);
+    const double fl_asm = tcp ? 2 * m * d4 * n + 2 * m * d2 * n * n
+                              : 2 * m * d4 * n + m * d2 * n * (n + 1) + (sepf ? 0.0 : 2 * m * d2 * n);
     const double fl_kin = 2 * m * d2 * n;
     const double fl_lu = 2 * n * n * n / 3 + 2 * n * n;
     if (ctx->d_err) CK(cudaMemsetAsync(ctx->d_err, 0, 4, ctx->stream));   // tensor-core error flag of this step
@@ -650,12 +655,12 @@ static rom_status run_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts, co
         const double na = (double)n_act;
         auto asm_launch = [&] { return launch_assembly(ctx, M, bt, o, nxt, ctx->stream); };
         auto force_launch = [&] {
-            if (tcp) launch_force(M, bt, o.fp64_residual != 0, ctx->stream);
+            if (sepf) launch_force(M, bt, o.fp64_residual != 0, ctx->stream);
             return 0;
         };
         if (timed(ctx, 1, na * fl_kin, [&] { return launch_kernel(1, M, bt, o, nxt, ctx->stream); }) ||
             timed(ctx, 2, na * fl_asm, asm_launch, (M.d == 3 && tcp && o.precision >= 2) ? 2 : 1) ||
-            (tcp && timed(ctx, 7, na * fl_kin, force_launch)) ||
+            (sepf && timed(ctx, 7, na * fl_kin, force_launch)) ||
             timed(ctx, 3, na * fl_lu, [&] { return launch_kernel(3, M, bt, o, nxt, ctx->stream); }) ||
             timed(ctx, 5, 0.0, [&] { return launch_kernel(5, M, bt, o, nxt, ctx->stream); }))
             return fail(ctx, ROM_E_ARG, "rom_step: basis size n=%d not supported by the assembly kernel", M.n);
@@ -753,7 +758,7 @@ static rom_status capture_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts
             int32_t *nxt = st->list2;
             bad |= launch_kernel(1, M, bt, o, nxt, bs);
             bad |= launch_assembly(ctx, M, bt, o, nxt, bs);
-            if (tc_path(ctx, M, o.precision)) launch_force(M, bt, o.fp64_residual != 0, bs);
+            if (tc_path(ctx, M, o.precision) || separate_force(M, o)) launch_force(M, bt, o.fp64_residual != 0, bs);
             bad |= launch_kernel(3, M, bt, o, nxt, bs);
             launch_graph_advance(bt, nxt, h, max_pass, bs);
             cudaGraph_t out = nullptr;

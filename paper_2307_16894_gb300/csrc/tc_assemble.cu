@@ -303,16 +303,16 @@ __global__ void __launch_bounds__(256) k_force(Model M, Batch Bt) {
 // separate FP32 compensation (Ogita, Rump & Oishi 2005), ~1e-13 relative to sum |terms|.  The FP64
 // pipe of this GPU runs at 1/64 of the FP32 rate, so the 12 FP32 operations of one double-float
 // multiply-add cost ~5x less than one DFMA.  The instances share G: a CTA of 256 threads takes
-// FDF_NI instances and 64 columns j (blockIdx.y), thread (j, ig) accumulates FDF_IPT instances.
+// FDF_NI instances and CW columns j (blockIdx.y), thread (j, ig) accumulates FDF_IPT instances.
 // Chunks of FDF_RC rows of G (cp.async) and of the v rows of the FDF_NI instances (through
 // registers, split on the way) are double-buffered in shared memory, so that the loads of the next
 // chunk overlap the arithmetic of this one.  Each thread sums its rows in a fixed order, so the
 // result does not depend on the launch.
 constexpr int FDF_RC = 32;                 // rows per staged chunk
-constexpr int FDF_IPT = 4;                 // instances per thread
-constexpr int FDF_NI = 4 * FDF_IPT;        // instances per CTA (4 groups of 64 columns)
+constexpr int FDF_NI = 16;                 // instances per CTA
 constexpr int FDF_LD = FDF_NI * FDF_RC / 256;   // staged v elements per thread and chunk
-constexpr int FDF_GLD = FDF_RC * 32 / 256;      // 16-byte G copies per thread and chunk
+// CW columns per CTA (64 for n > 32, else 32 so that small bases keep the threads busy):
+// 256 / CW column groups, each thread accumulating FDF_NI * CW / 256 instances
 
 __device__ __forceinline__ void df_mac(float &s, float &er, float2 g, float2 v) {
     const float pr = __fmul_rn(g.x, v.x);
@@ -331,16 +331,19 @@ __device__ __forceinline__ void fdf_cp16(void *dst, const void *src) {
                  : "memory");
 }
 
+template <int CW>
 __global__ void __launch_bounds__(256) k_force_df(Model M, Batch Bt) {
-    __shared__ __align__(16) float2 gs[2][FDF_RC][64];
+    constexpr int FDF_IPT = FDF_NI * CW / 256;          // instances per thread
+    constexpr int FDF_GLD = FDF_RC * (CW / 2) / 256;    // 16-byte G copies per thread and chunk
+    __shared__ __align__(16) float2 gs[2][FDF_RC][CW];
     __shared__ float2 vs[2][FDF_NI][FDF_RC];
     const int n_act = Bt.counts[0];
     const int p0 = blockIdx.x * FDF_NI;
     if (p0 >= n_act) return;
     const int n = M.n, np = (n + 1) & ~1, K = M.m * M.d2;
-    const int tid = threadIdx.x, ig = tid >> 6, jl = tid & 63;
-    const int j0 = blockIdx.y * 64, j = j0 + jl;
-    const int nc2 = min(64, np - j0) / 2;   // 16-byte column pairs of this column block
+    const int tid = threadIdx.x, ig = tid / CW, jl = tid % CW;
+    const int j0 = blockIdx.y * CW, j = j0 + jl;
+    const int nc2 = min(CW, np - j0) / 2;   // 16-byte column pairs of this column block
     const int nch = (K + FDF_RC - 1) / FDF_RC;
     // v staging map: element e = tid + 256 t of a chunk is row e % FDF_RC of instance slot e / FDF_RC
     const double *vrow[FDF_LD];
@@ -370,7 +373,7 @@ __global__ void __launch_bounds__(256) k_force_df(Model M, Batch Bt) {
         const int k0 = c * FDF_RC;
 #pragma unroll
         for (int t = 0; t < FDF_GLD; ++t) {
-            const int e = tid + 256 * t, row = e >> 5, q = e & 31;
+            const int e = tid + 256 * t, row = e / (CW / 2), q = e % (CW / 2);
             if (q < nc2 && k0 + row < K) fdf_cp16(&gs[c & 1][row][2 * q], M.Gdf + (size_t)(k0 + row) * np + j0 + 2 * q);
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
@@ -391,7 +394,7 @@ __global__ void __launch_bounds__(256) k_force_df(Model M, Batch Bt) {
         }
         const int rows = min(FDF_RC, K - c * FDF_RC);
         const float2 (*vb)[FDF_RC] = vs[c & 1] + ig * FDF_IPT;
-        const float2 (*gb)[64] = gs[c & 1];
+        const float2 (*gb)[CW] = gs[c & 1];
         if (colok) {
 #pragma unroll 4
             for (int r = 0; r < rows; ++r) {
@@ -469,8 +472,13 @@ static int launch_tc_t(const Model &M, Batch Bt, const unsigned char *img, int *
 // for, else FP64
 void launch_force(const Model &M, Batch Bt, bool fp64, cudaStream_t s) {
     if (M.Gdf && !fp64) {
-        const dim3 grid((unsigned)((Bt.B + FDF_NI - 1) / FDF_NI), (unsigned)((M.n + 63) / 64));
-        k_force_df<<<grid, 256, 0, s>>>(M, Bt);
+        if (M.n > 32) {
+            const dim3 grid((unsigned)((Bt.B + FDF_NI - 1) / FDF_NI), (unsigned)((M.n + 63) / 64));
+            k_force_df<64><<<grid, 256, 0, s>>>(M, Bt);
+        } else {
+            const dim3 grid((unsigned)((Bt.B + FDF_NI - 1) / FDF_NI), 1u);
+            k_force_df<32><<<grid, 256, 0, s>>>(M, Bt);
+        }
     } else {
         k_force<<<(int)Bt.B, 256, 0, s>>>(M, Bt);
     }

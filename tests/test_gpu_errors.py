@@ -21,7 +21,7 @@ def built():
 
 
 CASES = {"c2": (32, 8), "c3": (8, 6)}
-PRECS = [("fp64", False), ("fp32", False), ("tf32", False), ("tf32", True), ("bf16", False)]
+PRECS = [("fp64", False), ("fp32", False), ("fp32", True), ("tf32", False), ("tf32", True), ("bf16", False)]
 
 
 def run_case(name, prec, fp64_residual):
@@ -54,8 +54,6 @@ def test_errors_per_output(name):
         pytest.skip("3D model file not generated")
     rows = []
     for prec, f64r in PRECS:
-        if name == "c2" and f64r:
-            continue   # the 2D FP32 path forms its residual in FP64 anyway
         err, its = run_case(name, prec, f64r)
         label = prec + (" + FP64 residual" if f64r else "")
         rows.append((label, err, its))
