@@ -41,10 +41,10 @@ CONST_FP64_FLOP_PER_POINT = {(3, "mixed"): 1590.0, (3, "fp64"): 5917.0, (2, "mix
 # DRAM bytes (read + write) per evaluated cubature point of the constitutive kernel, from one ncu
 # capture of its first (all instances active) launch: --metrics dram__bytes_read.sum,
 # dram__bytes_write.sum -k regex:k_constitutive -s 0 -c 1 on `bench.py --workload c3 --batch 2048
-# --steps 2 --warmup 3 --no-cpu --no-e2e --no-graphs` (1.083 GB / 2048 x 600 points) and on
-# `bench.py --steps 2 --warmup 3 --no-cpu --no-e2e --no-graphs` (83.1 MB / 4096 x 160 points; the
+# --steps 2 --warmup 3 --no-cpu --no-e2e --no-graphs` (1.168 GB / 2048 x 600 points) and on
+# `bench.py --steps 2 --warmup 3 --no-cpu --no-e2e --no-graphs` (81.9 MB / 4096 x 160 points; the
 # 2D outputs stay in L2 during the kernel, so DRAM sees less than the algorithmic bytes)
-CONST_DRAM_BYTES_PER_POINT = {(3, "mixed"): 881.3, (2, "mixed"): 126.8}
+CONST_DRAM_BYTES_PER_POINT = {(3, "mixed"): 950.5, (2, "mixed"): 125.0}
 
 
 def parse():
