@@ -471,7 +471,7 @@ __global__ void __launch_bounds__(tc3::Cfg<MODE>::THREADS, 1)
                     : "r"(taddr));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                for (int q = 0; q < 32; ++q) v[hh * 32 + q] += (double)__uint_as_float(r[q]);
+                for (int q = 0; q < 32; ++q) v[hh * 32 + q] += f2d_exact(__uint_as_float(r[q]));   // widening off the FP64 pipe
             }
             }
             const int64_t b = bI[2 * p + ih];
@@ -827,7 +827,7 @@ __global__ void __launch_bounds__(tc4::THREADS, 1)
                 double *Kb = Bt.K + (size_t)b * n * n + (size_t)j * n;
 #pragma unroll
                 for (int k = 0; k < NCOLS; ++k)
-                    if (k < n) Kb[k] = (double)__uint_as_float(v[k]);
+                    if (k < n) Kb[k] = f2d_exact(__uint_as_float(v[k]));
             }
         }
     }
