@@ -71,3 +71,25 @@ def test_sensitivity_fd_2d():
 def test_sensitivity_fd_3d():
     """3D inclusion RVE (c3 model, n = 64, m = 600, three map coefficients), after 6 load steps."""
     check("c3", 1, 6, 1e-5, 1e-6)
+
+
+def test_sensitivity_objectivity_2d():
+    """With the polar split the step is objective, so dPbar/dmu(R Fbar) = R dPbar/dmu(Fbar): a
+    pin of the rotation handling of the sensitivities that does not use finite differences."""
+    rom, mu, coef, paths = workload.batch("c2", B=2)
+    q, Fp, xi = history(rom, coef, paths, 6)
+    F = paths[:, 6]
+    th = 0.7
+    R = np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
+    Finv, J = geometry(rom, coef)
+    dFinv, dJ = oracle.geometry_derivatives(rom, Finv, J)
+    outs = []
+    for FF in (F, np.einsum("ij,bjk->bik", R, F)):
+        o = oracle.rom_batch(rom, Finv, J, np.ascontiguousarray(FF), q.copy(), Fp.copy(), xi.copy(), 1e-12, 1e-15, 40,
+                             want_A=False, dFinv=dFinv, dJ=dJ)
+        assert (o["status"] == 0).all()
+        outs.append(o["dPdmu"])
+    rot = np.einsum("ij,bjkp->bikp", R, outs[0])
+    err = np.abs(outs[1] - rot).max() / np.abs(rot).max()
+    print("objectivity of dPbar/dmu: %.2e" % err)
+    assert err <= 1e-8
