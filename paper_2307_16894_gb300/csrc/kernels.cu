@@ -1000,7 +1000,7 @@ __device__ void schur_abar(const Model &M, const Batch &Bt, int64_t b, const dou
 }
 
 template <int D, typename TT>
-__global__ void __launch_bounds__(256, D == 3 ? 3 : 4) k_finalize(Model M, Batch Bt, StepOpts o, double *__restrict__ Pbar,
+__global__ void __launch_bounds__(256, 4) k_finalize(Model M, Batch Bt, StepOpts o, double *__restrict__ Pbar,
                                                   double *__restrict__ Abar, void *info_v, int CHF) {
     constexpr int D2 = D * D, D4 = D2 * D2;
     extern __shared__ __align__(16) unsigned char smem[];
