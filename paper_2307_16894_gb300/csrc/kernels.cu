@@ -621,11 +621,26 @@ __device__ bool newton_direction(const Batch &Bt, int64_t b, int n, int precisio
         }
         if (ok) return true;
         __syncthreads();
+        // FP64 fallback (rare): the shared-memory region holds only the FP32 factor, so the LU runs
+        // in place on K in global memory (K is assembled anew before the next solve, and the K of a
+        // converged instance is never factored here)
+        double *Kg = Bt.K + (size_t)b * n * n;
+        for (int j = tid; j < n; j += nt) x[j] = -r[j];
+        __syncthreads();
+        return block_lu_solve<double>(Kg, n, n, x, n, 1, s_piv);
     }
     for (int e = tid; e < n * n; e += nt) A[(e / n) * lda + e % n] = Kb[e];
     for (int j = tid; j < n; j += nt) x[j] = -r[j];
     __syncthreads();
     return block_lu_solve<double>(A, n, lda, x, n, 1, s_piv);
+}
+
+// shared memory of k_solve: the LU region (FP32 factor with its right-hand side and pivots on the
+// mixed paths with n >= 16, else the FP64 matrix), then x [n] doubles and the pivot scratch
+__host__ __device__ inline size_t solve_region_bytes(int n, int precision) {
+    const size_t f32 = ((size_t)n * (n + 1) + 2 * (size_t)n) * 4;
+    const size_t f64 = (size_t)n * (n + 1) * 8;
+    return ((precision >= 1 && n >= 16) ? ((f32 + 7) & ~(size_t)7) : f64);
 }
 
 constexpr int ESC_ITERS = 4;
@@ -646,7 +661,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve(Model M, Batch Bt, Step
     const int64_t b = Bt.list[p];
     const int n = M.n, tid = threadIdx.x, nt = blockDim.x;
     double *A = reinterpret_cast<double *>(smem);
-    double *x = A + (size_t)n * (n + 1);
+    double *x = reinterpret_cast<double *>(smem + solve_region_bytes(n, o.precision));
     const double *r = Bt.r + b * n;
     if (tid < 32) {   // residual norm: lane-strided partial sums, then a butterfly over the warp
         double s = 0.0;
@@ -674,8 +689,12 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve(Model M, Batch Bt, Step
         // at most the previous-step predictor's residual of the last step that evaluated one) or
         // also evaluate the previous-step predictor a_n + (a_n - a_{n-1}) and keep the better start
         c.r0 = rn;
-        const bool ok = isfinite(rn) && newton_direction(Bt, b, n, o.precision, A, x, &s_piv, red);
         const double rref = Bt.r0_prev ? Bt.r0_prev[b] : INFINITY;
+        // an instance that the learned start already converges needs no direction (and its K, the
+        // K at the solution, must not be factored in place by the solve's FP64 fallback)
+        const bool done = isfinite(rn) && isfinite(rref) && rn <= rref &&
+                          (rn <= fmax(o.tol_rel * rref, o.tol_abs) || o.max_iter == 0);
+        const bool ok = done || (isfinite(rn) && newton_direction(Bt, b, n, o.precision, A, x, &s_piv, red));
         if (ok && isfinite(rref) && rn <= rref) {
             c.tol = fmax(o.tol_rel * rref, o.tol_abs);
             c.rn_acc = rn;
@@ -1275,7 +1294,7 @@ static int launch_kernels_t(int which, const Model &M, Batch Bt, const StepOpts 
         return -1;
     }
     if (which == 3) {
-        const size_t sms = (size_t)M.n * (M.n + 1) * 8 + (size_t)M.n * 8 + (size_t)M.n * 4 + 16;
+        const size_t sms = solve_region_bytes(M.n, o.precision) + (size_t)M.n * 8 + (size_t)M.n * 4 + 16;
         cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sms);
         // n <= 32: one warp per instance (its block barriers cost next to nothing and twice as many
         // instances are resident per SM); the arithmetic and its order do not depend on the width
