@@ -917,12 +917,12 @@ static int launch_tc4(const Model &M, Batch Bt, const unsigned char *img, int *e
     return 0;
 }
 
-// mode 1 BF16, 2 TF32 (Y on the CUDA cores), 3 TF32 split (FP32-accurate), 4 TF32 with Y on the
-// tensor cores; sel 0 = all listed instances, 1 = those without, 2 = those with the
+// mode 1 BF16, 3 TF32 split (FP32-accurate), 4 TF32 with Y on the tensor cores (k_assemble_tc4;
+// it supersedes the TF32 variant of k_assemble_tc3 with Y on the CUDA cores, MODE 2, which is
+// not instantiated); sel 0 = all listed instances, 1 = those without, 2 = those with the
 // accurate-stiffness flag (Ctl::acc_k)
 int launch_tc3(int mode, const Model &M, Batch Bt, const unsigned char *img, int *err, int sel, cudaStream_t s) {
     return mode == 1 ? launch_tc3_t<1>(M, Bt, img, err, sel, s)
-         : mode == 2 ? launch_tc3_t<2>(M, Bt, img, err, sel, s)
          : mode == 3 ? launch_tc3_t<3>(M, Bt, img, err, sel, s)
          : mode == 4 ? launch_tc4(M, Bt, img, err, sel, s) : -1;
 }
