@@ -115,7 +115,8 @@ class BeamMesh:
         P = P.reshape(self.ne, 4, 2, 2)
         A = A.reshape(self.ne, 4, 2, 2, 2, 2)
         fe = np.einsum("eq,eqij,eqaj->eai", self.wdet, P, self.dNdX).reshape(self.ne, 16)
-        Ke = np.einsum("eq,eqaj,eqijkl,eqbl->eaibk", self.wdet, self.dNdX, A, self.dNdX).reshape(self.ne, 16, 16)
+        AB = np.einsum("eqijkl,eqbl->eqijbk", A, self.dNdX)                       # A : grad N_b
+        Ke = np.einsum("eq,eqaj,eqijbk->eaibk", self.wdet, self.dNdX, AB, optimize=True).reshape(self.ne, 16, 16)
         f = np.zeros(2 * self.nn)
         np.add.at(f, self.dofs, fe)
         K = sp.coo_matrix((Ke.ravel(), (self.rows, self.cols)), shape=(2 * self.nn, 2 * self.nn)).tocsr()
