@@ -1,0 +1,39 @@
+"""The benchmark's per-kernel roofline arithmetic (host logic, no GPU): achieved = algorithmic
+FLOPs / time, frac = achieved / peak, the unit that bounds each kernel group, and the traffic
+from the measured DRAM bytes per point."""
+import importlib.util
+import os
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_rooflines_c3_tf32(bench):
+    # one second of each group, with known FLOP counts
+    kin = 2.0 * 600 * 9 * 64
+    points = 1.0e6
+    prof = {"start": (0.0, 1, 0.0), "constitutive": (1000.0, 10, points / 600 * kin),
+            "assemble": (1000.0, 10, 2.0e14), "solve": (1000.0, 10, 1.0e12), "finalize": (0.0, 1, 0.0),
+            "bookkeeping": (0.0, 1, 0.0), "learned_start": (0.0, 0, 0.0), "force": (1000.0, 10, 3.0e12),
+            "sensitivity": (0.0, 0, 0.0)}
+    r = dict(workload="c3", prof=prof, prec="tf32", fp64_residual=False)
+    out = bench.kernel_rooflines(r, {"bf16_tflops": 2000.0})
+    c = out["constitutive"]
+    assert c["bound"] == "alu" and abs(c["achieved"] - points * 1590.0 / 1e12) < 1e-9
+    assert abs(c["frac"] - c["achieved"] / bench.FP64_PEAK_TFLOPS) < 1e-12
+    assert abs(c["traffic"] - points / 10 * 950.5) < 1e-3          # bytes per launch
+    a = out["assemble"]
+    assert a["bound"] == "tensor" and abs(a["peak"] - 1000.0) < 1e-9 and abs(a["achieved"] - 200.0) < 1e-9
+    f = out["force"]
+    assert abs(f["peak"] - bench.FP32_PEAK_TFLOPS / 12) < 1e-12 and abs(f["achieved"] - 3.0) < 1e-9
+    r["fp64_residual"] = True
+    assert abs(bench.kernel_rooflines(r, {})["force"]["peak"] - bench.FP64_PEAK_TFLOPS) < 1e-12

@@ -102,3 +102,17 @@ def test_fe2_gpu_vs_oracle(prec, tol):
     assert u_err <= tol and tip_err <= tol
     if prec == "fp64":
         assert out["macro_its"] == ref["macro_its"]
+
+
+def test_q8_shape_functions():
+    """partition of unity, nodal interpolation and derivatives vs central differences"""
+    for xi, eta in [(0.3, -0.7), (-0.2, 0.9), (0.0, 0.0)]:
+        N, dN = fe2.q8_shape(xi, eta)
+        assert abs(N.sum() - 1.0) <= 1e-14 and np.abs(dN.sum(0)).max() <= 1e-14
+        h = 1e-6
+        fd = np.stack([(fe2.q8_shape(xi + h, eta)[0] - fe2.q8_shape(xi - h, eta)[0]) / (2 * h),
+                       (fe2.q8_shape(xi, eta + h)[0] - fe2.q8_shape(xi, eta - h)[0]) / (2 * h)], 1)
+        assert np.abs(fd - dN).max() <= 1e-8
+    for a, (xa, ea) in enumerate(fe2.Q8_XI):
+        N, _ = fe2.q8_shape(xa, ea)
+        assert np.abs(N - np.eye(8)[a]).max() <= 1e-14

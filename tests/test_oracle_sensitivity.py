@@ -93,3 +93,19 @@ def test_sensitivity_objectivity_2d():
     err = np.abs(outs[1] - rot).max() / np.abs(rot).max()
     print("objectivity of dPbar/dmu: %.2e" % err)
     assert err <= 1e-8
+
+
+def test_geometry_derivatives_fd():
+    """dF_mu^-1/dmu and d|det F_mu|/dmu of the affine map vs central differences in mu."""
+    rom, mu, coef, paths = workload.batch("c3" if os.path.exists(os.path.join(workload.DATA, "rom_c3.npz")) else "c2",
+                                          B=2)
+    Finv, J = geometry(rom, coef)
+    dFinv, dJ = oracle.geometry_derivatives(rom, Finv, J)
+    h = 1e-6
+    for k in range(coef.shape[1]):
+        e = np.zeros_like(coef)
+        e[:, k] = h
+        Fp_, Jp = geometry(rom, coef + e)
+        Fm_, Jm = geometry(rom, coef - e)
+        assert np.abs((Fp_ - Fm_) / (2 * h) - dFinv[:, :, k]).max() <= 1e-7 * np.abs(dFinv).max()
+        assert np.abs((Jp - Jm) / (2 * h) - dJ[:, :, k]).max() <= 1e-7 * np.abs(dJ).max()
