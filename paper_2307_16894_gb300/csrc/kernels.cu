@@ -1262,7 +1262,6 @@ static int launch_assemble(const Model &M, Batch Bt, const StepOpts &o, cudaStre
 template <int D>
 static int launch_kernels_t(int which, const Model &M, Batch Bt, const StepOpts &o, int32_t *list_next,
                             cudaStream_t s) {
-    constexpr int D2 = D * D;
     if (which == 1) {
         const int64_t nthr = Bt.B * (int64_t)M.m;
         const int blk = 128;
