@@ -1,7 +1,9 @@
 """Two-scale FE^2 driver with the reduced RVE model at every macro Gauss point (Sec. 4.2,
-first-order homogenisation of Sec. 2): a 2D plane-strain macro beam [0, L] x [0, H] of 8-node
-serendipity (Q8) elements with 2 x 2 Gauss points, clamped at X = 0 and loaded by a parabolic
-shear traction of resultant T at X = L, solved by Newton's method on the macro displacement.
+first-order homogenisation of Sec. 2): a 2D plane-strain macro structure [0, W] x [0, H]
+(W = 2, H = 1) of 8-node serendipity (Q8) elements with 2 x 2 Gauss points (20 x 10 elements:
+the 200 elements, 800 quadrature points and 1322 degrees of freedom of the paper's second
+example), supported on Y = 0 and compressed by the distributed load
+T(X) = Tbar (1 - (2 X / W - 1)^2) on Y = H, solved by Newton's method on the macro displacement.
 At every macro Gauss point the effective stress Pbar and stiffness Abar come from the reduced
 micro problem (one batched rom_step over all macro points per macro iteration, with a
 per-point geometry parameter mu(X)).  The micro history is committed only at macro
@@ -11,7 +13,7 @@ every macro iteration.
 The micro solver is an object with save(), restore() and step(F [B, d, d]) -> (Pbar [B, d, d],
 Abar [B, d*d, d*d], status [B]); RomMicro wraps a library context and state.
 
-usage: python -m paper_2307_16894_gb300.fe2 [--nx 20 --ny 10 --steps 50 --T 10 --precision fp32]
+usage: python -m paper_2307_16894_gb300.fe2 [--nx 20 --ny 10 --steps 50 --T 60 --precision fp32]
 """
 import argparse
 import json
@@ -46,7 +48,8 @@ def q8_shape(xi, eta):
 
 
 class BeamMesh:
-    """[0, L] x [0, H] in nx x ny rectangular Q8 elements; 2 x 2 Gauss points per element."""
+    """[0, L] x [0, H] in nx x ny rectangular Q8 elements; 2 x 2 Gauss points per element;
+    the edge Y = 0 is fixed, the edge Y = H carries the load."""
 
     def __init__(self, L=2.0, H=1.0, nx=20, ny=10):
         self.L, self.H, self.nx, self.ny = L, H, nx, ny
@@ -81,23 +84,24 @@ class BeamMesh:
                 self.Xq[e, q] = N @ xe
         self.nq = self.ne * 4
         self.ids = ids
-        # clamped edge X = 0; the right edge X = L carries the traction
+        # the edge Y = 0 is fixed; the edge Y = H carries t_y(X) = -(1 - (2 X / L - 1)^2) per unit
+        # Tbar (consistent nodal forces, 3-point Gauss rule per quadratic edge)
         self.fixed = np.zeros((self.nn, 2), bool)
-        self.fixed[ids[0, :][ids[0, :] >= 0]] = True
+        self.fixed[ids[:, 0][ids[:, 0] >= 0]] = True
         self.free = np.flatnonzero(~self.fixed.ravel())
-        # consistent nodal forces of t_y(Y) = -6 Y (H - Y) / H^3 (unit resultant) on X = L
         f = np.zeros((self.nn, 2))
         s3 = np.sqrt(0.6)
-        for ey in range(ny):
-            nodes = [ids[2 * nx, 2 * ey], ids[2 * nx, 2 * ey + 1], ids[2 * nx, 2 * ey + 2]]
-            y0 = ey * hy
+        for ex in range(nx):
+            nodes = [ids[2 * ex, 2 * ny], ids[2 * ex + 1, 2 * ny], ids[2 * ex + 2, 2 * ny]]
+            x0 = ex * hx
             for s, wg in ((-s3, 5 / 9), (0.0, 8 / 9), (s3, 5 / 9)):
                 Nl = [0.5 * s * (s - 1), 1 - s * s, 0.5 * s * (s + 1)]
-                y = y0 + (s + 1) * hy / 2
-                t = -6.0 * y * (H - y) / H ** 3
+                x = x0 + (s + 1) * hx / 2
+                t = -(1.0 - (2.0 * x / L - 1.0) ** 2)
                 for a in range(3):
-                    f[nodes[a], 1] += wg * hy / 2 * Nl[a] * t
+                    f[nodes[a], 1] += wg * hx / 2 * Nl[a] * t
         self.f_unit = f.ravel()
+        self.ndof = 2 * self.nn
         # sparsity of the element stiffness scatter
         dofs = (2 * self.conn[:, :, None] + np.arange(2)[None, None]).reshape(self.ne, 16)
         self.dofs = dofs
@@ -124,7 +128,7 @@ class BeamMesh:
 
 
 def solve(mesh, micro, T_max, nsteps, tol=1e-8, max_it=25, verbose=False):
-    """Load steps T_k = k T_max / nsteps; Newton on the free macro dofs until
+    """Load steps Tbar_k = k T_max / nsteps; Newton on the free macro dofs until
     ||f_int - f_ext|| <= tol ||f_ext||.  Returns the displacement history and statistics."""
     u = np.zeros(2 * mesh.nn)
     free = mesh.free
@@ -152,7 +156,7 @@ def solve(mesh, micro, T_max, nsteps, tol=1e-8, max_it=25, verbose=False):
             du = spla.spsolve(K[free][:, free].tocsc(), -R)
             u[free] += du
         out["u"].append(u.copy())
-        tip = mesh.ids[2 * mesh.nx, mesh.ny]            # mid-height node of the loaded end
+        tip = mesh.ids[mesh.nx, 2 * mesh.ny]            # mid-span node of the loaded edge
         out["tip"].append(u.reshape(-1, 2)[tip].copy())
         out["compliance"].append(float(fext @ u))
         out["macro_its"].append(it)
@@ -205,7 +209,7 @@ def main():
     ap.add_argument("--nx", type=int, default=20)
     ap.add_argument("--ny", type=int, default=10)
     ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--T", type=float, default=10.0)
+    ap.add_argument("--T", type=float, default=60.0)
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "tf32", "bf16"])
     ap.add_argument("--model", default="c2")
     args = ap.parse_args()

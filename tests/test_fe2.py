@@ -2,11 +2,16 @@
 passes the patch test, the traction has the prescribed resultant, and with the FP64 oracle as
 the micro solver the macro Newton converges quadratically; on the GPU (gpu-marked test) the
 library's micro solver reproduces the oracle-driven two-scale solution."""
+import json
+import os
+
 import numpy as np
 import pytest
 
 import oracle
 from paper_2307_16894_gb300 import fe2, inputs, workload
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
 class OracleMicro:
@@ -35,9 +40,19 @@ class OracleMicro:
         return o["Pbar"], o["Abar"], o["status"]
 
 
+def test_paper_example2_mesh():
+    """the macro mesh of the paper's second example: 200 Q8 elements, 800 quadrature points,
+    1322 degrees of freedom on a W x H = 2 x 1 structure (tests/golden/paper_example2_macro.json)"""
+    g = json.load(open(os.path.join(GOLDEN, "paper_example2_macro.json")))
+    m = fe2.BeamMesh(L=g["W"], H=g["H"], nx=20, ny=10)
+    assert (m.ne, m.nq, m.ndof) == (g["elements"], g["quadrature_points"], g["dofs"])
+    # resultant of T(x) = Tbar (1 - (2x/W - 1)^2) per unit Tbar: 2 W / 3, compressive
+    assert np.allclose(m.f_unit.reshape(-1, 2).sum(0), [0.0, -2.0 * g["W"] / 3.0], atol=1e-13)
+
+
 def test_patch_and_traction():
     m = fe2.BeamMesh(nx=4, ny=2)
-    assert np.allclose(m.f_unit.reshape(-1, 2).sum(0), [0.0, -1.0], atol=1e-14)
+    assert np.allclose(m.f_unit.reshape(-1, 2).sum(0), [0.0, -4.0 / 3.0], atol=1e-14)
     lam, G = 1.0, 0.5
     A = np.zeros((2, 2, 2, 2))
     for i, j, k, l in np.ndindex(2, 2, 2, 2):
@@ -53,8 +68,8 @@ def test_patch_and_traction():
 
 
 def test_fe2_oracle_quadratic_convergence():
-    """2 x 1 macro elements (8 macro points) on the 2D porous RVE model, loaded into the plastic
-    range in 4 steps; within every step the macro residual contracts quadratically (the
+    """2 x 1 macro elements (8 macro points) on the 2D porous RVE model, compressed into the
+    plastic range in 4 steps; within every step the macro residual contracts quadratically (the
     consistent effective stiffness Abar of the micro problem)."""
     rom = workload.load_model(workload.WORKLOADS["c2"]["model"])
     mesh = fe2.BeamMesh(nx=2, ny=1)
@@ -62,7 +77,7 @@ def test_fe2_oracle_quadratic_convergence():
     micro = OracleMicro(rom, coef)
     u = np.zeros(2 * mesh.nn)
     for k in range(1, 5):
-        fext = 8.0 * k / 4 * mesh.f_unit
+        fext = 80.0 * k / 4 * mesh.f_unit
         micro.save()
         res = []
         for it in range(10):
@@ -92,9 +107,9 @@ def test_fe2_gpu_vs_oracle(prec, tol):
     rom = workload.load_model(workload.WORKLOADS["c2"]["model"])
     mesh = fe2.BeamMesh(nx=4, ny=2)
     coef = inputs.map_coefficients(2, fe2.beam_mu(mesh))
-    ref = fe2.solve(mesh, OracleMicro(rom, coef), 10.0, 5)
+    ref = fe2.solve(mesh, OracleMicro(rom, coef), 80.0, 5)
     gm = fe2.RomMicro(rom, coef, prec)
-    out = fe2.solve(mesh, gm, 10.0, 5)
+    out = fe2.solve(mesh, gm, 80.0, 5)
     gm.close()
     tip_err = np.abs(np.array(out["tip"]) - np.array(ref["tip"])).max() / np.abs(np.array(ref["tip"])).max()
     u_err = np.abs(out["u"][-1] - ref["u"][-1]).max() / np.abs(ref["u"][-1]).max()

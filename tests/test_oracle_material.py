@@ -1,13 +1,19 @@
 """Pins of the oracle's material point (Appendix A of arXiv 2307.16894) against
 facts fixed by the mathematics: closed forms, textbook special cases,
 invariants, finite differences."""
+import json
+import os
+
 import numpy as np
 import pytest
 
 import oracle
 
 MAT = dict(E=70e3, nu=0.3, law="power", s0=100.0, k=10.0, p=0.2)
-LIN = dict(E=10.0, nu=0.3, law="linear", s0=0.2, k=5.0, p=1.0)       # Sec. 4.1 matrix: E=10, nu=0.3, sy0=0.2, H=5
+# the matrix material of the paper's first example (tests/golden/paper_example1_material.json)
+_EX1 = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                   "paper_example1_material.json")))["matrix"]
+LIN = dict(E=_EX1["E"], nu=_EX1["nu"], law="linear", s0=_EX1["sigma_y0"], k=_EX1["H"], p=1.0)
 ELAST = dict(E=700e3, nu=0.3, law="power", s0=np.inf, k=0.0, p=1.0)
 
 
