@@ -13,7 +13,7 @@ every macro iteration.
 The micro solver is an object with save(), restore() and step(F [B, d, d]) -> (Pbar [B, d, d],
 Abar [B, d*d, d*d], status [B]); RomMicro wraps a library context and state.
 
-usage: python -m paper_2307_16894_gb300.fe2 [--nx 20 --ny 10 --steps 50 --T 60 --precision fp32]
+usage: python -m paper_2307_16894_gb300.fe2 [--nx 20 --ny 10 --steps 50 --T 80 --precision fp32]
 """
 import argparse
 import json
@@ -209,7 +209,7 @@ def main():
     ap.add_argument("--nx", type=int, default=20)
     ap.add_argument("--ny", type=int, default=10)
     ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--T", type=float, default=60.0)
+    ap.add_argument("--T", type=float, default=80.0)
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "tf32", "bf16"])
     ap.add_argument("--model", default="c2")
     args = ap.parse_args()
