@@ -1,7 +1,7 @@
 """ORACLE — test infrastructure only.
 
-Plain FP64 reference of the learned Newton-start network (a north-star
-extension; the paper is silent on the Newton predictor): a multilayer
+Plain FP64 reference of the learned Newton-start network (an addition to
+the method; the paper is silent on the Newton predictor): a multilayer
 perceptron with exact-erf GELU, inputs standardised by (x - x_mean)/x_std,
 trained on the mean squared error of standardised targets (y - y_mean)/y_std.
 Parameters are packed per linear map as W[out][in] row-major then b[out].
