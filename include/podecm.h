@@ -133,7 +133,7 @@ rom_status rom_load_basis(rom_ctx *ctx, int n, int m, const double *G);
 rom_status rom_load_cubature(rom_ctx *ctx, int m, const double *w, const int32_t *phase, int n_phase,
                              const rom_phase *phases, double omega_vol);
 
-/* Geometry (Sec. 2.1, Eq. weakform-dep-mapped; the online line 1 of Algorithm 1):
+/* Geometry (Sec. 2.1, Eq. weakform-dep-mapped; the geometry step that opens the online stage of Algorithm 1):
  * F_mu,i = I + sum_k mu[b][k] Gmu[i][a*d+r][k] at every point i of instance b.
  * Gmu[m][d*d][n_par] and mu[B][n_par] on the host, copied.  Fails with ROM_E_ARG
  * if any det F_mu <= 0.  1 <= n_par <= 4. */
@@ -151,7 +151,7 @@ rom_status rom_state_destroy(rom_state *st);
 rom_status rom_state_export(rom_ctx *ctx, const rom_state *st, double *a, double *Cpinv, double *xi);
 rom_status rom_state_import(rom_ctx *ctx, rom_state *st, const double *a, const double *Cpinv, const double *xi);
 
-/* One load step for all B instances (Algorithm 1 online lines 2-5).
+/* One load step for all B instances (the online Newton loop of Algorithm 1).
  * Fbar[B][d*d] in; Pbar[B][d*d] out; Abar[B][d^4] out (may be NULL if
  * opts->want_abar == 0); info[B] out (may be NULL).  Host buffers; the call
  * copies in, runs, copies out and synchronises.  Converged instances commit

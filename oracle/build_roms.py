@@ -1,4 +1,4 @@
-"""ORACLE — offline ROM construction (Algorithm 1 offline, lines 1-6).
+"""ORACLE — offline ROM construction (the offline stage of Algorithm 1).
 
 Writes data/rom_<name>.npz for the synthetic workloads: seeded training load
 paths -> full-order FE solves on the parent mesh (Sec. 2) -> POD of the
@@ -105,7 +105,7 @@ def build(name, verbose=True, nthreads=None):
 
 
 def _train_path(name, kind, seed, nst, nthreads, verbose):
-    """One seeded full-order training solve (Algorithm 1 offline lines 2-4)."""
+    """One seeded full-order training solve (the training solves of the offline stage of Algorithm 1)."""
     for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[var] = "1"
     cfg = CONFIGS[name]

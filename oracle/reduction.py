@@ -1,7 +1,7 @@
 """ORACLE — test infrastructure only.
 
-Offline reduction of arXiv 2307.16894 (Sec. 3.1-3.2, Algorithm 1 offline
-lines 4-6): POD of the fluctuation snapshots in the V^p inner product, POD of
+Offline reduction of arXiv 2307.16894 (Sec. 3.1-3.2, the reduction steps of
+the offline stage of Algorithm 1): POD of the fluctuation snapshots in the V^p inner product, POD of
 the weighted-stress snapshots W = P F_mu^-T |det F_mu| in L^2(Omega^p), and
 the empirical cubature (ECM) greedy that picks Gauss points and positive
 weights integrating the N*L products dphi_i/dX^p : B_l (Eq. integral_ecm).

@@ -1,5 +1,5 @@
 // CUDA kernels of one hyper-reduced load step (arXiv 2307.16894, Sec. 3.2-3.3,
-// Algorithm 1 online lines 2-5), batched over independent instances.
+// the online Newton loop of Algorithm 1), batched over independent instances.
 //
 // One Newton "pass" over the active instances is three launches:
 //   k_constitutive : one thread per (instance, cubature point): geometry (F_mu),
