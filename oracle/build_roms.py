@@ -47,6 +47,13 @@ CONFIGS = {
     "c3": dict(d=3, N=24, n=96, n_use=64, m=600, L=20, map_seed=11, phases=[MATRIX, INCLUSION],
                train=[("stretch", 3001 + i, 20) for i in range(8)], mu_range=(0.15, 0.35),
                fft_pcg=True, tol_rel=1e-9, parallel=True),
+    # the two-scale accuracy family (second example of Sec. 4.2, its sampling scheme): 2D 32x32 Q4, same
+    # void; N_train = 20 Sobol samples of (Uxx, Uyy, Uxy, mu), each applied with the 40-step load-unload
+    # amplitude; 40 POD modes kept, L = 20, ECM to integration error epsilon = 0.01.  The stretch ranges
+    # cover the macro states of the compressed structure (|Ubar - I| of order 1e-2).
+    "e2": dict(d=2, N=32, n=40, m=None, ecm_tol=0.01, L=20, map_seed=7, phases=[MATRIX],
+               train=[("sobol", i, 40) for i in range(20)], mu_range=(0.2, 0.35), parallel=True,
+               sobol=dict(n=20, seed=2307, ranges=[(0.995, 1.005), (0.98, 1.0), (-0.005, 0.005), (0.2, 0.35)])),
 }
 
 
@@ -87,9 +94,9 @@ def build(name, verbose=True, nthreads=None):
     n_use = cfg.get("n_use", n)
     Fint = reduction.ecm_integrands(gradPhi[..., :n_use], Bm)
     t1 = time.time()
-    sel, wsel, err = reduction.ecm_greedy(Fint, wq, m)
+    sel, wsel, err = reduction.ecm_greedy(Fint, wq, m, tol=cfg.get("ecm_tol"))
     if verbose:
-        print("[%s] ECM m=%d err=%.3e (%.1fs); sum w=%.6f vs %.6f" % (name, m, err, time.time() - t1,
+        print("[%s] ECM m=%d err=%.3e (%.1fs); sum w=%.6f vs %.6f" % (name, len(sel), err, time.time() - t1,
                                                                      wsel.sum(), wq.sum()), flush=True)
     rom = pack(mesh, cfg, modes, Gq, gradPhi, sel, wsel, err, n_use)
     rom.update(dict(lam_w=lam_w[:n], lam_W=lam_W[:L], n_snap=len(snaps_w)))
@@ -114,13 +121,18 @@ def _train_path(name, kind, seed, nst, nthreads, verbose):
     npar = 1 if d == 2 else 3
     modes = inputs.map_modes(d, npar, cfg["map_seed"])
     Gq = inputs.map_gradients(modes, mesh.X.reshape(-1, d))
-    rng = np.random.default_rng(seed)
-    mu = rng.uniform(*cfg["mu_range"], size=npar)
-    Finv, J = fe.geometry(Gq, inputs.map_coefficients(d, mu))
-    if kind == "u2d":
-        path = inputs.training_path_2d(seed, nst)
+    if kind == "sobol":
+        sc = cfg["sobol"]
+        smp = inputs.sobol_samples(sc["n"], sc["ranges"], sc["seed"])[seed]      # (Uxx, Uyy, Uxy, mu)
+        mu = smp[3:4]
+        path = inputs.load_unload_path(np.array([[smp[0], smp[2]], [smp[2], smp[1]]]), nst)
     else:
-        path = inputs.stretch_path(d, seed, nst, rotate=False)
+        mu = np.random.default_rng(seed).uniform(*cfg["mu_range"], size=npar)
+        if kind == "u2d":
+            path = inputs.training_path_2d(seed, nst)
+        else:
+            path = inputs.stretch_path(d, seed, nst, rotate=False)
+    Finv, J = fe.geometry(Gq, inputs.map_coefficients(d, mu))
     precond = fe.FFTPreconditioner(mesh, cfg["phases"][0]["E"], cfg["phases"][0]["nu"]) if cfg.get("fft_pcg") else None
     t1 = time.time()
     out = fe.solve_path(mesh, cfg["phases"], Finv, J, path, nthreads=nthreads, verbose=verbose,
@@ -150,6 +162,9 @@ def pack(mesh, cfg, modes, Gq, gradPhi, sel, wsel, err, n_use):
 VARIANTS = {
     "r2_n16_m100": ("c2", 16, 100), "r2_n24_m150": ("c2", 24, 150), "r2_n32_m200": ("c2", 32, 200),
     "r3_n48_m400": ("c3", 48, 400), "r3_n64_m650": ("c3", 64, 650), "r3_n95_m900": ("c3", 95, 900),
+    # two-scale accuracy family: N = 5 .. 40 modes, ECM to epsilon = 0.01 (m = None: set by the error bound)
+    # (the base model rom_e2 itself has N = 40)
+    "e2_n5": ("e2", 5, None), "e2_n10": ("e2", 10, None), "e2_n20": ("e2", 20, None), "e2_n30": ("e2", 30, None),
 }
 
 
@@ -164,9 +179,9 @@ def build_variant(name, verbose=True):
     mesh = fe.Mesh(d, cfg["N"], phase_2d if d == 2 else phase_3d)
     t1 = time.time()
     Fint = reduction.ecm_integrands(gradPhi[..., :n], Bm)
-    sel, wsel, err = reduction.ecm_greedy(Fint, wq, m)
+    sel, wsel, err = reduction.ecm_greedy(Fint, wq, m, tol=cfg.get("ecm_tol"))
     if verbose:
-        print("[%s] ECM m=%d err=%.3e (%.1fs)" % (name, m, err, time.time() - t1), flush=True)
+        print("[%s] ECM m=%d err=%.3e (%.1fs)" % (name, len(sel), err, time.time() - t1), flush=True)
     modes = inputs.map_modes(d, 1 if d == 2 else 3, cfg["map_seed"])
     rom = pack(mesh, cfg, modes, z["Gq"], gradPhi, sel, wsel, err, n)
     np.savez_compressed(os.path.join(DATA, "rom_%s.npz" % name), **rom)

@@ -14,6 +14,7 @@ are removed; nodes used only by removed elements carry no unknowns; one node
 is fixed to remove the rigid translation of the periodic field.
 """
 import itertools
+import os
 
 import numpy as np
 import scipy.sparse as sp
@@ -293,3 +294,70 @@ def effective_stiffness(mesh, K, Aq, Finv, J):
         dF[:, :, kl] += 1.0
         Abar[:, kl] = np.einsum("eg,egij,egj->i", wJ, A, dF)
     return Abar
+
+
+class FullMicro:
+    """Full-order micro problems at B macro points: the reference model of the two-scale
+    comparison of Sec. 4.2 (the "full FE^2" solution).  Every point has its own geometry
+    (F_mu^-1 and J at all Gauss points, from its mu), fluctuation field w and history
+    (F^p, xi).  step(F) solves Eq. full_newton at every point from its current state and
+    returns the effective stress (Eq. eff_stress_full) and stiffness (Eqs. tangentproblem,
+    eff_stiffness_full, with the tangent at the converged fluctuation); the converged
+    fluctuation and the trial history become the point's state.  save()/restore() bracket
+    the macro iterations of a load step, as for the reduced model, so the history is
+    committed only at macro convergence.
+
+    Finv: [B, nq, d, d], J: [B, nq] (fe.geometry per point); omega: |Omega^p|."""
+
+    def __init__(self, mesh, phases, Finv, J, omega=1.0, tol_rel=1e-10, tol_abs=1e-9, max_iter=40,
+                 nthreads=None):
+        self.mesh, self.phases = mesh, phases
+        self.Finv, self.J, self.omega = Finv, J, omega
+        B = len(J)
+        self.w = np.zeros((B, mesh.ndof))
+        self.Fp = np.tile(np.eye(3).ravel(), (B, mesh.nq, 1))
+        self.xi = np.zeros((B, mesh.nq))
+        self.tol_rel, self.tol_abs, self.max_iter, self.nthreads = tol_rel, tol_abs, max_iter, nthreads
+        self.saved = None
+        self.newton_iters = 0
+
+    def save(self):
+        self.saved = (self.w.copy(), self.Fp.copy(), self.xi.copy())
+
+    def restore(self):
+        self.w[:], self.Fp[:], self.xi[:] = self.saved
+
+    def _point(self, b, F):
+        mesh, d = self.mesh, self.mesh.d
+        sol = _newton(mesh, self.phases, self.Finv[b], self.J[b], F, self.w[b], self.Fp[b], self.xi[b],
+                      self.tol_rel, self.tol_abs, self.max_iter, 1)
+        if sol is None:
+            return None
+        w, res, it = sol
+        if res["Ke"] is None:
+            res = fe_elements(mesh, self.phases, self.Finv[b], self.J[b], F, w, self.Fp[b], self.xi[b],
+                              want_K=True, nthreads=1)
+        K = mesh.assemble_mat(res["Ke"])
+        Abar = effective_stiffness(mesh, K, res["Aq"], self.Finv[b], self.J[b])
+        gwq = np.tile(mesh.gw, mesh.ne)
+        Pbar = np.einsum("q,q,qab->ab", gwq, self.J[b], res["Pq"].reshape(mesh.nq, d, d)) / self.omega
+        return Pbar, Abar, w, res["Fp_tr"], res["xi_tr"], it
+
+    def step(self, F):
+        """The points are independent: they run on a thread pool (the element routines and
+        the sparse factorisations run outside the interpreter lock), one thread per point."""
+        from concurrent.futures import ThreadPoolExecutor
+        d = self.mesh.d
+        B = len(F)
+        Pbar = np.zeros((B, d, d))
+        Abar = np.zeros((B, d * d, d * d))
+        status = np.zeros(B, np.int32)
+        with ThreadPoolExecutor(self.nthreads or os.cpu_count() or 1) as ex:
+            results = list(ex.map(lambda b: self._point(b, F[b]), range(B)))
+        for b, r in enumerate(results):
+            if r is None:
+                status[b] = 1
+                continue
+            Pbar[b], Abar[b], self.w[b], self.Fp[b], self.xi[b], it = r
+            self.newton_iters += it
+        return Pbar, Abar, status

@@ -68,7 +68,7 @@ def ecm_integrands(gradPhi, Bmodes):
     return np.einsum("qabi,lqab->ilq", gradPhi, Bmodes).reshape(n * L, -1)
 
 
-def ecm_greedy(Fint, wq, m, volume_weight=10.0):
+def ecm_greedy(Fint, wq, m=None, volume_weight=10.0, tol=None):
     """Empirical cubature (after Hernandez et al. 2017): greedy choice of Gauss points
     with positive weights so that sum_sel w f ~= sum_all wq f for every integrand row of
     Fint [P, M] and for the constant (volume) integrand.
@@ -80,7 +80,8 @@ def ecm_greedy(Fint, wq, m, volume_weight=10.0):
     volume_weight) is appended.  At each step the candidate most aligned with the
     current integration residual is added and the weights are refit by non-negative
     least squares (points that fall to zero weight leave the set); the loop runs until
-    m points are selected (the configurations fix m).
+    m points are selected, or (m None) until the integration error below is <= tol, the
+    error bound epsilon of the ECM (Sec. 3.2).
 
     Returns (idx, w, err) with err = ||Z_sel w - Z wq|| / ||Z wq|| in the orthonormal
     basis (every basis function has unit L^2 norm, so this is the RMS integration error
@@ -97,8 +98,12 @@ def ecm_greedy(Fint, wq, m, volume_weight=10.0):
     sel = []
     wsel = np.zeros(0)
     r = bx.copy()
+    if m is None and tol is None:
+        raise ValueError("ecm_greedy needs m or tol")
+    nb = np.linalg.norm(bx)
+    limit = 20 * (m if m is not None else Mq)
     guard = 0
-    while len(sel) < m and guard < 20 * m:
+    while (len(sel) < m if m is not None else np.linalg.norm(r) > tol * nb) and guard < limit:
         guard += 1
         c = (Zx.T @ r) / colnorm
         c[sel] = -np.inf
@@ -109,7 +114,9 @@ def ecm_greedy(Fint, wq, m, volume_weight=10.0):
         sel = [p for p, kp in zip(cand, keep) if kp]
         wsel = wn[keep]
         r = bx - Zx[:, sel] @ wsel
-    if len(sel) != m:
+    err = np.linalg.norm(r) / nb
+    if m is not None and len(sel) != m:
         raise RuntimeError("ECM greedy stalled at %d of %d points" % (len(sel), m))
-    err = np.linalg.norm(r) / np.linalg.norm(bx)
+    if m is None and err > tol:
+        raise RuntimeError("ECM greedy stalled at error %.3e > %.3e with %d points" % (err, tol, len(sel)))
     return np.array(sel), wsel, err

@@ -3,7 +3,9 @@ first-order homogenisation of Sec. 2): a 2D plane-strain macro structure [0, W] 
 (W = 2, H = 1) of 8-node serendipity (Q8) elements with 2 x 2 Gauss points (20 x 10 elements:
 the 200 elements, 800 quadrature points and 1322 degrees of freedom of the paper's second
 example), supported on Y = 0 and compressed by the distributed load
-T(X) = Tbar (1 - (2 X / W - 1)^2) on Y = H, solved by Newton's method on the macro displacement.
+T(X) = Tbar (1 - (2 X / W - 1)^2) on Y = H (Tbar ramped up, and optionally back down to zero
+as in the paper's loading program), solved by Newton's method on the macro displacement; the
+compliance C = int_Gamma T u_y dx of every load step is the paper's accuracy measure.
 At every macro Gauss point the effective stress Pbar and stiffness Abar come from the reduced
 micro problem (one batched rom_step over all macro points per macro iteration, with a
 per-point geometry parameter mu(X)).  The micro history is committed only at macro
@@ -13,7 +15,7 @@ every macro iteration.
 The micro solver is an object with save(), restore() and step(F [B, d, d]) -> (Pbar [B, d, d],
 Abar [B, d*d, d*d], status [B]); RomMicro wraps a library context and state.
 
-usage: python -m paper_2307_16894_gb300.fe2 [--nx 20 --ny 10 --steps 50 --T 80 --precision fp32]
+usage: python -m paper_2307_16894_gb300.fe2 [--nx 20 --ny 10 --steps 50 --T 80 --precision fp32 --unload]
 """
 import argparse
 import json
@@ -127,15 +129,30 @@ class BeamMesh:
         return f, K
 
 
-def solve(mesh, micro, T_max, nsteps, tol=1e-8, max_it=25, verbose=False):
-    """Load steps Tbar_k = k T_max / nsteps; Newton on the free macro dofs until
-    ||f_int - f_ext|| <= tol ||f_ext||.  Returns the displacement history and statistics."""
+def load_levels(T_max, nsteps, unload=False):
+    """Tbar at every load step: a linear ramp from 0 to T_max over nsteps, or (unload) the
+    loading program of the paper's second example (Sec. 4.2): up to T_max over the first
+    half of the steps, back down to 0 over the second half."""
+    k = np.arange(1, nsteps + 1)
+    if not unload:
+        return T_max * k / nsteps
+    h = nsteps // 2
+    return T_max * np.where(k <= h, k / h, (nsteps - k) / max(nsteps - h, 1))
+
+
+def solve(mesh, micro, T_max, nsteps, unload=False, tol=1e-8, max_it=25, verbose=False):
+    """Load steps Tbar_k from load_levels(); Newton on the free macro dofs until
+    ||f_int - f_ext|| <= tol max_{j <= k} ||f_ext,j|| (the largest load applied so far, so
+    that steps back at zero load have a scale).  Returns the displacement history, the
+    compliance C_k = f_ext,k . u_k = int_Gamma T u_y dx of every load step (Sec. 4.2; exact
+    for the finite-element displacement with the consistent load vector) and statistics."""
     u = np.zeros(2 * mesh.nn)
     free = mesh.free
     out = dict(u=[], tip=[], compliance=[], macro_its=[], T=[])
-    for k in range(1, nsteps + 1):
-        T = T_max * k / nsteps
+    ref = 0.0
+    for k, T in enumerate(load_levels(T_max, nsteps, unload), start=1):
         fext = T * mesh.f_unit
+        ref = max(ref, np.linalg.norm(fext[free]))
         micro.save()
         for it in range(max_it + 1):
             F = mesh.deformation_gradients(u)
@@ -149,7 +166,7 @@ def solve(mesh, micro, T_max, nsteps, tol=1e-8, max_it=25, verbose=False):
             rn = np.linalg.norm(R)
             if verbose:
                 print("step %d it %d |R| %.3e" % (k, it, rn))
-            if rn <= tol * np.linalg.norm(fext[free]):
+            if rn <= tol * ref:
                 break
             if it == max_it:
                 raise RuntimeError("macro Newton did not converge at load step %d" % k)
@@ -160,8 +177,19 @@ def solve(mesh, micro, T_max, nsteps, tol=1e-8, max_it=25, verbose=False):
         out["tip"].append(u.reshape(-1, 2)[tip].copy())
         out["compliance"].append(float(fext @ u))
         out["macro_its"].append(it)
-        out["T"].append(T)
+        out["T"].append(float(T))
     return out
+
+
+def compliance_error(C, C_ref):
+    """Relative compliance error per load step, eps_C,k = |C_k - C_ref,k| / |C_ref,k|, and
+    its mean over the load steps (Sec. 4.2).  Steps with C_ref,k = 0 (no load applied: the
+    last step of the unloading program) have no relative error and are left out of the mean."""
+    C, C_ref = np.asarray(C, float), np.asarray(C_ref, float)
+    keep = C_ref != 0.0
+    eps = np.full(len(C), np.nan)
+    eps[keep] = np.abs(C[keep] - C_ref[keep]) / np.abs(C_ref[keep])
+    return eps, float(eps[keep].mean())
 
 
 class RomMicro:
@@ -210,6 +238,8 @@ def main():
     ap.add_argument("--ny", type=int, default=10)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--T", type=float, default=80.0)
+    ap.add_argument("--unload", action="store_true", help="load to T over the first half of the steps, "
+                    "unload to 0 over the second half (the paper's loading program)")
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "tf32", "bf16"])
     ap.add_argument("--model", default="c2")
     args = ap.parse_args()
@@ -219,9 +249,9 @@ def main():
     coef = inputs.map_coefficients(2, beam_mu(mesh))
     micro = RomMicro(rom, coef, args.precision)
     t0 = time.perf_counter()
-    out = solve(mesh, micro, args.T, args.steps)
+    out = solve(mesh, micro, args.T, args.steps, unload=args.unload)
     t = time.perf_counter() - t0
-    print(json.dumps(dict(macro_elements=mesh.ne, macro_points=mesh.nq, load_steps=args.steps,
+    print(json.dumps(dict(macro_elements=mesh.ne, macro_points=mesh.nq, load_steps=args.steps, unload=args.unload,
                           precision=args.precision, seconds=t, load_steps_per_s=args.steps / t,
                           micro_solves=micro.micro_solves, micro_solves_per_s=micro.micro_solves / t,
                           macro_iterations=int(sum(out["macro_its"])),

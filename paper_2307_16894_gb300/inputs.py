@@ -101,6 +101,30 @@ def training_path_2d(seed, n_steps, lo=0.9, hi=1.1, shear=0.1):
     return np.array([I + (k / n_steps) * (U - I) for k in range(1, n_steps + 1)])
 
 
+def sobol_samples(n, ranges, seed):
+    """n quasi-random points of the box prod_j [lo_j, hi_j] from a scrambled Sobol sequence
+    (seeded): the sampling of the training set of Sec. 4.2.  Returns [n, len(ranges)]."""
+    import warnings
+    from scipy.stats import qmc
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore")          # n need not be a power of two
+        z = qmc.Sobol(len(ranges), scramble=True, seed=seed).random(n)
+    lo = np.array([r[0] for r in ranges], float)
+    hi = np.array([r[1] for r in ranges], float)
+    return lo + z * (hi - lo)
+
+
+def load_unload_path(U, n_steps):
+    """A macro stretch Ubar applied with the piecewise-linear amplitude of Sec. 4.2: t rises
+    from 0 to 1 over the first half of the steps and falls back to 0 over the second half;
+    Fbar_k = I + t_k (Ubar - I), k = 1..n_steps."""
+    h = n_steps // 2
+    k = np.arange(1, n_steps + 1)
+    t = np.where(k <= h, k / h, (n_steps - k) / max(n_steps - h, 1))
+    I = np.eye(len(U))
+    return np.array([I + tk * (np.asarray(U) - I) for tk in t])
+
+
 def stretch_path(d, seed, n_steps, lo=0.9, hi=1.15, rotate=True):
     """Random principal stretches in [lo, hi]^d with random principal axes Q, and
     (if rotate) a random macro rotation Rbar; both ramped linearly over n_steps:
