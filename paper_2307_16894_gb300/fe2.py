@@ -86,6 +86,12 @@ class BeamMesh:
                 self.Xq[e, q] = N @ xe
         self.nq = self.ne * 4
         self.ids = ids
+        # gradient operator: vec(grad u)[2 i + j] = sum_(a, i') Bop[e, q, 2 i + j, 2 a + i'] u_e[2 a + i']
+        self.Bop = np.zeros((self.ne, 4, 4, 16))
+        for i in range(2):
+            for j in range(2):
+                self.Bop[:, :, 2 * i + j, i::2] = self.dNdX[:, :, :, j]
+        self.BopT_w = self.Bop.transpose(0, 1, 3, 2) * self.wdet[:, :, None, None]
         # the edge Y = 0 is fixed; the edge Y = H carries t_y(X) = -(1 - (2 X / L - 1)^2) per unit
         # Tbar (consistent nodal forces, 3-point Gauss rule per quadratic edge)
         self.fixed = np.zeros((self.nn, 2), bool)
@@ -109,6 +115,17 @@ class BeamMesh:
         self.dofs = dofs
         self.rows = np.repeat(dofs, 16, axis=1).ravel()
         self.cols = np.tile(dofs, (1, 16)).ravel()
+        # CSR pattern of the free-free block, built once: every element-matrix entry that
+        # couples two free dofs has a slot (slot[keep]); assembly is one weighted bincount
+        fmap = -np.ones(self.ndof, int)
+        fmap[self.free] = np.arange(len(self.free))
+        r, c = fmap[self.rows], fmap[self.cols]
+        self.keep = (r >= 0) & (c >= 0)
+        nf = len(self.free)
+        key = r[self.keep] * nf + c[self.keep]
+        uniq, self.slot = np.unique(key, return_inverse=True)
+        self.ff_indices = (uniq % nf).astype(np.int32)
+        self.ff_indptr = np.concatenate([[0], np.cumsum(np.bincount(uniq // nf, minlength=nf))]).astype(np.int32)
 
     def deformation_gradients(self, u):
         """F = I + grad u at every Gauss point, [ne * 4, 2, 2]"""
@@ -116,17 +133,31 @@ class BeamMesh:
         F = np.eye(2)[None, None] + np.einsum("eai,eqaj->eqij", ue, self.dNdX)
         return F.reshape(-1, 2, 2)
 
+    def element_arrays(self, P, A):
+        """element force vectors [ne, 16] and stiffness matrices [ne, 16, 16] from Pbar [nq, 2, 2]
+        and Abar [nq, 4, 4] (index (ij, kl)), 2 x 2 Gauss rule"""
+        P = P.reshape(self.ne, 4, 4, 1)
+        A = A.reshape(self.ne, 4, 4, 4)
+        fe = np.matmul(self.BopT_w, P)[..., 0].sum(1)
+        Ke = np.matmul(np.matmul(self.BopT_w, A), self.Bop).sum(1)
+        return fe, Ke
+
     def assemble(self, P, A):
-        """internal force and tangent from Pbar [nq, 2, 2], Abar [nq, 4, 4] (index (ij, kl))"""
-        P = P.reshape(self.ne, 4, 2, 2)
-        A = A.reshape(self.ne, 4, 2, 2, 2, 2)
-        fe = np.einsum("eq,eqij,eqaj->eai", self.wdet, P, self.dNdX).reshape(self.ne, 16)
-        AB = np.einsum("eqijkl,eqbl->eqijbk", A, self.dNdX)                       # A : grad N_b
-        Ke = np.einsum("eq,eqaj,eqijbk->eaibk", self.wdet, self.dNdX, AB, optimize=True).reshape(self.ne, 16, 16)
+        """internal force and tangent (all dofs) from Pbar [nq, 2, 2], Abar [nq, 4, 4]"""
+        fe, Ke = self.element_arrays(P, A)
         f = np.zeros(2 * self.nn)
         np.add.at(f, self.dofs, fe)
         K = sp.coo_matrix((Ke.ravel(), (self.rows, self.cols)), shape=(2 * self.nn, 2 * self.nn)).tocsr()
         return f, K
+
+    def assemble_free(self, P, A):
+        """internal force (all dofs) and the free-free block of the tangent (CSR, the pattern
+        built once in the constructor)"""
+        fe, Ke = self.element_arrays(P, A)
+        f = np.bincount(self.dofs.ravel(), weights=fe.ravel(), minlength=self.ndof)
+        data = np.bincount(self.slot, weights=Ke.ravel()[self.keep], minlength=len(self.ff_indices))
+        nf = len(self.free)
+        return f, sp.csr_matrix((data, self.ff_indices, self.ff_indptr), shape=(nf, nf))
 
 
 def load_levels(T_max, nsteps, unload=False):
@@ -161,7 +192,7 @@ def solve(mesh, micro, T_max, nsteps, unload=False, tol=1e-8, max_it=25, verbose
             P, A, status = micro.step(F)
             if (status != 0).any():
                 raise RuntimeError("micro problem did not converge at load step %d, macro iteration %d" % (k, it))
-            fint, K = mesh.assemble(P, A)
+            fint, Kff = mesh.assemble_free(P, A)
             R = (fint - fext)[free]
             rn = np.linalg.norm(R)
             if verbose:
@@ -170,7 +201,7 @@ def solve(mesh, micro, T_max, nsteps, unload=False, tol=1e-8, max_it=25, verbose
                 break
             if it == max_it:
                 raise RuntimeError("macro Newton did not converge at load step %d" % k)
-            du = spla.spsolve(K[free][:, free].tocsc(), -R)
+            du = spla.splu(Kff.tocsc(), permc_spec="MMD_AT_PLUS_A").solve(-R)
             u[free] += du
         out["u"].append(u.copy())
         tip = mesh.ids[mesh.nx, 2 * mesh.ny]            # mid-span node of the loaded edge

@@ -67,6 +67,31 @@ def test_patch_and_traction():
     assert np.abs(K @ u - f).max() <= 1e-15
 
 
+def test_element_arrays_and_free_assembly():
+    """Element force and stiffness against their definitions written out entry by entry,
+    f_(a i) = sum_q w_q P_ij dN_a/dX_j and K_(a i)(b k) = sum_q w_q dN_a/dX_j A_ijkl dN_b/dX_l,
+    and the free-free CSR assembly against slicing the full matrix."""
+    m = fe2.BeamMesh(nx=3, ny=2)
+    rng = np.random.default_rng(3)
+    P = rng.standard_normal((m.nq, 2, 2))
+    A = rng.standard_normal((m.nq, 4, 4))
+    fe, Ke = m.element_arrays(P, A)
+    A6 = A.reshape(m.ne, 4, 2, 2, 2, 2)
+    P4 = P.reshape(m.ne, 4, 2, 2)
+    for e in (0, m.ne - 1):
+        for a, i in np.ndindex(8, 2):
+            ref = sum(m.wdet[e, q] * P4[e, q, i, j] * m.dNdX[e, q, a, j] for q in range(4) for j in range(2))
+            assert abs(fe[e, 2 * a + i] - ref) <= 1e-13
+            for b, k in np.ndindex(8, 2):
+                ref = sum(m.wdet[e, q] * m.dNdX[e, q, a, j] * A6[e, q, i, j, k, l] * m.dNdX[e, q, b, l]
+                          for q in range(4) for j in range(2) for l in range(2))
+                assert abs(Ke[e, 2 * a + i, 2 * b + k] - ref) <= 1e-12
+    f1, K1 = m.assemble(P, A)
+    f2, K2 = m.assemble_free(P, A)
+    assert np.abs(f1 - f2).max() <= 1e-14
+    assert np.abs(K1[m.free][:, m.free].toarray() - K2.toarray()).max() <= 1e-13
+
+
 def test_fe2_oracle_quadratic_convergence():
     """2 x 1 macro elements (8 macro points) on the 2D porous RVE model, compressed into the
     plastic range in 4 steps; within every step the macro residual contracts quadratically (the
