@@ -11,7 +11,7 @@ times of both two-scale solutions on the host cores.
 The reduced micro model here is the FP64 oracle (test infrastructure); the library's micro
 solver reproduces it on the GPU to rounding (tests/test_fe2.py).
 
-usage: python tests/fe2_compliance_study.py [--nx 4 --ny 2 --steps 50 --T 80 --out study.json]
+usage: python tests/fe2_compliance_study.py [--nx 4 --ny 2 --steps 50 --T 60 --out study.json]
 """
 import argparse
 import json
@@ -49,7 +49,7 @@ def main():
     ap.add_argument("--nx", type=int, default=4)
     ap.add_argument("--ny", type=int, default=2)
     ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--T", type=float, default=80.0)
+    ap.add_argument("--T", type=float, default=60.0)
     ap.add_argument("--out", default=None)
     args = ap.parse_args()
     macro = fe2.BeamMesh(nx=args.nx, ny=args.ny)
