@@ -125,21 +125,25 @@ def test_fe2_oracle_quadratic_convergence():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("fp32", 1e-6)])
-def test_fe2_gpu_vs_oracle(prec, tol):
+@pytest.mark.parametrize("prec,tol,unload", [("fp64", 1e-9, False), ("fp32", 1e-6, False), ("fp64", 1e-9, True)])
+def test_fe2_gpu_vs_oracle(prec, tol, unload):
+    """monotonic loading to Tbar = 80 in 5 steps; and the load-unload program (up to 80 and
+    back to 0 in 6 steps: elastic unloading of plastically deformed micro problems)"""
     import __graft_entry__
     __graft_entry__.build()
     rom = workload.load_model(workload.WORKLOADS["c2"]["model"])
     mesh = fe2.BeamMesh(nx=4, ny=2)
     coef = inputs.map_coefficients(2, fe2.beam_mu(mesh))
-    ref = fe2.solve(mesh, OracleMicro(rom, coef), 80.0, 5)
+    nsteps = 6 if unload else 5
+    ref = fe2.solve(mesh, OracleMicro(rom, coef), 80.0, nsteps, unload=unload)
     gm = fe2.RomMicro(rom, coef, prec)
-    out = fe2.solve(mesh, gm, 80.0, 5)
+    out = fe2.solve(mesh, gm, 80.0, nsteps, unload=unload)
     gm.close()
     tip_err = np.abs(np.array(out["tip"]) - np.array(ref["tip"])).max() / np.abs(np.array(ref["tip"])).max()
     u_err = np.abs(out["u"][-1] - ref["u"][-1]).max() / np.abs(ref["u"][-1]).max()
     print(prec, "tip %.2e u %.2e macro its" % (tip_err, u_err), out["macro_its"], ref["macro_its"])
     assert u_err <= tol and tip_err <= tol
+    assert fe2.compliance_error(out["compliance"], ref["compliance"])[1] <= tol
     if prec == "fp64":
         assert out["macro_its"] == ref["macro_its"]
 
