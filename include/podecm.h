@@ -301,9 +301,9 @@ rom_status rom_features(rom_ctx *ctx, rom_state *st, const double *Fbar_d, float
  * Allocation-free step.  The paper has no counterpart: this is a deployment
  * variant of rom_step_device for callers that cannot call cudaMalloc -- a
  * macro solver running inside a pre-sized memory pool or arena it does not
- * own, a host application that must not grow its device footprint after
- * start-up, or code issuing the step while a stream is being captured (no
- * allocation allowed there).
+ * own, or a host application that must not grow its device footprint after
+ * start-up (where an allocation could fail or stall the rest of the
+ * application).
  *
  * The caller passes every array on the device: the model in the public
  * layouts (G[m][d*d][n], w[m], phase[m], Gmu[m][d*d][n_par]; the phase table

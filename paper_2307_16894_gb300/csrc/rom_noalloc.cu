@@ -1,10 +1,9 @@
 // Allocation-free load step (rom_step_noalloc in include/podecm.h).
 //
 // Some callers cannot allocate device memory: a solver that runs inside a
-// pre-sized memory pool or an arena it does not own, a host library that
-// must not grow the device footprint after start-up, or code that calls the
-// step while a stream is being captured into a CUDA graph (allocation is
-// not allowed there).  This entry point takes every model, state and output
+// pre-sized memory pool or an arena it does not own, or a host library that
+// must not grow the device footprint after start-up (an allocation there can
+// fail or stall the rest of the application).  This entry point takes every model, state and output
 // array from the caller and keeps the per-instance work arrays of the step
 // (trial iterate, Newton control, residual, stiffness, pulled-back tangents,
 // trial history, ...) in one file-scope device array of fixed size instead of

@@ -1,6 +1,6 @@
 """Learned Newton start on the GPU: the library's MLP forward/backward kernels vs the
 FP64 oracle MLP, training, and the learned start inside the reduced solve (the
-converged answer is the judge; the start only changes the iteration count)."""
+converged answer decides the result; the start only changes the iteration count)."""
 import numpy as np
 import pytest
 

@@ -1,6 +1,6 @@
 """rom_step_noalloc, the allocation-free step for callers that cannot call
-cudaMalloc (a solver inside a pre-sized pool or arena, a host application that
-must not grow its device footprint, code issuing work during stream capture).
+cudaMalloc (a solver inside a pre-sized pool or arena, or a host application that
+must not grow its device footprint after start-up).
 Its work space is a static device array; the test checks its outputs and
 updated state against rom_step (the allocating entry point) on two calls in a
 row, and that an oversized batch is refused.  Kept in a file of its own that
