@@ -114,22 +114,37 @@ class Clocks:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            f = [x.strip() for x in ln.split(",")]
-            if len(f) < 7:
-                continue
-            try:
-                sm.append(float(f[0]))
-                mx.append(float(f[1]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, f[3:7]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return parse_clock_lines(self.lines)
+
+
+def parse_clock_lines(lines):
+    """Median SM clock, maximum SM clock and the throttle reasons seen in nvidia-smi CSV lines
+    (clocks.sm, clocks.max.sm, power.draw, then the four reason columns in CLOCK_REASONS order)."""
+    sm, mx, reasons = [], [], set()
+    for ln in lines:
+        f = [x.strip() for x in ln.split(",")]
+        if len(f) < 7:
+            continue
+        try:
+            sm.append(float(f[0]))
+            mx.append(float(f[1]))
+        except ValueError:
+            continue
+        for nm, v in zip(CLOCK_REASONS, f[3:7]):
+            if v.lower() == "active":
+                reasons.add(nm)
+    return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+            "reasons": sorted(reasons), "samples": len(sm)}
+
+
+CLOCK_REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+# reasons that invalidate a timing (sw_power_cap is normal under load and only noted)
+INVALIDATING_REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown")
+
+
+def throttled(clk):
+    """True if a reason that invalidates the timing was active during the timed region."""
+    return any(r in INVALIDATING_REASONS for r in clk.get("reasons", []))
 
 
 def load_workload(args, first=0, B=None):
@@ -235,6 +250,18 @@ def run_ours(args, rank, world):
 
     graphs = not args.no_graphs
     ms, info, prof_main, clk = timed_region(graphs, profile=not graphs)
+    # a timing taken under a hardware or thermal slowdown is discarded and taken once more
+    # (the decision is the same on every rank, so the collectives inside stay matched)
+    again = throttled(clk)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([1 if again else 0], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        again = bool(t.item())
+    if again:
+        first = clk["reasons"]
+        ms, info, prof_main, clk = timed_region(graphs, profile=not graphs)
+        clk = dict(clk, remeasured=True, first_reasons=first)
     if graphs:
         # kernel times and FLOPs of the same K steps through the per-launch path (events per launch)
         ms_prof, _, prof, clk_prof = timed_region(False, profile=True)

@@ -22,3 +22,33 @@ def test_reference_arm_json_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def _bench():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_clock_samples_and_throttle_decision():
+    """nvidia-smi CSV lines (clocks.sm, clocks.max.sm, power.draw, hw_slowdown,
+    hw_thermal_slowdown, sw_thermal_slowdown, sw_power_cap): median clock, maximum clock and
+    reasons; only the hardware and thermal slowdowns make the bench take the timing again."""
+    b = _bench()
+    lines = ["2070, 2070, 900.1, Not Active, Not Active, Not Active, Not Active",
+             "1995, 2070, 1390.0, Not Active, Not Active, Not Active, Active",
+             "2055, 2070, 1200.0, Not Active, Not Active, Not Active, Not Active",
+             "[N/A], 2070, 0, Not Active, Not Active, Not Active, Not Active",   # unreadable sample
+             "garbled"]
+    c = b.parse_clock_lines(lines)
+    assert c["sm_mhz"] == 2055.0 and c["sm_max_mhz"] == 2070.0 and c["samples"] == 3
+    assert c["reasons"] == ["sw_power_cap"] and not b.throttled(c)
+    for col, name in zip(range(3, 6), ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown")):
+        f = lines[0].split(", ")
+        f[col] = "Active"
+        c = b.parse_clock_lines([", ".join(f)])
+        assert c["reasons"] == [name] and b.throttled(c)
+    assert b.parse_clock_lines([]) == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+    assert not b.throttled({"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]})
