@@ -53,7 +53,9 @@ _lib = None
 def lib():
     global _lib
     if _lib is None:
-        _lib = ctypes.CDLL(build())
+        # ORACLE_LIB names a prebuilt copy of this library to load instead; the planted-mistake
+        # tests point it at deliberately broken builds of these sources
+        _lib = ctypes.CDLL(os.environ.get("ORACLE_LIB") or build())
         d = ctypes.c_double
         i = ctypes.c_int
         p = ctypes.c_void_p

@@ -202,3 +202,40 @@ def test_plane_strain_block():
     A34 = A3.reshape(3, 3, 3, 3)[:2, :2, :2, :2].reshape(4, 4)
     assert np.array_equal(A2, A34)
     assert np.abs(Fp3[:2, 2]).max() == 0 and np.abs(Fp3[2, :2]).max() == 0
+
+
+def _two_step_nonproportional(ph):
+    """Plastic stretch along x, then a plastic shear: F^p after the second step is a product
+    of two non-commuting flow exponentials, so it is neither symmetric nor coaxial with the
+    second flow direction."""
+    F1 = np.diag([1.08, 0.96, 0.98])
+    F2 = F1 @ np.array([[1.0, 0.12, 0.0], [0.0, 1.0, 0.04], [0.0, 0.0, 1.0]])
+    _, _, Fp1, xi1, pl1 = mat1(F1, ph, tangent=False)
+    P2, _, Fp2, xi2, pl2 = mat1(F2, ph, Fp=Fp1, xi=xi1, tangent=False)
+    assert pl1 and pl2 and xi2 > xi1 > 0
+    assert np.abs(Fp2 - Fp2.T).max() > 1e-4      # the case is non-trivial
+    return F2, P2, Fp2, xi2
+
+
+@pytest.mark.parametrize("ph", [MAT, LIN])
+def test_committed_state_reproduces_stress(ph):
+    """The return map lands on the yield surface, and the committed history (F^p, xi) is
+    the one that produced the returned stress: evaluating the same F again from it gives
+    the same P and no further plastic flow (Eqs. j2_2, j2_4, j2_10)."""
+    F2, P2, Fp2, xi2 = _two_step_nonproportional(ph)
+    P3, _, Fp3, xi3, _ = mat1(F2, ph, Fp=Fp2, xi=xi2, tangent=False)
+    assert np.abs(P3 - P2).max() <= 1e-10 * np.abs(P2).max()
+    assert np.abs(Fp3 - Fp2).max() <= 1e-12 and abs(xi3 - xi2) <= 1e-12 * xi2
+
+
+@pytest.mark.parametrize("ph", [MAT, LIN, ELAST])
+def test_kirchhoff_stress_symmetric(ph):
+    """Balance of angular momentum: the Kirchhoff stress tau = P F^T is symmetric, also after
+    non-proportional plastic flow with a non-symmetric F^p."""
+    if np.isinf(ph["s0"]):
+        F2 = np.array([[1.05, 0.2, 0.0], [-0.1, 0.97, 0.03], [0.02, 0.0, 1.01]])
+        P2 = mat1(F2, ph, tangent=False)[0]
+    else:
+        F2, P2, _, _ = _two_step_nonproportional(ph)
+    tau = P2 @ F2.T
+    assert np.abs(tau - tau.T).max() <= 1e-12 * np.abs(tau).max()

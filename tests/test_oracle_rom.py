@@ -290,3 +290,21 @@ def test_linear_limit_homogeneous():
     expect = (D @ eps.ravel()).reshape(2, 2)
     assert np.abs(outs[0]["Pbar"][0] - expect).max() <= 1e-4 * np.abs(expect).max()
     assert np.abs(outs[0]["Abar"][0] - D).max() <= 1e-4 * np.abs(D).max()
+
+
+def test_rom_cubature_scale_invariance(small_rom):
+    """Scaling all cubature weights and the cell volume |Omega^p| by the same factor scales
+    f and K alike and leaves the solution, Pbar and Abar unchanged (Eqs. forcevector_ecm,
+    eff_stress_1, eff_stiffness_1: every cubature sum enters divided by |Omega^p| or as a
+    homogeneous equation)."""
+    s = small_rom
+    path = [np.array([[1.0 + 0.004 * k, 0.002 * k], [0.001 * k, 1.0 - 0.003 * k]]) for k in range(1, 4)]
+    ref, _ = run_rom(s["rom"], s["Finv"], s["J"], path, tol_rel=1e-12, tol_abs=1e-14)
+    rom2 = dict(s["rom"], w=2.5 * s["rom"]["w"], omega=2.5 * s["rom"]["omega"])
+    out, _ = run_rom(rom2, s["Finv"], s["J"], path, tol_rel=1e-12, tol_abs=1e-14)
+    assert ref[-1]["n_yield"][0] > 0
+    for a, b in zip(out, ref):
+        assert np.abs(a["q"] - b["q"]).max() <= 1e-10 * np.abs(b["q"]).max()
+        assert np.abs(a["Pbar"] - b["Pbar"]).max() <= 1e-10 * np.abs(b["Pbar"]).max()
+        assert np.abs(a["Abar"] - b["Abar"]).max() <= 1e-9 * np.abs(b["Abar"]).max()
+        assert a["iters"][0] == b["iters"][0]
