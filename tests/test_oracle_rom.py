@@ -308,3 +308,30 @@ def test_rom_cubature_scale_invariance(small_rom):
         assert np.abs(a["Pbar"] - b["Pbar"]).max() <= 1e-10 * np.abs(b["Pbar"]).max()
         assert np.abs(a["Abar"] - b["Abar"]).max() <= 1e-9 * np.abs(b["Abar"]).max()
         assert a["iters"][0] == b["iters"][0]
+
+
+@pytest.mark.parametrize("d,N", [(2, 16), (3, 6)])
+def test_vp_gram_matrix_closed_form(d, N):
+    """The V^p inner product (Eq. Vdotproduct: mass plus gradient term) on the full cell:
+    a constant field has norm^2 = volume = 1, and the interpolant of u_0 = sin(2 pi X_1) has
+    exactly the norm^2 of a piecewise-linear function of X_1 on the node spacing,
+    sum_cells h/3 (a^2 + a b + b^2) + sum_cells (b - a)^2 / h (the other directions have
+    unit extent and the 2x2(x2) Gauss rule integrates these products exactly)."""
+    mesh = fe.Mesh(d, N, lambda c: 0, fix_node=False)
+    MV = mesh.mass_and_laplace()
+    h = 1.0 / N
+    ids = np.arange(mesh.nnode)
+    x = (ids % N) * h                                    # node ids run x fastest
+    const = np.zeros(mesh.ndof)
+    const[mesh.dofmap[:, 0]] = 1.0
+    assert abs(const @ (MV @ const) - 1.0) <= 1e-12
+    u = np.zeros(mesh.ndof)
+    u[mesh.dofmap[:, 0]] = np.sin(2 * np.pi * x)
+    a = np.sin(2 * np.pi * np.arange(N) * h)
+    b = np.sin(2 * np.pi * (np.arange(N) + 1) * h)
+    exact = np.sum(h / 3.0 * (a * a + a * b + b * b)) + np.sum((b - a) ** 2 / h)
+    assert abs(u @ (MV @ u) - exact) <= 1e-12 * exact
+    # the two components are orthogonal and weighted alike
+    v = np.zeros(mesh.ndof)
+    v[mesh.dofmap[:, 1]] = np.sin(2 * np.pi * x)
+    assert abs(u @ (MV @ v)) <= 1e-12 * exact and abs(v @ (MV @ v) - exact) <= 1e-12 * exact
