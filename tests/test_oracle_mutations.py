@@ -91,3 +91,52 @@ def test_planted_mistake_fails_a_pin(tmp_path, mistake):
     # exit code 1: a pin failed (not a crash, a collection error or an interruption)
     assert r.returncode == 1, "planted mistake %s was not caught:\n%s" % (mistake[0], r.stdout[-3000:])
     assert " failed" in r.stdout
+
+
+# The MLP oracle (learned Newton start) is plain numpy: a planted copy of the module is loaded
+# from its text and the MLP pins run against it in this process.
+MLP_MISTAKES = [
+    ("gelu_grad_second_term_dropped",
+     " + x * np.exp(-0.5 * x * x) / np.sqrt(2.0 * np.pi)", ""),
+    ("input_standardisation_inverted", "h = (X - xm) / xs", "h = (X - xm) * xs"),
+    ("output_scale_dropped", "return out * ys + ym", "return out + ym"),
+    ("loss_gradient_factor_dropped", "d = 2.0 * r / r.size", "d = r / r.size"),
+    ("backprop_through_gelu_value", "d = d * gelu_grad(zs[l])", "d = d * gelu(zs[l])"),
+    ("bias_gradient_mean", "gb = d.sum(0)", "gb = d.mean(0)"),
+    ("bias_dropped_in_forward", "z = h @ W.T + b", "z = h @ W.T"),
+]
+
+
+def _planted_mlp(old, new):
+    import types
+    text = open(os.path.join(ORC, "mlp.py")).read()
+    assert text.count(old) == 1, "the original text must occur exactly once: %r" % old
+    mod = types.ModuleType("planted_mlp")
+    exec(compile(text.replace(old, new), "planted_mlp.py", "exec"), mod.__dict__)
+    return mod
+
+
+def _mlp_pins():
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    import test_oracle_mlp
+    return test_oracle_mlp, [getattr(test_oracle_mlp, f) for f in dir(test_oracle_mlp) if f.startswith("test_")]
+
+
+def test_mlp_control_copy_passes_pins(monkeypatch):
+    mod, pins = _mlp_pins()
+    monkeypatch.setattr(mod, "mlp", _planted_mlp("import numpy as np", "import numpy as np"))
+    for pin in pins:
+        pin()
+
+
+@pytest.mark.parametrize("mistake", MLP_MISTAKES, ids=[m[0] for m in MLP_MISTAKES])
+def test_planted_mlp_mistake_fails_a_pin(monkeypatch, mistake):
+    mod, pins = _mlp_pins()
+    monkeypatch.setattr(mod, "mlp", _planted_mlp(mistake[1], mistake[2]))
+    failed = []
+    for pin in pins:
+        try:
+            pin()
+        except AssertionError:
+            failed.append(pin.__name__)
+    assert failed, "planted mistake %s was not caught" % mistake[0]
