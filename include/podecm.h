@@ -120,6 +120,10 @@ typedef struct {
  * context; pass cudaStreamLegacy for the legacy default stream).  *ctx is set
  * to NULL on failure. */
 rom_status rom_create(rom_ctx **ctx, int dim, int device, void *cuda_stream);
+/* Wait for the context stream, then free everything the context owns (model copies, work
+ * and I/O buffers, the MLP, events) and the stream if the context created it; a stream
+ * passed to rom_create stays the caller's.  Destroy the context's states first: a state
+ * refers to its context.  NULL: ROM_E_ARG. */
 rom_status rom_destroy(rom_ctx *ctx);
 
 /* POD basis gradients at the cubature points (Sec. 3.1, Eq. pod_disp):
@@ -139,8 +143,12 @@ rom_status rom_load_cubature(rom_ctx *ctx, int m, const double *w, const int32_t
  * if any det F_mu <= 0.  1 <= n_par <= 4. */
 rom_status rom_set_geometry(rom_ctx *ctx, int64_t B, int n_par, const double *Gmu, const double *mu);
 
-/* Per-batch state for B instances: a = 0, C^p^-1 = I, xi = 0 (virgin material). */
+/* Per-batch state for B instances: a = 0, C^p^-1 = I, xi = 0 (virgin material).
+ * Library-owned device memory (history and the per-step work arrays, rom_state_bytes);
+ * ROM_E_STATE before rom_load_basis and rom_load_cubature, ROM_E_NOMEM if it does not fit. */
 rom_status rom_state_create(rom_ctx *ctx, int64_t B, rom_state **st);
+/* Free the state's device arrays, its captured graph and graph stream (the frees wait for
+ * work still using them).  Call before rom_destroy of its context.  NULL: ROM_E_ARG. */
 rom_status rom_state_destroy(rom_state *st);
 
 /* Canonical history to/from host buffers: a[B][n], Cpinv[B][m][nc] with
