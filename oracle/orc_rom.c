@@ -140,7 +140,7 @@ int orc_rom_step(int d, int n, int m, const double *G, const double *w, const in
                  int npar, const double *dFinv, const double *dJ, double *dPdmu)
 {
     const int d2 = d * d, d4 = d2 * d2;
-    rom_ws s = { d, n, m, G, w, Finv, J, Fbar, Fp, xi, phase, phases };
+    rom_ws s = { d, n, m, G, w, Finv, J, Fbar, Fp, xi, phase, phases, NULL, NULL, NULL, NULL, NULL, NULL, NULL };
     s.gF = malloc(sizeof(double) * (size_t)m * n * d2);   /* dphi_j/dX^p F_mu^-1 at each point */
     s.Pq = malloc(sizeof(double) * (size_t)m * d2);
     s.P33 = malloc(sizeof(double) * (size_t)m);
