@@ -45,6 +45,12 @@ MISTAKES = [
     ("lu_solve_permutation_dropped", R,
      "for (int k = 0; k < n; ++k) { int p = piv[k]; if (p != k) { double t = b[k]; b[k] = b[p]; b[p] = t; } }",
      "(void)piv;"),
+    # full-order FE element loops (Eqs. weakform-dep-mapped, Dweakform-dep), the brute-force reference
+    ("fe_force_without_det_F_mu", R, "const double wJ = a->gw[g] * a->J[qp];", "const double wJ = a->gw[g];"),
+    ("fe_shape_gradient_not_pulled_back", R, "s += a->dN[(g * nen + node) * d + rr] * Fi[rr * d + b];",
+     "s += (rr == b) * a->dN[(g * nen + node) * d + rr];"),
+    ("fe_kinematics_not_pulled_back", R, "s += H[i * d + rr] * Fi[rr * d + j];", "s += H[i * d + rr] * (rr == j);"),
+    ("fe_stiffness_tangent_indices_swapped", R, "A[(i * d + b) * d2 + k * d + l]", "A[(i * d + l) * d2 + k * d + b]"),
     # shape sensitivities, Eq. eff_sensitivities_full
     ("sensitivity_det_derivative_dropped", R, "rhs[j] -= w[i] * (J[i] * (t1 + t2) + dJk * t3);",
      "rhs[j] -= w[i] * (J[i] * (t1 + t2)); (void)dJk; (void)t3;"),
