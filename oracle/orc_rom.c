@@ -2,8 +2,8 @@
  * ORACLE — test infrastructure only (tests, smoke() and the CPU-baseline leg
  * of bench.py).  Plain FP64 CPU reference; shares no code with the CUDA path.
  *
- * 1. The online hyper-reduced solve (Sec. 3.2-3.3, Algorithm 1 online lines
- *    2-5), written literally:
+ * 1. The online hyper-reduced solve (Sec. 3.2-3.3, the online stage of
+ *    Algorithm 1), term by term as the equations state:
  *      f_j  = sum_q w_q [ (dphi_j/dX^p F_mu^-1) : P |det F_mu| ]          Eq. forcevector_ecm
  *      K_jk = sum_q w_q [ (dphi_j F_mu^-1) : A : (dphi_k F_mu^-1) |det F_mu| ]  Eq. stiffnessmatrix_ecm
  *      K da = -f,  a += da, until ||f|| <= tol                               Eq. red_newton, Sec. 2.1
