@@ -4,18 +4,31 @@ One bench "step" = one load step of the whole hot path for every instance of
 the batch: geometry, kinematics, FP64 return map, tangent, force and
 stiffness assembly, Newton with line search, effective stress and stiffness,
 history commit (all Newton iterations included).  Metric: macro-point ROM
-load-steps/s = instances x load steps / time.
+load-steps/s = instances x load steps / time, admissible only if the converged
+Pbar is within 1e-7 (relative) of the FP64 oracle.
 
-Default workload: 4096 macro points of the 2D plane-strain porous RVE family
-(64x64 Q4 parent mesh, POD n = 24, ECM m = 160), each with its own seeded
-geometry mu in [0.2, 0.35] and its own seeded 50-step load path (principal
-stretches 0.9-1.15, random axes and rotation).  Default precision: FP64
-residual, kinematics, return map, eigen log/exp and n x n solve with an FP32
-tangent and stiffness (--precision fp64 for the all-FP64 path); previous-step
-Newton predictor.  Each step is one CUDA-graph launch.
+Default workload: 16384 macro points of the 3D inclusion RVE family (24^3 hex8
+parent mesh, ellipsoidal inclusion with semi-axes mu in [0.15, 0.35]^3, POD
+n = 64, ECM m = 600), each with its own seeded 50-step load path (principal
+stretches 0.9-1.15, random rotation).  Default path: the mixed-precision
+solve -- FP64 return map, eigen log/exp, stresses, convergence test and
+refined n x n solve; double-float FP32 residual; TF32 tensor-core stiffness --
+with the learned Newton start (4 x 128 GELU network, BF16 weights) and its
+previous-step fallback.  Each step is one CUDA-graph launch.
+
+Beside the timed steps the line carries:
+  * fp64_gpu: the plain-start all-FP64 path on the same instances and load
+    steps, and vs_fp64_gpu = value / its value;
+  * full_path: all 50 load steps of the paths on a fresh state, with the count
+    of instance-steps that did not converge;
+  * accuracy: the timed steps' Pbar and Abar and the final reduced coordinates
+    and plastic strains of sampled instances against the FP64 oracle, which the
+    CPU-baseline leg runs on the same instances over the same load steps
+    (the line is flagged inadmissible, and the exit status is 3, if the Pbar
+    error exceeds 1e-7).
 
 usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                       [--workload c2|c3] [--precision fp64|fp32|tf32|bf16] [--start plain|prev|mlp]
+                       [--workload c2|c3|c5] [--precision fp64|fp32|tf32|bf16] [--start plain|prev|mlp]
 """
 import argparse
 import json
@@ -53,11 +66,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5"])
+    ap.add_argument("--workload", default="c3", choices=["c2", "c3", "c5"])
     ap.add_argument("--precision", default=None, choices=["fp64", "fp32", "tf32", "bf16"])
     ap.add_argument("--start", default=None, choices=["plain", "prev", "mlp"],
-                    help="Newton start (default: the learned start with data/mlp_<workload>.npz on the 2D workload, "
-                         "where it beats the previous-step predictor, else the previous-step predictor)")
+                    help="Newton start (default: the learned start with data/mlp_<workload>.npz where that "
+                         "network exists, else the previous-step predictor)")
     ap.add_argument("--mlp", default=None, help="trained learned-start network (npz) for --start mlp "
                                                 "(default data/mlp_<workload>.npz)")
     ap.add_argument("--no-graphs", action="store_true", help="time the host-driven pass loop instead of graphs")
@@ -67,11 +80,16 @@ def parse():
     ap.add_argument("--fp64-residual", action="store_true",
                     help="form the residual of the tensor-core paths in FP64 instead of double-float FP32 pairs")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg (and with it the accuracy check)")
+    ap.add_argument("--no-fp64-arm", action="store_true", help="skip the plain-start FP64 GPU arm")
+    ap.add_argument("--no-full-path", action="store_true", help="skip the run over all load steps of the paths")
+    ap.add_argument("--sample", type=int, default=None,
+                    help="instances the oracle runs for the CPU baseline and the accuracy check "
+                         "(default 16 for c3, 256 for c2)")
     args = ap.parse_args()
     default_mlp = os.path.join(ROOT, "data", "mlp_%s.npz" % args.workload)
     if args.start is None:
-        args.start = "mlp" if (args.workload == "c2" and os.path.exists(default_mlp)) else "prev"
+        args.start = "mlp" if os.path.exists(default_mlp) else "prev"
     if args.start == "mlp" and args.mlp is None:
         args.mlp = default_mlp
     return args
@@ -169,6 +187,15 @@ def flush_l2(buf):
     buf.add_(1.0)
 
 
+def sample_indices(B, ns):
+    """ns instances spread evenly over a batch of B (first and last included)."""
+    return np.unique(np.linspace(0, B - 1, max(1, min(ns, B))).round().astype(np.int64))
+
+
+def default_sample(args):
+    return args.sample or (16 if args.workload == "c3" else 256)
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_2307_16894_gb300 import binding
@@ -195,8 +222,10 @@ def run_ours(args, rank, world):
         warmstart.load_into(ctx, args.mlp, B)
     opts = binding.make_opts(**kw)
     Fd = torch.from_numpy(np.ascontiguousarray(paths.transpose(1, 0, 2, 3))).to("cuda")    # [steps, B, d, d]
-    Pd = torch.empty((B, d, d), dtype=torch.float64, device="cuda")
-    Ad = torch.empty((B, d * d, d * d), dtype=torch.float64, device="cuda")
+    # one output slice per timed step, so that the timed steps' Pbar and Abar can be checked afterwards
+    Pk = torch.empty((K, B, d, d), dtype=torch.float64, device="cuda")
+    Ak = torch.empty((K, B, d * d, d * d), dtype=torch.float64, device="cuda")
+    Pd, Ad = Pk[0], Ak[0]
     Id = torch.empty((B, binding.INFO_DTYPE.itemsize), dtype=torch.uint8, device="cuda")
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > 129 MB L2
     # CUDA-core assembly tiles picked by rom_autotune on the tangents of the first load step
@@ -209,11 +238,19 @@ def run_ours(args, rank, world):
     # shape sensitivities dPbar/dmu after every step (optional, inside the timed region)
     Sd = torch.empty(B * rom["d"] ** 2 * coef.shape[1], dtype=torch.float64, device="cuda") if args.sensitivity else None
 
-    def timed_region(graphs, profile):
+    def max_over_ranks(ms):
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    def timed_region(graphs, profile, o=opts, keep_state=False):
         st = ctx.state_create(B)
         ctx.use_graphs(graphs)
         for k in range(W):
-            ctx.step_device(st, opts, Fd[k], Pd, Ad, Id)
+            ctx.step_device(st, o, Fd[k], Pd, Ad, Id)
         torch.cuda.synchronize()
         if world > 1:
             import torch.distributed as dist
@@ -228,7 +265,7 @@ def run_ours(args, rank, world):
         for k in range(K):
             flush_l2(flush)
             ev[k][0].record(stream)
-            ctx.step_device(st, opts, Fd[W + k], Pd, Ad, Id)
+            ctx.step_device(st, o, Fd[W + k], Pk[k], Ak[k], Id)
             if Sd is not None:
                 ctx.sensitivity_device(st, Sd)
             ev[k][1].record(stream)
@@ -238,18 +275,15 @@ def run_ours(args, rank, world):
         if profile:
             ctx.profile(0)
         clk = clocks.stop()
-        ms = sum(a.elapsed_time(b) for a, b in ev)
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev))
         info = np.frombuffer(torch.cat(infos).cpu().numpy().tobytes(), dtype=binding.INFO_DTYPE)
+        if keep_state:
+            return ms, info, prof, clk, st
         st.close()
         return ms, info, prof, clk
 
     graphs = not args.no_graphs
-    ms, info, prof_main, clk = timed_region(graphs, profile=not graphs)
+    ms, info, prof_main, clk, st_main = timed_region(graphs, profile=not graphs, keep_state=True)
     # a timing taken under a hardware or thermal slowdown is discarded and taken once more
     # (the decision is the same on every rank, so the collectives inside stay matched)
     again = throttled(clk)
@@ -260,8 +294,16 @@ def run_ours(args, rank, world):
         again = bool(t.item())
     if again:
         first = clk["reasons"]
-        ms, info, prof_main, clk = timed_region(graphs, profile=not graphs)
+        st_main.close()
+        ms, info, prof_main, clk, st_main = timed_region(graphs, profile=not graphs, keep_state=True)
         clk = dict(clk, remeasured=True, first_reasons=first)
+    # the timed steps' outputs and final state of the sampled instances (accuracy check)
+    samp = sample_indices(B, default_sample(args))
+    si = torch.from_numpy(samp).cuda()
+    a_fin, _, xi_fin = st_main.export()
+    check = dict(idx=samp, Pbar=Pk.index_select(1, si).cpu().numpy(), Abar=Ak.index_select(1, si).cpu().numpy(),
+                 status=info["status"].reshape(K, B)[:, samp], a=a_fin[samp], xi=xi_fin[samp])
+    st_main.close()
     if graphs:
         # kernel times and FLOPs of the same K steps through the per-launch path (events per launch)
         ms_prof, _, prof, clk_prof = timed_region(False, profile=True)
@@ -274,8 +316,31 @@ def run_ours(args, rank, world):
     launches = sum(v[1] for v in groups.values())
     res = dict(value=value, ms=ms, n_ok=n_ok, n_total=len(info), iters_mean=float(info["iters"].mean()),
                evals_mean=float(info["evals"].mean()), prof=groups, dom=dom, launches=launches, clocks=clk,
-               prec=prec, fp64_residual=bool(args.fp64_residual), B=B, W=W, K=K, graphs=graphs, ms_profiled=ms_prof, clocks_profiled=clk_prof,
-               workload=args.workload, tile=tile)
+               prec=prec, fp64_residual=bool(args.fp64_residual), B=B, W=W, K=K, graphs=graphs, ms_profiled=ms_prof,
+               clocks_profiled=clk_prof, workload=args.workload, tile=tile, check=check)
+    # all load steps of the paths on a fresh state (graphs), with the instance-steps that did not converge
+    if not args.no_full_path:
+        ctx.use_graphs(graphs)
+        st = ctx.state_create(B)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stats = []
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for k in range(nsteps):
+            ctx.step_device(st, opts, Fd[k], Pd, Ad, Id)
+            stats.append(Id.clone())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msf = max_over_ranks(e0.elapsed_time(e1))
+        fi = np.frombuffer(torch.cat(stats).cpu().numpy().tobytes(), dtype=binding.INFO_DTYPE).reshape(nsteps, B)
+        bad = fi["status"] != 0
+        st.close()
+        res["full_path"] = dict(value=B * world * nsteps / (msf / 1e3), unit="macro-point load-steps/s",
+                                load_steps=nsteps, ms=msf, not_converged=int(bad.sum()), instance_steps=int(bad.size),
+                                first_failure_step=int(np.argmax(bad.any(1))) if bad.any() else None,
+                                newton_iters_mean=float(fi["iters"].mean()),
+                                note="every load step of the 50-step paths from the initial state; instances that "
+                                     "do not converge keep their last converged history")
     # end-to-end through the public host-buffer call (H2D of Fbar, D2H of Pbar, Abar, info each step)
     if not args.no_e2e:
         ctx.use_graphs(False)
@@ -293,6 +358,16 @@ def run_ours(args, rank, world):
                           h2d_bytes_per_step=B * d * d * 8,
                           d2h_bytes_per_step=B * (d * d + d ** 4) * 8 + B * binding.INFO_DTYPE.itemsize)
         st2.close()
+    # the plain-start all-FP64 path on the same instances and load steps (the method without the
+    # mixed precision and the learned start)
+    if not args.no_fp64_arm and prec != "fp64":
+        o64 = binding.make_opts(tol_rel=1e-10, tol_abs=rom["tol_abs"], max_iter=25, max_ls=6, precision="fp64",
+                                start="plain", polar_split=True, want_abar=True)
+        ms64, info64, _, clk64 = timed_region(graphs, profile=False, o=o64)
+        res["fp64_gpu"] = dict(value=B * world * K / (ms64 / 1e3), unit="macro-point load-steps/s",
+                               ms_per_step=ms64 / K, newton_iters_mean=float(info64["iters"].mean()),
+                               converged=int((info64["status"] == 0).sum()), total=len(info64),
+                               precision="fp64", start="plain", clocks=clk64)
     ctx.close()
     return res
 
@@ -327,34 +402,87 @@ def run_serving(args, rank, world):
                 groups=desc, clocks=clk)
 
 
-def cpu_baseline(args, n_inst=None, n_steps=None, budget_s=20.0):
+def cpu_baseline(args, n_inst=None, n_steps=None, budget_s=20.0, idx=None, keep=False):
     """The FP64 oracle (as it stands) on the host cores, on a bounded sample of the workload:
-    the first n_inst instances over the first n_steps load steps."""
+    instances idx (default: the first n_inst) over the first n_steps load steps (or until
+    budget_s has passed), each started from the previous-step predictor.  keep: also return
+    the oracle's Pbar and Abar of every step and its final reduced coordinates and plastic
+    strains (the accuracy check of the timed steps)."""
     import oracle
-    from paper_2307_16894_gb300 import workload  # noqa: F401
-    rom, mu, coef, paths = load_workload(args, B=n_inst or (512 if args.workload == "c2" else 16))
+    from paper_2307_16894_gb300 import workload
+    if idx is None:
+        rom, mu, coef, paths = load_workload(args, B=n_inst or (512 if args.workload == "c2" else 16))
+    else:
+        parts = [workload.batch(args.workload, B=1, first=int(i)) for i in idx]
+        rom = parts[0][0]
+        coef = np.concatenate([p[2] for p in parts])
+        paths = np.concatenate([p[3] for p in parts])
     B = len(coef)
     d, n, m = rom["d"], rom["n"], rom["m"]
     Gmu = rom["Gmu"].reshape(m, d, d, -1)
     Fm = np.eye(d)[None, None] + np.einsum("iack,bk->biac", Gmu, coef)
     Finv, J = np.linalg.inv(Fm), np.abs(np.linalg.det(Fm))
     q = np.zeros((B, n))
+    dq_prev = np.zeros((B, n))
     Fp = np.tile(np.eye(3), (B, m, 1, 1)).copy()
     xi = np.zeros((B, m))
-    prec, kw = solver_opts(args, rom)
     nthreads = os.cpu_count() or 1
+    steps = paths.shape[1] if n_steps is None else min(n_steps, paths.shape[1])
+    P_all, A_all, S_all = [], [], []
     t0 = time.perf_counter()
     done = 0
-    for k in range(paths.shape[1]):
-        oracle.rom_batch(rom, Finv, J, paths[:, k], q, Fp, xi, 1e-10, rom["tol_abs"], 25, max_ls=6,
-                         nthreads=nthreads)
+    for k in range(steps):
+        qs = q + dq_prev
+        o = oracle.rom_batch(rom, Finv, J, paths[:, k], qs, Fp, xi, 1e-10, rom["tol_abs"], 25, max_ls=6,
+                             nthreads=nthreads)
+        ok = o["status"] == 0
+        dq_prev[ok] = qs[ok] - q[ok]
+        q[ok] = qs[ok]
+        if keep:
+            P_all.append(o["Pbar"].copy())
+            A_all.append(o["Abar"].copy())
+            S_all.append(o["status"].copy())
         done += 1
-        if (n_steps and done >= n_steps) or time.perf_counter() - t0 > budget_s:
+        if budget_s is not None and time.perf_counter() - t0 > budget_s:
             break
     t = time.perf_counter() - t0
-    return dict(value=B * done / t, unit="macro-point load-steps/s", cores=nthreads, kind="oracle",
-                sample="%d instances x first %d load steps of the %s workload (%.1f s)" % (B, done, args.workload, t))
+    which = ("instances %s" % ",".join(str(int(i)) for i in idx)) if idx is not None else "the first %d instances" % B
+    res = dict(value=B * done / t, unit="macro-point load-steps/s", cores=nthreads, kind="oracle",
+               sample="%s (%d) x first %d load steps of the %s workload (%.1f s)" % (which, B, done, args.workload, t))
+    if keep:
+        res["_out"] = dict(Pbar=np.stack(P_all), Abar=np.stack(A_all), status=np.stack(S_all), q=q.copy(),
+                           xi=xi.copy(), steps=done)
+    return res
 
+
+def accuracy(check, ref, W, K, tol=1e-7):
+    """Errors of the timed steps' outputs on the sampled instances against the oracle: Pbar and
+    Abar per instance and step (max |difference| / max |oracle value| of that instance-step),
+    the reduced coordinates and plastic strains after the last timed step (over the sample).
+    An instance is compared while both sides agree on convergence; from the first step where one
+    side converges and the other does not, its histories differ and it is counted in `split`."""
+    if ref["steps"] < W + K:
+        return dict(checked=False, reason="the oracle ran %d of %d load steps" % (ref["steps"], W + K))
+    gs, os_ = check["status"], ref["status"][W:W + K]
+    # instances whose oracle run already stalled during the warm-up steps carry another history
+    alive = (ref["status"][:W] == 0).all(0) if W else np.ones(gs.shape[1], bool)
+    ep = ea = 0.0
+    compared = 0
+    for k in range(K):
+        alive &= gs[k] == os_[k]
+        for j in np.nonzero(alive & (os_[k] == 0))[0]:
+            P0, A0 = ref["Pbar"][W + k, j], ref["Abar"][W + k, j]
+            ep = max(ep, float(np.abs(check["Pbar"][k, j] - P0).max() / max(np.abs(P0).max(), 1e-300)))
+            ea = max(ea, float(np.abs(check["Abar"][k, j] - A0).max() / max(np.abs(A0).max(), 1e-300)))
+            compared += 1
+    fin = alive & (gs[-1] == 0)
+    eq = float(np.abs(check["a"][fin] - ref["q"][fin]).max() / max(np.abs(ref["q"][fin]).max(), 1e-300)) if fin.any() else None
+    exi = float(np.abs(check["xi"][fin] - ref["xi"][fin]).max() / max(np.abs(ref["xi"][fin]).max(), 1e-300)) if fin.any() else None
+    split = [int(i) for i in check["idx"][~alive]]
+    return dict(checked=True, instances=[int(i) for i in check["idx"]], load_steps=[W, W + K - 1],
+                pbar_rel_err=ep, abar_rel_err=ea, q_rel_err=eq, xi_rel_err=exi, instance_steps_compared=compared,
+                instance_steps=int(gs.size), split=split, tol_pbar=tol, admissible=bool(ep <= tol and compared > 0),
+                oracle="FP64, Newton tolerance 1e-10 relative, max 25 iterations, previous-step start")
 
 
 def kernel_rooflines(r, peaks):
@@ -401,8 +529,23 @@ def kernel_rooflines(r, peaks):
         else:   # double-float residual: 12 FP32 pipe operations per multiply-add
             add("force", "alu", prof["force"][2], FP32_PEAK_TFLOPS / 12,
                 "FP32 pipe / 12: double-float multiply-add of 12 FP32 operations")
-    add("solve", "alu", prof["solve"][2], FP64_PEAK_TFLOPS, "FP64 pipe")
+    # the LU runs in FP64 on the FP64 path and in FP32 (with FP64 refinement) on the mixed paths
+    if prec == "fp64":
+        add("solve", "alu", prof["solve"][2], FP64_PEAK_TFLOPS, "FP64 pipe")
+    else:
+        add("solve", "alu", prof["solve"][2], FP32_PEAK_TFLOPS, "FP32 pipe: FP32 LU with FP64 refinement")
     return out
+
+WORKLOAD_TEXT = {"c2": "2D porous RVE 64x64 Q4, n=24, m=160, B=4096, 50-step paths",
+                 "c3": "3D inclusion RVE 24^3 hex8, n=64, m=600, B=16384, 50-step paths"}
+
+
+def workload_name(args):
+    w = WORKLOAD_TEXT[args.workload]
+    if args.start == "mlp":
+        w += "; learned Newton start (MLP 4 x 128 GELU, BF16 weights)"
+    return w
+
 
 def main():
     args = parse()
@@ -419,7 +562,7 @@ def main():
         line = dict(metric=metric, value=cb["value"], unit=unit, n_gpus=args.gpus, steps=args.steps,
                     warmup=args.warmup, impl="reference", higher_is_better=True, scaling="weak",
                     vs_baseline=None, dtype="f64", data="synthetic",
-                    config=dict(workload=args.workload), cpu_baseline=cb,
+                    config=dict(workload=workload_name(args)), cpu_baseline=cb,
                     e2e=dict(value=cb["value"], unit=unit, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
         print(json.dumps(line))
         return
@@ -444,13 +587,12 @@ def main():
     rooflines = kernel_rooflines(r, peaks)
     roof = rooflines.get(r["dom"]) or dict(kernel=r["dom"], bound="alu", achieved=None, peak=FP64_PEAK_TFLOPS,
                                             unit="TFLOP/s", frac=None, traffic=None)
-    wl = {"c2": "2D porous RVE 64x64 Q4, n=24, m=160, B=4096, 50-step paths",
-          "c3": "3D inclusion RVE 24^3 hex8, n=64, m=600, B=16384, 50-step paths"}[args.workload]
     line = dict(metric=metric, value=r["value"], unit=unit, n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=r["ms"] / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype={"fp64": "f64", "fp32": "f64+f32", "tf32": "f64+tf32", "bf16": "f64+bf16"}[r["prec"]],
                 data="synthetic",
-                config=dict(workload=wl, B_per_gpu=r["B"], precision=r["prec"], start=args.start,
+                config=dict(workload=workload_name(args), B_per_gpu=r["B"], precision=r["prec"], start=args.start,
+                            load_steps_timed=[r["W"], r["W"] + r["K"] - 1],
                             sensitivity=bool(args.sensitivity),
                             residual=("fp64" if r["prec"] == "fp64" or args.fp64_residual else "double-float FP32 pairs"),
                             step_driver="CUDA graph, device-driven Newton loop" if r["graphs"] else "host-driven passes",
@@ -462,9 +604,25 @@ def main():
                 kernels={k: dict(ms=v[0], launches=v[1], gflop=v[2] / 1e9) for k, v in r["prof"].items()})
     if "e2e" in r:
         line["e2e"] = r["e2e"]
+    if "fp64_gpu" in r:
+        line["fp64_gpu"] = r["fp64_gpu"]
+        line["vs_fp64_gpu"] = r["value"] / r["fp64_gpu"]["value"]
+    if "full_path" in r:
+        line["full_path"] = r["full_path"]
+    admissible = True
     if not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(args)
+        # the oracle on the sampled instances over the warm-up and timed load steps: timed as the
+        # CPU baseline, and its outputs are the reference of the accuracy check
+        cb = cpu_baseline(args, idx=r["check"]["idx"], n_steps=r["W"] + r["K"], budget_s=None, keep=True)
+        ref = cb.pop("_out")
+        line["cpu_baseline"] = cb
+        line["accuracy"] = accuracy(r["check"], ref, r["W"], r["K"])
+        admissible = line["accuracy"].get("admissible", True)
+    else:
+        line["accuracy"] = dict(checked=False, reason="--no-cpu")
     print(json.dumps(line))
+    if not admissible:
+        sys.exit(3)
 
 
 if __name__ == "__main__":

@@ -52,3 +52,42 @@ def test_clock_samples_and_throttle_decision():
         assert c["reasons"] == [name] and b.throttled(c)
     assert b.parse_clock_lines([]) == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
     assert not b.throttled({"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]})
+
+
+def test_accuracy_check_of_the_timed_steps():
+    """The bench's accuracy check: the oracle's outputs on sampled instances over the warm-up and
+    timed load steps (the CPU-baseline leg) against the GPU's outputs of the timed steps.  Fed the
+    oracle's own outputs it reports zero error; a planted Pbar error above 1e-7 makes the line
+    inadmissible; an instance whose convergence status differs leaves the comparison from that
+    load step on (its histories differ from there)."""
+    import argparse
+    import numpy as np
+    b = _bench()
+    args = argparse.Namespace(workload="c2", batch=None)
+    idx = np.array([0, 3, 7])
+    W, K = 2, 3
+    cb = b.cpu_baseline(args, idx=idx, n_steps=W + K, budget_s=None, keep=True)
+    ref = cb.pop("_out")
+    assert ref["steps"] == W + K and ref["Pbar"].shape == (W + K, 3, 2, 2) and cb["kind"] == "oracle"
+    assert "instances 0,3,7" in cb["sample"]
+    check = dict(idx=idx, Pbar=ref["Pbar"][W:].copy(), Abar=ref["Abar"][W:].copy(), status=ref["status"][W:].copy(),
+                 a=ref["q"].copy(), xi=ref["xi"].copy())
+    acc = b.accuracy(check, ref, W, K)
+    assert acc["checked"] and acc["admissible"] and acc["pbar_rel_err"] == 0.0 and acc["q_rel_err"] == 0.0
+    bad = dict(check, Pbar=check["Pbar"].copy())
+    bad["Pbar"][1, 2] *= 1 + 1e-6
+    acc = b.accuracy(bad, ref, W, K)
+    assert not acc["admissible"] and 5e-7 < acc["pbar_rel_err"] < 2e-6
+    bad = dict(check, status=check["status"].copy(), Pbar=check["Pbar"].copy())
+    bad["status"][1, 0] = 5
+    bad["Pbar"][2, 0] *= 2.0          # after the split: not compared
+    acc = b.accuracy(bad, ref, W, K)
+    assert acc["admissible"] and acc["split"] == [0] and acc["instance_steps_compared"] == 3 * K - 2
+    assert not b.accuracy(check, dict(ref, steps=W + K - 1), W, K)["checked"]
+
+
+def test_sample_indices():
+    b = _bench()
+    s = b.sample_indices(16384, 16)
+    assert len(s) == 16 and s[0] == 0 and s[-1] == 16383 and (s[1:] > s[:-1]).all()
+    assert list(b.sample_indices(3, 16)) == [0, 1, 2]

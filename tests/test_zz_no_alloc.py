@@ -3,7 +3,8 @@ cudaMalloc (a solver inside a pre-sized pool or arena, or a host application tha
 must not grow its device footprint after start-up).
 Its work space is a static device array; the test checks its outputs and
 updated state against rom_step (the allocating entry point) on two calls in a
-row, and that an oversized batch is refused.  Kept in a file of its own that
+row, in FP64 and on the mixed FP32 path (FP32 tangent and stiffness, FP32 LU
+with FP64 refinement), and that an oversized batch is refused.  Kept in a file of its own that
 pytest collects last."""
 import numpy as np
 import pytest
@@ -23,7 +24,8 @@ def rel(a, b):
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
 
 
-def test_noalloc_matches_rom_step_two_calls():
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_noalloc_matches_rom_step_two_calls(prec):
     import torch
     rom = workload.load_model("rom_c1")
     d, n, m = rom["d"], rom["n"], rom["m"]
@@ -31,7 +33,12 @@ def test_noalloc_matches_rom_step_two_calls():
     rng = np.random.default_rng(21)
     mu = rng.uniform(0.2, 0.35, (B, 1))
     paths = np.stack([inputs.stretch_path(2, 900 + b, 4, 0.95, 1.06) for b in range(B)])
-    kw = dict(tol_rel=1e-10, tol_abs=rom["tol_abs"], max_iter=25, max_ls=6, precision="fp64", start="prev")
+    fp64 = prec == "fp64"
+    kw = dict(tol_rel=1e-10 if fp64 else 1e-9, tol_abs=rom["tol_abs"], max_iter=25 if fp64 else 50, max_ls=6,
+              precision=prec, start="prev")
+    # FP64: the same arithmetic as rom_step; FP32: both sides converge to the relative residual
+    # 1e-9 through their own FP32 stiffness, so they agree to well inside the 1e-7 bound on Pbar
+    tp, ta, tq = (1e-11, 1e-9, 1e-11) if fp64 else (1e-8, 1e-5, 1e-8)
     opts = binding.make_opts(**kw)
 
     # reference: the allocating context path
@@ -67,14 +74,18 @@ def test_noalloc_matches_rom_step_two_calls():
         torch.cuda.synchronize()
         P, A, info = ref[k]
         info2 = np.frombuffer(I_d.cpu().numpy().tobytes(), dtype=binding.INFO_DTYPE)
-        assert np.array_equal(info2["status"], info["status"]) and np.array_equal(info2["iters"], info["iters"])
+        assert np.array_equal(info2["status"], info["status"])
+        if fp64:
+            assert np.array_equal(info2["iters"], info["iters"])
+        else:
+            assert np.abs(info2["iters"] - info["iters"]).max() <= 1
         ok = info["status"] == 0
         assert ok.all()
-        assert rel(P_d.cpu().numpy(), P) <= 1e-11
-        assert rel(A_d.cpu().numpy(), A) <= 1e-9
-    assert rel(a_d.cpu().numpy(), a_ref) <= 1e-11
-    assert rel(np.swapaxes(cp_d.cpu().numpy(), 1, 2), cp_ref) <= 1e-11
-    assert np.abs(xi_d.cpu().numpy() - xi_ref).max() <= 1e-11 * max(xi_ref.max(), 1e-3)
+        assert rel(P_d.cpu().numpy(), P) <= tp
+        assert rel(A_d.cpu().numpy(), A) <= ta
+    assert rel(a_d.cpu().numpy(), a_ref) <= tq
+    assert rel(np.swapaxes(cp_d.cpu().numpy(), 1, 2), cp_ref) <= tq
+    assert np.abs(xi_d.cpu().numpy() - xi_ref).max() <= tq * max(xi_ref.max(), 1e-3)
 
 
 def test_noalloc_rejects_oversized_batch():
