@@ -140,8 +140,35 @@ rom_status rom_load_cubature(rom_ctx *ctx, int m, const double *w, const int32_t
 /* Geometry (Sec. 2.1, Eq. weakform-dep-mapped; the geometry step that opens the online stage of Algorithm 1):
  * F_mu,i = I + sum_k mu[b][k] Gmu[i][a*d+r][k] at every point i of instance b.
  * Gmu[m][d*d][n_par] and mu[B][n_par] on the host, copied.  Fails with ROM_E_ARG
- * if any det F_mu <= 0.  1 <= n_par <= 4. */
+ * if any det F_mu <= 0.  1 <= n_par <= 16. */
 rom_status rom_set_geometry(rom_ctx *ctx, int64_t B, int n_par, const double *Gmu, const double *mu);
+
+/* Geometry from the reduced auxiliary problem (Sec. 3.4, Eqs. auxiliary_problem and
+ * reduced_aux_problem; the geometry step of the online stage of Algorithm 1).  The map is
+ * Phi_mu = X + d with d the displacement of a linear-elastic parent domain whose outer boundary
+ * is fixed and whose parameterised interior boundary is moved by g(theta)(X) = sum_k theta_k
+ * T_k (X - X_c), theta_k = mu_k / mu_ref_k - 1.  Its reduced form: the free part of d lies in
+ * the span of n_rb modes psi_j, the prescribed part is the lifting L(theta), and
+ *   A_hat d_hat = b_hat(theta),  b_hat = M_deim b(theta)[P],  b(theta)[P] = S theta
+ * (discrete empirical interpolation of the forcing b = -K_FD L_D at the rows P; for boundary
+ * data linear in theta the rows are S theta exactly).  Per instance the library solves this
+ * n_rb x n_rb system on the device and sets
+ *   F_mu(X_i) = I + sum_k theta_k GL[i][.][k] + sum_j d_hat_j Gpsi[i][.][j],
+ * the map the step kernels use (rom_state / rom_step unchanged; rom_sensitivity is not
+ * available with this geometry: it needs at most 3 coefficients).
+ *   n_p   geometry parameters, 1 <= n_p <= 8;  n_rb RB modes, 1 <= n_rb <= 8;
+ *   n_deim DEIM rows, 1 <= n_deim <= 32;  n_p + n_rb <= 16;
+ *   mu_ref[n_p] (> 0), Ahat[n_rb][n_rb], Mdeim[n_rb][n_deim], S[n_deim][n_p],
+ *   GL[m][d*d][n_p], Gpsi[m][d*d][n_rb] (gradients at the cubature points, row-major vec),
+ *   mu[B][n_p]: all host buffers, copied (the model arrays are read once per call).
+ * The solve and a det F_mu > 0 check at every point of every instance run on the device;
+ * blocking.  ROM_E_ARG for bad sizes, a singular A_hat, or det F_mu <= 0 anywhere (the text
+ * names the first instance and point); ROM_E_STATE before rom_load_basis / rom_load_cubature. */
+typedef struct {
+    int32_t n_p, n_rb, n_deim;
+    const double *mu_ref, *Ahat, *Mdeim, *S, *GL, *Gpsi;
+} rom_aux_model;
+rom_status rom_set_geometry_aux(rom_ctx *ctx, int64_t B, const rom_aux_model *aux, const double *mu);
 
 /* Per-batch state for B instances: a = 0, C^p^-1 = I, xi = 0 (virgin material).
  * Library-owned device memory (history and the per-step work arrays, rom_state_bytes);

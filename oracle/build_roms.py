@@ -4,7 +4,13 @@ Writes data/rom_<name>.npz for the synthetic workloads: seeded training load
 paths -> full-order FE solves on the parent mesh (Sec. 2) -> POD of the
 fluctuation (V^p) and of the weighted stress (L^2) -> ECM points and weights
 (Sec. 3.2) -> basis gradients G_i = dphi_j/dX^p at the selected points.  The
-geometric map Gmu_k at the points comes from the seeded input generator.
+geometric map Gmu_k at the points comes from the seeded input generator, or,
+for the families marked map="aux", from the auxiliary linear-elasticity problem
+of Sec. 3.4 (oracle/aux.py): then Gmu_k = grad d of its full-order solution for
+theta = e_k (the map is linear in theta = mu / r_p - 1), and the file also holds
+the reduced auxiliary problem (RB operator, DEIM matrices, gradients of the
+lifting and of the RB modes at the selected points) that the library solves on
+the device.
 Every stored value is produced by this script from oracle code only.
 
 usage: python -m oracle.build_roms c1 [c2 c3 ...]
@@ -15,7 +21,7 @@ import time
 
 import numpy as np
 
-from . import fe, reduction
+from . import aux, fe, reduction
 from paper_2307_16894_gb300 import inputs
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -51,10 +57,49 @@ CONFIGS = {
     # void; N_train = 20 Sobol samples of (Uxx, Uyy, Uxy, mu), each applied with the 40-step load-unload
     # amplitude; 40 POD modes kept, L = 20, ECM to integration error epsilon = 0.01.  The stretch ranges
     # cover the macro states of the compressed structure (|Ubar - I| of order 1e-2).
+    # the auxiliary-problem families (Sec. 3.4): the map comes from the reduced linear-elasticity
+    # problem of the void (2D, 16x16 Q4, radius mu in [0.2, 0.35]) or of the inclusion (3D, 12^3 hex8,
+    # semi-axes mu in [0.15, 0.35]^3)
+    "a1": dict(d=2, N=16, n=8, m=40, L=20, map="aux", phases=[MATRIX], map_seed=0,
+               train=[("u2d", 5001 + i, 20) for i in range(3)], mu_range=(0.2, 0.35)),
+    "a3": dict(d=3, N=12, n=16, m=100, L=20, map="aux", phases=[MATRIX, INCLUSION], map_seed=0,
+               train=[("stretch", 6001 + i, 15) for i in range(4)], mu_range=(0.15, 0.35), parallel=True),
     "e2": dict(d=2, N=32, n=40, m=None, ecm_tol=0.01, L=20, map_seed=7, phases=[MATRIX],
                train=[("sobol", i, 40) for i in range(20)], mu_range=(0.2, 0.35), parallel=True,
                sobol=dict(n=20, seed=2307, ranges=[(0.995, 1.005), (0.98, 1.0), (-0.005, 0.005), (0.2, 0.35)])),
 }
+
+
+def aux_problem(cfg):
+    """the auxiliary geometry problem (Sec. 3.4) of a family with map = "aux" on its parent grid"""
+    d = cfg["d"]
+    return aux.AuxProblem(d, cfg["N"], phase_2d if d == 2 else phase_3d, "void" if d == 2 else "inclusion",
+                          VOID_R if d == 2 else INCL_R)
+
+
+def map_fields(cfg, mesh):
+    """Gmu_k at every Gauss point [nq, d, d, n_par] and the map coefficients of a parameter mu"""
+    d = cfg["d"]
+    if cfg.get("map") == "aux":
+        A = aux_problem(cfg)
+        return A.unit_gradients(), (lambda mu: aux.theta_of_mu(mu, A.r_p))
+    modes = inputs.map_modes(d, 1 if d == 2 else 3, cfg["map_seed"])
+    return inputs.map_gradients(modes, mesh.X.reshape(-1, d)), (lambda mu: inputs.map_coefficients(d, mu))
+
+
+def aux_reduced(cfg, sel):
+    """reduced auxiliary problem (RB + DEIM, Eq. reduced_aux_problem) trained on 2 N_p + 2 seeded
+    shapes of the family's range, with its fields at the selected points"""
+    A = aux_problem(cfg)
+    rng = np.random.default_rng(7)
+    mus = rng.uniform(*cfg["mu_range"], size=(2 * A.n_p + 2, A.n_p))
+    red = A.reduce(aux.theta_of_mu(mus, A.r_p))
+    GL, GP = A.reduced_fields(red)
+    d = cfg["d"]
+    m = len(sel)
+    return dict(aux_Ahat=red["Ahat"], aux_Mdeim=red["Mdeim"], aux_S=red["S"], aux_P=red["P"],
+                aux_mu_ref=np.full(A.n_p, A.r_p), aux_GL=GL[sel].reshape(m, d * d, -1),
+                aux_Gpsi=GP[sel].reshape(m, d * d, -1), aux_sigma=red["sigma_u"][:A.n_p + 1])
 
 
 def build(name, verbose=True, nthreads=None):
@@ -62,9 +107,8 @@ def build(name, verbose=True, nthreads=None):
     d, N = cfg["d"], cfg["N"]
     t0 = time.time()
     mesh = fe.Mesh(d, N, phase_2d if d == 2 else phase_3d)
-    npar = 1 if d == 2 else 3
-    modes = inputs.map_modes(d, npar, cfg["map_seed"])
-    Gq = inputs.map_gradients(modes, mesh.X.reshape(-1, d))              # [nq, d, d, npar]
+    Gq, _ = map_fields(cfg, mesh)                                        # [nq, d, d, npar]
+    modes = None
     if verbose:
         print("[%s] mesh ne=%d ndof=%d nq=%d" % (name, mesh.ne, mesh.ndof, mesh.nq), flush=True)
     snaps_w, snaps_W, train_info = [], [], []
@@ -100,6 +144,8 @@ def build(name, verbose=True, nthreads=None):
                                                                      wsel.sum(), wq.sum()), flush=True)
     rom = pack(mesh, cfg, modes, Gq, gradPhi, sel, wsel, err, n_use)
     rom.update(dict(lam_w=lam_w[:n], lam_W=lam_W[:L], n_snap=len(snaps_w)))
+    if cfg.get("map") == "aux":
+        rom.update(aux_reduced(cfg, sel))
     os.makedirs(DATA, exist_ok=True)
     np.savez_compressed(os.path.join(DATA, "rom_%s.npz" % name), **rom)
     # the full set of basis gradients at all Gauss points is kept out of the repo; the
@@ -119,8 +165,7 @@ def _train_path(name, kind, seed, nst, nthreads, verbose):
     d, N = cfg["d"], cfg["N"]
     mesh = fe.Mesh(d, N, phase_2d if d == 2 else phase_3d)
     npar = 1 if d == 2 else 3
-    modes = inputs.map_modes(d, npar, cfg["map_seed"])
-    Gq = inputs.map_gradients(modes, mesh.X.reshape(-1, d))
+    Gq, coef_of = map_fields(cfg, mesh)
     if kind == "sobol":
         sc = cfg["sobol"]
         smp = inputs.sobol_samples(sc["n"], sc["ranges"], sc["seed"])[seed]      # (Uxx, Uyy, Uxy, mu)
@@ -132,7 +177,7 @@ def _train_path(name, kind, seed, nst, nthreads, verbose):
             path = inputs.training_path_2d(seed, nst)
         else:
             path = inputs.stretch_path(d, seed, nst, rotate=False)
-    Finv, J = fe.geometry(Gq, inputs.map_coefficients(d, mu))
+    Finv, J = fe.geometry(Gq, coef_of(mu))
     precond = fe.FFTPreconditioner(mesh, cfg["phases"][0]["E"], cfg["phases"][0]["nu"]) if cfg.get("fft_pcg") else None
     t1 = time.time()
     out = fe.solve_path(mesh, cfg["phases"], Finv, J, path, nthreads=nthreads, verbose=verbose,
@@ -155,7 +200,8 @@ def pack(mesh, cfg, modes, Gq, gradPhi, sel, wsel, err, n_use):
                 ph_E=np.array([p["E"] for p in phases]), ph_nu=np.array([p["nu"] for p in phases]),
                 ph_law=np.array([1 if p["law"] == "power" else 0 for p in phases], np.int32),
                 ph_s0=np.array([p["s0"] for p in phases]), ph_k=np.array([p["k"] for p in phases]),
-                ph_p=np.array([p["p"] for p in phases]), map_seed=cfg["map_seed"], N=cfg["N"])
+                ph_p=np.array([p["p"] for p in phases]), map_seed=cfg["map_seed"], N=cfg["N"],
+                map=cfg.get("map", "synthetic"))
 
 
 # ragged serving family: basis truncations of the 2D and 3D models with their own ECM rules

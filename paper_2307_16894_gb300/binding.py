@@ -27,7 +27,7 @@ EXPORTED = ["rom_create", "rom_destroy", "rom_load_basis", "rom_load_cubature", 
             "rom_step_noalloc", "rom_mlp_init", "rom_mlp_nparams", "rom_mlp_params", "rom_mlp_norm",
             "rom_mlp_train_step", "rom_mlp_loss_grad", "rom_mlp_predict", "rom_features", "rom_debug_stiffness",
             "rom_debug_tangent", "rom_debug_residual", "rom_use_graphs", "rom_sensitivity", "rom_sensitivity_device",
-            "rom_state_bytes", "rom_autotune", "rom_serve"]
+            "rom_state_bytes", "rom_autotune", "rom_serve", "rom_set_geometry_aux"]
 
 KERNEL_GROUPS = ["start", "constitutive", "assemble", "solve", "finalize", "bookkeeping", "learned_start", "force",
                  "sensitivity"]
@@ -49,6 +49,12 @@ class RomNoallocModel(ctypes.Structure):
                 ("n_phase", ctypes.c_int32), ("G", ctypes.c_void_p), ("w", ctypes.c_void_p),
                 ("phase", ctypes.c_void_p), ("Gmu", ctypes.c_void_p), ("phases", ctypes.c_void_p),
                 ("omega_vol", ctypes.c_double)]
+
+
+class RomAuxModel(ctypes.Structure):
+    _fields_ = [("n_p", ctypes.c_int32), ("n_rb", ctypes.c_int32), ("n_deim", ctypes.c_int32),
+                ("mu_ref", ctypes.c_void_p), ("Ahat", ctypes.c_void_p), ("Mdeim", ctypes.c_void_p),
+                ("S", ctypes.c_void_p), ("GL", ctypes.c_void_p), ("Gpsi", ctypes.c_void_p)]
 
 
 class RomError(RuntimeError):
@@ -74,6 +80,7 @@ def lib(path=None):
     L.rom_load_basis.argtypes = [p, i, i, p]
     L.rom_load_cubature.argtypes = [p, i, p, p, i, p, d]
     L.rom_set_geometry.argtypes = [p, i64, i, p, p]
+    L.rom_set_geometry_aux.argtypes = [p, i64, p, p]
     L.rom_state_create.argtypes = [p, i64, pp]
     L.rom_state_destroy.argtypes = [p]
     L.rom_state_export.argtypes = [p, p, p, p, p]
@@ -187,6 +194,17 @@ class Context:
         B, n_par = mu.shape
         self._check(self.L.rom_set_geometry(self.h, B, n_par, _p(Gmu), _p(mu)), "rom_set_geometry")
         self.n_par = n_par
+
+    def set_geometry_aux(self, rom, mu):
+        """rom_set_geometry_aux: the reduced auxiliary problem (Sec. 3.4) of a model file with
+        map = "aux" (aux_mu_ref, aux_Ahat, aux_Mdeim, aux_S, aux_GL, aux_Gpsi), solved on the
+        device for the shape parameters mu [B, n_p]."""
+        keep = [_f64(rom[k]) for k in ("aux_mu_ref", "aux_Ahat", "aux_Mdeim", "aux_S", "aux_GL", "aux_Gpsi")]
+        mu = _f64(np.atleast_2d(mu))
+        n_p, n_rb, n_deim = keep[0].size, keep[1].shape[0], keep[2].shape[1]
+        a = RomAuxModel(n_p, n_rb, n_deim, *[k.ctypes.data for k in keep])
+        self._check(self.L.rom_set_geometry_aux(self.h, mu.shape[0], ctypes.byref(a), _p(mu)), "rom_set_geometry_aux")
+        self.n_par = n_p + n_rb
 
     def state_create(self, B):
         h = ctypes.c_void_p()

@@ -7,7 +7,7 @@
 namespace podecm {
 
 constexpr int MAX_PHASES = 8;
-constexpr int MAX_NPAR = 4;
+constexpr int MAX_NPAR = 16;
 constexpr int MAX_N = 128;
 
 // per-instance Newton control block

@@ -47,6 +47,12 @@ void launch_graph_advance(Batch Bt, const int32_t *list_next, cudaGraphCondition
                           cudaStream_t s);
 void launch_reset_pass(Batch Bt, cudaStream_t s);
 void launch_all_active(Batch Bt, cudaStream_t s);
+int aux_max();
+void launch_aux_geometry(int n_p, int n_rb, int n_deim, const double *mu_ref, const double *Ahat,
+                         const double *Mdeim, const double *S, int64_t B, const double *mu, double *coef, int *bad,
+                         cudaStream_t s);
+void launch_geom_check(int d, int m, int nc, int64_t B, const double *coef, const double *Gmu_T,
+                       unsigned long long *first_bad, cudaStream_t s);
 }  // namespace podecm
 
 using namespace podecm;
@@ -374,6 +380,74 @@ rom_status rom_set_geometry(rom_ctx *ctx, int64_t B, int n_par, const double *Gm
     CK(cudaMemcpy(ctx->mu, mu, (size_t)B * n_par * 8, cudaMemcpyHostToDevice));
     ctx->B = B;
     ctx->n_par = n_par;
+    ctx->has_geom = true;
+    ++ctx->graph_epoch;     // captured step graphs hold the coefficient array
+    return ROM_OK;
+}
+
+rom_status rom_set_geometry_aux(rom_ctx *ctx, int64_t B, const rom_aux_model *aux, const double *mu) {
+    if (!ctx) return ROM_E_ARG;
+    if (!ctx->has_basis && !ctx->has_cub) return fail(ctx, ROM_E_STATE, "rom_set_geometry_aux before basis/cubature");
+    if (B < 1 || !aux || !mu || !aux->mu_ref || !aux->Ahat || !aux->Mdeim || !aux->S || !aux->GL || !aux->Gpsi)
+        return fail(ctx, ROM_E_ARG, "rom_set_geometry_aux: bad arguments");
+    const int np = aux->n_p, nr = aux->n_rb, nd = aux->n_deim, nc = np + nr;
+    if (np < 1 || np > aux_max() || nr < 1 || nr > aux_max() || nd < 1 || nd > 4 * aux_max() || nc > MAX_NPAR)
+        return fail(ctx, ROM_E_ARG, "rom_set_geometry_aux: sizes n_p=%d n_rb=%d n_deim=%d out of range", np, nr, nd);
+    for (int k = 0; k < np; ++k)
+        if (!(aux->mu_ref[k] > 0) || !std::isfinite(aux->mu_ref[k]))
+            return fail(ctx, ROM_E_ARG, "rom_set_geometry_aux: mu_ref[%d] must be positive", k);
+    const int d = ctx->dim, d2 = d * d, m = ctx->m;
+    CK(cudaSetDevice(ctx->device));
+    // Gmu = [grad L_k, grad psi_j] in the kernels' layout [d2][nc][m]
+    std::vector<double> gt((size_t)d2 * nc * m);
+    for (int i = 0; i < m; ++i)
+        for (int c = 0; c < d2; ++c) {
+            for (int k = 0; k < np; ++k) gt[((size_t)c * nc + k) * m + i] = aux->GL[((size_t)i * d2 + c) * np + k];
+            for (int j = 0; j < nr; ++j) gt[((size_t)c * nc + np + j) * m + i] = aux->Gpsi[((size_t)i * d2 + c) * nr + j];
+        }
+    // small operators and the parameters in one staging buffer: mu_ref | Ahat | Mdeim | S | mu
+    const size_t n_small = (size_t)np + (size_t)nr * nr + (size_t)nr * nd + (size_t)nd * np;
+    std::vector<double> sm(n_small);
+    size_t o = 0;
+    for (int k = 0; k < np; ++k) sm[o++] = aux->mu_ref[k];
+    for (int e = 0; e < nr * nr; ++e) sm[o++] = aux->Ahat[e];
+    for (int e = 0; e < nr * nd; ++e) sm[o++] = aux->Mdeim[e];
+    for (int e = 0; e < nd * np; ++e) sm[o++] = aux->S[e];
+    void *p;
+    p = ctx->Gmu_T; dfree(p); ctx->Gmu_T = nullptr;
+    p = ctx->mu; dfree(p); ctx->mu = nullptr;
+    ctx->has_geom = false;
+    ++ctx->graph_epoch;
+    rom_status s;
+    double *work = nullptr;       // small operators, then mu [B][np]
+    unsigned long long *flags = nullptr;   // [0] first bad point, [1] singular A_hat (as int)
+    if ((s = dalloc(ctx, (void **)&ctx->Gmu_T, gt.size() * 8)) != ROM_OK) return s;
+    if ((s = dalloc(ctx, (void **)&ctx->mu, (size_t)B * nc * 8)) != ROM_OK) return s;
+    if ((s = dalloc(ctx, (void **)&work, (n_small + (size_t)B * np) * 8)) != ROM_OK) return s;
+    if ((s = dalloc(ctx, (void **)&flags, 16)) != ROM_OK) { p = work; dfree(p); return s; }
+    auto release = [&] { void *q = work; dfree(q); q = flags; dfree(q); };
+    const unsigned long long none = (unsigned long long)B * (unsigned long long)m;
+    unsigned long long hflags[2] = {none, 0ull};
+    cudaError_t e = cudaMemcpy(ctx->Gmu_T, gt.data(), gt.size() * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(work, sm.data(), n_small * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(work + n_small, mu, (size_t)B * np * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(flags, hflags, 16, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { release(); return fail(ctx, ROM_E_CUDA, "rom_set_geometry_aux: %s", cudaGetErrorString(e)); }
+    const double *d_ref = work, *d_A = d_ref + np, *d_M = d_A + (size_t)nr * nr, *d_S = d_M + (size_t)nr * nd;
+    launch_aux_geometry(np, nr, nd, d_ref, d_A, d_M, d_S, B, work + n_small, ctx->mu,
+                        reinterpret_cast<int *>(flags + 1), ctx->stream);
+    launch_geom_check(d, m, nc, B, ctx->mu, ctx->Gmu_T, flags, ctx->stream);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hflags, flags, 16, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    release();
+    if (e != cudaSuccess) return fail(ctx, ROM_E_CUDA, "rom_set_geometry_aux: %s", cudaGetErrorString(e));
+    if ((hflags[1] & 0xffffffffull) != 0) return fail(ctx, ROM_E_ARG, "rom_set_geometry_aux: singular reduced operator A_hat");
+    if (hflags[0] < none)
+        return fail(ctx, ROM_E_ARG, "rom_set_geometry_aux: det F_mu <= 0 at instance %lld point %d",
+                    (long long)(hflags[0] / (unsigned long long)m), (int)(hflags[0] % (unsigned long long)m));
+    ctx->B = B;
+    ctx->n_par = nc;
     ctx->has_geom = true;
     return ROM_OK;
 }

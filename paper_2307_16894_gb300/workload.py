@@ -19,6 +19,10 @@ WORKLOADS = {
     "c1": dict(model="rom_c1", B=1, steps=20, seed0=None, mu=(0.3, 0.3), uniaxial=True),
     "c2": dict(model="rom_c2", B=4096, steps=50, seed0=10_000, mu=(0.2, 0.35), stretch=(0.9, 1.15)),
     "c3": dict(model="rom_c3", B=16384, steps=50, seed0=20_000, mu=(0.15, 0.35), stretch=(0.9, 1.15)),
+    # geometry from the reduced auxiliary problem (rom_set_geometry_aux): the batch's "coefficients"
+    # are the shape parameters mu themselves (the device turns them into the map)
+    "a1": dict(model="rom_a1", B=256, steps=20, seed0=50_000, mu=(0.2, 0.35), stretch=(0.9, 1.15), aux=True),
+    "a3": dict(model="rom_a3", B=16384, steps=20, seed0=60_000, mu=(0.15, 0.35), stretch=(0.9, 1.15), aux=True),
 }
 
 
@@ -45,7 +49,8 @@ def truncate(rom, n):
 
 def batch(name, B=None, steps=None, first=0):
     """(mu [B, n_par], map coefficients [B, n_par], Fbar paths [B, steps, d, d]) of a workload;
-    instances first .. first+B-1 of the workload's seeded sequence."""
+    instances first .. first+B-1 of the workload's seeded sequence.  For the auxiliary-geometry
+    workloads the coefficients returned are mu (rom_set_geometry_aux takes the shape parameters)."""
     w = WORKLOADS[name]
     rom = load_model(w["model"])
     d = rom["d"]
@@ -57,7 +62,7 @@ def batch(name, B=None, steps=None, first=0):
     else:
         mu = np.stack([inputs.batch_mu(d, 1, w["seed0"] + first + b, *w["mu"])[0] for b in range(B)])
         paths = np.stack([inputs.stretch_path(d, w["seed0"] + first + b, steps, *w["stretch"]) for b in range(B)])
-    return rom, mu, inputs.map_coefficients(d, mu), paths
+    return rom, mu, (mu if w.get("aux") else inputs.map_coefficients(d, mu)), paths
 
 
 def shard(name, B_per_rank, rank, steps=None):

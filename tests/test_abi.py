@@ -42,6 +42,7 @@ def test_argument_errors_without_gpu(L):
     assert L.rom_last_error(None) == b"null context"
     assert L.rom_step(None, None, None, None, None, None, None) == binding.ROM_E_ARG
     assert L.rom_state_destroy(None) == binding.ROM_E_ARG
+    assert L.rom_set_geometry_aux(None, 1, None, None) == binding.ROM_E_ARG
 
 
 def test_struct_layouts():
@@ -49,3 +50,5 @@ def test_struct_layouts():
     assert ctypes.sizeof(binding.RomOpts) == 48   # 2 doubles, 7 int32, 4 bytes tail padding
     assert binding.RomOpts.fp64_residual.offset == 40
     assert binding.INFO_DTYPE.itemsize == 32
+    # rom_aux_model: three int32, 4 bytes padding, six pointers
+    assert ctypes.sizeof(binding.RomAuxModel) == 16 + 6 * 8 and binding.RomAuxModel.mu_ref.offset == 16
