@@ -36,7 +36,7 @@ def device_path(name, steps, prec, sample, mlp=True):
     returns per step the sampled instances' Pbar, Abar and info, and the final state."""
     import torch
     from paper_2307_16894_gb300 import warmstart
-    rom, mu, coef, paths = workload.batch(name, steps=max(steps) + 1)
+    rom, mu, coef, paths = workload.batch(name)          # the 50-step paths, as the benchmark runs them
     B, d = len(coef), rom["d"]
     ctx = binding.Context(d, 0, torch_stream())
     ctx.load_basis(rom["G"])
