@@ -333,6 +333,43 @@ rom_status rom_mlp_predict(rom_ctx *ctx, const float *X_d, int64_t N, int bf16, 
 rom_status rom_features(rom_ctx *ctx, rom_state *st, const double *Fbar_d, float *X_d);
 
 /* ---------------------------------------------------------------------------
+ * Offline stage on the device (the offline stage of Algorithm 1; Sec. 3.1-3.2).  These calls
+ * take no context: device pointers on `cuda_stream` (a cudaStream_t, NULL = legacy default
+ * stream), library-owned scratch allocated and freed inside the call, blocking.  FP64
+ * arithmetic.  errbuf (errlen bytes, may be NULL) receives the text of an error.
+ *
+ * rom_pod: POD by the method of snapshots (Eq. pod_disp and the orthonormality relation after
+ * it).  S[ns][N] holds the ns snapshots (one per row).  The inner product is u^T M v with M the
+ * CSR matrix (rowptr[N+1], col[nnz], val[nnz]; e.g. the V^p Gram matrix of Eq. Vdotproduct),
+ * or, with rowptr = NULL, the diagonal wdiag[N] (the L^2 POD of the weighted stress), or the
+ * identity (both NULL).  C = S M S^T, C = V diag(lam) V^T (parallel cyclic Jacobi), and
+ * Phi[j][.] = sum_a V[a][j] S[a][.] / sqrt(lam_j) for j < n_modes, so Phi M Phi^T = I.
+ * lam[ns]: all eigenvalues, descending; sweeps (may be NULL): Jacobi sweeps used.
+ * 1 <= n_modes <= ns <= 1024; ROM_E_ARG if n_modes exceeds the numerical rank (eigenvalues
+ * above 1e-14 lam_0), ROM_E_NOMEM / ROM_E_CUDA otherwise on failure. */
+rom_status rom_pod(void *cuda_stream, int64_t N, int ns, const double *S, const int32_t *rowptr,
+                   const int32_t *col, const double *val, const double *wdiag, int n_modes, double *Phi,
+                   double *lam, int *sweeps, char *errbuf, size_t errlen);
+
+/* rom_ecm: the empirical cubature greedy (Sec. 3.2, Eq. integral_ecm).  F[P][M] holds P
+ * integrands at the M Gauss points of the parent mesh, wq[M] their Gauss weights (device).
+ * The integrand space is replaced by an orthonormal basis Z (eigenpairs of F diag(wq) F^T;
+ * directions with eigenvalue <= 1e-13 of the largest are dropped) to which the constant
+ * function scaled by volume_weight / sqrt(sum wq) is appended; b = Z wq.  Each step adds the
+ * point whose column is most aligned with the residual r = b - Z_E w_E (score Z[:,x].r /
+ * |Z[:,x]|, ties to the lower index) and refits non-negative weights on the selected set by
+ * least squares: a rank-one extension of the Cholesky factor of Z_E^T Z_E when every weight
+ * stays positive, else an active-set (Lawson-Hanson) solve; points whose weight is not positive
+ * leave the set.  It stops when m points are selected (m >= 1), or, with m < 1, when
+ * |r| <= tol |b|, and gives up after 20 m (or 20 M) steps.  Outputs on the host: idx[cap]
+ * (point indices in selection order), w[cap], m_out, err (= |r| / |b|, may be NULL), rank (the
+ * basis dimension, may be NULL).  1 <= P <= 1024, cap >= m.  ROM_E_NOT_CONVERGED if the greedy
+ * stalls (the outputs then hold its last state). */
+rom_status rom_ecm(void *cuda_stream, int P, int64_t M, const double *F, const double *wq, int m, double tol,
+                   double volume_weight, int cap, int64_t *idx, double *w, int *m_out, double *err, int *rank,
+                   char *errbuf, size_t errlen);
+
+/* ---------------------------------------------------------------------------
  * Allocation-free step.  The paper has no counterpart: this is a deployment
  * variant of rom_step_device for callers that cannot call cudaMalloc -- a
  * macro solver running inside a pre-sized memory pool or arena it does not

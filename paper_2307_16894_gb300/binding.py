@@ -27,7 +27,7 @@ EXPORTED = ["rom_create", "rom_destroy", "rom_load_basis", "rom_load_cubature", 
             "rom_step_noalloc", "rom_mlp_init", "rom_mlp_nparams", "rom_mlp_params", "rom_mlp_norm",
             "rom_mlp_train_step", "rom_mlp_loss_grad", "rom_mlp_predict", "rom_features", "rom_debug_stiffness",
             "rom_debug_tangent", "rom_debug_residual", "rom_use_graphs", "rom_sensitivity", "rom_sensitivity_device",
-            "rom_state_bytes", "rom_autotune", "rom_serve", "rom_set_geometry_aux"]
+            "rom_state_bytes", "rom_autotune", "rom_serve", "rom_set_geometry_aux", "rom_pod", "rom_ecm"]
 
 KERNEL_GROUPS = ["start", "constitutive", "assemble", "solve", "finalize", "bookkeeping", "learned_start", "force",
                  "sensitivity"]
@@ -81,6 +81,8 @@ def lib(path=None):
     L.rom_load_cubature.argtypes = [p, i, p, p, i, p, d]
     L.rom_set_geometry.argtypes = [p, i64, i, p, p]
     L.rom_set_geometry_aux.argtypes = [p, i64, p, p]
+    L.rom_pod.argtypes = [p, i64, i, p, p, p, p, p, i, p, p, p, p, ctypes.c_size_t]
+    L.rom_ecm.argtypes = [p, i, i64, p, p, i, d, d, i, p, p, p, p, p, p, ctypes.c_size_t]
     L.rom_state_create.argtypes = [p, i64, pp]
     L.rom_state_destroy.argtypes = [p]
     L.rom_state_export.argtypes = [p, p, p, p, p]
@@ -400,3 +402,49 @@ def serve(ctxs, states, opts, F, P, A=None, I=None):
     if st != ROM_OK:
         raise RomError("rom_serve failed with status %d: %s" % (st, L.rom_last_error(ctxs[0].h).decode()))
     return np.array(ms[:])
+
+
+# ---- offline stage on the device (context-free calls)
+def pod(S_d, n_modes, M=None, wdiag_d=None, stream=None):
+    """rom_pod on torch CUDA tensors: S_d [ns, N] (float64); M a scipy CSR matrix (copied to the
+    device) or None; wdiag_d [N] or None.  Returns (Phi [n_modes, N] tensor, lam [ns] tensor, sweeps)."""
+    import torch
+    L = lib()
+    ns, N = S_d.shape
+    dev = S_d.device
+    Phi = torch.empty((n_modes, N), dtype=torch.float64, device=dev)
+    lam = torch.empty(ns, dtype=torch.float64, device=dev)
+    keep = []
+    rp = cl = vl = None
+    if M is not None:
+        rp = torch.as_tensor(np.ascontiguousarray(M.indptr, dtype=np.int32), device=dev)
+        cl = torch.as_tensor(np.ascontiguousarray(M.indices, dtype=np.int32), device=dev)
+        vl = torch.as_tensor(np.ascontiguousarray(M.data, dtype=np.float64), device=dev)
+        keep += [rp, cl, vl]
+    sw = ctypes.c_int()
+    err = ctypes.create_string_buffer(512)
+    st = ctypes.c_void_p(stream if stream is not None else torch.cuda.current_stream().cuda_stream)
+    s = L.rom_pod(st, N, ns, _p(S_d.contiguous()), _p(rp), _p(cl), _p(vl), _p(wdiag_d), int(n_modes), _p(Phi),
+                  _p(lam), ctypes.byref(sw), err, len(err))
+    if s != ROM_OK:
+        raise RomError("rom_pod failed with status %d: %s" % (s, err.value.decode()))
+    return Phi, lam, sw.value
+
+
+def ecm(F_d, wq_d, m=None, tol=None, volume_weight=10.0, cap=None, stream=None):
+    """rom_ecm on torch CUDA tensors F_d [P, M], wq_d [M] (float64).  Returns (idx, w, err, rank)."""
+    import torch
+    L = lib()
+    P, Mq = F_d.shape
+    mm = int(m) if m is not None else 0
+    cap = int(cap or (mm if mm > 0 else min(Mq, 4096)))
+    idx = np.zeros(cap, np.int64)
+    w = np.zeros(cap)
+    mo, rk, er = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    err = ctypes.create_string_buffer(512)
+    st = ctypes.c_void_p(stream if stream is not None else torch.cuda.current_stream().cuda_stream)
+    s = L.rom_ecm(st, P, Mq, _p(F_d.contiguous()), _p(wq_d.contiguous()), mm, float(tol or 0.0), float(volume_weight),
+                  cap, _p(idx), _p(w), ctypes.byref(mo), ctypes.byref(er), ctypes.byref(rk), err, len(err))
+    if s != ROM_OK:
+        raise RomError("rom_ecm failed with status %d: %s" % (s, err.value.decode()))
+    return idx[:mo.value], w[:mo.value], er.value, rk.value

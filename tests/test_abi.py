@@ -43,6 +43,11 @@ def test_argument_errors_without_gpu(L):
     assert L.rom_step(None, None, None, None, None, None, None) == binding.ROM_E_ARG
     assert L.rom_state_destroy(None) == binding.ROM_E_ARG
     assert L.rom_set_geometry_aux(None, 1, None, None) == binding.ROM_E_ARG
+    err = ctypes.create_string_buffer(256)
+    assert L.rom_pod(None, 0, 1, None, None, None, None, None, 1, None, None, None, err, 256) == binding.ROM_E_ARG
+    assert b"rom_pod" in err.value
+    assert L.rom_ecm(None, 0, 10, None, None, 5, 0.0, 10.0, 5, None, None, None, None, None, err, 256) == binding.ROM_E_ARG
+    assert b"rom_ecm" in err.value
 
 
 def test_struct_layouts():
