@@ -83,6 +83,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg (and with it the accuracy check)")
     ap.add_argument("--no-fp64-arm", action="store_true", help="skip the plain-start FP64 GPU arm")
     ap.add_argument("--no-full-path", action="store_true", help="skip the run over all load steps of the paths")
+    ap.add_argument("--serve-budget-gb", type=float, default=None,
+                    help="ragged workload: device budget for the instances' states (default: 80%% of free memory)")
     ap.add_argument("--sample", type=int, default=None,
                     help="instances the oracle runs for the CPU baseline and the accuracy check "
                          "(default 16 for c3, 256 for c2)")
@@ -380,7 +382,8 @@ def run_serving(args, rank, world):
     B_total = args.batch or 65536
     W, K = args.warmup, args.steps
     groups = serving.make_groups(B_total, share_2d=0.75, steps=W + K, seed0=40_000 + rank * B_total)
-    srv = serving.Server(groups, precision=args.precision or "fp32", start=args.start)
+    budget = int(args.serve_budget_gb * 2 ** 30) if args.serve_budget_gb else None
+    srv = serving.Server(groups, precision=args.precision or "fp32", start=args.start, budget_bytes=budget)
     for k in range(W):
         srv.step(k)
     clocks = Clocks(int(os.environ.get("LOCAL_RANK", 0)))
@@ -395,11 +398,14 @@ def run_serving(args, rank, world):
     clk = clocks.stop()
     ms = float(np.sum(walls))
     lat = np.concatenate(lats)
-    desc = ["%s:B=%d,n=%d,m=%d,wave=%d" % (g["name"], g["B"], g["rom"]["n"], g["rom"]["m"], g["wave"]) for g in groups]
+    desc = ["%s:B=%d,n=%d,m=%d" % (g["name"], g["B"], g["rom"]["n"], g["rom"]["m"]) for g in groups]
+    chunks = ["%s[%d:%d]@wave%d" % (groups[c["group"]]["name"], c["start"], c["start"] + c["count"], c["wave"])
+              for c in srv.chunks]
+    waves = len(srv.waves)
     srv.close()
     return dict(value=B_total * world * K / (ms / 1e3), ms=ms, lat_p50=float(np.percentile(lat, 50)),
                 lat_p99=float(np.percentile(lat, 99)), iters=float(np.mean(its)), ok=ok, total=B_total * K,
-                groups=desc, clocks=clk)
+                groups=desc, chunks=chunks, waves=waves, budget=srv.budget, clocks=clk)
 
 
 def cpu_baseline(args, n_inst=None, n_steps=None, budget_s=20.0, idx=None, keep=False):
@@ -572,8 +578,10 @@ def main():
             line = dict(metric=metric, value=r["value"], unit=unit, n_gpus=world, steps=args.steps,
                         warmup=args.warmup, ms_per_step=r["ms"] / args.steps, higher_is_better=True,
                         scaling="weak", vs_baseline=None, dtype="f64+f32", data="synthetic",
-                        config=dict(workload="ragged: 2D n 16/24/32 m 100/150/200 + 3D n 48/64/96 m 400/650/900",
-                                    groups=r["groups"], converged=r["ok"], total=r["total"],
+                        config=dict(workload="ragged: 2D n 16/24/32 m 100/150/200 + 3D n 48/64/95 m 400/650/900",
+                                    groups=r["groups"], chunks=r["chunks"], waves=r["waves"],
+                                    state_budget_bytes=r["budget"], graph_launches_per_step=r["waves"],
+                                    converged=r["ok"], total=r["total"],
                                     newton_iters_mean=r["iters"], l2="working set >> L2"),
                         latency_ms=dict(p50=r["lat_p50"], p99=r["lat_p99"]), roofline=None, clocks=r["clocks"])
             print(json.dumps(line))

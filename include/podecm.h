@@ -249,10 +249,15 @@ rom_status rom_state_bytes(const rom_ctx *ctx, int64_t B, int64_t *bytes);
 rom_status rom_autotune(rom_ctx *ctx, rom_state *st, const rom_opts *opts, int *tile, int *chunk, float *ms);
 
 /* Ragged serving: one load step for G groups (each its own model/context, state, options
- * and device I/O buffers) issued together; each group runs as one graph launch on its
- * context's stream, so groups of different basis size n and cubature size m overlap on the
- * GPU.  group_ms[g] (may be NULL) = time from the common start to the end of group g.
- * Abar_d / info_d may be NULL.  Blocking. */
+ * and device I/O buffers; contexts and states distinct) as ONE CUDA-graph launch: the call
+ * captures every group's step (start, learned start, its own device-driven WHILE node over
+ * the Newton passes, finalize) on parallel branches of one graph, so groups of different
+ * basis size n, cubature size m and Newton iteration count run concurrently, each for as many
+ * passes as its instances need.  The graph is launched on ctxs[0]'s stream after the inputs
+ * are copied into the states' staging buffers; the outputs are copied back.  group_ms[g] (may
+ * be NULL) = time from the launch to the end of group g's branch (an event node).  Abar_d /
+ * info_d may be NULL (Abar_d[g] is needed when opts[g].want_abar).  Blocking; the graph is
+ * built and released inside the call (a few ms for a handful of groups). */
 rom_status rom_serve(int G, rom_ctx *const *ctxs, rom_state *const *sts, const rom_opts *opts,
                      const double *const *Fbar_d, double *const *Pbar_d, double *const *Abar_d,
                      rom_step_info *const *info_d, float *group_ms);

@@ -778,10 +778,10 @@ static bool o_needs_recapture(const rom_state *st, const rom_opts *opts) {
 // node: the device decides how many passes to run (no host round trip per pass).  The graph
 // reads Fbar from and writes Pbar / Abar / info to buffers owned by the state, so one
 // instantiation serves every later step with the same options.
-static rom_status capture_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts) {
-    if (st->gexec) { cudaGraphExecDestroy(st->gexec); st->gexec = nullptr; }
-    st->g_valid = false;
-    if (!st->gstream) CK(cudaStreamCreateWithFlags(&st->gstream, cudaStreamNonBlocking));
+// Record the launches of one load step (start, learned start, the WHILE node over the Newton
+// passes, the FP32-accurate Abar assembly, finalize) on `cs`, which must be capturing.  Returns
+// a CUDA error (cudaSuccess if recorded) and sets *bad if a launch configuration was refused.
+static cudaError_t record_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts, cudaStream_t cs, int *bad_out) {
     StepOpts o;
     o.tol_rel = opts->tol_rel; o.tol_abs = opts->tol_abs; o.max_iter = opts->max_iter; o.max_ls = opts->max_ls;
     o.precision = opts->precision; o.start = opts->start; o.polar = opts->polar_split; o.want_abar = opts->want_abar;
@@ -792,9 +792,6 @@ static rom_status capture_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts
     bt.mu = ctx->mu;
     bt.err = ctx->d_err;
     const int max_pass = (opts->max_iter + 1) * (opts->max_ls + 1) + 2;
-    cudaStream_t cs = st->gstream;
-    cudaGraph_t graph = nullptr;
-    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     int bad = 0;
     if (ctx->d_err) cudaMemsetAsync(ctx->d_err, 0, 4, cs);   // tensor-core error flag of this step
     bad |= launch_start(M, bt, st->io_F, o, nullptr, cs);
@@ -847,6 +844,19 @@ static rom_status capture_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts
         bad |= launch_abar_assembly(ctx, M, bc, o, st->list2, cs);
     }
     if (e == cudaSuccess) bad |= launch_finalize(M, bt, o, st->io_P, st->io_A, st->io_info, cs);
+    *bad_out = bad;
+    return e;
+}
+
+static rom_status capture_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts) {
+    if (st->gexec) { cudaGraphExecDestroy(st->gexec); st->gexec = nullptr; }
+    st->g_valid = false;
+    if (!st->gstream) CK(cudaStreamCreateWithFlags(&st->gstream, cudaStreamNonBlocking));
+    cudaStream_t cs = st->gstream;
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    int bad = 0;
+    cudaError_t e = record_step(ctx, st, opts, cs, &bad);
     cudaError_t e3 = cudaStreamEndCapture(cs, &graph);
     if (e == cudaSuccess) e = e3;
     if (e != cudaSuccess || bad) {
@@ -1151,32 +1161,93 @@ rom_status rom_serve(int G, rom_ctx *const *ctxs, rom_state *const *sts, const r
                      rom_step_info *const *info_d, float *group_ms) {
     if (G < 1 || !ctxs || !sts || !opts || !Fbar_d || !Pbar_d) return ROM_E_ARG;
     rom_ctx *ctx = ctxs[0];
-    for (int g = 0; g < G; ++g)
-        if (!ctxs[g] || !sts[g] || ctxs[g]->device != ctx->device) return ROM_E_ARG;
-    CK(cudaSetDevice(ctx->device));
-    std::vector<cudaEvent_t> ev(G + 1);
-    for (auto &e : ev) CK(cudaEventCreate(&e));
-    CK(cudaEventRecord(ev[G], ctx->stream));
-    rom_status s = ROM_OK;
-    for (int g = 0; g < G && s == ROM_OK; ++g) {
-        rom_ctx *c = ctxs[g];
-        if (c->stream != ctx->stream) CK(cudaStreamWaitEvent(c->stream, ev[G], 0));
-        const bool gr = c->graphs;
-        c->graphs = true;
-        s = rom_step_device(c, sts[g], &opts[g], Fbar_d[g], Pbar_d[g], Abar_d ? Abar_d[g] : nullptr,
-                            info_d ? info_d[g] : nullptr);
-        c->graphs = gr;
-        if (s == ROM_OK) CK(cudaEventRecord(ev[g], c->stream));
-        else ctx->err = c->err;
+    if (!ctx) return ROM_E_ARG;
+    for (int g = 0; g < G; ++g) {
+        if (!ctxs[g] || !sts[g] || ctxs[g]->device != ctx->device || sts[g]->ctx != ctxs[g]) return ROM_E_ARG;
+        for (int h = 0; h < g; ++h)   // the branches of the graph must not share work buffers
+            if (sts[h] == sts[g] || ctxs[h] == ctxs[g])
+                return fail(ctx, ROM_E_ARG, "rom_serve: groups %d and %d share a context or state", h, g);
+        rom_status s = check_step(ctxs[g], sts[g], &opts[g]);
+        if (s != ROM_OK) { ctx->err = ctxs[g]->err; return s; }
+        if (opts[g].start == ROM_START_MLP && (s = ensure_feat(ctxs[g], sts[g]->B)) != ROM_OK) { ctx->err = ctxs[g]->err; return s; }
+        if (!Fbar_d[g] || !Pbar_d[g] || (opts[g].want_abar && (!Abar_d || !Abar_d[g])))
+            return fail(ctx, ROM_E_ARG, "rom_serve: null buffer of group %d", g);
     }
-    if (s == ROM_OK) {
-        for (int g = 0; g < G; ++g) {
-            CK(cudaEventSynchronize(ev[g]));
-            if (group_ms) CK(cudaEventElapsedTime(&group_ms[g], ev[G], ev[g]));
+    CK(cudaSetDevice(ctx->device));
+    for (int g = 0; g < G; ++g) {
+        sts[g]->last_prec = opts[g].precision;
+        if (!sts[g]->gstream) CK(cudaStreamCreateWithFlags(&sts[g]->gstream, cudaStreamNonBlocking));
+    }
+    // one graph for every group: fork from the first group's capture stream, each group's step
+    // (its own device-driven WHILE node over the Newton passes) on its own branch, an event node
+    // at the end of each branch, join
+    std::vector<cudaEvent_t> ev_done(G), ev_join(G);
+    cudaEvent_t ev_fork = nullptr, ev_start = nullptr;
+    auto destroy_events = [&] {
+        for (auto &e : ev_done) if (e) cudaEventDestroy(e);
+        for (auto &e : ev_join) if (e) cudaEventDestroy(e);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_start) cudaEventDestroy(ev_start);
+    };
+    cudaError_t e = cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev_start);
+    for (int g = 0; g < G && e == cudaSuccess; ++g) {
+        e = cudaEventCreate(&ev_done[g]);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_join[g], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) { destroy_events(); return fail(ctx, ROM_E_CUDA, "rom_serve: %s", cudaGetErrorString(e)); }
+    cudaStream_t origin = sts[0]->gstream;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int bad = 0;
+    e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_fork, origin);
+    for (int g = 0; g < G && e == cudaSuccess; ++g) {
+        cudaStream_t cs = sts[g]->gstream;
+        if (g > 0) e = cudaStreamWaitEvent(cs, ev_fork, 0);
+        int b = 0;
+        if (e == cudaSuccess) e = record_step(ctxs[g], sts[g], &opts[g], cs, &b);
+        bad |= b;
+        if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev_done[g], cs, cudaEventRecordExternal);
+        if (e == cudaSuccess && g > 0) {
+            e = cudaEventRecord(ev_join[g], cs);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(origin, ev_join[g], 0);
         }
     }
-    for (auto &e : ev) cudaEventDestroy(e);
-    return s;
+    cudaError_t e2 = cudaStreamEndCapture(origin, &graph);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess && !bad) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess || bad) {
+        cudaGetLastError();
+        destroy_events();
+        return fail(ctx, ROM_E_CUDA, "rom_serve: graph of %d groups: %s", G,
+                    e != cudaSuccess ? cudaGetErrorString(e) : "launch configuration");
+    }
+    // inputs into the states' staging buffers, one launch for all groups, outputs back
+    cudaStream_t L = ctx->stream;
+    for (int g = 0; g < G && e == cudaSuccess; ++g) {
+        const int d2 = ctxs[g]->dim * ctxs[g]->dim;
+        e = cudaMemcpyAsync(sts[g]->io_F, Fbar_d[g], (size_t)sts[g]->B * d2 * 8, cudaMemcpyDeviceToDevice, L);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ev_start, L);
+    if (e == cudaSuccess) e = cudaGraphLaunch(exec, L);
+    for (int g = 0; g < G && e == cudaSuccess; ++g) {
+        const int d2 = ctxs[g]->dim * ctxs[g]->dim;
+        const size_t B = (size_t)sts[g]->B;
+        e = cudaMemcpyAsync(Pbar_d[g], sts[g]->io_P, B * d2 * 8, cudaMemcpyDeviceToDevice, L);
+        if (e == cudaSuccess && opts[g].want_abar)
+            e = cudaMemcpyAsync(Abar_d[g], sts[g]->io_A, B * d2 * d2 * 8, cudaMemcpyDeviceToDevice, L);
+        if (e == cudaSuccess && info_d && info_d[g])
+            e = cudaMemcpyAsync(info_d[g], sts[g]->io_info, B * sizeof(rom_step_info), cudaMemcpyDeviceToDevice, L);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(L);
+    for (int g = 0; g < G && e == cudaSuccess; ++g)
+        if (group_ms) e = cudaEventElapsedTime(&group_ms[g], ev_start, ev_done[g]);
+    cudaGraphExecDestroy(exec);
+    destroy_events();
+    if (e != cudaSuccess) return fail(ctx, ROM_E_CUDA, "rom_serve: %s", cudaGetErrorString(e));
+    return ROM_OK;
 }
 
 rom_status rom_use_graphs(rom_ctx *ctx, int enable) {

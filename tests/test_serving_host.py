@@ -31,3 +31,30 @@ def test_make_groups_split_and_seeds():
         assert np.array_equal(g["coef"], inputs.map_coefficients(d, g["mu"]))
         b0 += g["B"]
     assert n3 >= 0
+
+
+def test_plan_waves_budget():
+    """Admission by footprint: every instance lands in exactly one wave, in group order; each
+    wave's states fit the budget; a group that does not fit is split at the budget boundary."""
+    import pytest
+    rng = np.random.default_rng(4)
+    for _ in range(20):
+        G = int(rng.integers(1, 7))
+        sizes = [int(x) for x in rng.integers(1, 300, G)]
+        per = [int(x) for x in rng.integers(10, 500, G)]
+        budget = int(rng.integers(max(per), 40 * max(per)))
+        waves = serving.plan_waves(sizes, per, budget)
+        seen = [np.zeros(B, int) for B in sizes]
+        order = []
+        for wave in waves:
+            assert wave and sum(cnt * per[g] for g, s0, cnt in wave) <= budget
+            for g, s0, cnt in wave:
+                assert cnt >= 1
+                seen[g][s0:s0 + cnt] += 1
+                order.append((g, s0))
+        assert all((s == 1).all() for s in seen)
+        assert order == sorted(order)
+    assert serving.plan_waves([10, 5], [100, 200], 10 ** 6) == [[(0, 0, 10), (1, 0, 5)]]
+    assert serving.plan_waves([10], [100], 350) == [[(0, 0, 3)], [(0, 3, 3)], [(0, 6, 3)], [(0, 9, 1)]]
+    with pytest.raises(ValueError):
+        serving.plan_waves([2], [500], 499)
