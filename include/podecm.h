@@ -374,6 +374,43 @@ rom_status rom_ecm(void *cuda_stream, int P, int64_t M, const double *F, const d
                    double volume_weight, int cap, int64_t *idx, double *w, int *m_out, double *err, int *rank,
                    char *errbuf, size_t errlen);
 
+/* rom_fe_train: the full-order training solves of the offline stage (Sec. 2.1: Eqs.
+ * weakform-dep-mapped, Dweakform-dep and full_newton) for S samples at once, each with its own
+ * geometry (F_mu = I + sum_k coef[s][k] Gmu[q][.][k] at the Gauss points) and load path
+ * Fbar[s][steps][d*d].  The mesh is given by its elements: edof[ne][nen*d] (global fluctuation
+ * dof of each element dof, -1 where fixed), the reference shape-function gradients
+ * dN[ngp][nen][d] with respect to X^p and the Gauss weights gw[ngp] (the same for every
+ * element of the structured grid), el_phase[ne] into phases[n_phase].  Each load step starts
+ * from the previous solution; Newton stops at ||f|| <= max(tol_rel ||f_0||, tol_abs) (at most
+ * max_iter iterations, backtracking line search on ||f||, halving up to 10 times), the linear
+ * systems are solved by Jacobi-preconditioned conjugate gradients to 1e-12 relative; a step
+ * whose Newton fails is split into half increments, at most max_split times.  Outputs (host):
+ * w[S][steps][ndof] the fluctuation snapshots, W[S][steps][ne*ngp][d*d] (may be NULL) the
+ * weighted stress J P F_mu^-T at the Gauss points, Pbar[S][steps][d*d] (|Omega^p| = 1),
+ * iters / substeps [S][steps] (may be NULL).  All host buffers; device work arrays are
+ * allocated and freed inside the call; blocking.  ROM_E_NOT_CONVERGED if a step still fails
+ * after max_split splits. */
+typedef struct {
+    int32_t d, ne, nen, ngp, ndof;
+    const int32_t *edof;
+    const double *dN, *gw;
+    const int32_t *el_phase;
+} rom_fe_mesh;
+rom_status rom_fe_train(const rom_fe_mesh *mesh, int n_phase, const rom_phase *phases, int S, int n_par,
+                        const double *Gmu, const double *coef, int steps, const double *Fbar, double tol_rel,
+                        double tol_abs, int max_iter, int max_split, double *w, double *W, double *Pbar,
+                        int32_t *iters, int32_t *substeps, char *errbuf, size_t errlen);
+
+/* rom_ecm_integrands: the integrands of the cubature fit (Eq. integral_ecm) on the device.
+ * Phi[n][ndof] (device): the fluctuation modes; B[L][ne*ngp][d*d] (device): the weighted-stress
+ * modes at the Gauss points.  Outputs (device): gradPhi[ne*ngp][d*d][n] = dphi_i/dX^p at every
+ * Gauss point (row-major vec, component-major) and F[n*L][ne*ngp] with F[i*L+l][q] =
+ * dphi_i/dX^p : B_l at Gauss point q.  The mesh (host arrays, see rom_fe_train) is copied.
+ * Blocking. */
+rom_status rom_ecm_integrands(void *cuda_stream, const rom_fe_mesh *mesh, int n, const double *Phi, int L,
+                              const double *B, double *gradPhi, double *F, char *errbuf, size_t errlen);
+
+
 /* ---------------------------------------------------------------------------
  * Allocation-free step.  The paper has no counterpart: this is a deployment
  * variant of rom_step_device for callers that cannot call cudaMalloc -- a

@@ -27,7 +27,8 @@ EXPORTED = ["rom_create", "rom_destroy", "rom_load_basis", "rom_load_cubature", 
             "rom_step_noalloc", "rom_mlp_init", "rom_mlp_nparams", "rom_mlp_params", "rom_mlp_norm",
             "rom_mlp_train_step", "rom_mlp_loss_grad", "rom_mlp_predict", "rom_features", "rom_debug_stiffness",
             "rom_debug_tangent", "rom_debug_residual", "rom_use_graphs", "rom_sensitivity", "rom_sensitivity_device",
-            "rom_state_bytes", "rom_autotune", "rom_serve", "rom_set_geometry_aux", "rom_pod", "rom_ecm"]
+            "rom_state_bytes", "rom_autotune", "rom_serve", "rom_set_geometry_aux", "rom_pod", "rom_ecm",
+            "rom_fe_train", "rom_ecm_integrands"]
 
 KERNEL_GROUPS = ["start", "constitutive", "assemble", "solve", "finalize", "bookkeeping", "learned_start", "force",
                  "sensitivity"]
@@ -57,6 +58,12 @@ class RomAuxModel(ctypes.Structure):
                 ("S", ctypes.c_void_p), ("GL", ctypes.c_void_p), ("Gpsi", ctypes.c_void_p)]
 
 
+class RomFeMesh(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int32), ("ne", ctypes.c_int32), ("nen", ctypes.c_int32), ("ngp", ctypes.c_int32),
+                ("ndof", ctypes.c_int32), ("edof", ctypes.c_void_p), ("dN", ctypes.c_void_p), ("gw", ctypes.c_void_p),
+                ("el_phase", ctypes.c_void_p)]
+
+
 class RomError(RuntimeError):
     pass
 
@@ -82,6 +89,8 @@ def lib(path=None):
     L.rom_set_geometry.argtypes = [p, i64, i, p, p]
     L.rom_set_geometry_aux.argtypes = [p, i64, p, p]
     L.rom_pod.argtypes = [p, i64, i, p, p, p, p, p, i, p, p, p, p, ctypes.c_size_t]
+    L.rom_fe_train.argtypes = [p, i, p, i, i, p, p, i, p, d, d, i, i, p, p, p, p, p, p, ctypes.c_size_t]
+    L.rom_ecm_integrands.argtypes = [p, p, i, p, i, p, p, p, p, ctypes.c_size_t]
     L.rom_ecm.argtypes = [p, i, i64, p, p, i, d, d, i, p, p, p, p, p, p, ctypes.c_size_t]
     L.rom_state_create.argtypes = [p, i64, pp]
     L.rom_state_destroy.argtypes = [p]
@@ -448,3 +457,65 @@ def ecm(F_d, wq_d, m=None, tol=None, volume_weight=10.0, cap=None, stream=None):
     if s != ROM_OK:
         raise RomError("rom_ecm failed with status %d: %s" % (s, err.value.decode()))
     return idx[:mo.value], w[:mo.value], er.value, rk.value
+
+
+def _phase_array(phases):
+    arr = (RomPhase * len(phases))()
+    for k, ph in enumerate(phases):
+        arr[k] = RomPhase(ph["E"], ph["nu"], 1 if ph.get("law", "power") == "power" else 0, ph["s0"], ph["k"],
+                          ph.get("p", 1.0))
+    return arr
+
+
+def fe_mesh(grid):
+    """rom_fe_mesh of a mesh.Grid (the arrays are kept alive on the returned structure)"""
+    keep = [np.ascontiguousarray(grid.edof, np.int32), _f64(grid.dN), _f64(grid.gw),
+            np.ascontiguousarray(grid.el_phase, np.int32)]
+    m = RomFeMesh(grid.d, grid.ne, grid.nen, grid.ngp, grid.ndof, *[k.ctypes.data for k in keep])
+    m._keep = keep
+    return m
+
+
+def fe_train(grid, phases, Gq, coef, paths, tol_rel=1e-10, tol_abs=1e-9, max_iter=40, max_split=8, want_W=True):
+    """rom_fe_train: full-order training solves of S samples.  Gq [nq, d, d, n_par], coef [S, n_par],
+    paths [S, steps, d, d] (host).  Returns dict(w [S, steps, ndof], W [S, steps, nq, d*d] or None,
+    Pbar [S, steps, d, d], iters, substeps)."""
+    L = lib()
+    d = grid.d
+    coef = _f64(np.atleast_2d(coef))
+    paths = _f64(paths)
+    S, steps = paths.shape[:2]
+    n_par = coef.shape[1]
+    Gq = _f64(Gq).reshape(grid.nq, d * d, n_par)
+    w = np.zeros((S, steps, grid.ndof))
+    W = np.zeros((S, steps, grid.nq, d * d)) if want_W else None
+    Pbar = np.zeros((S, steps, d, d))
+    its = np.zeros((S, steps), np.int32)
+    sub = np.zeros((S, steps), np.int32)
+    m = fe_mesh(grid)
+    arr = _phase_array(phases)
+    err = ctypes.create_string_buffer(512)
+    st = L.rom_fe_train(ctypes.byref(m), len(phases), ctypes.cast(arr, ctypes.c_void_p), S, n_par, _p(Gq), _p(coef),
+                        steps, _p(paths), float(tol_rel), float(tol_abs), int(max_iter), int(max_split), _p(w), _p(W),
+                        _p(Pbar), _p(its), _p(sub), err, len(err))
+    if st != ROM_OK:
+        raise RomError("rom_fe_train failed with status %d: %s" % (st, err.value.decode()))
+    return dict(w=w, W=W, Pbar=Pbar, iters=its, substeps=sub)
+
+
+def ecm_integrands(grid, Phi_d, B_d, stream=None):
+    """rom_ecm_integrands on torch CUDA tensors Phi_d [n, ndof], B_d [L, nq, d*d]; returns
+    (gradPhi [nq, d*d, n], F [n*L, nq]) tensors."""
+    import torch
+    L = lib()
+    n, Lm = Phi_d.shape[0], B_d.shape[0]
+    gradPhi = torch.empty((grid.nq, grid.d * grid.d, n), dtype=torch.float64, device=Phi_d.device)
+    F = torch.empty((n * Lm, grid.nq), dtype=torch.float64, device=Phi_d.device)
+    m = fe_mesh(grid)
+    err = ctypes.create_string_buffer(512)
+    st = ctypes.c_void_p(stream if stream is not None else torch.cuda.current_stream().cuda_stream)
+    s = L.rom_ecm_integrands(st, ctypes.byref(m), n, _p(Phi_d.contiguous()), Lm, _p(B_d.contiguous()), _p(gradPhi),
+                             _p(F), err, len(err))
+    if s != ROM_OK:
+        raise RomError("rom_ecm_integrands failed with status %d: %s" % (s, err.value.decode()))
+    return gradPhi, F

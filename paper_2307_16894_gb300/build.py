@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpodecm.so")
 SOURCES = ["kernels.cu", "rom_abi.cu", "rom_noalloc.cu", "mlp.cu", "tc_assemble.cu", "tc_assemble3.cu",
-           "aux_geometry.cu", "offline.cu"]
+           "aux_geometry.cu", "offline.cu", "fe_train.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]

@@ -862,3 +862,64 @@ extern "C" rom_status rom_ecm(void *cuda_stream, int P, int64_t M, const double 
                         err, tol, n_sel);
     return ROM_OK;
 }
+
+// ------------------------------------------------------------------ ECM integrands
+namespace podecm {
+// gradPhi[q][c][i] = sum_a Phi_i[dof(a, comp)] dN[g][a][r], c = comp * d + r, q = e * ngp + g
+__global__ void k_mode_gradients(int d, int ne, int nen, int ngp, int ndof, int n, const int32_t *__restrict__ edof,
+                                 const double *__restrict__ dN, const double *__restrict__ Phi, double *__restrict__ gradPhi) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nq = (int64_t)ne * ngp;
+    if (t >= nq * n) return;
+    const int i = (int)(t / nq);
+    const int64_t q = t - (int64_t)i * nq;
+    const int e = (int)(q / ngp), g = (int)(q - (int64_t)e * ngp);
+    const int d2 = d * d;
+    for (int comp = 0; comp < d; ++comp)
+        for (int r = 0; r < d; ++r) {
+            double s = 0.0;
+            for (int a = 0; a < nen; ++a) {
+                const int32_t k = edof[(size_t)e * nen * d + a * d + comp];
+                if (k >= 0) s = fma(Phi[(size_t)i * ndof + k], dN[((size_t)g * nen + a) * d + r], s);
+            }
+            gradPhi[((size_t)q * d2 + comp * d + r) * n + i] = s;
+        }
+}
+
+// F[i * L + l][q] = sum_c gradPhi[q][c][i] B[l][q][c]  (Eq. integral_ecm: the N L products)
+__global__ void k_integrands(int d2, int64_t nq, int n, int L, const double *__restrict__ gradPhi,
+                             const double *__restrict__ B, double *__restrict__ F) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nq * n * L) return;
+    const int row = (int)(t / nq);
+    const int64_t q = t - (int64_t)row * nq;
+    const int i = row / L, l = row - i * L;
+    double s = 0.0;
+    for (int c = 0; c < d2; ++c) s = fma(gradPhi[((size_t)q * d2 + c) * n + i], B[((size_t)l * nq + q) * d2 + c], s);
+    F[t] = s;
+}
+}  // namespace podecm
+
+extern "C" rom_status rom_ecm_integrands(void *cuda_stream, const rom_fe_mesh *mesh, int n, const double *Phi, int L,
+                                         const double *B, double *gradPhi, double *F, char *errbuf, size_t errlen) {
+    if (!mesh || !mesh->edof || !mesh->dN || n < 1 || L < 1 || !Phi || !B || !gradPhi || !F ||
+        (mesh->d != 2 && mesh->d != 3) || mesh->ne < 1 || mesh->nen < 1 || mesh->ngp < 1)
+        return off_fail(errbuf, errlen, ROM_E_ARG, "rom_ecm_integrands: bad arguments");
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const int d = mesh->d, nd = mesh->nen * d;
+    const int64_t nq = (int64_t)mesh->ne * mesh->ngp;
+    Scratch sc;
+    int32_t *edof = sc.get<int32_t>((size_t)mesh->ne * nd);
+    double *dN = sc.get<double>((size_t)mesh->ngp * mesh->nen * d);
+    if (sc.err != cudaSuccess) return off_fail(errbuf, errlen, ROM_E_NOMEM, "rom_ecm_integrands: %s", cudaGetErrorString(sc.err));
+    cudaError_t e = cudaMemcpyAsync(edof, mesh->edof, (size_t)mesh->ne * nd * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dN, mesh->dN, (size_t)mesh->ngp * mesh->nen * d * 8, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return off_fail(errbuf, errlen, ROM_E_CUDA, "rom_ecm_integrands: %s", cudaGetErrorString(e));
+    k_mode_gradients<<<blocks(nq * n, 128), 128, 0, s>>>(d, mesh->ne, mesh->nen, mesh->ngp, mesh->ndof, n, edof, dN, Phi,
+                                                         gradPhi);
+    k_integrands<<<blocks(nq * n * L, 256), 256, 0, s>>>(d * d, nq, n, L, gradPhi, B, F);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return off_fail(errbuf, errlen, ROM_E_CUDA, "rom_ecm_integrands: %s", cudaGetErrorString(e));
+    return ROM_OK;
+}

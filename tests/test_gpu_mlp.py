@@ -106,3 +106,62 @@ def test_learned_start_same_answer_fewer_iterations():
     assert np.mean(it_mlp) < np.mean(it_plain)
     h.close()
     pl.close()
+
+
+def test_learned_start_beats_previous_step_predictor_c3():
+    """The trained network of the 3D workload (data/mlp_c3.npz, trained on instances 30000 and
+    up) on held-out instances of the workload (B = 4096, the 50-step paths), TF32 stiffness in
+    graph mode: over load steps 12-24, where the plastic zone grows, it needs fewer Newton
+    iterations and less time than the previous-step predictor (the method without it); the two
+    starts are stepped alternately so that both see the same GPU conditions.  The converged Pbar
+    of sampled instances matches the FP64 oracle within 1e-7 at every step."""
+    import os
+    import torch
+    path = os.path.join(workload.DATA, "mlp_c3.npz")
+    if not os.path.exists(path):
+        pytest.skip("trained network absent")
+    rom, mu, coef, paths = workload.batch("c3", B=4096)
+    B, d = len(coef), 3
+    runs = {}
+    for start in ("prev", "mlp"):
+        ctx = binding.Context(d, 0, torch_stream())
+        ctx.load_basis(rom["G"])
+        ctx.load_cubature(rom["w"], rom["phase"], rom["phases"], rom["omega"])
+        ctx.set_geometry(rom["Gmu"], coef)
+        if start == "mlp":
+            warmstart.load_into(ctx, path, B)
+        ctx.use_graphs(True)
+        runs[start] = dict(ctx=ctx, st=ctx.state_create(B),
+                           opts=binding.make_opts(tol_rel=1e-9, tol_abs=rom["tol_abs"], max_iter=50, max_ls=6,
+                                                  precision="tf32", start=start),
+                           P=torch.empty((B, d, d), dtype=torch.float64, device="cuda"),
+                           A=torch.empty((B, 81), dtype=torch.float64, device="cuda"),
+                           I=torch.empty((B, binding.INFO_DTYPE.itemsize), dtype=torch.uint8, device="cuda"),
+                           its=[], ms=0.0)
+    Fd = torch.from_numpy(np.ascontiguousarray(paths.transpose(1, 0, 2, 3))).cuda()
+    sample = np.array([0, 1365, 2730, B - 1])
+    o = OracleRun(rom, coef[sample])
+    for k in range(25):
+        ref = o.step(paths[sample, k], tol_rel=1e-10, tol_abs=rom["tol_abs"], max_iter=25, start="prev")
+        for start, r in runs.items():
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            r["ctx"].step_device(r["st"], r["opts"], Fd[k], r["P"], r["A"], r["I"])
+            e1.record()
+            torch.cuda.synchronize()
+            info = np.frombuffer(r["I"].cpu().numpy().tobytes(), dtype=binding.INFO_DTYPE)
+            assert (info["status"] == 0).all(), (start, k)
+            ok = ref["status"] == 0
+            assert rel(r["P"].cpu().numpy()[sample][ok], ref["Pbar"][ok]) <= 1e-7, (start, k)
+            if k >= 12:
+                r["its"].append(info["iters"].mean())
+                r["ms"] += e0.elapsed_time(e1)
+    ip, im = np.mean(runs["prev"]["its"]), np.mean(runs["mlp"]["its"])
+    tp, tm = runs["prev"]["ms"], runs["mlp"]["ms"]
+    print("c3 steps 12-24, B=%d: Newton iterations prev %.4f, learned %.4f; time prev %.1f ms, learned %.1f ms"
+          % (B, ip, im, tp, tm))
+    for r in runs.values():
+        r["st"].close()
+        r["ctx"].close()
+    assert im < ip - 0.02
+    assert tm < tp

@@ -135,3 +135,71 @@ def test_ecm_synthetic_larger(M, P, m, kmax):
           "device %.3f s, oracle %.3f s" % (P, M, m, rank, same, m, err_d, err_o, t_d, t_o))
     assert list(sel_d) == list(sel_o)
     assert np.abs(w_d - w_o).max() <= 1e-8 * w_o.max()
+
+
+def a1_samples():
+    """the training samples of the 2D auxiliary-map family (seeded as in the oracle's build)"""
+    from paper_2307_16894_gb300 import inputs, mesh
+    cfg = build_roms.CONFIGS["a1"]
+    ofe = fe.Mesh(2, cfg["N"], build_roms.phase_2d)
+    Gq, coef_of = build_roms.map_fields(cfg, ofe)
+    coefs, paths = [], []
+    for kind, seed, nst in cfg["train"]:
+        mu = np.random.default_rng(seed).uniform(*cfg["mu_range"], size=1)
+        coefs.append(coef_of(mu))
+        paths.append(inputs.training_path_2d(seed, nst))
+    return cfg, mesh.Grid(2, cfg["N"], build_roms.phase_2d), Gq, np.array(coefs), np.array(paths)
+
+
+def test_device_training_solves_match_oracle(a1_offline):
+    """rom_fe_train (three samples solved together) against the oracle's full-order path solver on
+    the same samples: fluctuation and weighted-stress snapshots of every load step."""
+    cfg, grid, Gq, coefs, paths = a1_samples()
+    _, _, S_o, SW_o = a1_offline
+    t0 = time.perf_counter()
+    out = binding.fe_train(grid, cfg["phases"], Gq, coefs, paths)
+    t_d = time.perf_counter() - t0
+    w = out["w"].reshape(-1, grid.ndof)
+    W = out["W"].reshape(len(SW_o), -1)
+    ew = np.abs(w - S_o).max() / np.abs(S_o).max()
+    eW = np.abs(W - SW_o).max() / np.abs(SW_o).max()
+    print("training solves (3 samples x 20 steps, %d dofs): w %.2e, W %.2e, Newton its %s; device %.2f s"
+          % (grid.ndof, ew, eW, np.bincount(out["iters"].ravel()), t_d))
+    assert ew < 1e-8 and eW < 1e-8
+
+
+def _orbit_keys(X):
+    """the points up to the 8 symmetries of the square cell about its centre (the unit cell with
+    a centred void is invariant under them)"""
+    keys = []
+    for x, y in X - 0.5:
+        imgs = [(a * u, b * v) for u, v in ((x, y), (y, x)) for a in (1, -1) for b in (1, -1)]
+        keys.append(min((round(p * 1e9), round(q * 1e9)) for p, q in imgs))
+    return sorted(keys)
+
+
+def test_device_offline_build_matches_model_file():
+    """The whole offline stage on the device (training solves, both PODs, integrands, ECM) for the
+    2D auxiliary-map family against the oracle-built model file.  The cell with its centred void
+    is symmetric under the 8 symmetries of the square, so mirror-image cubature candidates tie
+    exactly and rounding at the 1e-14 level decides between them (the oracle's own greedy picks
+    other mirror images when its snapshots are perturbed by 1e-14).  Compared: the ECM error (to
+    1e-8), the total weight, the selected points up to the symmetries of the cell, and, on the
+    points both selections share, the basis gradients up to the sign of each mode."""
+    from paper_2307_16894_gb300 import offline, workload
+    cfg, grid, Gq, coefs, paths = a1_samples()
+    t0 = time.perf_counter()
+    rom, tr = offline.build(grid, cfg["phases"], Gq, coefs, paths, n=cfg["n"], L=cfg["L"], m=cfg["m"])
+    t_d = time.perf_counter() - t0
+    ref = workload.load_model("rom_a1")
+    same = [i for i in rom["qp_index"] if i in set(ref["qp_index"])]
+    print("offline stage on the device: %.2f s; ECM error %.6e (model file %.6e); %d of %d points shared, the rest "
+          "mirror images" % (t_d, rom["ecm_err"], ref["ecm_err"], len(same), len(ref["qp_index"])))
+    assert abs(rom["ecm_err"] - ref["ecm_err"]) <= 1e-8 * ref["ecm_err"]
+    assert abs(rom["w"].sum() - ref["w"].sum()) <= 1e-9
+    assert _orbit_keys(rom["X"]) == _orbit_keys(ref["X"])
+    a = [list(rom["qp_index"]).index(i) for i in same]
+    b = [list(ref["qp_index"]).index(i) for i in same]
+    Gd, Gr = rom["G"][a], ref["G"][b]
+    sgn = np.sign(np.einsum("icj,icj->j", Gd, Gr))
+    assert np.abs(Gd * sgn - Gr).max() <= 1e-6 * np.abs(Gr).max()
