@@ -176,8 +176,8 @@ def load_workload(args, first=0, B=None):
 
 def solver_opts(args, rom):
     # default: FP64 return map, eigen log/exp, stresses and convergence test; the residual of the
-    # tensor-core paths in double-float FP32 pairs (--fp64-residual: FP64); the 3D stiffness in
-    # TF32 on the tensor cores, the 2D stiffness in FP32 on the CUDA cores
+    # tensor-core paths in double-float FP32 pairs (--fp64-residual: FP64); the stiffness on the
+    # tensor cores: the 3D one in TF32, the 2D one FP32-accurate (TF32 hi/lo split)
     prec = args.precision or ("tf32" if args.workload == "c3" else "fp32")
     tol_rel = 1e-10 if prec == "fp64" else 1e-9
     max_iter = 25 if prec == "fp64" else 50
@@ -520,11 +520,11 @@ def kernel_rooflines(r, peaks):
         traffic = (points / nl * CONST_DRAM_BYTES_PER_POINT[key]) if key in CONST_DRAM_BYTES_PER_POINT else None
         add("constitutive", "alu", points * CONST_FP64_FLOP_PER_POINT[key], FP64_PEAK_TFLOPS,
             "FP64 pipe: 152 SM x 2 DFMA/clk x 2 FLOP x 2.07 GHz", traffic)
-    tc = (d == 3 and n <= 64 and prec != "fp64") or prec in ("tf32", "bf16")
-    if tc:
+    if n <= 64 and prec != "fp64":   # the stiffness runs on the tensor cores
         pk = bf16 * (1.0 if prec == "bf16" else 0.5)
         add("assemble", "tensor", prof["assemble"][2], pk,
-            src + " bf16_tflops" + ("" if prec == "bf16" else " x 0.5 (TF32 rate)"))
+            src + " bf16_tflops" + ("" if prec == "bf16" else " x 0.5 (TF32 rate)") +
+            ("; FP32 as a TF32 hi/lo split: 3 MMAs per algorithmic product" if prec == "fp32" else ""))
     elif prec == "fp64":
         add("assemble", "alu", prof["assemble"][2], FP64_PEAK_TFLOPS, "FP64 pipe")
     else:

@@ -82,9 +82,10 @@ typedef struct {
  *             (FP32 pairs, ~48 significant bits; residual error ~1e-12 of
  *             sum |terms|, see fp64_residual); the n x n solve by an FP32 LU with
  *             FP64 residual refinement (n >= 48, FP64 LU fallback) or an FP64 LU;
- *             the tangent and the stiffness contraction K in FP32 CUDA cores / TF32 /
- *             BF16 tensor cores (tcgen05, FP32 accumulation in tensor memory;
- *             n <= 64) -- an inexact-Newton Jacobian; the converged answer still
+ *             the tangent in FP32; the stiffness contraction K on the tcgen05 tensor
+ *             cores for n <= 64 (FP32 accumulation in tensor memory): FP32 as a TF32
+ *             hi/lo split (FP32-accurate), TF32, BF16; for n > 64 FP32 on the CUDA
+ *             cores -- an inexact-Newton Jacobian; the converged answer still
  *             satisfies the residual test.  With TF32/BF16 the K used for Abar is one
  *             extra FP32-accurate assembly at the converged iterate;
  *  start: ROM_START_PLAIN a0 = a_n; ROM_START_PREV a0 = a_n + (a_n - a_{n-1});
@@ -195,7 +196,7 @@ rom_status rom_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts, const dou
                     double *Pbar, double *Abar, rom_step_info *info);
 
 /* Same with device pointers; asynchronous on the context stream.
- * Tensor-core stiffness (3D models, and 2D in ROM_PREC_TF32/BF16): every pipeline wait inside
+ * Tensor-core stiffness (models with n <= 64, every precision but FP64): every pipeline wait inside
  * the kernel is bounded; if one gives up, rom_step (and rom_step_device without graphs)
  * returns ROM_E_CUDA after the Newton passes, and in graph mode the step's Abar entries are
  * NaN (Pbar, info and the history come from the residual test, which no tensor-core result

@@ -33,9 +33,9 @@ void mlp_train_step(MlpDev &M, const float *X, const float *Y, int64_t N, float 
 void mlp_loss_grad(MlpDev &M, const float *X, const float *Y, int64_t N, int bf16, float *grad_out, float *loss_out,
                    cudaStream_t s);
 void mlp_predict(MlpDev &M, const float *X, int64_t N, int bf16, double *out, cudaStream_t s);
-void tc_image_shape(int d, int fmt, int m, int *chunk_bytes, int *nchunks);
-void tc_build_image(int d, int fmt, int n, int m, const double *G, unsigned char *img);
-int launch_tc(int fmt, const Model &M, Batch Bt, const unsigned char *img, int *err, cudaStream_t s);
+size_t tc2_image_bytes(int fmt, int n, int m);
+void tc2_build_image(int fmt, int n, int m, const double *G, unsigned char *img);
+int launch_tc2(int mode, const Model &M, Batch Bt, const unsigned char *img, int *err, int sel, cudaStream_t s);
 size_t tc3_image_bytes(int m);
 void tc3_build_images(int n, int m, const double *G, unsigned char *img);
 int launch_tc3(int mode, const Model &M, Batch Bt, const unsigned char *img, int *err, int sel, cudaStream_t s);
@@ -285,10 +285,8 @@ rom_status rom_load_basis(rom_ctx *ctx, int n, int m, const double *G) {
     }
     if (n <= 64) {
         for (int f = 0; f < 2 && ctx->dim == 2; ++f) {
-            int cb, nch;
-            tc_image_shape(ctx->dim, f + 1, m, &cb, &nch);
-            std::vector<unsigned char> img((size_t)cb * nch);
-            tc_build_image(ctx->dim, f + 1, n, m, G, img.data());
+            std::vector<unsigned char> img(tc2_image_bytes(f + 1, n, m));
+            tc2_build_image(f + 1, n, m, G, img.data());
             if ((s = dalloc(ctx, (void **)&ctx->tc_img[f], img.size())) != ROM_OK) return s;
             CK(cudaMemcpy(ctx->tc_img[f], img.data(), img.size(), cudaMemcpyHostToDevice));
         }
@@ -653,23 +651,29 @@ static void prof_collect(rom_ctx *ctx) {
 }
 
 // the stiffness K runs on the tensor cores (and the residual in its own kernel, launch_force)
-// for 3D models with n <= 64 at every precision but FP64, and for 2D models in BF16/TF32
+// for models with n <= 64 at every precision but FP64
 static bool tc_path(const rom_ctx *ctx, const Model &M, int precision) {
-    return (M.d == 3 && ctx->tc3_img && precision >= 1) || precision >= 2;
+    return precision >= 1 && ((M.d == 3 && ctx->tc3_img) || (M.d == 2 && ctx->tc_img[1]));
 }
 
-// K of the active list: 3D models with n <= 64 use the 3D tensor-core kernel (BF16, TF32, or the
-// FP32-accurate TF32 split for precision fp32; in BF16 and TF32 the instances that the solve
-// flagged for an accurate stiffness get the split assembly); 2D models use the 2D tensor-core
-// kernel for BF16/TF32 and otherwise the SIMT kernel, which also produces the residual r
+// K of the active list on the tensor cores (n <= 64): BF16, TF32, or the FP32-accurate TF32 split
+// for precision fp32; in BF16 and TF32 the instances that the solve flagged for an accurate
+// stiffness get the split assembly.  3D: k_assemble_tc3 / tc4; 2D: k_assemble_tcp with the
+// instances packed along M.  FP64 (and n > 64) use the SIMT kernel, which can also produce the
+// residual r
 static int launch_assembly(rom_ctx *ctx, const Model &M, Batch bt, const StepOpts &o, int32_t *nxt, cudaStream_t s) {
     if (M.d == 3 && ctx->tc3_img && o.precision >= 1) {
         if (o.precision == 1) return launch_tc3(3, M, bt, ctx->tc3_img, ctx->d_err, 0, s);
         const int r = launch_tc3(o.precision == 3 ? 1 : 4, M, bt, ctx->tc3_img, ctx->d_err, 1, s);
         return r ? r : launch_tc3(3, M, bt, ctx->tc3_img, ctx->d_err, 2, s);
     }
-    if (o.precision >= 2)
-        return launch_tc(o.precision == 3 ? 1 : 2, M, bt, ctx->tc_img[o.precision == 3 ? 0 : 1], ctx->d_err, s);
+    if (M.d == 2 && ctx->tc_img[1] && o.precision >= 1) {
+        if (o.precision == 1) return launch_tc2(3, M, bt, ctx->tc_img[1], ctx->d_err, 0, s);
+        const int r = o.precision == 3 ? launch_tc2(1, M, bt, ctx->tc_img[0], ctx->d_err, 1, s)
+                                       : launch_tc2(2, M, bt, ctx->tc_img[1], ctx->d_err, 1, s);
+        return r ? r : launch_tc2(3, M, bt, ctx->tc_img[1], ctx->d_err, 2, s);
+    }
+    if (o.precision >= 2) return -1;
     return launch_kernel(2, M, bt, o, nxt, s);
 }
 
@@ -1108,7 +1112,8 @@ rom_status rom_state_bytes(const rom_ctx *ctx, int64_t B, int64_t *bytes) {
 rom_status rom_autotune(rom_ctx *ctx, rom_state *st, const rom_opts *opts, int *tile, int *chunk, float *ms) {
     rom_status s = check_step(ctx, st, opts);
     if (s != ROM_OK) return s;
-    if (opts->precision >= ROM_PREC_TF32 || (ctx->dim == 3 && ctx->tc3_img)) {   // the tensor-core tiles are fixed
+    if (opts->precision >= ROM_PREC_TF32 || (ctx->dim == 3 && ctx->tc3_img) ||
+        (opts->precision == ROM_PREC_FP32 && ctx->tc_img[1])) {   // the tensor-core tiles are fixed
         if (tile) *tile = 0;
         if (chunk) *chunk = 0;
         return ROM_OK;

@@ -1,275 +1,348 @@
-// Reduced stiffness K_b = sum_i G_i^T At_i G_i (Eq. stiffnessmatrix_ecm) on the 5th-generation
-// tensor cores (tcgen05.mma, BF16 or TF32 operands, FP32 accumulation in tensor memory).
+// Reduced stiffness of the 2D model, K_b = sum_i G_i^T At_i G_i (Eq. stiffnessmatrix_ecm), on the
+// 5th-generation tensor cores (tcgen05.mma, FP32 accumulation in tensor memory), with the
+// instances of a CTA packed along the MMA's M dimension; and the residual r = sum_i G_i^T v_i
+// (Eq. residual_ecm) in FP64 or double-float arithmetic.
 //
-// Formulation: K_b = Y_b^T G with Y_b = blockdiag_i(At_i) G (rows = (point i, component c)).
-// One CTA holds two instances (b0, b1): the MMA is D[128 x 64] += A[128 x K] B[64 x K]^T with
-//   A rows 0..63   = Y_b0^T (row j, column (i,c)),  A rows 64..127 = Y_b1^T,
-//   B rows j       = G[:, :, j] (column (i,c)),     D rows = K_b0 rows, then K_b1 rows.
-// The K dimension runs over chunks of PC cubature points (KC = PC * d^2 columns).  Per chunk:
-//   * the A tile (Y^T) is produced by all threads in FP32 from the FP32 tangent At and the
-//     FP32 basis copy, rounded to BF16/TF32 and stored in the canonical K-major layout;
-//   * the B tile is a pre-arranged image of G (same layout) fetched with one bulk copy
-//     (cp.async.bulk, the TMA engine) that completes on an mbarrier;
-//   * one thread issues KC/16 (BF16) or KC/8 (TF32) tcgen05.mma and commits them to an
-//     mbarrier, so the next chunk's producer work overlaps the tensor cores (2 stages).
-// Shared-memory operand layout (no swizzle, K-major): 8-row x 16-byte core matrices; core
-// matrices adjacent in K are 128 bytes apart (leading byte offset), 8-row groups are
-// SBO = KC * esize / 16 * 128 bytes apart (stride byte offset).
-// Every wait is bounded; on timeout the kernel records an error, waits (bounded) for its
-// own outstanding MMAs, frees its tensor memory and returns.
+// Formulation: K_b = Y_b^T G with Y_b[(i, c)][j] = sum_q At_i[q][c] G_i[q][j], so that
+// K[j][l] = sum_i sum_{q,c} G_i[q][j] At_i[q][c] G_i[c][l] (K itself, not K^T, when the FP32
+// tangent is not exactly symmetric).  A CTA holds S = min(16, floor(128 / n)) instances b_s in
+// consecutive n-row slots of one 128-row accumulator:
+//   D[128 x NB] += A[128 x K] B[NB x K]^T,   A row s n + j = row j of Y_{b_s}^T,
+//   B row l = G[:, :, l],  NB = n rounded up to 16,
+// so every MMA serves all S instances with the shared basis tile as its B operand (at n = 24,
+// 5 x 24 of the 128 rows carry work).  K runs over chunks of PC cubature points; each point's 4
+// components fill 16 bytes of a row in TF32 (PC = 8), two points do in BF16 (PC = 16), so a chunk
+// is 128 bytes of K per row in every mode: 8 core matrices, 4 MMAs (K = 8 TF32 / 16 BF16).
+//
+// Roles: 8 producer warps (256 threads in groups of 8: group item (unit u, instance s, block of
+// 8 rows), lane = row j of the block) read the tangent of point(s) u of instance s from a
+// cp.async-staged copy (the next chunk's copy overlaps this chunk's work), form Y for row j from
+// the FP32 basis chunk, round it and store 16 bytes per row and unit; one control thread issues the bulk copy (cp.async.bulk, the
+// TMA engine) of the chunk's image (FP32 basis, pre-arranged B tile(s)) into a 2-stage ring, then,
+// once the producers have arrived on the stage's mbarrier, the chunk's MMAs and one commit.
+// MODE 1 = BF16 operands, 2 = TF32, 3 = TF32 split: A = A_hi + A_lo, B = B_hi + B_lo with
+// A_hi = tf32(A), A_lo = tf32(A - A_hi); the MMAs form A_hi B_hi + A_lo B_hi + A_hi B_lo, an
+// FP32-accurate product (the dropped A_lo B_lo term is below FP32 rounding).
+// Accumulation: the tensor core adds into FP32 with truncation, so chunk c goes to accumulator
+// c % NH (NH of them side by side in tensor memory), the split's small terms to one more, and the
+// epilogue adds the accumulators: the chains stay a few MMAs long.
+// Every wait is bounded by the wall clock (1 s); on timeout the CTA records an error, stops
+// issuing work, waits (bounded) for its own copies and MMAs, frees its tensor memory and returns.
 #include <cuda_bf16.h>
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 
 #include "kernels.cuh"
+#include "tcgen05.cuh"
 
 namespace podecm {
 
-namespace tc {
+namespace tcp {
 
-constexpr int MROWS = 128;       // MMA M (two instances x 64 rows)
-constexpr int NCOLS = 64;        // MMA N (n padded to 64)
-constexpr int THREADS = 256;
-constexpr long long WAIT_LIMIT = 20000000;   // try_wait polls before giving up
+constexpr int D2 = 4, D4 = 16;
+constexpr int MROWS = 128;            // MMA M
+constexpr int MAX_S = 16;             // instances per CTA
+constexpr int NU = 8;                 // 16-byte K units per chunk and row
+constexpr int SBO_A = NU * 128;       // A and B tiles: 8-row groups 1024 bytes apart
+constexpr int SBO_B = NU * 128;
+constexpr int A_BYTES = MROWS / 8 * SBO_A;
+constexpr int NK = 4;                 // MMAs per chunk (32 bytes of K each)
+constexpr int NPROD = 256;
+constexpr int THREADS = NPROD + 32;
+constexpr int MAXIT = 8;              // producer items per 8-lane group and chunk (at most 7 for n <= 64)
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+template <int MODE>
+struct Cfg {
+    static constexpr bool SPLIT = MODE == 3;
+    static constexpr int PU = MODE == 1 ? 2 : 1;          // points per 16-byte unit
+    static constexpr int PC = NU * PU;                    // points per chunk
+    static constexpr int NAT = SPLIT ? 2 : 1;             // A tiles per stage
+    static constexpr int ASTR = D4 * PC + 4;              // staged tangent floats per instance (the
+                                                          // 4-float pad spreads instances over banks)
+    static constexpr int TMEM_COLS = SPLIT ? 256 : 128;
+};
+
+// launch geometry of a model (host-computed, passed by value)
+struct Geom {
+    int S, NB, nch;                 // instances per CTA, MMA N, chunks
+    int g32_bytes, b_bytes;         // FP32 basis chunk [PC][4][NB]; one B tile (NB rows x 128 bytes)
+    int chunk_bytes, copy_bytes;    // image bytes per chunk; bytes one CTA copies per chunk
+    int stage_bytes, as_bytes, smem;
+    int AS, NACC, NH;               // accumulator stride (tensor-memory columns), count, hi count
+};
+
+template <int MODE>
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    if (MODE == 1) tcx::mma_f16(d, a, b, idesc, acc);
+    else tcx::mma_tf32(d, a, b, idesc, acc);
 }
 
-__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;          // descriptor version for tcgen05
-    // base offset 0, LBO mode 0, layout type 0 (no swizzle)
-    return d;
-}
+}  // namespace tcp
 
-// kind::f16 / kind::tf32 instruction descriptor: D = F32, A/B formats, both K-major, N, M
-__host__ __device__ constexpr uint32_t make_idesc(uint32_t ab_format, int M, int N) {
-    return (1u << 4) | (ab_format << 7) | (ab_format << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase) {
-    const uint32_t a = smem_u32(bar);
-    for (long long it = 0; it < WAIT_LIMIT; ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n .reg .pred P1;\n mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n selp.b32 %0, 1, 0, P1;\n}\n"
-            : "=r"(done)
-            : "r"(a), "r"(phase)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-
-template <int FMT>
-__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
-    if (FMT == 1) {
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-                tmem_d),
-            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
-    } else {
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-                tmem_d),
-            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
-    }
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-
-// store one rounded element of the A tile (row r, column k) in the canonical layout
-template <int FMT>
-__device__ __forceinline__ void store_a(unsigned char *tile, int sbo, int r, int k, float v) {
-    if (FMT == 1) {
-        const int off = (r >> 3) * sbo + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
-        *reinterpret_cast<__nv_bfloat16 *>(tile + off) = __float2bfloat16(v);
-    } else {
-        const int off = (r >> 3) * sbo + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4;
-        *reinterpret_cast<float *>(tile + off) = v;   // the tensor core reads the TF32 part
-    }
-}
-
-}  // namespace tc
-
-// FMT: 1 = BF16 (PC = 16 points per chunk), 2 = TF32 (PC = 8)
-template <int D, int FMT>
-__global__ void __launch_bounds__(tc::THREADS, 1)
-    k_assemble_tc(Model M, Batch Bt, const unsigned char *__restrict__ Gimg, int nchunks, int *err_flag) {
-    using namespace tc;
-    constexpr int D2 = D * D, D4 = D2 * D2;
-    constexpr int PC = (FMT == 1) ? 16 : 8;
-    constexpr int KC = PC * D2;
-    constexpr int ES = (FMT == 1) ? 2 : 4;
-    constexpr int SBO = KC * ES / 16 * 128;
-    constexpr int A_BYTES = (MROWS / 8) * SBO;
-    constexpr int B_BYTES = (NCOLS / 8) * SBO;
-    constexpr int KSTEP = (FMT == 1) ? 16 : 8;
-    constexpr int NK = KC / KSTEP;
-    constexpr uint32_t IDESC = make_idesc(FMT == 1 ? 1u : 2u, MROWS, NCOLS);
-
+// sel: 0 every listed instance, 1 those without, 2 those with the accurate-stiffness flag
+template <int MODE>
+__global__ void __launch_bounds__(tcp::THREADS, 1)
+    k_assemble_tcp(Model M, Batch Bt, const unsigned char *__restrict__ img, tcp::Geom g, int *err_flag, int sel) {
+    using namespace tcx;
+    using namespace tcp;
+    using C = Cfg<MODE>;
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char *Ast[2] = {smem, smem + A_BYTES};
-    unsigned char *Bst[2] = {smem + 2 * A_BYTES, smem + 2 * A_BYTES + B_BYTES};
-    float *Gs = reinterpret_cast<float *>(smem + 2 * A_BYTES + 2 * B_BYTES);          // [PC][D2][64]
-    float *As = Gs + PC * D2 * NCOLS;                                                   // [2][PC][D4]
-    __shared__ __align__(8) uint64_t bar_mma[2], bar_load[2];
+    __shared__ __align__(8) uint64_t bar_full[2], bar_afull[2], bar_mma[2];
     __shared__ uint32_t tmem_base;
-    __shared__ int abort_s;
+    __shared__ int64_t bI[MAX_S];
+    __shared__ volatile int abort_s;
+    __shared__ int n_sel;
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const int n_act = Bt.counts[0];
-    const int p0 = 2 * blockIdx.x;
+    const int S = g.S;
+    const int p0 = S * blockIdx.x;
     if (p0 >= n_act) return;
-    const bool has1 = (p0 + 1) < n_act;
-    const int64_t bI[2] = {Bt.list[p0], has1 ? Bt.list[p0 + 1] : Bt.list[p0]};
-    const int n = M.n, m = M.m;
+    const int n = M.n, m = M.m, mA = M.mA, NB = g.NB, nch = g.nch;
     const float *At = reinterpret_cast<const float *>(Bt.At);
+    auto a_tile = [&](int st, int t) { return smem + (size_t)st * g.stage_bytes + (size_t)t * A_BYTES; };
+    auto img_tile = [&](int st) { return smem + (size_t)st * g.stage_bytes + (size_t)C::NAT * A_BYTES; };
+    // staged tangents of chunk c at As0 + (c & 1) * as_floats (arithmetic, so that no pointer array
+    // lands in local memory)
+    float *const As0 = reinterpret_cast<float *>(smem + 2 * (size_t)g.stage_bytes);
+    const int as_floats = g.as_bytes / 4;
 
-    if (warp == 0) {
+    if (tid == 0) n_sel = 0;
+    __syncthreads();
+    if (tid < S) {
+        int64_t b = -1;
+        if (p0 + tid < n_act) {
+            b = Bt.list[p0 + tid];
+            if (sel != 0 && ((Bt.ctl[b].acc_k != 0) != (sel == 2))) b = -1;
+        }
+        bI[tid] = b;
+        if (b >= 0) atomicAdd(&n_sel, 1);
+    }
+    __syncthreads();
+    if (n_sel == 0) return;
+    if (warp == NPROD / 32) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                     "r"(NCOLS));
+                     "r"(C::TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        mbar_init(&bar_mma[0], 1);
-        mbar_init(&bar_mma[1], 1);
-        mbar_init(&bar_load[0], 1);
-        mbar_init(&bar_load[1], 1);
+        for (int st = 0; st < 2; ++st) {
+            mbar_init(&bar_full[st], 1);
+            mbar_init(&bar_afull[st], NPROD);
+            mbar_init(&bar_mma[st], 1);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         abort_s = 0;
     }
+    // rows S n .. 127 of the A tiles are never produced: zero them once
+    const int pad = MROWS - S * n;
+    for (int e = tid; e < 2 * C::NAT * pad * NU; e += THREADS) {
+        const int u = e % NU, rest = e / NU;
+        const int r = S * n + rest % pad, t = rest / pad;
+        *reinterpret_cast<uint4 *>(a_tile(t / C::NAT, t % C::NAT) + (size_t)(r >> 3) * SBO_A + u * 128 + (r & 7) * 16) =
+            make_uint4(0u, 0u, 0u, 0u);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
-    uint32_t ph_mma[2] = {0, 0}, ph_load[2] = {0, 0};
-    int issued[2] = {0, 0};
 
-    for (int c = 0; c < nchunks; ++c) {
-        const int s = c & 1;
-        if (tid == 0) {
-            bool ok = true;
-            if (issued[s]) { ok = mbar_wait(&bar_mma[s], ph_mma[s]); ph_mma[s] ^= 1; issued[s] = 0; }
-            if (!ok) abort_s = 1;
-            else bulk_load(Bst[s], Gimg + (size_t)c * B_BYTES, B_BYTES, &bar_load[s]);
-        }
-        __syncthreads();
-        if (abort_s) break;
-        // stage the FP32 basis chunk and the two instances' tangents
-        const int c0 = c * PC;
-        for (int e = tid; e < PC * D2 * NCOLS; e += THREADS) {
-            const int j = e % NCOLS, rc = e / NCOLS;
-            const int ii = rc / D2;
-            const int q = rc - ii * D2;
-            Gs[e] = (j < n && c0 + ii < m) ? M.G32_pt[((size_t)(c0 + ii) * D2 + q) * n + j] : 0.f;
-        }
-        for (int e = tid; e < 2 * PC * D4; e += THREADS) {
-            const int inst = e / (PC * D4), rem = e - inst * PC * D4;
-            const int ce = rem / PC, ii = rem - ce * PC;
-            const bool valid = (inst == 0 || has1) && (c0 + ii < m);
-            As[(inst * PC + ii) * D4 + ce] = valid ? At[((size_t)bI[inst] * D4 + ce) * M.mA + c0 + ii] : 0.f;
-        }
-        __syncthreads();
-        // producer: A[inst*64 + j][ii*D2 + cc] = sum_e At[ii][e][cc] G[ii][e][j]
-        for (int e = tid; e < 2 * PC * NCOLS; e += THREADS) {
-            const int j = e % NCOLS, r2 = e / NCOLS;
-            const int ii = r2 % PC, inst = r2 / PC;
-            float g[D2];
+    if (tid < NPROD) {
+        // ------------------------------------------------------------------ producers
+        const int grp = tid >> 3, j8 = tid & 7;
+        // this thread's items (unit u, instance s, block of 8 rows; row blocks fastest, so that the
+        // groups of a warp mostly share one tangent and read distinct basis columns), decoded
+        // once: staged-tangent index, basis index and A-tile byte offset of row s n + j
+        const int NJB = (n + 7) >> 3, n_items = S * NU * NJB;
+        int it_a[MAXIT], it_g[MAXIT], it_st[MAXIT];
+        uint32_t it_live = 0, it_row = 0;
 #pragma unroll
-            for (int q = 0; q < D2; ++q) g[q] = Gs[(ii * D2 + q) * NCOLS + j];
-            const float *a = As + (inst * PC + ii) * D4;
-#pragma unroll
-            for (int cc = 0; cc < D2; ++cc) {
-                float y = 0.f;
-#pragma unroll
-                for (int q = 0; q < D2; ++q) y = fmaf(a[q * D2 + cc], g[q], y);   // Y = At^T G (K, not K^T)
-                tc::store_a<FMT>(Ast[s], SBO, inst * 64 + j, ii * D2 + cc, y);
-            }
+        for (int k = 0; k < MAXIT; ++k) {
+            const int it = grp + k * (NPROD / 8);
+            const int jb = it % NJB, rest = it / NJB;
+            const int s = rest % S, u = rest / S;
+            const int j = jb * 8 + j8, r = s * n + j;
+            it_a[k] = s * C::ASTR + u * C::PU;
+            it_g[k] = u * C::PU * D2 * NB + j;
+            it_st[k] = (r >> 3) * SBO_A + u * 128 + (r & 7) * 16;
+            if (it < n_items) it_live |= 1u << k;             // uniform over two warps
+            if (it < n_items && j < n) it_row |= 1u << k;
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-            const bool ok = mbar_wait(&bar_load[s], ph_load[s]);
-            ph_load[s] ^= 1;
-            if (!ok) {
-                abort_s = 1;
-            } else {
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t a0 = smem_u32(Ast[s]), b0 = smem_u32(Bst[s]);
-#pragma unroll
-                for (int k = 0; k < NK; ++k) {
-                    const uint64_t ad = tc::make_desc(a0 + k * 256, 128, SBO);
-                    const uint64_t bd = tc::make_desc(b0 + k * 256, 128, SBO);
-                    tc::mma<FMT>(tmem, ad, bd, IDESC, (c > 0 || k > 0) ? 1u : 0u);
+        // tangent rows (instance s, component e) of chunk c: PC / 4 pieces of 4 points each; whole
+        // pieces by cp.async, the pieces of absent instances and the points past m as zeros
+        auto prefetch = [&](int c, int buf) {
+            constexpr int PIECES = C::PC / 4;
+            const int c0 = c * C::PC;
+            for (int e = tid; e < S * D4 * PIECES; e += NPROD) {
+                const int h = e % PIECES, row = e / PIECES;
+                const int s = row / D4, comp = row - s * D4;
+                const int64_t b = bI[s];
+                const int p0 = c0 + 4 * h;
+                float *dst = As0 + buf * as_floats + s * C::ASTR + comp * C::PC + 4 * h;
+                if (b >= 0 && p0 + 4 <= m) {
+                    cp_async16(dst, At + ((size_t)b * D4 + comp) * mA + p0);
+                } else {
+                    const float *src = At + ((size_t)(b >= 0 ? b : 0) * D4 + comp) * mA + p0;
+                    float4 v;
+                    v.x = (b >= 0 && p0 + 0 < m) ? src[0] : 0.f;
+                    v.y = (b >= 0 && p0 + 1 < m) ? src[1] : 0.f;
+                    v.z = (b >= 0 && p0 + 2 < m) ? src[2] : 0.f;
+                    v.w = (b >= 0 && p0 + 3 < m) ? src[3] : 0.f;
+                    *reinterpret_cast<float4 *>(dst) = v;
                 }
-                tc::mma_commit(&bar_mma[s]);
-                issued[s] = 1;
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        prefetch(0, 0);
+        int local_abort = 0;
+        for (int c = 0; c < nch; ++c) {
+            const int st = c & 1;
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            if (bar_or(NPROD, local_abort | abort_s)) break;   // also: chunk c's tangents visible
+            if (c + 1 < nch) prefetch(c + 1, (c + 1) & 1);
+            const uint32_t par = (uint32_t)(c >> 1) & 1u;
+            if (!mbar_wait(&bar_full[st], par, &abort_s)) { local_abort = 1; continue; }
+            if (c >= 2 && !mbar_wait(&bar_mma[st], par ^ 1u, &abort_s)) { local_abort = 1; continue; }
+            const float *Gs = reinterpret_cast<const float *>(img_tile(st));
+            const float *Ab = As0 + (c & 1) * as_floats;
+            unsigned char *Ahi = a_tile(st, 0);
+            unsigned char *Alo = a_tile(st, C::NAT - 1);
+#pragma unroll
+            for (int k = 0; k < MAXIT; ++k) {
+                if (!((it_live >> k) & 1u)) break;
+                float a[C::PU][D4];
+#pragma unroll
+                for (int p = 0; p < C::PU; ++p)
+#pragma unroll
+                    for (int e = 0; e < D4; ++e) a[p][e] = Ab[it_a[k] + e * C::PC + p];
+                if ((it_row >> k) & 1u) {
+                    float y[C::PU][D2];
+#pragma unroll
+                    for (int p = 0; p < C::PU; ++p) {
+                        const float *gp = Gs + it_g[k] + p * D2 * NB;
+                        // Y row j of the point: y[c] = sum_q At[q][c] G[q][j], packed FP32 pairs
+                        float2 y01 = make_float2(0.f, 0.f), y23 = make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int q = 0; q < D2; ++q) {
+                            const float gv = gp[q * NB];
+                            const float2 gg = make_float2(gv, gv);
+                            y01 = __ffma2_rn(make_float2(a[p][q * D2 + 0], a[p][q * D2 + 1]), gg, y01);
+                            y23 = __ffma2_rn(make_float2(a[p][q * D2 + 2], a[p][q * D2 + 3]), gg, y23);
+                        }
+                        y[p][0] = y01.x; y[p][1] = y01.y; y[p][2] = y23.x; y[p][3] = y23.y;
+                    }
+                    if (MODE == 1) {
+                        const uint4 v = make_uint4(pack_bf16(y[0][0], y[0][1]), pack_bf16(y[0][2], y[0][3]),
+                                                   pack_bf16(y[C::PU - 1][0], y[C::PU - 1][1]),
+                                                   pack_bf16(y[C::PU - 1][2], y[C::PU - 1][3]));
+                        *reinterpret_cast<uint4 *>(Ahi + it_st[k]) = v;
+                    } else {
+                        uint32_t h[D2];
+#pragma unroll
+                        for (int cc = 0; cc < D2; ++cc) h[cc] = tf32_bits(y[0][cc]);
+                        *reinterpret_cast<uint4 *>(Ahi + it_st[k]) = make_uint4(h[0], h[1], h[2], h[3]);
+                        if (C::SPLIT) {
+                            uint32_t l[D2];
+#pragma unroll
+                            for (int cc = 0; cc < D2; ++cc) l[cc] = tf32_bits(y[0][cc] - __uint_as_float(h[cc]));
+                            *reinterpret_cast<uint4 *>(Alo + it_st[k]) = make_uint4(l[0], l[1], l[2], l[3]);
+                        }
+                    }
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(&bar_afull[st]);
+        }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+    } else if (tid == NPROD) {
+        // ------------------------------------------------------------- control thread
+        uint32_t copy_pending = 0, copy_par = 0;   // bit st: a copy into stage st in flight / its parity
+        int mma_pending = 0;
+        uint32_t mma_par = 0;
+        int mma_stage = 0;
+        const uint32_t idesc = make_idesc(MODE == 1 ? 1u : 2u, MROWS, NB);
+        auto issue_copies = [&](int c) {
+            const int st = c & 1;
+            mbar_expect_tx(&bar_full[st], (uint32_t)g.copy_bytes);
+            bulk_g2s(img_tile(st), img + (size_t)c * g.chunk_bytes, (uint32_t)g.copy_bytes, &bar_full[st]);
+            copy_pending |= 1u << st;
+            copy_par = (copy_par & ~(1u << st)) | (((uint32_t)(c >> 1) & 1u) << st);
+        };
+        issue_copies(0);
+        if (nch > 1) issue_copies(1);
+        for (int c = 0; c < nch; ++c) {
+            const int st = c & 1;
+            const uint32_t par = (uint32_t)(c >> 1) & 1u;
+            if (!mbar_wait(&bar_full[st], par, &abort_s)) break;
+            copy_pending &= ~(1u << st);
+            if (!mbar_wait(&bar_afull[st], par, &abort_s)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t ah = smem_u32(a_tile(st, 0)), al = smem_u32(a_tile(st, C::NAT - 1));
+            const uint32_t bh = smem_u32(img_tile(st) + g.g32_bytes), bl = bh + (uint32_t)g.b_bytes;
+            const uint32_t dh = tmem + (uint32_t)((c % g.NH) * g.AS), dl = tmem + (uint32_t)(g.NH * g.AS);
+#pragma unroll
+            for (int k = 0; k < NK; ++k) {
+                const uint64_t adh = make_desc(ah + k * 256, 128, SBO_A);
+                const uint64_t bdh = make_desc(bh + k * 256, 128, SBO_B);
+                tcp::mma<MODE>(dh, adh, bdh, idesc, (c >= g.NH || k > 0) ? 1u : 0u);
+                if (C::SPLIT) {
+                    tcp::mma<MODE>(dl, make_desc(al + k * 256, 128, SBO_A), bdh, idesc, (c > 0 || k > 0) ? 1u : 0u);
+                    tcp::mma<MODE>(dl, adh, make_desc(bl + k * 256, 128, SBO_B), idesc, 1u);
+                }
+            }
+            mma_commit(&bar_mma[st]);
+            mma_pending = 1;
+            mma_par = par;
+            mma_stage = st;
+            if (c + 2 < nch) {
+                if (!mbar_wait(&bar_mma[st], par, &abort_s)) break;
+                issue_copies(c + 2);
             }
         }
-        __syncthreads();
-        if (abort_s) break;
-    }
-    // drain: wait for the outstanding commits (bounded)
-    if (tid == 0) {
-        for (int s = 0; s < 2; ++s)
-            if (issued[s]) {
-                if (!mbar_wait(&bar_mma[s], ph_mma[s])) abort_s = 1;
-                ph_mma[s] ^= 1;
-            }
+        // drain: the last commit covers every MMA issued before it; outstanding copies must land
+        if (mma_pending && !mbar_wait(&bar_mma[mma_stage], mma_par, &abort_s)) mbar_drain(&bar_mma[mma_stage], mma_par);
+        for (int st = 0; st < 2; ++st)
+            if ((copy_pending >> st) & 1u) mbar_drain(&bar_full[st], (copy_par >> st) & 1u);
         if (abort_s && err_flag) atomicExch(err_flag, 1);
     }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (!abort_s && warp < 4) {
-        // warp w reads TMEM lanes 32w .. 32w+31 = output rows; 2 x 32 columns
-        const int row = warp * 32 + (tid & 31);
-        const int inst = row >> 6, j = row & 63;
-        float v[64];
+    if (!abort_s && tid < NPROD) {
+        // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (accumulator rows s n + j)
+        // and the 16-column groups w / 4, w / 4 + 2, ...; the accumulators are added in FP32 in a
+        // fixed order (the FP64 pipe runs at 1/64 of the FP32 rate) and widened exactly
+        const int row = (warp & 3) * 32 + (tid & 31);
+        const int s = row / n, j = row - s * n;
+        const bool ok = s < S && bI[s] >= 0;
+        double *Kb = ok ? Bt.K + (size_t)bI[s] * n * n + (size_t)j * n : nullptr;
+        const int nh_used = nch < g.NH ? nch : g.NH;
+        for (int c16 = warp >> 2; c16 < NB / 16; c16 += NPROD / 128) {
+            float acc[16];
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(half * 32);
-            uint32_t r[32];
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            for (int q = 0; q < 16; ++q) acc[q] = 0.f;
+            for (int ai = 0; ai < g.NACC; ++ai) {
+                if (ai >= nh_used && ai < g.NH) continue;   // accumulator never written
+                uint32_t r[16];
+                tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(ai * g.AS + c16 * 16), r);
+                tmem_wait_ld();
 #pragma unroll
-            for (int q = 0; q < 32; ++q) v[half * 32 + q] = __uint_as_float(r[q]);
-        }
-        if (j < n && (inst == 0 || has1)) {
-            double *Kb = Bt.K + (size_t)bI[inst] * n * n + (size_t)j * n;
-            for (int k = 0; k < n; ++k) Kb[k] = (double)v[k];
+                for (int q = 0; q < 16; ++q) acc[q] += __uint_as_float(r[q]);
+            }
+            if (ok)
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    if (c16 * 16 + q < n) Kb[c16 * 16 + q] = f2d_exact(acc[q]);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS));
+    if (warp == NPROD / 32) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS));
+    }
 }
 
 // force f = sum_i G_i^T v_i in FP64, one CTA per instance; the rows (point, component) are
@@ -415,56 +488,90 @@ __global__ void __launch_bounds__(256) k_force_df(Model M, Batch Bt) {
         }
 }
 
-// bytes of one B-operand chunk image and the chunk count for a model
-void tc_image_shape(int d, int fmt, int m, int *chunk_bytes, int *nchunks) {
-    const int d2 = d * d;
-    const int PC = fmt == 1 ? 16 : 8;
-    const int KC = PC * d2, ES = fmt == 1 ? 2 : 4;
-    const int SBO = KC * ES / 16 * 128;
-    *chunk_bytes = (tc::NCOLS / 8) * SBO;
-    *nchunks = (m + PC - 1) / PC;
+
+// ------------------------------------------------------------------------ host side
+
+// geometry of the packed 2D kernel for a model (mode 1 BF16, 2 TF32, 3 TF32 split)
+static tcp::Geom tcp_geom(int mode, int n, int m) {
+    using namespace tcp;
+    Geom g{};
+    const bool bf = mode == 1, split = mode == 3;
+    const int PC = bf ? 16 : 8;
+    g.S = std::min(MAX_S, MROWS / n);
+    g.NB = (n + 15) / 16 * 16;
+    g.nch = (m + PC - 1) / PC;
+    g.g32_bytes = PC * D2 * g.NB * 4;
+    g.b_bytes = g.NB / 8 * SBO_B;
+    g.chunk_bytes = g.g32_bytes + (bf ? 1 : 2) * g.b_bytes;
+    g.copy_bytes = g.g32_bytes + (split ? 2 : 1) * g.b_bytes;
+    g.stage_bytes = (split ? 2 : 1) * A_BYTES + (g.copy_bytes + 1023) / 1024 * 1024;
+    g.as_bytes = g.S * (D4 * PC + 4) * 4;
+    g.smem = 2 * g.stage_bytes + 2 * g.as_bytes;
+    g.AS = g.NB <= 32 ? 32 : 64;
+    g.NACC = (split ? 256 : 128) / g.AS;
+    g.NH = g.NACC - (split ? 1 : 0);
+    return g;
 }
 
-// host: pre-arranged B-operand image of G[m][d2][n] (n <= 64), chunk-major
-void tc_build_image(int d, int fmt, int n, int m, const double *G, unsigned char *img) {
-    const int d2 = d * d;
+// bytes of the 2D tensor-core image of a model: fmt 1 BF16, 2 TF32 (hi and lo tiles)
+size_t tc2_image_bytes(int fmt, int n, int m) {
+    const tcp::Geom g = tcp_geom(fmt == 1 ? 1 : 3, n, m);
+    return (size_t)g.nch * g.chunk_bytes;
+}
+
+// host: per chunk of PC points, the zero-padded FP32 basis [PC][4][NB] and the B-operand tile(s)
+// of G[m][4][n] (n <= 64): row l = basis column l, K slot k = (point, component) of the chunk,
+// canonical K-major layout; TF32 hi = tf32(g), lo = tf32(g - hi)
+void tc2_build_image(int fmt, int n, int m, const double *G, unsigned char *img) {
+    using namespace tcp;
+    const tcp::Geom g = tcp_geom(fmt == 1 ? 1 : 3, n, m);
     const int PC = fmt == 1 ? 16 : 8;
-    const int KC = PC * d2, ES = fmt == 1 ? 2 : 4;
-    const int SBO = KC * ES / 16 * 128;
-    int cb, nch;
-    tc_image_shape(d, fmt, m, &cb, &nch);
-    for (int c = 0; c < nch; ++c) {
-        unsigned char *t = img + (size_t)c * cb;
-        for (int j = 0; j < tc::NCOLS; ++j)
-            for (int k = 0; k < KC; ++k) {
-                const int ii = k / d2, q = k % d2, i = c * PC + ii;
-                const double g = (j < n && i < m) ? G[((size_t)i * d2 + q) * n + j] : 0.0;
-                if (fmt == 1) {
-                    const int off = (j >> 3) * SBO + (k >> 3) * 128 + (j & 7) * 16 + (k & 7) * 2;
-                    const __nv_bfloat16 h = __float2bfloat16((float)g);
-                    memcpy(t + off, &h, 2);
-                } else {
-                    const int off = (j >> 3) * SBO + (k >> 2) * 128 + (j & 7) * 16 + (k & 3) * 4;
-                    const float f = (float)g;
-                    memcpy(t + off, &f, 4);
+    memset(img, 0, (size_t)g.nch * g.chunk_bytes);
+    for (int c = 0; c < g.nch; ++c) {
+        unsigned char *t = img + (size_t)c * g.chunk_bytes;
+        for (int pt = 0; pt < PC; ++pt) {
+            const int i = c * PC + pt;
+            if (i >= m) continue;
+            for (int q = 0; q < D2; ++q)
+                for (int l = 0; l < n; ++l) {
+                    const double v = G[((size_t)i * D2 + q) * n + l];
+                    const float f = (float)v;
+                    memcpy(t + ((size_t)(pt * D2 + q) * g.NB + l) * 4, &f, 4);
+                    const int k = pt * D2 + q;
+                    unsigned char *b = t + g.g32_bytes;
+                    if (fmt == 1) {
+                        const size_t off = (size_t)(l >> 3) * SBO_B + (size_t)(k >> 3) * 128 + (l & 7) * 16 + (k & 7) * 2;
+                        const __nv_bfloat16 h = __float2bfloat16(f);
+                        memcpy(b + off, &h, 2);
+                    } else {
+                        const size_t off = (size_t)(l >> 3) * SBO_B + (size_t)(k >> 2) * 128 + (l & 7) * 16 + (k & 3) * 4;
+                        const float hi = tcx::tf32_round_host(f);
+                        const float lo = tcx::tf32_round_host(f - hi);
+                        memcpy(b + off, &hi, 4);
+                        memcpy(b + g.b_bytes + off, &lo, 4);
+                    }
                 }
-            }
+        }
     }
 }
 
-template <int D, int FMT>
-static int launch_tc_t(const Model &M, Batch Bt, const unsigned char *img, int *err, cudaStream_t s) {
-    constexpr int D2 = D * D, D4 = D2 * D2;
-    constexpr int PC = (FMT == 1) ? 16 : 8;
-    constexpr int KC = PC * D2, ES = (FMT == 1) ? 2 : 4;
-    constexpr int SBO = KC * ES / 16 * 128;
-    constexpr int A_BYTES = (tc::MROWS / 8) * SBO, B_BYTES = (tc::NCOLS / 8) * SBO;
-    const size_t sm = 2 * (size_t)A_BYTES + 2 * (size_t)B_BYTES + (size_t)PC * D2 * tc::NCOLS * 4 + 2 * (size_t)PC * D4 * 4;
-    if (M.n > tc::NCOLS) return -1;
-    const int nch = (M.m + PC - 1) / PC;
-    cudaFuncSetAttribute(k_assemble_tc<D, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_assemble_tc<D, FMT><<<(int)((Bt.B + 1) / 2), tc::THREADS, sm, s>>>(M, Bt, img, nch, err);
+template <int MODE>
+static int launch_tcp_t(const Model &M, Batch Bt, const unsigned char *img, int *err, int sel, cudaStream_t s) {
+    if (M.d != 2 || M.n < 1 || M.n > 64 || (M.mA & 3)) return -1;
+    const tcp::Geom g = tcp_geom(MODE, M.n, M.m);
+    if (g.S * tcp::NU * ((M.n + 7) / 8) > tcp::MAXIT * (tcp::NPROD / 8)) return -1;
+    cudaFuncSetAttribute(k_assemble_tcp<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, g.smem);
+    const int grid = (int)((Bt.B + g.S - 1) / g.S);
+    k_assemble_tcp<MODE><<<grid, tcp::THREADS, g.smem, s>>>(M, Bt, img, g, err, sel);
     return 0;
+}
+
+// 2D stiffness on the tensor cores: mode 1 BF16 and 2 TF32 (image fmt 1 / 2), 3 TF32 split
+// (FP32-accurate, image fmt 2); sel as in k_assemble_tcp
+int launch_tc2(int mode, const Model &M, Batch Bt, const unsigned char *img, int *err, int sel, cudaStream_t s) {
+    return mode == 1 ? launch_tcp_t<1>(M, Bt, img, err, sel, s)
+         : mode == 2 ? launch_tcp_t<2>(M, Bt, img, err, sel, s)
+         : mode == 3 ? launch_tcp_t<3>(M, Bt, img, err, sel, s) : -1;
 }
 
 // residual r = sum_i G_i^T v_i of the listed instances (paths whose stiffness kernel does not
@@ -484,9 +591,5 @@ void launch_force(const Model &M, Batch Bt, bool fp64, cudaStream_t s) {
     }
 }
 
-int launch_tc(int fmt, const Model &M, Batch Bt, const unsigned char *img, int *err, cudaStream_t s) {
-    if (M.d == 2) return fmt == 1 ? launch_tc_t<2, 1>(M, Bt, img, err, s) : launch_tc_t<2, 2>(M, Bt, img, err, s);
-    return fmt == 1 ? launch_tc_t<3, 1>(M, Bt, img, err, s) : launch_tc_t<3, 2>(M, Bt, img, err, s);
-}
 
 }  // namespace podecm

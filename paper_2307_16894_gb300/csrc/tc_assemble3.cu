@@ -34,16 +34,17 @@
 #include <cstring>
 
 #include "kernels.cuh"
+#include "tcgen05.cuh"
 
 namespace podecm {
 
 namespace tc3 {
+using namespace tcx;
 
 constexpr int D2 = 9, D4 = 81;
 constexpr int PC = 4;                         // cubature points per chunk
 constexpr int NCOLS = 64;                     // MMA N (n padded to 64)
 constexpr int GS_BYTES = PC * D2 * NCOLS * 4; // FP32 basis chunk [PC][9][64]
-constexpr unsigned long long WAIT_NS = 1000000000ull;   // 1 s per wait
 
 template <int MODE>
 struct Cfg {
@@ -81,117 +82,10 @@ struct Cfg {
                                       ((uint32_t)(NCOLS >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ unsigned long long now_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;          // descriptor version for tcgen05; no swizzle, base offset 0
-    return d;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred P1;\n mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n selp.b32 %0, 1, 0, P1;\n}\n"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return done != 0;
-}
-
-// bounded wait; gives up early when another thread of the CTA has raised the abort flag.  Between
-// polls the thread sleeps briefly, so that waiting warps leave the issue slots of their SM
-// sub-partition to the warps that work.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
-    if (mbar_test(bar, parity)) return true;
-    const unsigned long long t0 = now_ns();
-    for (;;) {
-        __nanosleep(40);
-        if (mbar_test(bar, parity)) return true;
-        if (*abort_flag) return false;
-        if (now_ns() - t0 > WAIT_NS) {
-            *abort_flag = 1;
-            return false;
-        }
-    }
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-
-// named barrier over the producer warps with an OR reduction (uniform abort decision)
-__device__ __forceinline__ int bar_or(int nthreads, int pred) {
-    int r;
-    asm volatile(
-        "{\n .reg .pred p, q;\n setp.ne.b32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.b32 %0, 1, 0, q;\n}\n"
-        : "=r"(r)
-        : "r"(pred), "r"(nthreads)
-        : "memory");
-    return r;
-}
-
-// TF32 rounding (nearest, ties away from zero) by integer operations on the bit pattern: add half
-// of the 13 dropped mantissa bits to the magnitude and clear them (finite inputs; two integer
-// instructions instead of a conversion-unit instruction)
-__device__ __forceinline__ uint32_t tf32_bits(float x) {
-    return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
-}
-
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<uint32_t *>(&h);
-}
-
 template <int MODE>
 __device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
-    constexpr uint32_t IDESC = Cfg<MODE>::IDESC;
-    if (MODE == 1) {
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-                tmem_d),
-            "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(acc));
-    } else {
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-                tmem_d),
-            "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(acc));
-    }
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
+    if (MODE == 1) mma_f16(tmem_d, adesc, bdesc, Cfg<MODE>::IDESC, acc);
+    else mma_tf32(tmem_d, adesc, bdesc, Cfg<MODE>::IDESC, acc);
 }
 
 // image offsets (bytes) inside the per-model image buffer
@@ -249,8 +143,8 @@ __global__ void __launch_bounds__(tc3::Cfg<MODE>::THREADS, 1)
     auto g_tile = [&](int s) {
         return reinterpret_cast<float *>(stage_ptr(s) + (size_t)C::NAT * C::A_BYTES + (size_t)C::NBT * C::B_BYTES);
     };
-    float *As[2] = {reinterpret_cast<float *>(smem + 2 * (size_t)C::STAGE),
-                    reinterpret_cast<float *>(smem + 2 * (size_t)C::STAGE + C::AS_BYTES)};
+    // staged tangents of buffer t at As0 + t * AS_BYTES / 4 (arithmetic, no pointer array in local memory)
+    float *const As0 = reinterpret_cast<float *>(smem + 2 * (size_t)C::STAGE);
 
     // sel: 0 every listed instance, 1 those without the accurate-stiffness flag, 2 those with it
     if (tid == 0) n_sel = 0;
@@ -296,7 +190,7 @@ __global__ void __launch_bounds__(tc3::Cfg<MODE>::THREADS, 1)
             for (int e = tid; e < C::NI * D4; e += C::NPROD) {
                 const int ie = e / D4, ce = e - ie * D4;
                 const int64_t be = bI[ie];
-                if (be >= 0) cp_async16(As[buf] + (size_t)e * PC, At + ((size_t)be * D4 + ce) * mA + c0);
+                if (be >= 0) cp_async16(As0 + (size_t)buf * (C::AS_BYTES / 4) + (size_t)e * PC, At + ((size_t)be * D4 + ce) * mA + c0);
             }
             asm volatile("cp.async.commit_group;" ::: "memory");
         };
@@ -312,7 +206,7 @@ __global__ void __launch_bounds__(tc3::Cfg<MODE>::THREADS, 1)
             if (c >= 2 && !mbar_wait(&bar_mma[s], par ^ 1u, &abort_s)) { local_abort = 1; continue; }
             float a[D4];
             const bool pt_ok = inst_ok && (c * PC + pt < m);
-            const float *asrc = As[c & 1] + (size_t)inst * D4 * PC + pt;
+            const float *asrc = As0 + (size_t)(c & 1) * (C::AS_BYTES / 4) + (size_t)inst * D4 * PC + pt;
 #pragma unroll
             for (int e = 0; e < D4; ++e) a[e] = pt_ok ? asrc[e * PC] : 0.f;
             const float *Gs = g_tile(s);
@@ -373,8 +267,7 @@ __global__ void __launch_bounds__(tc3::Cfg<MODE>::THREADS, 1)
         asm volatile("cp.async.wait_group 0;" ::: "memory");
     } else if (lane == 0) {
         // ------------------------------------------------------------- control thread
-        int copy_pending[2] = {0, 0};
-        uint32_t copy_par[2] = {0, 0};
+        uint32_t copy_pending = 0, copy_par = 0;   // bit s: a copy into stage s in flight / its parity
         int mma_pending = 0;
         uint32_t mma_par = 0;
         int mma_stage = 0;
@@ -385,8 +278,8 @@ __global__ void __launch_bounds__(tc3::Cfg<MODE>::THREADS, 1)
             bulk_g2s(g_tile(s), img_g32 + (size_t)c * GS_BYTES, GS_BYTES, &bar_full[s]);
             bulk_g2s(b_tile(s, 0), img_b0 + (size_t)c * C::B_BYTES, C::B_BYTES, &bar_full[s]);
             if (C::SPLIT) bulk_g2s(b_tile(s, 1), img_b1 + (size_t)c * C::B_BYTES, C::B_BYTES, &bar_full[s]);
-            copy_pending[s] = 1;
-            copy_par[s] = (uint32_t)(c >> 1) & 1u;
+            copy_pending |= 1u << s;
+            copy_par = (copy_par & ~(1u << s)) | (((uint32_t)(c >> 1) & 1u) << s);
         };
         issue_copies(0);
         if (nch > 1) issue_copies(1);
@@ -394,7 +287,7 @@ __global__ void __launch_bounds__(tc3::Cfg<MODE>::THREADS, 1)
             const int s = c & 1;
             const uint32_t par = (uint32_t)(c >> 1) & 1u;
             if (!mbar_wait(&bar_full[s], par, &abort_s)) break;
-            copy_pending[s] = 0;
+            copy_pending &= ~(1u << s);
             if (!mbar_wait(&bar_afull[s], par, &abort_s)) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int ah_idx = c % C::NH;
@@ -434,10 +327,7 @@ __global__ void __launch_bounds__(tc3::Cfg<MODE>::THREADS, 1)
             while (!mbar_test(&bar_mma[mma_stage], mma_par) && now_ns() - t0 < WAIT_NS) {}
         }
         for (int s = 0; s < 2; ++s)
-            if (copy_pending[s]) {
-                const unsigned long long t0 = now_ns();
-                while (!mbar_test(&bar_full[s], copy_par[s]) && now_ns() - t0 < WAIT_NS) {}
-            }
+            if ((copy_pending >> s) & 1u) mbar_drain(&bar_full[s], (copy_par >> s) & 1u);
         if (abort_s && err_flag) atomicExch(err_flag, 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -535,40 +425,6 @@ constexpr int TMEM_Y = 256;                      // D_K[ip] at columns 64 ip, D_
 constexpr uint32_t IDESC_Y = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NY >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 constexpr uint32_t IDESC_K = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NCOLS >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 
-__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-            tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
-}
-
-// named barrier `id` over `nthreads` threads with an OR reduction
-__device__ __forceinline__ int bar_or_id(int id, int nthreads, int pred) {
-    int r;
-    asm volatile(
-        "{\n .reg .pred p, q;\n setp.ne.b32 p, %1, 0;\n bar.red.or.pred q, %2, %3, p;\n selp.b32 %0, 1, 0, q;\n}\n"
-        : "=r"(r)
-        : "r"(pred), "r"(id), "r"(nthreads)
-        : "memory");
-    return r;
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t *r) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-}
-
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t *r) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "r"(taddr));
-}
 }  // namespace tc4
 
 __global__ void __launch_bounds__(tc4::THREADS, 1)
@@ -592,7 +448,7 @@ __global__ void __launch_bounds__(tc4::THREADS, 1)
     const ImgLayout L = img_layout(m);
     const int nch = L.nch;
     const float *At = reinterpret_cast<const float *>(Bt.At);
-    float *As[2] = {reinterpret_cast<float *>(smem + OFF_AS), reinterpret_cast<float *>(smem + OFF_AS + AS_BYTES)};
+    float *const As0 = reinterpret_cast<float *>(smem + OFF_AS);   // buffer t at As0 + t * AS_BYTES / 4
 
     if (tid == 0) n_sel = 0;
     __syncthreads();
@@ -674,7 +530,7 @@ __global__ void __launch_bounds__(tc4::THREADS, 1)
             for (int e = ptid; e < NI * D4; e += 128) {
                 const int ie = e / D4, ce = e - ie * D4;
                 const int64_t be = bI[ie];
-                if (be >= 0) cp_async16(As[buf] + (size_t)e * PC, At + ((size_t)be * D4 + ce) * mA + c0);
+                if (be >= 0) cp_async16(As0 + (size_t)buf * (AS_BYTES / 4) + (size_t)e * PC, At + ((size_t)be * D4 + ce) * mA + c0);
             }
             asm volatile("cp.async.commit_group;" ::: "memory");
         };
@@ -687,7 +543,7 @@ __global__ void __launch_bounds__(tc4::THREADS, 1)
             asm volatile("cp.async.wait_group 0;" ::: "memory");
             if (bar_or_id(1, 128, local_abort | abort_s)) break;   // also: chunk c's tangents visible
             if (c + 1 < nch) prefetch(c + 1, (c + 1) & 1);
-            const float *as = As[c & 1];
+            const float *as = As0 + (size_t)(c & 1) * (AS_BYTES / 4);
             const int kst = c % NBK;
             if (!mbar_wait(&bar_fbk[kst], (uint32_t)(c / NBK) & 1u, &abort_s)) { local_abort = 1; continue; }
             for (int pp = 0; pp < 2; ++pp) {
@@ -738,16 +594,15 @@ __global__ void __launch_bounds__(tc4::THREADS, 1)
         // issue order per chunk c: K-MMAs of half 0 (chunk c), Y-MMA of point pair 0 (chunk c + 1),
         // K-MMAs of half 1, Y-MMA of point pair 1, so that the Y of the next chunk and the
         // conversion of its first half overlap the K-GEMM of this chunk
-        int bk_pend[NBK] = {0, 0, 0};
-        uint32_t bk_par[NBK] = {0, 0, 0};
+        uint32_t bk_pend = 0, bk_par = 0;   // bit st: a copy into ring stage st in flight / its parity
         uint64_t *last_bar = nullptr;   // the last commit covers every MMA issued before it
         uint32_t last_par = 0;
         auto copy_bk = [&](int c) {
             const int st = c % NBK;
             mbar_expect_tx(&bar_fbk[st], B_BYTES);
             bulk_g2s(smem + OFF_BK + (size_t)st * B_BYTES, img + L.tf_hi + (size_t)c * B_BYTES, B_BYTES, &bar_fbk[st]);
-            bk_pend[st] = 1;
-            bk_par[st] = (uint32_t)(c / NBK) & 1u;
+            bk_pend |= 1u << st;
+            bk_par = (bk_par & ~(1u << st)) | (((uint32_t)(c / NBK) & 1u) << st);
         };
         auto issue_y = [&](int c, int pp) -> bool {
             const uint32_t par = (uint32_t)c & 1u;
@@ -790,7 +645,7 @@ __global__ void __launch_bounds__(tc4::THREADS, 1)
         for (int c = 0; ok && c < nch; ++c) {
             const int kst = c % NBK;
             if (!mbar_wait(&bar_fbk[kst], (uint32_t)(c / NBK) & 1u, &abort_s)) break;
-            bk_pend[kst] = 0;
+            bk_pend &= ~(1u << kst);
             if (c >= 1) {        // B stage (c + 2) % 3 = (c - 1) % 3 is free once the K-MMAs of chunk c - 1 are done
                 if (!mbar_wait(&bar_kh[1], (uint32_t)(c - 1) & 1u, &abort_s)) break;
                 if (c + 2 < nch) copy_bk(c + 2);
@@ -804,10 +659,7 @@ __global__ void __launch_bounds__(tc4::THREADS, 1)
             while (!mbar_test(last_bar, last_par) && now_ns() - t0 < WAIT_NS) {}
         }
         for (int st = 0; st < NBK; ++st)
-            if (bk_pend[st]) {
-                const unsigned long long t0 = now_ns();
-                while (!mbar_test(&bar_fbk[st], bk_par[st]) && now_ns() - t0 < WAIT_NS) {}
-            }
+            if ((bk_pend >> st) & 1u) mbar_drain(&bar_fbk[st], (bk_par >> st) & 1u);
         if (abort_s && err_flag) atomicExch(err_flag, 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -842,15 +694,6 @@ __global__ void __launch_bounds__(tc4::THREADS, 1)
 // ------------------------------------------------------------------------ host side
 
 size_t tc3_image_bytes(int m) { return tc3::img_layout(m).total; }
-
-static float tf32_round_host(float x) {
-    uint32_t u;
-    memcpy(&u, &x, 4);
-    if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x1000u) & ~0x1FFFu;   // nearest, ties away (cvt.rna)
-    float r;
-    memcpy(&r, &u, 4);
-    return r;
-}
 
 // B-operand images of G[m][9][n] (n <= 64) and the zero-padded FP32 basis chunks, one buffer
 void tc3_build_images(int n, int m, const double *G, unsigned char *img) {

@@ -96,6 +96,33 @@ def test_tc3_stiffness(B):
         assert fin and e <= tol, (prec, e)
 
 
+@pytest.mark.parametrize("model,B", [("rom_c1", 5), ("rom_c2", 37), ("rom_e2", 7), ("rom_e2_n5", 35),
+                                     ("rom_e2_n30", 9), ("rom_r2_n16_m100", 17), ("rom_r2_n32_m200", 6)])
+def test_tc2_stiffness(model, B):
+    """2D models on the packed tensor-core kernel (S = min(16, 128 // n) instances per CTA along
+    M, N = n rounded up to 16): K of the first Newton pass in BF16, TF32 and the TF32 hi/lo split
+    used for FP32 precision vs K = sum_i G_i^T At_i G_i in FP64 from the same FP32 tangent.  The
+    models span n = 5 .. 40 (S = 16 .. 3, N = 16 .. 48), chunk counts with a ragged last chunk
+    (m = 457, 205, 326) and batches that leave the last CTA partly filled."""
+    from paper_2307_16894_gb300 import inputs
+    rom = workload.load_model(model)
+    d = rom["d"]
+    assert d == 2 and rom["n"] <= 64
+    mu = np.stack([inputs.batch_mu(d, 1, 70_000 + b, 0.2, 0.35)[0] for b in range(B)])
+    coef = inputs.map_coefficients(d, mu)
+    F = np.stack([inputs.stretch_path(d, 70_000 + b, 6)[3] for b in range(B)])
+    errs = {}
+    for prec, tol in (("fp32", 1e-5), ("tf32", 1e-3), ("bf16", 5e-3)):
+        K, At = first_pass_K_At(rom, coef, F, prec)
+        Kref = stiffness_from_tangent(rom["G"], At)
+        err = np.linalg.norm(K - Kref, axis=(1, 2)) / np.linalg.norm(Kref, axis=(1, 2))
+        print("%s n=%d m=%d B=%d %s max rel Frobenius error of K: %.3e" % (model, rom["n"], rom["m"], B, prec,
+                                                                          err.max()))
+        errs[prec] = (np.isfinite(K).all(), err.max(), tol)
+    for prec, (fin, e, tol) in errs.items():
+        assert fin and e <= tol, (prec, e)
+
+
 def residual_check(name, B, prec, fp64_residual=False):
     rom, mu, coef, paths = workload.batch(name, B=B)
     g = GpuRun(rom, coef)
