@@ -130,12 +130,7 @@ __global__ void __launch_bounds__(128) k_fe_eval(FeMesh Mh, FeBatch Bb, int want
         double tau[3][3], Finv[3][3], cpn[6], xin;
         material_value<D, true>(F, cp, Bb.xi[sq], ph, Sm, tau, Finv, cpn, &xin);
         double P[3][3];
-        for (int a = 0; a < 3; ++a)
-            for (int b = 0; b < 3; ++b) {
-                double sum = 0.0;
-                for (int k = 0; k < 3; ++k) sum += tau[a][k] * Finv[b][k];
-                P[a][b] = sum;
-            }
+        stress_P<D>(tau, Finv, P);
         for (int k = 0; k < 6; ++k) Bb.cp_tr[sq * 6 + k] = cpn[k];
         Bb.xi_tr[sq] = xin;
         // f_a = F_mu^-T dN_a: the pull-back of the shape-function gradients

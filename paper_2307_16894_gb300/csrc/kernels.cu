@@ -246,15 +246,7 @@ __global__ void __launch_bounds__(128, (D == 3 && sizeof(TT) == 4) ? 4 : 1) k_co
     double tau[3][3], Finv[3][3], cpn[6], xin;
     material_value<D, sizeof(TT) == sizeof(double)>(F, cp, xi_n, ph, S, tau, Finv, cpn, &xin);
     double P[3][3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int bb = 0; bb < 3; ++bb) {
-            double s = 0.0;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) s += tau[a][k] * Finv[bb][k];
-            P[a][bb] = s;
-        }
+    stress_P<D>(tau, Finv, P);
     // a5: weighted pull-backs
     const size_t vb = (size_t)b * D2 * m + i;
 #pragma unroll

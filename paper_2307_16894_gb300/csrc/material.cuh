@@ -283,28 +283,36 @@ template <int D, bool FP64_SLOPE = true>
 __device__ __forceinline__ void material_value(const double F[3][3], const double cp[6], double xi_n,
                                                const PhaseD &ph, MatState &S, double tau[3][3],
                                                double Finv[3][3], double cp_new[6], double *xi_new) {
+    // plane strain (D = 2): F, C^p^-1 and every tensor below are block-diagonal, the in-plane
+    // 2 x 2 block and the 33 entry (F_33 = 1); only those entries are formed (the FP64 products
+    // with the structural zeros would cost FP64 issue slots: x * 0 is not folded under IEEE rules)
+    constexpr int K = D == 2 ? 2 : 3;
     const double C[3][3] = {{cp[0], cp[1], cp[2]}, {cp[1], cp[3], cp[4]}, {cp[2], cp[4], cp[5]}};
     // Z = C F^T, b = F Z
     double Z[3][3], b[3][3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < K; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
+        for (int j = 0; j < K; ++j) {
             double s = 0.0;
 #pragma unroll
-            for (int k = 0; k < 3; ++k) s += C[i][k] * F[j][k];
+            for (int k = 0; k < K; ++k) s += C[i][k] * F[j][k];
             Z[i][j] = s;
         }
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < K; ++i)
 #pragma unroll
-        for (int j = i; j < 3; ++j) {
+        for (int j = i; j < K; ++j) {
             double s = 0.0;
 #pragma unroll
-            for (int k = 0; k < 3; ++k) s += F[i][k] * Z[k][j];
+            for (int k = 0; k < K; ++k) s += F[i][k] * Z[k][j];
             b[i][j] = s;
             b[j][i] = s;
         }
+    if (D == 2) {
+        b[0][2] = b[2][0] = b[1][2] = b[2][1] = 0.0;
+        b[2][2] = cp[5];
+    }
     if (D == 2) {
         // one Jacobi rotation diagonalises the in-plane block; axis 3 is principal
         double c = 1.0, s = 0.0;
@@ -392,17 +400,31 @@ __device__ __forceinline__ void material_value(const double F[3][3], const doubl
     for (int a = 0; a < 3; ++a) S.tau[a] = ph.Kb * tr + 2.0 * G * S.beta * e[a];
     // Kirchhoff stress tau = N diag(tau_a) N^T
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < K; ++i)
 #pragma unroll
-        for (int j = i; j < 3; ++j) {
+        for (int j = i; j < K; ++j) {
             double s = 0.0;
 #pragma unroll
-            for (int a = 0; a < 3; ++a) s += S.N[i][a] * S.tau[a] * S.N[j][a];
+            for (int a = 0; a < K; ++a) s += S.N[i][a] * S.tau[a] * S.N[j][a];
             tau[i][j] = s;
             tau[j][i] = s;
         }
+    if (D == 2) {
+        tau[0][2] = tau[2][0] = tau[1][2] = tau[2][1] = 0.0;
+        tau[2][2] = S.tau[2];
+    }
     // F^-1 (adjugate)
-    {
+    if (D == 2) {
+        const double det = F[0][0] * F[1][1] - F[0][1] * F[1][0];
+        const double id = 1.0 / det;
+        Finv[0][0] = F[1][1] * id;
+        Finv[0][1] = -F[0][1] * id;
+        Finv[1][0] = -F[1][0] * id;
+        Finv[1][1] = F[0][0] * id;
+        Finv[0][2] = Finv[1][2] = Finv[2][0] = Finv[2][1] = 0.0;
+        Finv[2][2] = 1.0;
+        if (!(det > 0.0)) Finv[0][0] = NAN;   // det F <= 0: flagged as non-finite stress
+    } else {
         double c00 = F[1][1] * F[2][2] - F[1][2] * F[2][1];
         double c01 = F[1][2] * F[2][0] - F[1][0] * F[2][2];
         double c02 = F[1][0] * F[2][1] - F[1][1] * F[2][0];
@@ -426,42 +448,64 @@ __device__ __forceinline__ void material_value(const double F[3][3], const doubl
         for (int a = 0; a < 3; ++a) ln[a] = S.lam[a] * exp(-2.0 * S.dg * 1.2247448713915890491 * S.nh[a]);
         double bn[3][3], Wm[3][3];
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
+        for (int i = 0; i < K; ++i)
 #pragma unroll
-            for (int j = i; j < 3; ++j) {
+            for (int j = i; j < K; ++j) {
                 double s = 0.0;
 #pragma unroll
-                for (int a = 0; a < 3; ++a) s += S.N[i][a] * ln[a] * S.N[j][a];
+                for (int a = 0; a < K; ++a) s += S.N[i][a] * ln[a] * S.N[j][a];
                 bn[i][j] = s;
                 bn[j][i] = s;
             }
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
+        for (int i = 0; i < K; ++i)
 #pragma unroll
-            for (int j = 0; j < 3; ++j) {
+            for (int j = 0; j < K; ++j) {
                 double s = 0.0;
 #pragma unroll
-                for (int k = 0; k < 3; ++k) s += Finv[i][k] * bn[k][j];
+                for (int k = 0; k < K; ++k) s += Finv[i][k] * bn[k][j];
                 Wm[i][j] = s;
             }
         double c[3][3];
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
+        for (int i = 0; i < K; ++i)
 #pragma unroll
-            for (int j = i; j < 3; ++j) {
+            for (int j = i; j < K; ++j) {
                 double s = 0.0;
 #pragma unroll
-                for (int k = 0; k < 3; ++k) s += Wm[i][k] * Finv[j][k];
+                for (int k = 0; k < K; ++k) s += Wm[i][k] * Finv[j][k];
                 c[i][j] = s;
             }
+        if (D == 2) {
+            c[0][2] = c[1][2] = 0.0;
+            c[2][2] = ln[2];   // F_33 = 1
+        }
         cp_new[0] = c[0][0]; cp_new[1] = c[0][1]; cp_new[2] = c[0][2];
         cp_new[3] = c[1][1]; cp_new[4] = c[1][2]; cp_new[5] = c[2][2];
-        if (D == 2) { cp_new[2] = 0.0; cp_new[4] = 0.0; }
         *xi_new = xi_n + S.dg;
     } else {
 #pragma unroll
         for (int k = 0; k < 6; ++k) cp_new[k] = cp[k];
         *xi_new = xi_n;
+    }
+}
+
+// first Piola-Kirchhoff stress P = tau F^-T (plane strain: the in-plane block and P_33 = tau_33)
+template <int D>
+__device__ __forceinline__ void stress_P(const double tau[3][3], const double Finv[3][3], double P[3][3]) {
+    constexpr int K = D == 2 ? 2 : 3;
+#pragma unroll
+    for (int a = 0; a < K; ++a)
+#pragma unroll
+        for (int b = 0; b < K; ++b) {
+            double s = 0.0;
+#pragma unroll
+            for (int k = 0; k < K; ++k) s += tau[a][k] * Finv[b][k];
+            P[a][b] = s;
+        }
+    if (D == 2) {
+        P[0][2] = P[1][2] = P[2][0] = P[2][1] = 0.0;
+        P[2][2] = tau[2][2];
     }
 }
 
@@ -486,11 +530,14 @@ __device__ __forceinline__ void tangent_setup(const MatState &S, const PhaseD &p
     // algorithmic moduli of the radial return in principal log strains
     T cpl = T(0);
     if (S.plastic) cpl = T(6) * G * G * (T(1) / (T(3) * G + to_tangent<T>(S.hs)) - to_tangent<T>(S.dg) / to_tangent<T>(S.q_tr));
+    // plane strain: an in-plane direction dF leaves db, and with it every eigenbasis quantity
+    // below, in the in-plane block, so only that block of c, Z, N, F^-1 and P is formed
+    constexpr int K = D == 2 ? 2 : 3;
     const T nh[3] = {to_tangent<T>(S.nh[0]), to_tangent<T>(S.nh[1]), to_tangent<T>(S.nh[2])};
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
+    for (int a = 0; a < K; ++a)
 #pragma unroll
-        for (int b = 0; b < 3; ++b)
+        for (int b = 0; b < K; ++b)
             td.c[a][b] = to_tangent<T>(ph.Kb) + T(2) * G * beta * ((a == b ? T(1) : T(0)) - T(1) / T(3)) - cpl * nh[a] * nh[b];
     const T gb = G * beta;
     const T l0 = to_tangent<T>(S.lam[0]), l1 = to_tangent<T>(S.lam[1]), l2 = to_tangent<T>(S.lam[2]);
@@ -505,21 +552,21 @@ __device__ __forceinline__ void tangent_setup(const MatState &S, const PhaseD &p
     }
     td.inv2l[0] = T(0.5) / l0;
     td.inv2l[1] = T(0.5) / l1;
-    td.inv2l[2] = T(0.5) / l2;
+    td.inv2l[2] = D == 2 ? T(0) : T(0.5) / l2;
     T C[3][3], Ft[3][3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < K; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) Ft[i][j] = to_tangent<T>(F[i][j]);
+        for (int j = 0; j < K; ++j) Ft[i][j] = to_tangent<T>(F[i][j]);
     C[0][0] = to_tangent<T>(cp[0]); C[0][1] = C[1][0] = to_tangent<T>(cp[1]); C[0][2] = C[2][0] = to_tangent<T>(cp[2]);
     C[1][1] = to_tangent<T>(cp[3]); C[1][2] = C[2][1] = to_tangent<T>(cp[4]); C[2][2] = to_tangent<T>(cp[5]);
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < K; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
+        for (int j = 0; j < K; ++j) {
             T s = T(0);
 #pragma unroll
-            for (int k = 0; k < 3; ++k) s += C[i][k] * Ft[j][k];
+            for (int k = 0; k < K; ++k) s += C[i][k] * Ft[j][k];
             td.Z[i][j] = s;
             td.N[i][j] = to_tangent<T>(S.N[i][j]);
             td.Finv[i][j] = to_tangent<T>(Finv[i][j]);
@@ -527,50 +574,74 @@ __device__ __forceinline__ void tangent_setup(const MatState &S, const PhaseD &p
         }
 }
 
+// x_c of (x_0, x_1, x_2) by selects, so that a run-time c indexes no array (an array indexed at
+// run time would be placed in local memory)
+template <int D, typename T>
+__device__ __forceinline__ T pick(int c, T x0, T x1, T x2) {
+    return D == 2 ? (c == 0 ? x0 : x1) : (c == 0 ? x0 : (c == 1 ? x1 : x2));
+}
+
 // dP for the direction dF = e_c (x) f  (dF_kl = delta_kc f_l).  Only the D x D block is formed.
 template <int D, typename T>
 __device__ __forceinline__ void tangent_direction(const TangentData<T> &td, int c, const T f[3], T dP[3][3]) {
+    T Nc[3], Fc[3];   // row c of N, column c of F^-1
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        Nc[a] = pick<D, T>(c, td.N[0][a], td.N[1][a], td.N[2][a]);
+        Fc[a] = pick<D, T>(c, td.Finv[a][0], td.Finv[a][1], td.Finv[a][2]);
+    }
+    // plane strain: dF, db and the eigenbasis components stay in the in-plane block (K = 2)
+    constexpr int K = D == 2 ? 2 : 3;
     // g = Z^T f, h = N^T g
     T g[3], h[3];
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
+    for (int j = 0; j < K; ++j) {
         T s = T(0);
 #pragma unroll
         for (int l = 0; l < D; ++l) s += td.Z[l][j] * f[l];
         g[j] = s;
     }
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
+    for (int a = 0; a < K; ++a) {
         T s = T(0);
 #pragma unroll
-        for (int j = 0; j < 3; ++j) s += td.N[j][a] * g[j];
+        for (int j = 0; j < K; ++j) s += td.N[j][a] * g[j];
         h[a] = s;
     }
     // db'_ab = N_ca h_b + h_a N_cb
     T dbp[3][3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
+    for (int a = 0; a < K; ++a)
 #pragma unroll
-        for (int b = a; b < 3; ++b) {
-            dbp[a][b] = td.N[c][a] * h[b] + h[a] * td.N[c][b];
+        for (int b = a; b < K; ++b) {
+            dbp[a][b] = Nc[a] * h[b] + h[a] * Nc[b];
             dbp[b][a] = dbp[a][b];
         }
     T dt[3][3];
-    T w[3] = {dbp[0][0] * td.inv2l[0], dbp[1][1] * td.inv2l[1], dbp[2][2] * td.inv2l[2]};
+    T w[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) dt[a][a] = td.c[a][0] * w[0] + td.c[a][1] * w[1] + td.c[a][2] * w[2];
+    for (int a = 0; a < K; ++a) w[a] = dbp[a][a] * td.inv2l[a];
+#pragma unroll
+    for (int a = 0; a < K; ++a) {
+        T s = T(0);
+#pragma unroll
+        for (int b = 0; b < K; ++b) s += td.c[a][b] * w[b];
+        dt[a][a] = s;
+    }
     dt[0][1] = dt[1][0] = td.th[0] * dbp[0][1];
-    dt[0][2] = dt[2][0] = td.th[1] * dbp[0][2];
-    dt[1][2] = dt[2][1] = td.th[2] * dbp[1][2];
+    if (D == 3) {
+        dt[0][2] = dt[2][0] = td.th[1] * dbp[0][2];
+        dt[1][2] = dt[2][1] = td.th[2] * dbp[1][2];
+    }
     // d tau = N dt N^T (D x D block), then dP = d tau F^-T - (P f) (x) F^-1[:, c]
     T M[3][3];
 #pragma unroll
     for (int i = 0; i < D; ++i)
 #pragma unroll
-        for (int b = 0; b < 3; ++b) {
+        for (int b = 0; b < K; ++b) {
             T s = T(0);
 #pragma unroll
-            for (int a = 0; a < 3; ++a) s += td.N[i][a] * dt[a][b];
+            for (int a = 0; a < K; ++a) s += td.N[i][a] * dt[a][b];
             M[i][b] = s;
         }
     T dtau[3][3];
@@ -580,7 +651,7 @@ __device__ __forceinline__ void tangent_direction(const TangentData<T> &td, int 
         for (int j = 0; j < D; ++j) {
             T s = T(0);
 #pragma unroll
-            for (int b = 0; b < 3; ++b) s += M[i][b] * td.N[j][b];
+            for (int b = 0; b < K; ++b) s += M[i][b] * td.N[j][b];
             dtau[i][j] = s;
         }
     T Pf[3];
@@ -598,7 +669,7 @@ __device__ __forceinline__ void tangent_direction(const TangentData<T> &td, int 
             T s = T(0);
 #pragma unroll
             for (int k = 0; k < D; ++k) s += dtau[i][k] * td.Finv[j][k];
-            dP[i][j] = s - Pf[i] * td.Finv[j][c];
+            dP[i][j] = s - Pf[i] * Fc[j];
         }
 }
 
