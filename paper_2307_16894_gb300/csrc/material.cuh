@@ -151,11 +151,34 @@ __device__ __forceinline__ double f2d_exact(float x) {
     return __longlong_as_double((long long)(sign | (ee << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29)));
 }
 
+// 1/x to ~1e-14 relative: the FP32 reciprocal (x converted by integer operations) and one FP64
+// Newton step r (2 - x r).  For |x| in [1e-30, 1e30]; used where the result only scales a
+// quantity that is tiny against 1 (Jacobi rotation angles), so that 1e-14 relative error is far
+// below FP64 rounding of the final values.
+__device__ __forceinline__ double rcp_nr(double x) {
+    const double r = f2d_exact(__frcp_rn(to_tangent<float>(x)));
+    return r * fma(-x, r, 2.0);
+}
+
+// 1 / sqrt(x) for x = 1 + d, |d| <= 1e-6: 1 - d/2 + 3 d^2 / 8 (the next term, 5 d^3 / 16, is
+// below 3.2e-19); otherwise the library square root and division
+__device__ __forceinline__ double rsqrt_near1(double x) {
+    const double d = x - 1.0;
+    if (fabs(d) <= 1e-6) return fma(d, fma(0.375, d, -0.5), 1.0);
+    return 1.0 / sqrt(x);
+}
+
 // FP64-accurate symmetric 3x3 eigen-decomposition: FP32 Jacobi gives approximate
-// eigenvectors, which are made exactly orthonormal in FP64 (Gram-Schmidt + cross product)
-// and used to rotate b in FP64; FP64 Jacobi sweeps then finish the nearly diagonal matrix.
-// Rotations with |2 a_pq| <= 1e-3 |a_qq - a_pp| use the series t = e/2 - e^3/8,
-// c = 1 - t^2/2 + 3 t^4/8 (e = 2 a_pq / (a_qq - a_pp); truncation below 1e-16).
+// eigenvectors, which are made exactly orthonormal in FP64 (Gram-Schmidt + cross product; the
+// FP32 vectors have norms within ~1e-7 of 1, so their normalisation is a short series) and used
+// to rotate b in FP64; FP64 Jacobi sweeps then finish the nearly diagonal matrix (the first
+// sweep from off-diagonals ~1e-7 |lambda|, the second from ~1e-14 |lambda|).  Rotation
+// t = tan(angle) by the size of e = 2 a_pq / (a_qq - a_pp):
+//   |e| <= 1e-8: t = e / 2 and c = 1 (t^2 / 2 < 1.3e-17, below FP64 rounding of 1);
+//   |e| <= 1e-3: the series t = e/2 - e^3/8, c = 1 - t^2/2 + 3 t^4/8 (truncation below 1e-16);
+//   otherwise the closed form.
+// In the first two cases e is formed with rcp_nr (its 1e-14 relative error moves t by less
+// than 1e-17 absolute).
 __device__ __forceinline__ void eig3_mixed(const double b[3][3], double lam[3], double N[3][3]) {
     float af[3][3], Vf[3][3];
 #pragma unroll
@@ -168,7 +191,7 @@ __device__ __forceinline__ void eig3_mixed(const double b[3][3], double lam[3], 
         double n0 = 0.0;
 #pragma unroll
         for (int k = 0; k < 3; ++k) { q0[k] = f2d_exact(Vf[k][0]); n0 += q0[k] * q0[k]; }
-        const double i0 = 1.0 / sqrt(n0);
+        const double i0 = rsqrt_near1(n0);
 #pragma unroll
         for (int k = 0; k < 3; ++k) q0[k] *= i0;
         double dt = 0.0;
@@ -177,7 +200,7 @@ __device__ __forceinline__ void eig3_mixed(const double b[3][3], double lam[3], 
         double n1 = 0.0;
 #pragma unroll
         for (int k = 0; k < 3; ++k) { q1[k] = f2d_exact(Vf[k][1]) - dt * q0[k]; n1 += q1[k] * q1[k]; }
-        const double i1 = 1.0 / sqrt(n1);
+        const double i1 = rsqrt_near1(n1);
 #pragma unroll
         for (int k = 0; k < 3; ++k) q1[k] *= i1;
         q2[0] = q0[1] * q1[2] - q0[2] * q1[1];
@@ -218,9 +241,27 @@ __device__ __forceinline__ void eig3_mixed(const double b[3][3], double lam[3], 
             const double apq = a[p][q];
             if (fabs(apq) <= 1e-300) continue;
             const double gap = a[q][q] - a[p][p];
+            const double ag = fabs(gap);
             double t, c;
-            if (fabs(2.0 * apq) <= 1e-3 * fabs(gap)) {
-                const double e = 2.0 * apq / gap;
+            if (fabs(2.0 * apq) <= 1e-8 * ag && ag >= 1e-30 && ag <= 1e30) {
+                // tiny angle: a rotation with c = 1
+                t = apq * rcp_nr(gap);
+                a[p][p] -= t * apq;
+                a[q][q] += t * apq;
+                a[p][q] = a[q][p] = 0.0;
+                const double arp = a[r][p], arq = a[r][q];
+                a[r][p] = a[p][r] = fma(-t, arq, arp);
+                a[r][q] = a[q][r] = fma(t, arp, arq);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const double vkp = V[k][p], vkq = V[k][q];
+                    V[k][p] = fma(-t, vkq, vkp);
+                    V[k][q] = fma(t, vkp, vkq);
+                }
+                continue;
+            }
+            if (fabs(2.0 * apq) <= 1e-3 * ag) {
+                const double e = (ag >= 1e-30 && ag <= 1e30) ? 2.0 * apq * rcp_nr(gap) : 2.0 * apq / gap;
                 t = 0.5 * e - 0.125 * e * e * e;
                 const double t2 = t * t;
                 c = 1.0 - 0.5 * t2 + 0.375 * t2 * t2;
@@ -344,22 +385,38 @@ __device__ __forceinline__ void material_value(const double F[3][3], const doubl
     const double enorm = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
     const double G = ph.G;
     S.q_tr = sqrt(6.0) * G * enorm;
-    double h0;
-    const double sy_n = yield_stress(ph, xi_n, &h0);
-    S.plastic = (S.q_tr - sy_n) > 1e-12 * sy_n;
+    // FP32 copies by integer operations on the bit patterns (the conversion instruction would
+    // occupy the FP64 pipe): the power-law constants and the trial state, for the FP32 filter and
+    // the FP32 Newton start below
+    const bool pw = ph.law == 1 && !ph.elastic;
+    const float qf = to_tangent<float>(S.q_tr), xin = to_tangent<float>(xi_n);
+    const float s0f = to_tangent<float>(ph.s0), kf = to_tangent<float>(ph.k), pf = to_tangent<float>(ph.p);
+    // yield check (Eq. j2_2).  Power law: sigma_y(xi_n) in FP32 (relative error < 1e-6) decides the
+    // points more than 1e-5 below the yield surface elastic without the FP64 evaluation; the FP64
+    // test decides all others, so the decision is the FP64 test's everywhere
+    float syf = 0.f;
+    bool maybe_plastic = true;
+    if (pw) {
+        syf = s0f * expf(pf * logf(1.f + kf * xin));
+        maybe_plastic = qf >= syf * (1.f - 1e-5f);
+    }
+    double h0 = 0.0, sy_n = 0.0;
+    if (maybe_plastic) sy_n = yield_stress(ph, xi_n, &h0);
+    S.plastic = maybe_plastic && (S.q_tr - sy_n) > 1e-12 * sy_n;
     S.dg = 0.0;
     S.beta = 1.0;
     S.hs = h0;
     if (S.plastic) {
-        const double x0 = (S.q_tr - sy_n) / (3.0 * G + h0);
-        // power law: Newton in FP32 first (cheap pipe) to ~1e-7, then FP64 Newton steps; from an
-        // FP32-accurate start one FP64 step reaches FP64 precision (quadratic convergence), so the
-        // FP64 loop stops once a step is below 1e-6 |dg| (otherwise at 1e-15 |dg|, as from x0)
+        // power law: Newton in FP32 first (cheap pipe) to ~1e-7 from the FP32 linearised start,
+        // then FP64 Newton steps; from an FP32-accurate start one FP64 step reaches FP64 precision
+        // (quadratic convergence, and the hardening curvature is small against 3G), so the FP64
+        // loop stops once a step is below 1e-6 |dg| (otherwise at 1e-15 |dg|, as from the FP64
+        // linearised start)
         bool conv32 = false;
-        float xf = (float)x0;
-        if (ph.law == 1) {
-            const float qf = (float)S.q_tr, g3 = (float)(3.0 * G), xin = (float)xi_n;
-            const float s0f = (float)ph.s0, kf = (float)ph.k, pf = (float)ph.p;
+        float xf = 0.f;
+        if (pw) {
+            const float g3 = to_tangent<float>(3.0 * G);
+            xf = (qf - syf) / (g3 + syf * pf * kf / (1.f + kf * xin));
             for (int it = 0; it < 30; ++it) {
                 const float base = 1.f + kf * (xin + xf);
                 const float sy = s0f * expf(pf * logf(base));
@@ -369,7 +426,7 @@ __device__ __forceinline__ void material_value(const double F[3][3], const doubl
                 if (fabsf(step) <= 1e-6f * fabsf(xf)) { conv32 = isfinite(xf) && xf > 0.f; break; }
             }
         }
-        double x = conv32 ? (double)xf : x0;
+        double x = conv32 ? f2d_exact(xf) : (S.q_tr - sy_n) / (3.0 * G + h0);
         double hs = h0;
         for (int it = 0; it < 60; ++it) {
             const double sy = yield_stress(ph, xi_n + x, &hs);
@@ -382,16 +439,17 @@ __device__ __forceinline__ void material_value(const double F[3][3], const doubl
             yield_stress(ph, xi_n + x, &hs);
         } else if (ph.law == 1) {
             // slope for the (FP32) tangent only
-            const float base = 1.f + (float)ph.k * ((float)xi_n + (float)x);
-            hs = (double)((float)ph.s0 * expf((float)ph.p * logf(base)) * (float)ph.p * (float)ph.k / base);
+            const float base = 1.f + kf * (xin + to_tangent<float>(x));
+            hs = f2d_exact(s0f * expf(pf * logf(base)) * pf * kf / base);
         } else {
             hs = ph.k;
         }
         S.dg = x;
         S.hs = hs;
         S.beta = 1.0 - 3.0 * G * x / S.q_tr;
+        const double ien = 1.0 / enorm;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) S.nh[a] = e[a] / enorm;
+        for (int a = 0; a < 3; ++a) S.nh[a] = e[a] * ien;
     } else {
 #pragma unroll
         for (int a = 0; a < 3; ++a) S.nh[a] = 0.0;
