@@ -127,10 +127,8 @@ __global__ void __launch_bounds__(128) k_fe_eval(FeMesh Mh, FeBatch Bb, int want
         double cp[6];
         for (int k = 0; k < 6; ++k) cp[k] = Bb.cp[sq * 6 + k];
         MatState Sm;
-        double tau[3][3], Finv[3][3], cpn[6], xin;
-        material_value<D, true>(F, cp, Bb.xi[sq], ph, Sm, tau, Finv, cpn, &xin);
-        double P[3][3];
-        stress_P<D>(tau, Finv, P);
+        double P[3][3], Finv[3][3], cpn[6], xin;
+        material_value<D, true>(F, cp, Bb.xi[sq], ph, Sm, P, Finv, cpn, &xin);
         for (int k = 0; k < 6; ++k) Bb.cp_tr[sq * 6 + k] = cpn[k];
         Bb.xi_tr[sq] = xin;
         // f_a = F_mu^-T dN_a: the pull-back of the shape-function gradients

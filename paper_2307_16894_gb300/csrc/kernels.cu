@@ -111,6 +111,77 @@ __global__ void k_advance(int32_t *counts) {
     counts[1] = 0;
 }
 
+// ------------------------------------------------------------------ geometry
+// a1: F_mu = I + sum_k mu_k Gmu_k(X_i) at cubature point i of instance b (Eq. weakform-dep-mapped);
+// returns F_mu^-1 and w_i |det F_mu|
+template <int D>
+__device__ __forceinline__ void geometry_point(const Model &M, const double *mu, int64_t b, int i, double Fmi[D][D],
+                                               double *wJ) {
+    const int m = M.m;
+    double Fm[D][D];
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int r = 0; r < D; ++r) {
+            double s = (a == r) ? 1.0 : 0.0;
+            for (int k = 0; k < M.n_par; ++k)
+                s += mu[b * M.n_par + k] * M.Gmu_T[((size_t)(a * D + r) * M.n_par + k) * m + i];
+            Fm[a][r] = s;
+        }
+    double J;
+    if (D == 2) {
+        const double det = Fm[0][0] * Fm[1][1] - Fm[0][1] * Fm[1][0];
+        J = fabs(det);
+        const double id = 1.0 / det;
+        Fmi[0][0] = Fm[1][1] * id; Fmi[0][1] = -Fm[0][1] * id;
+        Fmi[1][0] = -Fm[1][0] * id; Fmi[1][1] = Fm[0][0] * id;
+    } else {
+        double c00 = Fm[1][1] * Fm[2][2] - Fm[1][2] * Fm[2][1];
+        double c01 = Fm[1][2] * Fm[2][0] - Fm[1][0] * Fm[2][2];
+        double c02 = Fm[1][0] * Fm[2][1] - Fm[1][1] * Fm[2][0];
+        const double det = Fm[0][0] * c00 + Fm[0][1] * c01 + Fm[0][2] * c02;
+        J = fabs(det);
+        const double id = 1.0 / det;
+        Fmi[0][0] = c00 * id; Fmi[1][0] = c01 * id; Fmi[2][0] = c02 * id;
+        Fmi[0][1] = (Fm[0][2] * Fm[2][1] - Fm[0][1] * Fm[2][2]) * id;
+        Fmi[1][1] = (Fm[0][0] * Fm[2][2] - Fm[0][2] * Fm[2][0]) * id;
+        Fmi[2][1] = (Fm[0][1] * Fm[2][0] - Fm[0][0] * Fm[2][1]) * id;
+        Fmi[0][2] = (Fm[0][1] * Fm[1][2] - Fm[0][2] * Fm[1][1]) * id;
+        Fmi[1][2] = (Fm[0][2] * Fm[1][0] - Fm[0][0] * Fm[1][2]) * id;
+        Fmi[2][2] = (Fm[0][0] * Fm[1][1] - Fm[0][1] * Fm[1][0]) * id;
+    }
+    *wJ = M.w[i] * J;
+}
+
+// the per-geometry cache geo[b][c][i]: F_mu^-1 entries c < d^2 (row-major), w_i J at c = d^2.  The
+// geometry of an instance is fixed over its load steps, so the FP64 work of a1 is done once
+// instead of in every Newton pass (FP64 is the constitutive kernel's bound; the cache adds
+// (d^2 + 1) x 8 bytes of reads per point and pass)
+template <int D>
+__global__ void k_geometry(Model M, const double *__restrict__ mu, int64_t B, double *__restrict__ geo) {
+    constexpr int D2 = D * D;
+    const int m = M.m;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= B * m) return;
+    const int64_t b = gid / m;
+    const int i = (int)(gid - b * m);
+    double Fmi[D][D], wJ;
+    geometry_point<D>(M, mu, b, i, Fmi, &wJ);
+    double *gp = geo + (size_t)b * (D2 + 1) * m + i;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int r = 0; r < D; ++r) gp[(size_t)(a * D + r) * m] = Fmi[a][r];
+    gp[(size_t)D2 * m] = wJ;
+}
+
+void launch_geometry(const Model &M, const double *mu, int64_t B, double *geo, cudaStream_t s) {
+    const int64_t n = B * M.m;
+    const unsigned grid = (unsigned)((n + 255) / 256);
+    if (M.d == 2) k_geometry<2><<<grid, 256, 0, s>>>(M, mu, B, geo);
+    else k_geometry<3><<<grid, 256, 0, s>>>(M, mu, B, geo);
+}
+
 // ------------------------------------------------------------------ constitutive
 // Mixed-precision kinematics in double-float arithmetic (FP32 pairs, products by TwoProd,
 // sums by TwoSum with a compensation term; Ogita, Rump & Oishi 2005): the FP64 pipe of this GPU
@@ -150,38 +221,18 @@ __global__ void __launch_bounds__(128, (D == 3 && sizeof(TT) == 4) ? 4 : 1) k_co
     const int i = (int)(gid - p * m);
     const int64_t b = Bt.list[p];
 
-    // a1: geometry F_mu = I + sum_k mu_k Gmu_k(X_i)
-    double Fm[D][D];
-    for (int a = 0; a < D; ++a)
-        for (int r = 0; r < D; ++r) {
-            double s = (a == r) ? 1.0 : 0.0;
-            for (int k = 0; k < M.n_par; ++k)
-                s += Bt.mu[b * M.n_par + k] * M.Gmu_T[((size_t)(a * D + r) * M.n_par + k) * m + i];
-            Fm[a][r] = s;
-        }
-    double Fmi[D][D], J;
-    if (D == 2) {
-        const double det = Fm[0][0] * Fm[1][1] - Fm[0][1] * Fm[1][0];
-        J = fabs(det);
-        const double id = 1.0 / det;
-        Fmi[0][0] = Fm[1][1] * id; Fmi[0][1] = -Fm[0][1] * id;
-        Fmi[1][0] = -Fm[1][0] * id; Fmi[1][1] = Fm[0][0] * id;
+    // a1: geometry F_mu = I + sum_k mu_k Gmu_k(X_i): F_mu^-1 and w_i J from the per-geometry cache
+    double Fmi[D][D], wJ;
+    if (Bt.geo) {
+        const double *gp = Bt.geo + (size_t)b * (D2 + 1) * m + i;
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+            for (int r = 0; r < D; ++r) Fmi[a][r] = gp[(size_t)(a * D + r) * m];
+        wJ = gp[(size_t)D2 * m];
     } else {
-        double c00 = Fm[1][1] * Fm[2][2] - Fm[1][2] * Fm[2][1];
-        double c01 = Fm[1][2] * Fm[2][0] - Fm[1][0] * Fm[2][2];
-        double c02 = Fm[1][0] * Fm[2][1] - Fm[1][1] * Fm[2][0];
-        const double det = Fm[0][0] * c00 + Fm[0][1] * c01 + Fm[0][2] * c02;
-        J = fabs(det);
-        const double id = 1.0 / det;
-        Fmi[0][0] = c00 * id; Fmi[1][0] = c01 * id; Fmi[2][0] = c02 * id;
-        Fmi[0][1] = (Fm[0][2] * Fm[2][1] - Fm[0][1] * Fm[2][2]) * id;
-        Fmi[1][1] = (Fm[0][0] * Fm[2][2] - Fm[0][2] * Fm[2][0]) * id;
-        Fmi[2][1] = (Fm[0][1] * Fm[2][0] - Fm[0][0] * Fm[2][1]) * id;
-        Fmi[0][2] = (Fm[0][1] * Fm[1][2] - Fm[0][2] * Fm[1][1]) * id;
-        Fmi[1][2] = (Fm[0][2] * Fm[1][0] - Fm[0][0] * Fm[1][2]) * id;
-        Fmi[2][2] = (Fm[0][0] * Fm[1][1] - Fm[0][1] * Fm[1][0]) * id;
+        geometry_point<D>(M, Bt.mu, b, i, Fmi, &wJ);
     }
-    const double wJ = M.w[i] * J;
 
     // a2: kinematics H = G_i a, F = Ubar + H F_mu^-1
     double H[D2];
@@ -243,22 +294,26 @@ __global__ void __launch_bounds__(128, (D == 3 && sizeof(TT) == 4) ? 4 : 1) k_co
     const double xi_n = Bt.xi[(size_t)b * m + i];
     const PhaseD &ph = c_phases[M.phase[i]];
     MatState S;
-    double tau[3][3], Finv[3][3], cpn[6], xin;
-    material_value<D, sizeof(TT) == sizeof(double)>(F, cp, xi_n, ph, S, tau, Finv, cpn, &xin);
-    double P[3][3];
-    stress_P<D>(tau, Finv, P);
+    double P[3][3], Finv[3][3], cpn[6], xin;
+    material_value<D, sizeof(TT) == sizeof(double)>(F, cp, xi_n, ph, S, P, Finv, cpn, &xin);
     // a5: weighted pull-backs
     const size_t vb = (size_t)b * D2 * m + i;
 #pragma unroll
-    for (int a = 0; a < D; ++a)
+    for (int a = 0; a < D; ++a) {
+        double wp[D];
+#pragma unroll
+        for (int r = 0; r < D; ++r) {
+            wp[r] = wJ * P[a][r];
+            Bt.wP[vb + (size_t)(a * D + r) * m] = wp[r];
+        }
 #pragma unroll
         for (int r = 0; r < D; ++r) {
             double s = 0.0;
 #pragma unroll
-            for (int bb = 0; bb < D; ++bb) s += P[a][bb] * Fmi[r][bb];
-            Bt.v[vb + (size_t)(a * D + r) * m] = wJ * s;
-            Bt.wP[vb + (size_t)(a * D + r) * m] = wJ * P[a][r];
+            for (int bb = 0; bb < D; ++bb) s += wp[bb] * Fmi[r][bb];
+            Bt.v[vb + (size_t)(a * D + r) * m] = s;
         }
+    }
     if (D == 2) {
         Bt.cp_tr[hb] = cpn[0]; Bt.cp_tr[hb + m] = cpn[1];
         Bt.cp_tr[hb + 2 * (size_t)m] = cpn[3]; Bt.cp_tr[hb + 3 * (size_t)m] = cpn[5];
@@ -288,7 +343,7 @@ __global__ void __launch_bounds__(128, (D == 3 && sizeof(TT) == 4) ? 4 : 1) k_co
         for (int s = 0; s < D; ++s) {
             TT f[3] = {TT(0), TT(0), TT(0)};
 #pragma unroll
-            for (int l = 0; l < D; ++l) f[l] = Fmt[s][l];
+            for (int l = 0; l < D; ++l) f[l] = pick<D, TT>(s, Fmt[0][l], Fmt[1][l], Fmt[D - 1][l]);
             TT dP[3][3];
             tangent_direction<D, TT>(td, c, f, dP);
             const int col = c * D + s;

@@ -57,6 +57,8 @@ struct Batch {
     double *r0_prev;         // [B] residual norm of the previous-step predictor when last evaluated (+inf
                              // if never), the reference of the learned start; may be null
     const int *err;          // tensor-core pipeline error flag (a bounded wait gave up), may be null
+    const double *geo;       // [B][d2 + 1][m] F_mu^-1 (row-major) and w_i J_mu per point, computed once
+                             // per geometry (k_geometry); null: the constitutive kernel forms them
 };
 
 // learned Newton start (mlp.cu)

@@ -179,13 +179,26 @@ __device__ __forceinline__ double rsqrt_near1(double x) {
 //   otherwise the closed form.
 // In the first two cases e is formed with rcp_nr (its 1e-14 relative error moves t by less
 // than 1e-17 absolute).
-__device__ __forceinline__ void eig3_mixed(const double b[3][3], double lam[3], double N[3][3]) {
+// Input b = F C F^T given by F and C (symmetric): b itself is formed only in FP32 for the
+// approximate start; the FP64 matrix is Q^T b Q = W^T C W with W = F^T Q.
+__device__ __forceinline__ void eig3_mixed(const double F[3][3], const double C[3][3], double lam[3], double N[3][3]) {
     float af[3][3], Vf[3][3];
+    {
+        float Ff[3][3], Cf[3][3], Zf[3][3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+        for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) af[i][j] = to_tangent<float>(b[i][j]);   // approximate start only
-    jacobi3_f32(af, Vf);
+            for (int j = 0; j < 3; ++j) { Ff[i][j] = to_tangent<float>(F[i][j]); Cf[i][j] = to_tangent<float>(C[i][j]); }
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) Zf[i][j] = Cf[i][0] * Ff[j][0] + Cf[i][1] * Ff[j][1] + Cf[i][2] * Ff[j][2];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = i; j < 3; ++j) af[i][j] = af[j][i] = Ff[i][0] * Zf[0][j] + Ff[i][1] * Zf[1][j] + Ff[i][2] * Zf[2][j];
+    }
+    jacobi3_f32(af, Vf);   // approximate start only
     double q0[3], q1[3], q2[3];
     {
         double n0 = 0.0;
@@ -208,14 +221,23 @@ __device__ __forceinline__ void eig3_mixed(const double b[3][3], double lam[3], 
         q2[2] = q0[0] * q1[1] - q0[1] * q1[0];
     }
     const double Q[3][3] = {{q0[0], q1[0], q2[0]}, {q0[1], q1[1], q2[1]}, {q0[2], q1[2], q2[2]}};
-    double a[3][3], T[3][3];
+    double a[3][3], W[3][3], T[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             double sm = 0.0;
 #pragma unroll
-            for (int k = 0; k < 3; ++k) sm += b[i][k] * Q[k][j];
+            for (int k = 0; k < 3; ++k) sm += F[k][i] * Q[k][j];
+            W[i][j] = sm;
+        }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            double sm = 0.0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) sm += C[i][k] * W[k][j];
             T[i][j] = sm;
         }
 #pragma unroll
@@ -224,7 +246,7 @@ __device__ __forceinline__ void eig3_mixed(const double b[3][3], double lam[3], 
         for (int j = i; j < 3; ++j) {
             double sm = 0.0;
 #pragma unroll
-            for (int k = 0; k < 3; ++k) sm += Q[k][i] * T[k][j];
+            for (int k = 0; k < 3; ++k) sm += W[k][i] * T[k][j];
             a[i][j] = sm;
             a[j][i] = sm;
         }
@@ -318,43 +340,28 @@ struct MatState {
 };
 
 // Value part.  F: 3x3 (plane strain: F[2][2] = 1, F[i][2] = F[2][i] = 0), cp: C^p^-1
-// (00, 01, 02, 11, 12, 22).  Outputs the state, the Kirchhoff stress tau (3x3), the
-// updated history cp_new, xi_new.  D = 2 uses the block structure.
+// (00, 01, 02, 11, 12, 22).  Outputs the state, the first Piola-Kirchhoff stress P = tau F^-T
+// (3x3), F^-1, the updated history cp_new, xi_new.  D = 2 uses the block structure.
 template <int D, bool FP64_SLOPE = true>
 __device__ __forceinline__ void material_value(const double F[3][3], const double cp[6], double xi_n,
-                                               const PhaseD &ph, MatState &S, double tau[3][3],
+                                               const PhaseD &ph, MatState &S, double P[3][3],
                                                double Finv[3][3], double cp_new[6], double *xi_new) {
     // plane strain (D = 2): F, C^p^-1 and every tensor below are block-diagonal, the in-plane
     // 2 x 2 block and the 33 entry (F_33 = 1); only those entries are formed (the FP64 products
     // with the structural zeros would cost FP64 issue slots: x * 0 is not folded under IEEE rules)
     constexpr int K = D == 2 ? 2 : 3;
     const double C[3][3] = {{cp[0], cp[1], cp[2]}, {cp[1], cp[3], cp[4]}, {cp[2], cp[4], cp[5]}};
-    // Z = C F^T, b = F Z
-    double Z[3][3], b[3][3];
-#pragma unroll
-    for (int i = 0; i < K; ++i)
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-            double s = 0.0;
-#pragma unroll
-            for (int k = 0; k < K; ++k) s += C[i][k] * F[j][k];
-            Z[i][j] = s;
-        }
-#pragma unroll
-    for (int i = 0; i < K; ++i)
-#pragma unroll
-        for (int j = i; j < K; ++j) {
-            double s = 0.0;
-#pragma unroll
-            for (int k = 0; k < K; ++k) s += F[i][k] * Z[k][j];
-            b[i][j] = s;
-            b[j][i] = s;
-        }
     if (D == 2) {
-        b[0][2] = b[2][0] = b[1][2] = b[2][1] = 0.0;
-        b[2][2] = cp[5];
-    }
-    if (D == 2) {
+        // b = F C F^T (in-plane block; b_33 = c_33): Z = C F^T, b = F Z
+        double Z[2][2], b[2][2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) Z[i][j] = C[i][0] * F[j][0] + C[i][1] * F[j][1];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = i; j < 2; ++j) b[i][j] = b[j][i] = F[i][0] * Z[0][j] + F[i][1] * Z[1][j];
         // one Jacobi rotation diagonalises the in-plane block; axis 3 is principal
         double c = 1.0, s = 0.0;
         const double apq = b[0][1];
@@ -369,12 +376,12 @@ __device__ __forceinline__ void material_value(const double F[3][3], const doubl
             S.lam[0] = b[0][0];
             S.lam[1] = b[1][1];
         }
-        S.lam[2] = b[2][2];
+        S.lam[2] = cp[5];
         S.N[0][0] = c;  S.N[0][1] = s;  S.N[0][2] = 0.0;
         S.N[1][0] = -s; S.N[1][1] = c;  S.N[1][2] = 0.0;
         S.N[2][0] = 0.0; S.N[2][1] = 0.0; S.N[2][2] = 1.0;
     } else {
-        eig3_mixed(b, S.lam, S.N);
+        eig3_mixed(F, C, S.lam, S.N);
     }
     double eps[3];
 #pragma unroll
@@ -456,21 +463,6 @@ __device__ __forceinline__ void material_value(const double F[3][3], const doubl
     }
 #pragma unroll
     for (int a = 0; a < 3; ++a) S.tau[a] = ph.Kb * tr + 2.0 * G * S.beta * e[a];
-    // Kirchhoff stress tau = N diag(tau_a) N^T
-#pragma unroll
-    for (int i = 0; i < K; ++i)
-#pragma unroll
-        for (int j = i; j < K; ++j) {
-            double s = 0.0;
-#pragma unroll
-            for (int a = 0; a < K; ++a) s += S.N[i][a] * S.tau[a] * S.N[j][a];
-            tau[i][j] = s;
-            tau[j][i] = s;
-        }
-    if (D == 2) {
-        tau[0][2] = tau[2][0] = tau[1][2] = tau[2][1] = 0.0;
-        tau[2][2] = S.tau[2];
-    }
     // F^-1 (adjugate)
     if (D == 2) {
         const double det = F[0][0] * F[1][1] - F[0][1] * F[1][0];
@@ -499,41 +491,54 @@ __device__ __forceinline__ void material_value(const double F[3][3], const doubl
         Finv[2][2] = (F[0][0] * F[1][1] - F[0][1] * F[1][0]) * id;
         if (!(det > 0.0)) Finv[0][0] = NAN;   // det F <= 0: flagged as non-finite stress
     }
+    // M = F^-1 N: P = tau F^-T = N diag(tau_a) N^T F^-T = N diag(tau_a) M^T, and the plastic
+    // history below C^p_new^-1 = F^-1 b_new F^-T = M diag(b_new,a) M^T
+    double Mx[3][3];
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+#pragma unroll
+        for (int a = 0; a < K; ++a) {
+            double s = 0.0;
+#pragma unroll
+            for (int k = 0; k < K; ++k) s += Finv[i][k] * S.N[k][a];
+            Mx[i][a] = s;
+        }
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        double nt[3];
+#pragma unroll
+        for (int a = 0; a < K; ++a) nt[a] = S.N[i][a] * S.tau[a];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            double s = 0.0;
+#pragma unroll
+            for (int a = 0; a < K; ++a) s += nt[a] * Mx[j][a];
+            P[i][j] = s;
+        }
+    }
+    if (D == 2) {
+        P[0][2] = P[1][2] = P[2][0] = P[2][1] = 0.0;
+        P[2][2] = S.tau[2];   // F_33 = 1, N_33 = 1
+    }
     if (S.plastic) {
-        // b_new = N diag(lambda_a exp(-2 dg sqrt(3/2) nhat_a)) N^T ; C^p_new^-1 = F^-1 b_new F^-T
+        // b_new = N diag(lambda_a exp(-2 dg sqrt(3/2) nhat_a)) N^T (Eq. j2_10 in the spatial form)
         double ln[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) ln[a] = S.lam[a] * exp(-2.0 * S.dg * 1.2247448713915890491 * S.nh[a]);
-        double bn[3][3], Wm[3][3];
-#pragma unroll
-        for (int i = 0; i < K; ++i)
-#pragma unroll
-            for (int j = i; j < K; ++j) {
-                double s = 0.0;
-#pragma unroll
-                for (int a = 0; a < K; ++a) s += S.N[i][a] * ln[a] * S.N[j][a];
-                bn[i][j] = s;
-                bn[j][i] = s;
-            }
-#pragma unroll
-        for (int i = 0; i < K; ++i)
-#pragma unroll
-            for (int j = 0; j < K; ++j) {
-                double s = 0.0;
-#pragma unroll
-                for (int k = 0; k < K; ++k) s += Finv[i][k] * bn[k][j];
-                Wm[i][j] = s;
-            }
         double c[3][3];
 #pragma unroll
-        for (int i = 0; i < K; ++i)
+        for (int i = 0; i < K; ++i) {
+            double ml[3];
+#pragma unroll
+            for (int a = 0; a < K; ++a) ml[a] = Mx[i][a] * ln[a];
 #pragma unroll
             for (int j = i; j < K; ++j) {
                 double s = 0.0;
 #pragma unroll
-                for (int k = 0; k < K; ++k) s += Wm[i][k] * Finv[j][k];
+                for (int a = 0; a < K; ++a) s += ml[a] * Mx[j][a];
                 c[i][j] = s;
             }
+        }
         if (D == 2) {
             c[0][2] = c[1][2] = 0.0;
             c[2][2] = ln[2];   // F_33 = 1
@@ -545,25 +550,6 @@ __device__ __forceinline__ void material_value(const double F[3][3], const doubl
 #pragma unroll
         for (int k = 0; k < 6; ++k) cp_new[k] = cp[k];
         *xi_new = xi_n;
-    }
-}
-
-// first Piola-Kirchhoff stress P = tau F^-T (plane strain: the in-plane block and P_33 = tau_33)
-template <int D>
-__device__ __forceinline__ void stress_P(const double tau[3][3], const double Finv[3][3], double P[3][3]) {
-    constexpr int K = D == 2 ? 2 : 3;
-#pragma unroll
-    for (int a = 0; a < K; ++a)
-#pragma unroll
-        for (int b = 0; b < K; ++b) {
-            double s = 0.0;
-#pragma unroll
-            for (int k = 0; k < K; ++k) s += tau[a][k] * Finv[b][k];
-            P[a][b] = s;
-        }
-    if (D == 2) {
-        P[0][2] = P[1][2] = P[2][0] = P[2][1] = 0.0;
-        P[2][2] = tau[2][2];
     }
 }
 

@@ -40,6 +40,7 @@ size_t tc3_image_bytes(int m);
 void tc3_build_images(int n, int m, const double *G, unsigned char *img);
 int launch_tc3(int mode, const Model &M, Batch Bt, const unsigned char *img, int *err, int sel, cudaStream_t s);
 void launch_force(const Model &M, Batch Bt, bool fp64, cudaStream_t s);
+void launch_geometry(const Model &M, const double *mu, int64_t B, double *geo, cudaStream_t s);
 int launch_sensitivity(const Model &M, Batch Bt, int precision, double *out, cudaStream_t s);
 bool separate_force(const Model &M, const StepOpts &o);
 void launch_list_converged(Batch Bt, cudaStream_t s);
@@ -92,6 +93,10 @@ struct rom_ctx {
     unsigned char *tc_img[2] = {nullptr, nullptr};   // 2D tensor-core B-operand images (BF16, TF32)
     unsigned char *tc3_img = nullptr;                 // 3D tensor-core images (tc_assemble3.cu)
     int *d_err = nullptr;
+    // per-geometry cache of F_mu^-1 and w J per point [B][d2 + 1][m], built before the first step
+    // after the basis, cubature or geometry changed (ensure_geo)
+    double *geo = nullptr;
+    bool geo_ok = false;
     // learned Newton start
     bool has_mlp = false, mlp_norm = false;
     MlpDev mlp{};
@@ -213,6 +218,7 @@ rom_status rom_destroy(rom_ctx *ctx) {
     p = ctx->tc_img[0]; dfree(p);
     p = ctx->tc_img[1]; dfree(p);
     p = ctx->tc3_img; dfree(p);
+    p = ctx->geo; dfree(p);
     p = ctx->d_err; dfree(p);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -298,6 +304,7 @@ rom_status rom_load_basis(rom_ctx *ctx, int n, int m, const double *G) {
     ctx->n = n;
     ctx->m = m;
     ctx->has_basis = true;
+    ctx->geo_ok = false;
     return ROM_OK;
 }
 
@@ -338,6 +345,7 @@ rom_status rom_load_cubature(rom_ctx *ctx, int m, const double *w, const int32_t
     ctx->nphase = n_phase;
     ctx->omega = omega_vol;
     ctx->has_cub = true;
+    ctx->geo_ok = false;
     return ROM_OK;
 }
 
@@ -379,6 +387,7 @@ rom_status rom_set_geometry(rom_ctx *ctx, int64_t B, int n_par, const double *Gm
     ctx->B = B;
     ctx->n_par = n_par;
     ctx->has_geom = true;
+    ctx->geo_ok = false;
     ++ctx->graph_epoch;     // captured step graphs hold the coefficient array
     return ROM_OK;
 }
@@ -415,6 +424,7 @@ rom_status rom_set_geometry_aux(rom_ctx *ctx, int64_t B, const rom_aux_model *au
     p = ctx->Gmu_T; dfree(p); ctx->Gmu_T = nullptr;
     p = ctx->mu; dfree(p); ctx->mu = nullptr;
     ctx->has_geom = false;
+    ctx->geo_ok = false;
     ++ctx->graph_epoch;
     rom_status s;
     double *work = nullptr;       // small operators, then mu [B][np]
@@ -567,6 +577,8 @@ rom_status rom_state_import(rom_ctx *ctx, rom_state *st, const double *a, const 
     return ROM_OK;
 }
 
+static rom_status ensure_geo(rom_ctx *ctx);
+
 static rom_status check_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts) {
     if (!ctx || !st || !opts || st->ctx != ctx) return ROM_E_ARG;
     if (!ctx->has_basis || !ctx->has_cub || !ctx->has_geom) return fail(ctx, ROM_E_STATE, "rom_step before basis/cubature/geometry");
@@ -582,7 +594,7 @@ static rom_status check_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts) 
         return fail(ctx, ROM_E_STATE, "rom_step: MLP input size %d does not match d^2 + n_par + 2n + 2", ctx->mlp.n_in);
     if (opts->precision >= ROM_PREC_TF32 && !ctx->tc_img[0] && !ctx->tc3_img)
         return fail(ctx, ROM_E_ARG, "rom_step: tensor-core precision needs n <= 64 (n = %d)", ctx->n);
-    return ROM_OK;
+    return ensure_geo(ctx);
 }
 
 static Model make_model(const rom_ctx *ctx) {
@@ -594,6 +606,24 @@ static Model make_model(const rom_ctx *ctx) {
     M.G32h_T = ctx->G32h_T; M.G32l_T = ctx->G32l_T; M.Gdf = ctx->Gdf;
     M.Gmu_T = ctx->Gmu_T; M.omega = ctx->omega;
     return M;
+}
+
+// the per-geometry cache (F_mu^-1 and w J per point); the cache belongs to the geometry, so a new
+// one is built (and captured graphs re-recorded, graph_epoch) when the model or geometry changed
+static rom_status ensure_geo(rom_ctx *ctx) {
+    if (ctx->geo_ok) return ROM_OK;
+    void *p = ctx->geo;
+    dfree(p);
+    ctx->geo = nullptr;
+    CK(cudaSetDevice(ctx->device));
+    rom_status s;
+    if ((s = dalloc(ctx, (void **)&ctx->geo, (size_t)ctx->B * (ctx->dim * ctx->dim + 1) * ctx->m * 8)) != ROM_OK)
+        return s;
+    launch_geometry(make_model(ctx), ctx->mu, ctx->B, ctx->geo, ctx->stream);
+    CK(cudaGetLastError());
+    ctx->geo_ok = true;
+    ++ctx->graph_epoch;
+    return ROM_OK;
 }
 
 }  // extern "C"
@@ -698,6 +728,7 @@ static rom_status run_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts, co
     const Model M = make_model(ctx);
     Batch bt = st->bt;
     bt.mu = ctx->mu;
+    bt.geo = ctx->geo;
     bt.err = ctx->d_err;
     int32_t *lists[2] = {st->bt.list, st->list2};
     const double n = M.n, m = M.m, d2 = M.d2, d4 = d2 * d2;
@@ -794,6 +825,7 @@ static cudaError_t record_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts
     const Model M = make_model(ctx);
     Batch bt = st->bt;
     bt.mu = ctx->mu;
+    bt.geo = ctx->geo;
     bt.err = ctx->d_err;
     const int max_pass = (opts->max_iter + 1) * (opts->max_ls + 1) + 2;
     int bad = 0;
