@@ -324,7 +324,10 @@ rom_status rom_profile_read(rom_ctx *ctx, int kernel, double *ms, int64_t *launc
  *   update goes to loss_d[1] (device, may be NULL).  Asynchronous.
  * rom_mlp_loss_grad: loss and gradient (packed like the parameters) without update;
  *   bf16 = 0 uses the FP32 weights.  Device outputs.  Asynchronous.
- * rom_mlp_predict: out_d[N][n_out] (double, raw units) for X_d[N][n_in].  Asynchronous.
+ * rom_mlp_predict: out_d[N][n_out] (double, raw units) for X_d[N][n_in].  bf16 = 1 with
+ *   width 128, n_in <= 256 and n_out <= 128: the whole network on the tcgen05 tensor cores
+ *   (one fused kernel per 128 rows, BF16 weights and activations, FP32 accumulation); other
+ *   shapes and bf16 = 0 (FP32 weights): CUDA-core kernels with FP32 activations.  Asynchronous.
  * rom_features: the features X_d[B][n_in] (device) of the step Fbar_d[B][d*d] for
  *   the current state of every instance.  Asynchronous. */
 rom_status rom_mlp_init(rom_ctx *ctx, int n_in, int width, int depth, int n_out, int64_t max_rows);

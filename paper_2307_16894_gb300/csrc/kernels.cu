@@ -190,10 +190,11 @@ void launch_geometry(const Model &M, const double *mu, int64_t B, double *geo, c
 // instances when m >= 128).
 constexpr int KIN_DF_SLOTS = 2;
 
-// 3D mixed precision: four 128-thread blocks per SM (128 registers, a few spilled to L1) hide the
-// FP64 pipe latency better than two blocks at ~200 registers (measured ~12% faster)
+// 3D mixed precision: five 128-thread blocks per SM (at most 102 registers, some spilled to L1)
+// hide the FP64 pipe latency better than fewer blocks at more registers (measured: 3 / 4 / 5 / 6
+// blocks 444.8 / 452.1 / 436.9 / 439.3 ms of this kernel over 6 load steps at B = 16384)
 template <int D, typename TT>
-__global__ void __launch_bounds__(128, (D == 3 && sizeof(TT) == 4) ? 4 : 1) k_constitutive(Model M, Batch Bt) {
+__global__ void __launch_bounds__(128, (D == 3 && sizeof(TT) == 4) ? 5 : 1) k_constitutive(Model M, Batch Bt) {
     constexpr int D2 = D * D;
     constexpr bool DF = sizeof(TT) == 4;
     const int m = M.m, n = M.n;

@@ -14,6 +14,7 @@
 #include <cmath>
 
 #include "kernels.cuh"
+#include "tcgen05.cuh"
 
 namespace podecm {
 
@@ -275,8 +276,193 @@ __global__ void k_out(int N, int C, const float *H, int ldh, const float *ym, co
     out[e] = (double)(H[(int64_t)i * ldh + j] * ys[j] + ym[j]);
 }
 
-// predictions for N rows of raw features X (in chunks of the work capacity)
-void mlp_predict(MlpDev &M, const float *X, int64_t N, int bf16, double *out, cudaStream_t s) {
+
+// ---------------------------------------------------------------- fused inference (tcgen05)
+// The whole network for 128 rows per CTA on the tensor cores: the standardised input, rounded
+// to BF16, is the A operand (128 rows x K, canonical K-major layout in shared memory); each
+// layer's BF16 weight matrix W_l[out][in] is the B operand (rows = out, K = in), placed in
+// shared memory in the same layout by the CTA itself; one thread issues the layer's
+// tcgen05.mma (kind::f16, M = 128, N = out, K = 16 each) into a 128 x 128 FP32 tensor-memory
+// accumulator; the epilogue (thread = row = tensor-memory lane) adds the bias, applies the
+// exact-erf GELU and writes the BF16 activations back as the next layer's A operand; the last
+// layer adds the bias and undoes the output standardisation.  Same parameters and arithmetic as
+// the CUDA-core path, except that the activations between layers are rounded to BF16 (the
+// operand type of the MMA).  A bounded wait that gives up writes zero predictions (the
+// previous-step predictor) for the CTA's rows and sets the error flag.
+namespace mlptc {
+constexpr int ROWS = 128;
+constexpr int THREADS = 128;
+constexpr int MAXL = 8;
+struct Geo {
+    int L, n_in, n_out, kp0, nout_p;   // layers, sizes, padded input width and output width
+    int w_off[MAXL];                   // byte offset of layer l's B image in shared memory
+    int a_off, smem;                   // A tile offset, dynamic shared memory
+    int64_t p_off[MAXL];               // element offset of layer l in the parameter vector
+};
+__host__ __device__ inline int l_in(const Geo &g, int l) { return l == 0 ? g.n_in : 128; }
+__host__ __device__ inline int l_out(const Geo &g, int l) { return l == g.L - 1 ? g.n_out : 128; }
+__host__ __device__ inline int l_kp(const Geo &g, int l) { return l == 0 ? g.kp0 : 128; }
+__host__ __device__ inline int l_np(const Geo &g, int l) { return l == g.L - 1 ? g.nout_p : 128; }
+// byte offset of element (row r, k) of a BF16 canonical K-major tile whose rows hold kp elements
+__host__ __device__ inline int off(int r, int k, int kp) {
+    return (r >> 3) * (kp / 8 * 128) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+}  // namespace mlptc
+
+__global__ void __launch_bounds__(mlptc::THREADS, 1)
+    k_mlp_tc(mlptc::Geo g, const __nv_bfloat16 *__restrict__ p16, const float *__restrict__ norm,
+             const float *__restrict__ X, int64_t N, double *__restrict__ out, int *err_flag) {
+    using namespace tcx;
+    using namespace mlptc;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int abort_s;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int64_t r0 = (int64_t)blockIdx.x * ROWS;
+    const int kpa = g.kp0 > 128 ? g.kp0 : 128;     // K capacity of the A tile
+    unsigned char *A = smem + g.a_off;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(128));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_s = 0;
+    }
+    // zero the shared memory (padding rows and K slots of every tile), then fill
+    for (int e = tid; e < g.smem / 16; e += THREADS) reinterpret_cast<uint4 *>(smem)[e] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    for (int l = 0; l < g.L; ++l) {
+        const int in = l_in(g, l), outl = l_out(g, l), kp = l_kp(g, l);
+        const __nv_bfloat16 *W = p16 + g.p_off[l];
+        unsigned char *img = smem + g.w_off[l];
+        if (l > 0) {
+            // rows of 128 inputs, 16-byte aligned: 8 weights per copy
+            for (int e = tid; e < outl * 16; e += THREADS) {
+                const int o = e >> 4, k = (e & 15) * 8;
+                *reinterpret_cast<uint4 *>(img + off(o, k, kp)) = *reinterpret_cast<const uint4 *>(W + (int64_t)o * in + k);
+            }
+        } else {
+            for (int e = tid; e < outl * in; e += THREADS) {
+                const int o = e / in, k = e - o * in;
+                *reinterpret_cast<__nv_bfloat16 *>(img + off(o, k, kp)) = W[e];
+            }
+        }
+    }
+    // standardised input rows, rounded to BF16
+    const float *mean = norm, *sd = norm + g.n_in;
+    for (int e = tid; e < ROWS * g.n_in; e += THREADS) {
+        const int r = e / g.n_in, k = e - r * g.n_in;
+        if (r0 + r < N) {
+            const float v = (X[(r0 + r) * g.n_in + k] - mean[k]) / sd[k];
+            *reinterpret_cast<__nv_bfloat16 *>(A + off(r, k, kpa)) = __float2bfloat16(v);
+        }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    const int64_t row = r0 + tid;
+    for (int l = 0; l < g.L; ++l) {
+        const int kp = l_kp(g, l), np = l_np(g, l), outl = l_out(g, l);
+        if (tid == 0) {
+            const uint32_t idesc = make_idesc(1u, ROWS, np);
+            const uint32_t a0 = smem_u32(A), b0 = smem_u32(smem + g.w_off[l]);
+            for (int k = 0; k < kp / 16; ++k)
+                mma_f16(tmem, make_desc(a0 + k * 256, 128, kpa / 8 * 128), make_desc(b0 + k * 256, 128, kp / 8 * 128),
+                        idesc, k > 0 ? 1u : 0u);
+            mma_commit(&bar);
+        }
+        __syncwarp();
+        if (!mbar_wait(&bar, (uint32_t)(l & 1), &abort_s)) abort_s = 1;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (abort_s) break;
+        const __nv_bfloat16 *bias = p16 + g.p_off[l] + (int64_t)outl * l_in(g, l);
+        const bool last = l == g.L - 1;
+        for (int c0 = 0; c0 < np; c0 += 16) {
+            uint32_t r[16];
+            tmem_ld16(tmem + lane_base + (uint32_t)c0, r);
+            tmem_wait_ld();
+            if (!last) {
+                uint32_t pk[8];
+#pragma unroll
+                for (int q = 0; q < 16; q += 2) {
+                    const float z0 = __uint_as_float(r[q]) + __bfloat162float(bias[c0 + q]);
+                    const float z1 = __uint_as_float(r[q + 1]) + __bfloat162float(bias[c0 + q + 1]);
+                    pk[q / 2] = pack_bf16(gelu(z0), gelu(z1));
+                }
+                // row tid, inputs c0 .. c0 + 15 of the next layer: two 16-byte core-matrix rows
+                *reinterpret_cast<uint4 *>(A + off(tid, c0, kpa)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                *reinterpret_cast<uint4 *>(A + off(tid, c0 + 8, kpa)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+            } else if (row < N) {
+                const float *ym = norm + 2 * g.n_in, *ys = ym + g.n_out;
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int j = c0 + q;
+                    if (j < g.n_out) {
+                        const float z = __uint_as_float(r[q]) + __bfloat162float(bias[j]);
+                        out[row * g.n_out + j] = (double)(z * ys[j] + ym[j]);
+                    }
+                }
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    if (abort_s) {
+        // the previous-step predictor for these rows; a committed MMA may still be in flight
+        if (tid == 0) mbar_drain(&bar, 0u), mbar_drain(&bar, 1u);
+        if (row < N)
+            for (int j = 0; j < g.n_out; ++j) out[row * g.n_out + j] = 0.0;
+        if (tid == 0 && err_flag) atomicExch(err_flag, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
+    }
+}
+
+// the fused kernel's geometry, or false when the network does not fit it (width 128, n_in and
+// n_out at most 256 and 128, the whole network in shared memory)
+static bool mlp_tc_geo(const MlpDev &M, mlptc::Geo &g) {
+    using namespace mlptc;
+    if (M.width != 128 || M.L > MAXL || M.n_in > 256 || M.n_out > 128 || M.n_in < 1 || M.n_out < 1) return false;
+    g.L = M.L; g.n_in = M.n_in; g.n_out = M.n_out;
+    g.kp0 = (M.n_in + 15) / 16 * 16;
+    g.nout_p = (M.n_out + 15) / 16 * 16;
+    int o = 0;
+    for (int l = 0; l < g.L; ++l) {
+        g.w_off[l] = o;
+        g.p_off[l] = layer_off(M, l);
+        o += l_np(g, l) * l_kp(g, l) * 2;
+        o = (o + 1023) / 1024 * 1024;
+    }
+    g.a_off = o;
+    o += ROWS * (g.kp0 > 128 ? g.kp0 : 128) * 2;
+    g.smem = o;
+    return g.smem <= 227 * 1024;
+}
+
+// predictions for N rows of raw features X: with BF16 weights on the tensor cores (k_mlp_tc)
+// when the network fits it, otherwise on the CUDA cores in chunks of the work capacity
+void mlp_predict(MlpDev &M, const float *X, int64_t N, int bf16, double *out, cudaStream_t s, int *err) {
+    mlptc::Geo g;
+    if (bf16 && mlp_tc_geo(M, g)) {
+        cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, g.smem);
+        k_mlp_tc<<<(unsigned)((N + mlptc::ROWS - 1) / mlptc::ROWS), mlptc::THREADS, g.smem, s>>>(
+            g, reinterpret_cast<const __nv_bfloat16 *>(M.p16), M.norm, X, N, out, err);
+        return;
+    }
     for (int64_t r0 = 0; r0 < N; r0 += M.cap) {
         const int64_t nr = (N - r0) < M.cap ? (N - r0) : M.cap;
         forward(M, X + r0 * M.n_in, nr, bf16, s);

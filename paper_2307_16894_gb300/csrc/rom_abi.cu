@@ -32,7 +32,7 @@ void mlp_train_step(MlpDev &M, const float *X, const float *Y, int64_t N, float 
                     cudaStream_t s);
 void mlp_loss_grad(MlpDev &M, const float *X, const float *Y, int64_t N, int bf16, float *grad_out, float *loss_out,
                    cudaStream_t s);
-void mlp_predict(MlpDev &M, const float *X, int64_t N, int bf16, double *out, cudaStream_t s);
+void mlp_predict(MlpDev &M, const float *X, int64_t N, int bf16, double *out, cudaStream_t s, int *err);
 size_t tc2_image_bytes(int fmt, int n, int m);
 void tc2_build_image(int fmt, int n, int m, const double *G, unsigned char *img);
 int launch_tc2(int mode, const Model &M, Batch Bt, const unsigned char *img, int *err, int sel, cudaStream_t s);
@@ -751,7 +751,7 @@ static rom_status run_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts, co
         if (s2 != ROM_OK) return s2;
         timed(ctx, 6, 0.0, [&] {
             launch_features(M, bt, bt.U_prev, ctx->d_feat, ctx->mlp.n_in, ctx->stream);
-            mlp_predict(ctx->mlp, ctx->d_feat, st->B, 1, ctx->d_pred, ctx->stream);
+            mlp_predict(ctx->mlp, ctx->d_feat, st->B, 1, ctx->d_pred, ctx->stream, ctx->d_err);
             launch_add_pred(bt, M.n, ctx->d_pred, ctx->stream);
             return 0;
         }, 3 + 2 * ctx->mlp.L);
@@ -834,7 +834,7 @@ static cudaError_t record_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts
     launch_reset_pass(bt, cs);
     if (o.start == ROM_START_MLP) {
         launch_features(M, bt, bt.U_prev, ctx->d_feat, ctx->mlp.n_in, cs);
-        mlp_predict(ctx->mlp, ctx->d_feat, st->B, 1, ctx->d_pred, cs);
+        mlp_predict(ctx->mlp, ctx->d_feat, st->B, 1, ctx->d_pred, cs, ctx->d_err);
         launch_add_pred(bt, M.n, ctx->d_pred, cs);
     }
     // conditional WHILE node for the Newton passes
@@ -1054,7 +1054,7 @@ rom_status rom_mlp_predict(rom_ctx *ctx, const float *X_d, int64_t N, int bf16, 
     if (!ctx || !X_d || !out_d || N < 1) return ROM_E_ARG;
     if (!ctx->has_mlp || !ctx->mlp_norm) return fail(ctx, ROM_E_STATE, "rom_mlp_predict: MLP or normalisation missing");
     CK(cudaSetDevice(ctx->device));
-    mlp_predict(ctx->mlp, X_d, N, bf16, out_d, ctx->stream);
+    mlp_predict(ctx->mlp, X_d, N, bf16, out_d, ctx->stream, nullptr);
     CK(cudaGetLastError());
     return ROM_OK;
 }

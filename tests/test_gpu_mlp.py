@@ -56,6 +56,38 @@ def test_mlp_grad_matches_oracle():
     ctx.close()
 
 
+@pytest.mark.parametrize("n_in,n_out,N", [(31, 24, 200), (142, 64, 300), (55, 24, 128)])
+def test_mlp_predict_tensor_cores(n_in, n_out, N):
+    """BF16 inference on the tensor cores (one fused tcgen05 kernel per 128 rows: BF16 weights and
+    activations, FP32 accumulation) against the FP64 oracle network with the same FP32 weights;
+    the shapes cover the 2D and 3D learned starts (n_in 55 / 142, n_out 24 / 64) and a partly
+    filled last CTA."""
+    import torch
+    rng = np.random.default_rng(1)
+    ctx = make_ctx(n_in, n_out, N)
+    p = warmstart.init_params(n_in, warmstart.WIDTH, warmstart.DEPTH, n_out, 5)
+    dims = [n_in] + [warmstart.WIDTH] * warmstart.DEPTH + [n_out]
+    o = 0
+    for a, b in zip(dims[:-1], dims[1:]):          # non-zero biases, so that the bias add is exercised
+        o += a * b
+        p[o:o + b] = rng.uniform(-0.3, 0.3, b).astype(np.float32)
+        o += b
+    ctx.mlp_params(p)
+    X = rng.standard_normal((N, n_in)).astype(np.float32)
+    Y = rng.standard_normal((N, n_out)).astype(np.float32)
+    norm = (X.mean(0), X.std(0), Y.mean(0), Y.std(0))
+    ctx.mlp_norm(*norm)
+    shp = omlp.shapes(n_in, warmstart.WIDTH, warmstart.DEPTH, n_out)
+    pr = omlp.predict(p.astype(np.float64), shp, X.astype(np.float64), np.concatenate(norm).astype(np.float64))
+    out = torch.full((N, n_out), np.nan, dtype=torch.float64, device="cuda")
+    ctx.mlp_predict(torch.from_numpy(X).cuda(), 1, out)
+    torch.cuda.synchronize()
+    o = out.cpu().numpy()
+    print("n_in %d n_out %d: tensor-core BF16 prediction rel error %.3e" % (n_in, n_out, rel(o, pr)))
+    assert np.isfinite(o).all() and rel(o, pr) <= 3e-2
+    ctx.close()
+
+
 def test_mlp_training_reduces_loss():
     import torch
     rng = np.random.default_rng(1)
