@@ -1129,8 +1129,17 @@ __global__ void __launch_bounds__(256, 4) k_finalize(Model M, Batch Bt, StepOpts
         double *Fm = A0 + D4;                                      // [CHF][D2]
         // FP32 path: the sums' staging area starts at Fm (its FP64 chunk is not used)
         unsigned char *work = reinterpret_cast<unsigned char *>(sizeof(TT) == 8 ? Fm + (size_t)CHF * D2 : Fm);
-        if (sizeof(TT) == 8) abar_sums_f64<D>(M, Bt, b, CHF, Bm, A0, Fm, reinterpret_cast<double *>(work));
-        else abar_sums_f32<D>(M, Bt, b, CHF, Bm, A0, reinterpret_cast<float *>(Fm));
+        if (Bt.Bsum) {
+            // B and A0 from the tensor cores (k_abar_tc3: Bsum[b] = [B (n x D2) | A0 (D4)])
+            const double *src = Bt.Bsum + (size_t)b * (n * D2 + D4);
+            for (int e = tid; e < n * D2; e += blockDim.x) Bm[e] = src[e];
+            for (int e = tid; e < D4; e += blockDim.x) A0[e] = src[n * D2 + e];
+            __syncthreads();
+        } else if (sizeof(TT) == 8) {
+            abar_sums_f64<D>(M, Bt, b, CHF, Bm, A0, Fm, reinterpret_cast<double *>(work));
+        } else {
+            abar_sums_f32<D>(M, Bt, b, CHF, Bm, A0, reinterpret_cast<float *>(Fm));
+        }
         // Schur complement with the factor of K at the solution (K* = K)
         if (sizeof(TT) == 8) schur_abar<D, double>(M, Bt, b, Bm, A0, work, AU);
         else schur_abar<D, float>(M, Bt, b, Bm, A0, work, AU);

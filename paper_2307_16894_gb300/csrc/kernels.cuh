@@ -57,6 +57,9 @@ struct Batch {
     double *r0_prev;         // [B] residual norm of the previous-step predictor when last evaluated (+inf
                              // if never), the reference of the learned start; may be null
     const int *err;          // tensor-core pipeline error flag (a bounded wait gave up), may be null
+    double *Bsum;            // [B][n d2 + d4]: B = sum_i G_i^T Ahat_i (n x d2) and A0 (d4) of the converged
+                             // instances from the tensor cores (k_abar_tc3) when non-null in the
+                             // finalize; else the finalize forms them
     const double *geo;       // [B][d2 + 1][m] F_mu^-1 (row-major) and w_i J_mu per point, computed once
                              // per geometry (k_geometry); null: the constitutive kernel forms them
 };

@@ -39,6 +39,7 @@ int launch_tc2(int mode, const Model &M, Batch Bt, const unsigned char *img, int
 size_t tc3_image_bytes(int m);
 void tc3_build_images(int n, int m, const double *G, unsigned char *img);
 int launch_tc3(int mode, const Model &M, Batch Bt, const unsigned char *img, int *err, int sel, cudaStream_t s);
+int launch_abar_tc3(const Model &M, Batch Bt, const unsigned char *img, double *Bsum, int *err, cudaStream_t s);
 void launch_force(const Model &M, Batch Bt, bool fp64, cudaStream_t s);
 void launch_geometry(const Model &M, const double *mu, int64_t B, double *geo, cudaStream_t s);
 int launch_sensitivity(const Model &M, Batch Bt, int precision, double *out, cudaStream_t s);
@@ -493,7 +494,8 @@ rom_status rom_state_create(rom_ctx *ctx, int64_t B, rom_state **out) {
         (s = A((void **)&bt.wP, Bz * d2 * m * 8)) || (s = A((void **)&bt.At, Bz * d2 * d2 * (size_t)((m + 3) & ~3) * 8)) ||
         (s = A((void **)&bt.cp_tr, Bz * ncp * m * 8)) || (s = A((void **)&bt.xi_tr, Bz * m * 8)) ||
         (s = A((void **)&bt.pl, Bz * m)) || (s = A((void **)&bt.r, Bz * n * 8)) ||
-        (s = A((void **)&bt.K, Bz * n * n * 8)) || (s = A((void **)&bt.Ubar, Bz * d2 * 8)) ||
+        (s = A((void **)&bt.K, Bz * n * n * 8)) || (s = A((void **)&bt.Bsum, Bz * (n * d2 + d2 * d2) * 8)) ||
+        (s = A((void **)&bt.Ubar, Bz * d2 * 8)) ||
         (s = A((void **)&bt.Rbar, Bz * d2 * 8)) || (s = A((void **)&bt.U_prev, Bz * d2 * 8)) ||
         (s = A((void **)&bt.r0_prev, Bz * 8)) ||
         (s = A((void **)&st->io_F, Bz * d2 * 8)) || (s = A((void **)&st->io_P, Bz * d2 * 8)) ||
@@ -779,12 +781,18 @@ static rom_status run_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts, co
         n_act = ctx->h_count[0];
         if (n_act == 0) break;
     }
+    // 3D tensor-core paths: the sums B = sum_i G_i^T Ahat_i of the effective stiffness on the
+    // tensor cores as well (k_abar_tc3 over the converged instances); the finalize then reads them
+    const bool tc_sums = tcp && M.d == 3 && ctx->tc3_img && o.want_abar;
     if (tcp) {
-        if (o.precision >= 2 && o.want_abar) {
+        if ((o.precision >= 2 && o.want_abar) || tc_sums) {
             Batch bc = bt;
             bc.list = lists[0];
             launch_list_converged(bc, ctx->stream);
-            timed(ctx, 2, 0.0, [&] { return launch_abar_assembly(ctx, M, bc, o, lists[1], ctx->stream); });
+            if (o.precision >= 2)
+                timed(ctx, 2, 0.0, [&] { return launch_abar_assembly(ctx, M, bc, o, lists[1], ctx->stream); });
+            if (tc_sums && timed(ctx, 4, 0.0, [&] { return launch_abar_tc3(M, bc, ctx->tc3_img, st->bt.Bsum, ctx->d_err, ctx->stream); }))
+                return fail(ctx, ROM_E_ARG, "rom_step: tensor-core Abar sums not available for this model");
         }
         CK(cudaMemcpyAsync(ctx->h_count + 4, ctx->d_err, 4, cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
@@ -793,7 +801,9 @@ static rom_status run_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts, co
             return fail(ctx, ROM_E_CUDA, "rom_step: tensor-core pipeline wait timed out");
         }
     }
-    if (timed(ctx, 4, 0.0, [&] { return launch_finalize(M, bt, o, Pbar_d, Abar_d, info_d, ctx->stream); }))
+    Batch bf = bt;
+    bf.Bsum = tc_sums ? st->bt.Bsum : nullptr;
+    if (timed(ctx, 4, 0.0, [&] { return launch_finalize(M, bf, o, Pbar_d, Abar_d, info_d, ctx->stream); }))
         return fail(ctx, ROM_E_ARG, "rom_step: n*d*d too large for the finalize kernel");
     CK(cudaGetLastError());
     prof_collect(ctx);
@@ -874,12 +884,16 @@ static cudaError_t record_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts
         }
         if (bs) cudaStreamDestroy(bs);
     }
-    if (e == cudaSuccess && o.precision >= 2 && o.want_abar) {
+    const bool tc_sums = tc_path(ctx, M, o.precision) && M.d == 3 && ctx->tc3_img && o.want_abar;
+    if (e == cudaSuccess && ((o.precision >= 2 && o.want_abar) || tc_sums)) {
         Batch bc = bt;
         launch_list_converged(bc, cs);
-        bad |= launch_abar_assembly(ctx, M, bc, o, st->list2, cs);
+        if (o.precision >= 2) bad |= launch_abar_assembly(ctx, M, bc, o, st->list2, cs);
+        if (tc_sums) bad |= launch_abar_tc3(M, bc, ctx->tc3_img, st->bt.Bsum, ctx->d_err, cs);
     }
-    if (e == cudaSuccess) bad |= launch_finalize(M, bt, o, st->io_P, st->io_A, st->io_info, cs);
+    Batch bf = bt;
+    bf.Bsum = tc_sums ? st->bt.Bsum : nullptr;
+    if (e == cudaSuccess) bad |= launch_finalize(M, bf, o, st->io_P, st->io_A, st->io_info, cs);
     *bad_out = bad;
     return e;
 }
@@ -1136,7 +1150,7 @@ rom_status rom_state_bytes(const rom_ctx *ctx, int64_t B, int64_t *bytes) {
     if (!ctx || !bytes || B < 1) return ROM_E_ARG;
     const int64_t d2 = ctx->dim * ctx->dim, n = ctx->n, m = ctx->m, ncp = ctx->dim == 2 ? 4 : 6;
     const int64_t per = n * 8 * 5 + (int64_t)sizeof(Ctl) + 8 + 8 + ncp * m * 8 * 2 + m * 8 * 2 + d2 * m * 8 * 2 +
-                        d2 * d2 * ((m + 3) & ~3) * 8 + m + n * n * 8 + d2 * 8 * 4 + d2 * d2 * 8 + 32;
+                        d2 * d2 * ((m + 3) & ~3) * 8 + m + n * n * 8 + (n * d2 + d2 * d2) * 8 + d2 * 8 * 4 + d2 * d2 * 8 + 32;
     *bytes = per * B + 64;
     return ROM_OK;
 }

@@ -691,6 +691,306 @@ __global__ void __launch_bounds__(tc4::THREADS, 1)
     }
 }
 
+// ---------------------------------------------------------------- Abar sums on the tensor cores
+// k_abar_tc3: for the converged instances, B_b = sum_i G_i^T Ahat_i (n x 9) with
+// Ahat_i[ar][(k,l)] = sum_s At_i[ar][(k,s)] F_mu,i[l][s] (the sums of the effective stiffness,
+// Eqs. eff_stiffness / eff_stiffness_ecm), FP32-accurate by the TF32 hi/lo split of
+// k_assemble_tc3 MODE 3.  Formulation: B_b^T = Ahat_b^T G with S = 14 instances packed along M,
+//   D[(s, kl)][l] += A[(s, kl)][(pt, ar)] G_pt[ar][l],
+// whose B operand is the stiffness assembly's TF32 image of G (chunks of 4 points, 12 K slots per
+// point, 9 used).  Roles as in k_assemble_tc3: 8 producer warps (tangent pieces staged by
+// cp.async, F_mu of the chunk's points, A = Ahat^T rows rounded to TF32 hi and lo), one control
+// thread (bulk copies of the B tiles into a 2-stage ring, 18 MMAs and one commit per chunk).
+// Chunk c goes to accumulator c % 7, the split's small terms to an eighth; the epilogue adds
+// them in FP32 and writes B_b [n][9] in FP64.  The producers also accumulate
+// A0_b = sum_i wJ A_i in the F_mu-pushed-forward form A0[(a,j)][(k,l)] =
+// sum_i sum_r F_mu[j][r] Ahat_i[(a,r)][(k,l)] (FP32 per thread, FP64 sum of two partials),
+// written after B_b: Bsum[b] = [B_b (n x 9) | A0_b (81)].  Every wait is bounded (1 s; error
+// flag, drain).
+namespace tca {
+using tc3::PC;
+using tc3::D2;
+using tc3::D4;
+constexpr int D = 3;
+constexpr int S = 14;                              // instances per CTA: rows (s, kl), 126 of 128
+constexpr int NPROD = 256, THREADS = NPROD + 32;
+constexpr int KP = 12, KC = PC * KP;               // 48 K slots per chunk
+constexpr int SBO_A = (KC / 4) * 128 + 16;         // +16 B spreads row groups over banks
+constexpr int A_BYTES = 16 * SBO_A;
+constexpr int B_BYTES = tc3::Cfg<2>::B_BYTES, SBO_B = tc3::Cfg<2>::SBO_B;
+constexpr int NK = KC / 8;                         // 6 K-steps per chunk
+constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;   // A hi, A lo, B hi, B lo
+constexpr int AS_FLOATS = S * D4 * PC;             // staged tangents [S][81][4]
+constexpr int FM_FLOATS = S * PC * D2;             // F_mu [S][4][9]
+constexpr int GM_DOUBLES = D2 * MAX_NPAR * PC;     // geometric-map gradients of a chunk [9 n_par][4]
+constexpr int SMEM = 2 * STAGE + 2 * AS_FLOATS * 4 + FM_FLOATS * 4 + 2 * GM_DOUBLES * 8;
+constexpr int NH = 7, NACC = 8;                    // 64-column accumulators in 512 columns
+constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(64 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}  // namespace tca
+
+__global__ void __launch_bounds__(tca::THREADS, 1)
+    k_abar_tc3(Model M, Batch Bt, const unsigned char *__restrict__ img, double *__restrict__ Bsum, int *err_flag) {
+    using namespace tc3;
+    using namespace tca;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar_full[2], bar_afull[2], bar_mma[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int64_t bI[S];
+    __shared__ double muS[S][MAX_NPAR];
+    __shared__ volatile int abort_s;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n_act = Bt.counts[0];
+    const int p0 = S * blockIdx.x;
+    if (p0 >= n_act) return;
+    const int np = M.n_par;
+    const int n = M.n, m = M.m, mA = M.mA;
+    const ImgLayout L = img_layout(m);
+    const int nch = L.nch;
+    const float *At = reinterpret_cast<const float *>(Bt.At);
+    auto a_tile = [&](int st, int t) { return smem + (size_t)st * STAGE + (size_t)t * A_BYTES; };
+    auto b_tile = [&](int st, int t) { return smem + (size_t)st * STAGE + 2 * (size_t)A_BYTES + (size_t)t * B_BYTES; };
+    float *const As0 = reinterpret_cast<float *>(smem + 2 * (size_t)STAGE);   // buffer t at As0 + t * AS_FLOATS
+    float *const Fms = As0 + 2 * AS_FLOATS;                                     // [S][PC][9]
+    double *const Gm0 = reinterpret_cast<double *>(Fms + FM_FLOATS);            // buffer t at Gm0 + t * GM_DOUBLES
+
+    if (tid < S) bI[tid] = (p0 + tid < n_act) ? (int64_t)Bt.list[p0 + tid] : -1;
+    for (int e = tid; e < S * np; e += THREADS) {
+        const int s = e / np, k = e - s * np;
+        muS[s][k] = (p0 + s < n_act) ? Bt.mu[(int64_t)Bt.list[p0 + s] * np + k] : 0.0;
+    }
+    if (warp == NPROD / 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int st = 0; st < 2; ++st) {
+            mbar_init(&bar_full[st], 1);
+            mbar_init(&bar_afull[st], NPROD);
+            mbar_init(&bar_mma[st], 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_s = 0;
+    }
+    // rows 126, 127 and the K slots 9..11 of every point are never produced: zero both A tiles of
+    // both stages once (the producers rewrite only the used slots)
+    for (int e = tid; e < 4 * A_BYTES / 16; e += THREADS) {
+        const int t = e / (A_BYTES / 16), w = e - t * (A_BYTES / 16);
+        *reinterpret_cast<uint4 *>(a_tile(t >> 1, t & 1) + (size_t)w * 16) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+
+    if (tid < NPROD) {
+        // ------------------------------------------------------------------ producers
+        // tangent rows (instance s, component ce) of chunk c: one 16-byte piece of its 4 points;
+        // absent instances and points past m as zeros (the columns past m of At are not written);
+        // and the chunk's geometric-map gradients Gmu_T[q][k][i] (plain loads, spread over the
+        // threads, so that the chunk's F_mu is formed from shared memory)
+        auto prefetch = [&](int c, int buf) {
+            const int c0 = c * PC;
+            for (int e = tid; e < D2 * np * PC; e += NPROD) {
+                const int qk = e / PC, pt = e - qk * PC;
+                Gm0[(size_t)buf * GM_DOUBLES + e] = (c0 + pt < m) ? M.Gmu_T[(size_t)qk * m + c0 + pt] : 0.0;
+            }
+            for (int e = tid; e < S * D4; e += NPROD) {
+                const int s = e / D4, ce = e - s * D4;
+                const int64_t b = bI[s];
+                float *dst = As0 + (size_t)buf * AS_FLOATS + (size_t)e * PC;
+                if (b >= 0 && c0 + PC <= m) {
+                    cp_async16(dst, At + ((size_t)b * D4 + ce) * mA + c0);
+                } else {
+                    const float *src = At + ((size_t)(b >= 0 ? b : 0) * D4 + ce) * mA + c0;
+                    float4 v;
+                    v.x = (b >= 0 && c0 + 0 < m) ? src[0] : 0.f;
+                    v.y = (b >= 0 && c0 + 1 < m) ? src[1] : 0.f;
+                    v.z = (b >= 0 && c0 + 2 < m) ? src[2] : 0.f;
+                    v.w = (b >= 0 && c0 + 3 < m) ? src[3] : 0.f;
+                    *reinterpret_cast<float4 *>(dst) = v;
+                }
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        prefetch(0, 0);
+        const bool prod_row = tid < 2 * S * D2;            // 252 of the 256 producer threads
+        const int prow = tid % (S * D2), pp = tid / (S * D2);
+        const int ps = prow / D2, pkl = prow - ps * D2;
+        const int pk = pkl / D, pl = pkl - pk * D;
+        float a0[D2];
+#pragma unroll
+        for (int q = 0; q < D2; ++q) a0[q] = 0.f;
+        int local_abort = 0;
+        for (int c = 0; c < nch; ++c) {
+            const int st = c & 1, c0 = c * PC;
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            if (bar_or_id(1, NPROD, local_abort | abort_s)) break;   // also: chunk c's tangents visible
+            if (c + 1 < nch) prefetch(c + 1, (c + 1) & 1);
+            // F_mu = I + sum_k mu_k Gmu_k at the chunk's points (zeros for absent instances and points)
+            const double *gm = Gm0 + (size_t)(c & 1) * GM_DOUBLES;
+            for (int e = tid; e < S * PC * D2; e += NPROD) {
+                const int s = e / (PC * D2), rem = e - s * (PC * D2);
+                const int pt = rem / D2, q = rem - pt * D2;
+                double v = 0.0;
+                if (bI[s] >= 0 && c0 + pt < m) {
+                    v = (q % 4 == 0) ? 1.0 : 0.0;
+                    for (int k = 0; k < np; ++k) v += muS[s][k] * gm[(q * np + k) * PC + pt];
+                }
+                Fms[(s * PC + pt) * D2 + q] = to_tangent<float>(v);
+            }
+            bar_or_id(2, NPROD, 0);
+            const uint32_t par = (uint32_t)(c >> 1) & 1u;
+            if (!mbar_wait(&bar_full[st], par, &abort_s)) { local_abort = 1; continue; }
+            if (c >= 2 && !mbar_wait(&bar_mma[st], par ^ 1u, &abort_s)) { local_abort = 1; continue; }
+            const float *as = As0 + (size_t)(c & 1) * AS_FLOATS;
+            unsigned char *Ahi = a_tile(st, 0), *Alo = a_tile(st, 1);
+            // thread (row r = s * 9 + kl, point pair pp) forms Ahat_{s,pt}[ar][kl], ar = 0..8, for
+            // pt = 2 pp, 2 pp + 1 (rows fastest within a warp), stores them rounded to TF32 hi and lo,
+            // and accumulates A0[(ia, jb)][kl] += sum_r F_mu[jb][r] Ahat[(ia, r)][kl] in FP32
+            if (prod_row) {
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int pt = 2 * pp + q;
+                    const float *fmp = Fms + (ps * PC + pt) * D2;
+                    const float *fm = fmp + pl * D;
+                    const float f0 = fm[0], f1 = fm[1], f2 = fm[2];
+                    const float *a = as + (size_t)ps * D4 * PC + pt;
+                    float y[D2];
+#pragma unroll
+                    for (int ar = 0; ar < D2; ++ar) {
+                        const int ce = ar * D2 + pk * D;
+                        y[ar] = fmaf(a[(ce + 2) * PC], f2, fmaf(a[(ce + 1) * PC], f1, a[ce * PC] * f0));
+                    }
+#pragma unroll
+                    for (int ia = 0; ia < D; ++ia)
+#pragma unroll
+                        for (int jb = 0; jb < D; ++jb)
+                            a0[ia * D + jb] = fmaf(fmp[jb * D + 2], y[ia * D + 2],
+                                                   fmaf(fmp[jb * D + 1], y[ia * D + 1], fmaf(fmp[jb * D], y[ia * D], a0[ia * D + jb])));
+                    uint32_t h[12], lo[12];
+#pragma unroll
+                    for (int k = 0; k < 12; ++k) {
+                        h[k] = k < D2 ? tf32_bits(y[k < D2 ? k : 0]) : 0u;
+                        lo[k] = k < D2 ? tf32_bits(y[k < D2 ? k : 0] - __uint_as_float(h[k])) : 0u;
+                    }
+                    const size_t rb = (size_t)(prow >> 3) * SBO_A + (size_t)(prow & 7) * 16;
+#pragma unroll
+                    for (int u = 0; u < 3; ++u) {
+                        *reinterpret_cast<uint4 *>(Ahi + rb + (size_t)(3 * pt + u) * 128) =
+                            make_uint4(h[4 * u], h[4 * u + 1], h[4 * u + 2], h[4 * u + 3]);
+                        *reinterpret_cast<uint4 *>(Alo + rb + (size_t)(3 * pt + u) * 128) =
+                            make_uint4(lo[4 * u], lo[4 * u + 1], lo[4 * u + 2], lo[4 * u + 3]);
+                    }
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(&bar_afull[st]);
+        }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        // A0 of the rows: the two point-pair partial sums added in a fixed order (the tangent
+        // staging area is free once every producer has left the loop)
+        const int quit = bar_or_id(1, NPROD, local_abort | abort_s);
+        float *red = As0;                                    // [S * 9][9] partials of pp = 1
+        if (prod_row && pp == 1)
+#pragma unroll
+            for (int q = 0; q < D2; ++q) red[prow * D2 + q] = a0[q];
+        bar_or_id(2, NPROD, 0);
+        if (!quit && prod_row && pp == 0 && bI[ps] >= 0) {
+            double *A0g = Bsum + (size_t)bI[ps] * (n * D2 + D4) + (size_t)n * D2;
+#pragma unroll
+            for (int q = 0; q < D2; ++q) A0g[q * D2 + pkl] = f2d_exact(a0[q]) + f2d_exact(red[prow * D2 + q]);
+        }
+    } else if (lane == 0) {
+        // ------------------------------------------------------------- control thread
+        uint32_t copy_pending = 0, copy_par = 0;
+        int mma_pending = 0;
+        uint32_t mma_par = 0;
+        int mma_stage = 0;
+        auto issue_copies = [&](int c) {
+            const int st = c & 1;
+            mbar_expect_tx(&bar_full[st], 2u * B_BYTES);
+            bulk_g2s(b_tile(st, 0), img + L.tf_hi + (size_t)c * B_BYTES, B_BYTES, &bar_full[st]);
+            bulk_g2s(b_tile(st, 1), img + L.tf_lo + (size_t)c * B_BYTES, B_BYTES, &bar_full[st]);
+            copy_pending |= 1u << st;
+            copy_par = (copy_par & ~(1u << st)) | (((uint32_t)(c >> 1) & 1u) << st);
+        };
+        issue_copies(0);
+        if (nch > 1) issue_copies(1);
+        for (int c = 0; c < nch; ++c) {
+            const int st = c & 1;
+            const uint32_t par = (uint32_t)(c >> 1) & 1u;
+            if (!mbar_wait(&bar_full[st], par, &abort_s)) break;
+            copy_pending &= ~(1u << st);
+            if (!mbar_wait(&bar_afull[st], par, &abort_s)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t ah = smem_u32(a_tile(st, 0)), al = smem_u32(a_tile(st, 1));
+            const uint32_t bh = smem_u32(b_tile(st, 0)), bl = smem_u32(b_tile(st, 1));
+            const uint32_t dh = tmem + (uint32_t)((c % NH) * 64), dl = tmem + (uint32_t)(NH * 64);
+#pragma unroll
+            for (int k = 0; k < NK; ++k) {
+                const uint64_t adh = make_desc(ah + k * 256, 128, SBO_A);
+                const uint64_t bdh = make_desc(bh + k * 256, 128, SBO_B);
+                mma_tf32(dh, adh, bdh, IDESC, (c >= NH || k > 0) ? 1u : 0u);
+                mma_tf32(dl, make_desc(al + k * 256, 128, SBO_A), bdh, IDESC, (c > 0 || k > 0) ? 1u : 0u);
+                mma_tf32(dl, adh, make_desc(bl + k * 256, 128, SBO_B), IDESC, 1u);
+            }
+            mma_commit(&bar_mma[st]);
+            mma_pending = 1;
+            mma_par = par;
+            mma_stage = st;
+            if (c + 2 < nch) {
+                if (!mbar_wait(&bar_mma[st], par, &abort_s)) break;
+                issue_copies(c + 2);
+            }
+        }
+        if (mma_pending && !mbar_wait(&bar_mma[mma_stage], mma_par, &abort_s)) mbar_drain(&bar_mma[mma_stage], mma_par);
+        for (int st = 0; st < 2; ++st)
+            if ((copy_pending >> st) & 1u) mbar_drain(&bar_full[st], (copy_par >> st) & 1u);
+        if (abort_s && err_flag) atomicExch(err_flag, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!abort_s && tid < NPROD) {
+        // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (rows s * 9 + kl), columns
+        // 32 (w / 4) .. + 31 (basis index l); accumulators added in FP32 in a fixed order
+        const int row = (warp & 3) * 32 + lane;
+        const int s = row / D2, kl = row - s * D2;
+        const bool ok = s < S && bI[s] >= 0;
+        double *Bb = ok ? Bsum + (size_t)bI[s] * (n * D2 + D4) + kl : nullptr;
+        const int nh_used = nch < NH ? nch : NH;
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            const int c0 = (warp >> 2) * 32 + h * 16;
+            float acc[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) acc[q] = 0.f;
+#pragma unroll 1
+            for (int ai = 0; ai < NACC; ++ai) {
+                if (ai >= nh_used && ai < NH) continue;
+                uint32_t r[16];
+                tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(ai * 64 + c0), r);
+                tmem_wait_ld();
+#pragma unroll
+                for (int q = 0; q < 16; ++q) acc[q] += __uint_as_float(r[q]);
+            }
+            if (ok)
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    if (c0 + q < n) Bb[(size_t)(c0 + q) * D2] = f2d_exact(acc[q]);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == NPROD / 32) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+    }
+}
+
 // ------------------------------------------------------------------------ host side
 
 size_t tc3_image_bytes(int m) { return tc3::img_layout(m).total; }
@@ -757,6 +1057,15 @@ static int launch_tc4(const Model &M, Batch Bt, const unsigned char *img, int *e
     cudaFuncSetAttribute(k_assemble_tc4, cudaFuncAttributeMaxDynamicSharedMemorySize, tc4::SMEM);
     const int grid = (int)((Bt.B + tc4::NI - 1) / tc4::NI);
     k_assemble_tc4<<<grid, tc4::THREADS, tc4::SMEM, s>>>(M, Bt, img, err, sel);
+    return 0;
+}
+
+// B_b = sum_i G_i^T Ahat_i [n][9] of the listed (converged) instances on the tensor cores
+int launch_abar_tc3(const Model &M, Batch Bt, const unsigned char *img, double *Bsum, int *err, cudaStream_t s) {
+    if (M.d != 3 || M.n > tc3::NCOLS || (M.mA & 3) || !Bsum) return -1;
+    cudaFuncSetAttribute(k_abar_tc3, cudaFuncAttributeMaxDynamicSharedMemorySize, tca::SMEM);
+    const int grid = (int)((Bt.B + tca::S - 1) / tca::S);
+    k_abar_tc3<<<grid, tca::THREADS, tca::SMEM, s>>>(M, Bt, img, Bsum, err);
     return 0;
 }
 
