@@ -500,18 +500,20 @@ __device__ bool block_lu_solve(T *A, int n, int lda, T *X, int ldx, int nrhs, in
     const int tx = tid & 15, ty = tid >> 4, NY = nt >> 4;
     for (int k = 0; k < n; ++k) {
         if (tid < 32) {
-            double best = -1.0;
+            // pivot search in the matrix's own precision (an FP32 matrix compared in FP64 would
+            // put conversions and compares on the FP64 pipe)
+            T best = T(-1);
             int bi = k;
             for (int i = k + tid; i < n; i += 32) {
-                const double v = fabs((double)A[i * lda + k]);
+                const T v = fabs(A[i * lda + k]);
                 if (v > best || (v == best && i < bi)) { best = v; bi = i; }
             }
             for (int off = 16; off > 0; off >>= 1) {
-                const double ob = __shfl_xor_sync(0xffffffffu, best, off);
+                const T ob = __shfl_xor_sync(0xffffffffu, best, off);
                 const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
                 if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
             }
-            if (tid == 0) *s_piv = (!(best > 0.0) || !isfinite(best)) ? -1 : bi;
+            if (tid == 0) *s_piv = (!(best > T(0)) || !isfinite(best)) ? -1 : bi;
         }
         __syncthreads();
         const int p = *s_piv;
@@ -1047,10 +1049,12 @@ __device__ void schur_abar(const Model &M, const Batch &Bt, int64_t b, const dou
     T *Zs = Aw + (size_t)n * ld;             // [D2][n + 1]
     int *piv = reinterpret_cast<int *>(Zs + (size_t)ld * D2);
     const double *Kb = Bt.K + (size_t)b * n * n;
-    for (int e = tid; e < n * n; e += blockDim.x) Aw[(e / n) * ld + e % n] = (T)Kb[e];
+    // FP32 copies by integer operations on the bit patterns (mantissa truncation: the FP32 path's
+    // K and B carry FP32-level errors already), not by conversion instructions on the FP64 pipe
+    for (int e = tid; e < n * n; e += blockDim.x) Aw[(e / n) * ld + e % n] = to_tangent<T>(Kb[e]);
     for (int e = tid; e < n * D2; e += blockDim.x) {
         const int kl = e / n, j = e - kl * n;
-        Zs[kl * ld + j] = (T)Bm[j * D2 + kl];
+        Zs[kl * ld + j] = to_tangent<T>(Bm[j * D2 + kl]);
     }
     __syncthreads();
     const bool ok = block_lu_solve<T>(Aw, n, ld, Zs, ld, D2, piv);
@@ -1058,7 +1062,7 @@ __device__ void schur_abar(const Model &M, const Batch &Bt, int64_t b, const dou
         const int ij = tid / D2, kl = tid - ij * D2;
         double s = A0[tid];
         if (ok)
-            for (int j = 0; j < n; ++j) s -= Bm[j * D2 + ij] * (double)Zs[(size_t)kl * ld + j];
+            for (int j = 0; j < n; ++j) s -= Bm[j * D2 + ij] * widen(Zs[(size_t)kl * ld + j]);
         else
             s = NAN;
         AU[tid] = s / M.omega;

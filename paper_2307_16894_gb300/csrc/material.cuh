@@ -168,6 +168,10 @@ __device__ __forceinline__ double rsqrt_near1(double x) {
     return 1.0 / sqrt(x);
 }
 
+// FP64 value of an FP64 or FP32 number (FP32 widened by integer operations)
+__device__ __forceinline__ double widen(double x) { return x; }
+__device__ __forceinline__ double widen(float x) { return f2d_exact(x); }
+
 // FP64-accurate symmetric 3x3 eigen-decomposition: FP32 Jacobi gives approximate
 // eigenvectors, which are made exactly orthonormal in FP64 (Gram-Schmidt + cross product; the
 // FP32 vectors have norms within ~1e-7 of 1, so their normalisation is a short series) and used

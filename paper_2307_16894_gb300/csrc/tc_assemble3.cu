@@ -722,8 +722,8 @@ constexpr int NK = KC / 8;                         // 6 K-steps per chunk
 constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;   // A hi, A lo, B hi, B lo
 constexpr int AS_FLOATS = S * D4 * PC;             // staged tangents [S][81][4]
 constexpr int FM_FLOATS = S * PC * D2;             // F_mu [S][4][9]
-constexpr int GM_DOUBLES = D2 * MAX_NPAR * PC;     // geometric-map gradients of a chunk [9 n_par][4]
-constexpr int SMEM = 2 * STAGE + 2 * AS_FLOATS * 4 + FM_FLOATS * 4 + 2 * GM_DOUBLES * 8;
+constexpr int GM_FLOATS = D2 * MAX_NPAR * PC;      // geometric-map gradients of a chunk [9 n_par][4]
+constexpr int SMEM = 2 * STAGE + 2 * AS_FLOATS * 4 + FM_FLOATS * 4 + 2 * GM_FLOATS * 4;
 constexpr int NH = 7, NACC = 8;                    // 64-column accumulators in 512 columns
 constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(64 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }  // namespace tca
@@ -736,7 +736,7 @@ __global__ void __launch_bounds__(tca::THREADS, 1)
     __shared__ __align__(8) uint64_t bar_full[2], bar_afull[2], bar_mma[2];
     __shared__ uint32_t tmem_base;
     __shared__ int64_t bI[S];
-    __shared__ double muS[S][MAX_NPAR];
+    __shared__ float muS[S][MAX_NPAR];
     __shared__ volatile int abort_s;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -752,12 +752,12 @@ __global__ void __launch_bounds__(tca::THREADS, 1)
     auto b_tile = [&](int st, int t) { return smem + (size_t)st * STAGE + 2 * (size_t)A_BYTES + (size_t)t * B_BYTES; };
     float *const As0 = reinterpret_cast<float *>(smem + 2 * (size_t)STAGE);   // buffer t at As0 + t * AS_FLOATS
     float *const Fms = As0 + 2 * AS_FLOATS;                                     // [S][PC][9]
-    double *const Gm0 = reinterpret_cast<double *>(Fms + FM_FLOATS);            // buffer t at Gm0 + t * GM_DOUBLES
+    float *const Gm0 = Fms + FM_FLOATS;                                         // buffer t at Gm0 + t * GM_FLOATS
 
     if (tid < S) bI[tid] = (p0 + tid < n_act) ? (int64_t)Bt.list[p0 + tid] : -1;
     for (int e = tid; e < S * np; e += THREADS) {
         const int s = e / np, k = e - s * np;
-        muS[s][k] = (p0 + s < n_act) ? Bt.mu[(int64_t)Bt.list[p0 + s] * np + k] : 0.0;
+        muS[s][k] = (p0 + s < n_act) ? to_tangent<float>(Bt.mu[(int64_t)Bt.list[p0 + s] * np + k]) : 0.f;
     }
     if (warp == NPROD / 32) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -795,7 +795,7 @@ __global__ void __launch_bounds__(tca::THREADS, 1)
             const int c0 = c * PC;
             for (int e = tid; e < D2 * np * PC; e += NPROD) {
                 const int qk = e / PC, pt = e - qk * PC;
-                Gm0[(size_t)buf * GM_DOUBLES + e] = (c0 + pt < m) ? M.Gmu_T[(size_t)qk * m + c0 + pt] : 0.0;
+                Gm0[(size_t)buf * GM_FLOATS + e] = (c0 + pt < m) ? to_tangent<float>(M.Gmu_T[(size_t)qk * m + c0 + pt]) : 0.f;
             }
             for (int e = tid; e < S * D4; e += NPROD) {
                 const int s = e / D4, ce = e - s * D4;
@@ -816,13 +816,16 @@ __global__ void __launch_bounds__(tca::THREADS, 1)
             asm volatile("cp.async.commit_group;" ::: "memory");
         };
         prefetch(0, 0);
-        const bool prod_row = tid < 2 * S * D2;            // 252 of the 256 producer threads
-        const int prow = tid % (S * D2), pp = tid / (S * D2);
-        const int ps = prow / D2, pkl = prow - ps * D2;
-        const int pk = pkl / D, pl = pkl - pk * D;
-        float a0[D2];
+        // thread (point pt, instance s, k): the rows (s, kl = 3 k + l), l = 0..2, of point pt, so
+        // that each staged tangent entry serves three rows (168 of the 256 producer threads)
+        const bool prod_row = tid < PC * S * D;
+        const int ppt = tid / (S * D), rest = tid - ppt * (S * D);
+        const int ps = rest / D, pk = rest - ps * D;
+        float a0[D][D2];                                   // A0 partial sums of the rows (s, 3 k + l)
 #pragma unroll
-        for (int q = 0; q < D2; ++q) a0[q] = 0.f;
+        for (int l = 0; l < D; ++l)
+#pragma unroll
+            for (int q = 0; q < D2; ++q) a0[l][q] = 0.f;
         int local_abort = 0;
         for (int c = 0; c < nch; ++c) {
             const int st = c & 1, c0 = c * PC;
@@ -830,16 +833,16 @@ __global__ void __launch_bounds__(tca::THREADS, 1)
             if (bar_or_id(1, NPROD, local_abort | abort_s)) break;   // also: chunk c's tangents visible
             if (c + 1 < nch) prefetch(c + 1, (c + 1) & 1);
             // F_mu = I + sum_k mu_k Gmu_k at the chunk's points (zeros for absent instances and points)
-            const double *gm = Gm0 + (size_t)(c & 1) * GM_DOUBLES;
+            const float *gm = Gm0 + (size_t)(c & 1) * GM_FLOATS;
             for (int e = tid; e < S * PC * D2; e += NPROD) {
                 const int s = e / (PC * D2), rem = e - s * (PC * D2);
                 const int pt = rem / D2, q = rem - pt * D2;
-                double v = 0.0;
+                float v = 0.f;   // F_mu in FP32: it only enters the FP32 Ahat
                 if (bI[s] >= 0 && c0 + pt < m) {
-                    v = (q % 4 == 0) ? 1.0 : 0.0;
-                    for (int k = 0; k < np; ++k) v += muS[s][k] * gm[(q * np + k) * PC + pt];
+                    v = (q % 4 == 0) ? 1.f : 0.f;
+                    for (int k = 0; k < np; ++k) v = fmaf(muS[s][k], gm[(q * np + k) * PC + pt], v);
                 }
-                Fms[(s * PC + pt) * D2 + q] = to_tangent<float>(v);
+                Fms[(s * PC + pt) * D2 + q] = v;
             }
             bar_or_id(2, NPROD, 0);
             const uint32_t par = (uint32_t)(c >> 1) & 1u;
@@ -847,41 +850,44 @@ __global__ void __launch_bounds__(tca::THREADS, 1)
             if (c >= 2 && !mbar_wait(&bar_mma[st], par ^ 1u, &abort_s)) { local_abort = 1; continue; }
             const float *as = As0 + (size_t)(c & 1) * AS_FLOATS;
             unsigned char *Ahi = a_tile(st, 0), *Alo = a_tile(st, 1);
-            // thread (row r = s * 9 + kl, point pair pp) forms Ahat_{s,pt}[ar][kl], ar = 0..8, for
-            // pt = 2 pp, 2 pp + 1 (rows fastest within a warp), stores them rounded to TF32 hi and lo,
-            // and accumulates A0[(ia, jb)][kl] += sum_r F_mu[jb][r] Ahat[(ia, r)][kl] in FP32
+            // Ahat_{s,pt}[ar][(k,l)] = sum_q At[ar][(k,q)] F_mu[l][q], ar = 0..8, l = 0..2, stored rounded
+            // to TF32 hi and lo; A0[(ia, jb)][(k,l)] += sum_r F_mu[jb][r] Ahat[(ia, r)][(k,l)] in FP32
             if (prod_row) {
+                const float *fm = Fms + (ps * PC + ppt) * D2;
+                float f[D2];
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const int pt = 2 * pp + q;
-                    const float *fmp = Fms + (ps * PC + pt) * D2;
-                    const float *fm = fmp + pl * D;
-                    const float f0 = fm[0], f1 = fm[1], f2 = fm[2];
-                    const float *a = as + (size_t)ps * D4 * PC + pt;
-                    float y[D2];
+                for (int q = 0; q < D2; ++q) f[q] = fm[q];
+                const float *a = as + (size_t)ps * D4 * PC + ppt;
+                float y[D][D2];
 #pragma unroll
-                    for (int ar = 0; ar < D2; ++ar) {
-                        const int ce = ar * D2 + pk * D;
-                        y[ar] = fmaf(a[(ce + 2) * PC], f2, fmaf(a[(ce + 1) * PC], f1, a[ce * PC] * f0));
-                    }
+                for (int ar = 0; ar < D2; ++ar) {
+                    const int ce = ar * D2 + pk * D;
+                    const float t0 = a[ce * PC], t1 = a[(ce + 1) * PC], t2 = a[(ce + 2) * PC];
+#pragma unroll
+                    for (int l = 0; l < D; ++l) y[l][ar] = fmaf(t2, f[l * D + 2], fmaf(t1, f[l * D + 1], t0 * f[l * D]));
+                }
+#pragma unroll
+                for (int l = 0; l < D; ++l) {
 #pragma unroll
                     for (int ia = 0; ia < D; ++ia)
 #pragma unroll
                         for (int jb = 0; jb < D; ++jb)
-                            a0[ia * D + jb] = fmaf(fmp[jb * D + 2], y[ia * D + 2],
-                                                   fmaf(fmp[jb * D + 1], y[ia * D + 1], fmaf(fmp[jb * D], y[ia * D], a0[ia * D + jb])));
+                            a0[l][ia * D + jb] = fmaf(f[jb * D + 2], y[l][ia * D + 2],
+                                                      fmaf(f[jb * D + 1], y[l][ia * D + 1],
+                                                           fmaf(f[jb * D], y[l][ia * D], a0[l][ia * D + jb])));
                     uint32_t h[12], lo[12];
 #pragma unroll
-                    for (int k = 0; k < 12; ++k) {
-                        h[k] = k < D2 ? tf32_bits(y[k < D2 ? k : 0]) : 0u;
-                        lo[k] = k < D2 ? tf32_bits(y[k < D2 ? k : 0] - __uint_as_float(h[k])) : 0u;
+                    for (int q = 0; q < 12; ++q) {
+                        h[q] = q < D2 ? tf32_bits(y[l][q < D2 ? q : 0]) : 0u;
+                        lo[q] = q < D2 ? tf32_bits(y[l][q < D2 ? q : 0] - __uint_as_float(h[q])) : 0u;
                     }
-                    const size_t rb = (size_t)(prow >> 3) * SBO_A + (size_t)(prow & 7) * 16;
+                    const int r = ps * D2 + pk * D + l;
+                    const size_t rb = (size_t)(r >> 3) * SBO_A + (size_t)(r & 7) * 16;
 #pragma unroll
                     for (int u = 0; u < 3; ++u) {
-                        *reinterpret_cast<uint4 *>(Ahi + rb + (size_t)(3 * pt + u) * 128) =
+                        *reinterpret_cast<uint4 *>(Ahi + rb + (size_t)(3 * ppt + u) * 128) =
                             make_uint4(h[4 * u], h[4 * u + 1], h[4 * u + 2], h[4 * u + 3]);
-                        *reinterpret_cast<uint4 *>(Alo + rb + (size_t)(3 * pt + u) * 128) =
+                        *reinterpret_cast<uint4 *>(Alo + rb + (size_t)(3 * ppt + u) * 128) =
                             make_uint4(lo[4 * u], lo[4 * u + 1], lo[4 * u + 2], lo[4 * u + 3]);
                     }
                 }
@@ -890,19 +896,26 @@ __global__ void __launch_bounds__(tca::THREADS, 1)
             mbar_arrive(&bar_afull[st]);
         }
         asm volatile("cp.async.wait_group 0;" ::: "memory");
-        // A0 of the rows: the two point-pair partial sums added in a fixed order (the tangent
-        // staging area is free once every producer has left the loop)
+        // A0: the four point partial sums of each row added in a fixed order (the tangent staging
+        // area is free once every producer has left the loop)
         const int quit = bar_or_id(1, NPROD, local_abort | abort_s);
-        float *red = As0;                                    // [S * 9][9] partials of pp = 1
-        if (prod_row && pp == 1)
+        float *red = As0;                                    // [PC][S * 9][9]
+        if (prod_row)
 #pragma unroll
-            for (int q = 0; q < D2; ++q) red[prow * D2 + q] = a0[q];
+            for (int l = 0; l < D; ++l)
+#pragma unroll
+                for (int q = 0; q < D2; ++q) red[((size_t)ppt * S * D2 + ps * D2 + pk * D + l) * D2 + q] = a0[l][q];
         bar_or_id(2, NPROD, 0);
-        if (!quit && prod_row && pp == 0 && bI[ps] >= 0) {
-            double *A0g = Bsum + (size_t)bI[ps] * (n * D2 + D4) + (size_t)n * D2;
+        if (!quit)
+            for (int e = tid; e < S * D2 * D2; e += NPROD) {
+                const int row = e / D2, q = e - row * D2;        // row = s * 9 + kl
+                const int s = row / D2, kl = row - s * D2;
+                if (bI[s] < 0) continue;
+                double v = 0.0;
 #pragma unroll
-            for (int q = 0; q < D2; ++q) A0g[q * D2 + pkl] = f2d_exact(a0[q]) + f2d_exact(red[prow * D2 + q]);
-        }
+                for (int pt = 0; pt < PC; ++pt) v += f2d_exact(red[((size_t)pt * S * D2 + row) * D2 + q]);
+                Bsum[(size_t)bI[s] * (n * D2 + D4) + (size_t)n * D2 + q * D2 + kl] = v;
+            }
     } else if (lane == 0) {
         // ------------------------------------------------------------- control thread
         uint32_t copy_pending = 0, copy_par = 0;
