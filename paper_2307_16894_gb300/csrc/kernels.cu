@@ -638,13 +638,15 @@ __device__ bool newton_direction(const Batch &Bt, int64_t b, int n, int precisio
         float *A32 = reinterpret_cast<float *>(A);
         float *y = A32 + (size_t)n * lda;                                 // n floats
         int *piv = reinterpret_cast<int *>(y + n);                        // n ints  (n lda + 2n floats <= 2 n lda)
-        for (int e = tid; e < n * n; e += nt) A32[(e / n) * lda + e % n] = (float)Kb[e];
-        for (int j = tid; j < n; j += nt) y[j] = (float)(-r[j]);
+        // FP64 <-> FP32 by integer operations on the bit patterns (the conversion instructions run
+        // on the FP64 pipe); the FP32 factor's truncation is corrected by the FP64 refinement
+        for (int e = tid; e < n * n; e += nt) A32[(e / n) * lda + e % n] = to_tangent<float>(Kb[e]);
+        for (int j = tid; j < n; j += nt) y[j] = to_tangent<float>(-r[j]);
         __syncthreads();
         bool ok = block_lu_factor<float>(A32, n, lda, piv, s_piv);
         if (ok) {
             block_lu_apply<float>(A32, n, lda, piv, y);
-            for (int j = tid; j < n; j += nt) x[j] = (double)y[j];
+            for (int j = tid; j < n; j += nt) x[j] = widen(y[j]);
             __syncthreads();
             double prev = INFINITY;
             for (int it = 0; it < 3; ++it) {
@@ -655,15 +657,15 @@ __device__ bool newton_direction(const Batch &Bt, int64_t b, int n, int precisio
                     const double *Ki = Kb + (size_t)i * n;
                     double s = 0.0;
                     for (int j = 0; j < n; ++j) s += Ki[j] * x[j];
-                    y[i] = (float)(-r[i] - s);
+                    y[i] = to_tangent<float>(-r[i] - s);
                 }
                 __syncthreads();
                 block_lu_apply<float>(A32, n, lda, piv, y);
                 double dl = 0.0, xl = 0.0;
-                for (int j = tid; j < n; j += nt) { dl = fmax(dl, fabs((double)y[j])); xl = fmax(xl, fabs(x[j])); }
+                for (int j = tid; j < n; j += nt) { dl = fmax(dl, widen(fabsf(y[j]))); xl = fmax(xl, fabs(x[j])); }
                 const double dn = block_max(dl, red), xn = block_max(xl, red);
                 if (!(dn <= 0.5 * prev)) { ok = false; break; }
-                for (int j = tid; j < n; j += nt) x[j] += (double)y[j];
+                for (int j = tid; j < n; j += nt) x[j] += widen(y[j]);
                 __syncthreads();
                 prev = dn;
                 if (dn <= 1e-15 * xn) break;
