@@ -40,6 +40,8 @@ size_t tc3_image_bytes(int m);
 void tc3_build_images(int n, int m, const double *G, unsigned char *img);
 int launch_tc3(int mode, const Model &M, Batch Bt, const unsigned char *img, int *err, int sel, cudaStream_t s);
 int launch_abar_tc3(const Model &M, Batch Bt, const unsigned char *img, double *Bsum, int *err, cudaStream_t s);
+int launch_abar_tcp(const Model &M, Batch Bt, const unsigned char *img, double *Bsum, int *err, cudaStream_t s);
+
 void launch_force(const Model &M, Batch Bt, bool fp64, cudaStream_t s);
 void launch_geometry(const Model &M, const double *mu, int64_t B, double *geo, cudaStream_t s);
 int launch_sensitivity(const Model &M, Batch Bt, int precision, double *out, cudaStream_t s);
@@ -682,6 +684,16 @@ static void prof_collect(rom_ctx *ctx) {
     ctx->recs.clear();
 }
 
+// the effective-stiffness sums of the converged instances on the tensor cores (3D: k_abar_tc3,
+// 2D: k_abar_tcp), for the tensor-core paths of models with n <= 64
+static bool tc_sums_path(const rom_ctx *ctx, const Model &M) {
+    return M.n_par <= MAX_NPAR && ((M.d == 3 && ctx->tc3_img) || (M.d == 2 && ctx->tc_img[1]));
+}
+static int launch_abar_sums(const rom_ctx *ctx, const Model &M, Batch bc, double *Bsum, cudaStream_t s) {
+    return M.d == 3 ? launch_abar_tc3(M, bc, ctx->tc3_img, Bsum, ctx->d_err, s)
+                    : launch_abar_tcp(M, bc, ctx->tc_img[1], Bsum, ctx->d_err, s);
+}
+
 // the stiffness K runs on the tensor cores (and the residual in its own kernel, launch_force)
 // for models with n <= 64 at every precision but FP64
 static bool tc_path(const rom_ctx *ctx, const Model &M, int precision) {
@@ -781,9 +793,9 @@ static rom_status run_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts, co
         n_act = ctx->h_count[0];
         if (n_act == 0) break;
     }
-    // 3D tensor-core paths: the sums B = sum_i G_i^T Ahat_i of the effective stiffness on the
-    // tensor cores as well (k_abar_tc3 over the converged instances); the finalize then reads them
-    const bool tc_sums = tcp && M.d == 3 && ctx->tc3_img && o.want_abar;
+    // tensor-core paths: the sums B = sum_i G_i^T Ahat_i and A0 of the effective stiffness on the
+    // tensor cores as well (over the converged instances); the finalize then reads them
+    const bool tc_sums = tcp && tc_sums_path(ctx, M) && o.want_abar;
     if (tcp) {
         if ((o.precision >= 2 && o.want_abar) || tc_sums) {
             Batch bc = bt;
@@ -791,7 +803,7 @@ static rom_status run_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts, co
             launch_list_converged(bc, ctx->stream);
             if (o.precision >= 2)
                 timed(ctx, 2, 0.0, [&] { return launch_abar_assembly(ctx, M, bc, o, lists[1], ctx->stream); });
-            if (tc_sums && timed(ctx, 4, 0.0, [&] { return launch_abar_tc3(M, bc, ctx->tc3_img, st->bt.Bsum, ctx->d_err, ctx->stream); }))
+            if (tc_sums && timed(ctx, 4, 0.0, [&] { return launch_abar_sums(ctx, M, bc, st->bt.Bsum, ctx->stream); }))
                 return fail(ctx, ROM_E_ARG, "rom_step: tensor-core Abar sums not available for this model");
         }
         CK(cudaMemcpyAsync(ctx->h_count + 4, ctx->d_err, 4, cudaMemcpyDeviceToHost, ctx->stream));
@@ -884,12 +896,12 @@ static cudaError_t record_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts
         }
         if (bs) cudaStreamDestroy(bs);
     }
-    const bool tc_sums = tc_path(ctx, M, o.precision) && M.d == 3 && ctx->tc3_img && o.want_abar;
+    const bool tc_sums = tc_path(ctx, M, o.precision) && tc_sums_path(ctx, M) && o.want_abar;
     if (e == cudaSuccess && ((o.precision >= 2 && o.want_abar) || tc_sums)) {
         Batch bc = bt;
         launch_list_converged(bc, cs);
         if (o.precision >= 2) bad |= launch_abar_assembly(ctx, M, bc, o, st->list2, cs);
-        if (tc_sums) bad |= launch_abar_tc3(M, bc, ctx->tc3_img, st->bt.Bsum, ctx->d_err, cs);
+        if (tc_sums) bad |= launch_abar_sums(ctx, M, bc, st->bt.Bsum, cs);
     }
     Batch bf = bt;
     bf.Bsum = tc_sums ? st->bt.Bsum : nullptr;

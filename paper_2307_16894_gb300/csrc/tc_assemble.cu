@@ -489,6 +489,285 @@ __global__ void __launch_bounds__(256) k_force_df(Model M, Batch Bt) {
 }
 
 
+// ---------------------------------------------------------------- Abar sums on the tensor cores (2D)
+// k_abar_tcp: the 2D counterpart of k_abar_tc3.  For the converged instances B_b = sum_i G_i^T
+// Ahat_i (n x 4) and A0_b (16), Ahat_i[ar][(k,l)] = sum_s At_i[ar][(k,s)] F_mu,i[l][s], FP32-accurate
+// by the TF32 hi/lo split.  B_b^T = Ahat_b^T G with 32 instances packed along M (rows (s, kl),
+// all 128 used), N = n rounded up to 16, K = (point, component) in the chunks of 8 points of the
+// packed stiffness kernel's TF32 image of G (its B operand here too).  Producer thread (point,
+// instance, k) forms the rows (s, 2k + l), l = 0, 1, and accumulates A0 in FP32; the control
+// thread copies the chunk's B tiles (one bulk copy of hi and lo) and issues 12 MMAs per chunk.
+// Output Bsum[b] = [B_b (n x 4) | A0_b (16)].  Every wait is bounded (1 s; error flag, drain).
+namespace tca2 {
+constexpr int D = 2, D2 = 4, D4 = 16;
+constexpr int S = 32;                              // instances per CTA (32 x 4 = 128 rows)
+constexpr int PC = 8;                              // points per chunk (the TF32 image's chunks)
+constexpr int NPROD = 256, THREADS = NPROD + 32;
+constexpr int A_BYTES = tcp::A_BYTES;              // 128 rows x 8 units of 16 bytes
+constexpr int AS_FLOATS = S * D4 * PC;             // staged tangents [S][16][8]
+constexpr int FM_FLOATS = S * PC * D2;             // F_mu [S][8][4]
+constexpr int GM_FLOATS = D2 * MAX_NPAR * PC;      // geometric-map gradients of a chunk
+}  // namespace tca2
+
+__global__ void __launch_bounds__(tca2::THREADS, 1)
+    k_abar_tcp(Model M, Batch Bt, const unsigned char *__restrict__ img, tcp::Geom g, double *__restrict__ Bsum,
+               int *err_flag) {
+    using namespace tcx;
+    using namespace tca2;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar_full[2], bar_afull[2], bar_mma[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int64_t bI[S];
+    __shared__ float muS[S][MAX_NPAR];
+    __shared__ volatile int abort_s;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n_act = Bt.counts[0];
+    const int p0 = S * blockIdx.x;
+    if (p0 >= n_act) return;
+    const int n = M.n, m = M.m, mA = M.mA, np = M.n_par, NB = g.NB, nch = g.nch;
+    const float *At = reinterpret_cast<const float *>(Bt.At);
+    const int stage = 2 * A_BYTES + 2 * g.b_bytes;
+    auto a_tile = [&](int st, int t) { return smem + (size_t)st * stage + (size_t)t * A_BYTES; };
+    auto b_tile = [&](int st) { return smem + (size_t)st * stage + 2 * (size_t)A_BYTES; };   // hi, then lo
+    float *const As0 = reinterpret_cast<float *>(smem + 2 * (size_t)stage);   // buffer t at As0 + t * AS_FLOATS
+    float *const Fms = As0 + 2 * AS_FLOATS;
+    float *const Gm0 = Fms + FM_FLOATS;                                         // buffer t at Gm0 + t * GM_FLOATS
+
+    if (tid < S) bI[tid] = (p0 + tid < n_act) ? (int64_t)Bt.list[p0 + tid] : -1;
+    for (int e = tid; e < S * np; e += THREADS) {
+        const int s = e / np, k = e - s * np;
+        muS[s][k] = (p0 + s < n_act) ? to_tangent<float>(Bt.mu[(int64_t)Bt.list[p0 + s] * np + k]) : 0.f;
+    }
+    if (warp == NPROD / 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(256));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int st = 0; st < 2; ++st) {
+            mbar_init(&bar_full[st], 1);
+            mbar_init(&bar_afull[st], NPROD);
+            mbar_init(&bar_mma[st], 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_s = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+
+    if (tid < NPROD) {
+        // ------------------------------------------------------------------ producers
+        // tangent rows (instance s, component ce) of chunk c: two 16-byte pieces of 4 points (zeros
+        // for absent instances and points past m), and the chunk's geometric-map gradients
+        auto prefetch = [&](int c, int buf) {
+            const int c0 = c * PC;
+            for (int e = tid; e < S * D4 * 2; e += NPROD) {
+                const int h = e & 1, row = e >> 1;
+                const int s = row / D4, ce = row - s * D4;
+                const int64_t b = bI[s];
+                const int q0 = c0 + 4 * h;
+                float *dst = As0 + (size_t)buf * AS_FLOATS + (size_t)row * PC + 4 * h;
+                if (b >= 0 && q0 + 4 <= m) {
+                    cp_async16(dst, At + ((size_t)b * D4 + ce) * mA + q0);
+                } else {
+                    const float *src = At + ((size_t)(b >= 0 ? b : 0) * D4 + ce) * mA + q0;
+                    float4 v;
+                    v.x = (b >= 0 && q0 + 0 < m) ? src[0] : 0.f;
+                    v.y = (b >= 0 && q0 + 1 < m) ? src[1] : 0.f;
+                    v.z = (b >= 0 && q0 + 2 < m) ? src[2] : 0.f;
+                    v.w = (b >= 0 && q0 + 3 < m) ? src[3] : 0.f;
+                    *reinterpret_cast<float4 *>(dst) = v;
+                }
+            }
+            for (int e = tid; e < D2 * np * PC; e += NPROD) {
+                const int qk = e / PC, pt = e - qk * PC;
+                Gm0[(size_t)buf * GM_FLOATS + e] = (c0 + pt < m) ? to_tangent<float>(M.Gmu_T[(size_t)qk * m + c0 + pt]) : 0.f;
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        prefetch(0, 0);
+        // thread (point pt, instance s, k): rows (s, 2 k + l), l = 0, 1; two such items per thread
+        float a0[2][D][D2];
+#pragma unroll
+        for (int t = 0; t < 2; ++t)
+#pragma unroll
+            for (int l = 0; l < D; ++l)
+#pragma unroll
+                for (int q = 0; q < D2; ++q) a0[t][l][q] = 0.f;
+        int local_abort = 0;
+        for (int c = 0; c < nch; ++c) {
+            const int st = c & 1, c0 = c * PC;
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            if (bar_or_id(1, NPROD, local_abort | abort_s)) break;   // also: chunk c's tangents visible
+            if (c + 1 < nch) prefetch(c + 1, (c + 1) & 1);
+            const float *gm = Gm0 + (size_t)(c & 1) * GM_FLOATS;
+            for (int e = tid; e < S * PC * D2; e += NPROD) {
+                const int s = e / (PC * D2), rem = e - s * (PC * D2);
+                const int pt = rem / D2, q = rem - pt * D2;
+                float v = 0.f;
+                if (bI[s] >= 0 && c0 + pt < m) {
+                    v = (q % 3 == 0) ? 1.f : 0.f;
+                    for (int k = 0; k < np; ++k) v = fmaf(muS[s][k], gm[(q * np + k) * PC + pt], v);
+                }
+                Fms[(s * PC + pt) * D2 + q] = v;
+            }
+            bar_or_id(2, NPROD, 0);
+            const uint32_t par = (uint32_t)(c >> 1) & 1u;
+            if (!mbar_wait(&bar_full[st], par, &abort_s)) { local_abort = 1; continue; }
+            if (c >= 2 && !mbar_wait(&bar_mma[st], par ^ 1u, &abort_s)) { local_abort = 1; continue; }
+            const float *as = As0 + (size_t)(c & 1) * AS_FLOATS;
+            unsigned char *Ahi = a_tile(st, 0), *Alo = a_tile(st, 1);
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                const int it = tid + t * NPROD;                   // < PC * S * D = 512
+                const int pt = it / (S * D), rest = it - pt * (S * D);
+                const int s = rest / D, k = rest - s * D;
+                const float *fm = Fms + (s * PC + pt) * D2;
+                const float f0 = fm[0], f1 = fm[1], f2 = fm[2], f3 = fm[3];
+                const float *a = as + (size_t)s * D4 * PC + pt;
+                float y[D][D2];
+#pragma unroll
+                for (int ar = 0; ar < D2; ++ar) {
+                    const int ce = ar * D2 + k * D;
+                    const float t0 = a[ce * PC], t1 = a[(ce + 1) * PC];
+                    y[0][ar] = fmaf(t1, f1, t0 * f0);
+                    y[1][ar] = fmaf(t1, f3, t0 * f2);
+                }
+#pragma unroll
+                for (int l = 0; l < D; ++l) {
+#pragma unroll
+                    for (int ia = 0; ia < D; ++ia)
+#pragma unroll
+                        for (int jb = 0; jb < D; ++jb)
+                            a0[t][l][ia * D + jb] = fmaf(fm[jb * D + 1], y[l][ia * D + 1], fmaf(fm[jb * D], y[l][ia * D], a0[t][l][ia * D + jb]));
+                    uint32_t h[D2], lo[D2];
+#pragma unroll
+                    for (int q = 0; q < D2; ++q) {
+                        h[q] = tf32_bits(y[l][q]);
+                        lo[q] = tf32_bits(y[l][q] - __uint_as_float(h[q]));
+                    }
+                    const int r = s * D2 + k * D + l;
+                    const size_t off = (size_t)(r >> 3) * tcp::SBO_A + (size_t)pt * 128 + (size_t)(r & 7) * 16;
+                    *reinterpret_cast<uint4 *>(Ahi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+                    *reinterpret_cast<uint4 *>(Alo + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(&bar_afull[st]);
+        }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        // A0: the eight point partial sums of each row added in a fixed order
+        const int quit = bar_or_id(1, NPROD, local_abort | abort_s);
+        float *red = As0;                                    // [PC][S * 4][4]
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const int it = tid + t * NPROD;
+            const int pt = it / (S * D), rest = it - pt * (S * D);
+            const int s = rest / D, k = rest - s * D;
+#pragma unroll
+            for (int l = 0; l < D; ++l)
+#pragma unroll
+                for (int q = 0; q < D2; ++q) red[((size_t)pt * S * D2 + s * D2 + k * D + l) * D2 + q] = a0[t][l][q];
+        }
+        bar_or_id(2, NPROD, 0);
+        if (!quit)
+            for (int e = tid; e < S * D2 * D2; e += NPROD) {
+                const int row = e / D2, q = e - row * D2;        // row = s * 4 + kl
+                const int s = row / D2, kl = row - s * D2;
+                if (bI[s] < 0) continue;
+                double v = 0.0;
+#pragma unroll
+                for (int pt = 0; pt < PC; ++pt) v += f2d_exact(red[((size_t)pt * S * D2 + row) * D2 + q]);
+                Bsum[(size_t)bI[s] * (n * D2 + D4) + (size_t)n * D2 + q * D2 + kl] = v;
+            }
+    } else if (lane == 0) {
+        // ------------------------------------------------------------- control thread
+        uint32_t copy_pending = 0, copy_par = 0;
+        int mma_pending = 0;
+        uint32_t mma_par = 0;
+        int mma_stage = 0;
+        const uint32_t idesc = make_idesc(2u, tcp::MROWS, NB);
+        auto issue_copies = [&](int c) {
+            const int st = c & 1;
+            mbar_expect_tx(&bar_full[st], 2u * g.b_bytes);
+            bulk_g2s(b_tile(st), img + (size_t)c * g.chunk_bytes + g.g32_bytes, 2u * g.b_bytes, &bar_full[st]);
+            copy_pending |= 1u << st;
+            copy_par = (copy_par & ~(1u << st)) | (((uint32_t)(c >> 1) & 1u) << st);
+        };
+        issue_copies(0);
+        if (nch > 1) issue_copies(1);
+        for (int c = 0; c < nch; ++c) {
+            const int st = c & 1;
+            const uint32_t par = (uint32_t)(c >> 1) & 1u;
+            if (!mbar_wait(&bar_full[st], par, &abort_s)) break;
+            copy_pending &= ~(1u << st);
+            if (!mbar_wait(&bar_afull[st], par, &abort_s)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t ah = smem_u32(a_tile(st, 0)), al = smem_u32(a_tile(st, 1));
+            const uint32_t bh = smem_u32(b_tile(st)), bl = bh + (uint32_t)g.b_bytes;
+            const uint32_t dh = tmem + (uint32_t)((c % g.NH) * g.AS), dl = tmem + (uint32_t)(g.NH * g.AS);
+#pragma unroll
+            for (int k = 0; k < tcp::NK; ++k) {
+                const uint64_t adh = make_desc(ah + k * 256, 128, tcp::SBO_A);
+                const uint64_t bdh = make_desc(bh + k * 256, 128, tcp::SBO_B);
+                mma_tf32(dh, adh, bdh, idesc, (c >= g.NH || k > 0) ? 1u : 0u);
+                mma_tf32(dl, make_desc(al + k * 256, 128, tcp::SBO_A), bdh, idesc, (c > 0 || k > 0) ? 1u : 0u);
+                mma_tf32(dl, adh, make_desc(bl + k * 256, 128, tcp::SBO_B), idesc, 1u);
+            }
+            mma_commit(&bar_mma[st]);
+            mma_pending = 1;
+            mma_par = par;
+            mma_stage = st;
+            if (c + 2 < nch) {
+                if (!mbar_wait(&bar_mma[st], par, &abort_s)) break;
+                issue_copies(c + 2);
+            }
+        }
+        if (mma_pending && !mbar_wait(&bar_mma[mma_stage], mma_par, &abort_s)) mbar_drain(&bar_mma[mma_stage], mma_par);
+        for (int st = 0; st < 2; ++st)
+            if ((copy_pending >> st) & 1u) mbar_drain(&bar_full[st], (copy_par >> st) & 1u);
+        if (abort_s && err_flag) atomicExch(err_flag, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!abort_s && tid < NPROD) {
+        // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (rows s * 4 + kl) and the
+        // 16-column groups w / 4, w / 4 + 2, ...; accumulators added in FP32 in a fixed order
+        const int row = (warp & 3) * 32 + lane;
+        const int s = row / D2, kl = row - s * D2;
+        const bool ok = bI[s] >= 0;
+        double *Bb = ok ? Bsum + (size_t)bI[s] * (n * D2 + D4) + kl : nullptr;
+        const int nh_used = nch < g.NH ? nch : g.NH;
+        for (int c16 = warp >> 2; c16 < NB / 16; c16 += NPROD / 128) {
+            float acc[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) acc[q] = 0.f;
+            for (int ai = 0; ai < g.NACC; ++ai) {
+                if (ai >= nh_used && ai < g.NH) continue;
+                uint32_t r[16];
+                tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(ai * g.AS + c16 * 16), r);
+                tmem_wait_ld();
+#pragma unroll
+                for (int q = 0; q < 16; ++q) acc[q] += __uint_as_float(r[q]);
+            }
+            if (ok)
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    if (c16 * 16 + q < n) Bb[(size_t)(c16 * 16 + q) * D2] = f2d_exact(acc[q]);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == NPROD / 32) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+    }
+}
+
 // ------------------------------------------------------------------------ host side
 
 // geometry of the packed 2D kernel for a model (mode 1 BF16, 2 TF32, 3 TF32 split)
@@ -563,6 +842,20 @@ static int launch_tcp_t(const Model &M, Batch Bt, const unsigned char *img, int 
     cudaFuncSetAttribute(k_assemble_tcp<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, g.smem);
     const int grid = (int)((Bt.B + g.S - 1) / g.S);
     k_assemble_tcp<MODE><<<grid, tcp::THREADS, g.smem, s>>>(M, Bt, img, g, err, sel);
+    return 0;
+}
+
+// B_b = sum_i G_i^T Ahat_i [n][4] and A0_b [16] of the listed (converged) 2D instances on the
+// tensor cores, from the TF32 image (fmt 2) of the packed stiffness kernel
+int launch_abar_tcp(const Model &M, Batch Bt, const unsigned char *img, double *Bsum, int *err, cudaStream_t s) {
+    using namespace tca2;
+    if (M.d != 2 || M.n < 1 || M.n > 64 || (M.mA & 3) || !Bsum || M.n_par > MAX_NPAR) return -1;
+    const tcp::Geom g = tcp_geom(3, M.n, M.m);
+    const int stage = 2 * A_BYTES + 2 * g.b_bytes;
+    const int smem = 2 * stage + 2 * AS_FLOATS * 4 + FM_FLOATS * 4 + 2 * GM_FLOATS * 4;
+    cudaFuncSetAttribute(k_abar_tcp, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const int grid = (int)((Bt.B + S - 1) / S);
+    k_abar_tcp<<<grid, THREADS, smem, s>>>(M, Bt, img, g, Bsum, err);
     return 0;
 }
 
