@@ -172,6 +172,47 @@ __device__ __forceinline__ double rsqrt_near1(double x) {
 __device__ __forceinline__ double widen(double x) { return x; }
 __device__ __forceinline__ double widen(float x) { return f2d_exact(x); }
 
+// ln x near 1 and exp x near 0 by their power series (Mercator's series of ln(1 + u) and the
+// exponential series), for the Hencky strains of the trial state (eigenvalues of b_tr within a few
+// percent of 1) and the plastic update (exponents 2 dg sqrt(3/2) |nhat_a| <= 2 dg): a handful of
+// FP64 FMAs instead of the library's range reduction.  ln: u = x - 1 (exact), |u| <= 1/32, terms to
+// u^11 / 11 (truncation below 3e-18 relative); exp: |x| <= 1/16, terms to x^9 / 9! (below 3e-18
+// relative).  Outside these ranges the library functions.
+__device__ __forceinline__ double log_near1(double x) {
+    const double u = x - 1.0;
+    if (fabs(u) <= 0.03125) {
+        double p = 1.0 / 11.0;
+        p = fma(u, p, -1.0 / 10.0);
+        p = fma(u, p, 1.0 / 9.0);
+        p = fma(u, p, -1.0 / 8.0);
+        p = fma(u, p, 1.0 / 7.0);
+        p = fma(u, p, -1.0 / 6.0);
+        p = fma(u, p, 1.0 / 5.0);
+        p = fma(u, p, -1.0 / 4.0);
+        p = fma(u, p, 1.0 / 3.0);
+        p = fma(u, p, -0.5);
+        p = fma(u, p, 1.0);
+        return u * p;
+    }
+    return log(x);
+}
+
+__device__ __forceinline__ double exp_near0(double x) {
+    if (fabs(x) <= 0.0625) {
+        double p = 1.0 / 362880.0;
+        p = fma(x, p, 1.0 / 40320.0);
+        p = fma(x, p, 1.0 / 5040.0);
+        p = fma(x, p, 1.0 / 720.0);
+        p = fma(x, p, 1.0 / 120.0);
+        p = fma(x, p, 1.0 / 24.0);
+        p = fma(x, p, 1.0 / 6.0);
+        p = fma(x, p, 0.5);
+        p = fma(x, p, 1.0);
+        return fma(x, p, 1.0);
+    }
+    return exp(x);
+}
+
 // FP64-accurate symmetric 3x3 eigen-decomposition: FP32 Jacobi gives approximate
 // eigenvectors, which are made exactly orthonormal in FP64 (Gram-Schmidt + cross product; the
 // FP32 vectors have norms within ~1e-7 of 1, so their normalisation is a short series) and used
@@ -389,7 +430,7 @@ __device__ __forceinline__ void material_value(const double F[3][3], const doubl
     }
     double eps[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) eps[a] = 0.5 * log(S.lam[a]);
+    for (int a = 0; a < 3; ++a) eps[a] = 0.5 * log_near1(S.lam[a]);
     const double tr = eps[0] + eps[1] + eps[2];
     const double mean = tr * (1.0 / 3.0);
     double e[3] = {eps[0] - mean, eps[1] - mean, eps[2] - mean};
@@ -528,7 +569,7 @@ __device__ __forceinline__ void material_value(const double F[3][3], const doubl
         // b_new = N diag(lambda_a exp(-2 dg sqrt(3/2) nhat_a)) N^T (Eq. j2_10 in the spatial form)
         double ln[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) ln[a] = S.lam[a] * exp(-2.0 * S.dg * 1.2247448713915890491 * S.nh[a]);
+        for (int a = 0; a < 3; ++a) ln[a] = S.lam[a] * exp_near0(-2.0 * S.dg * 1.2247448713915890491 * S.nh[a]);
         double c[3][3];
 #pragma unroll
         for (int i = 0; i < K; ++i) {
