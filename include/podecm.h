@@ -437,9 +437,12 @@ rom_status rom_ecm_integrands(void *cuda_stream, const rom_fe_mesh *mesh, int n,
  * 10 KB per instance for n = 8, m = 40 in 2D and 42 KB for n = 24, m = 160)
  * is rejected with ROM_E_ARG.  The call allocates nothing: no cudaMalloc,
  * cudaFree or allocating library routine.
+ *  - The call synchronises the stream: every Newton pass reads the active
+ *    count back to the host, and the phase table is swapped through host
+ *    memory.  It must not be called while the stream (or any stream of the
+ *    process, in global capture mode) is being captured into a graph.
  *  - The first call on a device looks up the device address of the static
- *    array (cudaGetSymbolAddress, with that device current); make that first
- *    call before any stream capture.
+ *    array (cudaGetSymbolAddress, with that device current).
  *  - All calls on a device share the array, and it keeps the previous call's
  *    contents (the call clears what must start at zero).  Calls that overlap
  *    on the GPU -- on different streams or host threads -- race on it; so do
