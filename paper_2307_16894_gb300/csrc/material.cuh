@@ -37,13 +37,16 @@ struct PhaseD {
     int elastic;         // s0 == +inf
 };
 
-__device__ __forceinline__ double yield_stress(const PhaseD &ph, double xi, double *slope) {
+// sigma_y(xi) and its slope; for the power law also 1 / (1 + k xi) (rbase, if given)
+__device__ __forceinline__ double yield_stress(const PhaseD &ph, double xi, double *slope, double *rbase = nullptr) {
     if (ph.elastic) { *slope = 0.0; return INFINITY; }
     if (ph.law == 0) { *slope = ph.k; return ph.s0 + ph.k * xi; }
     // (1 + k xi)^p as exp(p ln(1 + k xi)): two transcendental calls instead of pow()
     const double base = 1.0 + ph.k * xi;
     const double v = ph.s0 * exp(ph.p * log(base));
-    *slope = v * ph.p * ph.k / base;
+    const double rb = 1.0 / base;
+    *slope = v * ph.p * ph.k * rb;
+    if (rbase) *rbase = rb;
     return v;
 }
 
@@ -177,24 +180,32 @@ __device__ __forceinline__ double widen(float x) { return f2d_exact(x); }
 // percent of 1) and the plastic update (exponents 2 dg sqrt(3/2) |nhat_a| <= 2 dg): a handful of
 // FP64 FMAs instead of the library's range reduction.  ln: u = x - 1 (exact), |u| <= 1/32, terms to
 // u^11 / 11 (truncation below 3e-18 relative); exp: |x| <= 1/16, terms to x^9 / 9! (below 3e-18
-// relative).  Outside these ranges the library functions.
+// relative).  Outside these ranges the library functions.  The same series give the power-law
+// yield stress after an increment from the known sigma_y(xi_n) (see power_increment).
+__device__ __forceinline__ double log1p_series(double u) {   // |u| <= 1/32
+    double p = 1.0 / 11.0;
+    p = fma(u, p, -1.0 / 10.0);
+    p = fma(u, p, 1.0 / 9.0);
+    p = fma(u, p, -1.0 / 8.0);
+    p = fma(u, p, 1.0 / 7.0);
+    p = fma(u, p, -1.0 / 6.0);
+    p = fma(u, p, 1.0 / 5.0);
+    p = fma(u, p, -1.0 / 4.0);
+    p = fma(u, p, 1.0 / 3.0);
+    p = fma(u, p, -0.5);
+    p = fma(u, p, 1.0);
+    return u * p;
+}
+
 __device__ __forceinline__ double log_near1(double x) {
     const double u = x - 1.0;
-    if (fabs(u) <= 0.03125) {
-        double p = 1.0 / 11.0;
-        p = fma(u, p, -1.0 / 10.0);
-        p = fma(u, p, 1.0 / 9.0);
-        p = fma(u, p, -1.0 / 8.0);
-        p = fma(u, p, 1.0 / 7.0);
-        p = fma(u, p, -1.0 / 6.0);
-        p = fma(u, p, 1.0 / 5.0);
-        p = fma(u, p, -1.0 / 4.0);
-        p = fma(u, p, 1.0 / 3.0);
-        p = fma(u, p, -0.5);
-        p = fma(u, p, 1.0);
-        return u * p;
-    }
+    if (fabs(u) <= 0.03125) return log1p_series(u);
     return log(x);
+}
+
+__device__ __forceinline__ double log1p_near0(double u) {
+    if (fabs(u) <= 0.03125) return log1p_series(u);
+    return log1p(u);
 }
 
 __device__ __forceinline__ double exp_near0(double x) {
@@ -211,6 +222,19 @@ __device__ __forceinline__ double exp_near0(double x) {
         return fma(x, p, 1.0);
     }
     return exp(x);
+}
+
+// power-law yield stress after a plastic increment x from xi_n, from sy_n = sigma_y(xi_n) and
+// rb_n = 1 / (1 + k xi_n): 1 + k (xi_n + x) = (1 + k xi_n)(1 + u) with u = k x rb_n, so
+// sigma_y(xi_n + x) = sy_n (1 + u)^p = sy_n exp(p ln(1 + u)), and the slope is
+// p k sigma_y / (1 + k (xi_n + x)).  Return-map increments keep |u| and |p ln(1 + u)| inside
+// the ranges of the short series; larger ones take the library functions.
+__device__ __forceinline__ double power_increment(const PhaseD &ph, double sy_n, double rb_n, double x,
+                                                  double *slope) {
+    const double u = ph.k * x * rb_n;
+    const double v = sy_n * exp_near0(ph.p * log1p_near0(u));
+    *slope = v * ph.p * ph.k * rb_n / (1.0 + u);
+    return v;
 }
 
 // FP64-accurate symmetric 3x3 eigen-decomposition: FP32 Jacobi gives approximate
@@ -452,8 +476,8 @@ __device__ __forceinline__ void material_value(const double F[3][3], const doubl
         syf = s0f * expf(pf * logf(1.f + kf * xin));
         maybe_plastic = qf >= syf * (1.f - 1e-5f);
     }
-    double h0 = 0.0, sy_n = 0.0;
-    if (maybe_plastic) sy_n = yield_stress(ph, xi_n, &h0);
+    double h0 = 0.0, sy_n = 0.0, rb_n = 0.0;
+    if (maybe_plastic) sy_n = yield_stress(ph, xi_n, &h0, &rb_n);
     S.plastic = maybe_plastic && (S.q_tr - sy_n) > 1e-12 * sy_n;
     S.dg = 0.0;
     S.beta = 1.0;
@@ -465,14 +489,14 @@ __device__ __forceinline__ void material_value(const double F[3][3], const doubl
         // loop stops once a step is below 1e-6 |dg| (otherwise at 1e-15 |dg|, as from the FP64
         // linearised start)
         bool conv32 = false;
-        float xf = 0.f;
+        float xf = 0.f, hsf = 0.f;
         if (pw) {
             const float g3 = to_tangent<float>(3.0 * G);
             xf = (qf - syf) / (g3 + syf * pf * kf / (1.f + kf * xin));
             for (int it = 0; it < 30; ++it) {
                 const float base = 1.f + kf * (xin + xf);
                 const float sy = s0f * expf(pf * logf(base));
-                const float hsf = sy * pf * kf / base;
+                hsf = sy * pf * kf / base;
                 const float step = (qf - g3 * xf - sy) / (g3 + hsf);
                 xf += step;
                 if (fabsf(step) <= 1e-6f * fabsf(xf)) { conv32 = isfinite(xf) && xf > 0.f; break; }
@@ -480,21 +504,31 @@ __device__ __forceinline__ void material_value(const double F[3][3], const doubl
         }
         double x = conv32 ? f2d_exact(xf) : (S.q_tr - sy_n) / (3.0 * G + h0);
         double hs = h0;
-        for (int it = 0; it < 60; ++it) {
-            const double sy = yield_stress(ph, xi_n + x, &hs);
-            const double step = (S.q_tr - 3.0 * G * x - sy) / (3.0 * G + hs);
-            x += step;
-            if (fabs(step) <= 1e-15 * fabs(x)) break;
-            if (conv32 && fabs(step) <= 1e-6 * fabs(x)) break;
-        }
-        if (FP64_SLOPE) {
-            yield_stress(ph, xi_n + x, &hs);
-        } else if (ph.law == 1) {
-            // slope for the (FP32) tangent only
-            const float base = 1.f + kf * (xin + to_tangent<float>(x));
-            hs = f2d_exact(s0f * expf(pf * logf(base)) * pf * kf / base);
+        if (!FP64_SLOPE && conv32) {
+            // FP32 tangent: one FP64 Newton step from the FP32 solution (relative error ~1e-7) on
+            // the FP64 residual, with the FP32 slope in the denominator (its ~1e-7 relative error
+            // moves the result by ~1e-14 of the step); that slope also serves the FP32 tangent
+            hs = f2d_exact(hsf);
+            const double sy = sy_n * exp_near0(ph.p * log1p_near0(ph.k * x * rb_n));
+            x += (S.q_tr - 3.0 * G * x - sy) / (3.0 * G + hs);
         } else {
-            hs = ph.k;
+            for (int it = 0; it < 60; ++it) {
+                const double sy = pw ? power_increment(ph, sy_n, rb_n, x, &hs) : yield_stress(ph, xi_n + x, &hs);
+                const double step = (S.q_tr - 3.0 * G * x - sy) / (3.0 * G + hs);
+                x += step;
+                if (fabs(step) <= 1e-15 * fabs(x)) break;
+                if (conv32 && fabs(step) <= 1e-6 * fabs(x)) break;
+            }
+            if (FP64_SLOPE) {
+                if (pw) power_increment(ph, sy_n, rb_n, x, &hs);
+                else yield_stress(ph, xi_n + x, &hs);
+            } else if (ph.law == 1) {
+                // slope for the (FP32) tangent only
+                const float base = 1.f + kf * (xin + to_tangent<float>(x));
+                hs = f2d_exact(s0f * expf(pf * logf(base)) * pf * kf / base);
+            } else {
+                hs = ph.k;
+            }
         }
         S.dg = x;
         S.hs = hs;

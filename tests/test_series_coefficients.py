@@ -14,9 +14,9 @@ import pytest
 SRC = pathlib.Path(__file__).resolve().parents[1] / "paper_2307_16894_gb300" / "csrc" / "material.cuh"
 
 
-def _body(name):
+def _body(name, arg="x"):
     s = SRC.read_text()
-    i = s.index("double %s(double x)" % name)
+    i = s.index("double %s(double %s)" % (name, arg))
     j = s.index("\n}\n", i)
     return s[i:j]
 
@@ -30,12 +30,15 @@ def _num(expr):
     return float(expr)
 
 
+def _guard(body, var):
+    return float(re.search(r"fabs\(%s\) <= ([0-9.]+)" % var, body).group(1))
+
+
 def _horner(name, var):
-    body = _body(name)
+    body = _body(name, var)
     seed = re.search(r"double p = ([^;]+);", body).group(1)
     steps = re.findall(r"p = fma\(%s, p, ([^)]+)\);" % var, body)
-    guard = float(re.search(r"fabs\(%s\) <= ([0-9.]+)" % var, body).group(1))
-    return [_num(seed)] + [_num(c) for c in steps], guard, body
+    return [_num(seed)] + [_num(c) for c in steps], body
 
 
 def _eval(coef, t):
@@ -46,9 +49,12 @@ def _eval(coef, t):
 
 
 def test_log_near1_series():
-    coef, guard, body = _horner("log_near1", "u")
-    assert guard == 1 / 32
-    assert "return u * p;" in body and "return log(x);" in body
+    coef, body = _horner("log1p_series", "u")
+    assert "return u * p;" in body
+    for name, arg, fallback in (("log_near1", "x", "return log(x);"), ("log1p_near0", "u", "return log1p(u);")):
+        b = _body(name, arg)
+        assert _guard(b, "u") == 1 / 32 and "return log1p_series(u);" in b and fallback in b
+    guard = 1 / 32
     assert len(coef) == 11                                     # terms u .. u^11
     x = np.linspace(1 - guard, 1 + guard, 100_001)
     u = x - 1.0
@@ -60,7 +66,8 @@ def test_log_near1_series():
 
 
 def test_exp_near0_series():
-    coef, guard, body = _horner("exp_near0", "x")
+    coef, body = _horner("exp_near0", "x")
+    guard = _guard(body, "x")
     assert guard == 1 / 16
     assert "return fma(x, p, 1.0);" in body and "return exp(x);" in body
     assert len(coef) == 9                                      # terms x .. x^9 (plus the 1)
