@@ -55,12 +55,12 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12    # 152 SMs x 128 FFMA/clk x 2
 #       python bench.py [--workload c2] [--batch 2048] [--precision fp64 --start plain] --steps 1 \
 #       --warmup 10 --no-graphs --no-cpu --no-e2e --no-fp64-arm --no-full-path --profile-range
 # (the yield filter makes elastic points cheaper, so the count depends on the plastic fraction)
-CONST_FP64_FLOP_PER_POINT = {(3, "mixed"): 1367.3, (3, "fp64"): 5978.2, (2, "mixed"): 691.5, (2, "fp64"): 1593.4}
+CONST_FP64_FLOP_PER_POINT = {(3, "mixed"): 1225.9, (3, "fp64"): 5828.2, (2, "mixed"): 544.7, (2, "fp64"): 1433.9}
 # DRAM bytes (read + write) per evaluated point of the mixed-path constitutive kernel, from the same
-# captures with dram__bytes_read.sum and dram__bytes_write.sum added: c3 1298 MB / 2048 x 600 points
+# captures with dram__bytes_read.sum and dram__bytes_write.sum added: c3 1293 MB / 2048 x 600 points
 # (algorithmic ~660 per point; the rest is register-spill traffic of the five-block configuration
 # written back from L2), c2 105 MB / 4096 x 160 points
-CONST_DRAM_BYTES_PER_POINT = {(3, "mixed"): 1056.5, (2, "mixed"): 160.6}
+CONST_DRAM_BYTES_PER_POINT = {(3, "mixed"): 1052.1, (2, "mixed"): 161.0}
 
 
 def parse():
