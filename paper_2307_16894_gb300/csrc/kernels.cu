@@ -104,6 +104,8 @@ __global__ void k_start(Model M, Batch Bt, const double *__restrict__ Fbar, Step
 __global__ void k_set_counts(int32_t *counts, int64_t B) {
     counts[0] = (int32_t)B;
     counts[1] = 0;
+    counts[4] = 0;   // front / back positions of the final-pass partition (k_flag_final)
+    counts[5] = 0;
 }
 
 __global__ void k_advance(int32_t *counts) {
@@ -702,6 +704,16 @@ constexpr int ESC_ITERS = 4;
 // machine on the same values, so all branches are uniform over the block
 constexpr int SOLVE_THREADS = 128;
 
+// Euclidean norm of the reduced residual r[0..n) by one warp: lane-strided partial sums, then a
+// butterfly over the warp (every lane gets the total).  The solve's convergence test and the
+// final-pass flag (k_flag_final) both use this function, so they see the same bits.
+__device__ __forceinline__ double warp_residual_norm(const double *r, int n, int lane) {
+    double s = 0.0;
+    for (int j = lane; j < n; j += 32) s += r[j] * r[j];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    return sqrt(s);
+}
+
 __global__ void __launch_bounds__(SOLVE_THREADS) k_solve(Model M, Batch Bt, StepOpts o, int32_t *list_next) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double bc_rn;
@@ -715,11 +727,9 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve(Model M, Batch Bt, Step
     double *A = reinterpret_cast<double *>(smem);
     double *x = reinterpret_cast<double *>(smem + solve_region_bytes(n, o.precision));
     const double *r = Bt.r + b * n;
-    if (tid < 32) {   // residual norm: lane-strided partial sums, then a butterfly over the warp
-        double s = 0.0;
-        for (int j = tid; j < n; j += 32) s += r[j] * r[j];
-        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-        if (tid == 0) bc_rn = sqrt(s);
+    if (tid < 32) {
+        const double v = warp_residual_norm(r, n, tid);
+        if (tid == 0) bc_rn = v;
     }
     __syncthreads();
     const double rn = bc_rn;
@@ -839,6 +849,44 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_solve(Model M, Batch Bt, Step
             list_next[pos] = (int32_t)b;
         }
     }
+}
+
+// Tensor-core paths with a BF16/TF32 stiffness when the effective stiffness is wanted: after the
+// residual of a Newton pass and before its assembly, an instance that this pass's solve will find
+// converged (a trial evaluation in phase 1 that is accepted and meets ||r|| <= tol: the solve's
+// test on the same norm) needs its stiffness only for Abar.  It is flagged for the FP32-accurate
+// assembly now, instead of getting a low-precision K that would be discarded and an accurate one
+// after the Newton loop.  The list is then reordered, the flagged instances (and those flagged
+// earlier by the solve's escalation) last, so that the assembly CTAs, which take consecutive list
+// positions, hold instances of one kind.  One warp per list position; tmp holds B entries.
+__global__ void k_flag_final(Batch Bt, StepOpts o, int n, int32_t *tmp) {
+    const int n_act = Bt.counts[0];
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= n_act) return;   // whole warps leave together
+    const int32_t b = Bt.list[w];
+    const double rn = warp_residual_norm(Bt.r + (int64_t)b * n, n, lane);
+    if (lane == 0) {
+        Ctl &c = Bt.ctl[b];
+        int flag = c.acc_k;
+        if (c.phase == 1 && isfinite(rn) && rn <= c.tol && (c.ls >= o.max_ls || rn < c.rn_acc)) flag = 1;
+        c.acc_k = flag;
+        const int pos = flag ? n_act - 1 - atomicAdd(&Bt.counts[5], 1) : atomicAdd(&Bt.counts[4], 1);
+        tmp[pos] = b;
+    }
+}
+
+// the reordered list back into place; resets the partition positions for the next pass
+__global__ void k_take_list(Batch Bt, const int32_t *__restrict__ tmp) {
+    const int n_act = Bt.counts[0];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) { Bt.counts[4] = 0; Bt.counts[5] = 0; }
+    if (i < n_act) Bt.list[i] = tmp[i];
+}
+
+void launch_flag_final(const Model &M, Batch Bt, const StepOpts &o, int32_t *tmp, cudaStream_t s) {
+    k_flag_final<<<(int)((Bt.B * 32 + 255) / 256), 256, 0, s>>>(Bt, o, M.n, tmp);
+    k_take_list<<<(int)((Bt.B + 255) / 256), 256, 0, s>>>(Bt, tmp);
 }
 
 // --------------------------------------------------------------------- finalize

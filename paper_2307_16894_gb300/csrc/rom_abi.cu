@@ -47,6 +47,7 @@ void launch_geometry(const Model &M, const double *mu, int64_t B, double *geo, c
 int launch_sensitivity(const Model &M, Batch Bt, int precision, double *out, cudaStream_t s);
 bool separate_force(const Model &M, const StepOpts &o);
 void launch_list_converged(Batch Bt, cudaStream_t s);
+void launch_flag_final(const Model &M, Batch Bt, const StepOpts &o, int32_t *tmp, cudaStream_t s);
 void launch_graph_advance(Batch Bt, const int32_t *list_next, cudaGraphConditionalHandle h, int max_pass,
                           cudaStream_t s);
 void launch_reset_pass(Batch Bt, cudaStream_t s);
@@ -721,14 +722,25 @@ static int launch_assembly(rom_ctx *ctx, const Model &M, Batch bt, const StepOpt
     return launch_kernel(2, M, bt, o, nxt, s);
 }
 
-// the effective stiffness needs K at FP32 accuracy: after a BF16/TF32 solve, one FP32-accurate
-// assembly of the converged instances (list rebuilt by launch_list_converged); the residual is
-// not needed here
+// the effective stiffness needs K at FP32 accuracy: after a BF16/TF32 solve, the FP32-accurate
+// assembly of the converged instances (list rebuilt by launch_list_converged) whose last pass
+// assembled a low-precision K.  An instance with the accurate-stiffness flag got the accurate K in
+// its last pass (escalated by the solve, or flagged by k_flag_final in the pass that converged
+// it); the tensor-core kernels select the others (sel 1).  The residual is not needed here.
 static int launch_abar_assembly(rom_ctx *ctx, const Model &M, Batch bc, const StepOpts &o, int32_t *nxt,
                                 cudaStream_t s) {
+    if (M.d == 3 && ctx->tc3_img) return launch_tc3(3, M, bc, ctx->tc3_img, ctx->d_err, 1, s);
+    if (M.d == 2 && ctx->tc_img[1]) return launch_tc2(3, M, bc, ctx->tc_img[1], ctx->d_err, 1, s);
     StepOpts o32 = o;
     o32.precision = 1;
     return launch_assembly(ctx, M, bc, o32, nxt, s);
+}
+
+// BF16/TF32 stiffness on the tensor cores with Abar wanted: each Newton pass forms the residual
+// first, flags the instances that this pass converges for the accurate assembly and groups them
+// (launch_flag_final), then assembles
+static bool final_pass_flags(const rom_ctx *ctx, const Model &M, const StepOpts &o) {
+    return o.precision >= 2 && o.want_abar && tc_path(ctx, M, o.precision);
 }
 
 static rom_status run_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts, const double *Fbar_d, double *Pbar_d,
@@ -771,6 +783,7 @@ static rom_status run_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts, co
         }, 3 + 2 * ctx->mlp.L);
     }
     const int max_pass = (opts->max_iter + 1) * (opts->max_ls + 1) + 2;
+    const bool fin = final_pass_flags(ctx, M, o);
     int64_t n_act = st->B;
     for (int pass = 0; pass < max_pass; ++pass) {
         bt.list = lists[pass & 1];
@@ -781,10 +794,16 @@ static rom_status run_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts, co
             if (sepf) launch_force(M, bt, o.fp64_residual != 0, ctx->stream);
             return 0;
         };
-        if (timed(ctx, 1, na * fl_kin, [&] { return launch_kernel(1, M, bt, o, nxt, ctx->stream); }) ||
-            timed(ctx, 2, na * fl_asm, asm_launch, (M.d == 3 && tcp && o.precision >= 2) ? 2 : 1) ||
-            (sepf && timed(ctx, 7, na * fl_kin, force_launch)) ||
-            timed(ctx, 3, na * fl_lu, [&] { return launch_kernel(3, M, bt, o, nxt, ctx->stream); }) ||
+        const int asm_n = (tcp && o.precision >= 2) ? 2 : 1;
+        bool bad = timed(ctx, 1, na * fl_kin, [&] { return launch_kernel(1, M, bt, o, nxt, ctx->stream); }) != 0;
+        if (fin)
+            bad = bad || (sepf && timed(ctx, 7, na * fl_kin, force_launch)) ||
+                  timed(ctx, 5, 0.0, [&] { launch_flag_final(M, bt, o, nxt, ctx->stream); return 0; }, 2) ||
+                  timed(ctx, 2, na * fl_asm, asm_launch, asm_n);
+        else
+            bad = bad || timed(ctx, 2, na * fl_asm, asm_launch, asm_n) ||
+                  (sepf && timed(ctx, 7, na * fl_kin, force_launch));
+        if (bad || timed(ctx, 3, na * fl_lu, [&] { return launch_kernel(3, M, bt, o, nxt, ctx->stream); }) ||
             timed(ctx, 5, 0.0, [&] { return launch_kernel(5, M, bt, o, nxt, ctx->stream); }))
             return fail(ctx, ROM_E_ARG, "rom_step: basis size n=%d not supported by the assembly kernel", M.n);
         CK(cudaGetLastError());
@@ -885,9 +904,16 @@ static cudaError_t record_step(rom_ctx *ctx, rom_state *st, const rom_opts *opts
         if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             int32_t *nxt = st->list2;
+            const bool sepf = tc_path(ctx, M, o.precision) || separate_force(M, o);
             bad |= launch_kernel(1, M, bt, o, nxt, bs);
-            bad |= launch_assembly(ctx, M, bt, o, nxt, bs);
-            if (tc_path(ctx, M, o.precision) || separate_force(M, o)) launch_force(M, bt, o.fp64_residual != 0, bs);
+            if (final_pass_flags(ctx, M, o)) {
+                launch_force(M, bt, o.fp64_residual != 0, bs);
+                launch_flag_final(M, bt, o, nxt, bs);
+                bad |= launch_assembly(ctx, M, bt, o, nxt, bs);
+            } else {
+                bad |= launch_assembly(ctx, M, bt, o, nxt, bs);
+                if (sepf) launch_force(M, bt, o.fp64_residual != 0, bs);
+            }
             bad |= launch_kernel(3, M, bt, o, nxt, bs);
             launch_graph_advance(bt, nxt, h, max_pass, bs);
             cudaGraph_t out = nullptr;
