@@ -55,3 +55,19 @@ def test_rooflines_c2_fp32_on_tensor_cores(bench):
     assert a["bound"] == "tensor" and abs(a["peak"] - 1000.0) < 1e-9 and abs(a["achieved"] - 100.0) < 1e-9
     c = out["constitutive"]
     assert abs(c["achieved"] - points * bench.CONST_FP64_FLOP_PER_POINT[(2, "mixed")] / 1e12) < 1e-9
+
+
+@pytest.mark.parametrize("d,name", [(3, "k_constitutive_c3_mixed_b2048.md"), (2, "k_constitutive_c2_mixed_b4096.md")])
+def test_constants_match_the_committed_captures(bench, d, name):
+    """The per-point FP64 FLOP and DRAM constants the bench multiplies by are the ones the
+    committed ncu summaries of the constitutive kernels report, so a re-measured capture and the
+    bench cannot drift apart silently."""
+    import re
+    text = open(os.path.join(ROOT, "profiles", name)).read()
+    row = re.search(r"\| FP64 FLOP per point[^|]*\| ([0-9.]+) \| ([0-9.]+) \|", text)
+    assert row, "FLOP-per-point row missing in " + name
+    assert float(row.group(1)) == bench.CONST_FP64_FLOP_PER_POINT[(d, "mixed")]
+    assert float(row.group(2)) == bench.CONST_FP64_FLOP_PER_POINT[(d, "fp64")]
+    dram = re.search(r"\| DRAM read / write \| [0-9.]+ MB / [0-9.]+ MB = ([0-9.]+) B per point", text)
+    assert dram, "DRAM row missing in " + name
+    assert abs(float(dram.group(1)) - bench.CONST_DRAM_BYTES_PER_POINT[(d, "mixed")]) < 1.0
